@@ -1,0 +1,354 @@
+"""Pins for the CPU oracle: each test checks it against something other than itself
+(brute-force linear algebra, closed forms, continuum limits, invariants, and the
+paper's own worked example)."""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+from oracle import sph_poisson as O
+import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def geo_of(p):
+    return O.Geometry(p.r_if, p.th_if, p.nphi)
+
+
+# ------------------------------------------------------------------ O1 vs O2
+TINY = [
+    # nr, nth, nphi, grid, r_inner, outer_bc
+    (5, 4, 6, "log", 0.0, O.OUTER_MULTIPOLE),
+    (6, 5, 8, "uniform", 0.0, O.OUTER_MULTIPOLE),
+    (4, 3, 5, "rand", 0.2, O.OUTER_MULTIPOLE),
+    (5, 4, 6, "log", 0.0, O.OUTER_DIRICHLET),
+    (4, 6, 9, "uniform", 0.3, O.OUTER_DIRICHLET),
+    (3, 1, 4, "uniform", 0.0, O.OUTER_MULTIPOLE),     # one theta zone
+    (4, 4, 1, "uniform", 0.0, O.OUTER_MULTIPOLE),     # axisymmetric, Nphi = 1
+    (1, 3, 4, "uniform", 0.5, O.OUTER_MULTIPOLE),     # one radial shell
+    (7, 8, 12, "rand", 0.0, O.OUTER_MULTIPOLE),
+]
+
+
+@pytest.mark.parametrize("nr,nth,nphi,grid,rin,bc", TINY)
+def test_separated_equals_dense_lu(nr, nth, nphi, grid, rin, bc):
+    p = W.random_small(nr, nth, nphi, seed=nr * 7 + nth, grid=grid, r_inner=rin)
+    g = geo_of(p)
+    a = O.solve_separated(g, p.rho, outer_bc=bc)
+    b = O.solve_dense(g, p.rho, outer_bc=bc)
+    assert np.max(np.abs(a - b)) / np.max(np.abs(b)) <= 1e-13
+
+
+def test_separated_equals_dense_lu_nonuniform_theta():
+    p = W.random_small(5, 6, 8, seed=11, grid="log")
+    th = W.random_theta_interfaces(6, seed=3)
+    g = O.Geometry(p.r_if, th, p.nphi)
+    a = O.solve_separated(g, p.rho)
+    b = O.solve_dense(g, p.rho)
+    assert np.max(np.abs(a - b)) / np.max(np.abs(b)) <= 1e-13
+
+
+def test_backward_error_moderate_grid():
+    p = W.stellar_noise()
+    g = geo_of(p)
+    phi = O.solve_separated(g, p.rho)
+    eta, _ = O.residuals(g, phi, p.rho)
+    assert eta <= 1e-14
+
+
+# ------------------------------------------------------------ closed forms
+@pytest.mark.parametrize("bc", [O.OUTER_MULTIPOLE, O.OUTER_DIRICHLET])
+def test_gauss_law_spherical_source(bc):
+    """A spherically symmetric source excites only l=0; the conservative form then
+    fixes Phi by the enclosed mass (flux through r_{i+1/2} = G M_enc)."""
+    p = W.sphere_blob()
+    g = geo_of(p)
+    rho_r = (g.rc < 0.5).astype(float) + 0.3 * np.exp(-g.rc)
+    rho = np.broadcast_to(rho_r[:, None, None], (g.nr, g.nth, g.nphi))
+    phi = O.solve_separated(g, rho, outer_bc=bc)
+    ex = O.gauss_law_potential(g, rho_r, outer_bc=bc)
+    assert np.max(np.abs(phi - ex[:, None, None])) / np.max(np.abs(ex)) <= 1e-13
+    # log grid with an inner zero-flux boundary
+    r_if = np.logspace(-2, 0, 41)
+    g2 = O.Geometry(r_if, W.uniform_theta_interfaces(8), 8)
+    rho_r2 = 1.0 / (1.0 + (g2.rc / 0.1) ** 2)
+    phi2 = O.solve_separated(g2, np.broadcast_to(rho_r2[:, None, None], (40, 8, 8)), outer_bc=bc)
+    ex2 = O.gauss_law_potential(g2, rho_r2, outer_bc=bc)
+    assert np.max(np.abs(phi2 - ex2[:, None, None])) / np.max(np.abs(ex2)) <= 1e-13
+
+
+def test_homogeneous_sphere_second_order():
+    """Discrete Phi of a homogeneous sphere converges to the continuum potential at O(dr^2)."""
+    errs = []
+    for nr in (32, 64, 128):
+        g = O.Geometry(W.uniform_r_interfaces(nr), W.uniform_theta_interfaces(4), 4)
+        rho_r = (g.rc < 0.5).astype(float)
+        phi = O.solve_separated(g, np.broadcast_to(rho_r[:, None, None], (nr, 4, 4)))
+        ex = O.homogeneous_sphere_potential(g.rc, 0.5)
+        errs.append(np.max(np.abs(phi[:, 0, 0] - ex)) / np.max(np.abs(ex)))
+    assert errs[0] < 2e-3
+    assert 3.0 < errs[0] / errs[1] < 5.0 and 3.0 < errs[1] / errs[2] < 5.0
+
+
+def test_radial_stencil_exact_on_r_squared():
+    """On a uniform radial grid the finite-volume Delta_r of r^2 is exactly 6 away from
+    the outer boundary (the flux form integrates r^2 d(r^2)/dr exactly)."""
+    g = O.Geometry(W.uniform_r_interfaces(12), W.uniform_theta_interfaces(5), 6)
+    phi = np.broadcast_to((g.rc ** 2)[:, None, None], (12, 5, 6)).copy()
+    lap = O.apply_laplacian(g, phi, O.OUTER_DIRICHLET)
+    assert np.max(np.abs(lap[:-1] - 6.0)) <= 1e-12
+
+
+@pytest.mark.parametrize("func,eig", [
+    (lambda t, p: np.cos(t), -2.0),
+    (lambda t, p: np.sin(t) * np.cos(p), -2.0),
+    (lambda t, p: np.sin(t) ** 2 * np.sin(2 * p), -6.0),
+    (lambda t, p: (3 * np.cos(t) ** 2 - 1) * np.ones_like(p), -6.0),
+])
+def test_angular_operator_converges_to_spherical_laplacian(func, eig):
+    """Delta_hat_theta + S_j Delta_hat_phi applied to a spherical harmonic Y_l tends to
+    -l(l+1) Y_l at second order in the angular spacing (solid-angle weighted L2 norm;
+    the m=1 pole cells converge at first order in the max norm)."""
+    errs = []
+    for nth in (16, 32, 64):
+        g = O.Geometry(W.uniform_r_interfaces(2), W.uniform_theta_interfaces(nth), 2 * nth)
+        t = g.thc[:, None]
+        ph = W.phi_centres(2 * nth)[None, :]
+        u = np.broadcast_to(func(t, ph), (nth, 2 * nth)).copy()
+        e2 = (O.angular_apply(g, u) - eig * u) ** 2
+        errs.append(math.sqrt(np.sum(g.w[:, None] * e2) / (2.0 * 2 * nth)) / np.max(np.abs(eig * u)))
+    assert errs[0] < 0.02
+    assert 3.0 < errs[0] / errs[1] < 5.0 and 3.0 < errs[1] / errs[2] < 5.0
+
+
+def test_harmonic_function_second_order():
+    """x = r sin(theta) cos(phi) is harmonic: the full stencil gives O(h^2) away from
+    the radial boundaries (volume-weighted L2 norm; the pole cells are first order)."""
+    errs = []
+    for n in (8, 16, 32):
+        g = O.Geometry(W.uniform_r_interfaces(n, 0.5, 1.5), W.uniform_theta_interfaces(n), 2 * n)
+        x = (g.rc[:, None, None] * np.sin(g.thc)[None, :, None]
+             * np.cos(W.phi_centres(2 * n))[None, None, :])
+        inner = O.apply_laplacian(g, x, O.OUTER_DIRICHLET)[1:-1]
+        vol = np.broadcast_to(g.cell_volume()[1:-1, :, None], inner.shape)
+        errs.append(math.sqrt(np.sum(vol * inner ** 2) / np.sum(vol)))
+    assert 3.0 < errs[0] / errs[1] < 5.0 and 3.0 < errs[1] / errs[2] < 5.0
+
+
+# --------------------------------------------------------- conservation form
+@pytest.mark.parametrize("bc", [O.OUTER_MULTIPOLE, O.OUTER_DIRICHLET])
+def test_discrete_divergence_theorem(bc):
+    """sum_cells dV (L Phi) equals the flux through the outer surface only: every interior
+    r, theta and phi flux cancels between neighbours."""
+    p = W.random_small(5, 6, 8, seed=2, grid="rand", r_inner=0.1)
+    g = geo_of(p)
+    rng = np.random.default_rng(0)
+    phi = rng.standard_normal((5, 6, 8))
+    lap = O.apply_laplacian(g, phi, bc)
+    vol = g.cell_volume()[:, :, None]
+    grad = O.outer_gradient(g, phi[-1], bc)
+    outer = g.r_out ** 2 * g.dphi * np.sum(g.w[:, None] * grad)
+    total = np.sum(vol * lap)
+    assert abs(total - outer) <= 1e-12 * np.sum(np.abs(vol * lap))
+
+
+@pytest.mark.parametrize("bc", [O.OUTER_MULTIPOLE, O.OUTER_DIRICHLET])
+def test_volume_weighted_operator_is_symmetric(bc):
+    p = W.random_small(4, 5, 6, seed=5, grid="rand", r_inner=0.0)
+    g = geo_of(p)
+    mat = O.assemble_dense(g, bc)
+    vol = np.repeat(g.cell_volume().reshape(-1), g.nphi)
+    a = vol[:, None] * mat
+    assert np.max(np.abs(a - a.T)) <= 1e-12 * np.max(np.abs(a))
+
+
+def test_outer_operator_separated_equals_dense():
+    p = W.random_small(3, 6, 10, seed=9)
+    g = geo_of(p)
+    k = O.outer_operator_dense(g)
+    u = np.random.default_rng(1).standard_normal((6, 10))
+    a = (k @ u.reshape(-1)).reshape(6, 10)
+    b = O.outer_kappa_separated(g, u)
+    assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(a))
+
+
+def test_multipole_boundary_mimics_unbounded_domain():
+    """With sources inside r<0.5, the multipole outer boundary at r=1 reproduces the
+    solution of a grid extended far outwards (identical zones up to r=1); a Dirichlet
+    boundary at r=1 does not."""
+    nth, nphi = 8, 8
+    n_in = 32
+    r_in = W.uniform_r_interfaces(n_in)
+    ext = np.concatenate([r_in, 1.0 * np.exp(np.cumsum(np.full(160, 1.0 / 32)))])
+    th = W.uniform_theta_interfaces(nth)
+    g_in = O.Geometry(r_in, th, nphi)
+    g_ext = O.Geometry(ext, th, nphi)
+    rng = np.random.default_rng(4)
+    rho = np.zeros((len(ext) - 1, nth, nphi))
+    mask = g_ext.rc < 0.5
+    rho[mask] = rng.uniform(0, 1, (int(mask.sum()), nth, nphi))
+    far = O.solve_separated(g_ext, rho, outer_bc=O.OUTER_DIRICHLET)[:n_in]
+    mp = O.solve_separated(g_in, rho[:n_in], outer_bc=O.OUTER_MULTIPOLE)
+    di = O.solve_separated(g_in, rho[:n_in], outer_bc=O.OUTER_DIRICHLET)
+    scale = np.max(np.abs(far))
+    err_mp = np.max(np.abs(mp - far)) / scale
+    err_di = np.max(np.abs(di - far)) / scale
+    assert err_mp < 5e-3 and err_di > 20 * err_mp
+
+
+# ------------------------------------------------------------- theta basis
+def test_theta_eigenvectors_are_w_orthonormal_and_exact():
+    g = O.Geometry(W.log_r_interfaces(4), W.uniform_theta_interfaces(128), 256)
+    for m in (0, 1, 17, 64, 128):
+        lam, h = O.theta_eigen(g, m)
+        assert np.max(np.abs(h.T @ (g.w[:, None] * h) - np.eye(128))) <= 1e-13
+        d, e = O.theta_matrix(g, m)
+        b = np.diag(d) + np.diag(e, 1) + np.diag(e, -1)
+        # residual of the symmetric form T Q = Q Lambda, Q = W^(1/2) H, against ||T|| = max|lambda|
+        res = (b @ h - g.w[:, None] * h * lam[None, :]) / np.sqrt(g.w)[:, None]
+        assert np.max(np.abs(res)) <= 1e-13 * np.max(np.abs(lam))
+        assert np.all(lam <= 1e-9) and np.all(np.diff(lam) <= 0)
+        lam2 = scipy.linalg.eigh(b, np.diag(g.w), eigvals_only=True)
+        assert np.max(np.abs(np.sort(lam2)[::-1] - lam)) <= 1e-12 * np.max(np.abs(lam))
+
+
+def test_theta_matrix_matches_angular_stencil():
+    """W (Delta_hat_theta + S_j lambda_phi,m) from the tridiagonal builder equals the
+    full angular stencil acting on e_j cos(m phi)."""
+    g = O.Geometry(W.uniform_r_interfaces(2), W.random_theta_interfaces(7, seed=1), 12)
+    phc = W.phi_centres(12)
+    for m in (0, 1, 4, 6):
+        d, e = O.theta_matrix(g, m)
+        b = np.diag(d) + np.diag(e, 1) + np.diag(e, -1)
+        cos = np.cos(m * phc + 0.3)
+        for j in range(7):
+            u = np.zeros((7, 12))
+            u[j] = cos
+            a = O.angular_apply(g, u) * g.w[:, None]
+            assert np.allclose(a, b[:, j][:, None] * cos[None, :], rtol=0, atol=1e-12 * np.abs(b).max())
+
+
+def test_theta_eigenvalues_approach_continuum():
+    """Low eigenvalues approach -(m+n)(m+n+1), the spherical-harmonic values."""
+    g = O.Geometry(W.log_r_interfaces(4), W.uniform_theta_interfaces(128), 256)
+    for m in (0, 1, 2, 5):
+        lam, h = O.theta_eigen(g, m)
+        ell = m + np.arange(4)
+        ref = -ell * (ell + 1.0)
+        if m == 0:
+            assert abs(lam[0]) <= 1e-10
+            assert np.allclose(h[:, 0] * np.sign(h[0, 0]), 1.0 / math.sqrt(2.0), atol=1e-13)
+            assert np.allclose(lam[1:4], ref[1:], rtol=1e-3)
+        else:
+            assert np.allclose(lam[:4], ref, rtol=3e-3)
+
+
+def test_phi_eigenvalues_are_circulant_spectrum():
+    for nphi in (6, 8, 12, 32):
+        g = O.Geometry(W.uniform_r_interfaces(2), W.uniform_theta_interfaces(2), nphi)
+        c = np.zeros((nphi, nphi))
+        for k in range(nphi):
+            c[k, k] = -2.0
+            c[k, (k + 1) % nphi] += 1.0
+            c[k, (k - 1) % nphi] += 1.0
+        ev = np.sort(np.linalg.eigvalsh(c / g.dphi ** 2))
+        ours = np.sort(g.lambda_phi(np.arange(nphi)))
+        assert np.max(np.abs(ev - ours)) <= 1e-10 * np.max(np.abs(ev))
+
+
+def test_kappa_continuum_exponent():
+    """For lambda = -l(l+1) the exponent p is l+1: kappa = -(l+1)/r_out (r_out/r_N)^-(l+1)."""
+    for ell in range(6):
+        k = O.kappa(-ell * (ell + 1.0), 2.0, 1.5)
+        assert abs(k - (-(ell + 1) / 2.0 * (2.0 / 1.5) ** (-(ell + 1)))) <= 1e-14
+
+
+# --------------------------------------------------------- single eigenmode
+def test_single_eigenmode_reduces_to_one_radial_solve():
+    p = W.random_small(9, 6, 8, seed=3, grid="log")
+    g = geo_of(p)
+    m, ell = 3, 2
+    lam, h = O.theta_eigen(g, m)
+    phc = W.phi_centres(8)
+    q = np.random.default_rng(2).standard_normal(9)
+    ang = h[:, ell][:, None] * np.cos(m * phc)[None, :]
+    rho = q[:, None, None] * ang[None] / (4 * math.pi)
+    phi = O.solve_separated(g, rho)
+    # radial matrix read off the full operator applied to e_i (x) H_l cos(m phi)
+    kmat = O.outer_operator_dense(g)
+    j0, k0 = int(np.argmax(np.abs(h[:, ell]))), 0
+    mr = np.zeros((9, 9))
+    for i in range(9):
+        u = np.zeros((9, 6, 8))
+        u[i] = ang
+        mr[:, i] = O.apply_laplacian(g, u, O.OUTER_MULTIPOLE, kmat)[:, j0, k0] / ang[j0, k0]
+    assert np.max(np.abs(np.triu(mr, 2))) == 0 and np.max(np.abs(np.tril(mr, -2))) == 0
+    ab = np.zeros((3, 9))
+    ab[0, 1:] = np.diag(mr, 1)
+    ab[1] = np.diag(mr)
+    ab[2, :-1] = np.diag(mr, -1)
+    f = scipy.linalg.solve_banded((1, 1), ab, q)
+    ref = f[:, None, None] * ang[None]
+    assert np.max(np.abs(phi - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+# ---------------------------------------------------------------- symmetries
+def test_symmetries_shift_reflection_linearity():
+    p = W.random_small(6, 8, 12, seed=21, grid="log")
+    g = geo_of(p)
+    phi = O.solve_separated(g, p.rho)
+    sc = np.max(np.abs(phi))
+    shifted = O.solve_separated(g, np.roll(p.rho, 1, axis=2))
+    assert np.max(np.abs(shifted - np.roll(phi, 1, axis=2))) <= 1e-13 * sc
+    refl = O.solve_separated(g, p.rho[:, ::-1, :])
+    assert np.max(np.abs(refl - phi[:, ::-1, :])) <= 1e-13 * sc
+    rho2 = np.random.default_rng(5).uniform(size=p.rho.shape)
+    phi2 = O.solve_separated(g, rho2)
+    lin = O.solve_separated(g, 2.0 * p.rho - 3.0 * rho2)
+    assert np.max(np.abs(lin - (2.0 * phi - 3.0 * phi2))) <= 1e-13 * np.max(np.abs(lin))
+
+
+# ------------------------------------------------------- paper's worked example
+def _golden(name):
+    vals = {}
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.split("#")[0].strip()
+            if line:
+                k, *v = line.split()
+                vals[k] = [float(x) for x in v]
+    return vals
+
+
+@pytest.mark.slow
+def test_displaced_point_source_matches_paper():
+    """Sect. 5.1: a point source in one zone of a 550x128x256 log grid; the paper finds
+    max relative errors of about 10% next to the source."""
+    gv = _golden("point_source_sect5_1.txt")
+    nr, nth, nphi = int(gv["nr"][0]), int(gv["ntheta"][0]), int(gv["nphi"][0])
+    r_if = np.logspace(math.log10(gv["r_in"][0]), math.log10(gv["r_out"][0]), nr + 1)
+    g = O.Geometry(r_if, W.uniform_theta_interfaces(nth), nphi)
+    i, j, k = (int(x) - 1 for x in gv["zone_1based"])
+    rho = np.zeros((nr, nth, nphi))
+    rho[i, j, k] = gv["rho"][0]
+    phi = O.solve_separated(g, rho)
+    mass = g.cell_volume()[i, j] * gv["rho"][0]
+    ph = W.phi_centres(nphi)
+    st, ct = np.sin(g.thc), np.cos(g.thc)
+    x = g.rc[:, None, None] * st[None, :, None] * np.cos(ph)[None, None, :]
+    y = g.rc[:, None, None] * st[None, :, None] * np.sin(ph)[None, None, :]
+    z = g.rc[:, None, None] * ct[None, :, None] * np.ones(nphi)[None, None, :]
+    d = np.sqrt((x - x[i, j, k]) ** 2 + (y - y[i, j, k]) ** 2 + (z - z[i, j, k]) ** 2)
+    d[i, j, k] = 1.0
+    rel = np.abs(phi + mass / d) / (mass / d)
+    rel[i, j, k] = 0.0
+    d[i, j, k] = 0.0
+    bound = gv["max_rel_err_adjacent"][0]
+    adj = [rel[i + 1, j, k], rel[i - 1, j, k], rel[i, j + 1, k], rel[i, j - 1, k],
+           rel[i, j, k + 1], rel[i, j, k - 1]]
+    assert max(adj) <= bound
+    assert 0.5 * bound <= rel.max() <= 1.5 * bound
+    assert rel[d > 20 * d[i + 1, j, k]].max() < 1e-2
