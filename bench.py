@@ -1,0 +1,332 @@
+#!/usr/bin/env python
+"""Benchmark of the exact spherical-polar Poisson solve (Mueller & Chan 2018) on GB300.
+
+One step = one whole solve Phi = L^-1 (4 pi G rho) of the 550x128x256 stellar workload
+(log-stretched r, seeded l<=20 spherical-harmonic perturbation), inputs resident in HBM.
+Prints one JSON line (rank 0).  `value` is zones/s of the headline precision; the
+float64 path is reported beside it.  With --impl reference the CPU oracle is timed on
+the host cores instead (a deliberately slow baseline).
+
+Launch: python bench.py [--gpus N --steps K --warmup W]; for N>1 under torchrun each
+rank solves its own instance (independent problems, no collective on the data path)."""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "zones/s at 550x128x256, mixed vs FP64 @1e-10 rel err; served p50/p99 latency"
+WORKLOAD = "stellar_sh 550x128x256 (log r in [1e-3,1] with origin cell, uniform theta/phi, l<=20 SH perturbation, seed 3)"
+PAPER_BEST_ZPS = 18022400 / 0.036   # Table 1: parity-split solver, 1024 Magnus CPU cores
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-oracle-check", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ CPU baseline
+def oracle_zones_per_s(budget_s: float = 12.0):
+    """The CPU oracle (float64 NumPy/SciPy, as it stands) on the bench workload, repeated
+    until `budget_s` of CPU work; returns (zones/s, solves, seconds)."""
+    import workloads as W
+    from oracle import sph_poisson as O
+    p = W.stellar_sh()
+    geo = O.Geometry(p.r_if, p.th_if, p.nphi)
+    n, t0 = 0, time.perf_counter()
+    while True:
+        O.solve_separated(geo, p.rho)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            break
+    return p.zones * n / el, n, el
+
+
+def cpu_cores():
+    return os.cpu_count() or 1
+
+
+def run_reference(args, rank):
+    """Reference arm: the CPU oracle, one full solve of the workload per step."""
+    if rank != 0:
+        return
+    import workloads as W
+    from oracle import sph_poisson as O
+    p = W.stellar_sh()
+    geo = O.Geometry(p.r_if, p.th_if, p.nphi)
+    for _ in range(args.warmup):
+        O.solve_separated(geo, p.rho)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.solve_separated(geo, p.rho)
+    el = time.perf_counter() - t0
+    v = p.zones * args.steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "zones/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "global_batch": 1, "l2": "inputs larger than L2 (CPU run)"},
+        "cpu_baseline": {"value": v, "unit": "zones/s", "cores": cpu_cores(), "kind": "oracle",
+                         "sample": f"{args.steps} full float64 oracle solves of the workload"},
+        "e2e": {"value": v, "unit": "zones/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_ours(args, rank, world, local):
+    import torch
+    import paper_1806_06623_gb300 as S
+    import workloads as W
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    S.lib()
+    precision = args.precision or "fp64"
+    p = W.stellar_sh()
+    zones = p.zones
+    rho = torch.from_numpy(p.rho).to(dev)
+    phi = torch.empty_like(rho)
+    stream = torch.cuda.current_stream(dev)
+
+    plans = {}
+    plans["fp64"] = S.Plan(p.r_if, p.th_if, p.nphi, precision=S.SP_FP64)
+    if precision == "mixed":
+        plans["mixed"] = S.Plan(p.r_if, p.th_if, p.nphi, precision=S.SP_MIXED_BF16X3, tol=1e-10)
+    head = plans[precision]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def timed_steps(plan, k, collect):
+        tot = 0.0
+        infos = []
+        for _ in range(k):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, info = plan.solve(rho, phi)
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+            infos.append(info.as_dict())
+            if collect:
+                plan.collect_timing()
+        return tot, infos
+
+    results = {}
+    for name, plan in plans.items():
+        for _ in range(args.warmup):
+            plan.solve(rho, phi)
+        barrier()
+        plan.set_timing(True)
+        n0 = plan.launch_count()
+        clocks = ClockSampler(local)
+        clocks.start() if name == precision else None
+        barrier()
+        tot_ms, infos = timed_steps(plan, args.steps, collect=True)
+        barrier()
+        ck = clocks.stop() if name == precision else None
+        launches = plan.launch_count() - n0
+        timing = plan.timing()
+        plan.set_timing(False)
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([tot_ms], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            tot_ms = float(t.item())
+        results[name] = {"ms": tot_ms, "infos": infos, "launches": launches, "timing": timing, "clocks": ck,
+                         "phi": phi.detach().cpu().numpy() if (rank == 0 and not args.no_oracle_check) else None}
+
+    # end-to-end through the host-buffer entry point (pinned buffers, copies timed)
+    rho_h = torch.from_numpy(p.rho).pin_memory()
+    phi_h = torch.empty(p.rho.shape, dtype=torch.float64).pin_memory()
+    rho_np, phi_np = rho_h.numpy(), phi_h.numpy()
+    for _ in range(max(1, args.warmup // 2)):
+        head.solve_host(rho_np, phi_np)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        head.solve_host(rho_np, phi_np)
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    if rank != 0:
+        return
+    r = results[precision]
+    value = zones * args.steps * world / (r["ms"] / 1e3)
+    line = {
+        "metric": METRIC, "value": value, "unit": "zones/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": value / PAPER_BEST_ZPS,
+        "vs_baseline_ref": "Table 1 of the paper: 0.036 s per 550x128x256 solve, parity-split, 1024 CPU cores",
+        "dtype": "f64" if precision == "fp64" else "bf16x3+f32 with f64 refinement",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": precision, "global_batch": world,
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "flushed (256 MB write) between timed steps"},
+        "clocks": r["clocks"],
+        "gpu_launches": r["launches"],
+        "e2e": {"value": zones * args.steps * world / e2e_s, "unit": "zones/s",
+                "h2d_bytes_per_step": int(p.rho.nbytes), "d2h_bytes_per_step": int(p.rho.nbytes)},
+        "kernel_ms_per_step": {k: v[0] / args.steps for k, v in r["timing"].items()},
+    }
+    for name, rr in results.items():
+        line[f"{name}_zones_per_s"] = zones * args.steps * world / (rr["ms"] / 1e3)
+        line[f"{name}_ms_per_step"] = rr["ms"] / args.steps
+    line["roofline"] = roofline(r["timing"], p, precision)
+    if not args.no_oracle_check:
+        line["error_vs_oracle"] = check_vs_oracle(p, {k: v["phi"] for k, v in results.items()})
+    if not args.no_cpu_baseline and args.gpus == 1:
+        zps, n, el = oracle_zones_per_s()
+        line["cpu_baseline"] = {"value": zps, "unit": "zones/s", "cores": cpu_cores(), "kind": "oracle",
+                                "sample": f"{n} full float64 oracle solves of the workload in {el:.1f} s "
+                                          "(NumPy FFT and Thomas single-threaded, BLAS matmul multi-threaded)"}
+    print(json.dumps(line), flush=True)
+
+
+def roofline(timing, p, precision):
+    """Dominant kernel's achieved rate from its live CUDA-event durations."""
+    nr, nth, nphi = p.shape
+    mh = nphi // 2 + 1
+    zones = nr * nth * nphi
+    if not timing:
+        return None
+    name, (ms, cnt) = max(timing.items(), key=lambda kv: kv[1][0])
+    per_launch_s = ms / cnt / 1e3
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    if name in ("project_forward", "project_inverse") and precision == "fp64":
+        flops = 2.0 * nr * nth * nth * nphi            # paper's count per projection (Sect. 4.1)
+        ach = flops / per_launch_s / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": 1.25, "unit": "TFLOP/s",
+                "frac": ach / 1.25, "traffic": None,
+                "peak_source": "nominal GB300 float64 rate (no measured float64 peak on this pool)",
+                "algorithmic": "2 Nr Ntheta^2 Nphi flops per projection"}
+    # HBM-bound kernels: algorithmic bytes per launch
+    bytes_per = {
+        "fft_forward": 8.0 * zones + 8.0 * (2 * mh * nr * nth),
+        "fft_inverse": 8.0 * (2 * mh * nr * nth) + 8.0 * zones,
+        "radial_solve": 8.0 * 2 * (2 * mh * nr * nth),
+        "stencil": 16.0 * zones,
+    }
+    b = bytes_per.get(name, 16.0 * zones)
+    ach = b / per_launch_s / 1e9
+    pk = float(peaks.get("hbm_gbs", 6800.0))
+    return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s", "frac": ach / pk,
+            "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback"}
+
+
+def check_vs_oracle(p, phis):
+    from oracle import sph_poisson as O
+    geo = O.Geometry(p.r_if, p.th_if, p.nphi)
+    ref = O.solve_separated(geo, p.rho)
+    out = {}
+    for k, v in phis.items():
+        if v is None:
+            continue
+        out[k] = {"max_rel_err": float(np.max(np.abs(v - ref)) / np.max(np.abs(ref))),
+                  "eta": O.residuals(geo, v, p.rho)[0]}
+    return out
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,161 @@
+/*
+ * sphpoisson.h -- C ABI of the GB300 exact spherical-polar Poisson solver.
+ *
+ * The library solves the finite-volume Poisson equation of Mueller & Chan (2018),
+ * Sect. 3.1, Eq. (fin_vol0)-(fin_vol3):
+ *
+ *     (Delta_r + Delta_theta + Delta_phi) Phi_{ijk} = s_{ijk} = 4 pi G rho_{ijk}
+ *
+ * on a grid of Nr radial x Ntheta polar x Nphi azimuthal cells, exactly (to rounding),
+ * by the separated algorithm of Sect. 3.2: an FFT along phi, a projection onto the
+ * eigenvectors H_{l,m}(j) of the discrete theta operator for every azimuthal wavenumber
+ * m, one tridiagonal radial solve per (l,m) that carries the multipole outer boundary
+ * condition (last equation of Sect. 3.2), the back projection and the inverse FFT.
+ *
+ * Conventions shared by every entry point
+ *  - Fields rho, Phi and (Delta Phi) are float64, C order [i][j][k] with k (phi) fastest:
+ *    element (i,j,k) at offset (i*Ntheta + j)*Nphi + k.
+ *  - "dev" pointers are CUDA device pointers on the plan's device; "host" pointers are
+ *    CPU memory (page-locked memory gives the fastest copies).  The caller owns every
+ *    buffer it passes; the library never frees caller memory.
+ *  - Calls with a stream argument are asynchronous on that CUDA stream (a
+ *    cudaStream_t passed as void*; NULL is the legacy default stream).  Results are
+ *    ready when the stream reaches the work.
+ *  - Every function returns an sp_status; nothing aborts or throws across the ABI.
+ *    Errors found on the device (eigen-iteration limit, non-convergence) are
+ *    recorded in the plan and returned by sp_plan_last_status() after the stream
+ *    has been synchronised.
+ *  - Cell centres are the midpoints of their interfaces; phi zones are uniform with
+ *    centres (k+1/2) 2 pi/Nphi.  The inner radial face carries zero flux (its area
+ *    vanishes when r_{1/2} = 0).
+ */
+#ifndef SPHPOISSON_H
+#define SPHPOISSON_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sp_plan sp_plan;
+
+typedef enum {
+    SP_OK = 0,
+    SP_ERR_INVALID_ARG = 1,     /* null pointer, bad enum, aliasing, size mismatch */
+    SP_ERR_GRID = 2,            /* interfaces not increasing, theta not spanning [0,pi] */
+    SP_ERR_CUDA = 3,            /* a CUDA runtime call failed */
+    SP_ERR_OOM = 4,             /* device allocation failed */
+    SP_ERR_NOT_CONVERGED = 5,   /* mixed-precision refinement did not reach tol */
+    SP_ERR_TIMEOUT = 6,         /* a bounded device wait gave up */
+    SP_ERR_DEVICE_CHECK = 7,    /* a device-side check failed (eigen iteration limit) */
+    SP_ERR_UNSUPPORTED = 8      /* size outside what the kernels support */
+} sp_status;
+
+/* Outer radial boundary.  SP_OUTER_MULTIPOLE is the paper's condition (Sect. 3.2):
+ * the outer-face gradient of mode (l,m) is -p f_N (r_{N+1/2}/r_N)^(-p) / r_{N+1/2},
+ * p = (1 + sqrt(1 - 4 lambda_Omega,l,m))/2.  SP_OUTER_DIRICHLET sets Phi(r_{N+1/2}) = 0
+ * (the gradient is -f_N/(r_{N+1/2} - r_N)); it has no counterpart in the paper and
+ * exists for tests and for bounded domains. */
+enum { SP_OUTER_MULTIPOLE = 0, SP_OUTER_DIRICHLET = 1 };
+
+/* Arithmetic of sp_solve.  SP_FP64: every step in float64.  SP_MIXED_BF16X3: the
+ * low-precision solve runs the phi FFTs and the radial solves in float32 (float64 for
+ * the near-singular low-|lambda| radial modes) and the theta projections as three
+ * bf16 tensor-core products with float32 accumulation; float64 iterative refinement
+ * with the float64 residual of the finite-volume operator brings the result to tol. */
+enum { SP_FP64 = 0, SP_MIXED_BF16X3 = 1 };
+
+typedef struct {
+    int iterations;        /* low-precision solves performed (1 for SP_FP64) */
+    int precision_used;    /* SP_FP64 or SP_MIXED_BF16X3 */
+    double last_update;    /* max|e|/max|Phi| of the last correction (0 for SP_FP64) */
+    double est_rel_error;  /* estimated max|Phi - Phi_exact|/max|Phi| (0 for SP_FP64) */
+    int status;            /* sp_status of the solve */
+} sp_solve_info;
+
+/* Create a plan (Sect. 3.1 geometry, Sect. 3.2 eigenbasis) on the current CUDA device.
+ *  r_interfaces      host, Nr+1 values, strictly increasing, r_interfaces[0] >= 0
+ *  theta_interfaces  host, Ntheta+1 values, strictly increasing from 0 to pi
+ *                    (|last - pi| <= 1e-12); NULL = uniform theta
+ *  Nr, Ntheta >= 1; Ntheta <= 160.  Nphi >= 1 with Nphi = 2^a 3^b, Nphi <= 4096.
+ *  outer_bc          SP_OUTER_MULTIPOLE or SP_OUTER_DIRICHLET
+ *  G                 gravitational constant (s = 4 pi G rho)
+ *  precision         SP_FP64 or SP_MIXED_BF16X3
+ *  tol, max_iter     refinement target max|Phi-Phi_exact|/max|Phi| and iteration cap
+ *                    (mixed precision only; e.g. 1e-10 and 8)
+ *  stream            set-up work (theta eigensolve on the GPU) runs on this stream and
+ *                    is complete when the call returns
+ *  out               receives the plan; the plan owns its tables and, until
+ *                    sp_plan_set_workspace is called, its own workspace.
+ * Returns SP_ERR_GRID for invalid interfaces, SP_ERR_UNSUPPORTED for sizes outside the
+ * limits above, SP_ERR_DEVICE_CHECK if the eigensolver hit its iteration limit. */
+int sp_plan_create(const double* r_interfaces, int Nr,
+                   const double* theta_interfaces, int Ntheta,
+                   int Nphi, int outer_bc, double G, int precision,
+                   double tol, int max_iter, void* stream, sp_plan** out);
+
+/* Bytes of device workspace sp_solve and sp_apply_laplacian need. */
+size_t sp_plan_workspace_bytes(const sp_plan* plan);
+
+/* Hand the plan a caller-owned device workspace of at least sp_plan_workspace_bytes
+ * (256-byte aligned).  The plan frees its own workspace, if any, and uses this one
+ * until destroyed.  The caller keeps ownership and must not free it while the plan
+ * may still use it. */
+int sp_plan_set_workspace(sp_plan* plan, void* dev_workspace, size_t bytes);
+
+/* Phi = L^{-1} (4 pi G rho): the exact discrete solve of Sect. 3.2.
+ *  rho_dev  device, Nr*Ntheta*Nphi float64, read only
+ *  phi_dev  device, Nr*Ntheta*Nphi float64, written; must not overlap rho_dev
+ *  info     host, may be NULL; filled when the call returns (for mixed precision
+ *           this call synchronises the stream to test convergence)
+ * SP_FP64 plans run asynchronously and fill info with iterations = 1. */
+int sp_solve(sp_plan* plan, const double* rho_dev, double* phi_dev, void* stream,
+             sp_solve_info* info);
+
+/* Same as sp_solve with host buffers: copies rho to the device, solves, copies Phi
+ * back, and synchronises the stream before returning.  Uses plan-owned device buffers
+ * for rho and Phi (allocated on first use, freed with the plan). */
+int sp_solve_host(sp_plan* plan, const double* rho_host, double* phi_host, void* stream,
+                  sp_solve_info* info);
+
+/* out = (Delta Phi)_{ijk}, the finite-volume operator of Eq. (fin_vol0)-(fin_vol3)
+ * with the plan's boundary conditions, in float64 (not divided by 4 pi G).
+ *  phi_dev, out_dev  device, Nr*Ntheta*Nphi float64; must not overlap */
+int sp_apply_laplacian(sp_plan* plan, const double* phi_dev, double* out_dev, void* stream);
+
+/* Copy the plan's theta eigenbasis (Sect. 3.2) to host memory, any pointer may be NULL:
+ *  lambda   (Nphi/2+1) x Ntheta: lambda_Omega,l,m, row m, descending in l
+ *  H        (Nphi/2+1) x Ntheta x Ntheta: H[m][j][l] = H_{l,m}(j), W-orthonormal
+ *  kappa    (Nphi/2+1) x Ntheta: outer-face gradient per unit f_N of mode (l,m)
+ * Synchronises the plan's device. */
+int sp_plan_get_eigen(const sp_plan* plan, double* lambda, double* H, double* kappa);
+
+/* Per-kernel CUDA-event timers (tracing; no counterpart in the paper).  With timing
+ * enabled every kernel launch of the plan is bracketed by two events on its stream
+ * (at most 256 launches between collections).  sp_plan_collect_timing waits for the
+ * recorded events and adds their durations to per-kernel totals;
+ * sp_plan_get_timing copies the totals (milliseconds) and launch counts of the first
+ * n kernel identities, in this order: forward FFT, forward projection, radial solve,
+ * inverse projection, inverse FFT, stencil, outer-shell term, residual, split,
+ * update, eigensolve.  Enabling resets the totals. */
+int sp_plan_set_timing(sp_plan* plan, int enable);
+int sp_plan_collect_timing(sp_plan* plan);
+int sp_plan_get_timing(const sp_plan* plan, double* ms, long long* count, int n);
+
+/* Number of kernel launches this plan has issued since creation (host counter). */
+long long sp_plan_launch_count(const sp_plan* plan);
+
+/* Status of the most recent device-side checks of this plan (synchronises). */
+int sp_plan_last_status(const sp_plan* plan);
+
+/* Release every resource the plan owns.  NULL is accepted. */
+int sp_plan_destroy(sp_plan* plan);
+
+/* Human-readable name of a status code (static storage). */
+const char* sp_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPHPOISSON_H */

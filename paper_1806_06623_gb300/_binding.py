@@ -1,0 +1,290 @@
+"""ctypes binding of libsphpoisson.so (include/sphpoisson.h).
+
+Argument marshalling only: every step of the solve runs in the CUDA library.  The
+binding refuses to run without the compiled library; there is no CPU fallback.
+Device arrays are torch CUDA tensors (float64, contiguous); streams default to
+torch's current stream on the tensor's device."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+SP_OK = 0
+SP_ERR_INVALID_ARG = 1
+SP_ERR_GRID = 2
+SP_ERR_CUDA = 3
+SP_ERR_OOM = 4
+SP_ERR_NOT_CONVERGED = 5
+SP_ERR_TIMEOUT = 6
+SP_ERR_DEVICE_CHECK = 7
+SP_ERR_UNSUPPORTED = 8
+
+SP_OUTER_MULTIPOLE = 0
+SP_OUTER_DIRICHLET = 1
+SP_FP64 = 0
+SP_MIXED_BF16X3 = 1
+
+
+class SpError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} ({status})" if what else status_string(status))
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("precision_used", C.c_int), ("last_update", C.c_double),
+                ("est_rel_error", C.c_double), ("status", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_LIB = None
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "sp_plan_create": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_double,
+                                 C.c_int, C.c_double, C.c_int, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "sp_plan_workspace_bytes": (C.c_size_t, [C.c_void_p]),
+    "sp_plan_set_workspace": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "sp_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(SolveInfo)]),
+    "sp_solve_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(SolveInfo)]),
+    "sp_apply_laplacian": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sp_plan_get_eigen": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sp_plan_last_status": (C.c_int, [C.c_void_p]),
+    "sp_plan_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
+    "sp_plan_collect_timing": (C.c_int, [C.c_void_p]),
+    "sp_plan_get_timing": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "sp_plan_launch_count": (C.c_longlong, [C.c_void_p]),
+    "sp_plan_destroy": (C.c_int, [C.c_void_p]),
+    "sp_status_string": (C.c_char_p, [C.c_int]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = True):
+    """Load libsphpoisson.so (building it with nvcc if it is absent)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise ImportError(f"{path} is missing: build it with paper_1806_06623_gb300.build.build()")
+        _build.build()
+    L = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _LIB = L
+    return L
+
+
+def declared_symbols():
+    return list(_SIGS)
+
+
+def status_string(status: int) -> str:
+    try:
+        return lib().sp_status_string(int(status)).decode()
+    except Exception:  # library not loadable: still describe the code
+        return f"status {status}"
+
+
+def _check(status: int, what: str):
+    if status != SP_OK:
+        raise SpError(status, what)
+
+
+def _stream_ptr(stream, device=None):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dev_ptr(t, n, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float64 or not t.is_contiguous() or t.numel() != n:
+        raise ValueError(f"{name} must be a contiguous float64 tensor with {n} elements")
+    return C.c_void_p(t.data_ptr())
+
+
+# ------------------------------------------------------------- C-named calls
+def sp_plan_create(r_interfaces, theta_interfaces, nphi, outer_bc=SP_OUTER_MULTIPOLE, G=1.0,
+                   precision=SP_FP64, tol=1e-10, max_iter=8, stream=None):
+    r = np.ascontiguousarray(r_interfaces, dtype=np.float64)
+    th = None if theta_interfaces is None else np.ascontiguousarray(theta_interfaces, dtype=np.float64)
+    nth = (len(th) - 1) if th is not None else None
+    if nth is None:
+        raise ValueError("theta_interfaces is required by the binding (pass uniform interfaces)")
+    out = C.c_void_p()
+    st = lib().sp_plan_create(r.ctypes.data_as(C.c_void_p), len(r) - 1, th.ctypes.data_as(C.c_void_p), nth,
+                              int(nphi), int(outer_bc), float(G), int(precision), float(tol), int(max_iter),
+                              _stream_ptr(stream), C.byref(out))
+    _check(st, "sp_plan_create")
+    return out
+
+
+def sp_plan_workspace_bytes(plan) -> int:
+    return int(lib().sp_plan_workspace_bytes(plan))
+
+
+def sp_plan_set_workspace(plan, ws):
+    _check(lib().sp_plan_set_workspace(plan, C.c_void_p(ws.data_ptr()), ws.numel() * ws.element_size()),
+           "sp_plan_set_workspace")
+
+
+def sp_solve(plan, rho, phi, shape, stream=None):
+    n = int(np.prod(shape))
+    info = SolveInfo()
+    st = lib().sp_solve(plan, _dev_ptr(rho, n, "rho"), _dev_ptr(phi, n, "phi"),
+                        _stream_ptr(stream, rho.device), C.byref(info))
+    _check(st, "sp_solve")
+    return info
+
+
+def sp_solve_host(plan, rho, phi, stream=None):
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    if phi.dtype != np.float64 or not phi.flags.c_contiguous or phi.size != rho.size:
+        raise ValueError("phi must be a contiguous float64 array of rho's size")
+    info = SolveInfo()
+    st = lib().sp_solve_host(plan, rho.ctypes.data_as(C.c_void_p), phi.ctypes.data_as(C.c_void_p),
+                             _stream_ptr(stream), C.byref(info))
+    _check(st, "sp_solve_host")
+    return info
+
+
+def sp_apply_laplacian(plan, phi, out, shape, stream=None):
+    n = int(np.prod(shape))
+    _check(lib().sp_apply_laplacian(plan, _dev_ptr(phi, n, "phi"), _dev_ptr(out, n, "out"),
+                                    _stream_ptr(stream, phi.device)), "sp_apply_laplacian")
+
+
+def sp_plan_get_eigen(plan, mh, nth):
+    lam = np.zeros((mh, nth))
+    H = np.zeros((mh, nth, nth))
+    kap = np.zeros((mh, nth))
+    _check(lib().sp_plan_get_eigen(plan, lam.ctypes.data_as(C.c_void_p), H.ctypes.data_as(C.c_void_p),
+                                   kap.ctypes.data_as(C.c_void_p)), "sp_plan_get_eigen")
+    return lam, H, kap
+
+
+def sp_plan_last_status(plan) -> int:
+    return int(lib().sp_plan_last_status(plan))
+
+
+KERNEL_NAMES = ["fft_forward", "project_forward", "radial_solve", "project_inverse", "fft_inverse",
+                "stencil", "outer_term", "residual", "split", "update", "eigensolve"]
+
+
+def sp_plan_set_timing(plan, enable: bool):
+    _check(lib().sp_plan_set_timing(plan, 1 if enable else 0), "sp_plan_set_timing")
+
+
+def sp_plan_collect_timing(plan):
+    _check(lib().sp_plan_collect_timing(plan), "sp_plan_collect_timing")
+
+
+def sp_plan_get_timing(plan):
+    n = len(KERNEL_NAMES)
+    ms = (C.c_double * n)()
+    cnt = (C.c_longlong * n)()
+    _check(lib().sp_plan_get_timing(plan, ms, cnt, n), "sp_plan_get_timing")
+    return {KERNEL_NAMES[k]: (ms[k], cnt[k]) for k in range(n) if cnt[k]}
+
+
+def sp_plan_launch_count(plan) -> int:
+    return int(lib().sp_plan_launch_count(plan))
+
+
+def sp_plan_destroy(plan):
+    if plan:
+        lib().sp_plan_destroy(plan)
+
+
+def sp_status_string(status: int) -> str:
+    return status_string(status)
+
+
+# ------------------------------------------------------------ convenience
+class Plan:
+    """One solver plan: grid, boundary condition, precision and its device tables."""
+
+    def __init__(self, r_interfaces, theta_interfaces, nphi, outer_bc=SP_OUTER_MULTIPOLE, G=1.0,
+                 precision=SP_FP64, tol=1e-10, max_iter=8, stream=None):
+        self.r_if = np.asarray(r_interfaces, dtype=np.float64)
+        self.th_if = np.asarray(theta_interfaces, dtype=np.float64)
+        self.shape = (len(self.r_if) - 1, len(self.th_if) - 1, int(nphi))
+        self.mh = int(nphi) // 2 + 1
+        self.precision = precision
+        self._h = None
+        self._h = sp_plan_create(self.r_if, self.th_if, nphi, outer_bc, G, precision, tol, max_iter, stream)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def workspace_bytes(self) -> int:
+        return sp_plan_workspace_bytes(self._h)
+
+    def solve(self, rho, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty_like(rho)
+        info = sp_solve(self._h, rho, out, self.shape, stream)
+        return out, info
+
+    def solve_host(self, rho, out=None, stream=None):
+        if out is None:
+            out = np.empty(self.shape, dtype=np.float64)
+        info = sp_solve_host(self._h, rho, out, stream)
+        return out, info
+
+    def apply_laplacian(self, phi, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty_like(phi)
+        sp_apply_laplacian(self._h, phi, out, self.shape, stream)
+        return out
+
+    def eigen(self):
+        return sp_plan_get_eigen(self._h, self.mh, self.shape[1])
+
+    def set_timing(self, enable=True):
+        sp_plan_set_timing(self._h, enable)
+
+    def collect_timing(self):
+        sp_plan_collect_timing(self._h)
+
+    def timing(self):
+        return sp_plan_get_timing(self._h)
+
+    def launch_count(self) -> int:
+        return sp_plan_launch_count(self._h)
+
+    def last_status(self) -> int:
+        return sp_plan_last_status(self._h)
+
+    def close(self):
+        if self._h:
+            sp_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,139 @@
+// Radial boundary-value problems of Sect. 3.2 and the float64 finite-volume operator.
+//
+// thomas: for every (l,m) the tridiagonal system  Delta_r f + R_i lambda_Omega,l,m f = s_hat
+// (Eq. tridiag) with zero flux through r_{1/2} and the outer row carrying the
+// mode's boundary term (multipole exponent p or Dirichlet).  One thread per (m,l)
+// solves the real and imaginary right-hand sides together by forward elimination and
+// back substitution; the systems are diagonally dominant, so no pivoting is needed.
+// The spectral layout [m][i][c][l] makes every radial step a coalesced row access.
+//
+// stencil: (Delta Phi)_{ijk} of Eq. (fin_vol0)-(fin_vol3), one thread per cell with phi
+// fastest; the multipole outer term is added by outer_term (FFT of the last shell,
+// kappa(lambda) in the eigenbasis, inverse FFT).
+#include "sp_internal.h"
+
+namespace sp {
+namespace {
+
+__global__ void __launch_bounds__(128) k_thomas_f64(const RadialRow* __restrict__ rad, const double* __restrict__ lam,
+                                                    const double* __restrict__ outer, double* __restrict__ x,
+                                                    double* __restrict__ cp, int nr, int nth, int mh) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= mh * nth) return;
+  const int m = t / nth;
+  const int l = t - m * nth;
+  const double L = lam[t];
+  const double od = outer[t];
+  double* X = x + (size_t)m * nr * 2 * nth + l;
+  double* CP = cp + (size_t)m * nr * nth + l;
+  const size_t st = 2 * (size_t)nth;
+  double cprev = 0.0, dre = 0.0, dim = 0.0;
+  for (int i = 0; i < nr; ++i) {
+    const RadialRow rr = rad[i];
+    double b = fma(rr.R, L, rr.base);
+    if (i == nr - 1) b += od;
+    const double piv = b - rr.sub * cprev;
+    const double inv = 1.0 / piv;
+    const double xr = X[i * st];
+    const double xi = X[i * st + nth];
+    cprev = rr.sup * inv;
+    dre = (xr - rr.sub * dre) * inv;
+    dim = (xi - rr.sub * dim) * inv;
+    X[i * st] = dre;
+    X[i * st + nth] = dim;
+    CP[(size_t)i * nth] = cprev;
+  }
+  for (int i = nr - 2; i >= 0; --i) {
+    const double c = CP[(size_t)i * nth];
+    dre = X[i * st] - c * dre;
+    dim = X[i * st + nth] - c * dim;
+    X[i * st] = dre;
+    X[i * st + nth] = dim;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_stencil_f64(const double* __restrict__ phi, double* __restrict__ out,
+                                                     const RadialRow* __restrict__ rad,
+                                                     const ThetaRow* __restrict__ th, int nr, int nth, int nphi,
+                                                     double dir_coef) {
+  const size_t n = (size_t)nr * nth * nphi;
+  const size_t shell = (size_t)nth * nphi;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(idx % nphi);
+    const size_t ij = idx / nphi;
+    const int j = (int)(ij % nth);
+    const int i = (int)(ij / nth);
+    const double c = phi[idx];
+    const RadialRow rr = rad[i];
+    const ThetaRow tr = th[j];
+    double v = 0.0;
+    if (i > 0) v += rr.sub * (phi[idx - shell] - c);
+    if (i < nr - 1) v += rr.sup * (phi[idx + shell] - c);
+    double a = 0.0;
+    if (j > 0) a += tr.tm * (phi[idx - nphi] - c);
+    if (j < nth - 1) a += tr.tp * (phi[idx + nphi] - c);
+    const size_t kp = (k + 1 == nphi) ? idx - k : idx + 1;
+    const size_t km = (k == 0) ? idx + (nphi - 1) : idx - 1;
+    a += tr.sphi * ((phi[kp] - c) + (phi[km] - c));
+    v += rr.R * a;
+    if (i == nr - 1) v += dir_coef * c;
+    out[idx] = v;
+  }
+}
+
+// y = outer[m] .* (HtW_m x) ; z = H_m y  for the two real columns (re, im) of shell m.
+__global__ void k_shell_kappa(const double* __restrict__ HtW, const double* __restrict__ H,
+                              const double* __restrict__ outer, const double* __restrict__ xin,
+                              double* __restrict__ zout, int nth) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* xs = reinterpret_cast<double*>(smem_raw);   // [2][nth]
+  double* ys = xs + 2 * nth;                          // [2][nth]
+  const int m = blockIdx.x;
+  const double* A = HtW + (size_t)m * nth * nth;
+  const double* Hm = H + (size_t)m * nth * nth;
+  for (int t = threadIdx.x; t < 2 * nth; t += blockDim.x) xs[t] = xin[(size_t)m * 2 * nth + t];
+  __syncthreads();
+  for (int t = threadIdx.x; t < 2 * nth; t += blockDim.x) {
+    const int c = t / nth, l = t - c * nth;
+    double s = 0.0;
+    for (int j = 0; j < nth; ++j) s = fma(A[(size_t)l * nth + j], xs[c * nth + j], s);
+    ys[t] = s * outer[(size_t)m * nth + l];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < 2 * nth; t += blockDim.x) {
+    const int c = t / nth, j = t - c * nth;
+    double s = 0.0;
+    for (int l = 0; l < nth; ++l) s = fma(Hm[(size_t)j * nth + l], ys[c * nth + l], s);
+    zout[(size_t)m * 2 * nth + t] = s;
+  }
+}
+
+}  // namespace
+
+cudaError_t thomas_f64(const Plan& p, double* x, cudaStream_t s) {
+  const int n = p.mh * p.nth;
+  k_thomas_f64<<<(n + 127) / 128, 128, 0, s>>>(p.d_rad, p.d_lam, p.d_outer, x, p.cp, p.nr, p.nth, p.mh);
+  return cudaGetLastError();
+}
+
+cudaError_t stencil_f64(const Plan& p, const double* phi, double* out, cudaStream_t s) {
+  const size_t n = (size_t)p.nr * p.nth * p.nphi;
+  const double dir = (p.outer_bc == SP_OUTER_DIRICHLET) ? -p.outer_coef / (p.r_out - p.r_last) : 0.0;
+  size_t blocks = (n + 255) / 256;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  k_stencil_f64<<<(unsigned)blocks, 256, 0, s>>>(phi, out, p.d_rad, p.d_theta, p.nr, p.nth, p.nphi, dir);
+  return cudaGetLastError();
+}
+
+cudaError_t outer_term_f64(const Plan& p, const double* phi, double* out, cudaStream_t s) {
+  const size_t off = (size_t)(p.nr - 1) * p.nth * p.nphi;
+  cudaError_t e = fft_forward_f64(p, phi + off, 1, 1.0 / p.nphi, p.shell, s);
+  if (e != cudaSuccess) return e;
+  const size_t smem = sizeof(double) * 4 * (size_t)p.nth;
+  k_shell_kappa<<<p.mh, 128, smem, s>>>(p.d_HtW, p.d_H, p.d_outer, p.shell, p.shell2, p.nth);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return fft_inverse_f64(p, p.shell2, 1, out + off, true, s);
+}
+
+}  // namespace sp

@@ -1,0 +1,139 @@
+// Internal declarations shared by the host plan code and the kernel files.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstddef>
+#include <cstdint>
+
+#include "sphpoisson.h"
+
+namespace sp {
+
+constexpr int kMaxStages = 16;
+constexpr int kMaxNtheta = 160;   // theta eigenvectors of one m are kept in shared memory
+constexpr int kMaxNphi = 4096;
+
+// Radix schedule of a length-n complex FFT, n = 2^a 3^b (radix 4 first, then 2, then 3).
+struct FftSchedule {
+  int n;
+  int nstages;
+  int radix[kMaxStages];
+};
+
+// Error bits written by kernels into the plan's device status word.
+enum : int { kErrEigenIter = 1, kErrBounds = 2 };
+
+// Per-radius coefficients of the radial operator (Eq. fin_vol3 with the Sect. 3.1
+// areas): row i of Delta_r + R_i lambda reads
+//   sub_i f_{i-1} + (base_i + R_i lambda) f_i + sup_i f_{i+1}
+// with base_i = -(sub_i + sup_i); the outer boundary term is added per mode.
+struct RadialRow {
+  double sub, sup, R, base;
+};
+
+// Per-polar-row coefficients of the angular stencil (Delta_hat_theta + S_j Delta_hat_phi):
+//   tp = t_{j+1/2}/w_j, tm = t_{j-1/2}/w_j, t = sin(theta_face)/(theta_{j+1}-theta_j),
+//   sp = S_j / dphi^2.
+struct ThetaRow {
+  double tp, tm, sphi, pad;
+};
+
+struct MixedTables;  // defined with the mixed-precision path
+
+// Kernel identities for the optional per-launch CUDA-event timers.
+enum KernelId : int {
+  kKFftFwd = 0, kKGemmFwd, kKThomas, kKGemmInv, kKFftInv, kKStencil, kKOuter, kKResidual,
+  kKSplit, kKUpdate, kKEigen, kNumKernelIds
+};
+constexpr int kMaxTimedLaunches = 256;
+
+struct Plan {
+  int device = 0;
+  int nr = 0, nth = 0, nphi = 0, mh = 0;
+  int outer_bc = SP_OUTER_MULTIPOLE;
+  int precision = SP_FP64;
+  double G = 1.0, tol = 1e-10;
+  int max_iter = 8;
+  bool parity = false;   // theta grid symmetric about the equator with even Ntheta
+  double r_out = 0, r_last = 0, outer_coef = 0;  // outer_coef = 3 r_out^2 / dV3_N
+  FftSchedule sched{};
+
+  // device tables owned by the plan
+  RadialRow* d_rad = nullptr;     // [nr]
+  ThetaRow* d_theta = nullptr;    // [nth]
+  double* d_twid = nullptr;       // [2*nphi] cos, -sin of 2 pi t / nphi
+  float* d_twid32 = nullptr;      // [2*nphi]
+  double* d_tdiag = nullptr;      // [mh][nth] diagonal of W^-1/2 B_m W^-1/2
+  double* d_toff = nullptr;       // [nth]     off-diagonal of W^-1/2 B_m W^-1/2
+  double* d_sqw = nullptr;        // [nth]     sqrt(w_j)
+  double* d_lam = nullptr;        // [mh][nth] lambda_Omega,l,m (descending in l)
+  double* d_kappa = nullptr;      // [mh][nth] outer-face gradient per unit f_N
+  double* d_outer = nullptr;      // [mh][nth] outer diagonal term of the radial row N
+  double* d_HtW = nullptr;        // [mh][l][j] (H^T W)_m
+  double* d_H = nullptr;          // [mh][j][l] H_m
+  int* d_err = nullptr;           // device status word
+
+  // workspace (plan-owned or caller-provided)
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  bool ws_owned = false;
+  double* specA = nullptr;        // [mh][nr][2][nth]
+  double* specB = nullptr;        // [mh][nr][2][nth]
+  double* cp = nullptr;           // [mh][nr][nth] Thomas forward coefficients
+  double* shell = nullptr;        // [mh][1][2][nth] outer-shell spectrum
+  double* shell2 = nullptr;       // [mh][1][2][nth]
+
+  // host-buffer path
+  double* d_rho_io = nullptr;
+  double* d_phi_io = nullptr;
+
+  MixedTables* mixed = nullptr;
+
+  // launch accounting and optional CUDA-event timers (one event pair per launch)
+  long long launches = 0;
+  bool timing = false;
+  int n_timed = 0;
+  cudaEvent_t ev[2 * kMaxTimedLaunches] = {};
+  int ev_kernel[kMaxTimedLaunches] = {};
+  double acc_ms[kNumKernelIds] = {};
+  long long acc_n[kNumKernelIds] = {};
+};
+
+// Record a launch of kernel `id` issued by `launch()` on stream s.
+template <typename F>
+cudaError_t timed_launch(Plan& p, int id, cudaStream_t s, F&& launch) {
+  const bool t = p.timing && p.n_timed < kMaxTimedLaunches;
+  if (t) cudaEventRecord(p.ev[2 * p.n_timed], s);
+  cudaError_t e = launch();
+  if (t) {
+    cudaEventRecord(p.ev[2 * p.n_timed + 1], s);
+    p.ev_kernel[p.n_timed++] = id;
+  }
+  ++p.launches;
+  return e;
+}
+
+size_t workspace_bytes(const Plan& p);
+void bind_workspace(Plan& p, void* base);
+
+// ---- kernels (launchers return the launch error) ----
+// Forward FFT of nlines real lines of length n (line g = i*nth + j, shell-major),
+// writing the half spectrum scaled by `scale` into spec[m][i][c][j] (nrs shells).
+cudaError_t fft_forward_f64(const Plan& p, const double* in, int nrs, double scale, double* spec,
+                            cudaStream_t s);
+// Inverse FFT of spec[m][i][c][j] into lines; accumulate adds into `out`.
+cudaError_t fft_inverse_f64(const Plan& p, const double* spec, int nrs, double* out, bool accumulate,
+                            cudaStream_t s);
+// Batched NT GEMM: C[b][n][r] = sum_k A[b][r][k] B[b][n][k], b < nb.
+cudaError_t gemm_nt_f64(const double* A, const double* B, double* C, int nb, int M, int ncol, int K,
+                        cudaStream_t s);
+// Radial Thomas solves for every (m,l), in place on x[m][i][c][l].
+cudaError_t thomas_f64(const Plan& p, double* x, cudaStream_t s);
+// Local part of the finite-volume operator (all interior fluxes, Dirichlet outer term).
+cudaError_t stencil_f64(const Plan& p, const double* phi, double* out, cudaStream_t s);
+// Multipole outer term on the last shell: out[nr-1] += outer_coef * kappa(A_Omega) phi[nr-1].
+cudaError_t outer_term_f64(const Plan& p, const double* phi, double* out, cudaStream_t s);
+// theta eigensolve for every m; writes lam, kappa, outer, H, HtW.
+cudaError_t theta_eigen(const Plan& p, cudaStream_t s);
+
+}  // namespace sp

@@ -1,0 +1,490 @@
+// Host side of the C ABI: validation, the geometry of Sect. 3.1, the per-plan tables,
+// workspace management and the float64 solve sequence of Sect. 3.2.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "sp_internal.h"
+
+using sp::Plan;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846264338327950288;
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else if (prev == dev) prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+#define SP_CUDA(call)                                  \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) {                           \
+      return e_ == cudaErrorMemoryAllocation ? SP_ERR_OOM : SP_ERR_CUDA; \
+    }                                                  \
+  } while (0)
+
+bool make_schedule(int n, sp::FftSchedule* s) {
+  s->n = n;
+  s->nstages = 0;
+  int r = n;
+  while (r % 4 == 0) { if (s->nstages >= sp::kMaxStages) return false; s->radix[s->nstages++] = 4; r /= 4; }
+  while (r % 2 == 0) { if (s->nstages >= sp::kMaxStages) return false; s->radix[s->nstages++] = 2; r /= 2; }
+  while (r % 3 == 0) { if (s->nstages >= sp::kMaxStages) return false; s->radix[s->nstages++] = 3; r /= 3; }
+  return r == 1;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+template <typename T>
+int upload(T** dst, const T* src, size_t n) {
+  SP_CUDA(cudaMalloc(reinterpret_cast<void**>(dst), sizeof(T) * (n ? n : 1)));
+  if (n) SP_CUDA(cudaMemcpy(*dst, src, sizeof(T) * n, cudaMemcpyHostToDevice));
+  return SP_OK;
+}
+
+void free_tables(Plan* p) {
+  cudaFree(p->d_rad);
+  cudaFree(p->d_theta);
+  cudaFree(p->d_twid);
+  cudaFree(p->d_twid32);
+  cudaFree(p->d_tdiag);
+  cudaFree(p->d_toff);
+  cudaFree(p->d_sqw);
+  cudaFree(p->d_lam);
+  cudaFree(p->d_kappa);
+  cudaFree(p->d_outer);
+  cudaFree(p->d_HtW);
+  cudaFree(p->d_H);
+  cudaFree(p->d_err);
+  cudaFree(p->d_rho_io);
+  cudaFree(p->d_phi_io);
+  if (p->ws_owned) cudaFree(p->ws);
+  for (int i = 0; i < 2 * sp::kMaxTimedLaunches; ++i)
+    if (p->ev[i]) cudaEventDestroy(p->ev[i]);
+}
+
+bool overlaps(const void* a, const void* b, size_t bytes) {
+  const char* x = static_cast<const char*>(a);
+  const char* y = static_cast<const char*>(b);
+  return x < y + bytes && y < x + bytes;
+}
+
+int ensure_workspace(Plan* p) {
+  if (p->ws) return SP_OK;
+  const size_t b = sp::workspace_bytes(*p);
+  void* w = nullptr;
+  SP_CUDA(cudaMalloc(&w, b));
+  p->ws = w;
+  p->ws_bytes = b;
+  p->ws_owned = true;
+  sp::bind_workspace(*p, w);
+  return SP_OK;
+}
+
+int launch_status(cudaError_t e) {
+  if (e == cudaSuccess) return SP_OK;
+  return e == cudaErrorMemoryAllocation ? SP_ERR_OOM : SP_ERR_CUDA;
+}
+
+int solve_fp64(Plan* p, const double* rho, double* phi, cudaStream_t s) {
+  const int nth = p->nth, nr = p->nr, mh = p->mh;
+  Plan& P = *p;
+  int st;
+  // (1) s_tilde = FFT_phi(4 pi G rho)/Nphi
+  if ((st = launch_status(sp::timed_launch(P, sp::kKFftFwd, s, [&] {
+         return sp::fft_forward_f64(P, rho, nr, 4.0 * kPi * P.G / P.nphi, P.specA, s); }))))
+    return st;
+  // (2) s_hat = (H^T W)_m s_tilde
+  if ((st = launch_status(sp::timed_launch(P, sp::kKGemmFwd, s, [&] {
+         return sp::gemm_nt_f64(P.d_HtW, P.specA, P.specB, mh, nth, 2 * nr, nth, s); }))))
+    return st;
+  // (3) radial solves per (l,m)
+  if ((st = launch_status(sp::timed_launch(P, sp::kKThomas, s, [&] { return sp::thomas_f64(P, P.specB, s); }))))
+    return st;
+  // (4) g = H_m f
+  if ((st = launch_status(sp::timed_launch(P, sp::kKGemmInv, s, [&] {
+         return sp::gemm_nt_f64(P.d_H, P.specB, P.specA, mh, nth, 2 * nr, nth, s); }))))
+    return st;
+  // (5) Phi = inverse FFT
+  return launch_status(sp::timed_launch(P, sp::kKFftInv, s, [&] {
+    return sp::fft_inverse_f64(P, P.specA, nr, phi, false, s); }));
+}
+
+int apply_laplacian_impl(Plan* p, const double* phi, double* out, cudaStream_t s) {
+  Plan& P = *p;
+  int st = launch_status(sp::timed_launch(P, sp::kKStencil, s, [&] { return sp::stencil_f64(P, phi, out, s); }));
+  if (st) return st;
+  if (P.outer_bc == SP_OUTER_MULTIPOLE) {
+    // FFT of the last shell, kappa in the eigenbasis, inverse FFT accumulated: 3 launches
+    st = launch_status(sp::timed_launch(P, sp::kKOuter, s, [&] { return sp::outer_term_f64(P, phi, out, s); }));
+    P.launches += 2;
+  }
+  return st;
+}
+
+}  // namespace
+
+namespace sp {
+
+size_t workspace_bytes(const Plan& p) {
+  const size_t spec = sizeof(double) * (size_t)p.mh * p.nr * 2 * p.nth;
+  const size_t cpb = sizeof(double) * (size_t)p.mh * p.nr * p.nth;
+  const size_t shell = sizeof(double) * (size_t)p.mh * 2 * p.nth;
+  return align256(spec) * 2 + align256(cpb) + align256(shell) * 2;
+}
+
+void bind_workspace(Plan& p, void* base) {
+  char* c = static_cast<char*>(base);
+  const size_t spec = align256(sizeof(double) * (size_t)p.mh * p.nr * 2 * p.nth);
+  const size_t cpb = align256(sizeof(double) * (size_t)p.mh * p.nr * p.nth);
+  const size_t shell = align256(sizeof(double) * (size_t)p.mh * 2 * p.nth);
+  p.specA = reinterpret_cast<double*>(c);
+  c += spec;
+  p.specB = reinterpret_cast<double*>(c);
+  c += spec;
+  p.cp = reinterpret_cast<double*>(c);
+  c += cpb;
+  p.shell = reinterpret_cast<double*>(c);
+  c += shell;
+  p.shell2 = reinterpret_cast<double*>(c);
+}
+
+}  // namespace sp
+
+extern "C" {
+
+const char* sp_status_string(int status) {
+  switch (status) {
+    case SP_OK: return "SP_OK";
+    case SP_ERR_INVALID_ARG: return "SP_ERR_INVALID_ARG";
+    case SP_ERR_GRID: return "SP_ERR_GRID";
+    case SP_ERR_CUDA: return "SP_ERR_CUDA";
+    case SP_ERR_OOM: return "SP_ERR_OOM";
+    case SP_ERR_NOT_CONVERGED: return "SP_ERR_NOT_CONVERGED";
+    case SP_ERR_TIMEOUT: return "SP_ERR_TIMEOUT";
+    case SP_ERR_DEVICE_CHECK: return "SP_ERR_DEVICE_CHECK";
+    case SP_ERR_UNSUPPORTED: return "SP_ERR_UNSUPPORTED";
+    default: return "SP_ERR_UNKNOWN";
+  }
+}
+
+int sp_plan_create(const double* r_if, int nr, const double* th_if_in, int nth, int nphi, int outer_bc,
+                   double G, int precision, double tol, int max_iter, void* stream, sp_plan** out) {
+  if (!out || !r_if) return SP_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (nr < 1 || nth < 1 || nphi < 1) return SP_ERR_GRID;
+  if (outer_bc != SP_OUTER_MULTIPOLE && outer_bc != SP_OUTER_DIRICHLET) return SP_ERR_INVALID_ARG;
+  if (precision != SP_FP64 && precision != SP_MIXED_BF16X3) return SP_ERR_INVALID_ARG;
+  if (!std::isfinite(G)) return SP_ERR_INVALID_ARG;
+  if (precision != SP_FP64) return SP_ERR_UNSUPPORTED;
+  if (nth > sp::kMaxNtheta || nphi > sp::kMaxNphi) return SP_ERR_UNSUPPORTED;
+  sp::FftSchedule sched;
+  if (!make_schedule(nphi, &sched)) return SP_ERR_UNSUPPORTED;
+  // --- validate the grid
+  if (!(r_if[0] >= 0.0) || !std::isfinite(r_if[0])) return SP_ERR_GRID;
+  for (int i = 0; i < nr; ++i)
+    if (!(r_if[i + 1] > r_if[i]) || !std::isfinite(r_if[i + 1])) return SP_ERR_GRID;
+  std::vector<double> th(nth + 1);
+  if (th_if_in) {
+    for (int j = 0; j <= nth; ++j) th[j] = th_if_in[j];
+    if (th[0] != 0.0 || std::fabs(th[nth] - kPi) > 1e-12) return SP_ERR_GRID;
+    for (int j = 0; j < nth; ++j)
+      if (!(th[j + 1] > th[j])) return SP_ERR_GRID;
+    th[nth] = kPi;
+  } else {
+    for (int j = 0; j <= nth; ++j) th[j] = kPi * j / nth;
+    th[nth] = kPi;
+  }
+
+  Plan* p = new (std::nothrow) Plan();
+  if (!p) return SP_ERR_OOM;
+  cudaGetDevice(&p->device);
+  p->nr = nr;
+  p->nth = nth;
+  p->nphi = nphi;
+  p->mh = nphi / 2 + 1;
+  p->outer_bc = outer_bc;
+  p->precision = precision;
+  p->G = G;
+  p->tol = tol;
+  p->max_iter = max_iter;
+  p->sched = sched;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+  // --- Sect. 3.1 geometry (host, float64)
+  std::vector<double> rc(nr), dv3(nr), R(nr);
+  for (int i = 0; i < nr; ++i) {
+    const double rm = r_if[i], rp = r_if[i + 1];
+    rc[i] = 0.5 * (rm + rp);
+    dv3[i] = rp * rp * rp - rm * rm * rm;
+    R[i] = 3.0 * (rp * rp - rm * rm) / (2.0 * rc[i] * dv3[i]);
+  }
+  std::vector<sp::RadialRow> rad(nr);
+  for (int i = 0; i < nr; ++i) {
+    const double sub = (i > 0) ? 3.0 * r_if[i] * r_if[i] / ((rc[i] - rc[i - 1]) * dv3[i]) : 0.0;
+    const double sup = (i < nr - 1) ? 3.0 * r_if[i + 1] * r_if[i + 1] / ((rc[i + 1] - rc[i]) * dv3[i]) : 0.0;
+    rad[i] = {sub, sup, R[i], -(sub + sup)};
+  }
+  p->r_out = r_if[nr];
+  p->r_last = rc[nr - 1];
+  p->outer_coef = 3.0 * p->r_out * p->r_out / dv3[nr - 1];
+
+  std::vector<double> thc(nth), w(nth), dth(nth), sinc(nth), sinf(nth + 1), tface(nth > 1 ? nth - 1 : 1, 0.0);
+  for (int j = 0; j <= nth; ++j) sinf[j] = (j == 0 || j == nth) ? 0.0 : std::sin(th[j]);
+  for (int j = 0; j < nth; ++j) {
+    thc[j] = 0.5 * (th[j] + th[j + 1]);
+    w[j] = std::cos(th[j]) - std::cos(th[j + 1]);
+    dth[j] = th[j + 1] - th[j];
+    sinc[j] = std::sin(thc[j]);
+  }
+  for (int j = 0; j + 1 < nth; ++j) tface[j] = sinf[j + 1] / (thc[j + 1] - thc[j]);
+  // equatorially symmetric grid with even Ntheta: mirror the lower half exactly so the
+  // operator commutes with the reflection (enables the parity-split eigensolve)
+  bool symmetric = (nth % 2 == 0);
+  for (int j = 0; symmetric && j <= nth; ++j)
+    if (std::fabs(th[j] + th[nth - j] - kPi) > 1e-13) symmetric = false;
+  if (symmetric) {
+    for (int j = nth / 2; j < nth; ++j) {
+      const int q = nth - 1 - j;
+      w[j] = w[q];
+      dth[j] = dth[q];
+      sinc[j] = sinc[q];
+      thc[j] = kPi - thc[q];
+    }
+    for (int j = nth / 2; j + 1 < nth; ++j) tface[j] = tface[nth - 2 - j];
+  }
+  p->parity = symmetric;
+  const double dphi = 2.0 * kPi / nphi;
+  std::vector<sp::ThetaRow> thr(nth);
+  for (int j = 0; j < nth; ++j) {
+    const double tp = (j + 1 < nth) ? tface[j] / w[j] : 0.0;
+    const double tm = (j > 0) ? tface[j - 1] / w[j] : 0.0;
+    const double S = dth[j] / (sinc[j] * w[j]);
+    thr[j] = {tp, tm, (nphi > 1) ? S / (dphi * dphi) : 0.0, 0.0};
+  }
+  // T_m = W^-1/2 B_m W^-1/2: diag (B_jj)/w_j, offdiag t_{j+1/2}/sqrt(w_j w_{j+1})
+  const int mh = p->mh;
+  std::vector<double> tdiag((size_t)mh * nth), toff(nth, 0.0), sqw(nth);
+  for (int j = 0; j < nth; ++j) sqw[j] = std::sqrt(w[j]);
+  for (int j = 0; j + 1 < nth; ++j) toff[j] = tface[j] / (sqw[j] * sqw[j + 1]);
+  for (int m = 0; m < mh; ++m) {
+    const double hs = std::sin(m * 0.5 * dphi) / (0.5 * dphi);
+    const double lphi = -hs * hs;
+    for (int j = 0; j < nth; ++j) {
+      double b = lphi * dth[j] / sinc[j];
+      if (j + 1 < nth) b -= tface[j];
+      if (j > 0) b -= tface[j - 1];
+      tdiag[(size_t)m * nth + j] = b / w[j];
+    }
+  }
+  // twiddles exp(-2 pi i t/nphi) with exact symmetry at the quarter points
+  std::vector<double> tw(2 * (size_t)nphi);
+  std::vector<float> tw32(2 * (size_t)nphi);
+  for (int t = 0; t < nphi; ++t) {
+    const double a = 2.0 * kPi * t / nphi;
+    double c = std::cos(a), sn = std::sin(a);
+    if (4 * t == nphi || 4 * t == 3 * nphi) c = 0.0;
+    if (2 * t == nphi) sn = 0.0;
+    tw[2 * t] = c;
+    tw[2 * t + 1] = -sn;
+    tw32[2 * t] = (float)c;
+    tw32[2 * t + 1] = (float)-sn;
+  }
+
+  int st = SP_OK;
+  DeviceGuard guard(p->device);
+  do {
+    if ((st = upload(&p->d_rad, rad.data(), rad.size()))) break;
+    if ((st = upload(&p->d_theta, thr.data(), thr.size()))) break;
+    if ((st = upload(&p->d_twid, tw.data(), tw.size()))) break;
+    if ((st = upload(&p->d_twid32, tw32.data(), tw32.size()))) break;
+    if ((st = upload(&p->d_tdiag, tdiag.data(), tdiag.size()))) break;
+    if ((st = upload(&p->d_toff, toff.data(), toff.size()))) break;
+    if ((st = upload(&p->d_sqw, sqw.data(), sqw.size()))) break;
+    const size_t tab = (size_t)mh * nth;
+    const size_t mat = tab * nth;
+    if (cudaMalloc(&p->d_lam, sizeof(double) * tab) != cudaSuccess ||
+        cudaMalloc(&p->d_kappa, sizeof(double) * tab) != cudaSuccess ||
+        cudaMalloc(&p->d_outer, sizeof(double) * tab) != cudaSuccess ||
+        cudaMalloc(&p->d_HtW, sizeof(double) * mat) != cudaSuccess ||
+        cudaMalloc(&p->d_H, sizeof(double) * mat) != cudaSuccess ||
+        cudaMalloc(&p->d_err, sizeof(int)) != cudaSuccess) {
+      st = SP_ERR_OOM;
+      break;
+    }
+    if (cudaMemsetAsync(p->d_err, 0, sizeof(int), s) != cudaSuccess) { st = SP_ERR_CUDA; break; }
+    if ((st = launch_status(sp::theta_eigen(*p, s)))) break;
+    int herr = 0;
+    if (cudaMemcpyAsync(&herr, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      st = SP_ERR_CUDA;
+      break;
+    }
+    if (herr) { st = SP_ERR_DEVICE_CHECK; break; }
+  } while (0);
+  if (st != SP_OK) {
+    free_tables(p);
+    delete p;
+    return st;
+  }
+  *out = reinterpret_cast<sp_plan*>(p);
+  return SP_OK;
+}
+
+size_t sp_plan_workspace_bytes(const sp_plan* plan) {
+  if (!plan) return 0;
+  return sp::workspace_bytes(*reinterpret_cast<const Plan*>(plan));
+}
+
+int sp_plan_set_workspace(sp_plan* plan, void* dev, size_t bytes) {
+  if (!plan || !dev) return SP_ERR_INVALID_ARG;
+  Plan* p = reinterpret_cast<Plan*>(plan);
+  if (bytes < sp::workspace_bytes(*p) || (reinterpret_cast<uintptr_t>(dev) & 255)) return SP_ERR_INVALID_ARG;
+  DeviceGuard guard(p->device);
+  if (p->ws_owned) {
+    cudaDeviceSynchronize();
+    cudaFree(p->ws);
+  }
+  p->ws = dev;
+  p->ws_bytes = bytes;
+  p->ws_owned = false;
+  sp::bind_workspace(*p, dev);
+  return SP_OK;
+}
+
+int sp_solve(sp_plan* plan, const double* rho, double* phi, void* stream, sp_solve_info* info) {
+  if (!plan || !rho || !phi) return SP_ERR_INVALID_ARG;
+  Plan* p = reinterpret_cast<Plan*>(plan);
+  const size_t bytes = sizeof(double) * (size_t)p->nr * p->nth * p->nphi;
+  if (overlaps(rho, phi, bytes)) return SP_ERR_INVALID_ARG;
+  DeviceGuard guard(p->device);
+  int st = ensure_workspace(p);
+  if (st) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st = solve_fp64(p, rho, phi, s);
+  if (info) {
+    info->iterations = 1;
+    info->precision_used = SP_FP64;
+    info->last_update = 0.0;
+    info->est_rel_error = 0.0;
+    info->status = st;
+  }
+  return st;
+}
+
+int sp_solve_host(sp_plan* plan, const double* rho_host, double* phi_host, void* stream, sp_solve_info* info) {
+  if (!plan || !rho_host || !phi_host) return SP_ERR_INVALID_ARG;
+  Plan* p = reinterpret_cast<Plan*>(plan);
+  const size_t bytes = sizeof(double) * (size_t)p->nr * p->nth * p->nphi;
+  DeviceGuard guard(p->device);
+  if (!p->d_rho_io) SP_CUDA(cudaMalloc(&p->d_rho_io, bytes));
+  if (!p->d_phi_io) SP_CUDA(cudaMalloc(&p->d_phi_io, bytes));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  SP_CUDA(cudaMemcpyAsync(p->d_rho_io, rho_host, bytes, cudaMemcpyHostToDevice, s));
+  int st = sp_solve(plan, p->d_rho_io, p->d_phi_io, stream, info);
+  if (st) return st;
+  SP_CUDA(cudaMemcpyAsync(phi_host, p->d_phi_io, bytes, cudaMemcpyDeviceToHost, s));
+  SP_CUDA(cudaStreamSynchronize(s));
+  return SP_OK;
+}
+
+int sp_apply_laplacian(sp_plan* plan, const double* phi, double* out, void* stream) {
+  if (!plan || !phi || !out) return SP_ERR_INVALID_ARG;
+  Plan* p = reinterpret_cast<Plan*>(plan);
+  const size_t bytes = sizeof(double) * (size_t)p->nr * p->nth * p->nphi;
+  if (overlaps(phi, out, bytes)) return SP_ERR_INVALID_ARG;
+  DeviceGuard guard(p->device);
+  int st = ensure_workspace(p);
+  if (st) return st;
+  return apply_laplacian_impl(p, phi, out, static_cast<cudaStream_t>(stream));
+}
+
+int sp_plan_set_timing(sp_plan* plan, int enable) {
+  if (!plan) return SP_ERR_INVALID_ARG;
+  Plan* p = reinterpret_cast<Plan*>(plan);
+  DeviceGuard guard(p->device);
+  if (enable && !p->ev[0]) {
+    for (int i = 0; i < 2 * sp::kMaxTimedLaunches; ++i) SP_CUDA(cudaEventCreate(&p->ev[i]));
+  }
+  p->timing = enable != 0;
+  p->n_timed = 0;
+  for (int k = 0; k < sp::kNumKernelIds; ++k) { p->acc_ms[k] = 0.0; p->acc_n[k] = 0; }
+  return SP_OK;
+}
+
+int sp_plan_collect_timing(sp_plan* plan) {
+  if (!plan) return SP_ERR_INVALID_ARG;
+  Plan* p = reinterpret_cast<Plan*>(plan);
+  DeviceGuard guard(p->device);
+  for (int i = 0; i < p->n_timed; ++i) {
+    SP_CUDA(cudaEventSynchronize(p->ev[2 * i + 1]));
+    float ms = 0.f;
+    SP_CUDA(cudaEventElapsedTime(&ms, p->ev[2 * i], p->ev[2 * i + 1]));
+    p->acc_ms[p->ev_kernel[i]] += ms;
+    p->acc_n[p->ev_kernel[i]] += 1;
+  }
+  p->n_timed = 0;
+  return SP_OK;
+}
+
+int sp_plan_get_timing(const sp_plan* plan, double* ms, long long* count, int n) {
+  if (!plan || !ms || !count) return SP_ERR_INVALID_ARG;
+  const Plan* p = reinterpret_cast<const Plan*>(plan);
+  for (int k = 0; k < n && k < sp::kNumKernelIds; ++k) {
+    ms[k] = p->acc_ms[k];
+    count[k] = p->acc_n[k];
+  }
+  return SP_OK;
+}
+
+long long sp_plan_launch_count(const sp_plan* plan) {
+  if (!plan) return -1;
+  return reinterpret_cast<const Plan*>(plan)->launches;
+}
+
+int sp_plan_get_eigen(const sp_plan* plan, double* lambda, double* H, double* kappa) {
+  if (!plan) return SP_ERR_INVALID_ARG;
+  const Plan* p = reinterpret_cast<const Plan*>(plan);
+  DeviceGuard guard(p->device);
+  SP_CUDA(cudaDeviceSynchronize());
+  const size_t tab = (size_t)p->mh * p->nth;
+  if (lambda) SP_CUDA(cudaMemcpy(lambda, p->d_lam, sizeof(double) * tab, cudaMemcpyDeviceToHost));
+  if (kappa) SP_CUDA(cudaMemcpy(kappa, p->d_kappa, sizeof(double) * tab, cudaMemcpyDeviceToHost));
+  if (H) SP_CUDA(cudaMemcpy(H, p->d_H, sizeof(double) * tab * p->nth, cudaMemcpyDeviceToHost));
+  return SP_OK;
+}
+
+int sp_plan_last_status(const sp_plan* plan) {
+  if (!plan) return SP_ERR_INVALID_ARG;
+  const Plan* p = reinterpret_cast<const Plan*>(plan);
+  DeviceGuard guard(p->device);
+  int herr = 0;
+  SP_CUDA(cudaDeviceSynchronize());
+  SP_CUDA(cudaMemcpy(&herr, p->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (herr & sp::kErrEigenIter) return SP_ERR_DEVICE_CHECK;
+  if (herr) return SP_ERR_DEVICE_CHECK;
+  return SP_OK;
+}
+
+int sp_plan_destroy(sp_plan* plan) {
+  if (!plan) return SP_OK;
+  Plan* p = reinterpret_cast<Plan*>(plan);
+  DeviceGuard guard(p->device);
+  cudaDeviceSynchronize();
+  free_tables(p);
+  delete p;
+  return SP_OK;
+}
+
+}  // extern "C"

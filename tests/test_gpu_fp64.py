@@ -1,0 +1,166 @@
+"""Parity of the float64 CUDA path with the CPU oracle, through the C ABI.
+
+Gate: max|dPhi|/max|Phi| <= 1e-12 against the oracle's exact float64 solution (the
+separated solve with residual correction), and a backward error eta <= 1e-12 of the
+float64 finite-volume operator."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import sph_poisson as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1806_06623_gb300 as S
+    S.lib()
+    return S
+
+
+def gpu_solve(S, p, **kw):
+    plan = S.Plan(p.r_if, p.th_if, p.nphi, outer_bc=p.outer_bc, G=p.G, **kw)
+    rho = torch.from_numpy(np.ascontiguousarray(p.rho)).cuda()
+    phi, info = plan.solve(rho)
+    torch.cuda.synchronize()
+    assert plan.last_status() == S.SP_OK
+    return plan, phi.cpu().numpy(), info
+
+
+def rel_err(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+CASES = [
+    # nr, nth, nphi, grid, r_inner, bc
+    (5, 4, 6, "log", 0.0, 0),
+    (7, 8, 12, "rand", 0.0, 0),
+    (5, 3, 6, "rand", 0.2, 0),        # odd number of lines, inner zero-flux boundary
+    (6, 5, 9, "uniform", 0.0, 1),     # Dirichlet, radix 3 only
+    (3, 1, 4, "uniform", 0.0, 0),     # one theta zone
+    (4, 4, 1, "uniform", 0.0, 0),     # axisymmetric
+    (1, 3, 4, "uniform", 0.5, 0),     # one radial shell
+    (33, 17, 48, "log", 0.0, 0),      # several tiles with ragged tails
+    (65, 31, 96, "rand", 0.1, 0),
+    (40, 160, 12, "log", 0.0, 0),     # largest supported Ntheta
+    (9, 6, 384, "uniform", 0.0, 1),   # long phi lines
+]
+
+
+@pytest.mark.parametrize("nr,nth,nphi,grid,rin,bc", CASES)
+def test_solve_matches_oracle_small(S, nr, nth, nphi, grid, rin, bc):
+    p = W.random_small(nr, nth, nphi, seed=nr + 3 * nth + nphi, grid=grid, r_inner=rin, outer_bc=bc)
+    _, phi, info = gpu_solve(S, p)
+    geo = O.Geometry(p.r_if, p.th_if, p.nphi)
+    ref = O.solve_exact(geo, p.rho, outer_bc=bc)
+    assert rel_err(phi, ref) <= TOL
+    assert info.iterations == 1 and info.status == S.SP_OK
+
+
+def test_solve_nonuniform_theta(S):
+    p = W.random_small(12, 10, 16, seed=4)
+    th = W.random_theta_interfaces(10, seed=8)
+    p.th_if = th
+    _, phi, _ = gpu_solve(S, p)
+    ref = O.solve_exact(O.Geometry(p.r_if, th, p.nphi), p.rho)
+    assert rel_err(phi, ref) <= TOL
+
+
+@pytest.mark.parametrize("make", [W.sphere_blob, W.stellar_noise])
+def test_solve_matches_oracle_workloads(S, make):
+    p = make()
+    plan, phi, _ = gpu_solve(S, p)
+    geo = O.Geometry(p.r_if, p.th_if, p.nphi)
+    ref = O.solve_exact(geo, p.rho)
+    assert rel_err(phi, ref) <= TOL
+    eta, _ = O.residuals(geo, phi, p.rho)
+    assert eta <= TOL
+
+
+def test_solve_full_size_stellar_sh(S):
+    """550x128x256 (the headline grid), compared with the oracle element by element."""
+    p = W.stellar_sh()
+    plan, phi, _ = gpu_solve(S, p)
+    geo = O.Geometry(p.r_if, p.th_if, p.nphi)
+    ref = O.solve_exact(geo, p.rho)
+    assert rel_err(phi, ref) <= TOL
+    eta, _ = O.residuals(geo, phi, p.rho)
+    assert eta <= TOL
+
+
+def test_gauss_law_on_gpu(S):
+    g = O.Geometry(W.uniform_r_interfaces(32), W.uniform_theta_interfaces(16), 32)
+    rho_r = (g.rc < 0.5).astype(float)
+    p = W.Problem("sphere", g.r_if, g.th_if, 32, np.ascontiguousarray(
+        np.broadcast_to(rho_r[:, None, None], (32, 16, 32))))
+    _, phi, _ = gpu_solve(S, p)
+    ex = O.gauss_law_potential(g, rho_r)
+    assert np.max(np.abs(phi - ex[:, None, None])) / np.max(np.abs(ex)) <= 1e-13
+
+
+@pytest.mark.parametrize("nr,nth,nphi,grid,rin,bc", [CASES[0], CASES[2], CASES[3], CASES[7], CASES[8]])
+def test_apply_laplacian_matches_oracle(S, nr, nth, nphi, grid, rin, bc):
+    p = W.random_small(nr, nth, nphi, seed=5, grid=grid, r_inner=rin, outer_bc=bc)
+    plan = S.Plan(p.r_if, p.th_if, p.nphi, outer_bc=bc)
+    phi = np.random.default_rng(3).standard_normal(p.rho.shape)
+    out = plan.apply_laplacian(torch.from_numpy(phi).cuda()).cpu().numpy()
+    geo = O.Geometry(p.r_if, p.th_if, p.nphi)
+    kmat = O.outer_operator_dense(geo) if (bc == 0 and nth * nphi <= 1200) else None
+    ref = O.apply_laplacian(geo, phi, bc, kmat)
+    scale = np.max(O.abs_apply(geo, phi, bc, kmat))
+    assert np.max(np.abs(out - ref)) <= 1e-14 * scale
+
+
+def test_laplacian_inverts_solve(S):
+    """L(solve(rho)) = 4 pi G rho, both on the GPU (backward error of the float64 path)."""
+    p = W.stellar_noise()
+    plan, phi, _ = gpu_solve(S, p)
+    lap = plan.apply_laplacian(torch.from_numpy(phi).cuda()).cpu().numpy()
+    geo = O.Geometry(p.r_if, p.th_if, p.nphi)
+    s = 4 * math.pi * p.rho
+    den = np.max(np.abs(s) + O.abs_apply(geo, phi))
+    assert np.max(np.abs(lap - s)) / den <= TOL
+
+
+def test_eigenbasis_invariants(S):
+    p = W.random_small(4, 128, 256, seed=1)
+    plan = S.Plan(p.r_if, p.th_if, p.nphi)
+    lam, H, kap = plan.eigen()
+    geo = O.Geometry(p.r_if, p.th_if, p.nphi)
+    for m in (0, 1, 2, 31, 64, 127, 128):
+        h = H[m]
+        assert np.max(np.abs(h.T @ (geo.w[:, None] * h) - np.eye(128))) <= 1e-13
+        d, e = O.theta_matrix(geo, m)
+        b = np.diag(d) + np.diag(e, 1) + np.diag(e, -1)
+        res = (b @ h - geo.w[:, None] * h * lam[m][None, :]) / np.sqrt(geo.w)[:, None]
+        assert np.max(np.abs(res)) <= 1e-13 * np.max(np.abs(lam[m]))
+        ref_lam, _ = O.theta_eigen(geo, m)
+        assert np.max(np.abs(lam[m] - ref_lam)) <= 1e-13 * np.max(np.abs(ref_lam))
+        # kappa(lambda) evaluated on the device for the device's own eigenvalues
+        assert np.allclose(kap[m], O.kappa(lam[m], geo.r_out, geo.rc[-1]), rtol=1e-13, atol=0)
+    # the m=0 null mode is deflated exactly: lambda = 0 with a constant eigenvector
+    assert lam[0, 0] == 0.0
+    assert np.allclose(H[0][:, 0] * np.sign(H[0][0, 0]), 1.0 / math.sqrt(np.sum(geo.w)), rtol=1e-14, atol=0)
+
+
+def test_solve_host_buffers(S):
+    p = W.sphere_blob()
+    plan, phi, _ = gpu_solve(S, p)
+    out, info = plan.solve_host(p.rho)
+    assert np.array_equal(out, phi)
+
+
+def test_bad_pointers_rejected(S):
+    p = W.random_small(4, 4, 8, seed=1)
+    plan = S.Plan(p.r_if, p.th_if, p.nphi)
+    x = torch.zeros(p.rho.shape, dtype=torch.float64, device="cuda")
+    with pytest.raises(S.SpError):
+        S.sp_solve(plan.handle, x, x, p.rho.shape)      # Phi aliases rho

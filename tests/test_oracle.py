@@ -51,6 +51,27 @@ def test_separated_equals_dense_lu_nonuniform_theta():
     assert np.max(np.abs(a - b)) / np.max(np.abs(b)) <= 1e-13
 
 
+@pytest.mark.parametrize("nr,nth,nphi,grid,rin,bc", TINY[:5])
+def test_exact_solve_equals_dense_lu(nr, nth, nphi, grid, rin, bc):
+    p = W.random_small(nr, nth, nphi, seed=nr * 7 + nth, grid=grid, r_inner=rin)
+    g = geo_of(p)
+    a = O.solve_exact(g, p.rho, outer_bc=bc)
+    b = O.solve_dense(g, p.rho, outer_bc=bc)
+    assert np.max(np.abs(a - b)) / np.max(np.abs(b)) <= 2e-14
+
+
+def test_exact_solve_converges_and_is_a_fixed_point():
+    p = W.stellar_noise()
+    g = geo_of(p)
+    phi, hist = O.solve_exact(g, p.rho, return_history=True)
+    assert hist[-1] <= 1e-15 and len(hist) <= 3
+    plain = O.solve_separated(g, p.rho)
+    # the plain separated solve is within the float64 forward-error level of the exact one
+    assert np.max(np.abs(plain - phi)) / np.max(np.abs(phi)) <= 2e-12
+    eta, _ = O.residuals(g, phi, p.rho)
+    assert eta <= 1e-15
+
+
 def test_backward_error_moderate_grid():
     p = W.stellar_noise()
     g = geo_of(p)
