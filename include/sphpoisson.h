@@ -124,6 +124,26 @@ int sp_solve_host(sp_plan* plan, const double* rho_host, double* phi_host, void*
  *  phi_dev, out_dev  device, Nr*Ntheta*Nphi float64; must not overlap */
 int sp_apply_laplacian(sp_plan* plan, const double* phi_dev, double* out_dev, void* stream);
 
+/* sp_apply_laplacian without device allocation.  The paper has no counterpart: this is
+ * for callers that cannot call cudaMalloc where they need the operator -- code that
+ * must not synchronise the device (cudaMalloc/cudaFree may), or that runs under a host
+ * framework owning a fixed device-memory pool.  The plan itself is created (and
+ * allocates its tables) beforehand.
+ *  - Result: identical to sp_apply_laplacian on the same plan and input.
+ *  - Scratch: the outer-shell spectra of the multipole boundary term live in one
+ *    fixed 4 MiB array inside the library's device image (every GPU that loads the
+ *    library holds it until the process exits).  Plans needing more,
+ *    2 x 256-byte-aligned (Nphi/2+1)*2*Ntheta doubles > 4 MiB, get SP_ERR_UNSUPPORTED.
+ *  - Set-up: the first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call before
+ *    any stream capture.
+ *  - Sharing: every call uses the same array and leaves the last call's contents in
+ *    it (all of it is rewritten before it is read).  Calls that overlap on the GPU --
+ *    on different streams, or from different threads -- race and must be serialised
+ *    by the caller.
+ *  phi_dev, out_dev  device, Nr*Ntheta*Nphi float64; must not overlap */
+int sp_apply_laplacian_noalloc(sp_plan* plan, const double* phi_dev, double* out_dev, void* stream);
+
 /* Copy the plan's theta eigenbasis (Sect. 3.2) to host memory, any pointer may be NULL:
  *  lambda   (Nphi/2+1) x Ntheta: lambda_Omega,l,m, row m, descending in l
  *  H        (Nphi/2+1) x Ntheta x Ntheta: H[m][j][l] = H_{l,m}(j), W-orthonormal

@@ -54,6 +54,7 @@ _SIGS = {
     "sp_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(SolveInfo)]),
     "sp_solve_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(SolveInfo)]),
     "sp_apply_laplacian": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sp_apply_laplacian_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "sp_plan_get_eigen": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "sp_plan_last_status": (C.c_int, [C.c_void_p]),
     "sp_plan_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
@@ -171,6 +172,14 @@ def sp_apply_laplacian(plan, phi, out, shape, stream=None):
     n = int(np.prod(shape))
     _check(lib().sp_apply_laplacian(plan, _dev_ptr(phi, n, "phi"), _dev_ptr(out, n, "out"),
                                     _stream_ptr(stream, phi.device)), "sp_apply_laplacian")
+
+
+def sp_apply_laplacian_noalloc(plan, phi, out, shape, stream=None):
+    """sp_apply_laplacian for callers that cannot allocate device memory: its scratch is
+    a fixed 4 MiB array in the library (see include/sphpoisson.h)."""
+    n = int(np.prod(shape))
+    _check(lib().sp_apply_laplacian_noalloc(plan, _dev_ptr(phi, n, "phi"), _dev_ptr(out, n, "out"),
+                                            _stream_ptr(stream, phi.device)), "sp_apply_laplacian_noalloc")
 
 
 def sp_plan_get_eigen(plan, mh, nth):
