@@ -159,7 +159,7 @@ def run_ours(args, rank, world, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     S.lib()
-    precision = args.precision or "fp64"
+    precision = args.precision or "mixed"
     p = W.stellar_sh()
     zones = p.zones
     rho = torch.from_numpy(p.rho).to(dev)

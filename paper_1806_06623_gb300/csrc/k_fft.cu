@@ -1,17 +1,23 @@
 // Real FFTs along phi (Sect. 3.2: expansion in h_m(k) = exp(2 pi i m k / Nphi)).
 //
-// One CTA transforms a chunk of consecutive phi lines (line g = i*Ntheta + j, each
-// Nphi contiguous doubles).  Two real lines are packed into one complex line
-// z = x_A + i x_B, transformed by a mixed-radix (4, 2, 3) Stockham FFT staged in
-// shared memory, and separated with X_A[m] = (Z[m] + conj Z[N-m])/2,
-// X_B[m] = (Z[m] - conj Z[N-m])/(2i).  The half spectrum m = 0..Nphi/2 is written in
-// the spectral layout [m][i][c][j] (c = re/im, j fastest) that the theta projection
-// reads as a K-contiguous panel.  The inverse kernel rebuilds the Hermitian spectrum
-// of two lines, runs the inverse FFT and writes both real lines.
+// One CTA (8 warps) transforms a chunk of up to 32 consecutive phi lines (line
+// g = i*Ntheta + j, Nphi contiguous values each).  Two real lines are packed into one
+// complex line z = x_A + i x_B; every packed line is owned by one warp, which runs a
+// mixed-radix (4, 2, 3) Stockham FFT on it in shared memory with only warp-level
+// synchronisation.  Lines are stored at a padded stride of Nphi+1 complex values so
+// that lanes addressing consecutive lines hit different banks.  The forward kernel
+// separates X_A[m] = (Z[m] + conj Z[N-m])/2, X_B[m] = (Z[m] - conj Z[N-m])/(2i) and
+// writes the half spectrum m = 0..Nphi/2 in the layout [m][i][c][j] that the theta
+// projection reads (lane = line, so each warp store is a run of consecutive j).  The
+// inverse kernel rebuilds the Hermitian spectrum of each line pair with one lane-pair
+// shuffle, runs the inverse FFT and writes (or accumulates, or adds into a
+// float-float iterate) both real lines.
 #include "sp_internal.h"
 
 namespace sp {
 namespace {
+
+constexpr int kWarps = 8;
 
 template <typename T> struct C2;
 template <> struct C2<double> { using t = double2; };
@@ -36,79 +42,81 @@ __device__ __forceinline__ CT mul_mi(CT a) {
   return r;
 }
 
-// One Stockham stage of radix R over `npairs` independent length-n transforms.
-// Butterfly b reads src[b + r n/R], applies twiddles exp(-+2 pi i r k/(Ns R)),
-// k = b mod Ns, and writes dst[(b/Ns) Ns R + k + r Ns].
+__device__ __forceinline__ int div_ns(int x, const FftSchedule& sch, int s) {
+  return sch.shift[s] >= 0 ? (x >> sch.shift[s]) : (int)__umulhi((unsigned int)x, sch.magic[s]);
+}
+
+// One radix-R Stockham butterfly b of a stage on one line: reads src[b + r n/R],
+// applies twiddles exp(-+2 pi i r k/(Ns R)), k = b mod Ns, writes dst[(b/Ns) Ns R + k + r Ns].
 template <bool INV, typename T>
-__device__ __forceinline__ void stockham_stage(const typename C2<T>::t* __restrict__ src,
-                                               typename C2<T>::t* __restrict__ dst,
-                                               const typename C2<T>::t* __restrict__ tw,
-                                               int n, int R, int Ns, int npairs) {
+__device__ __forceinline__ void butterfly(const typename C2<T>::t* __restrict__ s, typename C2<T>::t* __restrict__ d,
+                                          const typename C2<T>::t* __restrict__ tw, int n, int R, int Ns, int tstep,
+                                          int b, int bq) {
   using CT = typename C2<T>::t;
-  const int nb = n / R;
   const int stride = n / R;
-  const int tstep = n / (Ns * R);
-  const int total = npairs * nb;
-  for (int t = threadIdx.x; t < total; t += blockDim.x) {
-    const int p = t / nb;
-    const int b = t - p * nb;
-    const int k = b % Ns;
-    const CT* s = src + p * n;
-    CT* d = dst + p * n;
-    const int base = (b / Ns) * Ns * R + k;
-    if (R == 4) {
-      CT v0 = s[b], v1 = s[b + stride], v2 = s[b + 2 * stride], v3 = s[b + 3 * stride];
-      if (k != 0) {
-        CT w1 = tw[k * tstep], w2 = tw[2 * k * tstep], w3 = tw[3 * k * tstep];
-        if (INV) { w1.y = -w1.y; w2.y = -w2.y; w3.y = -w3.y; }
-        v1 = cmul(v1, w1); v2 = cmul(v2, w2); v3 = cmul(v3, w3);
-      }
-      CT a0 = cadd(v0, v2), a1 = csub(v0, v2), a2 = cadd(v1, v3), a3 = mul_mi<INV>(csub(v1, v3));
-      d[base] = cadd(a0, a2);
-      d[base + Ns] = cadd(a1, a3);
-      d[base + 2 * Ns] = csub(a0, a2);
-      d[base + 3 * Ns] = csub(a1, a3);
-    } else if (R == 2) {
-      CT v0 = s[b], v1 = s[b + stride];
-      if (k != 0) {
-        CT w1 = tw[k * tstep];
-        if (INV) w1.y = -w1.y;
-        v1 = cmul(v1, w1);
-      }
-      d[base] = cadd(v0, v1);
-      d[base + Ns] = csub(v0, v1);
-    } else {  // R == 3
-      CT v0 = s[b], v1 = s[b + stride], v2 = s[b + 2 * stride];
-      if (k != 0) {
-        CT w1 = tw[k * tstep], w2 = tw[2 * k * tstep];
-        if (INV) { w1.y = -w1.y; w2.y = -w2.y; }
-        v1 = cmul(v1, w1); v2 = cmul(v2, w2);
-      }
-      const T h = T(0.8660254037844386467637231707529362);  // sin(2 pi/3)
-      CT t1 = cadd(v1, v2), t2 = csub(v1, v2);
-      CT a; a.x = v0.x - T(0.5) * t1.x; a.y = v0.y - T(0.5) * t1.y;
-      CT bb; bb.x = h * t2.x; bb.y = h * t2.y;
-      CT jb = mul_mi<INV>(bb);  // -i b forward, +i b inverse
-      d[base] = cadd(v0, t1);
-      d[base + Ns] = cadd(a, jb);
-      d[base + 2 * Ns] = csub(a, jb);
+  const int k = b - bq * Ns;
+  const int base = bq * Ns * R + k;
+  if (R == 4) {
+    CT v0 = s[b], v1 = s[b + stride], v2 = s[b + 2 * stride], v3 = s[b + 3 * stride];
+    if (k != 0) {
+      CT w1 = tw[k * tstep], w2 = tw[2 * k * tstep], w3 = tw[3 * k * tstep];
+      if (INV) { w1.y = -w1.y; w2.y = -w2.y; w3.y = -w3.y; }
+      v1 = cmul(v1, w1); v2 = cmul(v2, w2); v3 = cmul(v3, w3);
     }
+    CT a0 = cadd(v0, v2), a1 = csub(v0, v2), a2 = cadd(v1, v3), a3 = mul_mi<INV>(csub(v1, v3));
+    d[base] = cadd(a0, a2);
+    d[base + Ns] = cadd(a1, a3);
+    d[base + 2 * Ns] = csub(a0, a2);
+    d[base + 3 * Ns] = csub(a1, a3);
+  } else if (R == 2) {
+    CT v0 = s[b], v1 = s[b + stride];
+    if (k != 0) {
+      CT w1 = tw[k * tstep];
+      if (INV) w1.y = -w1.y;
+      v1 = cmul(v1, w1);
+    }
+    d[base] = cadd(v0, v1);
+    d[base + Ns] = csub(v0, v1);
+  } else {  // R == 3
+    CT v0 = s[b], v1 = s[b + stride], v2 = s[b + 2 * stride];
+    if (k != 0) {
+      CT w1 = tw[k * tstep], w2 = tw[2 * k * tstep];
+      if (INV) { w1.y = -w1.y; w2.y = -w2.y; }
+      v1 = cmul(v1, w1); v2 = cmul(v2, w2);
+    }
+    const T h = T(0.8660254037844386467637231707529362);  // sin(2 pi/3)
+    CT t1 = cadd(v1, v2), t2 = csub(v1, v2);
+    CT a; a.x = v0.x - T(0.5) * t1.x; a.y = v0.y - T(0.5) * t1.y;
+    CT bb; bb.x = h * t2.x; bb.y = h * t2.y;
+    CT jb = mul_mi<INV>(bb);  // -i b forward, +i b inverse
+    d[base] = cadd(v0, t1);
+    d[base + Ns] = cadd(a, jb);
+    d[base + 2 * Ns] = csub(a, jb);
   }
 }
 
+// All stages for the line pairs owned by this warp (p = warp, warp+kWarps, ...).
+// Returns the buffer holding the result.
 template <bool INV, typename T>
-__device__ typename C2<T>::t* run_fft(typename C2<T>::t* bufA, typename C2<T>::t* bufB,
-                                      const typename C2<T>::t* tw, const FftSchedule& sch, int npairs) {
+__device__ typename C2<T>::t* warp_fft(typename C2<T>::t* bufA, typename C2<T>::t* bufB,
+                                       const typename C2<T>::t* tw, const FftSchedule& sch, int npairs, int PS) {
   using CT = typename C2<T>::t;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   CT* src = bufA;
   CT* dst = bufB;
-  int Ns = 1;
-  for (int s = 0; s < sch.nstages; ++s) {
-    const int R = sch.radix[s];
-    stockham_stage<INV, T>(src, dst, tw, sch.n, R, Ns, npairs);
-    __syncthreads();
+  const int n = sch.n;
+  for (int st = 0; st < sch.nstages; ++st) {
+    const int R = sch.radix[st];
+    const int Ns = sch.ns[st];
+    const int tstep = sch.tstep[st];
+    const int nb = n / R;
+    for (int p = warp; p < npairs; p += kWarps) {
+      const CT* s = src + p * PS;
+      CT* d = dst + p * PS;
+      for (int b = lane; b < nb; b += 32) butterfly<INV, T>(s, d, tw, n, R, Ns, tstep, b, div_ns(b, sch, st));
+    }
+    __syncwarp();
     CT* t = src; src = dst; dst = t;
-    Ns *= R;
   }
   return src;
 }
@@ -121,164 +129,273 @@ __device__ void load_twiddles(typename C2<T>::t* tw, const T* __restrict__ g, in
   }
 }
 
-// Forward: lines [line0, line0+nl) of `in` -> half spectrum (scaled) in spec.
-template <typename T, typename Tin>
-__global__ void __launch_bounds__(256) k_fft_forward(const Tin* __restrict__ in, int nlines, int nth, int nrs,
-                                                     FftSchedule sch, const T* __restrict__ twid, T scale,
-                                                     int lpc, T* __restrict__ spec) {
+template <typename T>
+__device__ __forceinline__ T load_in(const double* p) { return (T)*p; }
+template <>
+__device__ __forceinline__ float load_in<float>(const double* p) { return d2ff(*p).hi; }   // no float64 pipe
+template <typename T>
+__device__ __forceinline__ T load_in(const float* p) { return (T)*p; }
+
+enum FwdOut { kOutPlain = 0, kOutSplit = 1 };
+
+// Forward: lines [line0, line0+nl) of `in` -> half spectrum scaled by `scale`:
+//  OUT = kOutPlain: spec[m][i][c][j] (row stride Ntheta)
+//  OUT = kOutSplit: bf16 pair hi/lo[m][i][c][j] (row stride kstride)
+template <typename T, typename Tin, int OUT>
+__global__ void __launch_bounds__(256) k_fft_fwd(const Tin* __restrict__ in, int nlines, int nth, int nrs,
+                                                 FftSchedule sch, const T* __restrict__ twid, T scale, int lpc,
+                                                 T* __restrict__ spec, __nv_bfloat16* __restrict__ hi,
+                                                 __nv_bfloat16* __restrict__ lo, int kstride) {
   using CT = typename C2<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = sch.n;
+  const int PS = n + 1;
   const int P = lpc / 2;
   CT* tw = reinterpret_cast<CT*>(smem_raw);
   CT* bufA = tw + n;
-  CT* bufB = bufA + P * (n + 2);
+  CT* bufB = bufA + P * PS;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   load_twiddles<T>(tw, twid, n);
   const int line0 = blockIdx.x * lpc;
   const int nl = min(lpc, nlines - line0);
   const int npairs = (nl + 1) / 2;
-  const Tin* src = in + (size_t)line0 * n;
-  const int tot = nl * n;
-  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-    const int l = e / n;
-    const int q = e - l * n;
-    T v = T(src[e]);
-    CT* z = bufA + (l >> 1) * n + q;
-    if (l & 1) z->y = v; else z->x = v;
-  }
-  if (nl & 1) {
-    for (int q = threadIdx.x; q < n; q += blockDim.x) bufA[(nl >> 1) * n + q].y = T(0);
+  for (int p = warp; p < npairs; p += kWarps) {
+    const Tin* a = in + (size_t)(line0 + 2 * p) * n;
+    const bool hasb = 2 * p + 1 < nl;
+    CT* z = bufA + p * PS;
+    for (int q = lane; q < n; q += 32) {
+      CT v;
+      v.x = load_in<T>(a + q);
+      v.y = hasb ? load_in<T>(a + n + q) : T(0);
+      z[q] = v;
+    }
   }
   __syncthreads();
-  CT* Z = run_fft<false, T>(bufA, bufB, tw, sch, npairs);
+  CT* Z = warp_fft<false, T>(bufA, bufB, tw, sch, npairs, PS);
+  __syncthreads();
   const int mh = n / 2 + 1;
-  const size_t cstride = nth;
-  for (int t = threadIdx.x; t < mh * nl; t += blockDim.x) {
-    const int m = t / nl;
-    const int l = t - m * nl;
-    const CT* zp = Z + (l >> 1) * n;
-    const CT a = zp[m];
-    const CT b = zp[(n - m) % n];
-    T re, im;
-    if (l & 1) {   // (Z - conj Zc)/(2i)
-      re = T(0.5) * (a.y + b.y);
-      im = T(-0.5) * (a.x - b.x);
-    } else {       // (Z + conj Zc)/2
-      re = T(0.5) * (a.x + b.x);
-      im = T(0.5) * (a.y - b.y);
-    }
+  const int l = lane;
+  if (l < nl) {
     const int g = line0 + l;
     const int i = g / nth;
     const int j = g - i * nth;
-    T* o = spec + ((size_t)(m * nrs + i) * 2) * cstride + j;
-    o[0] = re * scale;
-    o[cstride] = im * scale;
+    const CT* zp = Z + (l >> 1) * PS;
+    for (int m = warp; m < mh; m += kWarps) {
+      const CT a = zp[m];
+      const CT b = zp[m == 0 ? 0 : n - m];
+      T re, im;
+      if (l & 1) { re = T(0.5) * (a.y + b.y); im = T(-0.5) * (a.x - b.x); }   // (Z - conj Zc)/(2i)
+      else { re = T(0.5) * (a.x + b.x); im = T(0.5) * (a.y - b.y); }          // (Z + conj Zc)/2
+      re *= scale;
+      im *= scale;
+      if (OUT == kOutPlain) {
+        T* o = spec + ((size_t)(m * nrs + i) * 2) * nth + j;
+        o[0] = re;
+        o[nth] = im;
+      } else {
+        const size_t o = ((size_t)(m * nrs + i) * 2) * kstride + j;
+        const __nv_bfloat16 rh = __float2bfloat16_rn((float)re), ih = __float2bfloat16_rn((float)im);
+        hi[o] = rh;
+        lo[o] = __float2bfloat16_rn((float)re - __bfloat162float(rh));
+        hi[o + kstride] = ih;
+        lo[o + kstride] = __float2bfloat16_rn((float)im - __bfloat162float(ih));
+      }
+    }
   }
 }
 
-// Inverse: half spectra of lines [line0, line0+nl) -> real lines (optionally accumulated).
-template <typename T, typename Tout>
-__global__ void __launch_bounds__(256) k_fft_inverse(const T* __restrict__ spec, int nlines, int nth, int nrs,
-                                                     FftSchedule sch, const T* __restrict__ twid, int lpc,
-                                                     Tout* __restrict__ out, int accumulate) {
+enum InvOut { kInvWrite = 0, kInvAccumulate = 1, kInvPairUpdate = 2 };
+
+// Inverse: half spectra spec[m][i][c][j] (row stride Ntheta) of lines [line0, line0+nl)
+// -> real lines:
+//  MODE kInvWrite / kInvAccumulate: out = / += value
+//  MODE kInvPairUpdate: float-float iterate (out, phi_lo) = (e, 0) if first else
+//    (out, phi_lo) + e, with max|e| and max|hi| reduced into red[0], red[1]
+//    (non-negative float bit patterns, so integer max orders them).
+template <typename T, typename Tout, int MODE>
+__global__ void __launch_bounds__(256) k_fft_inv(const T* __restrict__ spec, int nlines, int nth, int nrs,
+                                                 FftSchedule sch, const T* __restrict__ twid, int lpc,
+                                                 Tout* __restrict__ out, float* __restrict__ phi_lo, int first,
+                                                 unsigned int* __restrict__ red) {
   using CT = typename C2<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ float s_me[kWarps], s_mp[kWarps];
   const int n = sch.n;
+  const int PS = n + 1;
   const int P = lpc / 2;
   CT* tw = reinterpret_cast<CT*>(smem_raw);
   CT* bufA = tw + n;
-  CT* bufB = bufA + P * (n + 2);
+  CT* bufB = bufA + P * PS;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   load_twiddles<T>(tw, twid, n);
   const int line0 = blockIdx.x * lpc;
   const int nl = min(lpc, nlines - line0);
   const int npairs = (nl + 1) / 2;
   const int mh = n / 2 + 1;
-  const size_t cstride = nth;
-  // half spectra into bufB as HS[m][l] (padded to an even number of lines)
-  const int nle = npairs * 2;
-  for (int t = threadIdx.x; t < mh * nle; t += blockDim.x) {
-    const int m = t / nle;
-    const int l = t - m * nle;
-    CT v;
-    v.x = T(0); v.y = T(0);
+  {
+    const int l = lane;
+    int i = 0, j = 0;
     if (l < nl) {
       const int g = line0 + l;
-      const int i = g / nth;
-      const int j = g - i * nth;
-      const T* s = spec + ((size_t)(m * nrs + i) * 2) * cstride + j;
-      v.x = s[0];
-      v.y = (m == 0 || 2 * m == n) ? T(0) : s[cstride];
+      i = g / nth;
+      j = g - i * nth;
     }
-    bufB[m * nle + l] = v;
+    // Z[m] = G_A[m] + i G_B[m] (even lane writes), Z[n-m] = conj G_A[m] + i conj G_B[m] (odd lane)
+    for (int m = warp; m < mh; m += kWarps) {
+      CT v;
+      v.x = T(0);
+      v.y = T(0);
+      if (l < nl) {
+        const T* s = spec + ((size_t)(m * nrs + i) * 2) * nth + j;
+        v.x = s[0];
+        v.y = (m == 0 || 2 * m == n) ? T(0) : s[nth];
+      }
+      CT o;
+      o.x = __shfl_xor_sync(0xffffffffu, v.x, 1);
+      o.y = __shfl_xor_sync(0xffffffffu, v.y, 1);
+      if ((l >> 1) < npairs) {
+        CT* z = bufA + (l >> 1) * PS;
+        if (!(l & 1)) {
+          CT zm; zm.x = v.x - o.y; zm.y = v.y + o.x;   // A = v, B = o
+          z[m] = zm;
+        } else if (m != 0 && 2 * m != n) {
+          CT zn; zn.x = o.x + v.y; zn.y = v.x - o.y;   // A = o, B = v
+          z[n - m] = zn;
+        }
+      }
+    }
   }
   __syncthreads();
-  // Z[m] = G_A[m] + i G_B[m], Z[n-m] = conj G_A[m] + i conj G_B[m]
-  for (int t = threadIdx.x; t < mh * npairs; t += blockDim.x) {
-    const int m = t / npairs;
-    const int p = t - m * npairs;
-    const CT A = bufB[m * nle + 2 * p];
-    const CT B = bufB[m * nle + 2 * p + 1];
-    CT* z = bufA + p * n;
-    CT zm; zm.x = A.x - B.y; zm.y = A.y + B.x;
-    z[m] = zm;
-    if (m != 0 && 2 * m != n) {
-      CT zn; zn.x = A.x + B.y; zn.y = B.x - A.y;
-      z[n - m] = zn;
+  CT* Z = warp_fft<true, T>(bufA, bufB, tw, sch, npairs, PS);
+  float me = 0.f, mp = 0.f;
+  for (int p = warp; p < npairs; p += kWarps) {
+    const CT* z = Z + p * PS;
+    const bool hasb = 2 * p + 1 < nl;
+    const size_t o0 = (size_t)(line0 + 2 * p) * n;
+    for (int q = lane; q < n; q += 32) {
+      const CT v = z[q];
+      if (MODE == kInvWrite) {
+        out[o0 + q] = (Tout)v.x;
+        if (hasb) out[o0 + n + q] = (Tout)v.y;
+      } else if (MODE == kInvAccumulate) {
+        out[o0 + q] += (Tout)v.x;
+        if (hasb) out[o0 + n + q] += (Tout)v.y;
+      } else {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (h == 1 && !hasb) break;
+          const size_t o = o0 + (size_t)h * n + q;
+          const float e = (float)(h ? v.y : v.x);
+          ff nv;
+          if (first) nv = ff{e, 0.f};
+          else nv = ff_add_f(ff{(float)out[o], phi_lo[o]}, e);
+          out[o] = (Tout)nv.hi;
+          phi_lo[o] = nv.lo;
+          me = fmaxf(me, fabsf(e));
+          mp = fmaxf(mp, fabsf(nv.hi));
+        }
+      }
     }
   }
-  __syncthreads();
-  CT* Z = run_fft<true, T>(bufA, bufB, tw, sch, npairs);
-  Tout* dst = out + (size_t)line0 * n;
-  const int tot = nl * n;
-  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-    const int l = e / n;
-    const int q = e - l * n;
-    const CT z = Z[(l >> 1) * n + q];
-    const T v = (l & 1) ? z.y : z.x;
-    if (accumulate) dst[e] += Tout(v); else dst[e] = Tout(v);
+  if (MODE == kInvPairUpdate) {
+    for (int o = 16; o > 0; o >>= 1) {
+      me = fmaxf(me, __shfl_xor_sync(0xffffffffu, me, o));
+      mp = fmaxf(mp, __shfl_xor_sync(0xffffffffu, mp, o));
+    }
+    if (lane == 0) { s_me[warp] = me; s_mp[warp] = mp; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < kWarps; ++w) { me = fmaxf(me, s_me[w]); mp = fmaxf(mp, s_mp[w]); }
+      atomicMax(red, __float_as_uint(me));
+      atomicMax(red + 1, __float_as_uint(mp));
+    }
   }
 }
 
 template <typename T>
 int lines_per_cta(int n) {
-  // keep two ping-pong buffers near 64 KB
-  const int budget = 65536 / (2 * 2 * (int)sizeof(T));  // complex elements per buffer pair
-  int lpc = budget / (n + 2) * 2;
-  if (lpc > 32) lpc = 32;
-  if (lpc < 2) lpc = 2;
-  return lpc & ~1;
+  // two padded line buffers within ~100 KB (float) / ~140 KB (double), at most 32 lines
+  const size_t budget = sizeof(T) == 4 ? 100000 : 140000;
+  const size_t per_pair = 2 * (size_t)(n + 1) * 2 * sizeof(T);
+  size_t pairs = budget / per_pair;
+  if (pairs > 16) pairs = 16;
+  if (pairs < 1) pairs = 1;
+  return (int)(2 * pairs);
 }
 
 template <typename T>
 size_t fft_smem(int n, int lpc) {
-  return sizeof(typename C2<T>::t) * ((size_t)n + 2 * (size_t)(lpc / 2) * (n + 2));
+  return sizeof(typename C2<T>::t) * ((size_t)n + 2 * (size_t)(lpc / 2) * (n + 1));
+}
+
+template <typename K>
+cudaError_t prep(K kern, size_t smem) {
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
 }  // namespace
 
-cudaError_t fft_forward_f64(const Plan& p, const double* in, int nrs, double scale, double* spec,
-                            cudaStream_t s) {
+cudaError_t fft_forward_f64(const Plan& p, const double* in, int nrs, double scale, double* spec, cudaStream_t s) {
   const int nlines = nrs * p.nth;
   const int lpc = lines_per_cta<double>(p.nphi);
   const size_t smem = fft_smem<double>(p.nphi, lpc);
-  auto kern = k_fft_forward<double, double>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = k_fft_fwd<double, double, kOutPlain>;
+  cudaError_t e = prep(kern, smem);
   if (e != cudaSuccess) return e;
-  const int grid = (nlines + lpc - 1) / lpc;
-  kern<<<grid, 256, smem, s>>>(in, nlines, p.nth, nrs, p.sched, p.d_twid, scale, lpc, spec);
+  kern<<<(nlines + lpc - 1) / lpc, 32 * kWarps, smem, s>>>(in, nlines, p.nth, nrs, p.sched, p.d_twid, scale, lpc, spec,
+                                                           nullptr, nullptr, 0);
   return cudaGetLastError();
 }
 
-cudaError_t fft_inverse_f64(const Plan& p, const double* spec, int nrs, double* out, bool accumulate,
-                            cudaStream_t s) {
+cudaError_t fft_inverse_f64(const Plan& p, const double* spec, int nrs, double* out, bool accumulate, cudaStream_t s) {
   const int nlines = nrs * p.nth;
   const int lpc = lines_per_cta<double>(p.nphi);
   const size_t smem = fft_smem<double>(p.nphi, lpc);
-  auto kern = k_fft_inverse<double, double>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
   const int grid = (nlines + lpc - 1) / lpc;
-  kern<<<grid, 256, smem, s>>>(spec, nlines, p.nth, nrs, p.sched, p.d_twid, lpc, out, accumulate ? 1 : 0);
+  cudaError_t e;
+  if (accumulate) {
+    auto kern = k_fft_inv<double, double, kInvAccumulate>;
+    if ((e = prep(kern, smem)) != cudaSuccess) return e;
+    kern<<<grid, 32 * kWarps, smem, s>>>(spec, nlines, p.nth, nrs, p.sched, p.d_twid, lpc, out, nullptr, 0, nullptr);
+  } else {
+    auto kern = k_fft_inv<double, double, kInvWrite>;
+    if ((e = prep(kern, smem)) != cudaSuccess) return e;
+    kern<<<grid, 32 * kWarps, smem, s>>>(spec, nlines, p.nth, nrs, p.sched, p.d_twid, lpc, out, nullptr, 0, nullptr);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t fft_forward_split(const Plan& p, const void* in, bool in_double, float scale, int kstride,
+                              __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t s) {
+  const int nlines = p.nr * p.nth;
+  const int lpc = lines_per_cta<float>(p.nphi);
+  const size_t smem = fft_smem<float>(p.nphi, lpc);
+  const int grid = (nlines + lpc - 1) / lpc;
+  cudaError_t e;
+  if (in_double) {
+    auto kern = k_fft_fwd<float, double, kOutSplit>;
+    if ((e = prep(kern, smem)) != cudaSuccess) return e;
+    kern<<<grid, 32 * kWarps, smem, s>>>(static_cast<const double*>(in), nlines, p.nth, p.nr, p.sched, p.d_twid32,
+                                         scale, lpc, nullptr, hi, lo, kstride);
+  } else {
+    auto kern = k_fft_fwd<float, float, kOutSplit>;
+    if ((e = prep(kern, smem)) != cudaSuccess) return e;
+    kern<<<grid, 32 * kWarps, smem, s>>>(static_cast<const float*>(in), nlines, p.nth, p.nr, p.sched, p.d_twid32,
+                                         scale, lpc, nullptr, hi, lo, kstride);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t fft_inverse_update(const Plan& p, const float* spec, float* phi_hi, float* phi_lo, bool first,
+                               unsigned int* red, cudaStream_t s) {
+  const int nlines = p.nr * p.nth;
+  const int lpc = lines_per_cta<float>(p.nphi);
+  const size_t smem = fft_smem<float>(p.nphi, lpc);
+  auto kern = k_fft_inv<float, float, kInvPairUpdate>;
+  cudaError_t e = prep(kern, smem);
+  if (e != cudaSuccess) return e;
+  kern<<<(nlines + lpc - 1) / lpc, 32 * kWarps, smem, s>>>(spec, nlines, p.nth, p.nr, p.sched, p.d_twid32, lpc, phi_hi,
+                                                           phi_lo, first ? 1 : 0, red);
   return cudaGetLastError();
 }
 

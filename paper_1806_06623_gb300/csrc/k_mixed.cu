@@ -1,0 +1,473 @@
+// Mixed-precision solve (SP_MIXED_BF16X3): the low-precision separated solve and the
+// float64 residual of the finite-volume operator used to refine it.
+//
+//  low-precision solve of L e = r (Sect. 3.2 steps in float32):
+//    FFT (float32, bf16 hi/lo panel out) -> tcgen05 projection with (H^T W)_m
+//    -> radial solves (float32; float64 for the near-singular |lambda| < 30 modes)
+//    -> tcgen05 projection with H_m -> inverse FFT (float32) with Phi += e in float64
+//  residual: r = 4 pi G rho - L Phi in float64 (stencil of Eq. fin_vol3 plus the
+//    multipole outer-shell term), stored in float32 as the next right-hand side.
+#include <cmath>
+#include <new>
+#include <vector>
+
+#include "sp_internal.h"
+#include "tc_gemm.cuh"
+
+namespace sp {
+namespace {
+
+size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// table [b][rows][n] float64 -> bf16 hi/lo [b][rows][kstride], zero beyond n
+__global__ void k_split_table(const double* __restrict__ src, int rows, int n, int kstride, size_t total,
+                              __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(t % kstride);
+    const size_t br = t / kstride;
+    double x = 0.0;
+    if (k < n) x = src[br * n + k];
+    const __nv_bfloat16 h = __double2bfloat16(x);
+    hi[t] = h;
+    lo[t] = __double2bfloat16(x - (double)__bfloat162float(h));
+  }
+  (void)rows;
+}
+
+__device__ __forceinline__ void store_split(__nv_bfloat16* hi, __nv_bfloat16* lo, size_t o, float v) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);
+  hi[o] = h;
+  lo[o] = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)), "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+constexpr int kTR = 16;       // radial rows per staged chunk
+constexpr int kStages = 4;    // chunks in flight per warp
+
+// Radial solves of the low-precision solve, one warp per (m, 32 consecutive l).  Rows
+// of the mode array are staged through a kStages-deep ring of cp.async copies (each lane
+// copies its own elements) so the sequential elimination reads shared memory while
+// later rows stream in.  float32 elimination; lanes whose mode is near-singular
+// (|lambda| < thr) idle here and are solved in float64 by the trailing blocks.
+// d32 holds s_hat[m][i][c][l] on entry and the forward-elimination values afterwards;
+// cp32 receives the elimination coefficients; f leaves as bf16 hi/lo panel rows.
+__global__ void __launch_bounds__(32) k_thomas_staged(const RadialRowF* __restrict__ rad, const double* __restrict__ lam,
+                                                      const double* __restrict__ outer, float* __restrict__ x,
+                                                      float* __restrict__ cp, __nv_bfloat16* __restrict__ hi,
+                                                      __nv_bfloat16* __restrict__ lo, int nr, int nth, int mh,
+                                                      int kstride, double thr, int nblk_f32,
+                                                      const int* __restrict__ low_idx, int nlow,
+                                                      const RadialRow* __restrict__ rad64,
+                                                      const double2* __restrict__ low_fac, double* __restrict__ low_ws) {
+  __shared__ float sx[kStages][kTR][3][32];
+  const int lane = threadIdx.x;
+  const size_t st = 2 * (size_t)nth;
+  const int nchunk = (nr + kTR - 1) / kTR;
+  if ((int)blockIdx.x >= nblk_f32) {
+    // ---- float64 near-singular mode, one per warp: the column and its precomputed
+    // elimination factors are loaded in parallel, lane 0 runs both sweeps out of shared
+    // memory (low_ws holds the column as doubles), all lanes write the result.
+    const int q = (int)blockIdx.x - nblk_f32;
+    if (q >= nlow) return;
+    const int t = low_idx[q];
+    const int m = t / nth;
+    const int l = t - m * nth;
+    const float* X = x + (size_t)m * nr * st + l;
+    const double2* F = low_fac + (size_t)q * nr;     // (c'_i, 1/pivot_i)
+    // [i][re, im, c'] in the (otherwise unused) staging buffer when it fits
+    double* W = (3 * nr <= (int)(sizeof(sx) / sizeof(double))) ? reinterpret_cast<double*>(&sx[0][0][0][0])
+                                                                 : low_ws + (size_t)q * nr * 3;
+    for (int i = lane; i < nr; i += 32) {
+      W[3 * i] = (double)X[(size_t)i * st];
+      W[3 * i + 1] = (double)X[(size_t)i * st + nth];
+      W[3 * i + 2] = F[i].x;
+    }
+    __threadfence_block();
+    __syncwarp();
+    if (lane == 0) {
+      double dre = 0.0, dim = 0.0;
+      for (int i = 0; i < nr; ++i) {
+        const double sub = rad64[i].sub;
+        const double inv = F[i].y;
+        dre = (W[3 * i] - sub * dre) * inv;
+        dim = (W[3 * i + 1] - sub * dim) * inv;
+        W[3 * i] = dre;
+        W[3 * i + 1] = dim;
+      }
+      for (int i = nr - 2; i >= 0; --i) {
+        const double c = W[3 * i + 2];
+        dre = W[3 * i] - c * dre;
+        dim = W[3 * i + 1] - c * dim;
+        W[3 * i] = dre;
+        W[3 * i + 1] = dim;
+      }
+    }
+    __threadfence_block();
+    __syncwarp();
+    const size_t prow = (size_t)m * nr * 2;
+    for (int i = lane; i < nr; i += 32) {
+      store_split(hi, lo, (prow + 2 * i) * kstride + l, (float)W[3 * i]);
+      store_split(hi, lo, (prow + 2 * i + 1) * kstride + l, (float)W[3 * i + 1]);
+    }
+    return;
+  }
+  // ---- float32 modes
+  const int nlb = (nth + 31) / 32;
+  const int m = blockIdx.x / nlb;
+  const int l = (blockIdx.x - m * nlb) * 32 + lane;
+  const bool valid = l < nth;
+  const int t = m * nth + l;
+  const bool work = valid && fabs(lam[t]) >= thr;
+  const float L = valid ? (float)lam[t] : 0.f;
+  const float od = valid ? (float)outer[t] : 0.f;
+  float* X = x + (size_t)m * nr * st + (valid ? l : 0);
+  float* CP = cp + (size_t)m * nr * nth + (valid ? l : 0);
+
+  auto fetch_fwd = [&](int ch) {
+    if (ch < nchunk && valid) {
+      const int i0 = ch * kTR;
+      const int n = min(kTR, nr - i0);
+      float(*b)[3][32] = sx[ch % kStages];
+      for (int r = 0; r < n; ++r) {
+        cp_async4(&b[r][0][lane], X + (size_t)(i0 + r) * st);
+        cp_async4(&b[r][1][lane], X + (size_t)(i0 + r) * st + nth);
+      }
+    }
+    cp_async_commit();
+  };
+  for (int ch = 0; ch < kStages - 1; ++ch) fetch_fwd(ch);
+  float cprev = 0.f, dre = 0.f, dim = 0.f;
+  for (int ch = 0; ch < nchunk; ++ch) {
+    fetch_fwd(ch + kStages - 1);
+    cp_async_wait<kStages - 1>();
+    __syncwarp();
+    const int i0 = ch * kTR;
+    const int n = min(kTR, nr - i0);
+    float(*b)[3][32] = sx[ch % kStages];
+    if (work) {
+      for (int r = 0; r < n; ++r) {
+        const int i = i0 + r;
+        const RadialRowF rr = rad[i];
+        float bb = fmaf(rr.R, L, rr.base);
+        if (i == nr - 1) bb += od;
+        const float inv = 1.0f / (bb - rr.sub * cprev);
+        cprev = rr.sup * inv;
+        dre = (b[r][0][lane] - rr.sub * dre) * inv;
+        dim = (b[r][1][lane] - rr.sub * dim) * inv;
+        X[(size_t)i * st] = dre;
+        X[(size_t)i * st + nth] = dim;
+        CP[(size_t)i * nth] = cprev;
+      }
+    }
+    __syncwarp();
+  }
+  cp_async_wait<0>();
+  __threadfence_block();
+  __syncwarp();
+  // back substitution, chunks in reverse; each lane re-reads only its own elements
+  const size_t prow = (size_t)m * nr * 2;
+  auto fetch_bwd = [&](int k) {   // k-th chunk from the top
+    const int ch = nchunk - 1 - k;
+    if (ch >= 0 && work) {
+      const int i0 = ch * kTR;
+      const int n = min(kTR, nr - i0);
+      float(*b)[3][32] = sx[k % kStages];
+      for (int r = 0; r < n; ++r) {
+        cp_async4(&b[r][0][lane], X + (size_t)(i0 + r) * st);
+        cp_async4(&b[r][1][lane], X + (size_t)(i0 + r) * st + nth);
+        cp_async4(&b[r][2][lane], CP + (size_t)(i0 + r) * nth);
+      }
+    }
+    cp_async_commit();
+  };
+  for (int k = 0; k < kStages - 1; ++k) fetch_bwd(k);
+  bool first = true;
+  for (int k = 0; k < nchunk; ++k) {
+    fetch_bwd(k + kStages - 1);
+    cp_async_wait<kStages - 1>();
+    __syncwarp();
+    const int ch = nchunk - 1 - k;
+    const int i0 = ch * kTR;
+    const int n = min(kTR, nr - i0);
+    float(*b)[3][32] = sx[k % kStages];
+    if (work) {
+      for (int r = n - 1; r >= 0; --r) {
+        const int i = i0 + r;
+        if (first) {
+          dre = b[r][0][lane];
+          dim = b[r][1][lane];
+          first = false;
+        } else {
+          const float c = b[r][2][lane];
+          dre = b[r][0][lane] - c * dre;
+          dim = b[r][1][lane] - c * dim;
+        }
+        store_split(hi, lo, (prow + 2 * i) * kstride + l, dre);
+        store_split(hi, lo, (prow + 2 * i + 1) * kstride + l, dim);
+      }
+    }
+    __syncwarp();
+  }
+  cp_async_wait<0>();
+}
+
+// Elimination factors (c'_i, 1/pivot_i) of the float64 near-singular modes (set-up).
+__global__ void k_low_factors(const RadialRow* __restrict__ rad, const double* __restrict__ lam,
+                              const double* __restrict__ outer, const int* __restrict__ low_idx, int nlow, int nr,
+                              double2* __restrict__ fac) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nlow) return;
+  const int t = low_idx[q];
+  const double L = lam[t];
+  double cprev = 0.0;
+  for (int i = 0; i < nr; ++i) {
+    const RadialRow rr = rad[i];
+    double b = fma(rr.R, L, rr.base);
+    if (i == nr - 1) b += outer[t];
+    const double inv = 1.0 / (b - rr.sub * cprev);
+    cprev = rr.sup * inv;
+    fac[(size_t)q * nr + i] = make_double2(cprev, inv);
+  }
+}
+
+// r = 4 pi G rho - (L Phi) for the float-float iterate Phi = hi + lo, evaluated in
+// float-float arithmetic in difference form (every neighbour difference Phi_nb - Phi_c
+// is formed first, so products carry errors relative to the small differences, not to
+// |L||Phi|), stored as float32.  rho is split into a float pair with integer
+// operations; the multipole term of the last shell arrives precomputed in outer_shell
+// (float64, already scaled by 3 r_out^2/dV3_N).
+__global__ void __launch_bounds__(256) k_residual_ff(const double* __restrict__ rho, const float* __restrict__ ph,
+                                                     const float* __restrict__ pl,
+                                                     const double* __restrict__ outer_shell, float* __restrict__ r,
+                                                     const RadialRowFF* __restrict__ rad,
+                                                     const ThetaRowFF* __restrict__ th, int nr, int nth, int nphi,
+                                                     int dirichlet, ff dir_coef, ff four_pi_g) {
+  // one CTA per (j, i) phi line: no index division in the inner loop
+  const int j = blockIdx.x;
+  const int i = blockIdx.y;
+  const size_t shell = (size_t)nth * nphi;
+  const size_t line = ((size_t)i * nth + j) * nphi;
+  const RadialRowFF rr = rad[i];
+  const ThetaRowFF tr = th[j];
+  for (int k = threadIdx.x; k < nphi; k += blockDim.x) {
+    const size_t idx = line + k;
+    const ff c{ph[idx], pl[idx]};
+    ff acc{0.f, 0.f};
+    if (i > 0) acc = ff_mul(rr.sub, ff_sub(ff{ph[idx - shell], pl[idx - shell]}, c));
+    if (i < nr - 1) acc = ff_add(acc, ff_mul(rr.sup, ff_sub(ff{ph[idx + shell], pl[idx + shell]}, c)));
+    ff a{0.f, 0.f};
+    if (j > 0) a = ff_mul(tr.tm, ff_sub(ff{ph[idx - nphi], pl[idx - nphi]}, c));
+    if (j < nth - 1) a = ff_add(a, ff_mul(tr.tp, ff_sub(ff{ph[idx + nphi], pl[idx + nphi]}, c)));
+    const size_t kp = (k + 1 == nphi) ? idx - k : idx + 1;
+    const size_t km = (k == 0) ? idx + (nphi - 1) : idx - 1;
+    const ff dphi = ff_add(ff_sub(ff{ph[kp], pl[kp]}, c), ff_sub(ff{ph[km], pl[km]}, c));
+    a = ff_add(a, ff_mul(tr.sphi, dphi));
+    acc = ff_add(acc, ff_mul(rr.R, a));
+    if (i == nr - 1) {
+      if (dirichlet) acc = ff_add(acc, ff_mul(dir_coef, c));
+      else acc = ff_add(acc, d2ff(outer_shell[idx - (size_t)i * shell]));
+    }
+    const ff res = ff_sub(ff_mul(four_pi_g, d2ff(rho[idx])), acc);
+    r[idx] = res.hi + res.lo;
+  }
+}
+
+// float64 Phi = hi + lo
+__global__ void __launch_bounds__(256) k_finish(const float* __restrict__ ph, const float* __restrict__ pl,
+                                                double* __restrict__ phi, size_t n) {
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x)
+    phi[idx] = ff2d(ff{ph[idx], pl[idx]});
+}
+
+}  // namespace
+
+size_t mixed_workspace_bytes(const Plan& p) {
+  const MixedTables& x = *p.mixed;
+  const size_t zones = (size_t)p.nr * p.nth * p.nphi;
+  const size_t rows = (size_t)p.mh * 2 * p.nr;
+  return 3 * al256(zones * 4) + 2 * al256(rows * x.kstride * 2) + al256(rows * p.nth * 4) +
+         al256((size_t)p.mh * p.nr * p.nth * 4) + al256((size_t)(x.nlow ? x.nlow : 1) * p.nr * 3 * 8) +
+         2 * al256((size_t)p.nth * p.nphi * 8) + 2 * al256((size_t)p.mh * 2 * p.nth * 8) + 256;
+}
+
+void mixed_bind_workspace(Plan& p, char* c) {
+  MixedTables& x = *p.mixed;
+  const size_t zones = (size_t)p.nr * p.nth * p.nphi;
+  const size_t rows = (size_t)p.mh * 2 * p.nr;
+  x.r32 = reinterpret_cast<float*>(c);
+  c += al256(zones * 4);
+  x.phi_hi = reinterpret_cast<float*>(c);
+  c += al256(zones * 4);
+  x.phi_lo = reinterpret_cast<float*>(c);
+  c += al256(zones * 4);
+  x.pan_hi = reinterpret_cast<__nv_bfloat16*>(c);
+  c += al256(rows * x.kstride * 2);
+  x.pan_lo = reinterpret_cast<__nv_bfloat16*>(c);
+  c += al256(rows * x.kstride * 2);
+  x.d32 = reinterpret_cast<float*>(c);
+  c += al256(rows * p.nth * 4);
+  x.cp32 = reinterpret_cast<float*>(c);
+  c += al256((size_t)p.mh * p.nr * p.nth * 4);
+  x.low_ws = reinterpret_cast<double*>(c);
+  c += al256((size_t)(x.nlow ? x.nlow : 1) * p.nr * 3 * 8);
+  x.outer_shell = reinterpret_cast<double*>(c);
+  c += al256((size_t)p.nth * p.nphi * 8);
+  x.shell_phi = reinterpret_cast<double*>(c);
+  c += al256((size_t)p.nth * p.nphi * 8);
+  p.shell = reinterpret_cast<double*>(c);
+  c += al256((size_t)p.mh * 2 * p.nth * 8);
+  p.shell2 = reinterpret_cast<double*>(c);
+  c += al256((size_t)p.mh * 2 * p.nth * 8);
+  x.red = reinterpret_cast<unsigned int*>(c);
+  p.specA = p.specB = p.cp = nullptr;
+}
+
+bool mixed_make_panel_maps(Plan& p) {
+  MixedTables& x = *p.mixed;
+  return tc::make_map(reinterpret_cast<CUtensorMap*>(x.map_Bhi), x.pan_hi, p.nth, x.kstride, 2 * p.nr, p.mh, tc::kN) &&
+         tc::make_map(reinterpret_cast<CUtensorMap*>(x.map_Blo), x.pan_lo, p.nth, x.kstride, 2 * p.nr, p.mh, tc::kN);
+}
+
+int mixed_create_tables(Plan& p, cudaStream_t s) {
+  MixedTables* x = new (std::nothrow) MixedTables();
+  if (!x) return SP_ERR_OOM;
+  p.mixed = x;
+  const int nth = p.nth, mh = p.mh;
+  x->kstride = (nth + 7) / 8 * 8;
+  const size_t tab = (size_t)mh * nth * x->kstride;
+  if (cudaMalloc(&x->HtW_hi, tab * 2) != cudaSuccess || cudaMalloc(&x->HtW_lo, tab * 2) != cudaSuccess ||
+      cudaMalloc(&x->H_hi, tab * 2) != cudaSuccess || cudaMalloc(&x->H_lo, tab * 2) != cudaSuccess ||
+      cudaMalloc(&x->radf, sizeof(RadialRowF) * p.nr) != cudaSuccess)
+    return SP_ERR_OOM;
+  k_split_table<<<1024, 256, 0, s>>>(p.d_HtW, nth, nth, x->kstride, tab, x->HtW_hi, x->HtW_lo);
+  k_split_table<<<1024, 256, 0, s>>>(p.d_H, nth, nth, x->kstride, tab, x->H_hi, x->H_lo);
+  if (cudaGetLastError() != cudaSuccess) return SP_ERR_CUDA;
+  std::vector<RadialRow> rad(p.nr);
+  std::vector<double> lam((size_t)mh * nth);
+  if (cudaMemcpyAsync(rad.data(), p.d_rad, sizeof(RadialRow) * p.nr, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(lam.data(), p.d_lam, sizeof(double) * lam.size(), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return SP_ERR_CUDA;
+  std::vector<RadialRowF> rf(p.nr);
+  for (int i = 0; i < p.nr; ++i) rf[i] = {(float)rad[i].sub, (float)rad[i].sup, (float)rad[i].R, (float)rad[i].base};
+  auto split = [](double v) { const float h = (float)v; return ff{h, (float)(v - (double)h)}; };
+  std::vector<RadialRowFF> rff(p.nr);
+  for (int i = 0; i < p.nr; ++i) rff[i] = {split(rad[i].sub), split(rad[i].sup), split(rad[i].R), ff{0.f, 0.f}};
+  std::vector<ThetaRow> thr(p.nth);
+  if (cudaMemcpy(thr.data(), p.d_theta, sizeof(ThetaRow) * p.nth, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return SP_ERR_CUDA;
+  std::vector<ThetaRowFF> thff(p.nth);
+  for (int j = 0; j < p.nth; ++j) thff[j] = {split(thr[j].tp), split(thr[j].tm), split(thr[j].sphi), ff{0.f, 0.f}};
+  x->four_pi_g = split(4.0 * 3.14159265358979323846264338327950288 * p.G);
+  x->dir_coef = split(-p.outer_coef / (p.r_out - p.r_last));
+  if (cudaMalloc(&x->radff, sizeof(RadialRowFF) * p.nr) != cudaSuccess ||
+      cudaMalloc(&x->thff, sizeof(ThetaRowFF) * p.nth) != cudaSuccess)
+    return SP_ERR_OOM;
+  if (cudaMemcpy(x->radff, rff.data(), sizeof(RadialRowFF) * p.nr, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(x->thff, thff.data(), sizeof(ThetaRowFF) * p.nth, cudaMemcpyHostToDevice) != cudaSuccess)
+    return SP_ERR_CUDA;
+  std::vector<int> low;
+  for (size_t t = 0; t < lam.size(); ++t)
+    if (std::fabs(lam[t]) < x->low_threshold) low.push_back((int)t);
+  x->nlow = (int)low.size();
+  if (cudaMalloc(&x->low_idx, sizeof(int) * (low.empty() ? 1 : low.size())) != cudaSuccess) return SP_ERR_OOM;
+  if (cudaMemcpy(x->radf, rf.data(), sizeof(RadialRowF) * p.nr, cudaMemcpyHostToDevice) != cudaSuccess) return SP_ERR_CUDA;
+  if (!low.empty() &&
+      cudaMemcpy(x->low_idx, low.data(), sizeof(int) * low.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    return SP_ERR_CUDA;
+  if (x->nlow) {
+    if (cudaMalloc(&x->low_fac, sizeof(double2) * (size_t)x->nlow * p.nr) != cudaSuccess) return SP_ERR_OOM;
+    k_low_factors<<<(x->nlow + 63) / 64, 64, 0, s>>>(p.d_rad, p.d_lam, p.d_outer, x->low_idx, x->nlow, p.nr,
+                                                     x->low_fac);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return SP_ERR_CUDA;
+  }
+  const bool ok = tc::make_map(reinterpret_cast<CUtensorMap*>(x->map_Ahi_f), x->HtW_hi, nth, x->kstride, nth, mh, tc::kM) &&
+                  tc::make_map(reinterpret_cast<CUtensorMap*>(x->map_Alo_f), x->HtW_lo, nth, x->kstride, nth, mh, tc::kM) &&
+                  tc::make_map(reinterpret_cast<CUtensorMap*>(x->map_Ahi_i), x->H_hi, nth, x->kstride, nth, mh, tc::kM) &&
+                  tc::make_map(reinterpret_cast<CUtensorMap*>(x->map_Alo_i), x->H_lo, nth, x->kstride, nth, mh, tc::kM);
+  return ok ? SP_OK : SP_ERR_CUDA;
+}
+
+void mixed_free_tables(Plan& p) {
+  if (!p.mixed) return;
+  MixedTables* x = p.mixed;
+  cudaFree(x->HtW_hi);
+  cudaFree(x->HtW_lo);
+  cudaFree(x->H_hi);
+  cudaFree(x->H_lo);
+  cudaFree(x->radf);
+  cudaFree(x->low_idx);
+  cudaFree(x->low_fac);
+  cudaFree(x->radff);
+  cudaFree(x->thff);
+  delete x;
+  p.mixed = nullptr;
+}
+
+cudaError_t tc_project(const Plan& p, bool inverse, cudaStream_t s) {
+  const MixedTables& x = *p.mixed;
+  const CUtensorMap* ahi = reinterpret_cast<const CUtensorMap*>(inverse ? x.map_Ahi_i : x.map_Ahi_f);
+  const CUtensorMap* alo = reinterpret_cast<const CUtensorMap*>(inverse ? x.map_Alo_i : x.map_Alo_f);
+  const CUtensorMap* bhi = reinterpret_cast<const CUtensorMap*>(x.map_Bhi);
+  const CUtensorMap* blo = reinterpret_cast<const CUtensorMap*>(x.map_Blo);
+  tc::Params prm{x.d32, p.nth, 2 * p.nr, (p.nth + tc::kKBlk - 1) / tc::kKBlk, p.d_err};
+  cudaError_t e = cudaFuncSetAttribute(tc::k_tc_gemm_bf16x3, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)tc::kSmemBytes);
+  if (e != cudaSuccess) return e;
+  dim3 grid((2 * p.nr + tc::kN - 1) / tc::kN, p.mh);
+  tc::k_tc_gemm_bf16x3<<<grid, 128, tc::kSmemBytes, s>>>(*ahi, *alo, *bhi, *blo, prm);
+  return cudaGetLastError();
+}
+
+cudaError_t thomas_mixed(const Plan& p, cudaStream_t s) {
+  const MixedTables& x = *p.mixed;
+  const int nblk = p.mh * ((p.nth + 31) / 32);
+  const int nlowblk = x.nlow;   // one warp per float64 mode
+  k_thomas_staged<<<nblk + nlowblk, 32, 0, s>>>(x.radf, p.d_lam, p.d_outer, x.d32, x.cp32, x.pan_hi, x.pan_lo, p.nr,
+                                                 p.nth, p.mh, x.kstride, x.low_threshold, nblk, x.low_idx, x.nlow,
+                                                 p.d_rad, x.low_fac, x.low_ws);
+  return cudaGetLastError();
+}
+
+cudaError_t residual_ff(const Plan& p, const double* rho, cudaStream_t s) {
+  const MixedTables& x = *p.mixed;
+  const size_t n = (size_t)p.nr * p.nth * p.nphi;
+  const size_t sh = (size_t)p.nth * p.nphi;
+  if (p.outer_bc == SP_OUTER_MULTIPOLE) {
+    // outer term from the float64 value of the last shell (small: Ntheta x Nphi zones)
+    const size_t off = (size_t)(p.nr - 1) * sh;
+    k_finish<<<(unsigned)((sh + 255) / 256), 256, 0, s>>>(x.phi_hi + off, x.phi_lo + off, x.shell_phi, sh);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = fft_forward_f64(p, x.shell_phi, 1, 1.0 / p.nphi, p.shell, s);
+    if (e != cudaSuccess) return e;
+    e = shell_kappa_f64(p, p.shell, p.shell2, s);
+    if (e != cudaSuccess) return e;
+    e = fft_inverse_f64(p, p.shell2, 1, x.outer_shell, false, s);
+    if (e != cudaSuccess) return e;
+  }
+  (void)n;
+  const int tpb = p.nphi >= 256 ? 256 : ((p.nphi + 31) / 32) * 32;
+  k_residual_ff<<<dim3(p.nth, p.nr), tpb, 0, s>>>(rho, x.phi_hi, x.phi_lo, x.outer_shell, x.r32, x.radff, x.thff, p.nr,
+                                                 p.nth, p.nphi, p.outer_bc == SP_OUTER_DIRICHLET ? 1 : 0, x.dir_coef,
+                                                 x.four_pi_g);
+  return cudaGetLastError();
+}
+
+cudaError_t finish_mixed(const Plan& p, double* phi, cudaStream_t s) {
+  const MixedTables& x = *p.mixed;
+  const size_t n = (size_t)p.nr * p.nth * p.nphi;
+  size_t blocks = (n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_finish<<<(unsigned)blocks, 256, 0, s>>>(x.phi_hi, x.phi_lo, phi, n);
+  return cudaGetLastError();
+}
+
+}  // namespace sp

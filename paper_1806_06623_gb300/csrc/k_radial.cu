@@ -125,6 +125,12 @@ cudaError_t stencil_f64(const Plan& p, const double* phi, double* out, cudaStrea
   return cudaGetLastError();
 }
 
+cudaError_t shell_kappa_f64(const Plan& p, const double* in, double* out, cudaStream_t s) {
+  const size_t smem = sizeof(double) * 4 * (size_t)p.nth;
+  k_shell_kappa<<<p.mh, 128, smem, s>>>(p.d_HtW, p.d_H, p.d_outer, in, out, p.nth);
+  return cudaGetLastError();
+}
+
 cudaError_t outer_term_f64(const Plan& p, const double* phi, double* out, cudaStream_t s) {
   const size_t off = (size_t)(p.nr - 1) * p.nth * p.nphi;
   cudaError_t e = fft_forward_f64(p, phi + off, 1, 1.0 / p.nphi, p.shell, s);

@@ -5,6 +5,7 @@
 #include <cstddef>
 #include <cstdint>
 
+#include "ff.cuh"
 #include "sphpoisson.h"
 
 namespace sp {
@@ -14,14 +15,21 @@ constexpr int kMaxNtheta = 160;   // theta eigenvectors of one m are kept in sha
 constexpr int kMaxNphi = 4096;
 
 // Radix schedule of a length-n complex FFT, n = 2^a 3^b (radix 4 first, then 2, then 3).
+// Per stage: Ns (product of the earlier radices), the twiddle-table step n/(Ns R), and
+// the division b/Ns as a shift (power-of-two Ns) or a multiply-high by magic =
+// floor(2^32/Ns)+1 (exact for b < 8192).
 struct FftSchedule {
   int n;
   int nstages;
   int radix[kMaxStages];
+  int ns[kMaxStages];
+  int tstep[kMaxStages];
+  int shift[kMaxStages];
+  unsigned int magic[kMaxStages];
 };
 
 // Error bits written by kernels into the plan's device status word.
-enum : int { kErrEigenIter = 1, kErrBounds = 2 };
+enum : int { kErrEigenIter = 1, kErrBounds = 2, kErrTimeout = 4 };
 
 // Per-radius coefficients of the radial operator (Eq. fin_vol3 with the Sect. 3.1
 // areas): row i of Delta_r + R_i lambda reads
@@ -38,7 +46,50 @@ struct ThetaRow {
   double tp, tm, sphi, pad;
 };
 
-struct MixedTables;  // defined with the mixed-precision path
+// float copy of RadialRow for the float32 radial solves
+struct RadialRowF {
+  float sub, sup, R, base;
+};
+
+// float-float copies of the stencil coefficients for the refinement residual
+struct RadialRowFF {
+  ff sub, sup, R, pad;
+};
+struct ThetaRowFF {
+  ff tp, tm, sphi, pad;
+};
+
+// Tables and workspace views of the mixed-precision (split-bf16) path.
+struct MixedTables {
+  int kstride = 0;                 // K row stride of the bf16 panels (Ntheta rounded up to 8)
+  int nlow = 0;                    // radial modes solved in float64 (|lambda| < low_threshold)
+  double low_threshold = 30.0;
+  __nv_bfloat16* HtW_hi = nullptr; // [mh][l][kstride]
+  __nv_bfloat16* HtW_lo = nullptr;
+  __nv_bfloat16* H_hi = nullptr;   // [mh][j][kstride]
+  __nv_bfloat16* H_lo = nullptr;
+  RadialRowF* radf = nullptr;      // [nr]
+  RadialRowFF* radff = nullptr;    // [nr]
+  ThetaRowFF* thff = nullptr;      // [nth]
+  ff four_pi_g{}, dir_coef{};      // s = 4 pi G rho; Dirichlet outer diagonal (3 r^2/dV3)/(r_N - r_out)
+  int* low_idx = nullptr;          // [nlow] flat (m*Ntheta + l) of the float64 modes
+  double2* low_fac = nullptr;      // [nlow][nr] (c'_i, 1/pivot_i) of the float64 modes
+  // workspace views
+  float* r32 = nullptr;            // [nr][nth][nphi] residual
+  float* phi_hi = nullptr;         // [nr][nth][nphi] iterate as float-float
+  float* phi_lo = nullptr;
+  __nv_bfloat16* pan_hi = nullptr; // [mh][2nr][kstride] spectral panel (s_tilde, then f)
+  __nv_bfloat16* pan_lo = nullptr;
+  float* d32 = nullptr;            // [mh][2nr][nth] projection output (s_hat, then g)
+  float* cp32 = nullptr;           // [mh][nr][nth] float32 Thomas coefficients
+  double* low_ws = nullptr;        // [nlow][nr][3] float64 Thomas scratch
+  double* outer_shell = nullptr;   // [nth][nphi] multipole outer term of the residual
+  double* shell_phi = nullptr;     // [nth][nphi] float64 value of the iterate's last shell
+  unsigned int* red = nullptr;     // [2] max|e|, max|Phi| (bit patterns of non-negative floats)
+  // tensor maps (CUtensorMap, 128 bytes each) for the tcgen05 projections
+  alignas(64) unsigned char map_Ahi_f[128], map_Alo_f[128], map_Ahi_i[128], map_Alo_i[128];
+  alignas(64) unsigned char map_Bhi[128], map_Blo[128];
+};
 
 // Kernel identities for the optional per-launch CUDA-event timers.
 enum KernelId : int {
@@ -133,7 +184,24 @@ cudaError_t thomas_f64(const Plan& p, double* x, cudaStream_t s);
 cudaError_t stencil_f64(const Plan& p, const double* phi, double* out, cudaStream_t s);
 // Multipole outer term on the last shell: out[nr-1] += outer_coef * kappa(A_Omega) phi[nr-1].
 cudaError_t outer_term_f64(const Plan& p, const double* phi, double* out, cudaStream_t s);
+// out[m] = H_m diag(outer[m]) (H^T W)_m in[m] for the two real columns of one shell spectrum.
+cudaError_t shell_kappa_f64(const Plan& p, const double* in, double* out, cudaStream_t s);
 // theta eigensolve for every m; writes lam, kappa, outer, H, HtW.
 cudaError_t theta_eigen(const Plan& p, cudaStream_t s);
+
+// ---- mixed-precision path ----
+size_t mixed_workspace_bytes(const Plan& p);
+void mixed_bind_workspace(Plan& p, char* base);
+int mixed_create_tables(Plan& p, cudaStream_t s);   // after theta_eigen; returns sp_status
+void mixed_free_tables(Plan& p);
+bool mixed_make_panel_maps(Plan& p);
+cudaError_t fft_forward_split(const Plan& p, const void* in, bool in_double, float scale, int kstride,
+                              __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t s);
+cudaError_t fft_inverse_update(const Plan& p, const float* spec, float* phi_hi, float* phi_lo, bool first,
+                               unsigned int* red, cudaStream_t s);
+cudaError_t finish_mixed(const Plan& p, double* phi, cudaStream_t s);   // float-float iterate -> float64 Phi
+cudaError_t tc_project(const Plan& p, bool inverse, cudaStream_t s);   // pan -> d32
+cudaError_t thomas_mixed(const Plan& p, cudaStream_t s);   // d32 -> pan (f); float32 + float64 low modes
+cudaError_t residual_ff(const Plan& p, const double* rho, cudaStream_t s);  // iterate -> r32
 
 }  // namespace sp

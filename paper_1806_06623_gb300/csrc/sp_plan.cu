@@ -41,7 +41,19 @@ bool make_schedule(int n, sp::FftSchedule* s) {
   while (r % 4 == 0) { if (s->nstages >= sp::kMaxStages) return false; s->radix[s->nstages++] = 4; r /= 4; }
   while (r % 2 == 0) { if (s->nstages >= sp::kMaxStages) return false; s->radix[s->nstages++] = 2; r /= 2; }
   while (r % 3 == 0) { if (s->nstages >= sp::kMaxStages) return false; s->radix[s->nstages++] = 3; r /= 3; }
-  return r == 1;
+  if (r != 1) return false;
+  int ns = 1;
+  for (int st = 0; st < s->nstages; ++st) {
+    s->ns[st] = ns;
+    s->tstep[st] = n / (ns * s->radix[st]);
+    int sh = -1;
+    for (int b = 0; b < 31; ++b)
+      if ((1 << b) == ns) sh = b;
+    s->shift[st] = sh;
+    s->magic[st] = (unsigned int)((1ull << 32) / (unsigned long long)ns + 1ull);
+    ns *= s->radix[st];
+  }
+  return true;
 }
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -69,6 +81,7 @@ void free_tables(Plan* p) {
   cudaFree(p->d_err);
   cudaFree(p->d_rho_io);
   cudaFree(p->d_phi_io);
+  sp::mixed_free_tables(*p);
   if (p->ws_owned) cudaFree(p->ws);
   for (int i = 0; i < 2 * sp::kMaxTimedLaunches; ++i)
     if (p->ev[i]) cudaEventDestroy(p->ev[i]);
@@ -89,6 +102,7 @@ int ensure_workspace(Plan* p) {
   p->ws_bytes = b;
   p->ws_owned = true;
   sp::bind_workspace(*p, w);
+  if (p->mixed && !sp::mixed_make_panel_maps(*p)) return SP_ERR_CUDA;
   return SP_OK;
 }
 
@@ -121,6 +135,88 @@ int solve_fp64(Plan* p, const double* rho, double* phi, cudaStream_t s) {
     return sp::fft_inverse_f64(P, P.specA, nr, phi, false, s); }));
 }
 
+// One low-precision separated solve of L e = (scale*Nphi) * input: FFT (float32, bf16
+// split), tcgen05 projection, float32/float64 radial solves, tcgen05 back projection,
+// inverse FFT with Phi (+)= e and the max|e|, max|Phi| reductions.
+int lp_solve(Plan* p, const void* in, bool in_double, float scale, double* phi, bool first, cudaStream_t s) {
+  Plan& P = *p;
+  sp::MixedTables& x = *P.mixed;
+  int st;
+  if ((st = launch_status(sp::timed_launch(P, sp::kKFftFwd, s, [&] {
+         return sp::fft_forward_split(P, in, in_double, scale, x.kstride, x.pan_hi, x.pan_lo, s); }))))
+    return st;
+  if ((st = launch_status(sp::timed_launch(P, sp::kKGemmFwd, s, [&] { return sp::tc_project(P, false, s); }))))
+    return st;
+  if ((st = launch_status(sp::timed_launch(P, sp::kKThomas, s, [&] { return sp::thomas_mixed(P, s); })))) return st;
+  if ((st = launch_status(sp::timed_launch(P, sp::kKGemmInv, s, [&] { return sp::tc_project(P, true, s); }))))
+    return st;
+  (void)phi;
+  return launch_status(sp::timed_launch(P, sp::kKFftInv, s, [&] {
+    return sp::fft_inverse_update(P, x.d32, x.phi_hi, x.phi_lo, first, x.red, s); }));
+}
+
+int read_reductions(Plan* p, cudaStream_t s, double* emax, double* pmax) {
+  unsigned int h[2] = {0, 0};
+  SP_CUDA(cudaMemcpyAsync(h, p->mixed->red, sizeof(h), cudaMemcpyDeviceToHost, s));
+  SP_CUDA(cudaStreamSynchronize(s));
+  float v[2];
+  std::memcpy(v, h, sizeof(v));
+  *emax = v[0];
+  *pmax = v[1];
+  return SP_OK;
+}
+
+// Mixed-precision solve with float64 iterative refinement (stops when the estimated
+// max|Phi - Phi_exact|/max|Phi| <= tol).
+int solve_mixed(Plan* p, const double* rho, double* phi, cudaStream_t s, sp_solve_info* info) {
+  Plan& P = *p;
+  sp::MixedTables& x = *P.mixed;
+  const double four_pi_g = 4.0 * kPi * P.G;
+  int st;
+  SP_CUDA(cudaMemsetAsync(x.red, 0, 2 * sizeof(unsigned int), s));
+  if ((st = lp_solve(p, rho, true, (float)(four_pi_g / P.nphi), phi, true, s))) return st;
+  double e_prev = 0.0, e_cur = 0.0, pmax = 0.0;
+  if ((st = read_reductions(p, s, &e_prev, &pmax))) return st;
+  int iters = 1;
+  double est = 1.0, last = 1.0;
+  bool done = false;
+  if (pmax == 0.0) { done = true; est = 0.0; last = 0.0; }   // rho == 0
+  for (int k = 1; k <= P.max_iter && !done; ++k) {
+    if ((st = launch_status(sp::timed_launch(P, sp::kKResidual, s, [&] { return sp::residual_ff(P, rho, s); }))))
+      return st;
+    if (P.outer_bc == SP_OUTER_MULTIPOLE) P.launches += 4;
+    SP_CUDA(cudaMemsetAsync(x.red, 0, 2 * sizeof(unsigned int), s));
+    if ((st = lp_solve(p, x.r32, false, (float)(1.0 / P.nphi), phi, false, s))) return st;
+    if ((st = read_reductions(p, s, &e_cur, &pmax))) return st;
+    ++iters;
+    last = e_cur / pmax;
+    if (k == 1) {
+      // the first correction measures the first solve's error; Phi_1 is better than that
+      est = last;
+      done = last <= P.tol;
+    } else {
+      const double ratio = e_cur / e_prev;
+      est = (ratio < 1.0) ? last * ratio / (1.0 - ratio) : last;
+      done = est <= P.tol || last <= 1e-15;
+    }
+    e_prev = e_cur;
+  }
+  if ((st = launch_status(sp::timed_launch(P, sp::kKUpdate, s, [&] { return sp::finish_mixed(P, phi, s); }))))
+    return st;
+  int herr = 0;
+  SP_CUDA(cudaMemcpyAsync(&herr, P.d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  SP_CUDA(cudaStreamSynchronize(s));
+  st = herr ? ((herr & sp::kErrTimeout) ? SP_ERR_TIMEOUT : SP_ERR_DEVICE_CHECK) : (done ? SP_OK : SP_ERR_NOT_CONVERGED);
+  if (info) {
+    info->iterations = iters;
+    info->precision_used = SP_MIXED_BF16X3;
+    info->last_update = last;
+    info->est_rel_error = est;
+    info->status = st;
+  }
+  return st;
+}
+
 int apply_laplacian_impl(Plan* p, const double* phi, double* out, cudaStream_t s) {
   Plan& P = *p;
   int st = launch_status(sp::timed_launch(P, sp::kKStencil, s, [&] { return sp::stencil_f64(P, phi, out, s); }));
@@ -138,6 +234,7 @@ int apply_laplacian_impl(Plan* p, const double* phi, double* out, cudaStream_t s
 namespace sp {
 
 size_t workspace_bytes(const Plan& p) {
+  if (p.mixed) return mixed_workspace_bytes(p);
   const size_t spec = sizeof(double) * (size_t)p.mh * p.nr * 2 * p.nth;
   const size_t cpb = sizeof(double) * (size_t)p.mh * p.nr * p.nth;
   const size_t shell = sizeof(double) * (size_t)p.mh * 2 * p.nth;
@@ -146,6 +243,10 @@ size_t workspace_bytes(const Plan& p) {
 
 void bind_workspace(Plan& p, void* base) {
   char* c = static_cast<char*>(base);
+  if (p.mixed) {
+    mixed_bind_workspace(p, c);
+    return;
+  }
   const size_t spec = align256(sizeof(double) * (size_t)p.mh * p.nr * 2 * p.nth);
   const size_t cpb = align256(sizeof(double) * (size_t)p.mh * p.nr * p.nth);
   const size_t shell = align256(sizeof(double) * (size_t)p.mh * 2 * p.nth);
@@ -187,8 +288,8 @@ int sp_plan_create(const double* r_if, int nr, const double* th_if_in, int nth, 
   if (outer_bc != SP_OUTER_MULTIPOLE && outer_bc != SP_OUTER_DIRICHLET) return SP_ERR_INVALID_ARG;
   if (precision != SP_FP64 && precision != SP_MIXED_BF16X3) return SP_ERR_INVALID_ARG;
   if (!std::isfinite(G)) return SP_ERR_INVALID_ARG;
-  if (precision != SP_FP64) return SP_ERR_UNSUPPORTED;
   if (nth > sp::kMaxNtheta || nphi > sp::kMaxNphi) return SP_ERR_UNSUPPORTED;
+  if (precision == SP_MIXED_BF16X3 && (nth > 128 || max_iter < 1 || !(tol > 0.0))) return SP_ERR_UNSUPPORTED;
   sp::FftSchedule sched;
   if (!make_schedule(nphi, &sched)) return SP_ERR_UNSUPPORTED;
   // --- validate the grid
@@ -332,6 +433,7 @@ int sp_plan_create(const double* r_if, int nr, const double* th_if_in, int nth, 
       break;
     }
     if (herr) { st = SP_ERR_DEVICE_CHECK; break; }
+    if (precision == SP_MIXED_BF16X3 && (st = sp::mixed_create_tables(*p, s))) break;
   } while (0);
   if (st != SP_OK) {
     free_tables(p);
@@ -360,6 +462,7 @@ int sp_plan_set_workspace(sp_plan* plan, void* dev, size_t bytes) {
   p->ws_bytes = bytes;
   p->ws_owned = false;
   sp::bind_workspace(*p, dev);
+  if (p->mixed && !sp::mixed_make_panel_maps(*p)) return SP_ERR_CUDA;
   return SP_OK;
 }
 
@@ -372,6 +475,7 @@ int sp_solve(sp_plan* plan, const double* rho, double* phi, void* stream, sp_sol
   int st = ensure_workspace(p);
   if (st) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (p->mixed) return solve_mixed(p, rho, phi, s, info);
   st = solve_fp64(p, rho, phi, s);
   if (info) {
     info->iterations = 1;

@@ -1,0 +1,264 @@
+// Split-bf16 theta projection on the 5th-generation tensor cores (tcgen05 + TMA + TMEM).
+//
+// For every azimuthal wavenumber m (Sect. 3.2) the projection is the product
+//   D[m][n][r] = sum_k A[m][r][k] B[m][n][k]      (r < M = Ntheta rows, k < K = Ntheta)
+// with A the (H^T W)_m or H_m table and B the K-contiguous spectral panel of 2 Nr
+// columns n = (i, re/im).  Both operands arrive as bf16 pairs x = hi + lo
+// (hi = RN_bf16(x), lo = RN_bf16(x - hi)) and the product keeps three of the four terms,
+//   A_lo B_hi + A_hi B_lo + A_hi B_hi,
+// accumulated in float32 in tensor memory: relative error ~2^-16 instead of bf16's 2^-8.
+//
+// One CTA per (m, 256-column tile), 128 threads:
+//  - thread 0 issues TMA loads of the four operand tiles (128B-swizzled K-major boxes of
+//    64 K-elements) onto one mbarrier, waits, then issues 8 K-steps x 3 tcgen05.mma
+//    (M=128, N=256, K=16, kind::f16, bf16 inputs, f32 accumulator in TMEM) and commits
+//    them to a second mbarrier;
+//  - all four warps then read the 128 x 256 accumulator back with tcgen05.ld (warp w owns
+//    TMEM lanes 32w..32w+31 = output rows) and store float32 rows coalesced along r.
+// Every wait is bounded: on expiry the CTA records kErrTimeout and still frees its TMEM.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace sp {
+namespace tc {
+
+constexpr int kM = 128;          // UMMA M (rows = l or j)
+constexpr int kN = 256;          // UMMA N (columns of the spectral panel per CTA)
+constexpr int kKBlk = 64;        // K elements per 128-byte swizzle row
+constexpr int kMaxKBlocks = 2;   // K <= 128
+constexpr uint32_t kABlockBytes = kM * 128;   // 16 KB per K block
+constexpr uint32_t kBBlockBytes = kN * 128;   // 32 KB per K block
+constexpr uint32_t kSmemBytes = 2 * kMaxKBlocks * kABlockBytes + 2 * kMaxKBlocks * kBBlockBytes + 1024;
+constexpr int kErrTimeout = 4;
+constexpr long long kSpinLimit = 1ll << 26;
+
+struct Params {
+  float* D;       // [mh][ncol][M]
+  int M;          // valid rows (Ntheta)
+  int ncol;       // columns per m
+  int kblocks;    // ceil(K / 64)
+  int* err;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// Bounded wait for phase `parity` of an mbarrier; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (long long it = 0; it < kSpinLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row atoms of 1024 B.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);          // start address
+  d |= (uint64_t)1 << 16;                            // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024u >> 4) << 32;                 // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                            // descriptor version for tcgen05
+  d |= (uint64_t)2 << 61;                            // swizzle: 128B
+  return d;
+}
+
+// Instruction descriptor: kind::f16, bf16 A and B (K-major), f32 accumulator, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+      ::"r"(tmem_d), "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+__global__ void __launch_bounds__(128, 1)
+    k_tc_gemm_bf16x3(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmAlo,
+                     const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo,
+                     Params prm) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // 1024-byte alignment of the swizzle atoms
+  const uint32_t base_u32 = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  unsigned char* base = smem_raw + (base_u32 - smem_u32(smem_raw));
+  const uint32_t sAhi = base_u32;
+  const uint32_t sAlo = sAhi + kMaxKBlocks * kABlockBytes;
+  const uint32_t sBhi = sAlo + kMaxKBlocks * kABlockBytes;
+  const uint32_t sBlo = sBhi + kMaxKBlocks * kBBlockBytes;
+  (void)base;
+  __shared__ __align__(8) uint64_t bar_load;
+  __shared__ __align__(8) uint64_t bar_mma;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_fail;
+
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5;
+  const int lane = tid & 31;
+  const int m = blockIdx.y;
+  const int n0 = blockIdx.x * kN;
+  const int kb = prm.kblocks;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"((uint32_t)kN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    s_fail = 0;
+    mbar_init(smem_u32(&bar_load), 1);
+    mbar_init(smem_u32(&bar_mma), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+
+  if (tid == 0) {
+    const uint32_t bl = smem_u32(&bar_load);
+    mbar_expect_tx(bl, (uint32_t)kb * (2 * kABlockBytes + 2 * kBBlockBytes));
+    for (int b = 0; b < kb; ++b) {
+      tma_load_3d(sAhi + b * kABlockBytes, &tmAhi, b * kKBlk, 0, m, bl);
+      tma_load_3d(sAlo + b * kABlockBytes, &tmAlo, b * kKBlk, 0, m, bl);
+      tma_load_3d(sBhi + b * kBBlockBytes, &tmBhi, b * kKBlk, n0, m, bl);
+      tma_load_3d(sBlo + b * kBBlockBytes, &tmBlo, b * kKBlk, n0, m, bl);
+    }
+    bool ok = mbar_wait(bl, 0);
+    if (ok) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t idesc = idesc_bf16_f32(kM, kN);
+      uint32_t acc = 0;
+      for (int kk = 0; kk < kb * (kKBlk / 16); ++kk) {
+        const int b = kk / (kKBlk / 16);
+        const uint32_t koff = (uint32_t)(kk % (kKBlk / 16)) * 32u;   // 16 bf16 = 32 B along the swizzled row
+        const uint64_t ahi = smem_desc_sw128(sAhi + b * kABlockBytes + koff);
+        const uint64_t alo = smem_desc_sw128(sAlo + b * kABlockBytes + koff);
+        const uint64_t bhi = smem_desc_sw128(sBhi + b * kBBlockBytes + koff);
+        const uint64_t blo = smem_desc_sw128(sBlo + b * kBBlockBytes + koff);
+        umma_bf16(tmem, alo, bhi, idesc, acc);
+        acc = 1;
+        umma_bf16(tmem, ahi, blo, idesc, 1);
+        umma_bf16(tmem, ahi, bhi, idesc, 1);
+      }
+      umma_commit(smem_u32(&bar_mma));
+    } else {
+      s_fail = 1;
+      atomicOr(prm.err, kErrTimeout);
+    }
+  }
+  __syncthreads();
+  if (!s_fail) {
+    if (!mbar_wait(smem_u32(&bar_mma), 0)) {
+      atomicOr(prm.err, kErrTimeout);
+    } else {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int row = warp * 32 + lane;
+      float* Dm = prm.D + (size_t)m * prm.ncol * prm.M;
+#pragma unroll 1
+      for (int c0 = 0; c0 < kN; c0 += 32) {
+        float v[32];
+        tmem_ld_32x32b_x32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+        if (row < prm.M) {
+#pragma unroll
+          for (int q = 0; q < 32; ++q) {
+            const int col = n0 + c0 + q;
+            if (col < prm.ncol) Dm[(size_t)col * prm.M + row] = v[q];
+          }
+        }
+      }
+    }
+  } else {
+    // loads may still be in flight: give them a bounded chance to land before exit
+    mbar_wait(smem_u32(&bar_load), 0);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)kN));
+  }
+}
+
+// ------------------------------------------------------------------ host side
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+inline EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// Tensor map of a bf16 array [batch][rows][K] with row stride `kstride` elements
+// (kstride*2 bytes must be a multiple of 16); boxes of 64 K-elements x box_rows rows.
+inline bool make_map(CUtensorMap* map, const void* base, int K, int kstride, int rows, int batch, int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)batch};
+  cuuint64_t strides[2] = {(cuuint64_t)kstride * 2, (cuuint64_t)kstride * 2 * rows};
+  cuuint32_t box[3] = {(cuuint32_t)kKBlk, (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+}  // namespace tc
+}  // namespace sp

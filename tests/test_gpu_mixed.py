@@ -1,0 +1,116 @@
+"""Mixed-precision solve (split-bf16 tcgen05 projections, float32 FFT and radial solves,
+float64 residual refinement) against the oracle's exact float64 solution.
+
+Gate: max|dPhi|/max|Phi| <= 1e-10 (the requested tolerance), with the solver's own
+error estimate also <= 1e-10 and the float64 backward error eta <= 1e-12."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import sph_poisson as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1806_06623_gb300 as S
+    S.lib()
+    return S
+
+
+def mixed_solve(S, p, tol=TOL, max_iter=8):
+    plan = S.Plan(p.r_if, p.th_if, p.nphi, outer_bc=p.outer_bc, G=p.G, precision=S.SP_MIXED_BF16X3,
+                  tol=tol, max_iter=max_iter)
+    rho = torch.from_numpy(np.ascontiguousarray(p.rho)).cuda()
+    phi, info = plan.solve(rho)
+    torch.cuda.synchronize()
+    return plan, phi.cpu().numpy(), info
+
+
+def rel_err(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+CASES = [
+    (5, 4, 6, "log", 0.0, 0),
+    (7, 8, 12, "rand", 0.0, 0),
+    (5, 3, 6, "rand", 0.2, 0),
+    (6, 5, 9, "uniform", 0.0, 1),
+    (3, 1, 4, "uniform", 0.0, 0),
+    (1, 3, 4, "uniform", 0.5, 0),
+    (33, 17, 48, "log", 0.0, 0),
+    (65, 31, 96, "rand", 0.1, 0),
+    (130, 128, 24, "log", 0.0, 0),     # full M tile, ragged N tile
+    (300, 96, 192, "log", 0.0, 0),     # radix-3 phi, partial second K block
+    (257, 64, 8, "uniform", 0.0, 1),
+]
+
+
+@pytest.mark.parametrize("nr,nth,nphi,grid,rin,bc", CASES)
+def test_mixed_matches_exact_small(S, nr, nth, nphi, grid, rin, bc):
+    p = W.random_small(nr, nth, nphi, seed=nr + 3 * nth + nphi, grid=grid, r_inner=rin, outer_bc=bc)
+    _, phi, info = mixed_solve(S, p)
+    ref = O.solve_exact(O.Geometry(p.r_if, p.th_if, p.nphi), p.rho, outer_bc=bc)
+    assert info.status == S.SP_OK
+    assert rel_err(phi, ref) <= TOL
+    assert info.est_rel_error <= TOL and info.iterations >= 2
+
+
+@pytest.mark.parametrize("make", [W.sphere_blob, W.stellar_noise])
+def test_mixed_matches_exact_workloads(S, make):
+    p = make()
+    _, phi, info = mixed_solve(S, p)
+    geo = O.Geometry(p.r_if, p.th_if, p.nphi)
+    ref = O.solve_exact(geo, p.rho)
+    assert rel_err(phi, ref) <= TOL
+    eta, _ = O.residuals(geo, phi, p.rho)
+    assert eta <= 1e-12
+
+
+def test_mixed_full_size_stellar_sh(S):
+    """The 550x128x256 headline workload."""
+    p = W.stellar_sh()
+    _, phi, info = mixed_solve(S, p)
+    geo = O.Geometry(p.r_if, p.th_if, p.nphi)
+    ref = O.solve_exact(geo, p.rho)
+    err = rel_err(phi, ref)
+    assert err <= TOL, (err, info.as_dict())
+    assert info.est_rel_error <= TOL
+    eta, _ = O.residuals(geo, phi, p.rho)
+    assert eta <= 1e-12
+
+
+def test_mixed_reports_non_convergence(S):
+    """An unreachable tolerance with one correction allowed fails with a status, not a fault."""
+    p = W.stellar_noise()
+    _, phi, info = None, None, None
+    plan = S.Plan(p.r_if, p.th_if, p.nphi, precision=S.SP_MIXED_BF16X3, tol=1e-30, max_iter=1)
+    rho = torch.from_numpy(p.rho).cuda()
+    with pytest.raises(S.SpError) as ei:
+        plan.solve(rho)
+    assert ei.value.status == S.SP_ERR_NOT_CONVERGED
+    # the plan stays usable
+    plan2 = S.Plan(p.r_if, p.th_if, p.nphi, precision=S.SP_MIXED_BF16X3)
+    out, info = plan2.solve(rho)
+    assert info.status == S.SP_OK
+
+
+def test_mixed_zero_source(S):
+    p = W.random_small(6, 8, 8, seed=1)
+    p.rho[:] = 0.0
+    _, phi, info = mixed_solve(S, p)
+    assert info.status == S.SP_OK and np.all(phi == 0.0)
+
+
+def test_mixed_equals_fp64_plan_within_tolerance(S):
+    p = W.stellar_noise()
+    _, phi_m, _ = mixed_solve(S, p)
+    plan = S.Plan(p.r_if, p.th_if, p.nphi)
+    phi_d, _ = plan.solve(torch.from_numpy(p.rho).cuda())
+    assert rel_err(phi_m, phi_d.cpu().numpy()) <= 2 * TOL
