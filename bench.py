@@ -37,7 +37,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default=None)
+    ap.add_argument("--precision", choices=["fp64", "mixed", "mixed_x3"], default=None,
+                    help="headline arithmetic: mixed = 6-product split bf16 (default), mixed_x3 = 3-product")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-oracle-check", action="store_true")
     return ap.parse_args()
@@ -168,8 +169,10 @@ def run_ours(args, rank, world, local):
 
     plans = {}
     plans["fp64"] = S.Plan(p.r_if, p.th_if, p.nphi, precision=S.SP_FP64)
+    if precision in ("mixed", "mixed_x3"):
+        plans["mixed_x3"] = S.Plan(p.r_if, p.th_if, p.nphi, precision=S.SP_MIXED_BF16X3, tol=1e-10)
     if precision == "mixed":
-        plans["mixed"] = S.Plan(p.r_if, p.th_if, p.nphi, precision=S.SP_MIXED_BF16X3, tol=1e-10)
+        plans["mixed"] = S.Plan(p.r_if, p.th_if, p.nphi, precision=S.SP_MIXED_BF16X6, tol=1e-10)
     head = plans[precision]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
 
@@ -246,7 +249,10 @@ def run_ours(args, rank, world, local):
         "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": value / PAPER_BEST_ZPS,
         "vs_baseline_ref": "Table 1 of the paper: 0.036 s per 550x128x256 solve, parity-split, 1024 CPU cores",
-        "dtype": "f64" if precision == "fp64" else "bf16x3+f32 with f64 refinement",
+        "dtype": {"fp64": "f64", "mixed_x3": "bf16 (2-plane split, 3 products) + f32, float-float refinement",
+                  "mixed": "bf16 (3-plane split, 6 products) + f32, float-float refinement"}[precision],
+        "tol": 1e-10,
+        "solve_info": r["infos"][-1],
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "precision": precision, "global_batch": world,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",

@@ -59,19 +59,24 @@ typedef enum {
  * exists for tests and for bounded domains. */
 enum { SP_OUTER_MULTIPOLE = 0, SP_OUTER_DIRICHLET = 1 };
 
-/* Arithmetic of sp_solve.  SP_FP64: every step in float64.  SP_MIXED_BF16X3: the
- * low-precision solve runs the phi FFTs and the radial solves in float32 (float64 for
- * the near-singular low-|lambda| radial modes) and the theta projections as three
- * bf16 tensor-core products with float32 accumulation; float64 iterative refinement
- * with the float64 residual of the finite-volume operator brings the result to tol. */
-enum { SP_FP64 = 0, SP_MIXED_BF16X3 = 1 };
+/* Arithmetic of sp_solve.  SP_FP64: every step in float64.  The mixed modes run a
+ * low-precision solve -- phi FFTs and radial solves in float32 (float64 for the
+ * near-singular |lambda| < 30 radial modes), theta projections on the tensor cores
+ * from bf16 split operands with float32 accumulation -- and refine it with the
+ * residual of the finite-volume operator evaluated in float-float (~48-bit)
+ * arithmetic until the estimated error is below tol:
+ *   SP_MIXED_BF16X3  operands split into 2 bf16 planes, 3 products (~2^-16 per product)
+ *   SP_MIXED_BF16X6  operands split into 3 bf16 planes, 6 products (~2^-24), which
+ *                    needs fewer refinement steps. */
+enum { SP_FP64 = 0, SP_MIXED_BF16X3 = 1, SP_MIXED_BF16X6 = 2 };
 
 typedef struct {
     int iterations;        /* low-precision solves performed (1 for SP_FP64) */
-    int precision_used;    /* SP_FP64 or SP_MIXED_BF16X3 */
+    int precision_used;    /* SP_FP64, SP_MIXED_BF16X3 or SP_MIXED_BF16X6 */
     double last_update;    /* max|e|/max|Phi| of the last correction (0 for SP_FP64) */
     double est_rel_error;  /* estimated max|Phi - Phi_exact|/max|Phi| (0 for SP_FP64) */
     int status;            /* sp_status of the solve */
+    double update_history[8]; /* max|e_k|/max|Phi| of the first 8 solves (k = 0 is the first solve) */
 } sp_solve_info;
 
 /* Create a plan (Sect. 3.1 geometry, Sect. 3.2 eigenbasis) on the current CUDA device.
@@ -81,7 +86,7 @@ typedef struct {
  *  Nr, Ntheta >= 1; Ntheta <= 160.  Nphi >= 1 with Nphi = 2^a 3^b, Nphi <= 4096.
  *  outer_bc          SP_OUTER_MULTIPOLE or SP_OUTER_DIRICHLET
  *  G                 gravitational constant (s = 4 pi G rho)
- *  precision         SP_FP64 or SP_MIXED_BF16X3
+ *  precision         SP_FP64, SP_MIXED_BF16X3 or SP_MIXED_BF16X6 (mixed: Ntheta <= 128)
  *  tol, max_iter     refinement target max|Phi-Phi_exact|/max|Phi| and iteration cap
  *                    (mixed precision only; e.g. 1e-10 and 8)
  *  stream            set-up work (theta eigensolve on the GPU) runs on this stream and

@@ -27,6 +27,7 @@ SP_OUTER_MULTIPOLE = 0
 SP_OUTER_DIRICHLET = 1
 SP_FP64 = 0
 SP_MIXED_BF16X3 = 1
+SP_MIXED_BF16X6 = 2
 
 
 class SpError(RuntimeError):
@@ -37,10 +38,12 @@ class SpError(RuntimeError):
 
 class SolveInfo(C.Structure):
     _fields_ = [("iterations", C.c_int), ("precision_used", C.c_int), ("last_update", C.c_double),
-                ("est_rel_error", C.c_double), ("status", C.c_int)]
+                ("est_rel_error", C.c_double), ("status", C.c_int), ("update_history", C.c_double * 8)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "update_history"}
+        d["update_history"] = list(self.update_history)[:max(0, min(8, self.iterations))]
+        return d
 
 
 _LIB = None

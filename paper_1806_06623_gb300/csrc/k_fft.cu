@@ -138,14 +138,24 @@ __device__ __forceinline__ T load_in(const float* p) { return (T)*p; }
 
 enum FwdOut { kOutPlain = 0, kOutSplit = 1 };
 
+// x -> bf16 planes x0 = RN(x), x1 = RN(x - x0) (, x2 = RN(x - x0 - x1))
+__device__ __forceinline__ void store_planes(const Planes& pl, size_t o, float x) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(x);
+  pl.p[0][o] = h;
+  const float r = x - __bfloat162float(h);
+  const __nv_bfloat16 m = __float2bfloat16_rn(r);
+  pl.p[1][o] = m;
+  if (pl.n == 3) pl.p[2][o] = __float2bfloat16_rn(r - __bfloat162float(m));
+}
+
 // Forward: lines [line0, line0+nl) of `in` -> half spectrum scaled by `scale`:
 //  OUT = kOutPlain: spec[m][i][c][j] (row stride Ntheta)
-//  OUT = kOutSplit: bf16 pair hi/lo[m][i][c][j] (row stride kstride)
+//  OUT = kOutSplit: bf16 planes pl[m][i][c][j] (row stride kstride)
+
 template <typename T, typename Tin, int OUT>
 __global__ void __launch_bounds__(256) k_fft_fwd(const Tin* __restrict__ in, int nlines, int nth, int nrs,
                                                  FftSchedule sch, const T* __restrict__ twid, T scale, int lpc,
-                                                 T* __restrict__ spec, __nv_bfloat16* __restrict__ hi,
-                                                 __nv_bfloat16* __restrict__ lo, int kstride) {
+                                                 T* __restrict__ spec, Planes pl, int kstride) {
   using CT = typename C2<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = sch.n;
@@ -194,11 +204,8 @@ __global__ void __launch_bounds__(256) k_fft_fwd(const Tin* __restrict__ in, int
         o[nth] = im;
       } else {
         const size_t o = ((size_t)(m * nrs + i) * 2) * kstride + j;
-        const __nv_bfloat16 rh = __float2bfloat16_rn((float)re), ih = __float2bfloat16_rn((float)im);
-        hi[o] = rh;
-        lo[o] = __float2bfloat16_rn((float)re - __bfloat162float(rh));
-        hi[o + kstride] = ih;
-        lo[o + kstride] = __float2bfloat16_rn((float)im - __bfloat162float(ih));
+        store_planes(pl, o, (float)re);
+        store_planes(pl, o + kstride, (float)im);
       }
     }
   }
@@ -343,7 +350,7 @@ cudaError_t fft_forward_f64(const Plan& p, const double* in, int nrs, double sca
   cudaError_t e = prep(kern, smem);
   if (e != cudaSuccess) return e;
   kern<<<(nlines + lpc - 1) / lpc, 32 * kWarps, smem, s>>>(in, nlines, p.nth, nrs, p.sched, p.d_twid, scale, lpc, spec,
-                                                           nullptr, nullptr, 0);
+                                                           Planes{{nullptr, nullptr, nullptr}, 0}, 0);
   return cudaGetLastError();
 }
 
@@ -365,8 +372,8 @@ cudaError_t fft_inverse_f64(const Plan& p, const double* spec, int nrs, double* 
   return cudaGetLastError();
 }
 
-cudaError_t fft_forward_split(const Plan& p, const void* in, bool in_double, float scale, int kstride,
-                              __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t s) {
+cudaError_t fft_forward_split(const Plan& p, const void* in, bool in_double, float scale, int kstride, Planes out,
+                              cudaStream_t s) {
   const int nlines = p.nr * p.nth;
   const int lpc = lines_per_cta<float>(p.nphi);
   const size_t smem = fft_smem<float>(p.nphi, lpc);
@@ -376,12 +383,12 @@ cudaError_t fft_forward_split(const Plan& p, const void* in, bool in_double, flo
     auto kern = k_fft_fwd<float, double, kOutSplit>;
     if ((e = prep(kern, smem)) != cudaSuccess) return e;
     kern<<<grid, 32 * kWarps, smem, s>>>(static_cast<const double*>(in), nlines, p.nth, p.nr, p.sched, p.d_twid32,
-                                         scale, lpc, nullptr, hi, lo, kstride);
+                                         scale, lpc, nullptr, out, kstride);
   } else {
     auto kern = k_fft_fwd<float, float, kOutSplit>;
     if ((e = prep(kern, smem)) != cudaSuccess) return e;
     kern<<<grid, 32 * kWarps, smem, s>>>(static_cast<const float*>(in), nlines, p.nth, p.nr, p.sched, p.d_twid32,
-                                         scale, lpc, nullptr, hi, lo, kstride);
+                                         scale, lpc, nullptr, out, kstride);
   }
   return cudaGetLastError();
 }

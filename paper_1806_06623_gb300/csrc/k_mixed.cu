@@ -8,6 +8,7 @@
 //  residual: r = 4 pi G rho - L Phi in float64 (stencil of Eq. fin_vol3 plus the
 //    multipole outer-shell term), stored in float32 as the next right-hand side.
 #include <cmath>
+#include <cstring>
 #include <new>
 #include <vector>
 
@@ -19,25 +20,30 @@ namespace {
 
 size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-// table [b][rows][n] float64 -> bf16 hi/lo [b][rows][kstride], zero beyond n
-__global__ void k_split_table(const double* __restrict__ src, int rows, int n, int kstride, size_t total,
-                              __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
+// table [b][rows][n] float64 -> bf16 planes [b][rows][kstride] (x0 = RN(x), x1 = RN(x - x0),
+// x2 = RN(x - x0 - x1), differences in float64), zero beyond n
+__global__ void k_split_table(const double* __restrict__ src, int n, int kstride, size_t total, Planes pl) {
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
     const int k = (int)(t % kstride);
     const size_t br = t / kstride;
     double x = 0.0;
     if (k < n) x = src[br * n + k];
     const __nv_bfloat16 h = __double2bfloat16(x);
-    hi[t] = h;
-    lo[t] = __double2bfloat16(x - (double)__bfloat162float(h));
+    pl.p[0][t] = h;
+    const double r = x - (double)__bfloat162float(h);
+    const __nv_bfloat16 m = __double2bfloat16(r);
+    pl.p[1][t] = m;
+    if (pl.n == 3) pl.p[2][t] = __double2bfloat16(r - (double)__bfloat162float(m));
   }
-  (void)rows;
 }
 
-__device__ __forceinline__ void store_split(__nv_bfloat16* hi, __nv_bfloat16* lo, size_t o, float v) {
+__device__ __forceinline__ void store_split(const Planes& pl, size_t o, float v) {
   const __nv_bfloat16 h = __float2bfloat16_rn(v);
-  hi[o] = h;
-  lo[o] = __float2bfloat16_rn(v - __bfloat162float(h));
+  pl.p[0][o] = h;
+  const float r = v - __bfloat162float(h);
+  const __nv_bfloat16 m = __float2bfloat16_rn(r);
+  pl.p[1][o] = m;
+  if (pl.n == 3) pl.p[2][o] = __float2bfloat16_rn(r - __bfloat162float(m));
 }
 
 __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
@@ -60,8 +66,7 @@ constexpr int kStages = 4;    // chunks in flight per warp
 // cp32 receives the elimination coefficients; f leaves as bf16 hi/lo panel rows.
 __global__ void __launch_bounds__(32) k_thomas_staged(const RadialRowF* __restrict__ rad, const double* __restrict__ lam,
                                                       const double* __restrict__ outer, float* __restrict__ x,
-                                                      float* __restrict__ cp, __nv_bfloat16* __restrict__ hi,
-                                                      __nv_bfloat16* __restrict__ lo, int nr, int nth, int mh,
+                                                      float* __restrict__ cp, Planes pl, int nr, int nth, int mh,
                                                       int kstride, double thr, int nblk_f32,
                                                       const int* __restrict__ low_idx, int nlow,
                                                       const RadialRow* __restrict__ rad64,
@@ -113,8 +118,8 @@ __global__ void __launch_bounds__(32) k_thomas_staged(const RadialRowF* __restri
     __syncwarp();
     const size_t prow = (size_t)m * nr * 2;
     for (int i = lane; i < nr; i += 32) {
-      store_split(hi, lo, (prow + 2 * i) * kstride + l, (float)W[3 * i]);
-      store_split(hi, lo, (prow + 2 * i + 1) * kstride + l, (float)W[3 * i + 1]);
+      store_split(pl, (prow + 2 * i) * kstride + l, (float)W[3 * i]);
+      store_split(pl, (prow + 2 * i + 1) * kstride + l, (float)W[3 * i + 1]);
     }
     return;
   }
@@ -209,8 +214,8 @@ __global__ void __launch_bounds__(32) k_thomas_staged(const RadialRowF* __restri
           dre = b[r][0][lane] - c * dre;
           dim = b[r][1][lane] - c * dim;
         }
-        store_split(hi, lo, (prow + 2 * i) * kstride + l, dre);
-        store_split(hi, lo, (prow + 2 * i + 1) * kstride + l, dim);
+        store_split(pl, (prow + 2 * i) * kstride + l, dre);
+        store_split(pl, (prow + 2 * i + 1) * kstride + l, dim);
       }
     }
     __syncwarp();
@@ -292,7 +297,7 @@ size_t mixed_workspace_bytes(const Plan& p) {
   const MixedTables& x = *p.mixed;
   const size_t zones = (size_t)p.nr * p.nth * p.nphi;
   const size_t rows = (size_t)p.mh * 2 * p.nr;
-  return 3 * al256(zones * 4) + 2 * al256(rows * x.kstride * 2) + al256(rows * p.nth * 4) +
+  return 3 * al256(zones * 4) + x.np * al256(rows * x.kstride * 2) + al256(rows * p.nth * 4) +
          al256((size_t)p.mh * p.nr * p.nth * 4) + al256((size_t)(x.nlow ? x.nlow : 1) * p.nr * 3 * 8) +
          2 * al256((size_t)p.nth * p.nphi * 8) + 2 * al256((size_t)p.mh * 2 * p.nth * 8) + 256;
 }
@@ -307,10 +312,13 @@ void mixed_bind_workspace(Plan& p, char* c) {
   c += al256(zones * 4);
   x.phi_lo = reinterpret_cast<float*>(c);
   c += al256(zones * 4);
-  x.pan_hi = reinterpret_cast<__nv_bfloat16*>(c);
-  c += al256(rows * x.kstride * 2);
-  x.pan_lo = reinterpret_cast<__nv_bfloat16*>(c);
-  c += al256(rows * x.kstride * 2);
+  for (int q = 0; q < 3; ++q) {
+    x.pan[q] = nullptr;
+    if (q < x.np) {
+      x.pan[q] = reinterpret_cast<__nv_bfloat16*>(c);
+      c += al256(rows * x.kstride * 2);
+    }
+  }
   x.d32 = reinterpret_cast<float*>(c);
   c += al256(rows * p.nth * 4);
   x.cp32 = reinterpret_cast<float*>(c);
@@ -331,8 +339,11 @@ void mixed_bind_workspace(Plan& p, char* c) {
 
 bool mixed_make_panel_maps(Plan& p) {
   MixedTables& x = *p.mixed;
-  return tc::make_map(reinterpret_cast<CUtensorMap*>(x.map_Bhi), x.pan_hi, p.nth, x.kstride, 2 * p.nr, p.mh, tc::kN) &&
-         tc::make_map(reinterpret_cast<CUtensorMap*>(x.map_Blo), x.pan_lo, p.nth, x.kstride, 2 * p.nr, p.mh, tc::kN);
+  const int bn = x.np == 3 ? tc::Cfg<3>::BN : tc::Cfg<2>::BN;
+  bool ok = true;
+  for (int q = 0; q < x.np; ++q)
+    ok = ok && tc::make_map(reinterpret_cast<CUtensorMap*>(x.map_B[q]), x.pan[q], p.nth, x.kstride, 2 * p.nr, p.mh, bn);
+  return ok;
 }
 
 int mixed_create_tables(Plan& p, cudaStream_t s) {
@@ -341,13 +352,14 @@ int mixed_create_tables(Plan& p, cudaStream_t s) {
   p.mixed = x;
   const int nth = p.nth, mh = p.mh;
   x->kstride = (nth + 7) / 8 * 8;
+  x->np = (p.precision == SP_MIXED_BF16X6) ? 3 : 2;
   const size_t tab = (size_t)mh * nth * x->kstride;
-  if (cudaMalloc(&x->HtW_hi, tab * 2) != cudaSuccess || cudaMalloc(&x->HtW_lo, tab * 2) != cudaSuccess ||
-      cudaMalloc(&x->H_hi, tab * 2) != cudaSuccess || cudaMalloc(&x->H_lo, tab * 2) != cudaSuccess ||
-      cudaMalloc(&x->radf, sizeof(RadialRowF) * p.nr) != cudaSuccess)
-    return SP_ERR_OOM;
-  k_split_table<<<1024, 256, 0, s>>>(p.d_HtW, nth, nth, x->kstride, tab, x->HtW_hi, x->HtW_lo);
-  k_split_table<<<1024, 256, 0, s>>>(p.d_H, nth, nth, x->kstride, tab, x->H_hi, x->H_lo);
+  for (int q = 0; q < x->np; ++q)
+    if (cudaMalloc(&x->HtW[q], tab * 2) != cudaSuccess || cudaMalloc(&x->Hm[q], tab * 2) != cudaSuccess)
+      return SP_ERR_OOM;
+  if (cudaMalloc(&x->radf, sizeof(RadialRowF) * p.nr) != cudaSuccess) return SP_ERR_OOM;
+  k_split_table<<<1024, 256, 0, s>>>(p.d_HtW, nth, x->kstride, tab, Planes{{x->HtW[0], x->HtW[1], x->HtW[2]}, x->np});
+  k_split_table<<<1024, 256, 0, s>>>(p.d_H, nth, x->kstride, tab, Planes{{x->Hm[0], x->Hm[1], x->Hm[2]}, x->np});
   if (cudaGetLastError() != cudaSuccess) return SP_ERR_CUDA;
   std::vector<RadialRow> rad(p.nr);
   std::vector<double> lam((size_t)mh * nth);
@@ -388,20 +400,20 @@ int mixed_create_tables(Plan& p, cudaStream_t s) {
                                                      x->low_fac);
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return SP_ERR_CUDA;
   }
-  const bool ok = tc::make_map(reinterpret_cast<CUtensorMap*>(x->map_Ahi_f), x->HtW_hi, nth, x->kstride, nth, mh, tc::kM) &&
-                  tc::make_map(reinterpret_cast<CUtensorMap*>(x->map_Alo_f), x->HtW_lo, nth, x->kstride, nth, mh, tc::kM) &&
-                  tc::make_map(reinterpret_cast<CUtensorMap*>(x->map_Ahi_i), x->H_hi, nth, x->kstride, nth, mh, tc::kM) &&
-                  tc::make_map(reinterpret_cast<CUtensorMap*>(x->map_Alo_i), x->H_lo, nth, x->kstride, nth, mh, tc::kM);
+  bool ok = true;
+  for (int q = 0; q < x->np; ++q)
+    ok = ok && tc::make_map(reinterpret_cast<CUtensorMap*>(x->map_Af[q]), x->HtW[q], nth, x->kstride, nth, mh, tc::kM) &&
+         tc::make_map(reinterpret_cast<CUtensorMap*>(x->map_Ai[q]), x->Hm[q], nth, x->kstride, nth, mh, tc::kM);
   return ok ? SP_OK : SP_ERR_CUDA;
 }
 
 void mixed_free_tables(Plan& p) {
   if (!p.mixed) return;
   MixedTables* x = p.mixed;
-  cudaFree(x->HtW_hi);
-  cudaFree(x->HtW_lo);
-  cudaFree(x->H_hi);
-  cudaFree(x->H_lo);
+  for (int q = 0; q < 3; ++q) {
+    cudaFree(x->HtW[q]);
+    cudaFree(x->Hm[q]);
+  }
   cudaFree(x->radf);
   cudaFree(x->low_idx);
   cudaFree(x->low_fac);
@@ -411,26 +423,33 @@ void mixed_free_tables(Plan& p) {
   p.mixed = nullptr;
 }
 
-cudaError_t tc_project(const Plan& p, bool inverse, cudaStream_t s) {
+template <int NP>
+cudaError_t tc_project_np(const Plan& p, bool inverse, cudaStream_t s) {
   const MixedTables& x = *p.mixed;
-  const CUtensorMap* ahi = reinterpret_cast<const CUtensorMap*>(inverse ? x.map_Ahi_i : x.map_Ahi_f);
-  const CUtensorMap* alo = reinterpret_cast<const CUtensorMap*>(inverse ? x.map_Alo_i : x.map_Alo_f);
-  const CUtensorMap* bhi = reinterpret_cast<const CUtensorMap*>(x.map_Bhi);
-  const CUtensorMap* blo = reinterpret_cast<const CUtensorMap*>(x.map_Blo);
+  tc::Maps maps;
+  for (int q = 0; q < NP; ++q) {
+    std::memcpy(&maps.a[q], inverse ? x.map_Ai[q] : x.map_Af[q], sizeof(CUtensorMap));
+    std::memcpy(&maps.b[q], x.map_B[q], sizeof(CUtensorMap));
+  }
   tc::Params prm{x.d32, p.nth, 2 * p.nr, (p.nth + tc::kKBlk - 1) / tc::kKBlk, p.d_err};
-  cudaError_t e = cudaFuncSetAttribute(tc::k_tc_gemm_bf16x3, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)tc::kSmemBytes);
+  constexpr uint32_t smem = tc::smem_bytes<NP>();
+  cudaError_t e = cudaFuncSetAttribute(tc::k_tc_gemm_split<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  dim3 grid((2 * p.nr + tc::kN - 1) / tc::kN, p.mh);
-  tc::k_tc_gemm_bf16x3<<<grid, 128, tc::kSmemBytes, s>>>(*ahi, *alo, *bhi, *blo, prm);
+  dim3 grid((2 * p.nr + tc::Cfg<NP>::BN - 1) / tc::Cfg<NP>::BN, p.mh);
+  tc::k_tc_gemm_split<NP><<<grid, 128, smem, s>>>(maps, prm);
   return cudaGetLastError();
+}
+
+cudaError_t tc_project(const Plan& p, bool inverse, cudaStream_t s) {
+  return p.mixed->np == 3 ? tc_project_np<3>(p, inverse, s) : tc_project_np<2>(p, inverse, s);
 }
 
 cudaError_t thomas_mixed(const Plan& p, cudaStream_t s) {
   const MixedTables& x = *p.mixed;
   const int nblk = p.mh * ((p.nth + 31) / 32);
   const int nlowblk = x.nlow;   // one warp per float64 mode
-  k_thomas_staged<<<nblk + nlowblk, 32, 0, s>>>(x.radf, p.d_lam, p.d_outer, x.d32, x.cp32, x.pan_hi, x.pan_lo, p.nr,
+  k_thomas_staged<<<nblk + nlowblk, 32, 0, s>>>(x.radf, p.d_lam, p.d_outer, x.d32, x.cp32,
+                                                 Planes{{x.pan[0], x.pan[1], x.pan[2]}, x.np}, p.nr,
                                                  p.nth, p.mh, x.kstride, x.low_threshold, nblk, x.low_idx, x.nlow,
                                                  p.d_rad, x.low_fac, x.low_ws);
   return cudaGetLastError();

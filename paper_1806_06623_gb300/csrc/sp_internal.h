@@ -61,13 +61,12 @@ struct ThetaRowFF {
 
 // Tables and workspace views of the mixed-precision (split-bf16) path.
 struct MixedTables {
+  int np = 2;                      // bf16 planes per operand: 2 (3 products) or 3 (6 products)
   int kstride = 0;                 // K row stride of the bf16 panels (Ntheta rounded up to 8)
   int nlow = 0;                    // radial modes solved in float64 (|lambda| < low_threshold)
   double low_threshold = 30.0;
-  __nv_bfloat16* HtW_hi = nullptr; // [mh][l][kstride]
-  __nv_bfloat16* HtW_lo = nullptr;
-  __nv_bfloat16* H_hi = nullptr;   // [mh][j][kstride]
-  __nv_bfloat16* H_lo = nullptr;
+  __nv_bfloat16* HtW[3] = {};      // planes of (H^T W)_m, [mh][l][kstride]
+  __nv_bfloat16* Hm[3] = {};       // planes of H_m, [mh][j][kstride]
   RadialRowF* radf = nullptr;      // [nr]
   RadialRowFF* radff = nullptr;    // [nr]
   ThetaRowFF* thff = nullptr;      // [nth]
@@ -78,8 +77,7 @@ struct MixedTables {
   float* r32 = nullptr;            // [nr][nth][nphi] residual
   float* phi_hi = nullptr;         // [nr][nth][nphi] iterate as float-float
   float* phi_lo = nullptr;
-  __nv_bfloat16* pan_hi = nullptr; // [mh][2nr][kstride] spectral panel (s_tilde, then f)
-  __nv_bfloat16* pan_lo = nullptr;
+  __nv_bfloat16* pan[3] = {};      // planes of the spectral panel [mh][2nr][kstride] (s_tilde, then f)
   float* d32 = nullptr;            // [mh][2nr][nth] projection output (s_hat, then g)
   float* cp32 = nullptr;           // [mh][nr][nth] float32 Thomas coefficients
   double* low_ws = nullptr;        // [nlow][nr][3] float64 Thomas scratch
@@ -87,8 +85,7 @@ struct MixedTables {
   double* shell_phi = nullptr;     // [nth][nphi] float64 value of the iterate's last shell
   unsigned int* red = nullptr;     // [2] max|e|, max|Phi| (bit patterns of non-negative floats)
   // tensor maps (CUtensorMap, 128 bytes each) for the tcgen05 projections
-  alignas(64) unsigned char map_Ahi_f[128], map_Alo_f[128], map_Ahi_i[128], map_Alo_i[128];
-  alignas(64) unsigned char map_Bhi[128], map_Blo[128];
+  alignas(64) unsigned char map_Af[3][128], map_Ai[3][128], map_B[3][128];
 };
 
 // Kernel identities for the optional per-launch CUDA-event timers.
@@ -195,8 +192,12 @@ void mixed_bind_workspace(Plan& p, char* base);
 int mixed_create_tables(Plan& p, cudaStream_t s);   // after theta_eigen; returns sp_status
 void mixed_free_tables(Plan& p);
 bool mixed_make_panel_maps(Plan& p);
-cudaError_t fft_forward_split(const Plan& p, const void* in, bool in_double, float scale, int kstride,
-                              __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t s);
+struct Planes {
+  __nv_bfloat16* p[3];
+  int n;
+};
+cudaError_t fft_forward_split(const Plan& p, const void* in, bool in_double, float scale, int kstride, Planes out,
+                              cudaStream_t s);
 cudaError_t fft_inverse_update(const Plan& p, const float* spec, float* phi_hi, float* phi_lo, bool first,
                                unsigned int* red, cudaStream_t s);
 cudaError_t finish_mixed(const Plan& p, double* phi, cudaStream_t s);   // float-float iterate -> float64 Phi

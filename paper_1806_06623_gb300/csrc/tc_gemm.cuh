@@ -3,17 +3,19 @@
 // For every azimuthal wavenumber m (Sect. 3.2) the projection is the product
 //   D[m][n][r] = sum_k A[m][r][k] B[m][n][k]      (r < M = Ntheta rows, k < K = Ntheta)
 // with A the (H^T W)_m or H_m table and B the K-contiguous spectral panel of 2 Nr
-// columns n = (i, re/im).  Both operands arrive as bf16 pairs x = hi + lo
-// (hi = RN_bf16(x), lo = RN_bf16(x - hi)) and the product keeps three of the four terms,
-//   A_lo B_hi + A_hi B_lo + A_hi B_hi,
-// accumulated in float32 in tensor memory: relative error ~2^-16 instead of bf16's 2^-8.
+// columns n = (i, re/im).  Both operands arrive as NP bf16 planes x = x0 + x1 (+ x2)
+// (x0 = RN_bf16(x), x1 = RN_bf16(x - x0), x2 = RN_bf16(x - x0 - x1)); the product keeps
+// every plane pair whose index sum is below NP, smallest terms first:
+//   NP = 2: A1 B0 + A0 B1 + A0 B0                              (3 products, ~2^-16)
+//   NP = 3: A2 B0 + A0 B2 + A1 B1 + A1 B0 + A0 B1 + A0 B0      (6 products, ~2^-24)
+// accumulated in float32 in tensor memory.
 //
-// One CTA per (m, 256-column tile), 128 threads:
-//  - thread 0 issues TMA loads of the four operand tiles (128B-swizzled K-major boxes of
-//    64 K-elements) onto one mbarrier, waits, then issues 8 K-steps x 3 tcgen05.mma
-//    (M=128, N=256, K=16, kind::f16, bf16 inputs, f32 accumulator in TMEM) and commits
-//    them to a second mbarrier;
-//  - all four warps then read the 128 x 256 accumulator back with tcgen05.ld (warp w owns
+// One CTA per (m, BN-column tile), 128 threads:
+//  - thread 0 issues TMA loads of the operand planes (128B-swizzled K-major boxes of
+//    64 K-elements) onto one mbarrier, waits, then issues the K-steps x products of
+//    tcgen05.mma (M=128, N=BN, K=16, kind::f16, bf16 inputs, f32 accumulator in TMEM)
+//    and commits them to a second mbarrier;
+//  - all four warps then read the 128 x BN accumulator back with tcgen05.ld (warp w owns
 //    TMEM lanes 32w..32w+31 = output rows) and store float32 rows coalesced along r.
 // Every wait is bounded: on expiry the CTA records kErrTimeout and still frees its TMEM.
 #pragma once
@@ -25,12 +27,18 @@ namespace sp {
 namespace tc {
 
 constexpr int kM = 128;          // UMMA M (rows = l or j)
-constexpr int kN = 256;          // UMMA N (columns of the spectral panel per CTA)
 constexpr int kKBlk = 64;        // K elements per 128-byte swizzle row
 constexpr int kMaxKBlocks = 2;   // K <= 128
-constexpr uint32_t kABlockBytes = kM * 128;   // 16 KB per K block
-constexpr uint32_t kBBlockBytes = kN * 128;   // 32 KB per K block
-constexpr uint32_t kSmemBytes = 2 * kMaxKBlocks * kABlockBytes + 2 * kMaxKBlocks * kBBlockBytes + 1024;
+constexpr uint32_t kABlockBytes = kM * 128;   // 16 KB per K block and plane
+
+template <int NP> struct Cfg;
+template <> struct Cfg<2> { static constexpr int BN = 256; };
+template <> struct Cfg<3> { static constexpr int BN = 128; };
+
+template <int NP>
+constexpr uint32_t smem_bytes() {
+  return NP * kMaxKBlocks * kABlockBytes + NP * kMaxKBlocks * (uint32_t)Cfg<NP>::BN * 128u + 1024u;
+}
 constexpr int kErrTimeout = 4;
 constexpr long long kSpinLimit = 1ll << 26;
 
@@ -40,6 +48,11 @@ struct Params {
   int ncol;       // columns per m
   int kblocks;    // ceil(K / 64)
   int* err;
+};
+
+struct Maps {
+  CUtensorMap a[3];   // A planes
+  CUtensorMap b[3];   // B planes
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -123,19 +136,15 @@ __device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, float (&v)[32
   for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
 }
 
-__global__ void __launch_bounds__(128, 1)
-    k_tc_gemm_bf16x3(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmAlo,
-                     const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo,
-                     Params prm) {
+template <int NP>
+__global__ void __launch_bounds__(128, 1) k_tc_gemm_split(const __grid_constant__ Maps maps, Params prm) {
+  constexpr int BN = Cfg<NP>::BN;
+  constexpr uint32_t kBBlockBytes = BN * 128u;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte alignment of the swizzle atoms
   const uint32_t base_u32 = (smem_u32(smem_raw) + 1023u) & ~1023u;
-  unsigned char* base = smem_raw + (base_u32 - smem_u32(smem_raw));
-  const uint32_t sAhi = base_u32;
-  const uint32_t sAlo = sAhi + kMaxKBlocks * kABlockBytes;
-  const uint32_t sBhi = sAlo + kMaxKBlocks * kABlockBytes;
-  const uint32_t sBlo = sBhi + kMaxKBlocks * kBBlockBytes;
-  (void)base;
+  const uint32_t sA = base_u32;                                  // [NP][kMaxKBlocks] x 16 KB
+  const uint32_t sB = sA + NP * kMaxKBlocks * kABlockBytes;      // [NP][kMaxKBlocks] x BN*128 B
   __shared__ __align__(8) uint64_t bar_load;
   __shared__ __align__(8) uint64_t bar_mma;
   __shared__ uint32_t tmem_base;
@@ -145,12 +154,12 @@ __global__ void __launch_bounds__(128, 1)
   const int warp = tid >> 5;
   const int lane = tid & 31;
   const int m = blockIdx.y;
-  const int n0 = blockIdx.x * kN;
+  const int n0 = blockIdx.x * BN;
   const int kb = prm.kblocks;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                 "r"((uint32_t)kN));
+                 "r"((uint32_t)BN));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
@@ -166,29 +175,33 @@ __global__ void __launch_bounds__(128, 1)
 
   if (tid == 0) {
     const uint32_t bl = smem_u32(&bar_load);
-    mbar_expect_tx(bl, (uint32_t)kb * (2 * kABlockBytes + 2 * kBBlockBytes));
-    for (int b = 0; b < kb; ++b) {
-      tma_load_3d(sAhi + b * kABlockBytes, &tmAhi, b * kKBlk, 0, m, bl);
-      tma_load_3d(sAlo + b * kABlockBytes, &tmAlo, b * kKBlk, 0, m, bl);
-      tma_load_3d(sBhi + b * kBBlockBytes, &tmBhi, b * kKBlk, n0, m, bl);
-      tma_load_3d(sBlo + b * kBBlockBytes, &tmBlo, b * kKBlk, n0, m, bl);
-    }
+    mbar_expect_tx(bl, (uint32_t)kb * NP * (kABlockBytes + kBBlockBytes));
+    for (int pl = 0; pl < NP; ++pl)
+      for (int b = 0; b < kb; ++b) {
+        tma_load_3d(sA + (pl * kMaxKBlocks + b) * kABlockBytes, &maps.a[pl], b * kKBlk, 0, m, bl);
+        tma_load_3d(sB + (pl * kMaxKBlocks + b) * kBBlockBytes, &maps.b[pl], b * kKBlk, n0, m, bl);
+      }
     bool ok = mbar_wait(bl, 0);
     if (ok) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t idesc = idesc_bf16_f32(kM, kN);
+      const uint32_t idesc = idesc_bf16_f32(kM, BN);
+      // plane pairs (a, b) with a + b < NP, smallest first
+      constexpr int npairs = NP == 2 ? 3 : 6;
+      const int pa[6] = {NP == 2 ? 1 : 2, 0, NP == 2 ? 0 : 1, 1, 0, 0};
+      const int pb[6] = {0, NP == 2 ? 1 : 2, NP == 2 ? 0 : 1, 0, 1, 0};
       uint32_t acc = 0;
       for (int kk = 0; kk < kb * (kKBlk / 16); ++kk) {
         const int b = kk / (kKBlk / 16);
         const uint32_t koff = (uint32_t)(kk % (kKBlk / 16)) * 32u;   // 16 bf16 = 32 B along the swizzled row
-        const uint64_t ahi = smem_desc_sw128(sAhi + b * kABlockBytes + koff);
-        const uint64_t alo = smem_desc_sw128(sAlo + b * kABlockBytes + koff);
-        const uint64_t bhi = smem_desc_sw128(sBhi + b * kBBlockBytes + koff);
-        const uint64_t blo = smem_desc_sw128(sBlo + b * kBBlockBytes + koff);
-        umma_bf16(tmem, alo, bhi, idesc, acc);
-        acc = 1;
-        umma_bf16(tmem, ahi, blo, idesc, 1);
-        umma_bf16(tmem, ahi, bhi, idesc, 1);
+#pragma unroll
+        for (int q = 0; q < npairs; ++q) {
+          const int qa = pa[q];
+          const int qb = pb[q];
+          const uint64_t da = smem_desc_sw128(sA + (qa * kMaxKBlocks + b) * kABlockBytes + koff);
+          const uint64_t db = smem_desc_sw128(sB + (qb * kMaxKBlocks + b) * kBBlockBytes + koff);
+          umma_bf16(tmem, da, db, idesc, acc);
+          acc = 1;
+        }
       }
       umma_commit(smem_u32(&bar_mma));
     } else {
@@ -205,7 +218,7 @@ __global__ void __launch_bounds__(128, 1)
       const int row = warp * 32 + lane;
       float* Dm = prm.D + (size_t)m * prm.ncol * prm.M;
 #pragma unroll 1
-      for (int c0 = 0; c0 < kN; c0 += 32) {
+      for (int c0 = 0; c0 < BN; c0 += 32) {
         float v[32];
         tmem_ld_32x32b_x32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
         if (row < prm.M) {
@@ -224,7 +237,7 @@ __global__ void __launch_bounds__(128, 1)
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)kN));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN));
   }
 }
 

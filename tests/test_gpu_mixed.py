@@ -24,8 +24,9 @@ def S():
     return S
 
 
-def mixed_solve(S, p, tol=TOL, max_iter=8):
-    plan = S.Plan(p.r_if, p.th_if, p.nphi, outer_bc=p.outer_bc, G=p.G, precision=S.SP_MIXED_BF16X3,
+def mixed_solve(S, p, tol=TOL, max_iter=8, precision=None):
+    precision = S.SP_MIXED_BF16X3 if precision is None else precision
+    plan = S.Plan(p.r_if, p.th_if, p.nphi, outer_bc=p.outer_bc, G=p.G, precision=precision,
                   tol=tol, max_iter=max_iter)
     rho = torch.from_numpy(np.ascontiguousarray(p.rho)).cuda()
     phi, info = plan.solve(rho)
@@ -52,20 +53,27 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("mode", ["x3", "x6"])
 @pytest.mark.parametrize("nr,nth,nphi,grid,rin,bc", CASES)
-def test_mixed_matches_exact_small(S, nr, nth, nphi, grid, rin, bc):
+def test_mixed_matches_exact_small(S, nr, nth, nphi, grid, rin, bc, mode):
     p = W.random_small(nr, nth, nphi, seed=nr + 3 * nth + nphi, grid=grid, r_inner=rin, outer_bc=bc)
-    _, phi, info = mixed_solve(S, p)
+    prec = S.SP_MIXED_BF16X3 if mode == "x3" else S.SP_MIXED_BF16X6
+    _, phi, info = mixed_solve(S, p, precision=prec)
     ref = O.solve_exact(O.Geometry(p.r_if, p.th_if, p.nphi), p.rho, outer_bc=bc)
     assert info.status == S.SP_OK
     assert rel_err(phi, ref) <= TOL
     assert info.est_rel_error <= TOL and info.iterations >= 2
+    # the estimate bounds the actual error
+    assert rel_err(phi, ref) <= max(info.est_rel_error, 1e-12)
 
 
-@pytest.mark.parametrize("make", [W.sphere_blob, W.stellar_noise])
-def test_mixed_matches_exact_workloads(S, make):
+@pytest.mark.parametrize("mode", ["x3", "x6"])
+@pytest.mark.parametrize("make", [W.sphere_blob, W.stellar_noise, lambda: W.ragged_instance(0),
+                                  lambda: W.ragged_instance(5)])
+def test_mixed_matches_exact_workloads(S, make, mode):
     p = make()
-    _, phi, info = mixed_solve(S, p)
+    prec = S.SP_MIXED_BF16X3 if mode == "x3" else S.SP_MIXED_BF16X6
+    _, phi, info = mixed_solve(S, p, precision=prec)
     geo = O.Geometry(p.r_if, p.th_if, p.nphi)
     ref = O.solve_exact(geo, p.rho)
     assert rel_err(phi, ref) <= TOL
@@ -73,10 +81,12 @@ def test_mixed_matches_exact_workloads(S, make):
     assert eta <= 1e-12
 
 
-def test_mixed_full_size_stellar_sh(S):
+@pytest.mark.parametrize("mode", ["x3", "x6"])
+def test_mixed_full_size_stellar_sh(S, mode):
     """The 550x128x256 headline workload."""
     p = W.stellar_sh()
-    _, phi, info = mixed_solve(S, p)
+    prec = S.SP_MIXED_BF16X3 if mode == "x3" else S.SP_MIXED_BF16X6
+    _, phi, info = mixed_solve(S, p, precision=prec)
     geo = O.Geometry(p.r_if, p.th_if, p.nphi)
     ref = O.solve_exact(geo, p.rho)
     err = rel_err(phi, ref)
