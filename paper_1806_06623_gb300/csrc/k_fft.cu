@@ -173,11 +173,25 @@ __global__ void __launch_bounds__(256) k_fft_fwd(const Tin* __restrict__ in, int
     const Tin* a = in + (size_t)(line0 + 2 * p) * n;
     const bool hasb = 2 * p + 1 < nl;
     CT* z = bufA + p * PS;
-    for (int q = lane; q < n; q += 32) {
-      CT v;
-      v.x = load_in<T>(a + q);
-      v.y = hasb ? load_in<T>(a + n + q) : T(0);
-      z[q] = v;
+    // four segments in flight per lane before any is stored
+    for (int q0 = lane; q0 < n; q0 += 128) {
+      T va[4], vb[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int q = q0 + 32 * u;
+        va[u] = (q < n) ? load_in<T>(a + q) : T(0);
+        vb[u] = (q < n && hasb) ? load_in<T>(a + n + q) : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int q = q0 + 32 * u;
+        if (q < n) {
+          CT v;
+          v.x = va[u];
+          v.y = vb[u];
+          z[q] = v;
+        }
+      }
     }
   }
   __syncthreads();
@@ -247,27 +261,37 @@ __global__ void __launch_bounds__(256) k_fft_inv(const T* __restrict__ spec, int
       i = g / nth;
       j = g - i * nth;
     }
-    // Z[m] = G_A[m] + i G_B[m] (even lane writes), Z[n-m] = conj G_A[m] + i conj G_B[m] (odd lane)
-    for (int m = warp; m < mh; m += kWarps) {
-      CT v;
-      v.x = T(0);
-      v.y = T(0);
-      if (l < nl) {
-        const T* s = spec + ((size_t)(m * nrs + i) * 2) * nth + j;
-        v.x = s[0];
-        v.y = (m == 0 || 2 * m == n) ? T(0) : s[nth];
+    // Z[m] = G_A[m] + i G_B[m] (even lane writes), Z[n-m] = conj G_A[m] + i conj G_B[m] (odd lane);
+    // four m-rows are loaded before any is consumed
+    for (int m0 = warp; m0 < mh; m0 += 4 * kWarps) {
+      CT vv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int m = m0 + u * kWarps;
+        vv[u].x = T(0);
+        vv[u].y = T(0);
+        if (l < nl && m < mh) {
+          const T* s = spec + ((size_t)(m * nrs + i) * 2) * nth + j;
+          vv[u].x = s[0];
+          vv[u].y = (m == 0 || 2 * m == n) ? T(0) : s[nth];
+        }
       }
-      CT o;
-      o.x = __shfl_xor_sync(0xffffffffu, v.x, 1);
-      o.y = __shfl_xor_sync(0xffffffffu, v.y, 1);
-      if ((l >> 1) < npairs) {
-        CT* z = bufA + (l >> 1) * PS;
-        if (!(l & 1)) {
-          CT zm; zm.x = v.x - o.y; zm.y = v.y + o.x;   // A = v, B = o
-          z[m] = zm;
-        } else if (m != 0 && 2 * m != n) {
-          CT zn; zn.x = o.x + v.y; zn.y = v.x - o.y;   // A = o, B = v
-          z[n - m] = zn;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int m = m0 + u * kWarps;
+        const CT v = vv[u];
+        CT o;
+        o.x = __shfl_xor_sync(0xffffffffu, v.x, 1);
+        o.y = __shfl_xor_sync(0xffffffffu, v.y, 1);
+        if (m < mh && (l >> 1) < npairs) {
+          CT* z = bufA + (l >> 1) * PS;
+          if (!(l & 1)) {
+            CT zm; zm.x = v.x - o.y; zm.y = v.y + o.x;   // A = v, B = o
+            z[m] = zm;
+          } else if (m != 0 && 2 * m != n) {
+            CT zn; zn.x = o.x + v.y; zn.y = v.x - o.y;   // A = o, B = v
+            z[n - m] = zn;
+          }
         }
       }
     }
@@ -279,27 +303,47 @@ __global__ void __launch_bounds__(256) k_fft_inv(const T* __restrict__ spec, int
     const CT* z = Z + p * PS;
     const bool hasb = 2 * p + 1 < nl;
     const size_t o0 = (size_t)(line0 + 2 * p) * n;
-    for (int q = lane; q < n; q += 32) {
-      const CT v = z[q];
-      if (MODE == kInvWrite) {
-        out[o0 + q] = (Tout)v.x;
-        if (hasb) out[o0 + n + q] = (Tout)v.y;
-      } else if (MODE == kInvAccumulate) {
-        out[o0 + q] += (Tout)v.x;
-        if (hasb) out[o0 + n + q] += (Tout)v.y;
-      } else {
+    if (MODE != kInvPairUpdate) {
+      for (int q = lane; q < n; q += 32) {
+        const CT v = z[q];
+        if (MODE == kInvWrite) {
+          out[o0 + q] = (Tout)v.x;
+          if (hasb) out[o0 + n + q] = (Tout)v.y;
+        } else {
+          out[o0 + q] += (Tout)v.x;
+          if (hasb) out[o0 + n + q] += (Tout)v.y;
+        }
+      }
+    } else {
+      // two lines x four segments of the iterate in flight per lane
+      for (int q0 = lane; q0 < n; q0 += 128) {
+        float oh[2][4], ol[2][4];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          if (h == 1 && !hasb) break;
-          const size_t o = o0 + (size_t)h * n + q;
-          const float e = (float)(h ? v.y : v.x);
-          ff nv;
-          if (first) nv = ff{e, 0.f};
-          else nv = ff_add_f(ff{(float)out[o], phi_lo[o]}, e);
-          out[o] = (Tout)nv.hi;
-          phi_lo[o] = nv.lo;
-          me = fmaxf(me, fabsf(e));
-          mp = fmaxf(mp, fabsf(nv.hi));
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int q = q0 + 32 * u;
+            const size_t o = o0 + (size_t)h * n + q;
+            const bool ok = q < n && (h == 0 || hasb) && !first;
+            oh[h][u] = ok ? (float)out[o] : 0.f;
+            ol[h][u] = ok ? phi_lo[o] : 0.f;
+          }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int q = q0 + 32 * u;
+          if (q >= n) continue;
+          const CT v = z[q];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            if (h == 1 && !hasb) continue;
+            const size_t o = o0 + (size_t)h * n + q;
+            const float e = (float)(h ? v.y : v.x);
+            const ff nv = first ? ff{e, 0.f} : ff_add_f(ff{oh[h][u], ol[h][u]}, e);
+            out[o] = (Tout)nv.hi;
+            phi_lo[o] = nv.lo;
+            me = fmaxf(me, fabsf(e));
+            mp = fmaxf(mp, fabsf(nv.hi));
+          }
         }
       }
     }

@@ -55,30 +55,33 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 constexpr int kTR = 16;       // radial rows per staged chunk
-constexpr int kStages = 4;    // chunks in flight per warp
+constexpr int kStages = 6;    // chunks in flight per warp
 
-// Radial solves of the low-precision solve, one warp per (m, 32 consecutive l).  Rows
-// of the mode array are staged through a kStages-deep ring of cp.async copies (each lane
-// copies its own elements) so the sequential elimination reads shared memory while
-// later rows stream in.  float32 elimination; lanes whose mode is near-singular
-// (|lambda| < thr) idle here and are solved in float64 by the trailing blocks.
-// d32 holds s_hat[m][i][c][l] on entry and the forward-elimination values afterwards;
-// cp32 receives the elimination coefficients; f leaves as bf16 hi/lo panel rows.
-__global__ void __launch_bounds__(32) k_thomas_staged(const RadialRowF* __restrict__ rad, const double* __restrict__ lam,
-                                                      const double* __restrict__ outer, float* __restrict__ x,
-                                                      float* __restrict__ cp, Planes pl, int nr, int nth, int mh,
+// Radial solves of the low-precision solve.  The elimination factors c'_i and 1/pivot_i
+// of every (m,l) system depend on the plan only and are precomputed (float64, rounded
+// to float32), so the sweeps carry no division: forward d_i = (x_i - sub_i d_{i-1})/piv_i,
+// backward f_i = d_i - c'_i f_{i+1}.  One warp per (m, c = re/im, 32 consecutive l);
+// rows of the mode array and of the factor tables stream through a kStages-deep ring
+// of cp.async copies (each lane copies its own elements) so each sweep reads shared
+// memory while later rows are in flight.  Lanes of near-singular modes (|lambda| < thr)
+// idle here; the trailing blocks solve those in float64, one mode per warp.
+// x holds s_hat[m][i][c][l] on entry and the forward values afterwards; f leaves as bf16
+// planes in the panel layout.
+__global__ void __launch_bounds__(32) k_thomas_staged(const float* __restrict__ sub_r, const double* __restrict__ lam,
+                                                      float* __restrict__ x, const float* __restrict__ fcp,
+                                                      const float* __restrict__ finv, Planes pl, int nr, int nth,
                                                       int kstride, double thr, int nblk_f32,
                                                       const int* __restrict__ low_idx, int nlow,
                                                       const RadialRow* __restrict__ rad64,
                                                       const double2* __restrict__ low_fac, double* __restrict__ low_ws) {
-  __shared__ float sx[kStages][kTR][3][32];
+  __shared__ float sx[kStages][kTR][2][32];
   const int lane = threadIdx.x;
   const size_t st = 2 * (size_t)nth;
   const int nchunk = (nr + kTR - 1) / kTR;
   if ((int)blockIdx.x >= nblk_f32) {
     // ---- float64 near-singular mode, one per warp: the column and its precomputed
     // elimination factors are loaded in parallel, lane 0 runs both sweeps out of shared
-    // memory (low_ws holds the column as doubles), all lanes write the result.
+    // memory (or low_ws when the column does not fit), all lanes write the result.
     const int q = (int)blockIdx.x - nblk_f32;
     if (q >= nlow) return;
     const int t = low_idx[q];
@@ -86,7 +89,6 @@ __global__ void __launch_bounds__(32) k_thomas_staged(const RadialRowF* __restri
     const int l = t - m * nth;
     const float* X = x + (size_t)m * nr * st + l;
     const double2* F = low_fac + (size_t)q * nr;     // (c'_i, 1/pivot_i)
-    // [i][re, im, c'] in the (otherwise unused) staging buffer when it fits
     double* W = (3 * nr <= (int)(sizeof(sx) / sizeof(double))) ? reinterpret_cast<double*>(&sx[0][0][0][0])
                                                                  : low_ws + (size_t)q * nr * 3;
     for (int i = lane; i < nr; i += 32) {
@@ -123,52 +125,46 @@ __global__ void __launch_bounds__(32) k_thomas_staged(const RadialRowF* __restri
     }
     return;
   }
-  // ---- float32 modes
+  // ---- float32 modes: block = (m, lb, c)
   const int nlb = (nth + 31) / 32;
-  const int m = blockIdx.x / nlb;
-  const int l = (blockIdx.x - m * nlb) * 32 + lane;
+  const int c = blockIdx.x & 1;
+  const int mb = blockIdx.x >> 1;
+  const int m = mb / nlb;
+  const int l = (mb - m * nlb) * 32 + lane;
   const bool valid = l < nth;
-  const int t = m * nth + l;
-  const bool work = valid && fabs(lam[t]) >= thr;
-  const float L = valid ? (float)lam[t] : 0.f;
-  const float od = valid ? (float)outer[t] : 0.f;
-  float* X = x + (size_t)m * nr * st + (valid ? l : 0);
-  float* CP = cp + (size_t)m * nr * nth + (valid ? l : 0);
+  const bool work = valid && fabs(lam[m * nth + l]) >= thr;
+  float* X = x + (size_t)m * nr * st + (size_t)c * nth + (valid ? l : 0);
+  const float* FC = fcp + (size_t)m * nr * nth + (valid ? l : 0);
+  const float* FI = finv + (size_t)m * nr * nth + (valid ? l : 0);
 
-  auto fetch_fwd = [&](int ch) {
-    if (ch < nchunk && valid) {
+  auto fetch = [&](int k, bool fwd) {   // k-th chunk in sweep order into ring slot k % kStages
+    const int ch = fwd ? k : nchunk - 1 - k;
+    if (ch >= 0 && ch < nchunk && work) {
       const int i0 = ch * kTR;
       const int n = min(kTR, nr - i0);
-      float(*b)[3][32] = sx[ch % kStages];
+      float(*b)[2][32] = sx[k % kStages];
       for (int r = 0; r < n; ++r) {
         cp_async4(&b[r][0][lane], X + (size_t)(i0 + r) * st);
-        cp_async4(&b[r][1][lane], X + (size_t)(i0 + r) * st + nth);
+        cp_async4(&b[r][1][lane], (fwd ? FI : FC) + (size_t)(i0 + r) * nth);
       }
     }
     cp_async_commit();
   };
-  for (int ch = 0; ch < kStages - 1; ++ch) fetch_fwd(ch);
-  float cprev = 0.f, dre = 0.f, dim = 0.f;
-  for (int ch = 0; ch < nchunk; ++ch) {
-    fetch_fwd(ch + kStages - 1);
+  // forward sweep
+  for (int k = 0; k < kStages - 1; ++k) fetch(k, true);
+  float d = 0.f;
+  for (int k = 0; k < nchunk; ++k) {
+    fetch(k + kStages - 1, true);
     cp_async_wait<kStages - 1>();
     __syncwarp();
-    const int i0 = ch * kTR;
-    const int n = min(kTR, nr - i0);
-    float(*b)[3][32] = sx[ch % kStages];
     if (work) {
+      const int i0 = k * kTR;
+      const int n = min(kTR, nr - i0);
+      float(*b)[2][32] = sx[k % kStages];
       for (int r = 0; r < n; ++r) {
         const int i = i0 + r;
-        const RadialRowF rr = rad[i];
-        float bb = fmaf(rr.R, L, rr.base);
-        if (i == nr - 1) bb += od;
-        const float inv = 1.0f / (bb - rr.sub * cprev);
-        cprev = rr.sup * inv;
-        dre = (b[r][0][lane] - rr.sub * dre) * inv;
-        dim = (b[r][1][lane] - rr.sub * dim) * inv;
-        X[(size_t)i * st] = dre;
-        X[(size_t)i * st + nth] = dim;
-        CP[(size_t)i * nth] = cprev;
+        d = fmaf(-sub_r[i], d, b[r][0][lane]) * b[r][1][lane];
+        X[(size_t)i * st] = d;
       }
     }
     __syncwarp();
@@ -177,50 +173,49 @@ __global__ void __launch_bounds__(32) k_thomas_staged(const RadialRowF* __restri
   __threadfence_block();
   __syncwarp();
   // back substitution, chunks in reverse; each lane re-reads only its own elements
-  const size_t prow = (size_t)m * nr * 2;
-  auto fetch_bwd = [&](int k) {   // k-th chunk from the top
-    const int ch = nchunk - 1 - k;
-    if (ch >= 0 && work) {
-      const int i0 = ch * kTR;
-      const int n = min(kTR, nr - i0);
-      float(*b)[3][32] = sx[k % kStages];
-      for (int r = 0; r < n; ++r) {
-        cp_async4(&b[r][0][lane], X + (size_t)(i0 + r) * st);
-        cp_async4(&b[r][1][lane], X + (size_t)(i0 + r) * st + nth);
-        cp_async4(&b[r][2][lane], CP + (size_t)(i0 + r) * nth);
-      }
-    }
-    cp_async_commit();
-  };
-  for (int k = 0; k < kStages - 1; ++k) fetch_bwd(k);
-  bool first = true;
+  const size_t prow = (size_t)m * nr * 2 + c;
+  for (int k = 0; k < kStages - 1; ++k) fetch(k, false);
+  float f = 0.f;
   for (int k = 0; k < nchunk; ++k) {
-    fetch_bwd(k + kStages - 1);
+    fetch(k + kStages - 1, false);
     cp_async_wait<kStages - 1>();
     __syncwarp();
-    const int ch = nchunk - 1 - k;
-    const int i0 = ch * kTR;
-    const int n = min(kTR, nr - i0);
-    float(*b)[3][32] = sx[k % kStages];
     if (work) {
+      const int ch = nchunk - 1 - k;
+      const int i0 = ch * kTR;
+      const int n = min(kTR, nr - i0);
+      float(*b)[2][32] = sx[k % kStages];
       for (int r = n - 1; r >= 0; --r) {
         const int i = i0 + r;
-        if (first) {
-          dre = b[r][0][lane];
-          dim = b[r][1][lane];
-          first = false;
-        } else {
-          const float c = b[r][2][lane];
-          dre = b[r][0][lane] - c * dre;
-          dim = b[r][1][lane] - c * dim;
-        }
-        store_split(pl, (prow + 2 * i) * kstride + l, dre);
-        store_split(pl, (prow + 2 * i + 1) * kstride + l, dim);
+        f = (i == nr - 1) ? b[r][0][lane] : fmaf(-b[r][1][lane], f, b[r][0][lane]);
+        store_split(pl, (prow + 2 * i) * kstride + l, f);
       }
     }
     __syncwarp();
   }
   cp_async_wait<0>();
+}
+
+// float32 elimination factors of every (m,l) radial system, computed in float64.
+__global__ void k_radial_factors(const RadialRow* __restrict__ rad, const double* __restrict__ lam,
+                                 const double* __restrict__ outer, int nr, int nth, int mh, float* __restrict__ fcp,
+                                 float* __restrict__ finv) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= mh * nth) return;
+  const int m = t / nth;
+  const int l = t - m * nth;
+  const double L = lam[t];
+  double cprev = 0.0;
+  for (int i = 0; i < nr; ++i) {
+    const RadialRow rr = rad[i];
+    double b = fma(rr.R, L, rr.base);
+    if (i == nr - 1) b += outer[t];
+    const double inv = 1.0 / (b - rr.sub * cprev);
+    cprev = rr.sup * inv;
+    const size_t o = ((size_t)m * nr + i) * nth + l;
+    fcp[o] = (float)cprev;
+    finv[o] = (float)inv;
+  }
 }
 
 // Elimination factors (c'_i, 1/pivot_i) of the float64 near-singular modes (set-up).
@@ -242,45 +237,101 @@ __global__ void k_low_factors(const RadialRow* __restrict__ rad, const double* _
   }
 }
 
+// Unnormalised float-float helpers for the residual: a value is (h, l) with |l| small
+// against |h| but not necessarily below half an ulp; one renormalisation at the end.
+__device__ __forceinline__ void ffd_diff(float bh, float bl, float ch, float cl, float& dh, float& dl) {
+  float e;
+  two_sum(bh, -ch, dh, e);
+  dl = e + (bl - cl);
+}
+__device__ __forceinline__ void ffd_mul(ff k, float dh, float dl, float& p, float& e) {
+  p = __fmul_rn(k.hi, dh);
+  e = fmaf(k.hi, dh, -p);
+  e = fmaf(k.hi, dl, e);
+  e = fmaf(k.lo, dh, e);
+}
+__device__ __forceinline__ void ffd_acc(float& ah, float& al, float ph, float pe) {
+  float s, e;
+  two_sum(ah, ph, s, e);
+  ah = s;
+  al += e + pe;
+}
+
 // r = 4 pi G rho - (L Phi) for the float-float iterate Phi = hi + lo, evaluated in
 // float-float arithmetic in difference form (every neighbour difference Phi_nb - Phi_c
 // is formed first, so products carry errors relative to the small differences, not to
 // |L||Phi|), stored as float32.  rho is split into a float pair with integer
 // operations; the multipole term of the last shell arrives precomputed in outer_shell
-// (float64, already scaled by 3 r_out^2/dV3_N).
+// (float64, already scaled by 3 r_out^2/dV3_N).  One CTA per (j, i) phi line.
 __global__ void __launch_bounds__(256) k_residual_ff(const double* __restrict__ rho, const float* __restrict__ ph,
                                                      const float* __restrict__ pl,
                                                      const double* __restrict__ outer_shell, float* __restrict__ r,
                                                      const RadialRowFF* __restrict__ rad,
                                                      const ThetaRowFF* __restrict__ th, int nr, int nth, int nphi,
                                                      int dirichlet, ff dir_coef, ff four_pi_g) {
-  // one CTA per (j, i) phi line: no index division in the inner loop
   const int j = blockIdx.x;
   const int i = blockIdx.y;
   const size_t shell = (size_t)nth * nphi;
   const size_t line = ((size_t)i * nth + j) * nphi;
   const RadialRowFF rr = rad[i];
   const ThetaRowFF tr = th[j];
+  const bool has_im = i > 0, has_ip = i < nr - 1, has_jm = j > 0, has_jp = j < nth - 1;
   for (int k = threadIdx.x; k < nphi; k += blockDim.x) {
     const size_t idx = line + k;
-    const ff c{ph[idx], pl[idx]};
-    ff acc{0.f, 0.f};
-    if (i > 0) acc = ff_mul(rr.sub, ff_sub(ff{ph[idx - shell], pl[idx - shell]}, c));
-    if (i < nr - 1) acc = ff_add(acc, ff_mul(rr.sup, ff_sub(ff{ph[idx + shell], pl[idx + shell]}, c)));
-    ff a{0.f, 0.f};
-    if (j > 0) a = ff_mul(tr.tm, ff_sub(ff{ph[idx - nphi], pl[idx - nphi]}, c));
-    if (j < nth - 1) a = ff_add(a, ff_mul(tr.tp, ff_sub(ff{ph[idx + nphi], pl[idx + nphi]}, c)));
+    const float ch = ph[idx], cl = pl[idx];
+    float dh, dl, p, e;
+    // radial fluxes
+    float rh = 0.f, rl = 0.f;
+    if (has_im) {
+      ffd_diff(ph[idx - shell], pl[idx - shell], ch, cl, dh, dl);
+      ffd_mul(rr.sub, dh, dl, p, e);
+      rh = p;
+      rl = e;
+    }
+    if (has_ip) {
+      ffd_diff(ph[idx + shell], pl[idx + shell], ch, cl, dh, dl);
+      ffd_mul(rr.sup, dh, dl, p, e);
+      ffd_acc(rh, rl, p, e);
+    }
+    // angular fluxes, scaled by R_i
+    float ah = 0.f, al = 0.f;
+    if (has_jm) {
+      ffd_diff(ph[idx - nphi], pl[idx - nphi], ch, cl, dh, dl);
+      ffd_mul(tr.tm, dh, dl, p, e);
+      ah = p;
+      al = e;
+    }
+    if (has_jp) {
+      ffd_diff(ph[idx + nphi], pl[idx + nphi], ch, cl, dh, dl);
+      ffd_mul(tr.tp, dh, dl, p, e);
+      ffd_acc(ah, al, p, e);
+    }
     const size_t kp = (k + 1 == nphi) ? idx - k : idx + 1;
     const size_t km = (k == 0) ? idx + (nphi - 1) : idx - 1;
-    const ff dphi = ff_add(ff_sub(ff{ph[kp], pl[kp]}, c), ff_sub(ff{ph[km], pl[km]}, c));
-    a = ff_add(a, ff_mul(tr.sphi, dphi));
-    acc = ff_add(acc, ff_mul(rr.R, a));
+    float qh, ql;
+    ffd_diff(ph[kp], pl[kp], ch, cl, qh, ql);
+    ffd_diff(ph[km], pl[km], ch, cl, dh, dl);
+    ffd_acc(qh, ql, dh, dl);
+    ffd_mul(tr.sphi, qh, ql, p, e);
+    ffd_acc(ah, al, p, e);
+    ff a;
+    fast_two_sum(ah, al, a.hi, a.lo);
+    ffd_mul(rr.R, a.hi, a.lo, p, e);
+    ffd_acc(rh, rl, p, e);
     if (i == nr - 1) {
-      if (dirichlet) acc = ff_add(acc, ff_mul(dir_coef, c));
-      else acc = ff_add(acc, d2ff(outer_shell[idx - (size_t)i * shell]));
+      if (dirichlet) {
+        ffd_mul(dir_coef, ch, cl, p, e);
+        ffd_acc(rh, rl, p, e);
+      } else {
+        const ff o = d2ff(outer_shell[idx - (size_t)i * shell]);
+        ffd_acc(rh, rl, o.hi, o.lo);
+      }
     }
-    const ff res = ff_sub(ff_mul(four_pi_g, d2ff(rho[idx])), acc);
-    r[idx] = res.hi + res.lo;
+    const ff sv = ff_mul(four_pi_g, d2ff(rho[idx]));
+    float th_, tl;
+    two_sum(sv.hi, -rh, th_, tl);
+    tl += sv.lo - rl;
+    r[idx] = th_ + tl;
   }
 }
 
@@ -298,7 +349,7 @@ size_t mixed_workspace_bytes(const Plan& p) {
   const size_t zones = (size_t)p.nr * p.nth * p.nphi;
   const size_t rows = (size_t)p.mh * 2 * p.nr;
   return 3 * al256(zones * 4) + x.np * al256(rows * x.kstride * 2) + al256(rows * p.nth * 4) +
-         al256((size_t)p.mh * p.nr * p.nth * 4) + al256((size_t)(x.nlow ? x.nlow : 1) * p.nr * 3 * 8) +
+         al256((size_t)(x.nlow ? x.nlow : 1) * p.nr * 3 * 8) +
          2 * al256((size_t)p.nth * p.nphi * 8) + 2 * al256((size_t)p.mh * 2 * p.nth * 8) + 256;
 }
 
@@ -321,8 +372,6 @@ void mixed_bind_workspace(Plan& p, char* c) {
   }
   x.d32 = reinterpret_cast<float*>(c);
   c += al256(rows * p.nth * 4);
-  x.cp32 = reinterpret_cast<float*>(c);
-  c += al256((size_t)p.mh * p.nr * p.nth * 4);
   x.low_ws = reinterpret_cast<double*>(c);
   c += al256((size_t)(x.nlow ? x.nlow : 1) * p.nr * 3 * 8);
   x.outer_shell = reinterpret_cast<double*>(c);
@@ -358,6 +407,11 @@ int mixed_create_tables(Plan& p, cudaStream_t s) {
     if (cudaMalloc(&x->HtW[q], tab * 2) != cudaSuccess || cudaMalloc(&x->Hm[q], tab * 2) != cudaSuccess)
       return SP_ERR_OOM;
   if (cudaMalloc(&x->radf, sizeof(RadialRowF) * p.nr) != cudaSuccess) return SP_ERR_OOM;
+  const size_t fac = (size_t)mh * p.nr * nth;
+  if (cudaMalloc(&x->fcp, sizeof(float) * fac) != cudaSuccess || cudaMalloc(&x->finv, sizeof(float) * fac) != cudaSuccess ||
+      cudaMalloc(&x->sub_r, sizeof(float) * p.nr) != cudaSuccess)
+    return SP_ERR_OOM;
+  k_radial_factors<<<(mh * nth + 127) / 128, 128, 0, s>>>(p.d_rad, p.d_lam, p.d_outer, p.nr, nth, mh, x->fcp, x->finv);
   k_split_table<<<1024, 256, 0, s>>>(p.d_HtW, nth, x->kstride, tab, Planes{{x->HtW[0], x->HtW[1], x->HtW[2]}, x->np});
   k_split_table<<<1024, 256, 0, s>>>(p.d_H, nth, x->kstride, tab, Planes{{x->Hm[0], x->Hm[1], x->Hm[2]}, x->np});
   if (cudaGetLastError() != cudaSuccess) return SP_ERR_CUDA;
@@ -391,6 +445,9 @@ int mixed_create_tables(Plan& p, cudaStream_t s) {
   x->nlow = (int)low.size();
   if (cudaMalloc(&x->low_idx, sizeof(int) * (low.empty() ? 1 : low.size())) != cudaSuccess) return SP_ERR_OOM;
   if (cudaMemcpy(x->radf, rf.data(), sizeof(RadialRowF) * p.nr, cudaMemcpyHostToDevice) != cudaSuccess) return SP_ERR_CUDA;
+  std::vector<float> subr(p.nr);
+  for (int i = 0; i < p.nr; ++i) subr[i] = (float)rad[i].sub;
+  if (cudaMemcpy(x->sub_r, subr.data(), sizeof(float) * p.nr, cudaMemcpyHostToDevice) != cudaSuccess) return SP_ERR_CUDA;
   if (!low.empty() &&
       cudaMemcpy(x->low_idx, low.data(), sizeof(int) * low.size(), cudaMemcpyHostToDevice) != cudaSuccess)
     return SP_ERR_CUDA;
@@ -415,6 +472,9 @@ void mixed_free_tables(Plan& p) {
     cudaFree(x->Hm[q]);
   }
   cudaFree(x->radf);
+  cudaFree(x->fcp);
+  cudaFree(x->finv);
+  cudaFree(x->sub_r);
   cudaFree(x->low_idx);
   cudaFree(x->low_fac);
   cudaFree(x->radff);
@@ -446,12 +506,12 @@ cudaError_t tc_project(const Plan& p, bool inverse, cudaStream_t s) {
 
 cudaError_t thomas_mixed(const Plan& p, cudaStream_t s) {
   const MixedTables& x = *p.mixed;
-  const int nblk = p.mh * ((p.nth + 31) / 32);
+  const int nblk = 2 * p.mh * ((p.nth + 31) / 32);
   const int nlowblk = x.nlow;   // one warp per float64 mode
-  k_thomas_staged<<<nblk + nlowblk, 32, 0, s>>>(x.radf, p.d_lam, p.d_outer, x.d32, x.cp32,
-                                                 Planes{{x.pan[0], x.pan[1], x.pan[2]}, x.np}, p.nr,
-                                                 p.nth, p.mh, x.kstride, x.low_threshold, nblk, x.low_idx, x.nlow,
-                                                 p.d_rad, x.low_fac, x.low_ws);
+  k_thomas_staged<<<nblk + nlowblk, 32, 0, s>>>(x.sub_r, p.d_lam, x.d32, x.fcp, x.finv,
+                                                 Planes{{x.pan[0], x.pan[1], x.pan[2]}, x.np}, p.nr, p.nth,
+                                                 x.kstride, x.low_threshold, nblk, x.low_idx, x.nlow, p.d_rad,
+                                                 x.low_fac, x.low_ws);
   return cudaGetLastError();
 }
 

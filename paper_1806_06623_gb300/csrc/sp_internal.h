@@ -79,7 +79,9 @@ struct MixedTables {
   float* phi_lo = nullptr;
   __nv_bfloat16* pan[3] = {};      // planes of the spectral panel [mh][2nr][kstride] (s_tilde, then f)
   float* d32 = nullptr;            // [mh][2nr][nth] projection output (s_hat, then g)
-  float* cp32 = nullptr;           // [mh][nr][nth] float32 Thomas coefficients
+  float* fcp = nullptr;            // [mh][nr][nth] radial elimination factors c'_i (plan tables)
+  float* finv = nullptr;           // [mh][nr][nth] 1/pivot_i
+  float* sub_r = nullptr;          // [nr] sub-diagonal of the radial rows
   double* low_ws = nullptr;        // [nlow][nr][3] float64 Thomas scratch
   double* outer_shell = nullptr;   // [nth][nphi] multipole outer term of the residual
   double* shell_phi = nullptr;     // [nth][nphi] float64 value of the iterate's last shell
