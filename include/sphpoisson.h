@@ -100,6 +100,13 @@ int sp_plan_create(const double* r_interfaces, int Nr,
                    int Nphi, int outer_bc, double G, int precision,
                    double tol, int max_iter, void* stream, sp_plan** out);
 
+/* A second plan for the same problem that shares the source plan's read-only tables
+ * (geometry, theta eigenbasis, radial elimination factors) and has its own workspace,
+ * so solves on the source and on its clones may run concurrently (for instance on
+ * different streams or host threads).  The tables live until the last of the plans
+ * sharing them is destroyed.  No counterpart in the paper. */
+int sp_plan_clone(const sp_plan* src, sp_plan** out);
+
 /* Bytes of device workspace sp_solve and sp_apply_laplacian need. */
 size_t sp_plan_workspace_bytes(const sp_plan* plan);
 
@@ -123,6 +130,17 @@ int sp_solve(sp_plan* plan, const double* rho_dev, double* phi_dev, void* stream
  * for rho and Phi (allocated on first use, freed with the plan). */
 int sp_solve_host(sp_plan* plan, const double* rho_host, double* phi_host, void* stream,
                   sp_solve_info* info);
+
+/* n independent solves (Sect. 3.2 for each), any mix of grids and precisions, as one
+ * call: instance q solves plans[q] with rho[q] -> phi[q] (device buffers as for
+ * sp_solve).  The plans must be distinct (use sp_plan_clone for several problems on one
+ * grid).  Work runs on internal streams forked from `stream` and joined back into it;
+ * mixed-precision instances refine in lock-step rounds with one host wait per round
+ * for the whole batch, so this call synchronises when any plan is mixed.
+ *  infos  host array of n entries or NULL.
+ * Returns the first failing instance's status (each infos[q].status is set). */
+int sp_solve_batched(sp_plan* const* plans, const double* const* rho_dev, double* const* phi_dev, int n,
+                     void* stream, sp_solve_info* infos);
 
 /* out = (Delta Phi)_{ijk}, the finite-volume operator of Eq. (fin_vol0)-(fin_vol3)
  * with the plan's boundary conditions, in float64 (not divided by 4 pi G).
@@ -170,6 +188,38 @@ int sp_plan_get_timing(const sp_plan* plan, double* ms, long long* count, int n)
 
 /* Number of kernel launches this plan has issued since creation (host counter). */
 long long sp_plan_launch_count(const sp_plan* plan);
+
+/* ---- continuous-batching solve server (no counterpart in the paper) ----
+ * Requests of any grid are queued and admitted into `slots` worker slots (one host
+ * thread and one CUDA stream each) as slots and the device-memory budget allow; plans
+ * are kept resident across requests of the same grid (least recently used plans are
+ * evicted when memory runs short) and every slot solves on its own clone, so requests
+ * that arrive while others run overlap with them on the device.  The device is the
+ * current CUDA device at sp_server_create. */
+typedef struct sp_server sp_server;
+typedef struct {
+    long long completed, failed, queued;
+    int running_peak;          /* most requests on the device at once */
+    int resident_plans;
+    long long evictions;
+    double mem_peak_bytes;     /* peak device memory accounted to plans and buffers */
+    double p50_ms, p99_ms, max_ms;   /* submit-to-completion latency of completed requests */
+    double zones_per_s;        /* zones completed / (last completion - first submission) */
+} sp_server_stats_t;
+
+/* mem_budget_bytes > 0 device bytes for plans, workspaces and staging; 1 <= slots <= 64. */
+int sp_server_create(size_t mem_budget_bytes, int slots, sp_server** out);
+/* Queue one solve (arguments as sp_plan_create, plus host buffers of Nr*Ntheta*Nphi
+ * doubles that must stay valid until sp_server_wait returns for the ticket). */
+int sp_server_submit(sp_server* server, const double* r_interfaces, int Nr, const double* theta_interfaces,
+                     int Ntheta, int Nphi, int outer_bc, double G, int precision, double tol, int max_iter,
+                     const double* rho_host, double* phi_host, long long* ticket);
+/* Wait for a ticket (timeout_s < 0: no limit); returns the solve's status or
+ * SP_ERR_TIMEOUT (the ticket stays valid).  A completed ticket is released. */
+int sp_server_wait(sp_server* server, long long ticket, double timeout_s, sp_solve_info* info);
+int sp_server_stats(sp_server* server, sp_server_stats_t* out);
+/* Finishes queued and running requests, then releases everything. */
+int sp_server_destroy(sp_server* server);
 
 /* Status of the most recent device-side checks of this plan (synchronises). */
 int sp_plan_last_status(const sp_plan* plan);

@@ -46,12 +46,31 @@ class SolveInfo(C.Structure):
         return d
 
 
+class ServerStats(C.Structure):
+    _fields_ = [("completed", C.c_longlong), ("failed", C.c_longlong), ("queued", C.c_longlong),
+                ("running_peak", C.c_int), ("resident_plans", C.c_int), ("evictions", C.c_longlong),
+                ("mem_peak_bytes", C.c_double), ("p50_ms", C.c_double), ("p99_ms", C.c_double),
+                ("max_ms", C.c_double), ("zones_per_s", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _LIB = None
 
 # name -> (restype, argtypes)
 _SIGS = {
     "sp_plan_create": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_double,
                                  C.c_int, C.c_double, C.c_int, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "sp_plan_clone": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p)]),
+    "sp_solve_batched": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "sp_server_create": (C.c_int, [C.c_size_t, C.c_int, C.POINTER(C.c_void_p)]),
+    "sp_server_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_int,
+                                   C.c_double, C.c_int, C.c_double, C.c_int, C.c_void_p, C.c_void_p,
+                                   C.POINTER(C.c_longlong)]),
+    "sp_server_wait": (C.c_int, [C.c_void_p, C.c_longlong, C.c_double, C.POINTER(SolveInfo)]),
+    "sp_server_stats": (C.c_int, [C.c_void_p, C.POINTER(ServerStats)]),
+    "sp_server_destroy": (C.c_int, [C.c_void_p]),
     "sp_plan_workspace_bytes": (C.c_size_t, [C.c_void_p]),
     "sp_plan_set_workspace": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "sp_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(SolveInfo)]),
@@ -140,6 +159,65 @@ def sp_plan_create(r_interfaces, theta_interfaces, nphi, outer_bc=SP_OUTER_MULTI
                               _stream_ptr(stream), C.byref(out))
     _check(st, "sp_plan_create")
     return out
+
+
+def sp_plan_clone(plan):
+    out = C.c_void_p()
+    _check(lib().sp_plan_clone(plan, C.byref(out)), "sp_plan_clone")
+    return out
+
+
+def sp_solve_batched(plans, rhos, phis, stream=None):
+    """plans: list of Plan; rhos, phis: lists of CUDA float64 tensors (one per plan)."""
+    n = len(plans)
+    if not (len(rhos) == len(phis) == n):
+        raise ValueError("plans, rhos and phis must have the same length")
+    hp = (C.c_void_p * n)(*[p.handle.value for p in plans])
+    rp = (C.c_void_p * n)(*[_dev_ptr(r, int(np.prod(p.shape)), "rho").value for p, r in zip(plans, rhos)])
+    pp = (C.c_void_p * n)(*[_dev_ptr(f, int(np.prod(p.shape)), "phi").value for p, f in zip(plans, phis)])
+    infos = (SolveInfo * n)()
+    dev = rhos[0].device if n else None
+    st = lib().sp_solve_batched(hp, rp, pp, n, _stream_ptr(stream, dev), infos)
+    _check(st, "sp_solve_batched")
+    return list(infos)
+
+
+def sp_server_create(mem_budget_bytes, slots):
+    out = C.c_void_p()
+    _check(lib().sp_server_create(int(mem_budget_bytes), int(slots), C.byref(out)), "sp_server_create")
+    return out
+
+
+def sp_server_submit(server, r_interfaces, theta_interfaces, nphi, rho, phi, outer_bc=SP_OUTER_MULTIPOLE, G=1.0,
+                     precision=SP_FP64, tol=1e-10, max_iter=8):
+    r = np.ascontiguousarray(r_interfaces, dtype=np.float64)
+    th = np.ascontiguousarray(theta_interfaces, dtype=np.float64)
+    if rho.dtype != np.float64 or not rho.flags.c_contiguous or phi.dtype != np.float64 or not phi.flags.c_contiguous:
+        raise ValueError("rho and phi must be contiguous float64 arrays")
+    t = C.c_longlong()
+    st = lib().sp_server_submit(server, r.ctypes.data_as(C.c_void_p), len(r) - 1, th.ctypes.data_as(C.c_void_p),
+                                len(th) - 1, int(nphi), int(outer_bc), float(G), int(precision), float(tol),
+                                int(max_iter), rho.ctypes.data_as(C.c_void_p), phi.ctypes.data_as(C.c_void_p),
+                                C.byref(t))
+    _check(st, "sp_server_submit")
+    return t.value, (r, th)
+
+
+def sp_server_wait(server, ticket, timeout_s=-1.0):
+    info = SolveInfo()
+    st = lib().sp_server_wait(server, int(ticket), float(timeout_s), C.byref(info))
+    return st, info
+
+
+def sp_server_stats(server):
+    s = ServerStats()
+    _check(lib().sp_server_stats(server, C.byref(s)), "sp_server_stats")
+    return s.as_dict()
+
+
+def sp_server_destroy(server):
+    if server:
+        lib().sp_server_destroy(server)
 
 
 def sp_plan_workspace_bytes(plan) -> int:
@@ -251,6 +329,14 @@ class Plan:
 
     def workspace_bytes(self) -> int:
         return sp_plan_workspace_bytes(self._h)
+
+    def clone(self):
+        """A plan sharing this plan's tables with its own workspace."""
+        c = Plan.__new__(Plan)
+        c.r_if, c.th_if, c.shape, c.mh, c.precision = self.r_if, self.th_if, self.shape, self.mh, self.precision
+        c._h = None
+        c._h = sp_plan_clone(self._h)
+        return c
 
     def solve(self, rho, out=None, stream=None):
         import torch

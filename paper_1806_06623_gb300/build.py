@@ -72,7 +72,7 @@ def build(verbose: bool = False, extra_flags=None) -> str:
                     print(f"[{os.path.basename(futs[f])}]\n{msg}", file=sys.stderr)
     if jobs or not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
         tmp = LIB + ".tmp"
-        cmd = [nvcc(), *ARCH, "-shared", "-Xcompiler", "-fPIC", "-o", tmp, *objs]
+        cmd = [nvcc(), *ARCH, "-shared", "-Xcompiler", "-fPIC", "-Xcompiler", "-pthread", "-o", tmp, *objs, "-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")

@@ -464,23 +464,29 @@ int mixed_create_tables(Plan& p, cudaStream_t s) {
   return ok ? SP_OK : SP_ERR_CUDA;
 }
 
-void mixed_free_tables(Plan& p) {
-  if (!p.mixed) return;
-  MixedTables* x = p.mixed;
+void mixed_free_shared(MixedTables& x) {
   for (int q = 0; q < 3; ++q) {
-    cudaFree(x->HtW[q]);
-    cudaFree(x->Hm[q]);
+    cudaFree(x.HtW[q]);
+    cudaFree(x.Hm[q]);
   }
-  cudaFree(x->radf);
-  cudaFree(x->fcp);
-  cudaFree(x->finv);
-  cudaFree(x->sub_r);
-  cudaFree(x->low_idx);
-  cudaFree(x->low_fac);
-  cudaFree(x->radff);
-  cudaFree(x->thff);
-  delete x;
-  p.mixed = nullptr;
+  cudaFree(x.radf);
+  cudaFree(x.fcp);
+  cudaFree(x.finv);
+  cudaFree(x.sub_r);
+  cudaFree(x.low_idx);
+  cudaFree(x.low_fac);
+  cudaFree(x.radff);
+  cudaFree(x.thff);
+}
+
+void mixed_clear_workspace(MixedTables& x) {
+  x.r32 = nullptr;
+  x.phi_hi = x.phi_lo = nullptr;
+  for (int q = 0; q < 3; ++q) x.pan[q] = nullptr;
+  x.d32 = nullptr;
+  x.low_ws = nullptr;
+  x.outer_shell = x.shell_phi = nullptr;
+  x.red = nullptr;
 }
 
 template <int NP>

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 
@@ -98,6 +99,10 @@ enum KernelId : int {
 constexpr int kMaxTimedLaunches = 256;
 
 struct Plan {
+  // Read-only tables (geometry rows, eigenbasis, elimination factors, bf16 planes) are
+  // shared by a plan and its clones and freed with the last of them; workspace, error
+  // word, host-buffer staging and timers belong to each plan.
+  std::atomic<int>* table_refs = nullptr;
   int device = 0;
   int nr = 0, nth = 0, nphi = 0, mh = 0;
   int outer_bc = SP_OUTER_MULTIPOLE;
@@ -138,6 +143,7 @@ struct Plan {
   double* d_phi_io = nullptr;
 
   MixedTables* mixed = nullptr;
+  unsigned int* h_red = nullptr;  // pinned host copy of the mixed-path reductions
 
   // launch accounting and optional CUDA-event timers (one event pair per launch)
   long long launches = 0;
@@ -192,7 +198,8 @@ cudaError_t theta_eigen(const Plan& p, cudaStream_t s);
 size_t mixed_workspace_bytes(const Plan& p);
 void mixed_bind_workspace(Plan& p, char* base);
 int mixed_create_tables(Plan& p, cudaStream_t s);   // after theta_eigen; returns sp_status
-void mixed_free_tables(Plan& p);
+void mixed_free_shared(MixedTables& x);     // tables shared with clones
+void mixed_clear_workspace(MixedTables& x);  // forget workspace views (clone set-up)
 bool mixed_make_panel_maps(Plan& p);
 struct Planes {
   __nv_bfloat16* p[3];
@@ -206,5 +213,25 @@ cudaError_t finish_mixed(const Plan& p, double* phi, cudaStream_t s);   // float
 cudaError_t tc_project(const Plan& p, bool inverse, cudaStream_t s);   // pan -> d32
 cudaError_t thomas_mixed(const Plan& p, cudaStream_t s);   // d32 -> pan (f); float32 + float64 low modes
 cudaError_t residual_ff(const Plan& p, const double* rho, cudaStream_t s);  // iterate -> r32
+
+// ---- solve phases shared by sp_solve, sp_solve_batched and the server ----
+// Refinement state of one mixed-precision solve.
+struct MixedRun {
+  double e_prev = 0.0, pmax = 0.0, est = 1.0, last = 1.0;
+  double hist[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int iters = 0;   // low-precision solves issued and read
+  bool done = false;
+};
+int mixed_start(Plan* p, const double* rho, cudaStream_t s);
+int mixed_correct(Plan* p, const double* rho, cudaStream_t s);
+int mixed_issue_read(Plan* p, cudaStream_t s);
+void mixed_decide(Plan* p, MixedRun& R);
+int mixed_finish(Plan* p, double* phi, cudaStream_t s, const MixedRun& R, sp_solve_info* info);
+int mixed_finish_issue(Plan* p, double* phi, cudaStream_t s);
+int mixed_finish_status(Plan* p, const MixedRun& R, sp_solve_info* info);
+size_t plan_table_bytes(const Plan& p);
+int fill_fp64_info(int st, sp_solve_info* info);
+int solve_fp64_async(Plan* p, const double* rho, double* phi, cudaStream_t s);
+int ensure_plan_workspace(Plan* p);
 
 }  // namespace sp

@@ -65,23 +65,31 @@ int upload(T** dst, const T* src, size_t n) {
   return SP_OK;
 }
 
+// Release what the plan owns; the shared tables go with the last plan using them.
 void free_tables(Plan* p) {
-  cudaFree(p->d_rad);
-  cudaFree(p->d_theta);
-  cudaFree(p->d_twid);
-  cudaFree(p->d_twid32);
-  cudaFree(p->d_tdiag);
-  cudaFree(p->d_toff);
-  cudaFree(p->d_sqw);
-  cudaFree(p->d_lam);
-  cudaFree(p->d_kappa);
-  cudaFree(p->d_outer);
-  cudaFree(p->d_HtW);
-  cudaFree(p->d_H);
+  const bool last = !p->table_refs || p->table_refs->fetch_sub(1) == 1;
+  if (last) {
+    cudaFree(p->d_rad);
+    cudaFree(p->d_theta);
+    cudaFree(p->d_twid);
+    cudaFree(p->d_twid32);
+    cudaFree(p->d_tdiag);
+    cudaFree(p->d_toff);
+    cudaFree(p->d_sqw);
+    cudaFree(p->d_lam);
+    cudaFree(p->d_kappa);
+    cudaFree(p->d_outer);
+    cudaFree(p->d_HtW);
+    cudaFree(p->d_H);
+    if (p->mixed) sp::mixed_free_shared(*p->mixed);
+    delete p->table_refs;
+  }
+  delete p->mixed;
+  p->mixed = nullptr;
   cudaFree(p->d_err);
   cudaFree(p->d_rho_io);
   cudaFree(p->d_phi_io);
-  sp::mixed_free_tables(*p);
+  if (p->h_red) cudaFreeHost(p->h_red);
   if (p->ws_owned) cudaFree(p->ws);
   for (int i = 0; i < 2 * sp::kMaxTimedLaunches; ++i)
     if (p->ev[i]) cudaEventDestroy(p->ev[i]);
@@ -156,71 +164,131 @@ int lp_solve(Plan* p, const void* in, bool in_double, float scale, double* phi, 
     return sp::fft_inverse_update(P, x.d32, x.phi_hi, x.phi_lo, first, x.red, s); }));
 }
 
-int read_reductions(Plan* p, cudaStream_t s, double* emax, double* pmax) {
-  unsigned int h[2] = {0, 0};
-  SP_CUDA(cudaMemcpyAsync(h, p->mixed->red, sizeof(h), cudaMemcpyDeviceToHost, s));
-  SP_CUDA(cudaStreamSynchronize(s));
-  float v[2];
-  std::memcpy(v, h, sizeof(v));
-  *emax = v[0];
-  *pmax = v[1];
+}  // namespace
+
+namespace sp {
+
+// First low-precision solve of L Phi = 4 pi G rho (asynchronous).
+int mixed_start(Plan* p, const double* rho, cudaStream_t s) {
+  SP_CUDA(cudaMemsetAsync(p->mixed->red, 0, 2 * sizeof(unsigned int), s));
+  return lp_solve(p, rho, true, (float)(4.0 * kPi * p->G / p->nphi), nullptr, true, s);
+}
+
+// One correction: float-float residual, then the low-precision solve of L e = r (asynchronous).
+int mixed_correct(Plan* p, const double* rho, cudaStream_t s) {
+  Plan& P = *p;
+  int st;
+  if ((st = launch_status(timed_launch(P, kKResidual, s, [&] { return residual_ff(P, rho, s); })))) return st;
+  if (P.outer_bc == SP_OUTER_MULTIPOLE) P.launches += 4;
+  SP_CUDA(cudaMemsetAsync(P.mixed->red, 0, 2 * sizeof(unsigned int), s));
+  return lp_solve(p, P.mixed->r32, false, (float)(1.0 / P.nphi), nullptr, false, s);
+}
+
+// Queue the copy of the reductions of the last low-precision solve to pinned host memory.
+int mixed_issue_read(Plan* p, cudaStream_t s) {
+  SP_CUDA(cudaMemcpyAsync(p->h_red, p->mixed->red, 2 * sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
   return SP_OK;
 }
 
-// Mixed-precision solve with float64 iterative refinement (stops when the estimated
-// max|Phi - Phi_exact|/max|Phi| <= tol).
-int solve_mixed(Plan* p, const double* rho, double* phi, cudaStream_t s, sp_solve_info* info) {
-  Plan& P = *p;
-  sp::MixedTables& x = *P.mixed;
-  const double four_pi_g = 4.0 * kPi * P.G;
-  int st;
-  SP_CUDA(cudaMemsetAsync(x.red, 0, 2 * sizeof(unsigned int), s));
-  if ((st = lp_solve(p, rho, true, (float)(four_pi_g / P.nphi), phi, true, s))) return st;
-  double e_prev = 0.0, e_cur = 0.0, pmax = 0.0;
-  if ((st = read_reductions(p, s, &e_prev, &pmax))) return st;
-  int iters = 1;
-  double est = 1.0, last = 1.0;
-  double hist[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  hist[0] = pmax > 0.0 ? e_prev / pmax : 0.0;
-  bool done = false;
-  if (pmax == 0.0) { done = true; est = 0.0; last = 0.0; }   // rho == 0
-  for (int k = 1; k <= P.max_iter && !done; ++k) {
-    if ((st = launch_status(sp::timed_launch(P, sp::kKResidual, s, [&] { return sp::residual_ff(P, rho, s); }))))
-      return st;
-    if (P.outer_bc == SP_OUTER_MULTIPOLE) P.launches += 4;
-    SP_CUDA(cudaMemsetAsync(x.red, 0, 2 * sizeof(unsigned int), s));
-    if ((st = lp_solve(p, x.r32, false, (float)(1.0 / P.nphi), phi, false, s))) return st;
-    if ((st = read_reductions(p, s, &e_cur, &pmax))) return st;
-    last = e_cur / pmax;
-    if (iters < 8) hist[iters] = last;
-    ++iters;
-    // |e_k| measures the error of the previous iterate; the current one is smaller by the
-    // contraction factor of the refinement, taken as the larger of the observed ratio of
-    // successive corrections and a bound for the mode (largest ratio measured over the
-    // stellar, ragged, point-mass and random-source workloads, times two: 1.9e-5 for 6
-    // products, 1.2e-3 for 3 products).
-    const double bound = (x.np == 3) ? 4e-5 : 2.5e-3;
-    const double ratio = (k >= 2 && e_prev > 0.0) ? e_cur / e_prev : 0.0;
-    const double c = ratio > bound ? ratio : bound;
-    est = c < 1.0 ? last * c / (1.0 - c) : last;
-    done = est <= P.tol || last <= 1e-15;
-    e_prev = e_cur;
+// After the stream has reached the copy: update the refinement state.  |e_k| measures the
+// error of the previous iterate; the current one is smaller by the contraction factor of
+// the refinement, taken as the larger of the observed ratio of successive corrections and
+// a bound for the mode (largest ratio measured over the stellar, ragged, point-mass and
+// random-source workloads, times two: 1.9e-5 for 6 products, 1.2e-3 for 3 products).
+void mixed_decide(Plan* p, MixedRun& R) {
+  float v[2];
+  std::memcpy(v, p->h_red, sizeof(v));
+  const double e_cur = v[0];
+  R.pmax = v[1];
+  if (R.iters == 0) {
+    R.e_prev = e_cur;
+    R.hist[0] = R.pmax > 0.0 ? e_cur / R.pmax : 0.0;
+    R.iters = 1;
+    if (R.pmax == 0.0) {   // rho == 0
+      R.done = true;
+      R.est = R.last = 0.0;
+    }
+    return;
   }
-  if ((st = launch_status(sp::timed_launch(P, sp::kKUpdate, s, [&] { return sp::finish_mixed(P, phi, s); }))))
-    return st;
-  int herr = 0;
-  SP_CUDA(cudaMemcpyAsync(&herr, P.d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
-  SP_CUDA(cudaStreamSynchronize(s));
-  st = herr ? ((herr & sp::kErrTimeout) ? SP_ERR_TIMEOUT : SP_ERR_DEVICE_CHECK) : (done ? SP_OK : SP_ERR_NOT_CONVERGED);
+  R.last = e_cur / R.pmax;
+  if (R.iters < 8) R.hist[R.iters] = R.last;
+  const double bound = (p->mixed->np == 3) ? 4e-5 : 2.5e-3;
+  const double ratio = (R.iters >= 2 && R.e_prev > 0.0) ? e_cur / R.e_prev : 0.0;
+  const double c = ratio > bound ? ratio : bound;
+  R.est = c < 1.0 ? R.last * c / (1.0 - c) : R.last;
+  R.done = R.est <= p->tol || R.last <= 1e-15;
+  R.e_prev = e_cur;
+  ++R.iters;
+}
+
+// Float-float iterate -> float64 Phi and the copy of the device status word (asynchronous).
+int mixed_finish_issue(Plan* p, double* phi, cudaStream_t s) {
+  Plan& P = *p;
+  int st;
+  if ((st = launch_status(timed_launch(P, kKUpdate, s, [&] { return finish_mixed(P, phi, s); })))) return st;
+  SP_CUDA(cudaMemcpyAsync(P.h_red + 2, P.d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  return SP_OK;
+}
+
+// After the stream has reached mixed_finish_issue: status and info.
+int mixed_finish_status(Plan* p, const MixedRun& R, sp_solve_info* info) {
+  Plan& P = *p;
+  const int herr = (int)P.h_red[2];
+  const int st = herr ? ((herr & kErrTimeout) ? SP_ERR_TIMEOUT : SP_ERR_DEVICE_CHECK)
+                      : (R.done ? SP_OK : SP_ERR_NOT_CONVERGED);
   if (info) {
-    info->iterations = iters;
+    info->iterations = R.iters;
     info->precision_used = P.precision;
-    info->last_update = last;
-    info->est_rel_error = est;
+    info->last_update = R.last;
+    info->est_rel_error = R.est;
     info->status = st;
-    for (int q = 0; q < 8; ++q) info->update_history[q] = hist[q];
+    for (int q = 0; q < 8; ++q) info->update_history[q] = R.hist[q];
   }
   return st;
+}
+
+int mixed_finish(Plan* p, double* phi, cudaStream_t s, const MixedRun& R, sp_solve_info* info) {
+  int st = mixed_finish_issue(p, phi, s);
+  if (st) return st;
+  SP_CUDA(cudaStreamSynchronize(s));
+  return mixed_finish_status(p, R, info);
+}
+
+int solve_fp64_async(Plan* p, const double* rho, double* phi, cudaStream_t s) { return solve_fp64(p, rho, phi, s); }
+int ensure_plan_workspace(Plan* p) { return ensure_workspace(p); }
+
+int fill_fp64_info(int st, sp_solve_info* info) {
+  if (info) {
+    info->iterations = 1;
+    info->precision_used = SP_FP64;
+    info->last_update = 0.0;
+    info->est_rel_error = 0.0;
+    info->status = st;
+    for (int q = 0; q < 8; ++q) info->update_history[q] = 0.0;
+  }
+  return st;
+}
+
+}  // namespace sp
+
+namespace {
+
+// Mixed-precision solve with float-float iterative refinement (stops when the estimated
+// max|Phi - Phi_exact|/max|Phi| <= tol).
+int solve_mixed(Plan* p, const double* rho, double* phi, cudaStream_t s, sp_solve_info* info) {
+  sp::MixedRun R;
+  int st;
+  if ((st = sp::mixed_start(p, rho, s))) return st;
+  if ((st = sp::mixed_issue_read(p, s))) return st;
+  SP_CUDA(cudaStreamSynchronize(s));
+  sp::mixed_decide(p, R);
+  for (int k = 1; k <= p->max_iter && !R.done; ++k) {
+    if ((st = sp::mixed_correct(p, rho, s))) return st;
+    if ((st = sp::mixed_issue_read(p, s))) return st;
+    SP_CUDA(cudaStreamSynchronize(s));
+    sp::mixed_decide(p, R);
+  }
+  return sp::mixed_finish(p, phi, s, R, info);
 }
 
 int apply_laplacian_impl(Plan* p, const double* phi, double* out, cudaStream_t s) {
@@ -316,6 +384,11 @@ int sp_plan_create(const double* r_if, int nr, const double* th_if_in, int nth, 
 
   Plan* p = new (std::nothrow) Plan();
   if (!p) return SP_ERR_OOM;
+  p->table_refs = new (std::nothrow) std::atomic<int>(1);
+  if (!p->table_refs) {
+    delete p;
+    return SP_ERR_OOM;
+  }
   cudaGetDevice(&p->device);
   p->nr = nr;
   p->nth = nth;
@@ -440,6 +513,10 @@ int sp_plan_create(const double* r_if, int nr, const double* th_if_in, int nth, 
     }
     if (herr) { st = SP_ERR_DEVICE_CHECK; break; }
     if (precision != SP_FP64 && (st = sp::mixed_create_tables(*p, s))) break;
+    if (precision != SP_FP64 && cudaMallocHost(&p->h_red, 4 * sizeof(unsigned int)) != cudaSuccess) {
+      st = SP_ERR_OOM;
+      break;
+    }
   } while (0);
   if (st != SP_OK) {
     free_tables(p);
@@ -447,6 +524,46 @@ int sp_plan_create(const double* r_if, int nr, const double* th_if_in, int nth, 
     return st;
   }
   *out = reinterpret_cast<sp_plan*>(p);
+  return SP_OK;
+}
+
+int sp_plan_clone(const sp_plan* src_plan, sp_plan** out) {
+  if (!src_plan || !out) return SP_ERR_INVALID_ARG;
+  *out = nullptr;
+  const Plan* src = reinterpret_cast<const Plan*>(src_plan);
+  DeviceGuard guard(src->device);
+  Plan* c = new (std::nothrow) Plan(*src);
+  if (!c) return SP_ERR_OOM;
+  // per-plan state starts fresh; the tables are shared
+  c->table_refs->fetch_add(1);
+  c->d_err = nullptr;
+  c->ws = nullptr;
+  c->ws_bytes = 0;
+  c->ws_owned = false;
+  c->specA = c->specB = c->cp = c->shell = c->shell2 = nullptr;
+  c->d_rho_io = c->d_phi_io = nullptr;
+  c->h_red = nullptr;
+  c->launches = 0;
+  c->timing = false;
+  c->n_timed = 0;
+  for (int i = 0; i < 2 * sp::kMaxTimedLaunches; ++i) c->ev[i] = nullptr;
+  for (int k = 0; k < sp::kNumKernelIds; ++k) { c->acc_ms[k] = 0.0; c->acc_n[k] = 0; }
+  c->mixed = nullptr;
+  int st = SP_OK;
+  if (src->mixed) {
+    c->mixed = new (std::nothrow) sp::MixedTables(*src->mixed);
+    if (!c->mixed) st = SP_ERR_OOM;
+    else sp::mixed_clear_workspace(*c->mixed);
+    if (st == SP_OK && cudaMallocHost(&c->h_red, 4 * sizeof(unsigned int)) != cudaSuccess) st = SP_ERR_OOM;
+  }
+  if (st == SP_OK && cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess) st = SP_ERR_OOM;
+  if (st == SP_OK && cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess) st = SP_ERR_CUDA;
+  if (st != SP_OK) {
+    free_tables(c);
+    delete c;
+    return st;
+  }
+  *out = reinterpret_cast<sp_plan*>(c);
   return SP_OK;
 }
 
@@ -482,16 +599,7 @@ int sp_solve(sp_plan* plan, const double* rho, double* phi, void* stream, sp_sol
   if (st) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (p->mixed) return solve_mixed(p, rho, phi, s, info);
-  st = solve_fp64(p, rho, phi, s);
-  if (info) {
-    info->iterations = 1;
-    info->precision_used = SP_FP64;
-    info->last_update = 0.0;
-    info->est_rel_error = 0.0;
-    info->status = st;
-    for (int q = 0; q < 8; ++q) info->update_history[q] = 0.0;
-  }
-  return st;
+  return sp::fill_fp64_info(solve_fp64(p, rho, phi, s), info);
 }
 
 int sp_solve_host(sp_plan* plan, const double* rho_host, double* phi_host, void* stream, sp_solve_info* info) {
@@ -599,3 +707,20 @@ int sp_plan_destroy(sp_plan* plan) {
 }
 
 }  // extern "C"
+
+namespace sp {
+
+// Device bytes of the tables a plan shares with its clones.
+size_t plan_table_bytes(const Plan& p) {
+  const size_t tab = (size_t)p.mh * p.nth;
+  size_t b = 2 * tab * p.nth * sizeof(double) + 3 * tab * sizeof(double) + (size_t)p.nr * sizeof(RadialRow) +
+             (size_t)p.nth * sizeof(ThetaRow) + 2 * (size_t)p.nphi * (sizeof(double) + sizeof(float)) + tab * sizeof(double);
+  if (p.mixed) {
+    const MixedTables& x = *p.mixed;
+    b += 2 * (size_t)x.np * tab * x.kstride * 2 + 2 * (size_t)p.mh * p.nr * p.nth * sizeof(float) +
+         (size_t)p.nr * (sizeof(RadialRowF) + sizeof(RadialRowFF) + sizeof(float)) + (size_t)x.nlow * p.nr * 16;
+  }
+  return b;
+}
+
+}  // namespace sp

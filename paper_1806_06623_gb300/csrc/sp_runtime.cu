@@ -1,0 +1,527 @@
+// Batched solves and the continuous-batching solve server.
+//
+// sp_solve_batched runs independent problems (any mix of grids and precisions) on a pool
+// of streams forked from the caller's stream.  Float64 solves are issued back to back;
+// the mixed-precision refinements advance in lock-step rounds -- every unfinished
+// instance issues its next correction, then one host wait per round reads all their
+// update norms -- so the batch costs a few host synchronisations instead of a few per
+// instance, and the instances' kernels overlap on the device.
+//
+// The server admits solve requests of any grid size from a queue into worker slots (one
+// host thread and one stream each) while the device-memory budget allows, keeps plans
+// (geometry, eigenbasis, elimination factors) resident across requests of the same grid
+// and hands every slot its own clone of them (own workspace, shared tables), so requests
+// that arrive while others run start as soon as a slot and memory are free and their
+// kernels overlap on the device.  Latency is measured from submission to completion.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "sp_internal.h"
+
+using sp::Plan;
+
+namespace {
+
+constexpr int kBatchStreams = 8;
+
+struct StreamPool {
+  cudaStream_t s[kBatchStreams] = {};
+  cudaEvent_t ev[kBatchStreams + 1] = {};
+};
+
+std::mutex g_pool_mu;
+std::map<int, StreamPool*> g_pools;
+
+StreamPool* pool_for(int dev) {
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  auto it = g_pools.find(dev);
+  if (it != g_pools.end()) return it->second;
+  StreamPool* sp = new (std::nothrow) StreamPool();
+  if (!sp) return nullptr;
+  for (int k = 0; k < kBatchStreams; ++k)
+    if (cudaStreamCreateWithFlags(&sp->s[k], cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+  for (int k = 0; k <= kBatchStreams; ++k)
+    if (cudaEventCreateWithFlags(&sp->ev[k], cudaEventDisableTiming) != cudaSuccess) return nullptr;
+  g_pools[dev] = sp;
+  return sp;
+}
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? SP_OK : (e == cudaErrorMemoryAllocation ? SP_ERR_OOM : SP_ERR_CUDA); }
+
+struct DeviceScope {
+  int prev = -1;
+  explicit DeviceScope(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceScope() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+
+extern "C" int sp_solve_batched(sp_plan* const* plans, const double* const* rho, double* const* phi, int n,
+                                void* stream, sp_solve_info* infos) {
+  if (n < 0) return SP_ERR_INVALID_ARG;
+  if (n == 0) return SP_OK;
+  if (!plans || !rho || !phi) return SP_ERR_INVALID_ARG;
+  std::vector<Plan*> P(n);
+  for (int i = 0; i < n; ++i) {
+    if (!plans[i] || !rho[i] || !phi[i]) return SP_ERR_INVALID_ARG;
+    P[i] = reinterpret_cast<Plan*>(plans[i]);
+    if (P[i]->device != P[0]->device) return SP_ERR_INVALID_ARG;
+    const size_t bytes = sizeof(double) * (size_t)P[i]->nr * P[i]->nth * P[i]->nphi;
+    const char* a = reinterpret_cast<const char*>(rho[i]);
+    const char* b = reinterpret_cast<const char*>(phi[i]);
+    if (a < b + bytes && b < a + bytes) return SP_ERR_INVALID_ARG;
+  }
+  {
+    std::vector<Plan*> sorted(P);
+    std::sort(sorted.begin(), sorted.end());
+    if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end()) return SP_ERR_INVALID_ARG;   // shared workspace
+  }
+  DeviceScope dev(P[0]->device);
+  StreamPool* pool = pool_for(P[0]->device);
+  if (!pool) return SP_ERR_CUDA;
+  for (int i = 0; i < n; ++i) {
+    const int st = sp::ensure_plan_workspace(P[i]);
+    if (st) return st;
+  }
+  cudaStream_t user = static_cast<cudaStream_t>(stream);
+  const int ns = std::min(n, kBatchStreams);
+  int st = cuda_status(cudaEventRecord(pool->ev[kBatchStreams], user));
+  for (int k = 0; k < ns && !st; ++k) st = cuda_status(cudaStreamWaitEvent(pool->s[k], pool->ev[kBatchStreams], 0));
+  if (st) return st;
+
+  std::vector<int> status(n, SP_OK);
+  std::vector<sp::MixedRun> runs(n);
+  auto stream_of = [&](int i) { return pool->s[i % ns]; };
+  // round 0: float64 solves and the first low-precision solves
+  for (int i = 0; i < n; ++i) {
+    if (P[i]->mixed) {
+      status[i] = sp::mixed_start(P[i], rho[i], stream_of(i));
+      if (!status[i]) status[i] = sp::mixed_issue_read(P[i], stream_of(i));
+    } else {
+      status[i] = sp::solve_fp64_async(P[i], rho[i], phi[i], stream_of(i));
+    }
+  }
+  // refinement rounds
+  std::vector<int> active;
+  for (int i = 0; i < n; ++i)
+    if (P[i]->mixed && !status[i]) active.push_back(i);
+  while (!active.empty()) {
+    for (int k = 0; k < ns; ++k)
+      if (cudaStreamSynchronize(pool->s[k]) != cudaSuccess) return SP_ERR_CUDA;
+    std::vector<int> next;
+    for (int i : active) {
+      sp::mixed_decide(P[i], runs[i]);
+      if (!runs[i].done && runs[i].iters - 1 < P[i]->max_iter) next.push_back(i);
+    }
+    for (int i : next) {
+      status[i] = sp::mixed_correct(P[i], rho[i], stream_of(i));
+      if (!status[i]) status[i] = sp::mixed_issue_read(P[i], stream_of(i));
+    }
+    active.clear();
+    for (int i : next)
+      if (!status[i]) active.push_back(i);
+  }
+  // float-float iterates -> float64 results
+  for (int i = 0; i < n; ++i)
+    if (P[i]->mixed && !status[i]) status[i] = sp::mixed_finish_issue(P[i], phi[i], stream_of(i));
+  bool any_mixed = false;
+  for (int i = 0; i < n; ++i) any_mixed = any_mixed || P[i]->mixed;
+  if (any_mixed)
+    for (int k = 0; k < ns; ++k)
+      if (cudaStreamSynchronize(pool->s[k]) != cudaSuccess) return SP_ERR_CUDA;
+  int first_err = SP_OK;
+  for (int i = 0; i < n; ++i) {
+    if (P[i]->mixed) {
+      if (!status[i]) status[i] = sp::mixed_finish_status(P[i], runs[i], infos ? &infos[i] : nullptr);
+      else if (infos) infos[i].status = status[i];
+    } else {
+      sp::fill_fp64_info(status[i], infos ? &infos[i] : nullptr);
+    }
+    if (status[i] && !first_err) first_err = status[i];
+  }
+  // join the pool back into the caller's stream
+  for (int k = 0; k < ns; ++k) {
+    if (cudaEventRecord(pool->ev[k], pool->s[k]) != cudaSuccess) return SP_ERR_CUDA;
+    if (cudaStreamWaitEvent(user, pool->ev[k], 0) != cudaSuccess) return SP_ERR_CUDA;
+  }
+  return first_err;
+}
+
+// ======================================================================== server
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+  long long ticket = 0;
+  std::string key;
+  std::vector<double> r_if, th_if;
+  int nphi = 0, outer_bc = 0, precision = 0, max_iter = 8;
+  double G = 1.0, tol = 1e-10;
+  const double* rho = nullptr;
+  double* phi = nullptr;
+  size_t zones = 0;
+  size_t io_bytes = 0;
+  int status = SP_OK;
+  sp_solve_info info{};
+  bool done = false;
+  Clock::time_point t_submit, t_done;
+};
+
+struct Resident {
+  sp_plan* master = nullptr;
+  size_t table_bytes = 0;
+  size_t clone_bytes = 0;   // workspace of one clone
+  int active = 0;
+  bool creating = false;
+  int create_status = SP_OK;
+  long long last_used = 0;
+  std::vector<sp_plan*> idle;   // clones with a workspace, ready for reuse
+};
+
+std::string make_key(const Request& q) {
+  std::string k;
+  auto put = [&](const void* p, size_t n) { k.append(static_cast<const char*>(p), n); };
+  const int hdr[5] = {(int)q.r_if.size(), (int)q.th_if.size(), q.nphi, q.outer_bc, q.precision};
+  put(hdr, sizeof(hdr));
+  put(&q.G, sizeof(double));
+  put(&q.tol, sizeof(double));
+  put(&q.max_iter, sizeof(int));
+  put(q.r_if.data(), q.r_if.size() * sizeof(double));
+  put(q.th_if.data(), q.th_if.size() * sizeof(double));
+  return k;
+}
+
+}  // namespace
+
+struct sp_server {
+  int device = 0;
+  size_t budget = 0;
+  int slots = 0;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Request*> queue;
+  std::unordered_map<long long, Request*> requests;
+  std::map<std::string, Resident> resident;
+  size_t mem_used = 0, mem_peak = 0;
+  long long next_ticket = 1, clock = 0;
+  int running = 0, running_peak = 0;
+  bool stopping = false;
+  std::vector<std::thread> workers;
+  // statistics
+  std::vector<double> latency_ms;
+  double zones_done = 0.0;
+  long long completed = 0, failed = 0, evictions = 0;
+  bool have_first = false;
+  Clock::time_point t_first, t_last;
+
+  void worker(int slot);
+  bool evict_for(size_t need);   // caller holds mu
+};
+
+bool sp_server::evict_for(size_t need) {
+  while (mem_used + need > budget) {
+    auto victim = resident.end();
+    for (auto it = resident.begin(); it != resident.end(); ++it) {
+      if (it->second.active || it->second.creating || !it->second.master) continue;
+      if (victim == resident.end() || it->second.last_used < victim->second.last_used) victim = it;
+    }
+    if (victim == resident.end()) return false;
+    for (sp_plan* c : victim->second.idle) {
+      sp_plan_destroy(c);
+      mem_used -= victim->second.clone_bytes;
+    }
+    sp_plan_destroy(victim->second.master);
+    mem_used -= victim->second.table_bytes;
+    resident.erase(victim);
+    ++evictions;
+  }
+  return true;
+}
+
+void sp_server::worker(int slot) {
+  (void)slot;
+  cudaSetDevice(device);
+  cudaStream_t s = nullptr;
+  cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  double* d_io = nullptr;
+  size_t d_io_bytes = 0;
+  std::unique_lock<std::mutex> lock(mu);
+  while (true) {
+    // admit the oldest request whose plan memory fits (or any request when nothing runs)
+    Request* q = nullptr;
+    size_t reserve = 0;
+    cv_work.wait(lock, [&] { return stopping || !queue.empty(); });
+    if (queue.empty()) {
+      if (stopping) break;
+      continue;
+    }
+    for (auto it = queue.begin(); it != queue.end(); ++it) {
+      Request* c = *it;
+      auto r = resident.find(c->key);
+      const bool have = r != resident.end() && r->second.master;
+      if (r != resident.end() && r->second.creating) continue;   // another slot builds its plan
+      // rough need before the plan exists: tables + workspace of the float64 layout
+      size_t need = c->io_bytes;
+      if (!have) need += 64u << 20;
+      else if (r->second.idle.empty()) need += r->second.clone_bytes;
+      if (mem_used + need <= budget || evict_for(need) || running == 0) {
+        q = c;
+        reserve = c->io_bytes;
+        queue.erase(it);
+        break;
+      }
+    }
+    if (!q) {
+      cv_work.wait_for(lock, std::chrono::milliseconds(2));
+      continue;
+    }
+    ++running;
+    running_peak = std::max(running_peak, running);
+    mem_used += reserve;
+    mem_peak = std::max(mem_peak, mem_used);
+    // resident plan for this grid (built once, outside the lock)
+    Resident& res = resident[q->key];
+    while (res.creating) cv_done.wait(lock);
+    int st = SP_OK;
+    if (!res.master) {
+      res.creating = true;
+      lock.unlock();
+      sp_plan* m = nullptr;
+      cudaSetDevice(device);
+      st = sp_plan_create(q->r_if.data(), (int)q->r_if.size() - 1, q->th_if.data(), (int)q->th_if.size() - 1,
+                          q->nphi, q->outer_bc, q->G, q->precision, q->tol, q->max_iter, s, &m);
+      lock.lock();
+      res.creating = false;
+      if (st == SP_OK) {
+        res.master = m;
+        const Plan* pm = reinterpret_cast<const Plan*>(m);
+        res.table_bytes = sp::plan_table_bytes(*pm);
+        res.clone_bytes = sp_plan_workspace_bytes(m);
+        mem_used += res.table_bytes;
+        mem_peak = std::max(mem_peak, mem_used);
+      }
+      cv_done.notify_all();
+    }
+    sp_plan* plan = nullptr;
+    if (st == SP_OK) {
+      res.active += 1;
+      res.last_used = ++clock;
+      if (!res.idle.empty()) {
+        plan = res.idle.back();
+        res.idle.pop_back();
+      } else {
+        mem_used += res.clone_bytes;
+        mem_peak = std::max(mem_peak, mem_used);
+      }
+    }
+    sp_plan* master = res.master;
+    const size_t clone_bytes = res.clone_bytes;
+    lock.unlock();
+    // ---- run on this slot's stream
+    if (st == SP_OK && !plan) st = sp_plan_clone(master, &plan);
+    const size_t need_io = 2 * q->zones * sizeof(double);
+    if (st == SP_OK && d_io_bytes < need_io) {
+      cudaFree(d_io);
+      d_io = nullptr;
+      d_io_bytes = 0;
+      if (cudaMalloc(&d_io, need_io) != cudaSuccess) st = SP_ERR_OOM;
+      else d_io_bytes = need_io;
+    }
+    sp_solve_info info{};
+    if (st == SP_OK) {
+      const size_t b = q->zones * sizeof(double);
+      double* drho = d_io;
+      double* dphi = d_io + q->zones;
+      st = cuda_status(cudaMemcpyAsync(drho, q->rho, b, cudaMemcpyHostToDevice, s));
+      if (!st) st = sp_solve(plan, drho, dphi, s, &info);
+      if (!st) st = cuda_status(cudaMemcpyAsync(q->phi, dphi, b, cudaMemcpyDeviceToHost, s));
+      if (!st) st = cuda_status(cudaStreamSynchronize(s));
+    }
+    lock.lock();
+    --running;
+    mem_used -= reserve;
+    Resident& r2 = resident[q->key];
+    if (plan) {
+      r2.active -= 1;
+      if (st == SP_OK || st == SP_ERR_NOT_CONVERGED) {
+        r2.idle.push_back(plan);
+      } else {
+        sp_plan_destroy(plan);
+        mem_used -= clone_bytes;
+      }
+    } else if (st != SP_OK && r2.master && master) {
+      // clone failed: release the reservation made for it
+      r2.active -= 1;
+      mem_used -= clone_bytes;
+    }
+    q->status = st;
+    q->info = info;
+    q->info.status = st;
+    q->t_done = Clock::now();
+    q->done = true;
+    if (st == SP_OK) {
+      ++completed;
+      latency_ms.push_back(std::chrono::duration<double, std::milli>(q->t_done - q->t_submit).count());
+      zones_done += (double)q->zones;
+      t_last = q->t_done;
+    } else {
+      ++failed;
+    }
+    cv_done.notify_all();
+    cv_work.notify_all();
+  }
+  lock.unlock();
+  cudaFree(d_io);
+  cudaStreamDestroy(s);
+}
+
+extern "C" int sp_server_create(size_t mem_budget_bytes, int slots, sp_server** out) {
+  if (!out || slots < 1 || slots > 64 || mem_budget_bytes == 0) return SP_ERR_INVALID_ARG;
+  *out = nullptr;
+  sp_server* sv = new (std::nothrow) sp_server();
+  if (!sv) return SP_ERR_OOM;
+  cudaGetDevice(&sv->device);
+  sv->budget = mem_budget_bytes;
+  sv->slots = slots;
+  try {
+    for (int k = 0; k < slots; ++k) sv->workers.emplace_back(&sp_server::worker, sv, k);
+  } catch (...) {
+    {
+      std::lock_guard<std::mutex> lock(sv->mu);
+      sv->stopping = true;
+    }
+    sv->cv_work.notify_all();
+    for (auto& t : sv->workers) t.join();
+    delete sv;
+    return SP_ERR_OOM;
+  }
+  *out = sv;
+  return SP_OK;
+}
+
+extern "C" int sp_server_submit(sp_server* sv, const double* r_interfaces, int nr, const double* theta_interfaces,
+                                int ntheta, int nphi, int outer_bc, double G, int precision, double tol, int max_iter,
+                                const double* rho_host, double* phi_host, long long* ticket) {
+  if (!sv || !r_interfaces || !rho_host || !phi_host || !ticket || nr < 1 || ntheta < 1 || nphi < 1)
+    return SP_ERR_INVALID_ARG;
+  Request* q = new (std::nothrow) Request();
+  if (!q) return SP_ERR_OOM;
+  q->r_if.assign(r_interfaces, r_interfaces + nr + 1);
+  if (theta_interfaces) {
+    q->th_if.assign(theta_interfaces, theta_interfaces + ntheta + 1);
+  } else {
+    q->th_if.resize(ntheta + 1);
+    for (int j = 0; j <= ntheta; ++j) q->th_if[j] = 3.14159265358979323846264338327950288 * j / ntheta;
+  }
+  q->nphi = nphi;
+  q->outer_bc = outer_bc;
+  q->precision = precision;
+  q->max_iter = max_iter;
+  q->G = G;
+  q->tol = tol;
+  q->rho = rho_host;
+  q->phi = phi_host;
+  q->zones = (size_t)nr * ntheta * nphi;
+  q->io_bytes = 2 * q->zones * sizeof(double);
+  q->key = make_key(*q);
+  q->t_submit = Clock::now();
+  {
+    std::lock_guard<std::mutex> lock(sv->mu);
+    if (sv->stopping) {
+      delete q;
+      return SP_ERR_INVALID_ARG;
+    }
+    q->ticket = sv->next_ticket++;
+    if (!sv->have_first) {
+      sv->have_first = true;
+      sv->t_first = q->t_submit;
+    }
+    sv->requests[q->ticket] = q;
+    sv->queue.push_back(q);
+    *ticket = q->ticket;
+  }
+  sv->cv_work.notify_one();
+  return SP_OK;
+}
+
+extern "C" int sp_server_wait(sp_server* sv, long long ticket, double timeout_s, sp_solve_info* info) {
+  if (!sv) return SP_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lock(sv->mu);
+  auto it = sv->requests.find(ticket);
+  if (it == sv->requests.end()) return SP_ERR_INVALID_ARG;
+  Request* q = it->second;
+  const auto deadline = Clock::now() + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double>(timeout_s));
+  while (!q->done) {
+    if (timeout_s >= 0 && sv->cv_done.wait_until(lock, deadline) == std::cv_status::timeout && !q->done)
+      return SP_ERR_TIMEOUT;
+    if (timeout_s < 0) sv->cv_done.wait(lock);
+  }
+  const int st = q->status;
+  if (info) *info = q->info;
+  sv->requests.erase(it);
+  delete q;
+  return st;
+}
+
+extern "C" int sp_server_stats(sp_server* sv, sp_server_stats_t* out) {
+  if (!sv || !out) return SP_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(sv->mu);
+  std::memset(out, 0, sizeof(*out));
+  out->completed = sv->completed;
+  out->failed = sv->failed;
+  out->queued = (long long)sv->queue.size();
+  out->running_peak = sv->running_peak;
+  out->resident_plans = (int)sv->resident.size();
+  out->evictions = sv->evictions;
+  out->mem_peak_bytes = (double)sv->mem_peak;
+  if (!sv->latency_ms.empty()) {
+    std::vector<double> l(sv->latency_ms);
+    std::sort(l.begin(), l.end());
+    auto pct = [&](double q) {
+      const double pos = q * (double)(l.size() - 1);
+      const size_t a = (size_t)pos;
+      const size_t b = std::min(a + 1, l.size() - 1);
+      return l[a] + (pos - (double)a) * (l[b] - l[a]);
+    };
+    out->p50_ms = pct(0.50);
+    out->p99_ms = pct(0.99);
+    out->max_ms = l.back();
+    const double span = std::chrono::duration<double>(sv->t_last - sv->t_first).count();
+    out->zones_per_s = span > 0 ? sv->zones_done / span : 0.0;
+  }
+  return SP_OK;
+}
+
+extern "C" int sp_server_destroy(sp_server* sv) {
+  if (!sv) return SP_OK;
+  {
+    std::lock_guard<std::mutex> lock(sv->mu);
+    sv->stopping = true;
+  }
+  sv->cv_work.notify_all();
+  for (auto& t : sv->workers) t.join();
+  DeviceScope dev(sv->device);
+  for (auto& kv : sv->resident) {
+    for (sp_plan* c : kv.second.idle) sp_plan_destroy(c);
+    if (kv.second.master) sp_plan_destroy(kv.second.master);
+  }
+  for (auto& kv : sv->requests) delete kv.second;
+  delete sv;
+  return SP_OK;
+}

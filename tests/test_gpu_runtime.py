@@ -1,0 +1,134 @@
+"""Plan clones, batched solves and the continuous-batching server.
+
+Every instance solved in a batch or in the server's mix must equal the same problem
+solved alone on its own plan (bitwise: the kernel path is identical), and stay within
+the precision's tolerance of the oracle."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import sph_poisson as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1806_06623_gb300 as S
+    S.lib()
+    return S
+
+
+def alone(S, p, precision):
+    plan = S.Plan(p.r_if, p.th_if, p.nphi, outer_bc=p.outer_bc, precision=precision)
+    phi, info = plan.solve(torch.from_numpy(p.rho).cuda())
+    torch.cuda.synchronize()
+    return phi.cpu().numpy(), info
+
+
+def test_clone_shares_tables_and_matches(S):
+    p = W.stellar_noise()
+    for prec in (S.SP_FP64, S.SP_MIXED_BF16X6):
+        plan = S.Plan(p.r_if, p.th_if, p.nphi, precision=prec)
+        clone = plan.clone()
+        rho = torch.from_numpy(p.rho).cuda()
+        a, _ = plan.solve(rho)
+        plan.close()                       # the clone keeps the shared tables alive
+        b, _ = clone.solve(rho)
+        torch.cuda.synchronize()
+        assert torch.equal(a, b)
+        clone.close()
+
+
+def test_batched_matches_alone_ragged(S):
+    probs = [W.ragged_instance(i) for i in range(6)] + [W.sphere_blob()]
+    precs = [S.SP_MIXED_BF16X6, S.SP_FP64, S.SP_MIXED_BF16X3, S.SP_MIXED_BF16X6, S.SP_FP64, S.SP_MIXED_BF16X6,
+             S.SP_FP64]
+    plans = [S.Plan(p.r_if, p.th_if, p.nphi, precision=q) for p, q in zip(probs, precs)]
+    rhos = [torch.from_numpy(p.rho).cuda() for p in probs]
+    phis = [torch.empty_like(r) for r in rhos]
+    infos = S.sp_solve_batched(plans, rhos, phis)
+    torch.cuda.synchronize()
+    for p, q, phi, info in zip(probs, precs, phis, infos):
+        ref_alone, info_alone = alone(S, p, q)
+        assert info.status == S.SP_OK
+        assert np.array_equal(phi.cpu().numpy(), ref_alone)
+        assert info.iterations == info_alone.iterations
+    # two of them against the oracle
+    for k in (0, 6):
+        p = probs[k]
+        ref = O.solve_exact(O.Geometry(p.r_if, p.th_if, p.nphi), p.rho)
+        err = np.max(np.abs(phis[k].cpu().numpy() - ref)) / np.max(np.abs(ref))
+        assert err <= (1e-10 if precs[k] != S.SP_FP64 else 1e-12)
+
+
+def test_batched_rejects_shared_plan(S):
+    p = W.random_small(8, 8, 8, seed=1)
+    plan = S.Plan(p.r_if, p.th_if, p.nphi)
+    r = torch.from_numpy(p.rho).cuda()
+    with pytest.raises(S.SpError):
+        S.sp_solve_batched([plan, plan], [r, r], [torch.empty_like(r), torch.empty_like(r)])
+
+
+def test_server_mix_equals_alone(S):
+    # several grids, repeated grids (resident plans), both precisions, interleaved
+    specs = []
+    for i in range(12):
+        p = W.ragged_instance(i % 5)
+        prec = S.SP_MIXED_BF16X6 if i % 3 else S.SP_FP64
+        specs.append((p, prec))
+    srv = S.sp_server_create(8 << 30, 4)
+    try:
+        outs, tickets, keep = [], [], []
+        for p, prec in specs:
+            out = np.empty_like(p.rho)
+            t, k = S.sp_server_submit(srv, p.r_if, p.th_if, p.nphi, p.rho, out, precision=prec)
+            outs.append(out)
+            tickets.append(t)
+            keep.append(k)
+        for (p, prec), out, t in zip(specs, outs, tickets):
+            st, info = S.sp_server_wait(srv, t, 120.0)
+            assert st == S.SP_OK
+            ref_alone, _ = alone(S, p, prec)
+            assert np.array_equal(out, ref_alone)
+        stats = S.sp_server_stats(srv)
+        assert stats["completed"] == len(specs) and stats["failed"] == 0
+        assert stats["p50_ms"] > 0 and stats["p99_ms"] >= stats["p50_ms"]
+        assert stats["resident_plans"] >= 5
+    finally:
+        S.sp_server_destroy(srv)
+
+
+def test_server_evicts_under_a_small_budget(S):
+    probs = [W.ragged_instance(i) for i in range(4)]
+    srv = S.sp_server_create(256 << 20, 1)   # one slot: plans of earlier grids must make room
+    try:
+        for p in probs + probs[:2]:
+            out = np.empty_like(p.rho)
+            t, _ = S.sp_server_submit(srv, p.r_if, p.th_if, p.nphi, p.rho, out, precision=S.SP_MIXED_BF16X6)
+            st, _ = S.sp_server_wait(srv, t, 120.0)
+            assert st == S.SP_OK
+            ref_alone, _ = alone(S, p, S.SP_MIXED_BF16X6)
+            assert np.array_equal(out, ref_alone)
+        stats = S.sp_server_stats(srv)
+        assert stats["evictions"] >= 1
+    finally:
+        S.sp_server_destroy(srv)
+
+
+def test_server_wait_timeout_then_completes(S):
+    p = W.stellar_sh()
+    srv = S.sp_server_create(8 << 30, 1)
+    try:
+        out = np.empty_like(p.rho)
+        t, _ = S.sp_server_submit(srv, p.r_if, p.th_if, p.nphi, p.rho, out, precision=S.SP_FP64)
+        st, _ = S.sp_server_wait(srv, t, 0.0)
+        assert st in (S.SP_ERR_TIMEOUT, S.SP_OK)
+        if st == S.SP_ERR_TIMEOUT:
+            st, _ = S.sp_server_wait(srv, t, 120.0)
+        assert st == S.SP_OK
+    finally:
+        S.sp_server_destroy(srv)
