@@ -41,6 +41,9 @@ def parse():
                     help="headline arithmetic: mixed = 6-product split bf16 (default), mixed_x3 = 3-product")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-oracle-check", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 64-instance ragged batch")
+    ap.add_argument("--no-served", action="store_true", help="skip the served Poisson-arrival stream")
+    ap.add_argument("--served-requests", type=int, default=400)
     return ap.parse_args()
 
 
@@ -267,6 +270,10 @@ def run_ours(args, rank, world, local):
         line[f"{name}_zones_per_s"] = zones * args.steps * world / (rr["ms"] / 1e3)
         line[f"{name}_ms_per_step"] = rr["ms"] / args.steps
     line["roofline"] = roofline(r["timing"], p, precision)
+    if not args.no_batched:
+        line["batched"] = run_batched(S, W, torch, dev, check=not args.no_oracle_check)
+    if not args.no_served:
+        line["served"] = run_served(S, W, torch, args.served_requests)
     if not args.no_oracle_check:
         line["error_vs_oracle"] = check_vs_oracle(p, {k: v["phi"] for k, v in results.items()})
     if not args.no_cpu_baseline and args.gpus == 1:
@@ -275,6 +282,99 @@ def run_ours(args, rank, world, local):
                                 "sample": f"{n} full float64 oracle solves of the workload in {el:.1f} s "
                                           "(NumPy FFT and Thomas single-threaded, BLAS matmul multi-threaded)"}
     print(json.dumps(line), flush=True)
+
+
+def run_batched(S, W, torch, dev, check=True, n=64, reps=3):
+    """64 independent ragged solves (Nr in [64,512], Ntheta in {32,64,96,128}, Nphi = 2 Ntheta)
+    as one sp_solve_batched call; zones/s for float64 and the 6-product mixed mode."""
+    probs = W.ragged_batch(n)
+    zones = sum(p.zones for p in probs)
+    rhos = [torch.from_numpy(p.rho).to(dev) for p in probs]
+    out = {"workload": f"ragged_batch: {n} instances, {zones} zones", "instances": n, "zones": zones}
+    for name, prec in (("fp64", S.SP_FP64), ("mixed", S.SP_MIXED_BF16X6)):
+        plans = [S.Plan(p.r_if, p.th_if, p.nphi, precision=prec, tol=1e-10) for p in probs]
+        phis = [torch.empty_like(r) for r in rhos]
+        S.sp_solve_batched(plans, rhos, phis)          # warm-up (workspaces, module load)
+        torch.cuda.synchronize(dev)
+        ts = []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            infos = S.sp_solve_batched(plans, rhos, phis)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = statistics.median(ts)
+        d = {"ms_per_batch": ms, "zones_per_s": zones / (ms / 1e3),
+             "max_est_rel_error": max(i.est_rel_error for i in infos),
+             "iterations": sorted({int(i.iterations) for i in infos})}
+        if check:
+            from oracle import sph_poisson as O
+            errs = []
+            for k in (0, 17, 40):
+                q = probs[k]
+                ref = O.solve_exact(O.Geometry(q.r_if, q.th_if, q.nphi), q.rho)
+                errs.append(float(np.max(np.abs(phis[k].cpu().numpy() - ref)) / np.max(np.abs(ref))))
+            d["max_rel_err_vs_oracle_sample"] = max(errs)
+        out[name] = d
+        for pl in plans:
+            pl.close()
+    return out
+
+
+def run_served(S, W, torch, n_requests, rates=(200.0, 2000.0, 20000.0)):
+    """Poisson arrivals of solves: 90% one of the 64 ragged-batch instances, 10% the
+    550x128x256 workload; 40 GB device-memory budget, resident plans, 8 slots; host
+    buffers page-locked as a serving client would keep them.  p50/p99 latency from
+    submission to completion, and zones/s."""
+    probs = {k: W.ragged_instance(k) for k in range(64)}
+    probs[-1] = W.stellar_sh()
+    pin = {}
+    for k, p in probs.items():
+        rho = torch.from_numpy(p.rho).pin_memory().numpy()
+        outs = [torch.empty(p.rho.shape, dtype=torch.float64).pin_memory().numpy() for _ in range(4)]
+        pin[k] = (rho, outs)
+    out = {"workload": f"served_stream: {n_requests} Poisson arrivals, 90% from the 64 ragged-batch instances, "
+                       f"10% 550x128x256; 40 GB budget, 8 slots, page-locked host buffers"}
+    for name, prec in (("mixed", S.SP_MIXED_BF16X6), ("fp64", S.SP_FP64)):
+        for rate in rates:
+            if name == "fp64" and rate != rates[0]:
+                continue
+            srv = S.sp_server_create(40 << 30, 8)
+            try:
+                for k, p in probs.items():          # make every grid's plan resident (not measured)
+                    t, _ = S.sp_server_submit(srv, p.r_if, p.th_if, p.nphi, pin[k][0], pin[k][1][0], precision=prec)
+                    S.sp_server_wait(srv, t, 300.0)
+                S.sp_server_reset_stats(srv)
+                arr = W.served_stream(n_requests, rate_hz=rate, seed=5)
+                use = {k: 0 for k in probs}
+                tickets = []
+                t0 = time.perf_counter()
+                for rq in arr:
+                    now = time.perf_counter() - t0
+                    if rq["t"] > now:
+                        time.sleep(rq["t"] - now)
+                    k = rq["problem"]
+                    p = probs[k]
+                    buf = pin[k][1][use[k] % 4]
+                    use[k] += 1
+                    t, _ = S.sp_server_submit(srv, p.r_if, p.th_if, p.nphi, pin[k][0], buf, precision=prec)
+                    tickets.append(t)
+                fails = {}
+                for t in tickets:
+                    st, _ = S.sp_server_wait(srv, t, 300.0)
+                    if st != S.SP_OK:
+                        fails[S.sp_status_string(st)] = fails.get(S.sp_status_string(st), 0) + 1
+                st_ = S.sp_server_stats(srv)
+                out[f"{name}@{int(rate)}/s"] = {"p50_ms": st_["p50_ms"], "p99_ms": st_["p99_ms"],
+                                                "max_ms": st_["max_ms"], "zones_per_s": st_["zones_per_s"],
+                                                "completed": st_["completed"], "failed": fails,
+                                                "running_peak": st_["running_peak"],
+                                                "evictions": st_["evictions"]}
+            finally:
+                S.sp_server_destroy(srv)
+    return out
 
 
 def roofline(timing, p, precision):

@@ -218,6 +218,8 @@ int sp_server_submit(sp_server* server, const double* r_interfaces, int Nr, cons
  * SP_ERR_TIMEOUT (the ticket stays valid).  A completed ticket is released. */
 int sp_server_wait(sp_server* server, long long ticket, double timeout_s, sp_solve_info* info);
 int sp_server_stats(sp_server* server, sp_server_stats_t* out);
+/* Forget the latency and throughput record (for instance after warming resident plans). */
+int sp_server_reset_stats(sp_server* server);
 /* Finishes queued and running requests, then releases everything. */
 int sp_server_destroy(sp_server* server);
 

@@ -71,6 +71,7 @@ _SIGS = {
     "sp_server_wait": (C.c_int, [C.c_void_p, C.c_longlong, C.c_double, C.POINTER(SolveInfo)]),
     "sp_server_stats": (C.c_int, [C.c_void_p, C.POINTER(ServerStats)]),
     "sp_server_destroy": (C.c_int, [C.c_void_p]),
+    "sp_server_reset_stats": (C.c_int, [C.c_void_p]),
     "sp_plan_workspace_bytes": (C.c_size_t, [C.c_void_p]),
     "sp_plan_set_workspace": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "sp_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(SolveInfo)]),
@@ -213,6 +214,10 @@ def sp_server_stats(server):
     s = ServerStats()
     _check(lib().sp_server_stats(server, C.byref(s)), "sp_server_stats")
     return s.as_dict()
+
+
+def sp_server_reset_stats(server):
+    _check(lib().sp_server_reset_stats(server), "sp_server_reset_stats")
 
 
 def sp_server_destroy(server):

@@ -241,7 +241,7 @@ size_t theta_eigen_smem(int nth, bool parity) {
 cudaError_t theta_eigen(const Plan& p, cudaStream_t s) {
   const int nth = p.nth;
   const size_t smem = theta_eigen_smem(nth, p.parity);
-  cudaError_t e = cudaFuncSetAttribute(k_theta_eigen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_smem(k_theta_eigen, smem);
   if (e != cudaSuccess) return e;
   int threads = ((nth + 31) / 32) * 32;
   if (threads < 32) threads = 32;

@@ -381,7 +381,7 @@ size_t fft_smem(int n, int lpc) {
 
 template <typename K>
 cudaError_t prep(K kern, size_t smem) {
-  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return allow_smem(kern, smem);
 }
 
 }  // namespace

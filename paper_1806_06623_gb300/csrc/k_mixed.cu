@@ -499,7 +499,7 @@ cudaError_t tc_project_np(const Plan& p, bool inverse, cudaStream_t s) {
   }
   tc::Params prm{x.d32, p.nth, 2 * p.nr, (p.nth + tc::kKBlk - 1) / tc::kKBlk, p.d_err};
   constexpr uint32_t smem = tc::smem_bytes<NP>();
-  cudaError_t e = cudaFuncSetAttribute(tc::k_tc_gemm_split<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_smem(tc::k_tc_gemm_split<NP>, smem);
   if (e != cudaSuccess) return e;
   dim3 grid((2 * p.nr + tc::Cfg<NP>::BN - 1) / tc::Cfg<NP>::BN, p.mh);
   tc::k_tc_gemm_split<NP><<<grid, 128, smem, s>>>(maps, prm);

@@ -169,6 +169,16 @@ cudaError_t timed_launch(Plan& p, int id, cudaStream_t s, F&& launch) {
   return e;
 }
 
+// Allow `kernel` up to `bytes` of dynamic shared memory.  The attribute is raised once
+// per kernel to the device's opt-in maximum and never lowered, so concurrent launches of
+// the same kernel for different plan sizes (several host threads) cannot undercut each
+// other.  Returns cudaErrorInvalidValue when `bytes` exceeds what the device allows.
+cudaError_t allow_dynamic_smem(const void* kernel, size_t bytes);
+template <typename K>
+cudaError_t allow_smem(K* kernel, size_t bytes) {
+  return allow_dynamic_smem(reinterpret_cast<const void*>(kernel), bytes);
+}
+
 size_t workspace_bytes(const Plan& p);
 void bind_workspace(Plan& p, void* base);
 

@@ -2,6 +2,8 @@
 // workspace management and the float64 solve sequence of Sect. 3.2.
 #include <cmath>
 #include <cstdio>
+#include <mutex>
+#include <unordered_map>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -721,6 +723,32 @@ size_t plan_table_bytes(const Plan& p) {
          (size_t)p.nr * (sizeof(RadialRowF) + sizeof(RadialRowFF) + sizeof(float)) + (size_t)x.nlow * p.nr * 16;
   }
   return b;
+}
+
+}  // namespace sp
+
+namespace sp {
+
+cudaError_t allow_dynamic_smem(const void* kernel, size_t bytes) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, size_t> allowed;   // kernel -> dynamic bytes allowed
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const void* key = reinterpret_cast<const void*>(reinterpret_cast<uintptr_t>(kernel) ^ ((uintptr_t)dev << 56));
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = allowed.find(key);
+  if (it == allowed.end()) {
+    int optin = 0;
+    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    if ((e = cudaFuncGetAttributes(&fa, kernel)) != cudaSuccess) return e;
+    const size_t dyn = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+    if ((e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn)) != cudaSuccess)
+      return e;
+    it = allowed.emplace(key, dyn).first;
+  }
+  return bytes <= it->second ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 }  // namespace sp

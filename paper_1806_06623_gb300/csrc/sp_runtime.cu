@@ -235,6 +235,19 @@ struct sp_server {
 };
 
 bool sp_server::evict_for(size_t need) {
+  // idle clones first (their workspaces), least recently used grids first
+  while (mem_used + need > budget) {
+    auto victim = resident.end();
+    for (auto it = resident.begin(); it != resident.end(); ++it) {
+      if (it->second.idle.empty()) continue;
+      if (victim == resident.end() || it->second.last_used < victim->second.last_used) victim = it;
+    }
+    if (victim == resident.end()) break;
+    sp_plan_destroy(victim->second.idle.back());
+    victim->second.idle.pop_back();
+    mem_used -= victim->second.clone_bytes;
+  }
+  // then whole plans nobody uses
   while (mem_used + need > budget) {
     auto victim = resident.end();
     for (auto it = resident.begin(); it != resident.end(); ++it) {
@@ -505,6 +518,17 @@ extern "C" int sp_server_stats(sp_server* sv, sp_server_stats_t* out) {
     const double span = std::chrono::duration<double>(sv->t_last - sv->t_first).count();
     out->zones_per_s = span > 0 ? sv->zones_done / span : 0.0;
   }
+  return SP_OK;
+}
+
+extern "C" int sp_server_reset_stats(sp_server* sv) {
+  if (!sv) return SP_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(sv->mu);
+  sv->latency_ms.clear();
+  sv->zones_done = 0.0;
+  sv->completed = sv->failed = 0;
+  sv->running_peak = sv->running;
+  sv->have_first = false;
   return SP_OK;
 }
 

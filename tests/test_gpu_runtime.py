@@ -132,3 +132,29 @@ def test_server_wait_timeout_then_completes(S):
         assert st == S.SP_OK
     finally:
         S.sp_server_destroy(srv)
+
+
+def test_server_burst_of_mixed_sizes_all_succeed(S):
+    """Many requests of different grids at once: slots run different plan sizes
+    concurrently (shared-memory attributes, plan building and clones race here)."""
+    probs = [W.ragged_instance(i) for i in range(8)] + [W.random_small(40, 32, 6, seed=3),
+                                                     W.random_small(70, 96, 48, seed=4)]
+    srv = S.sp_server_create(16 << 30, 8)
+    try:
+        outs, tickets = [], []
+        for rep in range(4):
+            for k, p in enumerate(probs):
+                prec = (S.SP_MIXED_BF16X6, S.SP_FP64, S.SP_MIXED_BF16X3)[(k + rep) % 3]
+                out = np.empty_like(p.rho)
+                t, _ = S.sp_server_submit(srv, p.r_if, p.th_if, p.nphi, p.rho, out, precision=prec)
+                outs.append((p, prec, out))
+                tickets.append(t)
+        for (p, prec, out), t in zip(outs, tickets):
+            st, _ = S.sp_server_wait(srv, t, 300.0)
+            assert st == S.SP_OK, S.sp_status_string(st)
+        for p, prec, out in outs[:10]:
+            ref_alone, _ = alone(S, p, prec)
+            assert np.array_equal(out, ref_alone)
+        assert S.sp_server_stats(srv)["failed"] == 0
+    finally:
+        S.sp_server_destroy(srv)

@@ -24,8 +24,8 @@ Workload recipes (all densities sampled at cell centres, G = 1):
 * ``ragged_batch`` 64 instances, Nr uniform in [64,512], Ntheta in
   {32,64,96,128}, Nphi = 2 Ntheta, profile core radius uniform in
   [0.05,0.2] and one point-mass zone (1% of the mass) at a random position.
-* ``served_stream`` Poisson arrivals (mean 200/s); 90% drawn from the ragged
-  size mix, 10% at 550x128x256.
+* ``served_stream`` Poisson arrivals (mean 200/s); 90% of the requests solve one of
+  the 64 ragged-batch instances, 10% the 550x128x256 stellar workload.
 
 The log-stretched radial grid has an origin cell: r_{1/2} = 0 and
 r_{i+1/2} = 10^(-3 + 3 (i-1)/(Nr-1)) for i = 1..Nr, so it spans [1e-3, 1]
@@ -231,22 +231,20 @@ def ragged_batch(n: int = 64, base_seed: int = 4):
 
 
 def served_stream(n_requests: int, rate_hz: float = 200.0, seed: int = 5,
-                  big_fraction: float = 0.1):
-    """Arrival times (s) and request sizes for the served workload.
+                  big_fraction: float = 0.1, n_grids: int = 64):
+    """Arrival times (s) and problems of the served workload: Poisson arrivals; 90% of
+    the requests solve one of the ``n_grids`` ragged-batch instances (their grids and
+    densities), 10% the 550x128x256 stellar workload.
 
-    Returns a list of dicts with keys ``t`` (arrival time), ``shape``
-    (Nr, Ntheta, Nphi) and ``seed`` (per-request density seed)."""
+    Returns a list of dicts with keys ``t`` (arrival time) and ``problem`` (an index
+    into the ragged batch, or -1 for the 550x128x256 workload)."""
     rng = np.random.default_rng(seed)
     gaps = rng.exponential(1.0 / rate_hz, size=n_requests)
     t = np.cumsum(gaps) - gaps[0]
     out = []
     for q in range(n_requests):
-        if rng.uniform() < big_fraction:
-            shape = (550, 128, 256)
-        else:
-            nth = int(RAGGED_NTHETA[int(rng.integers(0, len(RAGGED_NTHETA)))])
-            shape = (int(rng.integers(64, 513)), nth, 2 * nth)
-        out.append({"t": float(t[q]), "shape": shape, "seed": int(rng.integers(0, 2**31 - 1))})
+        big = rng.uniform() < big_fraction
+        out.append({"t": float(t[q]), "problem": -1 if big else int(rng.integers(0, n_grids))})
     return out
 
 
