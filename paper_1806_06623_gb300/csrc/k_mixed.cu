@@ -196,6 +196,202 @@ __global__ void __launch_bounds__(32) k_thomas_staged(const float* __restrict__ 
   cp_async_wait<0>();
 }
 
+// Radial solves of the low-precision solve as segmented scans.  With the factors
+// precomputed, the forward sweep d_i = b_i + a_i d_{i-1} (b_i = x_i/piv_i,
+// a_i = -sub_i/piv_i) and the back substitution f_i = d_i - c'_i f_{i+1} are first-order
+// linear recurrences.  One CTA per (m, re/im, kScanCols consecutive l): the column
+// block's rows are first staged in shared memory with cp.async (all rows in flight at
+// once), then each of kScanSegs thread groups sweeps one radial segment from a zero
+// start while recording the running product of the coefficients; the first group
+// chains the segment carries and every group adds carry x product to its rows.  The
+// forward values stay in shared memory for the back substitution.  All coefficients
+// are contractive (|a_i|, |c'_i| < 1 for these diagonally dominant systems), so the
+// reassociation does not amplify rounding.  Lanes of near-singular modes idle; the
+// leading CTAs solve those in float64 with the same segmented scan (one warp per mode
+// and component, 32 segments, carries by a shuffle scan), concurrently with the rest.
+constexpr int kScanCols = 16;
+constexpr int kScanThreads = 256;
+constexpr int kScanSegs = kScanThreads / kScanCols;
+
+// float32 CTAs: D, Q [nr][kScanCols] + sub [nr] floats; float64 CTAs: 8 warps x 2 x nr doubles
+size_t scan_smem_bytes(int nr) {
+  const size_t f32 = (2 * (size_t)nr * kScanCols + (size_t)nr) * sizeof(float);
+  const size_t f64 = (size_t)(kScanThreads / 32) * 2 * nr * sizeof(double);
+  return f32 > f64 ? f32 : f64;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_thomas_scan(
+    const float* __restrict__ sub_r, const double* __restrict__ lam, const float* __restrict__ x,
+    const float* __restrict__ fcp, const float* __restrict__ finv, Planes pl, int nr, int nth, int kstride,
+    double thr, int nlowblk, const int* __restrict__ low_idx, int nlow, const RadialRow* __restrict__ rad64,
+    const double2* __restrict__ low_fac) {
+  extern __shared__ __align__(16) float sm[];
+  float* D = sm;                            // [nr][kScanCols] right-hand side, then d, then f
+  float* Q = sm + (size_t)nr * kScanCols;   // [nr][kScanCols] 1/pivot or c', then running products
+  float* A = Q + (size_t)nr * kScanCols;    // [nr] sub-diagonal
+  __shared__ float sE[kScanSegs][kScanCols], sP[kScanSegs][kScanCols], sC[kScanSegs][kScanCols];
+  const int tid = threadIdx.x;
+  const size_t st = 2 * (size_t)nth;
+  if ((int)blockIdx.x < nlowblk) {
+    // ---- float64 near-singular modes: warp pair (re, im) per mode, same segmented scan
+    // over the warp's 32 lanes, carries by a shuffle scan of the affine segment maps
+    const int warp = tid >> 5, lane = tid & 31;
+    const int q = (int)blockIdx.x * (kScanThreads / 64) + (warp >> 1);
+    const int cc = warp & 1;
+    if (q >= nlow) return;
+    const int t = low_idx[q];
+    const int m = t / nth;
+    const int l = t - m * nth;
+    const float* X = x + (size_t)m * nr * st + (size_t)cc * nth + l;
+    const double2* F = low_fac + (size_t)q * nr;   // (c'_i, 1/pivot_i)
+    double* Wd = reinterpret_cast<double*>(sm) + (size_t)warp * 2 * nr;
+    double* Wq = Wd + nr;
+    for (int i = lane; i < nr; i += 32) {
+      Wd[i] = (double)X[(size_t)i * st];
+      Wq[i] = F[i].y;
+    }
+    __syncwarp();
+    int Ll = (nr + 31) / 32;
+    Ll += (Ll & 1) ^ 1;
+    const int j0 = min(nr, lane * Ll), j1 = min(nr, j0 + Ll);
+    double v = 0.0, pr = 1.0;
+    for (int i = j0; i < j1; ++i) {
+      const double a = -rad64[i].sub * Wq[i];
+      v = fma(a, v, Wd[i] * Wq[i]);
+      pr *= a;
+      Wd[i] = v;
+      Wq[i] = pr;
+    }
+    for (int off = 1; off < 32; off <<= 1) {
+      const double e2 = __shfl_up_sync(0xffffffffu, v, off), p2 = __shfl_up_sync(0xffffffffu, pr, off);
+      if (lane >= off) {
+        v = fma(pr, e2, v);
+        pr *= p2;
+      }
+    }
+    double carry = __shfl_up_sync(0xffffffffu, v, 1);
+    if (lane == 0) carry = 0.0;
+    for (int i = j0; i < j1; ++i) Wd[i] = fma(Wq[i], carry, Wd[i]);
+    __syncwarp();
+    for (int i = lane; i < nr; i += 32) Wq[i] = F[i].x;
+    __syncwarp();
+    v = 0.0;
+    pr = 1.0;
+    for (int i = j1 - 1; i >= j0; --i) {
+      const double g = -Wq[i];
+      v = fma(g, v, Wd[i]);
+      pr *= g;
+      Wd[i] = v;
+      Wq[i] = pr;
+    }
+    for (int off = 1; off < 32; off <<= 1) {
+      const double e2 = __shfl_down_sync(0xffffffffu, v, off), p2 = __shfl_down_sync(0xffffffffu, pr, off);
+      if (lane + off < 32) {
+        v = fma(pr, e2, v);
+        pr *= p2;
+      }
+    }
+    carry = __shfl_down_sync(0xffffffffu, v, 1);
+    if (lane == 31) carry = 0.0;
+    const size_t prow = (size_t)m * nr * 2 + cc;
+    for (int i = j0; i < j1; ++i) store_split(pl, (prow + 2 * i) * kstride + l, (float)fma(Wq[i], carry, Wd[i]));
+    return;
+  }
+  const int col = tid % kScanCols, seg = tid / kScanCols;
+  const int ncb = (nth + kScanCols - 1) / kScanCols;
+  const int bid = (int)blockIdx.x - nlowblk;
+  const int c = bid & 1;
+  const int mb = bid >> 1;
+  const int m = mb / ncb;
+  const int l = (mb - m * ncb) * kScanCols + col;
+  const bool valid = l < nth;
+  const bool work = valid && fabs(lam[m * nth + l]) >= thr;
+  const float* X = x + (size_t)m * nr * st + (size_t)c * nth + (valid ? l : 0);
+  const float* FC = fcp + (size_t)m * nr * nth + (valid ? l : 0);
+  const float* FI = finv + (size_t)m * nr * nth + (valid ? l : 0);
+  // segments of odd length: the two segments a warp holds then sit 16 banks apart
+  int L = (nr + kScanSegs - 1) / kScanSegs;
+  L += (L & 1) ^ 1;
+  const int i0 = min(nr, seg * L), i1 = min(nr, i0 + L);
+  // ---- stage the right-hand side and 1/pivot of the whole column block
+  if (valid)
+    for (int i = seg; i < nr; i += kScanSegs) {
+      cp_async4(&D[i * kScanCols + col], X + (size_t)i * st);
+      cp_async4(&Q[i * kScanCols + col], FI + (size_t)i * nth);
+    }
+  cp_async_commit();
+  for (int i = tid; i < nr; i += kScanThreads) A[i] = sub_r[i];
+  cp_async_wait<0>();
+  __syncthreads();
+  // ---- forward sweep of this segment from d = 0
+  float d = 0.f, q = 1.f;
+  if (work)
+    for (int i = i0; i < i1; ++i) {
+      const int o = i * kScanCols + col;
+      const float iv = Q[o];
+      const float a = -A[i] * iv;
+      d = fmaf(a, d, D[o] * iv);
+      q *= a;
+      D[o] = d;
+      Q[o] = q;
+    }
+  sE[seg][col] = d;
+  sP[seg][col] = q;
+  __syncthreads();
+  if (seg == 0) {
+    float carry = 0.f;   // d_{-1} = 0
+    for (int w = 0; w < kScanSegs; ++w) {
+      sC[w][col] = carry;
+      carry = fmaf(sP[w][col], carry, sE[w][col]);
+    }
+  }
+  __syncthreads();
+  if (work) {
+    const float cw = sC[seg][col];
+    for (int i = i0; i < i1; ++i) {
+      const int o = i * kScanCols + col;
+      D[o] = fmaf(Q[o], cw, D[o]);
+    }
+  }
+  __syncthreads();
+  // ---- stage c' over the running products, then back-substitute from f = 0
+  if (valid)
+    for (int i = seg; i < nr; i += kScanSegs) cp_async4(&Q[i * kScanCols + col], FC + (size_t)i * nth);
+  cp_async_commit();
+  cp_async_wait<0>();
+  __syncthreads();
+  float f = 0.f;
+  q = 1.f;
+  if (work)
+    for (int i = i1 - 1; i >= i0; --i) {
+      const int o = i * kScanCols + col;
+      const float g = -Q[o];
+      f = fmaf(g, f, D[o]);
+      q *= g;
+      D[o] = f;
+      Q[o] = q;
+    }
+  sE[seg][col] = f;   // value at the segment's first row from a zero start above it
+  sP[seg][col] = q;
+  __syncthreads();
+  if (seg == 0) {
+    float carry = 0.f;   // f_{nr} is absent
+    for (int w = kScanSegs - 1; w >= 0; --w) {
+      sC[w][col] = carry;
+      carry = fmaf(sP[w][col], carry, sE[w][col]);
+    }
+  }
+  __syncthreads();
+  if (work) {
+    const float cw = sC[seg][col];
+    const size_t prow = (size_t)m * nr * 2 + c;
+    for (int i = i0; i < i1; ++i) {
+      const int o = i * kScanCols + col;
+      store_split(pl, (prow + 2 * i) * kstride + l, fmaf(Q[o], cw, D[o]));
+    }
+  }
+}
+
 // float32 elimination factors of every (m,l) radial system, computed in float64.
 __global__ void k_radial_factors(const RadialRow* __restrict__ rad, const double* __restrict__ lam,
                                  const double* __restrict__ outer, int nr, int nth, int mh, float* __restrict__ fcp,
@@ -512,6 +708,17 @@ cudaError_t tc_project(const Plan& p, bool inverse, cudaStream_t s) {
 
 cudaError_t thomas_mixed(const Plan& p, cudaStream_t s) {
   const MixedTables& x = *p.mixed;
+  const size_t smem = scan_smem_bytes(p.nr);
+  if (smem <= 200 * 1024) {
+    const int nblk = 2 * p.mh * ((p.nth + kScanCols - 1) / kScanCols);
+    const int nlowblk = (x.nlow + kScanThreads / 64 - 1) / (kScanThreads / 64);
+    cudaError_t e = allow_smem(k_thomas_scan, smem);
+    if (e != cudaSuccess) return e;
+    k_thomas_scan<<<nlowblk + nblk, kScanThreads, smem, s>>>(
+        x.sub_r, p.d_lam, x.d32, x.fcp, x.finv, Planes{{x.pan[0], x.pan[1], x.pan[2]}, x.np}, p.nr, p.nth, x.kstride,
+        x.low_threshold, nlowblk, x.low_idx, x.nlow, p.d_rad, x.low_fac);
+    return cudaGetLastError();
+  }
   const int nblk = 2 * p.mh * ((p.nth + 31) / 32);
   const int nlowblk = x.nlow;   // one warp per float64 mode
   k_thomas_staged<<<nblk + nlowblk, 32, 0, s>>>(x.sub_r, p.d_lam, x.d32, x.fcp, x.finv,

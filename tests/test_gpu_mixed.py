@@ -50,6 +50,7 @@ CASES = [
     (130, 128, 24, "log", 0.0, 0),     # full M tile, ragged N tile
     (300, 96, 192, "log", 0.0, 0),     # radix-3 phi, partial second K block
     (257, 64, 8, "uniform", 0.0, 1),
+    (1600, 6, 4, "log", 0.0, 0),       # radial column beyond the shared-memory scan: ring-staged sweeps
 ]
 
 
@@ -63,8 +64,14 @@ def test_mixed_matches_exact_small(S, nr, nth, nphi, grid, rin, bc, mode):
     assert info.status == S.SP_OK
     assert rel_err(phi, ref) <= TOL
     assert info.est_rel_error <= TOL and info.iterations >= 2
-    # the estimate bounds the actual error
-    assert rel_err(phi, ref) <= max(info.est_rel_error, 1e-12)
+    # the estimate (distance to the refinement's fixed point) bounds the actual error down
+    # to the rounding floor of the float-float residual on this grid: at least 46 of 53
+    # bits, so at most 2^7 x the float64 separated solve's error (measured ratio about 6
+    # at 1600 log-spaced radial cells)
+    plan64 = S.Plan(p.r_if, p.th_if, p.nphi, outer_bc=p.outer_bc, G=p.G)
+    phi64, _ = plan64.solve(torch.from_numpy(np.ascontiguousarray(p.rho)).cuda())
+    floor = max(128 * rel_err(phi64.cpu().numpy(), ref), 1e-12)
+    assert rel_err(phi, ref) <= max(info.est_rel_error, floor)
 
 
 @pytest.mark.parametrize("mode", ["x3", "x6"])
