@@ -364,12 +364,15 @@ __global__ void __launch_bounds__(256) k_fft_inv(const T* __restrict__ spec, int
 }
 
 template <typename T>
-int lines_per_cta(int n) {
-  // two padded line buffers within ~100 KB (float) / ~140 KB (double), at most 32 lines
+int lines_per_cta(int n, int nlines) {
+  // two padded line buffers within ~100 KB (float) / ~140 KB (double), at most 32 lines;
+  // with few lines (one shell), fewer per CTA so that about two CTAs per SM have work
   const size_t budget = sizeof(T) == 4 ? 100000 : 140000;
   const size_t per_pair = 2 * (size_t)(n + 1) * 2 * sizeof(T);
   size_t pairs = budget / per_pair;
   if (pairs > 16) pairs = 16;
+  const size_t few = (size_t)nlines / (2 * 2 * 152);
+  if (pairs > few) pairs = few;
   if (pairs < 1) pairs = 1;
   return (int)(2 * pairs);
 }
@@ -388,7 +391,7 @@ cudaError_t prep(K kern, size_t smem) {
 
 cudaError_t fft_forward_f64(const Plan& p, const double* in, int nrs, double scale, double* spec, cudaStream_t s) {
   const int nlines = nrs * p.nth;
-  const int lpc = lines_per_cta<double>(p.nphi);
+  const int lpc = lines_per_cta<double>(p.nphi, nlines);
   const size_t smem = fft_smem<double>(p.nphi, lpc);
   auto kern = k_fft_fwd<double, double, kOutPlain>;
   cudaError_t e = prep(kern, smem);
@@ -400,7 +403,7 @@ cudaError_t fft_forward_f64(const Plan& p, const double* in, int nrs, double sca
 
 cudaError_t fft_inverse_f64(const Plan& p, const double* spec, int nrs, double* out, bool accumulate, cudaStream_t s) {
   const int nlines = nrs * p.nth;
-  const int lpc = lines_per_cta<double>(p.nphi);
+  const int lpc = lines_per_cta<double>(p.nphi, nlines);
   const size_t smem = fft_smem<double>(p.nphi, lpc);
   const int grid = (nlines + lpc - 1) / lpc;
   cudaError_t e;
@@ -419,7 +422,7 @@ cudaError_t fft_inverse_f64(const Plan& p, const double* spec, int nrs, double* 
 cudaError_t fft_forward_split(const Plan& p, const void* in, bool in_double, float scale, int kstride, Planes out,
                               cudaStream_t s) {
   const int nlines = p.nr * p.nth;
-  const int lpc = lines_per_cta<float>(p.nphi);
+  const int lpc = lines_per_cta<float>(p.nphi, nlines);
   const size_t smem = fft_smem<float>(p.nphi, lpc);
   const int grid = (nlines + lpc - 1) / lpc;
   cudaError_t e;
@@ -440,7 +443,7 @@ cudaError_t fft_forward_split(const Plan& p, const void* in, bool in_double, flo
 cudaError_t fft_inverse_update(const Plan& p, const float* spec, float* phi_hi, float* phi_lo, bool first,
                                unsigned int* red, cudaStream_t s) {
   const int nlines = p.nr * p.nth;
-  const int lpc = lines_per_cta<float>(p.nphi);
+  const int lpc = lines_per_cta<float>(p.nphi, nlines);
   const size_t smem = fft_smem<float>(p.nphi, lpc);
   auto kern = k_fft_inv<float, float, kInvPairUpdate>;
   cudaError_t e = prep(kern, smem);

@@ -458,55 +458,102 @@ __device__ __forceinline__ void ffd_acc(float& ah, float& al, float ph, float pe
 // is formed first, so products carry errors relative to the small differences, not to
 // |L||Phi|), stored as float32.  rho is split into a float pair with integer
 // operations; the multipole term of the last shell arrives precomputed in outer_shell
-// (float64, already scaled by 3 r_out^2/dV3_N).  One CTA per (j, i) phi line.
-__global__ void __launch_bounds__(256) k_residual_ff(const double* __restrict__ rho, const float* __restrict__ ph,
-                                                     const float* __restrict__ pl,
-                                                     const double* __restrict__ outer_shell, float* __restrict__ r,
-                                                     const RadialRowFF* __restrict__ rad,
-                                                     const ThetaRowFF* __restrict__ th, int nr, int nth, int nphi,
-                                                     int dirichlet, ff dir_coef, ff four_pi_g) {
+// (float64, already scaled by 3 r_out^2/dV3_N).
+// One CTA per (j, chunk of kResRows radial rows, block of phi columns); each thread
+// marches outward along its (j, k) column with the radial window in registers, so the
+// difference across face i+1/2 serves as the inner difference of row i+1 (negated,
+// exactly), and the phi neighbours come from the row's line staged in shared memory.
+constexpr int kResRows = 16;
+constexpr int kResThreads = 256;
+
+__global__ void __launch_bounds__(kResThreads) k_residual_ff(const double* __restrict__ rho,
+                                                             const float* __restrict__ ph,
+                                                             const float* __restrict__ pl,
+                                                             const double* __restrict__ outer_shell,
+                                                             float* __restrict__ r,
+                                                             const RadialRowFF* __restrict__ rad,
+                                                             const ThetaRowFF* __restrict__ th, int nr, int nth,
+                                                             int nphi, int dirichlet, ff dir_coef, ff four_pi_g) {
+  __shared__ float line[2][2][kResThreads + 2];   // [row parity][hi, lo][k - k0 + 1]
   const int j = blockIdx.x;
-  const int i = blockIdx.y;
+  const int i0 = blockIdx.y * kResRows, i1 = min(nr, i0 + kResRows);
+  const int t = threadIdx.x;
+  const int k0 = blockIdx.z * blockDim.x;
+  const int nk = min((int)blockDim.x, nphi - k0);   // columns of this CTA
+  const bool act = t < nk;
+  const int k = k0 + (act ? t : nk - 1);
+  const int kl = k0 == 0 ? nphi - 1 : k0 - 1;       // periodic halo columns
+  const int kr = k0 + nk == nphi ? 0 : k0 + nk;
   const size_t shell = (size_t)nth * nphi;
-  const size_t line = ((size_t)i * nth + j) * nphi;
-  const RadialRowFF rr = rad[i];
   const ThetaRowFF tr = th[j];
-  const bool has_im = i > 0, has_ip = i < nr - 1, has_jm = j > 0, has_jp = j < nth - 1;
-  for (int k = threadIdx.x; k < nphi; k += blockDim.x) {
-    const size_t idx = line + k;
-    const float ch = ph[idx], cl = pl[idx];
+  const bool has_jm = j > 0, has_jp = j < nth - 1;
+  const float* PH = ph + (size_t)j * nphi;
+  const float* PL = pl + (size_t)j * nphi;
+  size_t oc = (size_t)i0 * shell;
+  float ch = PH[oc + k], cl = PL[oc + k];
+  float mh = 0.f, ml = 0.f;   // Phi(i-1) - Phi(i)
+  if (i0 > 0) ffd_diff(PH[oc - shell + k], PL[oc - shell + k], ch, cl, mh, ml);
+  for (int i = i0; i < i1; ++i, oc += shell) {
+    float* bh = line[i & 1][0];
+    float* bl = line[i & 1][1];
+    if (act) {
+      bh[t + 1] = ch;
+      bl[t + 1] = cl;
+    }
+    if (t == 0) {
+      bh[0] = PH[oc + kl];
+      bl[0] = PL[oc + kl];
+      bh[nk + 1] = PH[oc + kr];
+      bl[nk + 1] = PL[oc + kr];
+    }
+    const bool has_ip = i < nr - 1;
+    float nh = 0.f, nl = 0.f, jmh = 0.f, jml = 0.f, jph = 0.f, jpl = 0.f;
+    if (has_ip) {
+      nh = PH[oc + shell + k];
+      nl = PL[oc + shell + k];
+    }
+    if (has_jm) {
+      jmh = PH[oc - nphi + k];
+      jml = PL[oc - nphi + k];
+    }
+    if (has_jp) {
+      jph = PH[oc + nphi + k];
+      jpl = PL[oc + nphi + k];
+    }
+    const double rv = rho[oc + (size_t)j * nphi + k];
+    const RadialRowFF rr = rad[i];
+    __syncthreads();
     float dh, dl, p, e;
     // radial fluxes
     float rh = 0.f, rl = 0.f;
-    if (has_im) {
-      ffd_diff(ph[idx - shell], pl[idx - shell], ch, cl, dh, dl);
-      ffd_mul(rr.sub, dh, dl, p, e);
+    if (i > 0) {
+      ffd_mul(rr.sub, mh, ml, p, e);
       rh = p;
       rl = e;
     }
     if (has_ip) {
-      ffd_diff(ph[idx + shell], pl[idx + shell], ch, cl, dh, dl);
+      ffd_diff(nh, nl, ch, cl, dh, dl);
       ffd_mul(rr.sup, dh, dl, p, e);
       ffd_acc(rh, rl, p, e);
+      mh = -dh;
+      ml = -dl;
     }
     // angular fluxes, scaled by R_i
     float ah = 0.f, al = 0.f;
     if (has_jm) {
-      ffd_diff(ph[idx - nphi], pl[idx - nphi], ch, cl, dh, dl);
+      ffd_diff(jmh, jml, ch, cl, dh, dl);
       ffd_mul(tr.tm, dh, dl, p, e);
       ah = p;
       al = e;
     }
     if (has_jp) {
-      ffd_diff(ph[idx + nphi], pl[idx + nphi], ch, cl, dh, dl);
+      ffd_diff(jph, jpl, ch, cl, dh, dl);
       ffd_mul(tr.tp, dh, dl, p, e);
       ffd_acc(ah, al, p, e);
     }
-    const size_t kp = (k + 1 == nphi) ? idx - k : idx + 1;
-    const size_t km = (k == 0) ? idx + (nphi - 1) : idx - 1;
     float qh, ql;
-    ffd_diff(ph[kp], pl[kp], ch, cl, qh, ql);
-    ffd_diff(ph[km], pl[km], ch, cl, dh, dl);
+    ffd_diff(bh[t + 2], bl[t + 2], ch, cl, qh, ql);
+    ffd_diff(bh[t], bl[t], ch, cl, dh, dl);
     ffd_acc(qh, ql, dh, dl);
     ffd_mul(tr.sphi, qh, ql, p, e);
     ffd_acc(ah, al, p, e);
@@ -514,20 +561,22 @@ __global__ void __launch_bounds__(256) k_residual_ff(const double* __restrict__ 
     fast_two_sum(ah, al, a.hi, a.lo);
     ffd_mul(rr.R, a.hi, a.lo, p, e);
     ffd_acc(rh, rl, p, e);
-    if (i == nr - 1) {
+    if (!has_ip) {
       if (dirichlet) {
         ffd_mul(dir_coef, ch, cl, p, e);
         ffd_acc(rh, rl, p, e);
       } else {
-        const ff o = d2ff(outer_shell[idx - (size_t)i * shell]);
+        const ff o = d2ff(outer_shell[(size_t)j * nphi + k]);
         ffd_acc(rh, rl, o.hi, o.lo);
       }
     }
-    const ff sv = ff_mul(four_pi_g, d2ff(rho[idx]));
+    const ff sv = ff_mul(four_pi_g, d2ff(rv));
     float th_, tl;
     two_sum(sv.hi, -rh, th_, tl);
     tl += sv.lo - rl;
-    r[idx] = th_ + tl;
+    if (act) r[oc + (size_t)j * nphi + k] = th_ + tl;
+    ch = nh;
+    cl = nl;
   }
 }
 
@@ -746,10 +795,10 @@ cudaError_t residual_ff(const Plan& p, const double* rho, cudaStream_t s) {
     if (e != cudaSuccess) return e;
   }
   (void)n;
-  const int tpb = p.nphi >= 256 ? 256 : ((p.nphi + 31) / 32) * 32;
-  k_residual_ff<<<dim3(p.nth, p.nr), tpb, 0, s>>>(rho, x.phi_hi, x.phi_lo, x.outer_shell, x.r32, x.radff, x.thff, p.nr,
-                                                 p.nth, p.nphi, p.outer_bc == SP_OUTER_DIRICHLET ? 1 : 0, x.dir_coef,
-                                                 x.four_pi_g);
+  const int tpb = p.nphi >= kResThreads ? kResThreads : ((p.nphi + 31) / 32) * 32;
+  const dim3 grid(p.nth, (p.nr + kResRows - 1) / kResRows, (p.nphi + tpb - 1) / tpb);
+  k_residual_ff<<<grid, tpb, 0, s>>>(rho, x.phi_hi, x.phi_lo, x.outer_shell, x.r32, x.radff, x.thff, p.nr, p.nth,
+                                     p.nphi, p.outer_bc == SP_OUTER_DIRICHLET ? 1 : 0, x.dir_coef, x.four_pi_g);
   return cudaGetLastError();
 }
 

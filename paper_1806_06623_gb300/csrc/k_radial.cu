@@ -81,30 +81,46 @@ __global__ void __launch_bounds__(256) k_stencil_f64(const double* __restrict__ 
   }
 }
 
-// y = outer[m] .* (HtW_m x) ; z = H_m y  for the two real columns (re, im) of shell m.
-__global__ void k_shell_kappa(const double* __restrict__ HtW, const double* __restrict__ H,
-                              const double* __restrict__ outer, const double* __restrict__ xin,
-                              double* __restrict__ zout, int nth) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* xs = reinterpret_cast<double*>(smem_raw);   // [2][nth]
-  double* ys = xs + 2 * nth;                          // [2][nth]
-  const int m = blockIdx.x;
+// Outer-shell operator of the multipole condition per m: O_m = H_m diag(outer_m) (H^T W)_m
+// (set-up; one CTA per (j, m) row, threads over j').
+__global__ void k_outer_operator(const double* __restrict__ HtW, const double* __restrict__ H,
+                                 const double* __restrict__ outer, double* __restrict__ O, int nth) {
+  const int j = blockIdx.x, m = blockIdx.y;
+  const double* Hm = H + ((size_t)m * nth + j) * nth;
   const double* A = HtW + (size_t)m * nth * nth;
-  const double* Hm = H + (size_t)m * nth * nth;
-  for (int t = threadIdx.x; t < 2 * nth; t += blockDim.x) xs[t] = xin[(size_t)m * 2 * nth + t];
-  __syncthreads();
-  for (int t = threadIdx.x; t < 2 * nth; t += blockDim.x) {
-    const int c = t / nth, l = t - c * nth;
+  const double* om = outer + (size_t)m * nth;
+  for (int jp = threadIdx.x; jp < nth; jp += blockDim.x) {
     double s = 0.0;
-    for (int j = 0; j < nth; ++j) s = fma(A[(size_t)l * nth + j], xs[c * nth + j], s);
-    ys[t] = s * outer[(size_t)m * nth + l];
+    for (int l = 0; l < nth; ++l) s = fma(Hm[l] * om[l], A[(size_t)l * nth + jp], s);
+    O[((size_t)m * nth + j) * nth + jp] = s;
   }
-  __syncthreads();
-  for (int t = threadIdx.x; t < 2 * nth; t += blockDim.x) {
-    const int c = t / nth, j = t - c * nth;
-    double s = 0.0;
-    for (int l = 0; l < nth; ++l) s = fma(Hm[(size_t)j * nth + l], ys[c * nth + l], s);
-    zout[(size_t)m * 2 * nth + t] = s;
+}
+
+// z_m = O_m x_m for the two real columns (re, im) of the outer shell's spectrum: one warp
+// per row j of O_m, lanes over j' (coalesced), shuffle reduction.
+constexpr int kShellRows = 8;
+__global__ void __launch_bounds__(32 * kShellRows) k_shell_apply(const double* __restrict__ O,
+                                                                 const double* __restrict__ xin,
+                                                                 double* __restrict__ zout, int nth) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m = blockIdx.y;
+  const int j = blockIdx.x * kShellRows + warp;
+  if (j >= nth) return;
+  const double* row = O + ((size_t)m * nth + j) * nth;
+  const double* x = xin + (size_t)m * 2 * nth;
+  double s0 = 0.0, s1 = 0.0;
+  for (int jp = lane; jp < nth; jp += 32) {
+    const double o = row[jp];
+    s0 = fma(o, x[jp], s0);
+    s1 = fma(o, x[nth + jp], s1);
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    s0 += __shfl_down_sync(0xffffffffu, s0, off);
+    s1 += __shfl_down_sync(0xffffffffu, s1, off);
+  }
+  if (lane == 0) {
+    zout[(size_t)m * 2 * nth + j] = s0;
+    zout[(size_t)m * 2 * nth + nth + j] = s1;
   }
 }
 
@@ -126,8 +142,13 @@ cudaError_t stencil_f64(const Plan& p, const double* phi, double* out, cudaStrea
 }
 
 cudaError_t shell_kappa_f64(const Plan& p, const double* in, double* out, cudaStream_t s) {
-  const size_t smem = sizeof(double) * 4 * (size_t)p.nth;
-  k_shell_kappa<<<p.mh, 128, smem, s>>>(p.d_HtW, p.d_H, p.d_outer, in, out, p.nth);
+  k_shell_apply<<<dim3((p.nth + kShellRows - 1) / kShellRows, p.mh), 32 * kShellRows, 0, s>>>(p.d_oshell, in, out,
+                                                                                           p.nth);
+  return cudaGetLastError();
+}
+
+cudaError_t outer_operator_f64(const Plan& p, cudaStream_t s) {
+  k_outer_operator<<<dim3(p.nth, p.mh), 128, 0, s>>>(p.d_HtW, p.d_H, p.d_outer, p.d_oshell, p.nth);
   return cudaGetLastError();
 }
 
@@ -135,9 +156,7 @@ cudaError_t outer_term_f64(const Plan& p, const double* phi, double* out, cudaSt
   const size_t off = (size_t)(p.nr - 1) * p.nth * p.nphi;
   cudaError_t e = fft_forward_f64(p, phi + off, 1, 1.0 / p.nphi, p.shell, s);
   if (e != cudaSuccess) return e;
-  const size_t smem = sizeof(double) * 4 * (size_t)p.nth;
-  k_shell_kappa<<<p.mh, 128, smem, s>>>(p.d_HtW, p.d_H, p.d_outer, p.shell, p.shell2, p.nth);
-  e = cudaGetLastError();
+  e = shell_kappa_f64(p, p.shell, p.shell2, s);
   if (e != cudaSuccess) return e;
   return fft_inverse_f64(p, p.shell2, 1, out + off, true, s);
 }

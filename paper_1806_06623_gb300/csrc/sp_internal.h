@@ -126,6 +126,7 @@ struct Plan {
   double* d_outer = nullptr;      // [mh][nth] outer diagonal term of the radial row N
   double* d_HtW = nullptr;        // [mh][l][j] (H^T W)_m
   double* d_H = nullptr;          // [mh][j][l] H_m
+  double* d_oshell = nullptr;     // [mh][j][j'] H_m diag(outer_m) (H^T W)_m (multipole only)
   int* d_err = nullptr;           // device status word
 
   // workspace (plan-owned or caller-provided)
@@ -201,6 +202,7 @@ cudaError_t stencil_f64(const Plan& p, const double* phi, double* out, cudaStrea
 cudaError_t outer_term_f64(const Plan& p, const double* phi, double* out, cudaStream_t s);
 // out[m] = H_m diag(outer[m]) (H^T W)_m in[m] for the two real columns of one shell spectrum.
 cudaError_t shell_kappa_f64(const Plan& p, const double* in, double* out, cudaStream_t s);
+cudaError_t outer_operator_f64(const Plan& p, cudaStream_t s);
 // theta eigensolve for every m; writes lam, kappa, outer, H, HtW.
 cudaError_t theta_eigen(const Plan& p, cudaStream_t s);
 

@@ -83,6 +83,7 @@ void free_tables(Plan* p) {
     cudaFree(p->d_outer);
     cudaFree(p->d_HtW);
     cudaFree(p->d_H);
+    cudaFree(p->d_oshell);
     if (p->mixed) sp::mixed_free_shared(*p->mixed);
     delete p->table_refs;
   }
@@ -514,6 +515,10 @@ int sp_plan_create(const double* r_if, int nr, const double* th_if_in, int nth, 
       break;
     }
     if (herr) { st = SP_ERR_DEVICE_CHECK; break; }
+    if (outer_bc == SP_OUTER_MULTIPOLE) {
+      if (cudaMalloc(&p->d_oshell, sizeof(double) * mat) != cudaSuccess) { st = SP_ERR_OOM; break; }
+      if ((st = launch_status(sp::outer_operator_f64(*p, s)))) break;
+    }
     if (precision != SP_FP64 && (st = sp::mixed_create_tables(*p, s))) break;
     if (precision != SP_FP64 && cudaMallocHost(&p->h_red, 4 * sizeof(unsigned int)) != cudaSuccess) {
       st = SP_ERR_OOM;
@@ -715,7 +720,7 @@ namespace sp {
 // Device bytes of the tables a plan shares with its clones.
 size_t plan_table_bytes(const Plan& p) {
   const size_t tab = (size_t)p.mh * p.nth;
-  size_t b = 2 * tab * p.nth * sizeof(double) + 3 * tab * sizeof(double) + (size_t)p.nr * sizeof(RadialRow) +
+  size_t b = (p.d_oshell ? 3 : 2) * tab * p.nth * sizeof(double) + 3 * tab * sizeof(double) + (size_t)p.nr * sizeof(RadialRow) +
              (size_t)p.nth * sizeof(ThetaRow) + 2 * (size_t)p.nphi * (sizeof(double) + sizeof(float)) + tab * sizeof(double);
   if (p.mixed) {
     const MixedTables& x = *p.mixed;
