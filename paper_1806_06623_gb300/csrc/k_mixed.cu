@@ -742,12 +742,17 @@ cudaError_t tc_project_np(const Plan& p, bool inverse, cudaStream_t s) {
     std::memcpy(&maps.a[q], inverse ? x.map_Ai[q] : x.map_Af[q], sizeof(CUtensorMap));
     std::memcpy(&maps.b[q], x.map_B[q], sizeof(CUtensorMap));
   }
-  tc::Params prm{x.d32, p.nth, 2 * p.nr, (p.nth + tc::kKBlk - 1) / tc::kKBlk, p.d_err};
+  // one CTA per SM: split an m's column tiles over several CTAs only while the grid
+  // still fits in one wave
+  const int tiles = (2 * p.nr + tc::Cfg<NP>::BN - 1) / tc::Cfg<NP>::BN;
+  int nsplit = p.num_sms / p.mh;
+  if (nsplit > tiles) nsplit = tiles;
+  if (nsplit < 1) nsplit = 1;
+  tc::Params prm{x.d32, p.nth, 2 * p.nr, (p.nth + tc::kKBlk - 1) / tc::kKBlk, nsplit, p.d_err};
   constexpr uint32_t smem = tc::smem_bytes<NP>();
   cudaError_t e = allow_smem(tc::k_tc_gemm_split<NP>, smem);
   if (e != cudaSuccess) return e;
-  dim3 grid((2 * p.nr + tc::Cfg<NP>::BN - 1) / tc::Cfg<NP>::BN, p.mh);
-  tc::k_tc_gemm_split<NP><<<grid, 128, smem, s>>>(maps, prm);
+  tc::k_tc_gemm_split<NP><<<dim3(nsplit, p.mh), tc::kThreads, smem, s>>>(maps, prm);
   return cudaGetLastError();
 }
 

@@ -104,6 +104,7 @@ struct Plan {
   // word, host-buffer staging and timers belong to each plan.
   std::atomic<int>* table_refs = nullptr;
   int device = 0;
+  int num_sms = 1;                // streaming multiprocessors of the device
   int nr = 0, nth = 0, nphi = 0, mh = 0;
   int outer_bc = SP_OUTER_MULTIPOLE;
   int precision = SP_FP64;

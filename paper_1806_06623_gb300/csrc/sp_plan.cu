@@ -393,6 +393,8 @@ int sp_plan_create(const double* r_if, int nr, const double* th_if_in, int nth, 
     return SP_ERR_OOM;
   }
   cudaGetDevice(&p->device);
+  if (cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess || p->num_sms < 1)
+    p->num_sms = 1;
   p->nr = nr;
   p->nth = nth;
   p->nphi = nphi;

@@ -10,14 +10,19 @@
 //   NP = 3: A2 B0 + A0 B2 + A1 B1 + A1 B0 + A0 B1 + A0 B0      (6 products, ~2^-24)
 // accumulated in float32 in tensor memory.
 //
-// One CTA per (m, BN-column tile), 128 threads:
-//  - thread 0 issues TMA loads of the operand planes (128B-swizzled K-major boxes of
-//    64 K-elements) onto one mbarrier, waits, then issues the K-steps x products of
-//    tcgen05.mma (M=128, N=BN, K=16, kind::f16, bf16 inputs, f32 accumulator in TMEM)
-//    and commits them to a second mbarrier;
-//  - all four warps then read the 128 x BN accumulator back with tcgen05.ld (warp w owns
-//    TMEM lanes 32w..32w+31 = output rows) and store float32 rows coalesced along r.
-// Every wait is bounded: on expiry the CTA records kErrTimeout and still frees its TMEM.
+// Persistent per m, warp-specialised pipeline (192 threads, one CTA per SM):
+//  - warp 0 (one lane) loads the A planes of m once (TMA, 128B-swizzled K-major boxes of
+//    64 K-elements), then streams the B planes of the CTA's column tiles through a
+//    two-stage shared-memory ring (full/empty mbarriers per stage);
+//  - warp 1 (one lane) issues, per tile, the K-steps x products of tcgen05.mma
+//    (M=128, N=BN, K=16, kind::f16, bf16 inputs, f32 accumulator) into one of two TMEM
+//    accumulators and commits to the stage's empty barrier and the accumulator's full
+//    barrier;
+//  - warps 2..5 drain the other accumulator meanwhile (tcgen05.ld; warp w owns TMEM
+//    lanes 32 (w mod 4) .. +31 = output rows) and store float32 rows coalesced along r.
+// So loads of tile t+1, products of tile t and the epilogue of tile t-1 overlap.  Every
+// wait is bounded and also watches a shared abort flag: on expiry the CTA records
+// kErrTimeout, the other roles leave their loops, and TMEM is still freed.
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -32,12 +37,17 @@ constexpr int kMaxKBlocks = 2;   // K <= 128
 constexpr uint32_t kABlockBytes = kM * 128;   // 16 KB per K block and plane
 
 template <int NP> struct Cfg;
-template <> struct Cfg<2> { static constexpr int BN = 256; };
-template <> struct Cfg<3> { static constexpr int BN = 128; };
+template <> struct Cfg<2> { static constexpr int BN = 128; };
+template <> struct Cfg<3> { static constexpr int BN = 64; };
+constexpr int kStagesB = 2;
+constexpr int kThreads = 192;
+
+template <int NP>
+__host__ __device__ constexpr uint32_t stage_bytes() { return NP * kMaxKBlocks * (uint32_t)Cfg<NP>::BN * 128u; }
 
 template <int NP>
 constexpr uint32_t smem_bytes() {
-  return NP * kMaxKBlocks * kABlockBytes + NP * kMaxKBlocks * (uint32_t)Cfg<NP>::BN * 128u + 1024u;
+  return NP * kMaxKBlocks * kABlockBytes + kStagesB * stage_bytes<NP>() + 1024u;
 }
 constexpr int kErrTimeout = 4;
 constexpr long long kSpinLimit = 1ll << 26;
@@ -47,6 +57,7 @@ struct Params {
   int M;          // valid rows (Ntheta)
   int ncol;       // columns per m
   int kblocks;    // ceil(K / 64)
+  int nsplit;     // CTAs per m (gridDim.x); each takes a contiguous range of column tiles
   int* err;
 };
 
@@ -65,6 +76,27 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Bounded wait for phase `parity` of an mbarrier; false on timeout or when *abort is set.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint32_t bar, uint32_t parity, volatile int* abort) {
+  for (long long it = 0; it < kSpinLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((it & 255) == 255 && *abort) return false;
+  }
+  return false;
 }
 
 // Bounded wait for phase `parity` of an mbarrier; false on timeout.
@@ -137,90 +169,145 @@ __device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, float (&v)[32
 }
 
 template <int NP>
-__global__ void __launch_bounds__(128, 1) k_tc_gemm_split(const __grid_constant__ Maps maps, Params prm) {
+__global__ void __launch_bounds__(kThreads, 1) k_tc_gemm_split(const __grid_constant__ Maps maps, Params prm) {
   constexpr int BN = Cfg<NP>::BN;
   constexpr uint32_t kBBlockBytes = BN * 128u;
+  constexpr uint32_t kStage = stage_bytes<NP>();
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte alignment of the swizzle atoms
   const uint32_t base_u32 = (smem_u32(smem_raw) + 1023u) & ~1023u;
   const uint32_t sA = base_u32;                                  // [NP][kMaxKBlocks] x 16 KB
-  const uint32_t sB = sA + NP * kMaxKBlocks * kABlockBytes;      // [NP][kMaxKBlocks] x BN*128 B
-  __shared__ __align__(8) uint64_t bar_load;
-  __shared__ __align__(8) uint64_t bar_mma;
+  const uint32_t sB = sA + NP * kMaxKBlocks * kABlockBytes;      // [kStagesB][NP][kMaxKBlocks] x BN*128 B
+  __shared__ __align__(8) uint64_t bar_a;
+  __shared__ __align__(8) uint64_t bar_full[kStagesB], bar_empty[kStagesB];
+  __shared__ __align__(8) uint64_t bar_tfull[2], bar_tempty[2];
   __shared__ uint32_t tmem_base;
-  __shared__ int s_fail;
+  __shared__ int s_abort;
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
   const int lane = tid & 31;
   const int m = blockIdx.y;
-  const int n0 = blockIdx.x * BN;
   const int kb = prm.kblocks;
+  const int tiles = (prm.ncol + BN - 1) / BN;
+  const int t0 = (int)(((long long)tiles * blockIdx.x) / prm.nsplit);
+  const int t1 = (int)(((long long)tiles * (blockIdx.x + 1)) / prm.nsplit);
+  const int nt = t1 - t0;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                 "r"((uint32_t)BN));
+                 "r"((uint32_t)(2 * BN)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  if (tid == 0) {
-    s_fail = 0;
-    mbar_init(smem_u32(&bar_load), 1);
-    mbar_init(smem_u32(&bar_mma), 1);
+  if (tid == 32) {
+    s_abort = 0;
+    mbar_init(smem_u32(&bar_a), 1);
+    for (int q = 0; q < kStagesB; ++q) {
+      mbar_init(smem_u32(&bar_full[q]), 1);
+      mbar_init(smem_u32(&bar_empty[q]), 1);
+    }
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(smem_u32(&bar_tfull[q]), 1);
+      mbar_init(smem_u32(&bar_tempty[q]), 128);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
+  volatile int* abort = &s_abort;
+  auto fail = [&]() {
+    *abort = 1;
+    atomicOr(prm.err, kErrTimeout);
+  };
 
-  if (tid == 0) {
-    const uint32_t bl = smem_u32(&bar_load);
-    mbar_expect_tx(bl, (uint32_t)kb * NP * (kABlockBytes + kBBlockBytes));
-    for (int pl = 0; pl < NP; ++pl)
-      for (int b = 0; b < kb; ++b) {
-        tma_load_3d(sA + (pl * kMaxKBlocks + b) * kABlockBytes, &maps.a[pl], b * kKBlk, 0, m, bl);
-        tma_load_3d(sB + (pl * kMaxKBlocks + b) * kBBlockBytes, &maps.b[pl], b * kKBlk, n0, m, bl);
+  if (warp == 0) {
+    if (lane == 0 && nt > 0) {
+      // ---- producer
+      const uint32_t ba = smem_u32(&bar_a);
+      mbar_expect_tx(ba, (uint32_t)kb * NP * kABlockBytes);
+      for (int pl = 0; pl < NP; ++pl)
+        for (int b = 0; b < kb; ++b) tma_load_3d(sA + (pl * kMaxKBlocks + b) * kABlockBytes, &maps.a[pl], b * kKBlk, 0, m, ba);
+      int issued = 0;
+      for (int t = 0; t < nt; ++t) {
+        const int st = t % kStagesB;
+        const uint32_t ph = (uint32_t)(t / kStagesB) & 1u;
+        if (t >= kStagesB && !mbar_wait_or_abort(smem_u32(&bar_empty[st]), ph ^ 1u, abort)) {
+          fail();
+          break;
+        }
+        const uint32_t bf = smem_u32(&bar_full[st]);
+        mbar_expect_tx(bf, (uint32_t)kb * NP * kBBlockBytes);
+        const int n0 = (t0 + t) * BN;
+        for (int pl = 0; pl < NP; ++pl)
+          for (int b = 0; b < kb; ++b)
+            tma_load_3d(sB + st * kStage + (pl * kMaxKBlocks + b) * kBBlockBytes, &maps.b[pl], b * kKBlk, n0, m, bf);
+        issued = t + 1;
       }
-    bool ok = mbar_wait(bl, 0);
-    if (ok) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      // copies in flight land before the CTA frees its shared memory
+      mbar_wait(ba, 0);
+      for (int t = issued - kStagesB > 0 ? issued - kStagesB : 0; t < issued; ++t)
+        mbar_wait(smem_u32(&bar_full[t % kStagesB]), (uint32_t)(t / kStagesB) & 1u);
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && nt > 0) {
+      // ---- MMA issuer
       const uint32_t idesc = idesc_bf16_f32(kM, BN);
-      // plane pairs (a, b) with a + b < NP, smallest first
       constexpr int npairs = NP == 2 ? 3 : 6;
       const int pa[6] = {NP == 2 ? 1 : 2, 0, NP == 2 ? 0 : 1, 1, 0, 0};
       const int pb[6] = {0, NP == 2 ? 1 : 2, NP == 2 ? 0 : 1, 0, 1, 0};
-      uint32_t acc = 0;
-      for (int kk = 0; kk < kb * (kKBlk / 16); ++kk) {
-        const int b = kk / (kKBlk / 16);
-        const uint32_t koff = (uint32_t)(kk % (kKBlk / 16)) * 32u;   // 16 bf16 = 32 B along the swizzled row
-#pragma unroll
-        for (int q = 0; q < npairs; ++q) {
-          const int qa = pa[q];
-          const int qb = pb[q];
-          const uint64_t da = smem_desc_sw128(sA + (qa * kMaxKBlocks + b) * kABlockBytes + koff);
-          const uint64_t db = smem_desc_sw128(sB + (qb * kMaxKBlocks + b) * kBBlockBytes + koff);
-          umma_bf16(tmem, da, db, idesc, acc);
-          acc = 1;
+      bool ok = mbar_wait_or_abort(smem_u32(&bar_a), 0, abort);
+      for (int t = 0; ok && t < nt; ++t) {
+        const int st = t % kStagesB;
+        const uint32_t ph = (uint32_t)(t / kStagesB) & 1u;
+        const int acc_buf = t & 1;
+        const uint32_t aph = (uint32_t)(t >> 1) & 1u;
+        if (!mbar_wait_or_abort(smem_u32(&bar_full[st]), ph, abort) ||
+            (t >= 2 && !mbar_wait_or_abort(smem_u32(&bar_tempty[acc_buf]), aph ^ 1u, abort))) {
+          ok = false;
+          break;
         }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t dt = tmem + (uint32_t)(acc_buf * BN);
+        const uint32_t bst = sB + st * kStage;
+        uint32_t acc = 0;
+        for (int kk = 0; kk < kb * (kKBlk / 16); ++kk) {
+          const int b = kk / (kKBlk / 16);
+          const uint32_t koff = (uint32_t)(kk % (kKBlk / 16)) * 32u;   // 16 bf16 = 32 B along the swizzled row
+#pragma unroll
+          for (int q = 0; q < npairs; ++q) {
+            const uint64_t da = smem_desc_sw128(sA + (pa[q] * kMaxKBlocks + b) * kABlockBytes + koff);
+            const uint64_t db = smem_desc_sw128(bst + (pb[q] * kMaxKBlocks + b) * kBBlockBytes + koff);
+            umma_bf16(dt, da, db, idesc, acc);
+            acc = 1;
+          }
+        }
+        umma_commit(smem_u32(&bar_empty[st]));
+        umma_commit(smem_u32(&bar_tfull[acc_buf]));
       }
-      umma_commit(smem_u32(&bar_mma));
-    } else {
-      s_fail = 1;
-      atomicOr(prm.err, kErrTimeout);
+      if (!ok) fail();
     }
-  }
-  __syncthreads();
-  if (!s_fail) {
-    if (!mbar_wait(smem_u32(&bar_mma), 0)) {
-      atomicOr(prm.err, kErrTimeout);
-    } else {
+  } else {
+    // ---- epilogue: warps 2..5
+    const int quarter = warp & 3;
+    const int row = quarter * 32 + lane;
+    float* Dm = prm.D + (size_t)m * prm.ncol * prm.M;
+    for (int t = 0; t < nt; ++t) {
+      const int acc_buf = t & 1;
+      const uint32_t aph = (uint32_t)(t >> 1) & 1u;
+      // every lane polls; the warp proceeds only together (tcgen05.ld is warp-collective)
+      const bool ok_lane = mbar_wait_or_abort(smem_u32(&bar_tfull[acc_buf]), aph, abort);
+      if (!__all_sync(0xffffffffu, ok_lane)) {
+        if (lane == 0) fail();
+        break;
+      }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int row = warp * 32 + lane;
-      float* Dm = prm.D + (size_t)m * prm.ncol * prm.M;
+      const int n0 = (t0 + t) * BN;
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += 32) {
         float v[32];
-        tmem_ld_32x32b_x32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+        tmem_ld_32x32b_x32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc_buf * BN + c0), v);
         if (row < prm.M) {
 #pragma unroll
           for (int q = 0; q < 32; ++q) {
@@ -229,15 +316,16 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm_split(const __grid_constant_
           }
         }
       }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(smem_u32(&bar_tempty[acc_buf]));
     }
-  } else {
-    // loads may still be in flight: give them a bounded chance to land before exit
-    mbar_wait(smem_u32(&bar_load), 0);
   }
+  // the last products complete before TMEM is freed
+  if (tid == 32 && nt > 0 && !*abort) mbar_wait(smem_u32(&bar_tfull[(nt - 1) & 1]), (uint32_t)((nt - 1) >> 1) & 1u);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * BN)));
   }
 }
 
