@@ -18,6 +18,7 @@ namespace sp {
 namespace {
 
 constexpr int kWarps = 8;
+constexpr int kLoadU = 16;   // input values in flight per thread in the forward load
 
 template <typename T> struct C2;
 template <> struct C2<double> { using t = double2; };
@@ -169,31 +170,29 @@ __global__ void __launch_bounds__(256) k_fft_fwd(const Tin* __restrict__ in, int
   const int line0 = blockIdx.x * lpc;
   const int nl = min(lpc, nlines - line0);
   const int npairs = (nl + 1) / 2;
-  for (int p = warp; p < npairs; p += kWarps) {
-    const Tin* a = in + (size_t)(line0 + 2 * p) * n;
-    const bool hasb = 2 * p + 1 < nl;
-    CT* z = bufA + p * PS;
-    // four segments in flight per lane before any is stored
-    for (int q0 = lane; q0 < n; q0 += 128) {
-      T va[4], vb[4];
+  // The CTA's lines are contiguous in memory: all threads load them together with
+  // kLoadU values per thread in flight, then scatter into the packed complex lines.
+  const int tot = nl * n;
+  const Tin* src = in + (size_t)line0 * n;
+  for (int e0 = threadIdx.x; e0 < tot; e0 += blockDim.x * kLoadU) {
+    T v[kLoadU];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int q = q0 + 32 * u;
-        va[u] = (q < n) ? load_in<T>(a + q) : T(0);
-        vb[u] = (q < n && hasb) ? load_in<T>(a + n + q) : T(0);
-      }
+    for (int u = 0; u < kLoadU; ++u) {
+      const int e = e0 + u * (int)blockDim.x;
+      v[u] = e < tot ? load_in<T>(src + e) : T(0);
+    }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int q = q0 + 32 * u;
-        if (q < n) {
-          CT v;
-          v.x = va[u];
-          v.y = vb[u];
-          z[q] = v;
-        }
+    for (int u = 0; u < kLoadU; ++u) {
+      const int e = e0 + u * (int)blockDim.x;
+      if (e < tot) {
+        const int line = sch.nshift >= 0 ? (e >> sch.nshift) : (int)__umulhi((unsigned int)e, sch.nmagic);
+        const int q = e - line * n;
+        reinterpret_cast<T*>(bufA + (line >> 1) * PS + q)[line & 1] = v[u];
       }
     }
   }
+  if (nl & 1)
+    for (int q = threadIdx.x; q < n; q += blockDim.x) bufA[(nl >> 1) * PS + q].y = T(0);
   __syncthreads();
   CT* Z = warp_fft<false, T>(bufA, bufB, tw, sch, npairs, PS);
   __syncthreads();

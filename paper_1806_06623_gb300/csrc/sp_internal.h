@@ -27,6 +27,8 @@ struct FftSchedule {
   int tstep[kMaxStages];
   int shift[kMaxStages];
   unsigned int magic[kMaxStages];
+  int nshift;            // log2 n for powers of two, else -1
+  unsigned int nmagic;   // ceil(2^32 / n) otherwise: floor(x/n) = umulhi(x, nmagic) for x < 32 n
 };
 
 // Error bits written by kernels into the plan's device status word.

@@ -55,6 +55,10 @@ bool make_schedule(int n, sp::FftSchedule* s) {
     s->magic[st] = (unsigned int)((1ull << 32) / (unsigned long long)ns + 1ull);
     ns *= s->radix[st];
   }
+  s->nshift = -1;
+  for (int b = 0; b < 31; ++b)
+    if ((1 << b) == n) s->nshift = b;
+  s->nmagic = s->nshift >= 0 ? 0u : (unsigned int)(((1ull << 32) + (unsigned long long)n - 1ull) / (unsigned long long)n);
   return true;
 }
 

@@ -255,8 +255,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm_split(const __grid_cons
       // ---- MMA issuer
       const uint32_t idesc = idesc_bf16_f32(kM, BN);
       constexpr int npairs = NP == 2 ? 3 : 6;
-      const int pa[6] = {NP == 2 ? 1 : 2, 0, NP == 2 ? 0 : 1, 1, 0, 0};
-      const int pb[6] = {0, NP == 2 ? 1 : 2, NP == 2 ? 0 : 1, 0, 1, 0};
+      constexpr int pa[6] = {NP == 2 ? 1 : 2, 0, NP == 2 ? 0 : 1, 1, 0, 0};
+      constexpr int pb[6] = {0, NP == 2 ? 1 : 2, NP == 2 ? 0 : 1, 0, 1, 0};
+      // descriptors differ only in the start-address field (address >> 4, below 2^14 for
+      // any shared-memory address), so each is a base plus a compile-time offset
+      const uint64_t dA0 = smem_desc_sw128(sA);
       bool ok = mbar_wait_or_abort(smem_u32(&bar_a), 0, abort);
       for (int t = 0; ok && t < nt; ++t) {
         const int st = t % kStagesB;
@@ -270,17 +273,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm_split(const __grid_cons
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t dt = tmem + (uint32_t)(acc_buf * BN);
-        const uint32_t bst = sB + st * kStage;
-        uint32_t acc = 0;
-        for (int kk = 0; kk < kb * (kKBlk / 16); ++kk) {
-          const int b = kk / (kKBlk / 16);
-          const uint32_t koff = (uint32_t)(kk % (kKBlk / 16)) * 32u;   // 16 bf16 = 32 B along the swizzled row
+        const uint64_t dB0 = smem_desc_sw128(sB + st * kStage);
 #pragma unroll
-          for (int q = 0; q < npairs; ++q) {
-            const uint64_t da = smem_desc_sw128(sA + (pa[q] * kMaxKBlocks + b) * kABlockBytes + koff);
-            const uint64_t db = smem_desc_sw128(bst + (pb[q] * kMaxKBlocks + b) * kBBlockBytes + koff);
-            umma_bf16(dt, da, db, idesc, acc);
-            acc = 1;
+        for (int b = 0; b < kMaxKBlocks; ++b) {
+          if (b < kb) {
+#pragma unroll
+            for (int k4 = 0; k4 < kKBlk / 16; ++k4) {   // 16 bf16 = 32 B along the swizzled row
+#pragma unroll
+              for (int q = 0; q < npairs; ++q) {
+                const uint64_t da = dA0 + (((uint32_t)(pa[q] * kMaxKBlocks + b) * kABlockBytes + k4 * 32u) >> 4);
+                const uint64_t db = dB0 + (((uint32_t)(pb[q] * kMaxKBlocks + b) * kBBlockBytes + k4 * 32u) >> 4);
+                umma_bf16(dt, da, db, idesc, (b | k4 | q) ? 1u : 0u);
+              }
+            }
           }
         }
         umma_commit(smem_u32(&bar_empty[st]));
@@ -304,15 +309,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm_split(const __grid_cons
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int n0 = (t0 + t) * BN;
+      float* dst = Dm + (size_t)n0 * prm.M + row;
+      const bool full = n0 + BN <= prm.ncol;
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += 32) {
         float v[32];
         tmem_ld_32x32b_x32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc_buf * BN + c0), v);
         if (row < prm.M) {
+          if (full) {
 #pragma unroll
-          for (int q = 0; q < 32; ++q) {
-            const int col = n0 + c0 + q;
-            if (col < prm.ncol) Dm[(size_t)col * prm.M + row] = v[q];
+            for (int q = 0; q < 32; ++q) dst[(size_t)(c0 + q) * prm.M] = v[q];
+          } else {
+#pragma unroll
+            for (int q = 0; q < 32; ++q)
+              if (n0 + c0 + q < prm.ncol) dst[(size_t)(c0 + q) * prm.M] = v[q];
           }
         }
       }
