@@ -473,10 +473,11 @@ __global__ void __launch_bounds__(kResThreads) k_residual_ff(const double* __res
                                                              float* __restrict__ r,
                                                              const RadialRowFF* __restrict__ rad,
                                                              const ThetaRowFF* __restrict__ th, int nr, int nth,
-                                                             int nphi, int dirichlet, ff dir_coef, ff four_pi_g) {
+                                                             int nphi, int chunk0, int dirichlet, ff dir_coef,
+                                                             ff four_pi_g) {
   __shared__ float line[2][2][kResThreads + 2];   // [row parity][hi, lo][k - k0 + 1]
   const int j = blockIdx.x;
-  const int i0 = blockIdx.y * kResRows, i1 = min(nr, i0 + kResRows);
+  const int i0 = (chunk0 + (int)blockIdx.y) * kResRows, i1 = min(nr, i0 + kResRows);
   const int t = threadIdx.x;
   const int k0 = blockIdx.z * blockDim.x;
   const int nk = min((int)blockDim.x, nphi - k0);   // columns of this CTA
@@ -782,29 +783,46 @@ cudaError_t thomas_mixed(const Plan& p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+int create_side_stream(Plan& p) {
+  if (!p.mixed || p.outer_bc != SP_OUTER_MULTIPOLE) return SP_OK;
+  int lo = 0, hi = 0;
+  if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&p.side, cudaStreamNonBlocking, hi) != cudaSuccess ||
+      cudaEventCreateWithFlags(&p.ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&p.ev_join, cudaEventDisableTiming) != cudaSuccess)
+    return SP_ERR_CUDA;
+  return SP_OK;
+}
+
 cudaError_t residual_ff(const Plan& p, const double* rho, cudaStream_t s) {
   const MixedTables& x = *p.mixed;
-  const size_t n = (size_t)p.nr * p.nth * p.nphi;
   const size_t sh = (size_t)p.nth * p.nphi;
-  if (p.outer_bc == SP_OUTER_MULTIPOLE) {
-    // outer term from the float64 value of the last shell (small: Ntheta x Nphi zones)
-    const size_t off = (size_t)(p.nr - 1) * sh;
-    k_finish<<<(unsigned)((sh + 255) / 256), 256, 0, s>>>(x.phi_hi + off, x.phi_lo + off, x.shell_phi, sh);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    e = fft_forward_f64(p, x.shell_phi, 1, 1.0 / p.nphi, p.shell, s);
-    if (e != cudaSuccess) return e;
-    e = shell_kappa_f64(p, p.shell, p.shell2, s);
-    if (e != cudaSuccess) return e;
-    e = fft_inverse_f64(p, p.shell2, 1, x.outer_shell, false, s);
-    if (e != cudaSuccess) return e;
-  }
-  (void)n;
   const int tpb = p.nphi >= kResThreads ? kResThreads : ((p.nphi + 31) / 32) * 32;
-  const dim3 grid(p.nth, (p.nr + kResRows - 1) / kResRows, (p.nphi + tpb - 1) / tpb);
-  k_residual_ff<<<grid, tpb, 0, s>>>(rho, x.phi_hi, x.phi_lo, x.outer_shell, x.r32, x.radff, x.thff, p.nr, p.nth,
-                                     p.nphi, p.outer_bc == SP_OUTER_DIRICHLET ? 1 : 0, x.dir_coef, x.four_pi_g);
-  return cudaGetLastError();
+  const int nchunk = (p.nr + kResRows - 1) / kResRows;
+  auto rows = [&](int c0, int nc, cudaStream_t st) {
+    const dim3 grid(p.nth, nc, (p.nphi + tpb - 1) / tpb);
+    k_residual_ff<<<grid, tpb, 0, st>>>(rho, x.phi_hi, x.phi_lo, x.outer_shell, x.r32, x.radff, x.thff, p.nr, p.nth,
+                                        p.nphi, c0, p.outer_bc == SP_OUTER_DIRICHLET ? 1 : 0, x.dir_coef,
+                                        x.four_pi_g);
+    return cudaGetLastError();
+  };
+  if (p.outer_bc != SP_OUTER_MULTIPOLE) return rows(0, nchunk, s);
+  // The multipole term of the last shell (small: Ntheta x Nphi zones, float64 FFTs and
+  // per-m operator) runs on the high-priority side stream while the interior rows,
+  // which do not need it, run here; the chunk holding the last shell follows the join.
+  cudaError_t e;
+  if ((e = cudaEventRecord(p.ev_fork, s)) != cudaSuccess || (e = cudaStreamWaitEvent(p.side, p.ev_fork, 0)) != cudaSuccess)
+    return e;
+  const size_t off = (size_t)(p.nr - 1) * sh;
+  k_finish<<<(unsigned)((sh + 255) / 256), 256, 0, p.side>>>(x.phi_hi + off, x.phi_lo + off, x.shell_phi, sh);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = fft_forward_f64(p, x.shell_phi, 1, 1.0 / p.nphi, p.shell, p.side)) != cudaSuccess) return e;
+  if ((e = shell_kappa_f64(p, p.shell, p.shell2, p.side)) != cudaSuccess) return e;
+  if ((e = fft_inverse_f64(p, p.shell2, 1, x.outer_shell, false, p.side)) != cudaSuccess) return e;
+  if ((e = cudaEventRecord(p.ev_join, p.side)) != cudaSuccess) return e;
+  if (nchunk > 1 && (e = rows(0, nchunk - 1, s)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(s, p.ev_join, 0)) != cudaSuccess) return e;
+  return rows(nchunk - 1, 1, s);
 }
 
 cudaError_t finish_mixed(const Plan& p, double* phi, cudaStream_t s) {

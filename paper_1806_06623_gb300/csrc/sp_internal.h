@@ -148,6 +148,10 @@ struct Plan {
 
   MixedTables* mixed = nullptr;
   unsigned int* h_red = nullptr;  // pinned host copy of the mixed-path reductions
+  // side stream (high priority) and fork/join events: the multipole shell term of the
+  // mixed residual runs beside the residual's interior rows
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
   // launch accounting and optional CUDA-event timers (one event pair per launch)
   long long launches = 0;
@@ -228,6 +232,7 @@ cudaError_t finish_mixed(const Plan& p, double* phi, cudaStream_t s);   // float
 cudaError_t tc_project(const Plan& p, bool inverse, cudaStream_t s);   // pan -> d32
 cudaError_t thomas_mixed(const Plan& p, cudaStream_t s);   // d32 -> pan (f); float32 + float64 low modes
 cudaError_t residual_ff(const Plan& p, const double* rho, cudaStream_t s);  // iterate -> r32
+int create_side_stream(Plan& p);   // side stream and events of a mixed multipole plan; sp_status
 
 // ---- solve phases shared by sp_solve, sp_solve_batched and the server ----
 // Refinement state of one mixed-precision solve.

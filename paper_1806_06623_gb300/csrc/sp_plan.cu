@@ -100,6 +100,9 @@ void free_tables(Plan* p) {
   if (p->ws_owned) cudaFree(p->ws);
   for (int i = 0; i < 2 * sp::kMaxTimedLaunches; ++i)
     if (p->ev[i]) cudaEventDestroy(p->ev[i]);
+  if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+  if (p->ev_join) cudaEventDestroy(p->ev_join);
+  if (p->side) cudaStreamDestroy(p->side);
 }
 
 bool overlaps(const void* a, const void* b, size_t bytes) {
@@ -186,7 +189,7 @@ int mixed_correct(Plan* p, const double* rho, cudaStream_t s) {
   Plan& P = *p;
   int st;
   if ((st = launch_status(timed_launch(P, kKResidual, s, [&] { return residual_ff(P, rho, s); })))) return st;
-  if (P.outer_bc == SP_OUTER_MULTIPOLE) P.launches += 4;
+  if (P.outer_bc == SP_OUTER_MULTIPOLE) P.launches += 5;   // shell: finish, FFT, apply, inverse FFT; split residual
   SP_CUDA(cudaMemsetAsync(P.mixed->red, 0, 2 * sizeof(unsigned int), s));
   return lp_solve(p, P.mixed->r32, false, (float)(1.0 / P.nphi), nullptr, false, s);
 }
@@ -530,6 +533,7 @@ int sp_plan_create(const double* r_if, int nr, const double* th_if_in, int nth, 
       st = SP_ERR_OOM;
       break;
     }
+    if ((st = sp::create_side_stream(*p))) break;
   } while (0);
   if (st != SP_OK) {
     free_tables(p);
@@ -569,6 +573,9 @@ int sp_plan_clone(const sp_plan* src_plan, sp_plan** out) {
     else sp::mixed_clear_workspace(*c->mixed);
     if (st == SP_OK && cudaMallocHost(&c->h_red, 4 * sizeof(unsigned int)) != cudaSuccess) st = SP_ERR_OOM;
   }
+  c->side = nullptr;
+  c->ev_fork = c->ev_join = nullptr;
+  if (st == SP_OK) st = sp::create_side_stream(*c);
   if (st == SP_OK && cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess) st = SP_ERR_OOM;
   if (st == SP_OK && cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess) st = SP_ERR_CUDA;
   if (st != SP_OK) {
