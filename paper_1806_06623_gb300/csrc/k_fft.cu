@@ -137,26 +137,12 @@ __device__ __forceinline__ float load_in<float>(const double* p) { return d2ff(*
 template <typename T>
 __device__ __forceinline__ T load_in(const float* p) { return (T)*p; }
 
-enum FwdOut { kOutPlain = 0, kOutSplit = 1 };
-
-// x -> bf16 planes x0 = RN(x), x1 = RN(x - x0) (, x2 = RN(x - x0 - x1))
-__device__ __forceinline__ void store_planes(const Planes& pl, size_t o, float x) {
-  const __nv_bfloat16 h = __float2bfloat16_rn(x);
-  pl.p[0][o] = h;
-  const float r = x - __bfloat162float(h);
-  const __nv_bfloat16 m = __float2bfloat16_rn(r);
-  pl.p[1][o] = m;
-  if (pl.n == 3) pl.p[2][o] = __float2bfloat16_rn(r - __bfloat162float(m));
-}
-
-// Forward: lines [line0, line0+nl) of `in` -> half spectrum scaled by `scale`:
-//  OUT = kOutPlain: spec[m][i][c][j] (row stride Ntheta)
-//  OUT = kOutSplit: bf16 planes pl[m][i][c][j] (row stride kstride)
-
-template <typename T, typename Tin, int OUT>
+// Forward: lines [line0, line0+nl) of `in` -> half spectrum scaled by `scale`,
+// spec[m][i][c][j] with row stride `rs` (Ntheta, or the padded panel stride).
+template <typename T, typename Tin>
 __global__ void __launch_bounds__(256) k_fft_fwd(const Tin* __restrict__ in, int nlines, int nth, int nrs,
                                                  FftSchedule sch, const T* __restrict__ twid, T scale, int lpc,
-                                                 T* __restrict__ spec, Planes pl, int kstride) {
+                                                 T* __restrict__ spec, int rs) {
   using CT = typename C2<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = sch.n;
@@ -211,15 +197,9 @@ __global__ void __launch_bounds__(256) k_fft_fwd(const Tin* __restrict__ in, int
       else { re = T(0.5) * (a.x + b.x); im = T(0.5) * (a.y - b.y); }          // (Z + conj Zc)/2
       re *= scale;
       im *= scale;
-      if (OUT == kOutPlain) {
-        T* o = spec + ((size_t)(m * nrs + i) * 2) * nth + j;
-        o[0] = re;
-        o[nth] = im;
-      } else {
-        const size_t o = ((size_t)(m * nrs + i) * 2) * kstride + j;
-        store_planes(pl, o, (float)re);
-        store_planes(pl, o + kstride, (float)im);
-      }
+      T* o = spec + ((size_t)(m * nrs + i) * 2) * rs + j;
+      o[0] = re;
+      o[rs] = im;
     }
   }
 }
@@ -392,11 +372,11 @@ cudaError_t fft_forward_f64(const Plan& p, const double* in, int nrs, double sca
   const int nlines = nrs * p.nth;
   const int lpc = lines_per_cta<double>(p.nphi, nlines);
   const size_t smem = fft_smem<double>(p.nphi, lpc);
-  auto kern = k_fft_fwd<double, double, kOutPlain>;
+  auto kern = k_fft_fwd<double, double>;
   cudaError_t e = prep(kern, smem);
   if (e != cudaSuccess) return e;
   kern<<<(nlines + lpc - 1) / lpc, 32 * kWarps, smem, s>>>(in, nlines, p.nth, nrs, p.sched, p.d_twid, scale, lpc, spec,
-                                                           Planes{{nullptr, nullptr, nullptr}, 0}, 0);
+                                                           p.nth);
   return cudaGetLastError();
 }
 
@@ -418,7 +398,7 @@ cudaError_t fft_inverse_f64(const Plan& p, const double* spec, int nrs, double* 
   return cudaGetLastError();
 }
 
-cudaError_t fft_forward_split(const Plan& p, const void* in, bool in_double, float scale, int kstride, Planes out,
+cudaError_t fft_forward_panel(const Plan& p, const void* in, bool in_double, float scale, int kstride, float* out,
                               cudaStream_t s) {
   const int nlines = p.nr * p.nth;
   const int lpc = lines_per_cta<float>(p.nphi, nlines);
@@ -426,15 +406,15 @@ cudaError_t fft_forward_split(const Plan& p, const void* in, bool in_double, flo
   const int grid = (nlines + lpc - 1) / lpc;
   cudaError_t e;
   if (in_double) {
-    auto kern = k_fft_fwd<float, double, kOutSplit>;
+    auto kern = k_fft_fwd<float, double>;
     if ((e = prep(kern, smem)) != cudaSuccess) return e;
     kern<<<grid, 32 * kWarps, smem, s>>>(static_cast<const double*>(in), nlines, p.nth, p.nr, p.sched, p.d_twid32,
-                                         scale, lpc, nullptr, out, kstride);
+                                         scale, lpc, out, kstride);
   } else {
-    auto kern = k_fft_fwd<float, float, kOutSplit>;
+    auto kern = k_fft_fwd<float, float>;
     if ((e = prep(kern, smem)) != cudaSuccess) return e;
     kern<<<grid, 32 * kWarps, smem, s>>>(static_cast<const float*>(in), nlines, p.nth, p.nr, p.sched, p.d_twid32,
-                                         scale, lpc, nullptr, out, kstride);
+                                         scale, lpc, out, kstride);
   }
   return cudaGetLastError();
 }

@@ -37,15 +37,6 @@ __global__ void k_split_table(const double* __restrict__ src, int n, int kstride
   }
 }
 
-__device__ __forceinline__ void store_split(const Planes& pl, size_t o, float v) {
-  const __nv_bfloat16 h = __float2bfloat16_rn(v);
-  pl.p[0][o] = h;
-  const float r = v - __bfloat162float(h);
-  const __nv_bfloat16 m = __float2bfloat16_rn(r);
-  pl.p[1][o] = m;
-  if (pl.n == 3) pl.p[2][o] = __float2bfloat16_rn(r - __bfloat162float(m));
-}
-
 __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)), "l"(gmem)
                : "memory");
@@ -69,7 +60,7 @@ constexpr int kStages = 6;    // chunks in flight per warp
 // planes in the panel layout.
 __global__ void __launch_bounds__(32) k_thomas_staged(const float* __restrict__ sub_r, const double* __restrict__ lam,
                                                       float* __restrict__ x, const float* __restrict__ fcp,
-                                                      const float* __restrict__ finv, Planes pl, int nr, int nth,
+                                                      const float* __restrict__ finv, float* __restrict__ pl, int nr, int nth,
                                                       int kstride, double thr, int nblk_f32,
                                                       const int* __restrict__ low_idx, int nlow,
                                                       const RadialRow* __restrict__ rad64,
@@ -120,8 +111,8 @@ __global__ void __launch_bounds__(32) k_thomas_staged(const float* __restrict__ 
     __syncwarp();
     const size_t prow = (size_t)m * nr * 2;
     for (int i = lane; i < nr; i += 32) {
-      store_split(pl, (prow + 2 * i) * kstride + l, (float)W[3 * i]);
-      store_split(pl, (prow + 2 * i + 1) * kstride + l, (float)W[3 * i + 1]);
+      pl[(prow + 2 * i) * kstride + l] = (float)W[3 * i];
+      pl[(prow + 2 * i + 1) * kstride + l] = (float)W[3 * i + 1];
     }
     return;
   }
@@ -188,7 +179,7 @@ __global__ void __launch_bounds__(32) k_thomas_staged(const float* __restrict__ 
       for (int r = n - 1; r >= 0; --r) {
         const int i = i0 + r;
         f = (i == nr - 1) ? b[r][0][lane] : fmaf(-b[r][1][lane], f, b[r][0][lane]);
-        store_split(pl, (prow + 2 * i) * kstride + l, f);
+        pl[(prow + 2 * i) * kstride + l] = f;
       }
     }
     __syncwarp();
@@ -222,7 +213,7 @@ size_t scan_smem_bytes(int nr) {
 
 __global__ void __launch_bounds__(kScanThreads) k_thomas_scan(
     const float* __restrict__ sub_r, const double* __restrict__ lam, const float* __restrict__ x,
-    const float* __restrict__ fcp, const float* __restrict__ finv, Planes pl, int nr, int nth, int kstride,
+    const float* __restrict__ fcp, const float* __restrict__ finv, float* __restrict__ pl, int nr, int nth, int kstride,
     double thr, int nlowblk, const int* __restrict__ low_idx, int nlow, const RadialRow* __restrict__ rad64,
     const double2* __restrict__ low_fac) {
   extern __shared__ __align__(16) float sm[];
@@ -294,7 +285,7 @@ __global__ void __launch_bounds__(kScanThreads) k_thomas_scan(
     carry = __shfl_down_sync(0xffffffffu, v, 1);
     if (lane == 31) carry = 0.0;
     const size_t prow = (size_t)m * nr * 2 + cc;
-    for (int i = j0; i < j1; ++i) store_split(pl, (prow + 2 * i) * kstride + l, (float)fma(Wq[i], carry, Wd[i]));
+    for (int i = j0; i < j1; ++i) pl[(prow + 2 * i) * kstride + l] = (float)fma(Wq[i], carry, Wd[i]);
     return;
   }
   const int col = tid % kScanCols, seg = tid / kScanCols;
@@ -387,7 +378,7 @@ __global__ void __launch_bounds__(kScanThreads) k_thomas_scan(
     const size_t prow = (size_t)m * nr * 2 + c;
     for (int i = i0; i < i1; ++i) {
       const int o = i * kScanCols + col;
-      store_split(pl, (prow + 2 * i) * kstride + l, fmaf(Q[o], cw, D[o]));
+      pl[(prow + 2 * i) * kstride + l] = fmaf(Q[o], cw, D[o]);
     }
   }
 }
@@ -594,7 +585,7 @@ size_t mixed_workspace_bytes(const Plan& p) {
   const MixedTables& x = *p.mixed;
   const size_t zones = (size_t)p.nr * p.nth * p.nphi;
   const size_t rows = (size_t)p.mh * 2 * p.nr;
-  return 3 * al256(zones * 4) + x.np * al256(rows * x.kstride * 2) + al256(rows * p.nth * 4) +
+  return 3 * al256(zones * 4) + al256(rows * x.kstride * 4) + al256(rows * p.nth * 4) +
          al256((size_t)(x.nlow ? x.nlow : 1) * p.nr * 3 * 8) +
          2 * al256((size_t)p.nth * p.nphi * 8) + 2 * al256((size_t)p.mh * 2 * p.nth * 8) + 256;
 }
@@ -609,13 +600,8 @@ void mixed_bind_workspace(Plan& p, char* c) {
   c += al256(zones * 4);
   x.phi_lo = reinterpret_cast<float*>(c);
   c += al256(zones * 4);
-  for (int q = 0; q < 3; ++q) {
-    x.pan[q] = nullptr;
-    if (q < x.np) {
-      x.pan[q] = reinterpret_cast<__nv_bfloat16*>(c);
-      c += al256(rows * x.kstride * 2);
-    }
-  }
+  x.panel = reinterpret_cast<float*>(c);
+  c += al256(rows * x.kstride * 4);
   x.d32 = reinterpret_cast<float*>(c);
   c += al256(rows * p.nth * 4);
   x.low_ws = reinterpret_cast<double*>(c);
@@ -630,15 +616,6 @@ void mixed_bind_workspace(Plan& p, char* c) {
   c += al256((size_t)p.mh * 2 * p.nth * 8);
   x.red = reinterpret_cast<unsigned int*>(c);
   p.specA = p.specB = p.cp = nullptr;
-}
-
-bool mixed_make_panel_maps(Plan& p) {
-  MixedTables& x = *p.mixed;
-  const int bn = x.np == 3 ? tc::Cfg<3>::BN : tc::Cfg<2>::BN;
-  bool ok = true;
-  for (int q = 0; q < x.np; ++q)
-    ok = ok && tc::make_map(reinterpret_cast<CUtensorMap*>(x.map_B[q]), x.pan[q], p.nth, x.kstride, 2 * p.nr, p.mh, bn);
-  return ok;
 }
 
 int mixed_create_tables(Plan& p, cudaStream_t s) {
@@ -728,7 +705,7 @@ void mixed_free_shared(MixedTables& x) {
 void mixed_clear_workspace(MixedTables& x) {
   x.r32 = nullptr;
   x.phi_hi = x.phi_lo = nullptr;
-  for (int q = 0; q < 3; ++q) x.pan[q] = nullptr;
+  x.panel = nullptr;
   x.d32 = nullptr;
   x.low_ws = nullptr;
   x.outer_shell = x.shell_phi = nullptr;
@@ -739,17 +716,14 @@ template <int NP>
 cudaError_t tc_project_np(const Plan& p, bool inverse, cudaStream_t s) {
   const MixedTables& x = *p.mixed;
   tc::Maps maps;
-  for (int q = 0; q < NP; ++q) {
-    std::memcpy(&maps.a[q], inverse ? x.map_Ai[q] : x.map_Af[q], sizeof(CUtensorMap));
-    std::memcpy(&maps.b[q], x.map_B[q], sizeof(CUtensorMap));
-  }
+  for (int q = 0; q < NP; ++q) std::memcpy(&maps.a[q], inverse ? x.map_Ai[q] : x.map_Af[q], sizeof(CUtensorMap));
   // one CTA per SM: split an m's column tiles over several CTAs only while the grid
   // still fits in one wave
   const int tiles = (2 * p.nr + tc::Cfg<NP>::BN - 1) / tc::Cfg<NP>::BN;
   int nsplit = p.num_sms / p.mh;
   if (nsplit > tiles) nsplit = tiles;
   if (nsplit < 1) nsplit = 1;
-  tc::Params prm{x.d32, p.nth, 2 * p.nr, (p.nth + tc::kKBlk - 1) / tc::kKBlk, nsplit, p.d_err};
+  tc::Params prm{x.d32, x.panel, p.nth, p.nth, x.kstride, 2 * p.nr, (p.nth + tc::kKBlk - 1) / tc::kKBlk, nsplit, p.d_err};
   constexpr uint32_t smem = tc::smem_bytes<NP>();
   cudaError_t e = allow_smem(tc::k_tc_gemm_split<NP>, smem);
   if (e != cudaSuccess) return e;
@@ -770,14 +744,14 @@ cudaError_t thomas_mixed(const Plan& p, cudaStream_t s) {
     cudaError_t e = allow_smem(k_thomas_scan, smem);
     if (e != cudaSuccess) return e;
     k_thomas_scan<<<nlowblk + nblk, kScanThreads, smem, s>>>(
-        x.sub_r, p.d_lam, x.d32, x.fcp, x.finv, Planes{{x.pan[0], x.pan[1], x.pan[2]}, x.np}, p.nr, p.nth, x.kstride,
+        x.sub_r, p.d_lam, x.d32, x.fcp, x.finv, x.panel, p.nr, p.nth, x.kstride,
         x.low_threshold, nlowblk, x.low_idx, x.nlow, p.d_rad, x.low_fac);
     return cudaGetLastError();
   }
   const int nblk = 2 * p.mh * ((p.nth + 31) / 32);
   const int nlowblk = x.nlow;   // one warp per float64 mode
   k_thomas_staged<<<nblk + nlowblk, 32, 0, s>>>(x.sub_r, p.d_lam, x.d32, x.fcp, x.finv,
-                                                 Planes{{x.pan[0], x.pan[1], x.pan[2]}, x.np}, p.nr, p.nth,
+                                                 x.panel, p.nr, p.nth,
                                                  x.kstride, x.low_threshold, nblk, x.low_idx, x.nlow, p.d_rad,
                                                  x.low_fac, x.low_ws);
   return cudaGetLastError();

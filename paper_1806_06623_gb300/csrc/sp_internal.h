@@ -80,7 +80,7 @@ struct MixedTables {
   float* r32 = nullptr;            // [nr][nth][nphi] residual
   float* phi_hi = nullptr;         // [nr][nth][nphi] iterate as float-float
   float* phi_lo = nullptr;
-  __nv_bfloat16* pan[3] = {};      // planes of the spectral panel [mh][2nr][kstride] (s_tilde, then f)
+  float* panel = nullptr;          // spectral panel [mh][2nr][kstride] float32 (s_tilde, then f)
   float* d32 = nullptr;            // [mh][2nr][nth] projection output (s_hat, then g)
   float* fcp = nullptr;            // [mh][nr][nth] radial elimination factors c'_i (plan tables)
   float* finv = nullptr;           // [mh][nr][nth] 1/pivot_i
@@ -90,7 +90,7 @@ struct MixedTables {
   double* shell_phi = nullptr;     // [nth][nphi] float64 value of the iterate's last shell
   unsigned int* red = nullptr;     // [2] max|e|, max|Phi| (bit patterns of non-negative floats)
   // tensor maps (CUtensorMap, 128 bytes each) for the tcgen05 projections
-  alignas(64) unsigned char map_Af[3][128], map_Ai[3][128], map_B[3][128];
+  alignas(64) unsigned char map_Af[3][128], map_Ai[3][128];
 };
 
 // Kernel identities for the optional per-launch CUDA-event timers.
@@ -219,12 +219,11 @@ void mixed_bind_workspace(Plan& p, char* base);
 int mixed_create_tables(Plan& p, cudaStream_t s);   // after theta_eigen; returns sp_status
 void mixed_free_shared(MixedTables& x);     // tables shared with clones
 void mixed_clear_workspace(MixedTables& x);  // forget workspace views (clone set-up)
-bool mixed_make_panel_maps(Plan& p);
 struct Planes {
   __nv_bfloat16* p[3];
   int n;
 };
-cudaError_t fft_forward_split(const Plan& p, const void* in, bool in_double, float scale, int kstride, Planes out,
+cudaError_t fft_forward_panel(const Plan& p, const void* in, bool in_double, float scale, int kstride, float* out,
                               cudaStream_t s);
 cudaError_t fft_inverse_update(const Plan& p, const float* spec, float* phi_hi, float* phi_lo, bool first,
                                unsigned int* red, cudaStream_t s);

@@ -120,7 +120,6 @@ int ensure_workspace(Plan* p) {
   p->ws_bytes = b;
   p->ws_owned = true;
   sp::bind_workspace(*p, w);
-  if (p->mixed && !sp::mixed_make_panel_maps(*p)) return SP_ERR_CUDA;
   return SP_OK;
 }
 
@@ -161,8 +160,7 @@ int lp_solve(Plan* p, const void* in, bool in_double, float scale, double* phi, 
   sp::MixedTables& x = *P.mixed;
   int st;
   if ((st = launch_status(sp::timed_launch(P, sp::kKFftFwd, s, [&] {
-         return sp::fft_forward_split(P, in, in_double, scale, x.kstride,
-                                      sp::Planes{{x.pan[0], x.pan[1], x.pan[2]}, x.np}, s); }))))
+         return sp::fft_forward_panel(P, in, in_double, scale, x.kstride, x.panel, s); }))))
     return st;
   if ((st = launch_status(sp::timed_launch(P, sp::kKGemmFwd, s, [&] { return sp::tc_project(P, false, s); }))))
     return st;
@@ -605,7 +603,6 @@ int sp_plan_set_workspace(sp_plan* plan, void* dev, size_t bytes) {
   p->ws_bytes = bytes;
   p->ws_owned = false;
   sp::bind_workspace(*p, dev);
-  if (p->mixed && !sp::mixed_make_panel_maps(*p)) return SP_ERR_CUDA;
   return SP_OK;
 }
 

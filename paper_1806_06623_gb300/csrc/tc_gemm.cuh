@@ -2,29 +2,33 @@
 //
 // For every azimuthal wavenumber m (Sect. 3.2) the projection is the product
 //   D[m][n][r] = sum_k A[m][r][k] B[m][n][k]      (r < M = Ntheta rows, k < K = Ntheta)
-// with A the (H^T W)_m or H_m table and B the K-contiguous spectral panel of 2 Nr
-// columns n = (i, re/im).  Both operands arrive as NP bf16 planes x = x0 + x1 (+ x2)
-// (x0 = RN_bf16(x), x1 = RN_bf16(x - x0), x2 = RN_bf16(x - x0 - x1)); the product keeps
-// every plane pair whose index sum is below NP, smallest terms first:
+// with A the (H^T W)_m or H_m table and B the K-contiguous float32 spectral panel of
+// 2 Nr columns n = (i, re/im).  Both operands enter the products as NP bf16 planes
+// x = x0 + x1 (+ x2) (x0 = RN_bf16(x), x1 = RN_bf16(x - x0), x2 = RN_bf16(x - x0 - x1));
+// the table's planes are precomputed, the panel's are formed in shared memory.  The
+// product keeps every plane pair whose index sum is below NP, smallest terms first:
 //   NP = 2: A1 B0 + A0 B1 + A0 B0                              (3 products, ~2^-16)
 //   NP = 3: A2 B0 + A0 B2 + A1 B1 + A1 B0 + A0 B1 + A0 B0      (6 products, ~2^-24)
 // accumulated in float32 in tensor memory.
 //
-// Persistent per m, warp-specialised pipeline (192 threads, one CTA per SM):
+// Persistent per m, warp-specialised pipeline (448 threads, one CTA per SM):
 //  - warp 0 (one lane) loads the A planes of m once (TMA, 128B-swizzled K-major boxes of
-//    64 K-elements), then streams the B planes of the CTA's column tiles through a
-//    two-stage shared-memory ring (full/empty mbarriers per stage);
+//    64 K-elements);
+//  - warps 6..13 stream the panel rows of the CTA's column tiles (float4 loads, the
+//    next tile in flight while the current one is converted), split them into bf16
+//    planes and store those in the 128B-swizzled K-major layout of a two-stage ring
+//    (full/empty mbarriers per stage, fence.proxy.async before the arrival);
 //  - warp 1 (one lane) issues, per tile, the K-steps x products of tcgen05.mma
 //    (M=128, N=BN, K=16, kind::f16, bf16 inputs, f32 accumulator) into one of two TMEM
 //    accumulators and commits to the stage's empty barrier and the accumulator's full
 //    barrier;
 //  - warps 2..5 drain the other accumulator meanwhile (tcgen05.ld; warp w owns TMEM
 //    lanes 32 (w mod 4) .. +31 = output rows) and store float32 rows coalesced along r.
-// So loads of tile t+1, products of tile t and the epilogue of tile t-1 overlap.  Every
-// wait is bounded and also watches a shared abort flag: on expiry the CTA records
+// Every wait is bounded and also watches a shared abort flag: on expiry the CTA records
 // kErrTimeout, the other roles leave their loops, and TMEM is still freed.
 #pragma once
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 
@@ -37,10 +41,13 @@ constexpr int kMaxKBlocks = 2;   // K <= 128
 constexpr uint32_t kABlockBytes = kM * 128;   // 16 KB per K block and plane
 
 template <int NP> struct Cfg;
-template <> struct Cfg<2> { static constexpr int BN = 128; };
+template <> struct Cfg<2> { static constexpr int BN = 64; };
 template <> struct Cfg<3> { static constexpr int BN = 64; };
 constexpr int kStagesB = 2;
-constexpr int kThreads = 192;
+constexpr int kConvWarps = 8;
+constexpr int kConvThreads = 32 * kConvWarps;
+constexpr int kThreads = 192 + kConvThreads;
+constexpr int kConvMax = 8;   // float4 chunks per converter thread and tile (BN = 64, K <= 128)
 
 template <int NP>
 __host__ __device__ constexpr uint32_t stage_bytes() { return NP * kMaxKBlocks * (uint32_t)Cfg<NP>::BN * 128u; }
@@ -53,17 +60,19 @@ constexpr int kErrTimeout = 4;
 constexpr long long kSpinLimit = 1ll << 26;
 
 struct Params {
-  float* D;       // [mh][ncol][M]
-  int M;          // valid rows (Ntheta)
-  int ncol;       // columns per m
-  int kblocks;    // ceil(K / 64)
-  int nsplit;     // CTAs per m (gridDim.x); each takes a contiguous range of column tiles
+  float* D;          // [mh][ncol][M]
+  const float* B;    // panel [mh][ncol][kstride] float32
+  int M;             // valid rows (Ntheta)
+  int K;             // valid K (Ntheta)
+  int kstride;       // panel row stride (multiple of 8)
+  int ncol;          // columns per m
+  int kblocks;       // ceil(K / 64)
+  int nsplit;        // CTAs per m (gridDim.x); each takes a contiguous range of column tiles
   int* err;
 };
 
 struct Maps {
   CUtensorMap a[3];   // A planes
-  CUtensorMap b[3];   // B planes
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -76,6 +85,18 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void st_shared_v2(uint32_t addr, uint32_t a, uint32_t b) {
+  asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(a), "r"(b) : "memory");
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
 }
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
@@ -203,7 +224,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm_split(const __grid_cons
     s_abort = 0;
     mbar_init(smem_u32(&bar_a), 1);
     for (int q = 0; q < kStagesB; ++q) {
-      mbar_init(smem_u32(&bar_full[q]), 1);
+      mbar_init(smem_u32(&bar_full[q]), kConvThreads);
       mbar_init(smem_u32(&bar_empty[q]), 1);
     }
     for (int q = 0; q < 2; ++q) {
@@ -224,31 +245,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm_split(const __grid_cons
 
   if (warp == 0) {
     if (lane == 0 && nt > 0) {
-      // ---- producer
+      // ---- table planes of m, once
       const uint32_t ba = smem_u32(&bar_a);
       mbar_expect_tx(ba, (uint32_t)kb * NP * kABlockBytes);
       for (int pl = 0; pl < NP; ++pl)
         for (int b = 0; b < kb; ++b) tma_load_3d(sA + (pl * kMaxKBlocks + b) * kABlockBytes, &maps.a[pl], b * kKBlk, 0, m, ba);
-      int issued = 0;
-      for (int t = 0; t < nt; ++t) {
-        const int st = t % kStagesB;
-        const uint32_t ph = (uint32_t)(t / kStagesB) & 1u;
-        if (t >= kStagesB && !mbar_wait_or_abort(smem_u32(&bar_empty[st]), ph ^ 1u, abort)) {
-          fail();
-          break;
-        }
-        const uint32_t bf = smem_u32(&bar_full[st]);
-        mbar_expect_tx(bf, (uint32_t)kb * NP * kBBlockBytes);
-        const int n0 = (t0 + t) * BN;
-        for (int pl = 0; pl < NP; ++pl)
-          for (int b = 0; b < kb; ++b)
-            tma_load_3d(sB + st * kStage + (pl * kMaxKBlocks + b) * kBBlockBytes, &maps.b[pl], b * kKBlk, n0, m, bf);
-        issued = t + 1;
-      }
-      // copies in flight land before the CTA frees its shared memory
+      // the copy lands before the CTA frees its shared memory
       mbar_wait(ba, 0);
-      for (int t = issued - kStagesB > 0 ? issued - kStagesB : 0; t < issued; ++t)
-        mbar_wait(smem_u32(&bar_full[t % kStagesB]), (uint32_t)(t / kStagesB) & 1u);
     }
   } else if (warp == 1) {
     if (lane == 0 && nt > 0) {
@@ -293,7 +296,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm_split(const __grid_cons
       }
       if (!ok) fail();
     }
-  } else {
+  } else if (warp < 6) {
     // ---- epilogue: warps 2..5
     const int quarter = warp & 3;
     const int row = quarter * 32 + lane;
@@ -328,6 +331,66 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm_split(const __grid_cons
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       mbar_arrive(smem_u32(&bar_tempty[acc_buf]));
+    }
+  } else {
+    // ---- panel converter: warps 6..13.  Chunk c = ct + kConvThreads u of a tile is the
+    // float4 (row r, k = 4 k4 .. 4 k4 + 3) with cpr = 16 kb chunks per row, so a warp
+    // reads whole 256- or 512-byte row segments.
+    const int ct = tid - 192;
+    const int cpr = kb * (kKBlk / 4);
+    const int cshift = kb == 2 ? 5 : 4;
+    const int nper = BN * cpr / kConvThreads;   // 8 (K <= 128) or 4 (K <= 64)
+    const float* Bm = prm.B + (size_t)m * prm.ncol * prm.kstride;
+    auto fetch = [&](int t, float4 (&v)[kConvMax]) {
+      const int n0 = (t0 + t) * BN;
+#pragma unroll
+      for (int u = 0; u < kConvMax; ++u) {
+        v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        const int c = ct + kConvThreads * u;
+        const int r = c >> cshift, k4 = c & (cpr - 1);
+        if (u < nper && n0 + r < prm.ncol && 4 * k4 < prm.kstride)
+          v[u] = __ldg(reinterpret_cast<const float4*>(Bm + (size_t)(n0 + r) * prm.kstride + 4 * k4));
+      }
+    };
+    float4 cur[kConvMax], nxt[kConvMax];
+    if (nt > 0) fetch(0, cur);
+    for (int t = 0; t < nt; ++t) {
+      if (t + 1 < nt) fetch(t + 1, nxt);
+      const int st = t % kStagesB;
+      const uint32_t ph = (uint32_t)(t / kStagesB) & 1u;
+      if (t >= kStagesB && !mbar_wait_or_abort(smem_u32(&bar_empty[st]), ph ^ 1u, abort)) {
+        fail();
+        break;
+      }
+      const uint32_t bst = sB + st * kStage;
+#pragma unroll
+      for (int u = 0; u < kConvMax; ++u) {
+        if (u < nper) {
+          const int c = ct + kConvThreads * u;
+          const int r = c >> cshift, k4 = c & (cpr - 1);
+          const int b = k4 >> 4, kc4 = k4 & 15;
+          // 16-byte chunk kc4/2 of row r sits at chunk (kc4/2) ^ (r mod 8) of the 128-byte row
+          const uint32_t off = (uint32_t)r * 128u + ((uint32_t)((kc4 >> 1) ^ (r & 7)) << 4) + (uint32_t)(kc4 & 1) * 8u;
+          float x[4] = {cur[u].x, cur[u].y, cur[u].z, cur[u].w};
+          __nv_bfloat16 h[3][4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const float v = (4 * k4 + e < prm.K) ? x[e] : 0.f;
+            h[0][e] = __float2bfloat16_rn(v);
+            const float r1 = v - __bfloat162float(h[0][e]);
+            h[1][e] = __float2bfloat16_rn(r1);
+            if (NP == 3) h[2][e] = __float2bfloat16_rn(r1 - __bfloat162float(h[1][e]));
+          }
+#pragma unroll
+          for (int pl = 0; pl < NP; ++pl)
+            st_shared_v2(bst + (uint32_t)(pl * kMaxKBlocks + b) * kBBlockBytes + off, pack_bf16(h[pl][0], h[pl][1]),
+                         pack_bf16(h[pl][2], h[pl][3]));
+        }
+      }
+      fence_proxy_async_smem();
+      mbar_arrive(smem_u32(&bar_full[st]));
+#pragma unroll
+      for (int u = 0; u < kConvMax; ++u) cur[u] = nxt[u];
     }
   }
   // the last products complete before TMEM is freed
