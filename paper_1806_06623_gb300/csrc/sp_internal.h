@@ -238,13 +238,16 @@ int create_side_stream(Plan& p);   // side stream and events of a mixed multipol
 struct MixedRun {
   double e_prev = 0.0, pmax = 0.0, est = 1.0, last = 1.0;
   double hist[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  int iters = 0;   // low-precision solves issued and read
+  int iters = 0;       // low-precision solves read
+  int pending = 0;     // reductions copied to host slots but not yet read (at most 2)
+  int next_slot = 0;   // host slot of the next copy
   bool done = false;
 };
+constexpr int kRedErrWord = 4;   // h_red: two slots of (max|e|, max|Phi|), then the status word
 int mixed_start(Plan* p, const double* rho, cudaStream_t s);
 int mixed_correct(Plan* p, const double* rho, cudaStream_t s);
-int mixed_issue_read(Plan* p, cudaStream_t s);
-void mixed_decide(Plan* p, MixedRun& R);
+int mixed_issue_read(Plan* p, cudaStream_t s, MixedRun& R);
+void mixed_decide(Plan* p, MixedRun& R);   // after the stream has reached the pending copies
 int mixed_finish(Plan* p, double* phi, cudaStream_t s, const MixedRun& R, sp_solve_info* info);
 int mixed_finish_issue(Plan* p, double* phi, cudaStream_t s);
 int mixed_finish_status(Plan* p, const MixedRun& R, sp_solve_info* info);

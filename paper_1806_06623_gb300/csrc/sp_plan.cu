@@ -192,20 +192,26 @@ int mixed_correct(Plan* p, const double* rho, cudaStream_t s) {
   return lp_solve(p, P.mixed->r32, false, (float)(1.0 / P.nphi), nullptr, false, s);
 }
 
-// Queue the copy of the reductions of the last low-precision solve to pinned host memory.
-int mixed_issue_read(Plan* p, cudaStream_t s) {
-  SP_CUDA(cudaMemcpyAsync(p->h_red, p->mixed->red, 2 * sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+// Queue the copy of the reductions of the last low-precision solve to the next of two
+// pinned host slots.
+int mixed_issue_read(Plan* p, cudaStream_t s, MixedRun& R) {
+  SP_CUDA(cudaMemcpyAsync(p->h_red + 2 * R.next_slot, p->mixed->red, 2 * sizeof(unsigned int), cudaMemcpyDeviceToHost,
+                          s));
+  R.next_slot ^= 1;
+  ++R.pending;
   return SP_OK;
 }
 
-// After the stream has reached the copy: update the refinement state.  |e_k| measures the
-// error of the previous iterate; the current one is smaller by the contraction factor of
-// the refinement, taken as the larger of the observed ratio of successive corrections and
-// a bound for the mode (largest ratio measured over the stellar, ragged, point-mass and
-// random-source workloads, times two: 1.9e-5 for 6 products, 1.2e-3 for 3 products).
-void mixed_decide(Plan* p, MixedRun& R) {
+namespace {
+
+// One low-precision solve's reductions: |e_k| measures the error of the previous iterate;
+// the current one is smaller by the contraction factor of the refinement, taken as the
+// larger of the observed ratio of successive corrections and a bound for the mode
+// (largest ratio measured over the stellar, ragged, point-mass and random-source
+// workloads, times two: 1.9e-5 for 6 products, 1.2e-3 for 3 products).
+void decide_one(Plan* p, MixedRun& R, const unsigned int* slot) {
   float v[2];
-  std::memcpy(v, p->h_red, sizeof(v));
+  std::memcpy(v, slot, sizeof(v));
   const double e_cur = v[0];
   R.pmax = v[1];
   if (R.iters == 0) {
@@ -229,19 +235,29 @@ void mixed_decide(Plan* p, MixedRun& R) {
   ++R.iters;
 }
 
+}  // namespace
+
+// Read the pending slots in issue order; a solve queued behind one that already met the
+// tolerance is not counted (its correction is below the tolerance by construction).
+void mixed_decide(Plan* p, MixedRun& R) {
+  int slot = (R.next_slot - R.pending) & 1;
+  for (; R.pending > 0; --R.pending, slot ^= 1)
+    if (!R.done) decide_one(p, R, p->h_red + 2 * slot);
+}
+
 // Float-float iterate -> float64 Phi and the copy of the device status word (asynchronous).
 int mixed_finish_issue(Plan* p, double* phi, cudaStream_t s) {
   Plan& P = *p;
   int st;
   if ((st = launch_status(timed_launch(P, kKUpdate, s, [&] { return finish_mixed(P, phi, s); })))) return st;
-  SP_CUDA(cudaMemcpyAsync(P.h_red + 2, P.d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  SP_CUDA(cudaMemcpyAsync(P.h_red + kRedErrWord, P.d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
   return SP_OK;
 }
 
 // After the stream has reached mixed_finish_issue: status and info.
 int mixed_finish_status(Plan* p, const MixedRun& R, sp_solve_info* info) {
   Plan& P = *p;
-  const int herr = (int)P.h_red[2];
+  const int herr = (int)P.h_red[kRedErrWord];
   const int st = herr ? ((herr & kErrTimeout) ? SP_ERR_TIMEOUT : SP_ERR_DEVICE_CHECK)
                       : (R.done ? SP_OK : SP_ERR_NOT_CONVERGED);
   if (info) {
@@ -286,13 +302,21 @@ namespace {
 int solve_mixed(Plan* p, const double* rho, double* phi, cudaStream_t s, sp_solve_info* info) {
   sp::MixedRun R;
   int st;
+  // The first low-precision solve meets the tolerance only for rho == 0, so the first
+  // correction is queued right behind it and both are read after one synchronisation.
   if ((st = sp::mixed_start(p, rho, s))) return st;
-  if ((st = sp::mixed_issue_read(p, s))) return st;
+  if ((st = sp::mixed_issue_read(p, s, R))) return st;
+  int k = 1;
+  if (p->max_iter >= 1) {
+    if ((st = sp::mixed_correct(p, rho, s))) return st;
+    if ((st = sp::mixed_issue_read(p, s, R))) return st;
+    k = 2;
+  }
   SP_CUDA(cudaStreamSynchronize(s));
   sp::mixed_decide(p, R);
-  for (int k = 1; k <= p->max_iter && !R.done; ++k) {
+  for (; k <= p->max_iter && !R.done; ++k) {
     if ((st = sp::mixed_correct(p, rho, s))) return st;
-    if ((st = sp::mixed_issue_read(p, s))) return st;
+    if ((st = sp::mixed_issue_read(p, s, R))) return st;
     SP_CUDA(cudaStreamSynchronize(s));
     sp::mixed_decide(p, R);
   }
@@ -527,7 +551,7 @@ int sp_plan_create(const double* r_if, int nr, const double* th_if_in, int nth, 
       if ((st = launch_status(sp::outer_operator_f64(*p, s)))) break;
     }
     if (precision != SP_FP64 && (st = sp::mixed_create_tables(*p, s))) break;
-    if (precision != SP_FP64 && cudaMallocHost(&p->h_red, 4 * sizeof(unsigned int)) != cudaSuccess) {
+    if (precision != SP_FP64 && cudaMallocHost(&p->h_red, 8 * sizeof(unsigned int)) != cudaSuccess) {
       st = SP_ERR_OOM;
       break;
     }
@@ -569,7 +593,7 @@ int sp_plan_clone(const sp_plan* src_plan, sp_plan** out) {
     c->mixed = new (std::nothrow) sp::MixedTables(*src->mixed);
     if (!c->mixed) st = SP_ERR_OOM;
     else sp::mixed_clear_workspace(*c->mixed);
-    if (st == SP_OK && cudaMallocHost(&c->h_red, 4 * sizeof(unsigned int)) != cudaSuccess) st = SP_ERR_OOM;
+    if (st == SP_OK && cudaMallocHost(&c->h_red, 8 * sizeof(unsigned int)) != cudaSuccess) st = SP_ERR_OOM;
   }
   c->side = nullptr;
   c->ev_fork = c->ev_join = nullptr;
