@@ -14,14 +14,15 @@
 // Persistent per m, warp-specialised pipeline (448 threads, one CTA per SM):
 //  - warp 0 (one lane) loads the A planes of m once (TMA, 128B-swizzled K-major boxes of
 //    64 K-elements);
-//  - warps 6..13 stream the panel rows of the CTA's column tiles (float4 loads, the
-//    next tile in flight while the current one is converted), split them into bf16
-//    planes and store those in the 128B-swizzled K-major layout of a two-stage ring
-//    (full/empty mbarriers per stage, fence.proxy.async before the arrival);
-//  - warp 1 (one lane) issues, per tile, the K-steps x products of tcgen05.mma
-//    (M=128, N=BN, K=16, kind::f16, bf16 inputs, f32 accumulator) into one of two TMEM
-//    accumulators and commits to the stage's empty barrier and the accumulator's full
-//    barrier;
+//  - warps 6..13 stream the panel rows of the CTA's column tiles one K block at a time
+//    (float4 loads, the next block in flight while the current one is converted),
+//    split them into bf16 planes and store those in the 128B-swizzled K-major layout of
+//    a ring of stages (full/empty mbarriers per stage, fence.proxy.async before the
+//    arrival);
+//  - warp 1 (one lane) issues, per K block, the K-steps x products of tcgen05.mma
+//    (M=128, N=BN=128, K=16, kind::f16, bf16 inputs, f32 accumulator) into one of two
+//    TMEM accumulators and commits to the stage's empty barrier (and, after a tile's
+//    last K block, to the accumulator's full barrier);
 //  - warps 2..5 drain the other accumulator meanwhile (tcgen05.ld; warp w owns TMEM
 //    lanes 32 (w mod 4) .. +31 = output rows) and store float32 rows coalesced along r.
 // Every wait is bounded and also watches a shared abort flag: on expiry the CTA records
@@ -41,20 +42,22 @@ constexpr int kMaxKBlocks = 2;   // K <= 128
 constexpr uint32_t kABlockBytes = kM * 128;   // 16 KB per K block and plane
 
 template <int NP> struct Cfg;
-template <> struct Cfg<2> { static constexpr int BN = 64; };
-template <> struct Cfg<3> { static constexpr int BN = 64; };
-constexpr int kStagesB = 2;
+// N = 128 per MMA (N = 64 runs at about half the per-column rate); the panel streams
+// through shared memory one K block (64 K-elements) of a tile at a time
+template <> struct Cfg<2> { static constexpr int BN = 128; static constexpr int kStages = 4; };
+template <> struct Cfg<3> { static constexpr int BN = 128; static constexpr int kStages = 2; };
 constexpr int kConvWarps = 8;
 constexpr int kConvThreads = 32 * kConvWarps;
 constexpr int kThreads = 192 + kConvThreads;
-constexpr int kConvMax = 8;   // float4 chunks per converter thread and tile (BN = 64, K <= 128)
+constexpr int kConvPer = 8;   // float4 chunks per converter thread and K block (BN = 128 rows x 16)
 
+// one stage: the NP planes of one K block of a BN-column tile
 template <int NP>
-__host__ __device__ constexpr uint32_t stage_bytes() { return NP * kMaxKBlocks * (uint32_t)Cfg<NP>::BN * 128u; }
+__host__ __device__ constexpr uint32_t stage_bytes() { return NP * (uint32_t)Cfg<NP>::BN * 128u; }
 
 template <int NP>
 constexpr uint32_t smem_bytes() {
-  return NP * kMaxKBlocks * kABlockBytes + kStagesB * stage_bytes<NP>() + 1024u;
+  return NP * kMaxKBlocks * kABlockBytes + Cfg<NP>::kStages * stage_bytes<NP>() + 1024u;
 }
 constexpr int kErrTimeout = 4;
 constexpr long long kSpinLimit = 1ll << 26;
@@ -95,8 +98,16 @@ __device__ __forceinline__ void st_shared_v2(uint32_t addr, uint32_t a, uint32_t
   asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(a), "r"(b) : "memory");
 }
 
-__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi) {
-  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+// Round-to-nearest-even of a finite float to bf16 with integer operations (faster than
+// the conversion unit here), returned as float bits with the low half zero.
+__device__ __forceinline__ uint32_t bf16_rn_bits(float v) {
+  const uint32_t u = __float_as_uint(v);
+  return (u + 0x7FFFu + ((u >> 16) & 1u)) & 0xFFFF0000u;
+}
+
+// Bulk prefetch of [p, p + bytes) into L2 (16-byte aligned address and size).
+__device__ __forceinline__ void prefetch_l2_bulk(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
@@ -192,15 +203,16 @@ __device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, float (&v)[32
 template <int NP>
 __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm_split(const __grid_constant__ Maps maps, Params prm) {
   constexpr int BN = Cfg<NP>::BN;
-  constexpr uint32_t kBBlockBytes = BN * 128u;
+  constexpr int S = Cfg<NP>::kStages;
+  constexpr uint32_t kPlaneBytes = BN * 128u;   // one plane of one K block
   constexpr uint32_t kStage = stage_bytes<NP>();
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte alignment of the swizzle atoms
   const uint32_t base_u32 = (smem_u32(smem_raw) + 1023u) & ~1023u;
   const uint32_t sA = base_u32;                                  // [NP][kMaxKBlocks] x 16 KB
-  const uint32_t sB = sA + NP * kMaxKBlocks * kABlockBytes;      // [kStagesB][NP][kMaxKBlocks] x BN*128 B
+  const uint32_t sB = sA + NP * kMaxKBlocks * kABlockBytes;      // [S][NP] x BN*128 B
   __shared__ __align__(8) uint64_t bar_a;
-  __shared__ __align__(8) uint64_t bar_full[kStagesB], bar_empty[kStagesB];
+  __shared__ __align__(8) uint64_t bar_full[S], bar_empty[S];
   __shared__ __align__(8) uint64_t bar_tfull[2], bar_tempty[2];
   __shared__ uint32_t tmem_base;
   __shared__ int s_abort;
@@ -214,6 +226,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm_split(const __grid_cons
   const int t0 = (int)(((long long)tiles * blockIdx.x) / prm.nsplit);
   const int t1 = (int)(((long long)tiles * (blockIdx.x + 1)) / prm.nsplit);
   const int nt = t1 - t0;
+  const int nq = nt * kb;   // work chunks q = (tile t = q / kb, K block b = q % kb)
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
@@ -223,7 +236,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm_split(const __grid_cons
   if (tid == 32) {
     s_abort = 0;
     mbar_init(smem_u32(&bar_a), 1);
-    for (int q = 0; q < kStagesB; ++q) {
+    for (int q = 0; q < S; ++q) {
       mbar_init(smem_u32(&bar_full[q]), kConvThreads);
       mbar_init(smem_u32(&bar_empty[q]), 1);
     }
@@ -264,35 +277,32 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm_split(const __grid_cons
       // any shared-memory address), so each is a base plus a compile-time offset
       const uint64_t dA0 = smem_desc_sw128(sA);
       bool ok = mbar_wait_or_abort(smem_u32(&bar_a), 0, abort);
-      for (int t = 0; ok && t < nt; ++t) {
-        const int st = t % kStagesB;
-        const uint32_t ph = (uint32_t)(t / kStagesB) & 1u;
+      for (int q = 0; ok && q < nq; ++q) {
+        const int t = q / kb, b = q - t * kb;
+        const int st = q % S;
+        const uint32_t ph = (uint32_t)(q / S) & 1u;
         const int acc_buf = t & 1;
         const uint32_t aph = (uint32_t)(t >> 1) & 1u;
         if (!mbar_wait_or_abort(smem_u32(&bar_full[st]), ph, abort) ||
-            (t >= 2 && !mbar_wait_or_abort(smem_u32(&bar_tempty[acc_buf]), aph ^ 1u, abort))) {
+            (b == 0 && t >= 2 && !mbar_wait_or_abort(smem_u32(&bar_tempty[acc_buf]), aph ^ 1u, abort))) {
           ok = false;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t dt = tmem + (uint32_t)(acc_buf * BN);
         const uint64_t dB0 = smem_desc_sw128(sB + st * kStage);
+        const uint64_t dAb = dA0 + (uint64_t)(((uint32_t)b * kABlockBytes) >> 4);
 #pragma unroll
-        for (int b = 0; b < kMaxKBlocks; ++b) {
-          if (b < kb) {
+        for (int k4 = 0; k4 < kKBlk / 16; ++k4) {   // 16 bf16 = 32 B along the swizzled row
 #pragma unroll
-            for (int k4 = 0; k4 < kKBlk / 16; ++k4) {   // 16 bf16 = 32 B along the swizzled row
-#pragma unroll
-              for (int q = 0; q < npairs; ++q) {
-                const uint64_t da = dA0 + (((uint32_t)(pa[q] * kMaxKBlocks + b) * kABlockBytes + k4 * 32u) >> 4);
-                const uint64_t db = dB0 + (((uint32_t)(pb[q] * kMaxKBlocks + b) * kBBlockBytes + k4 * 32u) >> 4);
-                umma_bf16(dt, da, db, idesc, (b | k4 | q) ? 1u : 0u);
-              }
-            }
+          for (int i = 0; i < npairs; ++i) {
+            const uint64_t da = dAb + (((uint32_t)pa[i] * kMaxKBlocks * kABlockBytes + k4 * 32u) >> 4);
+            const uint64_t db = dB0 + (((uint32_t)pb[i] * kPlaneBytes + k4 * 32u) >> 4);
+            umma_bf16(dt, da, db, idesc, (b | k4 | i) ? 1u : 0u);
           }
         }
         umma_commit(smem_u32(&bar_empty[st]));
-        umma_commit(smem_u32(&bar_tfull[acc_buf]));
+        if (b == kb - 1) umma_commit(smem_u32(&bar_tfull[acc_buf]));
       }
       if (!ok) fail();
     }
@@ -321,11 +331,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm_split(const __grid_cons
         if (row < prm.M) {
           if (full) {
 #pragma unroll
-            for (int q = 0; q < 32; ++q) dst[(size_t)(c0 + q) * prm.M] = v[q];
+            for (int i = 0; i < 32; ++i) dst[(size_t)(c0 + i) * prm.M] = v[i];
           } else {
 #pragma unroll
-            for (int q = 0; q < 32; ++q)
-              if (n0 + c0 + q < prm.ncol) dst[(size_t)(c0 + q) * prm.M] = v[q];
+            for (int i = 0; i < 32; ++i)
+              if (n0 + c0 + i < prm.ncol) dst[(size_t)(c0 + i) * prm.M] = v[i];
           }
         }
       }
@@ -333,64 +343,72 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm_split(const __grid_cons
       mbar_arrive(smem_u32(&bar_tempty[acc_buf]));
     }
   } else {
-    // ---- panel converter: warps 6..13.  Chunk c = ct + kConvThreads u of a tile is the
-    // float4 (row r, k = 4 k4 .. 4 k4 + 3) with cpr = 16 kb chunks per row, so a warp
-    // reads whole 256- or 512-byte row segments.
+    // ---- panel converter: warps 6..13.  Chunk c = ct + kConvThreads u of a K block is
+    // the float4 (row r = c / 16, k = 64 b + 4 (c mod 16) .. + 3), so a half-warp reads
+    // one 256-byte row segment.
     const int ct = tid - 192;
-    const int cpr = kb * (kKBlk / 4);
-    const int cshift = kb == 2 ? 5 : 4;
-    const int nper = BN * cpr / kConvThreads;   // 8 (K <= 128) or 4 (K <= 64)
     const float* Bm = prm.B + (size_t)m * prm.ncol * prm.kstride;
-    auto fetch = [&](int t, float4 (&v)[kConvMax]) {
+    auto fetch = [&](int q, float4 (&v)[kConvPer]) {
+      const int t = q / kb, b = q - t * kb;
       const int n0 = (t0 + t) * BN;
 #pragma unroll
-      for (int u = 0; u < kConvMax; ++u) {
+      for (int u = 0; u < kConvPer; ++u) {
         v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
         const int c = ct + kConvThreads * u;
-        const int r = c >> cshift, k4 = c & (cpr - 1);
-        if (u < nper && n0 + r < prm.ncol && 4 * k4 < prm.kstride)
-          v[u] = __ldg(reinterpret_cast<const float4*>(Bm + (size_t)(n0 + r) * prm.kstride + 4 * k4));
+        const int r = c >> 4, k = b * kKBlk + 4 * (c & 15);
+        if (n0 + r < prm.ncol && k < prm.kstride)
+          v[u] = __ldg(reinterpret_cast<const float4*>(Bm + (size_t)(n0 + r) * prm.kstride + k));
       }
     };
-    float4 cur[kConvMax], nxt[kConvMax];
-    if (nt > 0) fetch(0, cur);
-    for (int t = 0; t < nt; ++t) {
-      if (t + 1 < nt) fetch(t + 1, nxt);
-      const int st = t % kStagesB;
-      const uint32_t ph = (uint32_t)(t / kStagesB) & 1u;
-      if (t >= kStagesB && !mbar_wait_or_abort(smem_u32(&bar_empty[st]), ph ^ 1u, abort)) {
+    // one thread keeps the rows of the tiles two ahead on their way into L2 (a tile's
+    // rows are contiguous), so the register loads of the next K block hit L2
+    auto prefetch_tile = [&](int t) {
+      if (ct != 0 || t >= nt) return;
+      const int n0 = (t0 + t) * BN;
+      const int rows = min(BN, prm.ncol - n0);
+      prefetch_l2_bulk(Bm + (size_t)n0 * prm.kstride, (uint32_t)rows * (uint32_t)prm.kstride * 4u);
+    };
+    prefetch_tile(0);
+    prefetch_tile(1);
+    float4 cur[kConvPer], nxt[kConvPer];
+    if (nq > 0) fetch(0, cur);
+    for (int q = 0; q < nq; ++q) {
+      if (q % kb == 0) prefetch_tile(q / kb + 2);
+      if (q + 1 < nq) fetch(q + 1, nxt);
+      const int st = q % S;
+      const uint32_t ph = (uint32_t)(q / S) & 1u;
+      if (q >= S && !mbar_wait_or_abort(smem_u32(&bar_empty[st]), ph ^ 1u, abort)) {
         fail();
         break;
       }
+      const int b = q % kb;
       const uint32_t bst = sB + st * kStage;
 #pragma unroll
-      for (int u = 0; u < kConvMax; ++u) {
-        if (u < nper) {
-          const int c = ct + kConvThreads * u;
-          const int r = c >> cshift, k4 = c & (cpr - 1);
-          const int b = k4 >> 4, kc4 = k4 & 15;
-          // 16-byte chunk kc4/2 of row r sits at chunk (kc4/2) ^ (r mod 8) of the 128-byte row
-          const uint32_t off = (uint32_t)r * 128u + ((uint32_t)((kc4 >> 1) ^ (r & 7)) << 4) + (uint32_t)(kc4 & 1) * 8u;
-          float x[4] = {cur[u].x, cur[u].y, cur[u].z, cur[u].w};
-          __nv_bfloat16 h[3][4];
+      for (int u = 0; u < kConvPer; ++u) {
+        const int c = ct + kConvThreads * u;
+        const int r = c >> 4, kc4 = c & 15;
+        const int k = b * kKBlk + 4 * kc4;
+        // 16-byte chunk kc4/2 of row r sits at chunk (kc4/2) ^ (r mod 8) of the 128-byte row
+        const uint32_t off = (uint32_t)r * 128u + ((uint32_t)((kc4 >> 1) ^ (r & 7)) << 4) + (uint32_t)(kc4 & 1) * 8u;
+        const float x[4] = {cur[u].x, cur[u].y, cur[u].z, cur[u].w};
+        uint32_t h[3][4];
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const float v = (4 * k4 + e < prm.K) ? x[e] : 0.f;
-            h[0][e] = __float2bfloat16_rn(v);
-            const float r1 = v - __bfloat162float(h[0][e]);
-            h[1][e] = __float2bfloat16_rn(r1);
-            if (NP == 3) h[2][e] = __float2bfloat16_rn(r1 - __bfloat162float(h[1][e]));
-          }
-#pragma unroll
-          for (int pl = 0; pl < NP; ++pl)
-            st_shared_v2(bst + (uint32_t)(pl * kMaxKBlocks + b) * kBBlockBytes + off, pack_bf16(h[pl][0], h[pl][1]),
-                         pack_bf16(h[pl][2], h[pl][3]));
+        for (int e = 0; e < 4; ++e) {
+          const float v = (k + e < prm.K) ? x[e] : 0.f;
+          h[0][e] = bf16_rn_bits(v);
+          const float r1 = v - __uint_as_float(h[0][e]);
+          h[1][e] = bf16_rn_bits(r1);
+          h[2][e] = bf16_rn_bits(r1 - __uint_as_float(h[1][e]));
         }
+#pragma unroll
+        for (int pl = 0; pl < NP; ++pl)
+          st_shared_v2(bst + (uint32_t)pl * kPlaneBytes + off, __byte_perm(h[pl][0], h[pl][1], 0x7632),
+                       __byte_perm(h[pl][2], h[pl][3], 0x7632));
       }
       fence_proxy_async_smem();
       mbar_arrive(smem_u32(&bar_full[st]));
 #pragma unroll
-      for (int u = 0; u < kConvMax; ++u) cur[u] = nxt[u];
+      for (int u = 0; u < kConvPer; ++u) cur[u] = nxt[u];
     }
   }
   // the last products complete before TMEM is freed
