@@ -122,6 +122,103 @@ __device__ typename C2<T>::t* warp_fft(typename C2<T>::t* bufA, typename C2<T>::
   return src;
 }
 
+// ---- Nphi = 256: two radix-16 Stockham passes, each butterfly a 4 x 4 DFT in registers.
+// Pass 1 (Ns = 1) reads z[b + 16 r] and writes the padded intermediate w[17 b + r];
+// pass 2 (Ns = 16) reads w[17 r + b], twiddles by exp(-+2 pi i r b / 256) and writes
+// the spectrum z[b + 16 q].  Half a warp per line pair (lane = butterfly b), so a warp
+// runs two pairs per pass (pairs w and w + kWarps, as in the generic path, so the owner
+// of a pair is the same in every phase); the padding keeps both passes free of bank
+// conflicts.
+constexpr int kPad256 = 272;   // 16 x 17 intermediate stride per line pair
+
+template <bool INV, typename CT>
+__device__ __forceinline__ void dft4(CT& a, CT& b, CT& c, CT& d) {
+  const CT y0 = cadd(a, c), y1 = csub(a, c), y2 = cadd(b, d), y3 = mul_mi<INV>(csub(b, d));
+  a = cadd(y0, y2);
+  b = cadd(y1, y3);
+  c = csub(y0, y2);
+  d = csub(y1, y3);
+}
+
+// In-register 16-point DFT of v[r] (r = 0..15); result X[q] in v[q].
+template <bool INV, typename T>
+__device__ __forceinline__ void dft16(typename C2<T>::t (&v)[16]) {
+  using CT = typename C2<T>::t;
+  // 4-point DFTs over r1 for each r2 (r = r2 + 4 r1): u[r2][q1] in v[r2 + 4 q1]
+#pragma unroll
+  for (int r2 = 0; r2 < 4; ++r2) dft4<INV>(v[r2], v[r2 + 4], v[r2 + 8], v[r2 + 12]);
+  // twiddles exp(-+2 pi i r2 q1 / 16)
+  const T c1 = T(0.92387953251128675613), s1 = T(0.38268343236508977173), h = T(0.70710678118654752440);
+  auto tw = [&](CT& x, T c, T sn) {   // x *= c - i sn (forward) or c + i sn (inverse)
+    const T sg = INV ? sn : -sn;
+    CT r;
+    r.x = x.x * c - x.y * sg;
+    r.y = x.x * sg + x.y * c;
+    x = r;
+  };
+  tw(v[5], c1, s1);   // r2 = 1, q1 = 1: w^1
+  tw(v[9], h, h);     // r2 = 1, q1 = 2: w^2
+  tw(v[13], s1, c1);  // r2 = 1, q1 = 3: w^3
+  tw(v[6], h, h);     // r2 = 2, q1 = 1: w^2
+  v[10] = mul_mi<INV>(v[10]);   // r2 = 2, q1 = 2: w^4 = -+i
+  tw(v[14], -h, h);   // r2 = 2, q1 = 3: w^6
+  tw(v[7], s1, c1);   // r2 = 3, q1 = 1: w^3
+  tw(v[11], -h, h);   // r2 = 3, q1 = 2: w^6
+  tw(v[15], -c1, -s1);   // r2 = 3, q1 = 3: w^9
+  // 4-point DFTs over r2 for each q1: X[q1 + 4 q2] lands in v[4 q1 + q2]
+#pragma unroll
+  for (int q1 = 0; q1 < 4; ++q1) dft4<INV>(v[4 * q1], v[4 * q1 + 1], v[4 * q1 + 2], v[4 * q1 + 3]);
+}
+
+template <bool INV, typename T>
+__device__ typename C2<T>::t* warp_fft256(typename C2<T>::t* bufA, typename C2<T>::t* bufB,
+                                          const typename C2<T>::t* tw, int npairs, int PS) {
+  using CT = typename C2<T>::t;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int b = lane & 15;
+  CT v[16];
+  for (int p0 = warp; p0 < npairs; p0 += 2 * kWarps) {
+    const int p = p0 + (lane >> 4) * kWarps;   // pair p stays with warp p mod kWarps
+    if (p < npairs) {
+      const CT* z = bufA + p * PS;
+#pragma unroll
+      for (int r = 0; r < 16; ++r) v[r] = z[b + 16 * r];
+      dft16<INV, T>(v);
+      CT* w = bufB + p * kPad256;
+      // X[q] with q = q1 + 4 q2 is in v[4 q1 + q2]; Stockham pass 1 output index 16 b + q
+#pragma unroll
+      for (int q1 = 0; q1 < 4; ++q1)
+#pragma unroll
+        for (int q2 = 0; q2 < 4; ++q2) w[17 * b + q1 + 4 * q2] = v[4 * q1 + q2];
+    }
+  }
+  __syncwarp();
+  for (int p0 = warp; p0 < npairs; p0 += 2 * kWarps) {
+    const int p = p0 + (lane >> 4) * kWarps;   // pair p stays with warp p mod kWarps
+    if (p < npairs) {
+      const CT* w = bufB + p * kPad256;
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {
+        CT x = w[17 * r + b];
+        if (r != 0 && b != 0) {
+          CT t = tw[r * b];
+          if (INV) t.y = -t.y;
+          x = cmul(x, t);
+        }
+        v[r] = x;
+      }
+      dft16<INV, T>(v);
+      CT* z = bufA + p * PS;
+#pragma unroll
+      for (int q1 = 0; q1 < 4; ++q1)
+#pragma unroll
+        for (int q2 = 0; q2 < 4; ++q2) z[b + 16 * (q1 + 4 * q2)] = v[4 * q1 + q2];
+    }
+  }
+  __syncwarp();
+  return bufA;
+}
+
 template <typename T>
 __device__ void load_twiddles(typename C2<T>::t* tw, const T* __restrict__ g, int n) {
   for (int t = threadIdx.x; t < n; t += blockDim.x) {
@@ -140,7 +237,7 @@ __device__ __forceinline__ T load_in(const float* p) { return (T)*p; }
 // Forward: lines [line0, line0+nl) of `in` -> half spectrum scaled by `scale`,
 // spec[m][i][c][j] with row stride `rs` (Ntheta, or the padded panel stride).
 template <typename T, typename Tin>
-__global__ void __launch_bounds__(256) k_fft_fwd(const Tin* __restrict__ in, int nlines, int nth, int nrs,
+__global__ void __launch_bounds__(256, 3) k_fft_fwd(const Tin* __restrict__ in, int nlines, int nth, int nrs,
                                                  FftSchedule sch, const T* __restrict__ twid, T scale, int lpc,
                                                  T* __restrict__ spec, int rs) {
   using CT = typename C2<T>::t;
@@ -180,7 +277,7 @@ __global__ void __launch_bounds__(256) k_fft_fwd(const Tin* __restrict__ in, int
   if (nl & 1)
     for (int q = threadIdx.x; q < n; q += blockDim.x) bufA[(nl >> 1) * PS + q].y = T(0);
   __syncthreads();
-  CT* Z = warp_fft<false, T>(bufA, bufB, tw, sch, npairs, PS);
+  CT* Z = n == 256 ? warp_fft256<false, T>(bufA, bufB, tw, npairs, PS) : warp_fft<false, T>(bufA, bufB, tw, sch, npairs, PS);
   __syncthreads();
   const int mh = n / 2 + 1;
   const int l = lane;
@@ -213,7 +310,7 @@ enum InvOut { kInvWrite = 0, kInvAccumulate = 1, kInvPairUpdate = 2 };
 //    (out, phi_lo) + e, with max|e| and max|hi| reduced into red[0], red[1]
 //    (non-negative float bit patterns, so integer max orders them).
 template <typename T, typename Tout, int MODE>
-__global__ void __launch_bounds__(256) k_fft_inv(const T* __restrict__ spec, int nlines, int nth, int nrs,
+__global__ void __launch_bounds__(256, 3) k_fft_inv(const T* __restrict__ spec, int nlines, int nth, int nrs,
                                                  FftSchedule sch, const T* __restrict__ twid, int lpc,
                                                  Tout* __restrict__ out, float* __restrict__ phi_lo, int first,
                                                  unsigned int* __restrict__ red) {
@@ -276,7 +373,7 @@ __global__ void __launch_bounds__(256) k_fft_inv(const T* __restrict__ spec, int
     }
   }
   __syncthreads();
-  CT* Z = warp_fft<true, T>(bufA, bufB, tw, sch, npairs, PS);
+  CT* Z = n == 256 ? warp_fft256<true, T>(bufA, bufB, tw, npairs, PS) : warp_fft<true, T>(bufA, bufB, tw, sch, npairs, PS);
   float me = 0.f, mp = 0.f;
   for (int p = warp; p < npairs; p += kWarps) {
     const CT* z = Z + p * PS;
@@ -358,7 +455,9 @@ int lines_per_cta(int n, int nlines) {
 
 template <typename T>
 size_t fft_smem(int n, int lpc) {
-  return sizeof(typename C2<T>::t) * ((size_t)n + 2 * (size_t)(lpc / 2) * (n + 1));
+  const size_t P = (size_t)(lpc / 2);
+  const size_t psb = n == 256 ? (size_t)kPad256 : (size_t)n + 1;
+  return sizeof(typename C2<T>::t) * ((size_t)n + P * (n + 1) + P * psb);
 }
 
 template <typename K>
