@@ -41,6 +41,10 @@ __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)), "l"(gmem)
                : "memory");
 }
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)), "l"(gmem)
+               : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
@@ -297,35 +301,52 @@ __global__ void __launch_bounds__(kScanThreads) k_thomas_scan(
   const int l = (mb - m * ncb) * kScanCols + col;
   const bool valid = l < nth;
   const bool work = valid && fabs(lam[m * nth + l]) >= thr;
-  const float* X = x + (size_t)m * nr * st + (size_t)c * nth + (valid ? l : 0);
-  const float* FC = fcp + (size_t)m * nr * nth + (valid ? l : 0);
-  const float* FI = finv + (size_t)m * nr * nth + (valid ? l : 0);
   // segments of odd length: the two segments a warp holds then sit 16 banks apart
   int L = (nr + kScanSegs - 1) / kScanSegs;
   L += (L & 1) ^ 1;
   const int i0 = min(nr, seg * L), i1 = min(nr, i0 + L);
-  // ---- stage the right-hand side and 1/pivot of the whole column block
-  if (valid)
-    for (int i = seg; i < nr; i += kScanSegs) {
-      cp_async4(&D[i * kScanCols + col], X + (size_t)i * st);
-      cp_async4(&Q[i * kScanCols + col], FI + (size_t)i * nth);
+  // ---- stage the right-hand side and 1/pivot of the whole column block: 16-byte copies
+  // (4 threads per 16-column row) when rows start on 16-byte boundaries, else 4-byte
+  const int lb0 = (mb - m * ncb) * kScanCols;
+  const bool vec4 = (nth & 3) == 0;
+  auto stage = [&](float* dst, const float* src, size_t rstride) {   // src: column lb0 of row 0
+    if (vec4) {
+      const int c4 = tid & 3, r0 = tid >> 2;
+      if (lb0 + 4 * c4 < nth) {
+        const float* g = src + 4 * c4 + (size_t)r0 * rstride;
+        float* sd = dst + r0 * kScanCols + 4 * c4;
+        for (int i = r0; i < nr; i += kScanThreads / 4, g += (kScanThreads / 4) * rstride, sd += (kScanThreads / 4) * kScanCols)
+          cp_async16(sd, g);
+      }
+    } else if (valid) {
+      const float* g = src + col + (size_t)seg * rstride;
+      float* sd = dst + seg * kScanCols + col;
+      for (int i = seg; i < nr; i += kScanSegs, g += kScanSegs * rstride, sd += kScanSegs * kScanCols) cp_async4(sd, g);
     }
+  };
+  stage(D, x + (size_t)m * nr * st + (size_t)c * nth + lb0, st);
+  stage(Q, finv + (size_t)m * nr * nth + lb0, nth);
   cp_async_commit();
   for (int i = tid; i < nr; i += kScanThreads) A[i] = sub_r[i];
   cp_async_wait<0>();
   __syncthreads();
+  const int nseg = i1 - i0;
   // ---- forward sweep of this segment from d = 0
   float d = 0.f, q = 1.f;
-  if (work)
-    for (int i = i0; i < i1; ++i) {
-      const int o = i * kScanCols + col;
-      const float iv = Q[o];
-      const float a = -A[i] * iv;
-      d = fmaf(a, d, D[o] * iv);
+  if (work) {
+    float* Dp = D + i0 * kScanCols + col;
+    float* Qp = Q + i0 * kScanCols + col;
+    const float* Ap = A + i0;
+#pragma unroll 4
+    for (int n = 0; n < nseg; ++n) {
+      const float iv = Qp[n * kScanCols];
+      const float a = -Ap[n] * iv;
+      d = fmaf(a, d, Dp[n * kScanCols] * iv);
       q *= a;
-      D[o] = d;
-      Q[o] = q;
+      Dp[n * kScanCols] = d;
+      Qp[n * kScanCols] = q;
     }
+  }
   sE[seg][col] = d;
   sP[seg][col] = q;
   __syncthreads();
@@ -339,29 +360,31 @@ __global__ void __launch_bounds__(kScanThreads) k_thomas_scan(
   __syncthreads();
   if (work) {
     const float cw = sC[seg][col];
-    for (int i = i0; i < i1; ++i) {
-      const int o = i * kScanCols + col;
-      D[o] = fmaf(Q[o], cw, D[o]);
-    }
+    float* Dp = D + i0 * kScanCols + col;
+    const float* Qp = Q + i0 * kScanCols + col;
+#pragma unroll 4
+    for (int n = 0; n < nseg; ++n) Dp[n * kScanCols] = fmaf(Qp[n * kScanCols], cw, Dp[n * kScanCols]);
   }
   __syncthreads();
   // ---- stage c' over the running products, then back-substitute from f = 0
-  if (valid)
-    for (int i = seg; i < nr; i += kScanSegs) cp_async4(&Q[i * kScanCols + col], FC + (size_t)i * nth);
+  stage(Q, fcp + (size_t)m * nr * nth + lb0, nth);
   cp_async_commit();
   cp_async_wait<0>();
   __syncthreads();
   float f = 0.f;
   q = 1.f;
-  if (work)
-    for (int i = i1 - 1; i >= i0; --i) {
-      const int o = i * kScanCols + col;
-      const float g = -Q[o];
-      f = fmaf(g, f, D[o]);
+  if (work) {
+    float* Dp = D + (i1 - 1) * kScanCols + col;
+    float* Qp = Q + (i1 - 1) * kScanCols + col;
+#pragma unroll 4
+    for (int n = 0; n < nseg; ++n) {
+      const float g = -Qp[-n * kScanCols];
+      f = fmaf(g, f, Dp[-n * kScanCols]);
       q *= g;
-      D[o] = f;
-      Q[o] = q;
+      Dp[-n * kScanCols] = f;
+      Qp[-n * kScanCols] = q;
     }
+  }
   sE[seg][col] = f;   // value at the segment's first row from a zero start above it
   sP[seg][col] = q;
   __syncthreads();
@@ -375,11 +398,12 @@ __global__ void __launch_bounds__(kScanThreads) k_thomas_scan(
   __syncthreads();
   if (work) {
     const float cw = sC[seg][col];
-    const size_t prow = (size_t)m * nr * 2 + c;
-    for (int i = i0; i < i1; ++i) {
-      const int o = i * kScanCols + col;
-      pl[(prow + 2 * i) * kstride + l] = fmaf(Q[o], cw, D[o]);
-    }
+    const float* Dp = D + i0 * kScanCols + col;
+    const float* Qp = Q + i0 * kScanCols + col;
+    float* out = pl + ((size_t)m * nr * 2 + c + 2 * (size_t)i0) * kstride + l;
+    const size_t ostep = 2 * (size_t)kstride;
+#pragma unroll 4
+    for (int n = 0; n < nseg; ++n) out[n * ostep] = fmaf(Qp[n * kScanCols], cw, Dp[n * kScanCols]);
   }
 }
 
