@@ -487,7 +487,7 @@ __global__ void __launch_bounds__(kResThreads) k_residual_ff(const double* __res
                                                              const double* __restrict__ outer_shell,
                                                              float* __restrict__ r,
                                                              const RadialRowFF* __restrict__ rad,
-                                                             const ThetaRowFF* __restrict__ th, int nr, int nth,
+                                                             const ThetaRowFF* __restrict__ ang, int nr, int nth,
                                                              int nphi, int chunk0, int dirichlet, ff dir_coef,
                                                              ff four_pi_g) {
   __shared__ float line[2][2][kResThreads + 2];   // [row parity][hi, lo][k - k0 + 1]
@@ -501,15 +501,20 @@ __global__ void __launch_bounds__(kResThreads) k_residual_ff(const double* __res
   const int kl = k0 == 0 ? nphi - 1 : k0 - 1;       // periodic halo columns
   const int kr = k0 + nk == nphi ? 0 : k0 + nk;
   const size_t shell = (size_t)nth * nphi;
-  const ThetaRowFF tr = th[j];
   const bool has_jm = j > 0, has_jp = j < nth - 1;
-  const float* PH = ph + (size_t)j * nphi;
-  const float* PL = pl + (size_t)j * nphi;
-  size_t oc = (size_t)i0 * shell;
-  float ch = PH[oc + k], cl = PL[oc + k];
+  // pointers at (i, j, 0) and (i, j, k), stepped one shell per row
+  const size_t c0 = (size_t)i0 * shell + (size_t)j * nphi;
+  const float* hrow = ph + c0;
+  const float* lrow = pl + c0;
+  const float* hp = hrow + k;
+  const float* lp = lrow + k;
+  const double* rp = rho + c0 + k;
+  float* op = r + c0 + k;
+  const ThetaRowFF* angp = ang + (size_t)i0 * nth + j;
+  float ch = hp[0], cl = lp[0];
   float mh = 0.f, ml = 0.f;   // Phi(i-1) - Phi(i)
-  if (i0 > 0) ffd_diff(PH[oc - shell + k], PL[oc - shell + k], ch, cl, mh, ml);
-  for (int i = i0; i < i1; ++i, oc += shell) {
+  if (i0 > 0) ffd_diff(hp[-(ptrdiff_t)shell], lp[-(ptrdiff_t)shell], ch, cl, mh, ml);
+  for (int i = i0; i < i1; ++i) {
     float* bh = line[i & 1][0];
     float* bl = line[i & 1][1];
     if (act) {
@@ -517,82 +522,83 @@ __global__ void __launch_bounds__(kResThreads) k_residual_ff(const double* __res
       bl[t + 1] = cl;
     }
     if (t == 0) {
-      bh[0] = PH[oc + kl];
-      bl[0] = PL[oc + kl];
-      bh[nk + 1] = PH[oc + kr];
-      bl[nk + 1] = PL[oc + kr];
+      bh[0] = hrow[kl];
+      bl[0] = lrow[kl];
+      bh[nk + 1] = hrow[kr];
+      bl[nk + 1] = lrow[kr];
     }
     const bool has_ip = i < nr - 1;
     float nh = 0.f, nl = 0.f, jmh = 0.f, jml = 0.f, jph = 0.f, jpl = 0.f;
     if (has_ip) {
-      nh = PH[oc + shell + k];
-      nl = PL[oc + shell + k];
+      nh = hp[shell];
+      nl = lp[shell];
     }
     if (has_jm) {
-      jmh = PH[oc - nphi + k];
-      jml = PL[oc - nphi + k];
+      jmh = hp[-nphi];
+      jml = lp[-nphi];
     }
     if (has_jp) {
-      jph = PH[oc + nphi + k];
-      jpl = PL[oc + nphi + k];
+      jph = hp[nphi];
+      jpl = lp[nphi];
     }
-    const double rv = rho[oc + (size_t)j * nphi + k];
+    const double rv = *rp;
     const RadialRowFF rr = rad[i];
+    const ThetaRowFF ar = *angp;   // R_i x (t_j+1/2, t_j-1/2, S_j lambda-free phi coefficient)
     __syncthreads();
     float dh, dl, p, e;
-    // radial fluxes
-    float rh = 0.f, rl = 0.f;
+    // L Phi as one unnormalised float-float sum of coefficient x difference terms
+    float sh = 0.f, sl = 0.f;
     if (i > 0) {
       ffd_mul(rr.sub, mh, ml, p, e);
-      rh = p;
-      rl = e;
+      sh = p;
+      sl = e;
     }
     if (has_ip) {
       ffd_diff(nh, nl, ch, cl, dh, dl);
       ffd_mul(rr.sup, dh, dl, p, e);
-      ffd_acc(rh, rl, p, e);
+      ffd_acc(sh, sl, p, e);
       mh = -dh;
       ml = -dl;
     }
-    // angular fluxes, scaled by R_i
-    float ah = 0.f, al = 0.f;
     if (has_jm) {
       ffd_diff(jmh, jml, ch, cl, dh, dl);
-      ffd_mul(tr.tm, dh, dl, p, e);
-      ah = p;
-      al = e;
+      ffd_mul(ar.tm, dh, dl, p, e);
+      ffd_acc(sh, sl, p, e);
     }
     if (has_jp) {
       ffd_diff(jph, jpl, ch, cl, dh, dl);
-      ffd_mul(tr.tp, dh, dl, p, e);
-      ffd_acc(ah, al, p, e);
+      ffd_mul(ar.tp, dh, dl, p, e);
+      ffd_acc(sh, sl, p, e);
     }
     float qh, ql;
     ffd_diff(bh[t + 2], bl[t + 2], ch, cl, qh, ql);
     ffd_diff(bh[t], bl[t], ch, cl, dh, dl);
     ffd_acc(qh, ql, dh, dl);
-    ffd_mul(tr.sphi, qh, ql, p, e);
-    ffd_acc(ah, al, p, e);
-    ff a;
-    fast_two_sum(ah, al, a.hi, a.lo);
-    ffd_mul(rr.R, a.hi, a.lo, p, e);
-    ffd_acc(rh, rl, p, e);
+    ffd_mul(ar.sphi, qh, ql, p, e);
+    ffd_acc(sh, sl, p, e);
     if (!has_ip) {
       if (dirichlet) {
         ffd_mul(dir_coef, ch, cl, p, e);
-        ffd_acc(rh, rl, p, e);
+        ffd_acc(sh, sl, p, e);
       } else {
         const ff o = d2ff(outer_shell[(size_t)j * nphi + k]);
-        ffd_acc(rh, rl, o.hi, o.lo);
+        ffd_acc(sh, sl, o.hi, o.lo);
       }
     }
     const ff sv = ff_mul(four_pi_g, d2ff(rv));
     float th_, tl;
-    two_sum(sv.hi, -rh, th_, tl);
-    tl += sv.lo - rl;
-    if (act) r[oc + (size_t)j * nphi + k] = th_ + tl;
+    two_sum(sv.hi, -sh, th_, tl);
+    tl += sv.lo - sl;
+    if (act) *op = th_ + tl;
     ch = nh;
     cl = nl;
+    hrow += shell;
+    lrow += shell;
+    hp += shell;
+    lp += shell;
+    rp += shell;
+    op += shell;
+    angp += nth;
   }
 }
 
@@ -601,6 +607,16 @@ __global__ void __launch_bounds__(256) k_finish(const float* __restrict__ ph, co
                                                 double* __restrict__ phi, size_t n) {
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x)
     phi[idx] = ff2d(ff{ph[idx], pl[idx]});
+}
+
+// The same for 16-byte aligned arrays, four values per thread and step.
+__global__ void __launch_bounds__(256) k_finish4(const float4* __restrict__ ph, const float4* __restrict__ pl,
+                                                 double2* __restrict__ phi, size_t n4) {
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n4; q += (size_t)gridDim.x * blockDim.x) {
+    const float4 h = __ldg(ph + q), l = __ldg(pl + q);
+    phi[2 * q] = make_double2(ff2d(ff{h.x, l.x}), ff2d(ff{h.y, l.y}));
+    phi[2 * q + 1] = make_double2(ff2d(ff{h.z, l.z}), ff2d(ff{h.w, l.w}));
+  }
 }
 
 }  // namespace
@@ -676,15 +692,19 @@ int mixed_create_tables(Plan& p, cudaStream_t s) {
   std::vector<ThetaRow> thr(p.nth);
   if (cudaMemcpy(thr.data(), p.d_theta, sizeof(ThetaRow) * p.nth, cudaMemcpyDeviceToHost) != cudaSuccess)
     return SP_ERR_CUDA;
-  std::vector<ThetaRowFF> thff(p.nth);
-  for (int j = 0; j < p.nth; ++j) thff[j] = {split(thr[j].tp), split(thr[j].tm), split(thr[j].sphi), ff{0.f, 0.f}};
+  // R_i x angular coefficients of every (i, j), split from their float64 products
+  std::vector<ThetaRowFF> thff((size_t)p.nr * p.nth);
+  for (int i = 0; i < p.nr; ++i)
+    for (int j = 0; j < p.nth; ++j)
+      thff[(size_t)i * p.nth + j] = {split(rad[i].R * thr[j].tp), split(rad[i].R * thr[j].tm),
+                                     split(rad[i].R * thr[j].sphi), ff{0.f, 0.f}};
   x->four_pi_g = split(4.0 * 3.14159265358979323846264338327950288 * p.G);
   x->dir_coef = split(-p.outer_coef / (p.r_out - p.r_last));
   if (cudaMalloc(&x->radff, sizeof(RadialRowFF) * p.nr) != cudaSuccess ||
-      cudaMalloc(&x->thff, sizeof(ThetaRowFF) * p.nth) != cudaSuccess)
+      cudaMalloc(&x->thff, sizeof(ThetaRowFF) * thff.size()) != cudaSuccess)
     return SP_ERR_OOM;
   if (cudaMemcpy(x->radff, rff.data(), sizeof(RadialRowFF) * p.nr, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(x->thff, thff.data(), sizeof(ThetaRowFF) * p.nth, cudaMemcpyHostToDevice) != cudaSuccess)
+      cudaMemcpy(x->thff, thff.data(), sizeof(ThetaRowFF) * thff.size(), cudaMemcpyHostToDevice) != cudaSuccess)
     return SP_ERR_CUDA;
   std::vector<int> low;
   for (size_t t = 0; t < lam.size(); ++t)
@@ -826,8 +846,18 @@ cudaError_t residual_ff(const Plan& p, const double* rho, cudaStream_t s) {
 cudaError_t finish_mixed(const Plan& p, double* phi, cudaStream_t s) {
   const MixedTables& x = *p.mixed;
   const size_t n = (size_t)p.nr * p.nth * p.nphi;
+  const bool aligned = ((reinterpret_cast<uintptr_t>(phi) | reinterpret_cast<uintptr_t>(x.phi_hi) |
+                         reinterpret_cast<uintptr_t>(x.phi_lo)) & 15u) == 0 && (n & 3) == 0;
+  if (aligned) {
+    size_t blocks = (n / 4 + 255) / 256;
+    if (blocks > (size_t)p.num_sms * 8) blocks = (size_t)p.num_sms * 8;
+    k_finish4<<<(unsigned)blocks, 256, 0, s>>>(reinterpret_cast<const float4*>(x.phi_hi),
+                                               reinterpret_cast<const float4*>(x.phi_lo),
+                                               reinterpret_cast<double2*>(phi), n / 4);
+    return cudaGetLastError();
+  }
   size_t blocks = (n + 255) / 256;
-  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks > (size_t)p.num_sms * 16) blocks = (size_t)p.num_sms * 16;
   k_finish<<<(unsigned)blocks, 256, 0, s>>>(x.phi_hi, x.phi_lo, phi, n);
   return cudaGetLastError();
 }

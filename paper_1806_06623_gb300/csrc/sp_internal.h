@@ -72,7 +72,7 @@ struct MixedTables {
   __nv_bfloat16* Hm[3] = {};       // planes of H_m, [mh][j][kstride]
   RadialRowF* radf = nullptr;      // [nr]
   RadialRowFF* radff = nullptr;    // [nr]
-  ThetaRowFF* thff = nullptr;      // [nth]
+  ThetaRowFF* thff = nullptr;      // [nr][nth] R_i x (t_j+1/2, t_j-1/2, phi coefficient) as float pairs
   ff four_pi_g{}, dir_coef{};      // s = 4 pi G rho; Dirichlet outer diagonal (3 r^2/dV3)/(r_N - r_out)
   int* low_idx = nullptr;          // [nlow] flat (m*Ntheta + l) of the float64 modes
   double2* low_fac = nullptr;      // [nlow][nr] (c'_i, 1/pivot_i) of the float64 modes

@@ -759,7 +759,8 @@ size_t plan_table_bytes(const Plan& p) {
   if (p.mixed) {
     const MixedTables& x = *p.mixed;
     b += 2 * (size_t)x.np * tab * x.kstride * 2 + 2 * (size_t)p.mh * p.nr * p.nth * sizeof(float) +
-         (size_t)p.nr * (sizeof(RadialRowF) + sizeof(RadialRowFF) + sizeof(float)) + (size_t)x.nlow * p.nr * 16;
+         (size_t)p.nr * (sizeof(RadialRowF) + sizeof(RadialRowFF) + sizeof(float)) + (size_t)x.nlow * p.nr * 16 +
+         (size_t)p.nr * p.nth * sizeof(ThetaRowFF);
   }
   return b;
 }
