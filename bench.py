@@ -210,16 +210,20 @@ def run_ours(args, rank, world, local):
         for _ in range(args.warmup):
             plan.solve(rho, phi)
         barrier()
-        plan.set_timing(True)
         n0 = plan.launch_count()
         clocks = ClockSampler(local)
         clocks.start() if name == precision else None
         barrier()
-        tot_ms, infos = timed_steps(plan, args.steps, collect=True)
+        tot_ms, infos = timed_steps(plan, args.steps, collect=False)
         barrier()
         ck = clocks.stop() if name == precision else None
         launches = plan.launch_count() - n0
-        timing = plan.timing()
+        # per-kernel breakdown in a separate pass: the per-launch CUDA events stay out of
+        # the timed steps above
+        nb = min(args.steps, 5)
+        plan.set_timing(True)   # also clears the accumulators
+        timed_steps(plan, nb, collect=True)
+        timing = {k: (v[0] * args.steps / nb, v[1] * args.steps // nb) for k, v in plan.timing().items()}
         plan.set_timing(False)
         if world > 1:
             import torch.distributed as dist
@@ -272,7 +276,7 @@ def run_ours(args, rank, world, local):
     for name, rr in results.items():
         line[f"{name}_zones_per_s"] = zones * args.steps * world / (rr["ms"] / 1e3)
         line[f"{name}_ms_per_step"] = rr["ms"] / args.steps
-    line["roofline"] = roofline(r["timing"], p, precision)
+    line["roofline"] = roofline(r["timing"], p, precision, args.steps, r["infos"][-1].get("iterations", 2))
     if not args.no_batched:
         line["batched"] = run_batched(S, W, torch, dev, check=not args.no_oracle_check)
     if not args.no_served:
@@ -380,11 +384,50 @@ def run_served(S, W, torch, n_requests, rates=(200.0, 2000.0, 20000.0)):
     return out
 
 
-def roofline(timing, p, precision):
-    """Dominant kernel's achieved rate from its live CUDA-event durations."""
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch from an ncu capture of the
+# named command (full workload), per kernel group; kept only while the kernel is unchanged
+NCU_TRAFFIC = {
+    "mixed": {
+        "residual": {"bytes": (288.57 + 58.18) * 1e6, "kernel": "k_residual_ff (interior rows)",
+                     "profile": "profiles/mixed_x6_550x128x256_kernels.md"},
+    },
+}
+
+
+def algorithmic_bytes_per_step(p, precision, iters=2):
+    """Bytes each kernel group must move per solve (inputs read once, outputs written once).
+
+    Z = zones, S = spectral values 2 mh Nr Ntheta.  Mixed path with `iters` low-precision
+    solves: forward FFTs read rho (8 B) then r (4 B) and write the float32 panel (4 B);
+    projections read and write 4 B per spectral value plus the NP bf16 table planes;
+    radial solves read the spectrum and both float32 factor tables and write the panel;
+    inverse FFTs read the spectrum and write (then read and write) the float-float
+    iterate; the residual reads rho and the iterate and writes r; the update reads the
+    iterate and writes float64 Phi."""
     nr, nth, nphi = p.shape
     mh = nphi // 2 + 1
-    zones = nr * nth * nphi
+    Z = float(nr * nth * nphi)
+    S = float(2 * mh * nr * nth)
+    if precision == "fp64":
+        return {"fft_forward": 8 * Z + 8 * S, "project_forward": 16 * S + 8 * mh * nth * nth,
+                "radial_solve": 16 * S + 8 * S / 2, "project_inverse": 16 * S + 8 * mh * nth * nth,
+                "fft_inverse": 8 * S + 8 * Z}
+    npl = 3 if precision == "mixed" else 2
+    T = 2.0 * npl * mh * nth * nth
+    c = iters - 1   # corrections
+    return {"fft_forward": (8 * Z + 4 * S) + c * (4 * Z + 4 * S),
+            "project_forward": iters * (8 * S + T),
+            "radial_solve": iters * (4 * S + 4 * S + 4 * S),
+            "project_inverse": iters * (8 * S + T),
+            "fft_inverse": (4 * S + 8 * Z) + c * (4 * S + 16 * Z),
+            "residual": c * 20 * Z,
+            "update": 16 * Z}
+
+
+def roofline(timing, p, precision, steps, iters=2):
+    """Dominant kernel group's achieved rate: algorithmic bytes per launch over its
+    average live CUDA-event duration."""
+    nr, nth, nphi = p.shape
     if not timing:
         return None
     name, (ms, cnt) = max(timing.items(), key=lambda kv: kv[1][0])
@@ -401,18 +444,17 @@ def roofline(timing, p, precision):
                 "frac": ach / 1.25, "traffic": None,
                 "peak_source": "nominal GB300 float64 rate (no measured float64 peak on this pool)",
                 "algorithmic": "2 Nr Ntheta^2 Nphi flops per projection"}
-    # HBM-bound kernels: algorithmic bytes per launch
-    bytes_per = {
-        "fft_forward": 8.0 * zones + 8.0 * (2 * mh * nr * nth),
-        "fft_inverse": 8.0 * (2 * mh * nr * nth) + 8.0 * zones,
-        "radial_solve": 8.0 * 2 * (2 * mh * nr * nth),
-        "stencil": 16.0 * zones,
-    }
-    b = bytes_per.get(name, 16.0 * zones)
+    per_step = algorithmic_bytes_per_step(p, precision, iters).get(name)
+    if per_step is None:
+        return None
+    b = per_step * steps / cnt          # per launch
     ach = b / per_launch_s / 1e9
     pk = float(peaks.get("hbm_gbs", 6800.0))
+    tr = NCU_TRAFFIC.get(precision, {}).get(name)
     return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s", "frac": ach / pk,
-            "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback"}
+            "traffic": tr["bytes"] if tr else None, "traffic_source": tr["profile"] if tr else None,
+            "algorithmic_bytes_per_launch": b,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s"}
 
 
 def check_vs_oracle(p, phis):

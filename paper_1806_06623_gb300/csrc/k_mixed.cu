@@ -488,11 +488,11 @@ __global__ void __launch_bounds__(kResThreads) k_residual_ff(const double* __res
                                                              float* __restrict__ r,
                                                              const RadialRowFF* __restrict__ rad,
                                                              const ThetaRowFF* __restrict__ ang, int nr, int nth,
-                                                             int nphi, int chunk0, int dirichlet, ff dir_coef,
-                                                             ff four_pi_g) {
+                                                             int nphi, int row_begin, int row_end, int dirichlet,
+                                                             ff dir_coef, ff four_pi_g) {
   __shared__ float line[2][2][kResThreads + 2];   // [row parity][hi, lo][k - k0 + 1]
   const int j = blockIdx.x;
-  const int i0 = (chunk0 + (int)blockIdx.y) * kResRows, i1 = min(nr, i0 + kResRows);
+  const int i0 = row_begin + (int)blockIdx.y * kResRows, i1 = min(row_end, i0 + kResRows);
   const int t = threadIdx.x;
   const int k0 = blockIdx.z * blockDim.x;
   const int nk = min((int)blockDim.x, nphi - k0);   // columns of this CTA
@@ -816,18 +816,17 @@ cudaError_t residual_ff(const Plan& p, const double* rho, cudaStream_t s) {
   const MixedTables& x = *p.mixed;
   const size_t sh = (size_t)p.nth * p.nphi;
   const int tpb = p.nphi >= kResThreads ? kResThreads : ((p.nphi + 31) / 32) * 32;
-  const int nchunk = (p.nr + kResRows - 1) / kResRows;
-  auto rows = [&](int c0, int nc, cudaStream_t st) {
-    const dim3 grid(p.nth, nc, (p.nphi + tpb - 1) / tpb);
+  auto rows = [&](int r0, int r1, cudaStream_t st) {   // rows [r0, r1)
+    const dim3 grid(p.nth, (r1 - r0 + kResRows - 1) / kResRows, (p.nphi + tpb - 1) / tpb);
     k_residual_ff<<<grid, tpb, 0, st>>>(rho, x.phi_hi, x.phi_lo, x.outer_shell, x.r32, x.radff, x.thff, p.nr, p.nth,
-                                        p.nphi, c0, p.outer_bc == SP_OUTER_DIRICHLET ? 1 : 0, x.dir_coef,
+                                        p.nphi, r0, r1, p.outer_bc == SP_OUTER_DIRICHLET ? 1 : 0, x.dir_coef,
                                         x.four_pi_g);
     return cudaGetLastError();
   };
-  if (p.outer_bc != SP_OUTER_MULTIPOLE) return rows(0, nchunk, s);
+  if (p.outer_bc != SP_OUTER_MULTIPOLE) return rows(0, p.nr, s);
   // The multipole term of the last shell (small: Ntheta x Nphi zones, float64 FFTs and
   // per-m operator) runs on the high-priority side stream while the interior rows,
-  // which do not need it, run here; the chunk holding the last shell follows the join.
+  // which do not need it, run here; the last shell alone follows the join.
   cudaError_t e;
   if ((e = cudaEventRecord(p.ev_fork, s)) != cudaSuccess || (e = cudaStreamWaitEvent(p.side, p.ev_fork, 0)) != cudaSuccess)
     return e;
@@ -838,9 +837,9 @@ cudaError_t residual_ff(const Plan& p, const double* rho, cudaStream_t s) {
   if ((e = shell_kappa_f64(p, p.shell, p.shell2, p.side)) != cudaSuccess) return e;
   if ((e = fft_inverse_f64(p, p.shell2, 1, x.outer_shell, false, p.side)) != cudaSuccess) return e;
   if ((e = cudaEventRecord(p.ev_join, p.side)) != cudaSuccess) return e;
-  if (nchunk > 1 && (e = rows(0, nchunk - 1, s)) != cudaSuccess) return e;
+  if (p.nr > 1 && (e = rows(0, p.nr - 1, s)) != cudaSuccess) return e;
   if ((e = cudaStreamWaitEvent(s, p.ev_join, 0)) != cudaSuccess) return e;
-  return rows(nchunk - 1, 1, s);
+  return rows(p.nr - 1, p.nr, s);
 }
 
 cudaError_t finish_mixed(const Plan& p, double* phi, cudaStream_t s) {
