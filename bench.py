@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-instance ragged batch")
     ap.add_argument("--no-served", action="store_true", help="skip the served Poisson-arrival stream")
     ap.add_argument("--served-requests", type=int, default=400)
+    ap.add_argument("--no-small", action="store_true", help="skip the 32x16x32 and 128x64x128 configurations")
     ap.add_argument("--headline-only", action="store_true",
                     help="time the headline precision only (no float64 / 3-product comparison plans)")
     return ap.parse_args()
@@ -277,6 +278,8 @@ def run_ours(args, rank, world, local):
         line[f"{name}_zones_per_s"] = zones * args.steps * world / (rr["ms"] / 1e3)
         line[f"{name}_ms_per_step"] = rr["ms"] / args.steps
     line["roofline"] = roofline(r["timing"], p, precision, args.steps, r["infos"][-1].get("iterations", 2))
+    if not args.no_small:
+        line["small_configs"] = run_small(S, W, torch, dev, check=not args.no_oracle_check)
     if not args.no_batched:
         line["batched"] = run_batched(S, W, torch, dev, check=not args.no_oracle_check)
     if not args.no_served:
@@ -289,6 +292,43 @@ def run_ours(args, rank, world, local):
                                 "sample": f"{n} full float64 oracle solves of the workload in {el:.1f} s "
                                           "(NumPy FFT and Thomas single-threaded, BLAS matmul multi-threaded)"}
     print(json.dumps(line), flush=True)
+
+
+def run_small(S, W, torch, dev, check=True, steps=20, warmup=3):
+    """The two smaller configurations (32x16x32 sphere, 128x64x128 stellar noise): one
+    solve per step, float64 and 6-product mixed; these fit in L2, so the numbers are
+    L2-resident rates (no flush between steps)."""
+    out = {}
+    for make in (W.sphere_blob, W.stellar_noise):
+        p = make()
+        rho = torch.from_numpy(p.rho).to(dev)
+        phi = torch.empty_like(rho)
+        stream = torch.cuda.current_stream(dev)
+        key = "x".join(str(v) for v in p.shape)
+        res = {"zones": p.zones, "l2": "resident (inputs smaller than L2)"}
+        ref = None
+        if check:
+            from oracle import sph_poisson as O
+            ref = O.solve_separated(O.Geometry(p.r_if, p.th_if, p.nphi), p.rho)
+        for name, prec in (("fp64", S.SP_FP64), ("mixed", S.SP_MIXED_BF16X6)):
+            plan = S.Plan(p.r_if, p.th_if, p.nphi, precision=prec, tol=1e-10)
+            for _ in range(warmup):
+                plan.solve(rho, phi)
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                _, info = plan.solve(rho, phi)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            r = {"ms_per_step": ms, "zones_per_s": p.zones / (ms / 1e3), "iterations": info.iterations}
+            if ref is not None:
+                r["max_rel_err_vs_oracle"] = float(np.max(np.abs(phi.cpu().numpy() - ref)) / np.max(np.abs(ref)))
+            res[name] = r
+            plan.close()
+        out[key] = res
+    return out
 
 
 def run_batched(S, W, torch, dev, check=True, n=64, reps=3):
