@@ -442,8 +442,9 @@ def algorithmic_bytes_per_step(p, precision, iters=2):
     projections read and write 4 B per spectral value plus the NP bf16 table planes;
     radial solves read the spectrum and both float32 factor tables and write the panel;
     inverse FFTs read the spectrum and write (then read and write) the float-float
-    iterate; the residual reads rho and the iterate and writes r; the update reads the
-    iterate and writes float64 Phi."""
+    iterate, a correction's also writing float64 Phi; the residual reads rho and the
+    iterate and writes r; without a correction a separate update reads the iterate and
+    writes float64 Phi."""
     nr, nth, nphi = p.shape
     mh = nphi // 2 + 1
     Z = float(nr * nth * nphi)
@@ -459,9 +460,9 @@ def algorithmic_bytes_per_step(p, precision, iters=2):
             "project_forward": iters * (8 * S + T),
             "radial_solve": iters * (4 * S + 4 * S + 4 * S),
             "project_inverse": iters * (8 * S + T),
-            "fft_inverse": (4 * S + 8 * Z) + c * (4 * S + 16 * Z),
+            "fft_inverse": (4 * S + 8 * Z) + c * (4 * S + 24 * Z),   # corrections also write float64 Phi
             "residual": c * 20 * Z,
-            "update": 16 * Z}
+            "update": 16 * Z if c == 0 else 0.0}
 
 
 def roofline(timing, p, precision, steps, iters=2):

@@ -325,12 +325,15 @@ enum InvOut { kInvWrite = 0, kInvAccumulate = 1, kInvPairUpdate = 2 };
 //  MODE kInvWrite / kInvAccumulate: out = / += value
 //  MODE kInvPairUpdate: float-float iterate (out, phi_lo) = (e, 0) if first else
 //    (out, phi_lo) + e, with max|e| and max|hi| reduced into red[0], red[1]
-//    (non-negative float bit patterns, so integer max orders them).
+//    (non-negative float bit patterns, so integer max orders them); with phi64 given,
+//    the updated iterate is also written as float64 (the solve's output when this
+//    correction turns out to be the last).
 template <typename T, typename Tout, int MODE>
 __global__ void __launch_bounds__(256, 3) k_fft_inv(const T* __restrict__ spec, int nlines, int nth, int nrs,
                                                  FftSchedule sch, const T* __restrict__ twid, int lpc,
                                                  Tout* __restrict__ out, float* __restrict__ phi_lo, int first,
-                                                 unsigned int* __restrict__ red, int ahead) {
+                                                 unsigned int* __restrict__ red, int ahead,
+                                                 double* __restrict__ phi64) {
   using CT = typename C2<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ float s_me[kWarps], s_mp[kWarps];
@@ -440,6 +443,7 @@ __global__ void __launch_bounds__(256, 3) k_fft_inv(const T* __restrict__ spec, 
             const ff nv = first ? ff{e, 0.f} : ff_add_f(ff{oh[h][u], ol[h][u]}, e);
             out[o] = (Tout)nv.hi;
             phi_lo[o] = nv.lo;
+            if (phi64) phi64[o] = ff2d(nv);
             me = fmaxf(me, fabsf(e));
             mp = fmaxf(mp, fabsf(nv.hi));
           }
@@ -522,11 +526,11 @@ cudaError_t fft_inverse_f64(const Plan& p, const double* spec, int nrs, double* 
   if (accumulate) {
     auto kern = k_fft_inv<double, double, kInvAccumulate>;
     if ((e = prep(kern, smem)) != cudaSuccess) return e;
-    kern<<<grid, 32 * kWarps, smem, s>>>(spec, nlines, p.nth, nrs, p.sched, p.d_twid, lpc, out, nullptr, 0, nullptr, 0);
+    kern<<<grid, 32 * kWarps, smem, s>>>(spec, nlines, p.nth, nrs, p.sched, p.d_twid, lpc, out, nullptr, 0, nullptr, 0, nullptr);
   } else {
     auto kern = k_fft_inv<double, double, kInvWrite>;
     if ((e = prep(kern, smem)) != cudaSuccess) return e;
-    kern<<<grid, 32 * kWarps, smem, s>>>(spec, nlines, p.nth, nrs, p.sched, p.d_twid, lpc, out, nullptr, 0, nullptr, 0);
+    kern<<<grid, 32 * kWarps, smem, s>>>(spec, nlines, p.nth, nrs, p.sched, p.d_twid, lpc, out, nullptr, 0, nullptr, 0, nullptr);
   }
   return cudaGetLastError();
 }
@@ -553,7 +557,7 @@ cudaError_t fft_forward_panel(const Plan& p, const void* in, bool in_double, flo
 }
 
 cudaError_t fft_inverse_update(const Plan& p, const float* spec, float* phi_hi, float* phi_lo, bool first,
-                               unsigned int* red, cudaStream_t s) {
+                               unsigned int* red, double* phi64, cudaStream_t s) {
   const int nlines = p.nr * p.nth;
   const int lpc = lines_per_cta<float>(p.nphi, nlines);
   const size_t smem = fft_smem<float>(p.nphi, lpc);
@@ -562,7 +566,7 @@ cudaError_t fft_inverse_update(const Plan& p, const float* spec, float* phi_hi, 
   if (e != cudaSuccess) return e;
   // (prefetching the iterate a wave ahead measured slower here: ahead = 0)
   kern<<<(nlines + lpc - 1) / lpc, 32 * kWarps, smem, s>>>(spec, nlines, p.nth, p.nr, p.sched, p.d_twid32, lpc, phi_hi,
-                                                           phi_lo, first ? 1 : 0, red, 0);
+                                                           phi_lo, first ? 1 : 0, red, 0, first ? nullptr : phi64);
   return cudaGetLastError();
 }
 

@@ -148,6 +148,7 @@ struct Plan {
 
   MixedTables* mixed = nullptr;
   unsigned int* h_red = nullptr;  // pinned host copy of the mixed-path reductions
+  const double* phi64_written = nullptr;   // output already holding the current iterate in float64
   // side stream (high priority) and fork/join events: the multipole shell term of the
   // mixed residual runs beside the residual's interior rows
   cudaStream_t side = nullptr;
@@ -226,7 +227,7 @@ struct Planes {
 cudaError_t fft_forward_panel(const Plan& p, const void* in, bool in_double, float scale, int kstride, float* out,
                               cudaStream_t s);
 cudaError_t fft_inverse_update(const Plan& p, const float* spec, float* phi_hi, float* phi_lo, bool first,
-                               unsigned int* red, cudaStream_t s);
+                               unsigned int* red, double* phi64, cudaStream_t s);
 cudaError_t finish_mixed(const Plan& p, double* phi, cudaStream_t s);   // float-float iterate -> float64 Phi
 cudaError_t tc_project(const Plan& p, bool inverse, cudaStream_t s);   // pan -> d32
 cudaError_t thomas_mixed(const Plan& p, cudaStream_t s);   // d32 -> pan (f); float32 + float64 low modes
@@ -245,7 +246,7 @@ struct MixedRun {
 };
 constexpr int kRedErrWord = 4;   // h_red: two slots of (max|e|, max|Phi|), then the status word
 int mixed_start(Plan* p, const double* rho, cudaStream_t s);
-int mixed_correct(Plan* p, const double* rho, cudaStream_t s);
+int mixed_correct(Plan* p, const double* rho, double* phi, cudaStream_t s);
 int mixed_issue_read(Plan* p, cudaStream_t s, MixedRun& R);
 void mixed_decide(Plan* p, MixedRun& R);   // after the stream has reached the pending copies
 int mixed_finish(Plan* p, double* phi, cudaStream_t s, const MixedRun& R, sp_solve_info* info);

@@ -167,9 +167,8 @@ int lp_solve(Plan* p, const void* in, bool in_double, float scale, double* phi, 
   if ((st = launch_status(sp::timed_launch(P, sp::kKThomas, s, [&] { return sp::thomas_mixed(P, s); })))) return st;
   if ((st = launch_status(sp::timed_launch(P, sp::kKGemmInv, s, [&] { return sp::tc_project(P, true, s); }))))
     return st;
-  (void)phi;
   return launch_status(sp::timed_launch(P, sp::kKFftInv, s, [&] {
-    return sp::fft_inverse_update(P, x.d32, x.phi_hi, x.phi_lo, first, x.red, s); }));
+    return sp::fft_inverse_update(P, x.d32, x.phi_hi, x.phi_lo, first, x.red, phi, s); }));
 }
 
 }  // namespace
@@ -178,18 +177,22 @@ namespace sp {
 
 // First low-precision solve of L Phi = 4 pi G rho (asynchronous).
 int mixed_start(Plan* p, const double* rho, cudaStream_t s) {
+  p->phi64_written = nullptr;
   SP_CUDA(cudaMemsetAsync(p->mixed->red, 0, 2 * sizeof(unsigned int), s));
   return lp_solve(p, rho, true, (float)(4.0 * kPi * p->G / p->nphi), nullptr, true, s);
 }
 
-// One correction: float-float residual, then the low-precision solve of L e = r (asynchronous).
-int mixed_correct(Plan* p, const double* rho, cudaStream_t s) {
+// One correction: float-float residual, then the low-precision solve of L e = r
+// (asynchronous); its inverse FFT also writes the updated iterate to phi in float64.
+int mixed_correct(Plan* p, const double* rho, double* phi, cudaStream_t s) {
   Plan& P = *p;
   int st;
   if ((st = launch_status(timed_launch(P, kKResidual, s, [&] { return residual_ff(P, rho, s); })))) return st;
   if (P.outer_bc == SP_OUTER_MULTIPOLE) P.launches += 5;   // shell: finish, FFT, apply, inverse FFT; split residual
   SP_CUDA(cudaMemsetAsync(P.mixed->red, 0, 2 * sizeof(unsigned int), s));
-  return lp_solve(p, P.mixed->r32, false, (float)(1.0 / P.nphi), nullptr, false, s);
+  st = lp_solve(p, P.mixed->r32, false, (float)(1.0 / P.nphi), phi, false, s);
+  if (st == SP_OK) P.phi64_written = phi;
+  return st;
 }
 
 // Queue the copy of the reductions of the last low-precision solve to the next of two
@@ -249,7 +252,10 @@ void mixed_decide(Plan* p, MixedRun& R) {
 int mixed_finish_issue(Plan* p, double* phi, cudaStream_t s) {
   Plan& P = *p;
   int st;
-  if ((st = launch_status(timed_launch(P, kKUpdate, s, [&] { return finish_mixed(P, phi, s); })))) return st;
+  // the last correction's inverse FFT already wrote phi; otherwise convert the iterate
+  if (P.phi64_written != phi &&
+      (st = launch_status(timed_launch(P, kKUpdate, s, [&] { return finish_mixed(P, phi, s); }))))
+    return st;
   SP_CUDA(cudaMemcpyAsync(P.h_red + kRedErrWord, P.d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
   return SP_OK;
 }
@@ -308,14 +314,14 @@ int solve_mixed(Plan* p, const double* rho, double* phi, cudaStream_t s, sp_solv
   if ((st = sp::mixed_issue_read(p, s, R))) return st;
   int k = 1;
   if (p->max_iter >= 1) {
-    if ((st = sp::mixed_correct(p, rho, s))) return st;
+    if ((st = sp::mixed_correct(p, rho, phi, s))) return st;
     if ((st = sp::mixed_issue_read(p, s, R))) return st;
     k = 2;
   }
   SP_CUDA(cudaStreamSynchronize(s));
   sp::mixed_decide(p, R);
   for (; k <= p->max_iter && !R.done; ++k) {
-    if ((st = sp::mixed_correct(p, rho, s))) return st;
+    if ((st = sp::mixed_correct(p, rho, phi, s))) return st;
     if ((st = sp::mixed_issue_read(p, s, R))) return st;
     SP_CUDA(cudaStreamSynchronize(s));
     sp::mixed_decide(p, R);

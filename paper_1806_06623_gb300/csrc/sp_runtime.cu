@@ -113,7 +113,7 @@ extern "C" int sp_solve_batched(sp_plan* const* plans, const double* const* rho,
       // the first correction goes right behind the first solve (see solve_mixed)
       status[i] = sp::mixed_start(P[i], rho[i], stream_of(i));
       if (!status[i]) status[i] = sp::mixed_issue_read(P[i], stream_of(i), runs[i]);
-      if (!status[i] && P[i]->max_iter >= 1) status[i] = sp::mixed_correct(P[i], rho[i], stream_of(i));
+      if (!status[i] && P[i]->max_iter >= 1) status[i] = sp::mixed_correct(P[i], rho[i], phi[i], stream_of(i));
       if (!status[i] && P[i]->max_iter >= 1) status[i] = sp::mixed_issue_read(P[i], stream_of(i), runs[i]);
     } else {
       status[i] = sp::solve_fp64_async(P[i], rho[i], phi[i], stream_of(i));
@@ -132,7 +132,7 @@ extern "C" int sp_solve_batched(sp_plan* const* plans, const double* const* rho,
       if (!runs[i].done && runs[i].iters - 1 < P[i]->max_iter) next.push_back(i);
     }
     for (int i : next) {
-      status[i] = sp::mixed_correct(P[i], rho[i], stream_of(i));
+      status[i] = sp::mixed_correct(P[i], rho[i], phi[i], stream_of(i));
       if (!status[i]) status[i] = sp::mixed_issue_read(P[i], stream_of(i), runs[i]);
     }
     active.clear();
