@@ -57,6 +57,25 @@ def dist_env():
     return rank, world, local
 
 
+# ------------------------------------------------------------ multi-rank
+def max_over_ranks(x, world, device):
+    """Largest value of x over all ranks of the default process group (x itself for one
+    rank): the job's time is its slowest rank's."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank_step, steps, world, seconds):
+    """Units processed by all ranks per second of the slowest rank (weak scaling: every
+    rank solves its own instance)."""
+    return units_per_rank_step * steps * world / seconds
+
+
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -226,11 +245,7 @@ def run_ours(args, rank, world, local):
         timed_steps(plan, nb, collect=True)
         timing = {k: (v[0] * args.steps / nb, v[1] * args.steps // nb) for k, v in plan.timing().items()}
         plan.set_timing(False)
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([tot_ms], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            tot_ms = float(t.item())
+        tot_ms = max_over_ranks(tot_ms, world, dev)
         results[name] = {"ms": tot_ms, "infos": infos, "launches": launches, "timing": timing, "clocks": ck,
                          "phi": phi.detach().cpu().numpy() if (rank == 0 and not args.no_oracle_check) else None}
 
@@ -245,16 +260,12 @@ def run_ours(args, rank, world, local):
     for _ in range(args.steps):
         head.solve_host(rho_np, phi_np)
     e2e_s = time.perf_counter() - t0
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, world, dev)
 
     if rank != 0:
         return
     r = results[precision]
-    value = zones * args.steps * world / (r["ms"] / 1e3)
+    value = whole_job_rate(zones, args.steps, world, r["ms"] / 1e3)
     line = {
         "metric": METRIC, "value": value, "unit": "zones/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True,
@@ -270,12 +281,12 @@ def run_ours(args, rank, world, local):
                    "l2": "flushed (256 MB write) between timed steps"},
         "clocks": r["clocks"],
         "gpu_launches": r["launches"],
-        "e2e": {"value": zones * args.steps * world / e2e_s, "unit": "zones/s",
+        "e2e": {"value": whole_job_rate(zones, args.steps, world, e2e_s), "unit": "zones/s",
                 "h2d_bytes_per_step": int(p.rho.nbytes), "d2h_bytes_per_step": int(p.rho.nbytes)},
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in r["timing"].items()},
     }
     for name, rr in results.items():
-        line[f"{name}_zones_per_s"] = zones * args.steps * world / (rr["ms"] / 1e3)
+        line[f"{name}_zones_per_s"] = whole_job_rate(zones, args.steps, world, rr["ms"] / 1e3)
         line[f"{name}_ms_per_step"] = rr["ms"] / args.steps
     line["roofline"] = roofline(r["timing"], p, precision, args.steps, r["infos"][-1].get("iterations", 2))
     if not args.no_small:
