@@ -191,6 +191,16 @@ int sp_plan_set_timing(sp_plan* plan, int enable);
 int sp_plan_collect_timing(sp_plan* plan);
 int sp_plan_get_timing(const sp_plan* plan, double* ms, long long* count, int n);
 
+/* CUDA-graph replay of a mixed solve's first phase (no counterpart in the paper; on by
+ * default).  Phase A of sp_solve and sp_solve_batched -- the first low-precision solve,
+ * the first correction and the copies of their reductions to host -- is captured on a
+ * private stream of the plan at the second solve and replayed with one cudaGraphLaunch
+ * on the caller's stream while rho, phi and the workspace stay the same (it is captured
+ * again when one of them changes; sp_plan_set_workspace drops it).  Results are bitwise
+ * those of the launch-by-launch path.  With per-kernel timing enabled the plan launches
+ * kernel by kernel.  Returns SP_ERR_INVALID_ARG for a NULL plan. */
+int sp_plan_set_graphs(sp_plan* plan, int enable);
+
 /* Number of kernel launches this plan has issued since creation (host counter). */
 long long sp_plan_launch_count(const sp_plan* plan);
 

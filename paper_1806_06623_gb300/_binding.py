@@ -83,6 +83,7 @@ _SIGS = {
     "sp_plan_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "sp_plan_collect_timing": (C.c_int, [C.c_void_p]),
     "sp_plan_get_timing": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "sp_plan_set_graphs": (C.c_int, [C.c_void_p, C.c_int]),
     "sp_plan_launch_count": (C.c_longlong, [C.c_void_p]),
     "sp_plan_destroy": (C.c_int, [C.c_void_p]),
     "sp_status_string": (C.c_char_p, [C.c_int]),
@@ -374,6 +375,9 @@ class Plan:
 
     def timing(self):
         return sp_plan_get_timing(self._h)
+
+    def set_graphs(self, enable=True):
+        _check(lib().sp_plan_set_graphs(self._h, int(bool(enable))), "sp_plan_set_graphs")
 
     def launch_count(self) -> int:
         return sp_plan_launch_count(self._h)

@@ -149,6 +149,17 @@ struct Plan {
   MixedTables* mixed = nullptr;
   unsigned int* h_red = nullptr;  // pinned host copy of the mixed-path reductions
   const double* phi64_written = nullptr;   // output already holding the current iterate in float64
+  // CUDA graph of phase A of a mixed solve (first low-precision solve + first correction
+  // with their host reads), captured on a private stream for one (rho, phi, workspace)
+  bool graphs = true;
+  bool phase_a_warm = false;      // one direct phase A ran (attributes set, workspace bound)
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t ga_exec = nullptr;
+  const void* ga_rho = nullptr;
+  const void* ga_phi = nullptr;
+  const void* ga_ws = nullptr;
+  long long ga_launches = 0;
+  int ga_pending = 0;
   // side stream (high priority) and fork/join events: the multipole shell term of the
   // mixed residual runs beside the residual's interior rows
   cudaStream_t side = nullptr;
@@ -248,6 +259,10 @@ constexpr int kRedErrWord = 4;   // h_red: two slots of (max|e|, max|Phi|), then
 int mixed_start(Plan* p, const double* rho, cudaStream_t s);
 int mixed_correct(Plan* p, const double* rho, double* phi, cudaStream_t s);
 int mixed_issue_read(Plan* p, cudaStream_t s, MixedRun& R);
+// First low-precision solve and (max_iter >= 1) the first correction, each with the copy
+// of its reductions to a host slot; replayed from a CUDA graph when the plan allows.
+int mixed_phase_a(Plan* p, const double* rho, double* phi, cudaStream_t s, MixedRun& R);
+void drop_phase_graph(Plan& p);
 void mixed_decide(Plan* p, MixedRun& R);   // after the stream has reached the pending copies
 int mixed_finish(Plan* p, double* phi, cudaStream_t s, const MixedRun& R, sp_solve_info* info);
 int mixed_finish_issue(Plan* p, double* phi, cudaStream_t s);

@@ -100,6 +100,8 @@ void free_tables(Plan* p) {
   if (p->ws_owned) cudaFree(p->ws);
   for (int i = 0; i < 2 * sp::kMaxTimedLaunches; ++i)
     if (p->ev[i]) cudaEventDestroy(p->ev[i]);
+  sp::drop_phase_graph(*p);
+  if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   if (p->ev_fork) cudaEventDestroy(p->ev_fork);
   if (p->ev_join) cudaEventDestroy(p->ev_join);
   if (p->side) cudaStreamDestroy(p->side);
@@ -202,6 +204,82 @@ int mixed_issue_read(Plan* p, cudaStream_t s, MixedRun& R) {
                           s));
   R.next_slot ^= 1;
   ++R.pending;
+  return SP_OK;
+}
+
+namespace {
+
+int phase_a_direct(Plan* p, const double* rho, double* phi, cudaStream_t s, MixedRun& R) {
+  int st;
+  if ((st = mixed_start(p, rho, s))) return st;
+  if ((st = mixed_issue_read(p, s, R))) return st;
+  if (p->max_iter >= 1) {
+    if ((st = mixed_correct(p, rho, phi, s))) return st;
+    if ((st = mixed_issue_read(p, s, R))) return st;
+  }
+  return SP_OK;
+}
+
+// Capture phase A on the plan's private stream (thread-local capture mode, so other host
+// threads' calls are unaffected) and instantiate it; false leaves the plan without a graph.
+bool capture_phase_a(Plan* p, const double* rho, double* phi) {
+  if (!p->cap_stream && cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    p->cap_stream = nullptr;
+    return false;
+  }
+  const long long l0 = p->launches;
+  MixedRun Rc;
+  if (cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return false;
+  const int st = phase_a_direct(p, rho, phi, p->cap_stream, Rc);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(p->cap_stream, &g);
+  p->ga_launches = p->launches - l0;
+  p->launches = l0;   // nothing ran yet
+  bool ok = st == SP_OK && e == cudaSuccess && g != nullptr;
+  if (ok && cudaGraphInstantiate(&p->ga_exec, g, 0) != cudaSuccess) {
+    p->ga_exec = nullptr;
+    ok = false;
+  }
+  if (g) cudaGraphDestroy(g);
+  if (!ok) {
+    cudaGetLastError();   // clear a capture error; the plan runs phase A directly from now on
+    p->graphs = false;
+    return false;
+  }
+  p->ga_rho = rho;
+  p->ga_phi = phi;
+  p->ga_ws = p->ws;
+  p->ga_pending = Rc.pending;
+  return true;
+}
+
+}  // namespace
+
+void drop_phase_graph(Plan& p) {
+  if (p.ga_exec) cudaGraphExecDestroy(p.ga_exec);
+  p.ga_exec = nullptr;
+  p.ga_rho = p.ga_phi = p.ga_ws = nullptr;
+}
+
+// The first call runs directly (it sets the kernels' shared-memory attributes and binds the
+// workspace); later calls replay a graph captured for the same rho, phi and workspace
+// (re-captured when one of them changes).  Per-launch timers need the direct path.
+int mixed_phase_a(Plan* p, const double* rho, double* phi, cudaStream_t s, MixedRun& R) {
+  if (!p->graphs || p->timing || !p->phase_a_warm) {
+    const int st = phase_a_direct(p, rho, phi, s, R);
+    if (st == SP_OK) p->phase_a_warm = true;
+    return st;
+  }
+  if (!(p->ga_exec && p->ga_rho == rho && p->ga_phi == phi && p->ga_ws == p->ws)) {
+    drop_phase_graph(*p);
+    if (!capture_phase_a(p, rho, phi)) return phase_a_direct(p, rho, phi, s, R);
+  }
+  SP_CUDA(cudaGraphLaunch(p->ga_exec, s));
+  // host bookkeeping of what the graph did: its reductions sit in the first host slots
+  R.pending = p->ga_pending;
+  R.next_slot = p->ga_pending & 1;
+  p->phi64_written = p->max_iter >= 1 ? phi : nullptr;
+  p->launches += p->ga_launches;
   return SP_OK;
 }
 
@@ -310,14 +388,8 @@ int solve_mixed(Plan* p, const double* rho, double* phi, cudaStream_t s, sp_solv
   int st;
   // The first low-precision solve meets the tolerance only for rho == 0, so the first
   // correction is queued right behind it and both are read after one synchronisation.
-  if ((st = sp::mixed_start(p, rho, s))) return st;
-  if ((st = sp::mixed_issue_read(p, s, R))) return st;
-  int k = 1;
-  if (p->max_iter >= 1) {
-    if ((st = sp::mixed_correct(p, rho, phi, s))) return st;
-    if ((st = sp::mixed_issue_read(p, s, R))) return st;
-    k = 2;
-  }
+  if ((st = sp::mixed_phase_a(p, rho, phi, s, R))) return st;
+  int k = p->max_iter >= 1 ? 2 : 1;
   SP_CUDA(cudaStreamSynchronize(s));
   sp::mixed_decide(p, R);
   for (; k <= p->max_iter && !R.done; ++k) {
@@ -603,6 +675,10 @@ int sp_plan_clone(const sp_plan* src_plan, sp_plan** out) {
   }
   c->side = nullptr;
   c->ev_fork = c->ev_join = nullptr;
+  c->cap_stream = nullptr;
+  c->ga_exec = nullptr;
+  c->ga_rho = c->ga_phi = c->ga_ws = nullptr;
+  c->phase_a_warm = false;
   if (st == SP_OK) st = sp::create_side_stream(*c);
   if (st == SP_OK && cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess) st = SP_ERR_OOM;
   if (st == SP_OK && cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess) st = SP_ERR_CUDA;
@@ -633,6 +709,7 @@ int sp_plan_set_workspace(sp_plan* plan, void* dev, size_t bytes) {
   p->ws_bytes = bytes;
   p->ws_owned = false;
   sp::bind_workspace(*p, dev);
+  sp::drop_phase_graph(*p);
   return SP_OK;
 }
 
@@ -674,6 +751,15 @@ int sp_apply_laplacian(sp_plan* plan, const double* phi, double* out, void* stre
   int st = ensure_workspace(p);
   if (st) return st;
   return apply_laplacian_impl(p, phi, out, static_cast<cudaStream_t>(stream));
+}
+
+int sp_plan_set_graphs(sp_plan* plan, int enable) {
+  if (!plan) return SP_ERR_INVALID_ARG;
+  Plan* p = reinterpret_cast<Plan*>(plan);
+  DeviceGuard guard(p->device);
+  p->graphs = enable != 0;
+  if (!p->graphs) sp::drop_phase_graph(*p);
+  return SP_OK;
 }
 
 int sp_plan_set_timing(sp_plan* plan, int enable) {

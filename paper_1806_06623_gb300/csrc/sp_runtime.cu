@@ -111,10 +111,7 @@ extern "C" int sp_solve_batched(sp_plan* const* plans, const double* const* rho,
   for (int i = 0; i < n; ++i) {
     if (P[i]->mixed) {
       // the first correction goes right behind the first solve (see solve_mixed)
-      status[i] = sp::mixed_start(P[i], rho[i], stream_of(i));
-      if (!status[i]) status[i] = sp::mixed_issue_read(P[i], stream_of(i), runs[i]);
-      if (!status[i] && P[i]->max_iter >= 1) status[i] = sp::mixed_correct(P[i], rho[i], phi[i], stream_of(i));
-      if (!status[i] && P[i]->max_iter >= 1) status[i] = sp::mixed_issue_read(P[i], stream_of(i), runs[i]);
+      status[i] = sp::mixed_phase_a(P[i], rho[i], phi[i], stream_of(i), runs[i]);
     } else {
       status[i] = sp::solve_fp64_async(P[i], rho[i], phi[i], stream_of(i));
     }

@@ -158,3 +158,43 @@ def test_server_burst_of_mixed_sizes_all_succeed(S):
         assert S.sp_server_stats(srv)["failed"] == 0
     finally:
         S.sp_server_destroy(srv)
+
+
+@pytest.mark.parametrize("prec_name", ["SP_MIXED_BF16X6", "SP_MIXED_BF16X3"])
+def test_graph_replay_equals_direct(S, prec_name):
+    """Phase A replayed from a CUDA graph gives bitwise the launch-by-launch result, also
+    after the output buffer, the source or the workspace changes (re-capture)."""
+    prec = getattr(S, prec_name)
+    p = W.stellar_noise()
+    q = W.random_small(128, 64, 128, seed=11)
+    direct = S.Plan(p.r_if, p.th_if, p.nphi, precision=prec)
+    direct.set_graphs(False)
+    rho_p = torch.from_numpy(p.rho).cuda()
+    rho_q = torch.from_numpy(q.rho).cuda()
+    ref_p, info_p = direct.solve(rho_p)
+    ref_q, _ = direct.solve(rho_q)
+    plan = S.Plan(p.r_if, p.th_if, p.nphi, precision=prec)
+    out_a = torch.empty_like(rho_p)
+    out_b = torch.empty_like(rho_p)
+    n_direct = None
+    for k in range(4):                     # direct, capture + replay, replay, replay
+        n0 = plan.launch_count()
+        _, info = plan.solve(rho_p, out_a)
+        torch.cuda.synchronize()
+        assert torch.equal(out_a, ref_p), k
+        assert info.iterations == info_p.iterations and info.est_rel_error == info_p.est_rel_error
+        n = plan.launch_count() - n0
+        n_direct = n if n_direct is None else n_direct
+        assert n == n_direct               # the launch counter counts replayed kernels too
+    plan.solve(rho_p, out_b)               # another output buffer: captured again
+    torch.cuda.synchronize()
+    assert torch.equal(out_b, ref_p)
+    plan.solve(rho_q, out_b)               # another source
+    torch.cuda.synchronize()
+    assert torch.equal(out_b, ref_q)
+    ws = torch.empty(plan.workspace_bytes() // 8 + 64, dtype=torch.float64, device="cuda")
+    S.sp_plan_set_workspace(plan._h, ws)   # the graph goes with the old workspace
+    plan.solve(rho_p, out_a)
+    plan.solve(rho_p, out_a)
+    torch.cuda.synchronize()
+    assert torch.equal(out_a, ref_p)
