@@ -245,6 +245,25 @@ template <>
 __device__ __forceinline__ float load_in<float>(const double* p) { return d2ff(*p).hi; }   // no float64 pipe
 template <typename T>
 __device__ __forceinline__ T load_in(const float* p) { return (T)*p; }
+template <typename T>
+__device__ __forceinline__ T cvt_in(double x) { return (T)x; }
+template <>
+__device__ __forceinline__ float cvt_in<float>(double x) { return d2ff(x).hi; }   // no float64 pipe
+template <typename T>
+__device__ __forceinline__ T cvt_in(float x) { return (T)x; }
+
+// 16-byte vector of the input type: V values of one line
+template <typename Tin> struct Vec16;
+template <> struct Vec16<double> {
+  using t = double2;
+  static constexpr int V = 2;
+  __device__ static double at(const double2& w, int i) { return i ? w.y : w.x; }
+};
+template <> struct Vec16<float> {
+  using t = float4;
+  static constexpr int V = 4;
+  __device__ static float at(const float4& w, int i) { return i == 0 ? w.x : (i == 1 ? w.y : (i == 2 ? w.z : w.w)); }
+};
 
 // Forward: lines [line0, line0+nl) of `in` -> half spectrum scaled by `scale`,
 // spec[m][i][c][j] with row stride `rs` (Ntheta, or the padded panel stride).
@@ -274,6 +293,34 @@ __global__ void __launch_bounds__(256, 3) k_fft_fwd(const Tin* __restrict__ in, 
   // kLoadU values per thread in flight, then scatter into the packed complex lines.
   const int tot = nl * n;
   const Tin* src = in + (size_t)line0 * n;
+  using VT = typename Vec16<Tin>::t;
+  constexpr int V = Vec16<Tin>::V;
+  if (n % V == 0 && (reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
+    // 16-byte loads (V values of one line each), kLoadU values per thread in flight
+    constexpr int U = kLoadU / V;
+    const VT* vsrc = reinterpret_cast<const VT*>(src);
+    const int totv = tot / V;
+    for (int e0 = threadIdx.x; e0 < totv; e0 += blockDim.x * U) {
+      VT w[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * (int)blockDim.x;
+        if (e < totv) w[u] = __ldg(vsrc + e);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * (int)blockDim.x;
+        if (e < totv) {
+          const int ev = e * V;
+          const int line = sch.nshift >= 0 ? (ev >> sch.nshift) : (int)__umulhi((unsigned int)ev, sch.nmagic);
+          const int q = ev - line * n;
+          T* dst = reinterpret_cast<T*>(bufA + (line >> 1) * PS + q) + (line & 1);
+#pragma unroll
+          for (int i = 0; i < V; ++i) dst[2 * i] = cvt_in<T>(Vec16<Tin>::at(w[u], i));
+        }
+      }
+    }
+  } else
   for (int e0 = threadIdx.x; e0 < tot; e0 += blockDim.x * kLoadU) {
     T v[kLoadU];
 #pragma unroll
