@@ -464,6 +464,55 @@ __global__ void __launch_bounds__(256, 3) k_fft_inv(const T* __restrict__ spec, 
         }
       }
     } else {
+      if ((n & 3) == 0 && (reinterpret_cast<uintptr_t>(phi64) & 15u) == 0) {
+        // 16-byte accesses (a float64 output on an 8-byte boundary takes the scalar
+        // path): each lane owns 4 consecutive points; two lines x two
+        // segments of the iterate in flight per lane
+        for (int qb = 4 * lane; qb < n; qb += 256) {
+          float4 oh[2][2], ol[2][2];
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int sg = 0; sg < 2; ++sg) {
+              const int q = qb + 128 * sg;
+              const size_t o = o0 + (size_t)h * n + q;
+              const bool ok = q < n && (h == 0 || hasb) && !first;
+              oh[h][sg] = ok ? *reinterpret_cast<const float4*>(out + o) : make_float4(0.f, 0.f, 0.f, 0.f);
+              ol[h][sg] = ok ? *reinterpret_cast<const float4*>(phi_lo + o) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+          for (int sg = 0; sg < 2; ++sg) {
+            const int q = qb + 128 * sg;
+            if (q >= n) continue;
+            CT v[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) v[i] = z[q + i];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              if (h == 1 && !hasb) continue;
+              const size_t o = o0 + (size_t)h * n + q;
+              const float oh4[4] = {oh[h][sg].x, oh[h][sg].y, oh[h][sg].z, oh[h][sg].w};
+              const float ol4[4] = {ol[h][sg].x, ol[h][sg].y, ol[h][sg].z, ol[h][sg].w};
+              float nh[4], nl[4];
+#pragma unroll
+              for (int i = 0; i < 4; ++i) {
+                const float e = (float)(h ? v[i].y : v[i].x);
+                const ff nv = first ? ff{e, 0.f} : ff_add_f(ff{oh4[i], ol4[i]}, e);
+                nh[i] = nv.hi;
+                nl[i] = nv.lo;
+                me = fmaxf(me, fabsf(e));
+                mp = fmaxf(mp, fabsf(nv.hi));
+              }
+              *reinterpret_cast<float4*>(out + o) = make_float4(nh[0], nh[1], nh[2], nh[3]);
+              *reinterpret_cast<float4*>(phi_lo + o) = make_float4(nl[0], nl[1], nl[2], nl[3]);
+              if (phi64) {
+                reinterpret_cast<double2*>(phi64 + o)[0] = make_double2(ff2d(ff{nh[0], nl[0]}), ff2d(ff{nh[1], nl[1]}));
+                reinterpret_cast<double2*>(phi64 + o)[1] = make_double2(ff2d(ff{nh[2], nl[2]}), ff2d(ff{nh[3], nl[3]}));
+              }
+            }
+          }
+        }
+      } else
       // two lines x four segments of the iterate in flight per lane
       for (int q0 = lane; q0 < n; q0 += 128) {
         float oh[2][4], ol[2][4];
