@@ -198,7 +198,11 @@ int sp_plan_get_timing(const sp_plan* plan, double* ms, long long* count, int n)
  * on the caller's stream while rho, phi and the workspace stay the same (it is captured
  * again when one of them changes; sp_plan_set_workspace drops it).  Results are bitwise
  * those of the launch-by-launch path.  With per-kernel timing enabled the plan launches
- * kernel by kernel.  Returns SP_ERR_INVALID_ARG for a NULL plan. */
+ * kernel by kernel.  The capture runs in thread-local mode, but a device-wide
+ * synchronisation made by another host thread during it (sp_plan_destroy does one) can
+ * fail, so turn graphs off for plans solved while other threads create or destroy
+ * plans; the solve server's slots run without graphs.  Returns SP_ERR_INVALID_ARG for
+ * a NULL plan. */
 int sp_plan_set_graphs(sp_plan* plan, int enable);
 
 /* Number of kernel launches this plan has issued since creation (host counter). */

@@ -468,6 +468,7 @@ int sp_plan_create(const double* r_if, int nr, const double* th_if_in, int nth, 
                    double G, int precision, double tol, int max_iter, void* stream, sp_plan** out) {
   if (!out || !r_if) return SP_ERR_INVALID_ARG;
   *out = nullptr;
+  cudaGetLastError();   // an earlier failed call of this thread is not this call's error
   if (nr < 1 || nth < 1 || nphi < 1) return SP_ERR_GRID;
   if (outer_bc != SP_OUTER_MULTIPOLE && outer_bc != SP_OUTER_DIRICHLET) return SP_ERR_INVALID_ARG;
   if (precision != SP_FP64 && precision != SP_MIXED_BF16X3 && precision != SP_MIXED_BF16X6) return SP_ERR_INVALID_ARG;
@@ -645,6 +646,7 @@ int sp_plan_create(const double* r_if, int nr, const double* th_if_in, int nth, 
 }
 
 int sp_plan_clone(const sp_plan* src_plan, sp_plan** out) {
+  cudaGetLastError();   // an earlier failed call of this thread is not this call's error
   if (!src_plan || !out) return SP_ERR_INVALID_ARG;
   *out = nullptr;
   const Plan* src = reinterpret_cast<const Plan*>(src_plan);
@@ -714,6 +716,7 @@ int sp_plan_set_workspace(sp_plan* plan, void* dev, size_t bytes) {
 }
 
 int sp_solve(sp_plan* plan, const double* rho, double* phi, void* stream, sp_solve_info* info) {
+  cudaGetLastError();   // an earlier failed call of this thread is not this call's error
   if (!plan || !rho || !phi) return SP_ERR_INVALID_ARG;
   Plan* p = reinterpret_cast<Plan*>(plan);
   const size_t bytes = sizeof(double) * (size_t)p->nr * p->nth * p->nphi;
@@ -727,6 +730,7 @@ int sp_solve(sp_plan* plan, const double* rho, double* phi, void* stream, sp_sol
 }
 
 int sp_solve_host(sp_plan* plan, const double* rho_host, double* phi_host, void* stream, sp_solve_info* info) {
+  cudaGetLastError();   // an earlier failed call of this thread is not this call's error
   if (!plan || !rho_host || !phi_host) return SP_ERR_INVALID_ARG;
   Plan* p = reinterpret_cast<Plan*>(plan);
   const size_t bytes = sizeof(double) * (size_t)p->nr * p->nth * p->nphi;

@@ -73,6 +73,7 @@ struct DeviceScope {
 
 extern "C" int sp_solve_batched(sp_plan* const* plans, const double* const* rho, double* const* phi, int n,
                                 void* stream, sp_solve_info* infos) {
+  cudaGetLastError();   // an earlier failed call of this thread is not this call's error
   if (n < 0) return SP_ERR_INVALID_ARG;
   if (n == 0) return SP_OK;
   if (!plans || !rho || !phi) return SP_ERR_INVALID_ARG;
@@ -347,7 +348,9 @@ void sp_server::worker(int slot) {
     const size_t clone_bytes = res.clone_bytes;
     lock.unlock();
     // ---- run on this slot's stream
-    if (st == SP_OK && !plan) st = sp_plan_clone(master, &plan);
+    // slots launch kernel by kernel: a graph capture on one slot's thread while another
+    // slot's thread allocates or synchronises would make that thread's call fail
+    if (st == SP_OK && !plan && (st = sp_plan_clone(master, &plan)) == SP_OK) sp_plan_set_graphs(plan, 0);
     const size_t need_io = 2 * q->zones * sizeof(double);
     if (st == SP_OK && d_io_bytes < need_io) {
       cudaFree(d_io);

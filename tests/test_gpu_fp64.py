@@ -164,3 +164,26 @@ def test_bad_pointers_rejected(S):
     x = torch.zeros(p.rho.shape, dtype=torch.float64, device="cuda")
     with pytest.raises(S.SpError):
         S.sp_solve(plan.handle, x, x, p.rho.shape)      # Phi aliases rho
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_solve_host_mixed_equals_device(pinned):
+    """Host-buffer solve of a mixed plan, with page-locked and with pageable buffers, gives
+    bitwise the device-buffer result, also on the graph-replayed repeats."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1806_06623_gb300 as S
+    p = W.stellar_noise()
+    plan = S.Plan(p.r_if, p.th_if, p.nphi, precision=S.SP_MIXED_BF16X6)
+    ref, _ = plan.solve(torch.from_numpy(p.rho).cuda())
+    ref = ref.cpu().numpy()
+    if pinned:
+        rho_h = torch.from_numpy(p.rho).pin_memory()
+        phi_h = torch.empty(p.rho.shape, dtype=torch.float64).pin_memory()
+        rho_np, phi_np = rho_h.numpy(), phi_h.numpy()
+    else:
+        rho_np, phi_np = np.ascontiguousarray(p.rho), np.empty_like(p.rho)
+    for _ in range(3):                      # direct, then graph capture and replays
+        phi_np[:] = 0.0
+        plan.solve_host(rho_np, phi_np)
+        assert np.array_equal(phi_np, ref)
