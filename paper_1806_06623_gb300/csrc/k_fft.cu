@@ -411,11 +411,11 @@ __global__ void __launch_bounds__(256, 3) k_fft_inv(const T* __restrict__ spec, 
       j = g - i * nth;
     }
     // Z[m] = G_A[m] + i G_B[m] (even lane writes), Z[n-m] = conj G_A[m] + i conj G_B[m] (odd lane);
-    // four m-rows are loaded before any is consumed
-    for (int m0 = warp; m0 < mh; m0 += 4 * kWarps) {
-      CT vv[4];
+    // eight m-rows are loaded before any is consumed
+    for (int m0 = warp; m0 < mh; m0 += 8 * kWarps) {
+      CT vv[8];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < 8; ++u) {
         const int m = m0 + u * kWarps;
         vv[u].x = T(0);
         vv[u].y = T(0);
@@ -426,7 +426,7 @@ __global__ void __launch_bounds__(256, 3) k_fft_inv(const T* __restrict__ spec, 
         }
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < 8; ++u) {
         const int m = m0 + u * kWarps;
         const CT v = vv[u];
         CT o;
