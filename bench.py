@@ -439,7 +439,7 @@ def run_served(S, W, torch, n_requests, rates=(200.0, 2000.0, 20000.0)):
 # named command (full workload), per kernel group; kept only while the kernel is unchanged
 NCU_TRAFFIC = {
     "mixed": {
-        "residual": {"bytes": (291.25 + 59.09) * 1e6, "kernel": "k_residual_ff (interior rows)",
+        "residual": {"bytes": (291.32 + 59.17) * 1e6, "kernel": "k_residual_ff (interior rows)",
                      "profile": "profiles/mixed_x6_550x128x256_kernels.md"},
     },
 }
