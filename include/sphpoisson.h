@@ -74,12 +74,13 @@ typedef struct {
     int iterations;        /* low-precision solves performed (1 for SP_FP64) */
     int precision_used;    /* SP_FP64, SP_MIXED_BF16X3 or SP_MIXED_BF16X6 */
     double last_update;    /* max|e|/max|Phi| of the last correction (0 for SP_FP64) */
-    double est_rel_error;  /* estimated max|Phi - Phi_fix|/max|Phi| (0 for SP_FP64), Phi_fix the
-                              fixed point of the refinement.  Phi_fix differs from the exact
-                              solution by the rounding floor of the float-float residual (at
-                              least 46 significant bits), which grows with the grid's
-                              conditioning: about 2e-12 at 550 log-spaced radial cells, 1e-11
-                              at 1600, always below the 1e-10 tolerance class */
+    double est_rel_error;  /* estimated max|Phi - Phi_exact|/max|Phi| (0 for SP_FP64): the larger of
+                              the refinement's contraction estimate and its precision floor
+                              8 x 2^-48 x (Nphi / 2 pi)^2 (the 48-bit float-float iterate seen
+                              through the phi part of the operator; 4.7e-11 at Nphi = 256).
+                              When the floor exceeds tol the solve stops and returns
+                              SP_ERR_NOT_CONVERGED: use SP_FP64 or a looser tol there
+                              (at tol 1e-10 the mixed modes reach Nphi = 372) */
     int status;            /* sp_status of the solve */
     double update_history[8]; /* max|e_k|/max|Phi| of the first 8 solves (k = 0 is the first solve) */
 } sp_solve_info;

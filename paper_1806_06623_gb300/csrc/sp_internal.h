@@ -254,6 +254,7 @@ struct MixedRun {
   int pending = 0;     // reductions copied to host slots but not yet read (at most 2)
   int next_slot = 0;   // host slot of the next copy
   bool done = false;
+  bool floor_limited = false;   // the iterate's precision floor is above the tolerance
 };
 constexpr int kRedErrWord = 4;   // h_red: two slots of (max|e|, max|Phi|), then the status word
 int mixed_start(Plan* p, const double* rho, cudaStream_t s);

@@ -311,7 +311,17 @@ void decide_one(Plan* p, MixedRun& R, const unsigned int* slot) {
   const double ratio = (R.iters >= 2 && R.e_prev > 0.0) ? e_cur / R.e_prev : 0.0;
   const double c = ratio > bound ? ratio : bound;
   R.est = c < 1.0 ? R.last * c / (1.0 - c) : R.last;
-  R.done = R.est <= p->tol || R.last <= 1e-15;
+  // Precision floor of the refinement: the float-float iterate carries 48 bits, and its
+  // representation error reaches the residual through the phi part of the operator,
+  // whose largest eigenvalue grows as (Nphi / 2 pi)^2; the fixed point then differs
+  // from the exact solution by up to floor = 8 x 2^-48 x (Nphi / 2 pi)^2 (8: the largest
+  // measured ratio of error to 2^-48 (Nphi / 2 pi)^2 was 5.9, over Ntheta 8 and 64,
+  // Nphi 128..4096).  Below the floor no further correction helps.
+  const double kq = p->nphi / (2.0 * kPi);
+  const double floor = 8.0 * 3.552713678800501e-15 * kq * kq;
+  if (floor > R.est) R.est = floor;
+  R.floor_limited = floor > p->tol;
+  R.done = R.est <= p->tol || R.last <= 1e-15 || R.floor_limited;
   R.e_prev = e_cur;
   ++R.iters;
 }
@@ -343,7 +353,7 @@ int mixed_finish_status(Plan* p, const MixedRun& R, sp_solve_info* info) {
   Plan& P = *p;
   const int herr = (int)P.h_red[kRedErrWord];
   const int st = herr ? ((herr & kErrTimeout) ? SP_ERR_TIMEOUT : SP_ERR_DEVICE_CHECK)
-                      : (R.done ? SP_OK : SP_ERR_NOT_CONVERGED);
+                      : ((R.done && !R.floor_limited) ? SP_OK : SP_ERR_NOT_CONVERGED);
   if (info) {
     info->iterations = R.iters;
     info->precision_used = P.precision;

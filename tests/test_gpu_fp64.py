@@ -52,6 +52,8 @@ CASES = [
     (65, 31, 96, "rand", 0.1, 0),
     (40, 160, 12, "log", 0.0, 0),     # largest supported Ntheta
     (9, 6, 384, "uniform", 0.0, 1),   # long phi lines
+    (3, 4, 4096, "log", 0.0, 0),      # largest supported Nphi
+    (2, 3, 3072, "uniform", 0.0, 1),  # long radix-3 line, Dirichlet
 ]
 
 

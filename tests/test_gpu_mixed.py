@@ -51,7 +51,30 @@ CASES = [
     (300, 96, 192, "log", 0.0, 0),     # radix-3 phi, partial second K block
     (257, 64, 8, "uniform", 0.0, 1),
     (1600, 6, 4, "log", 0.0, 0),       # radial column beyond the shared-memory scan: ring-staged sweeps
+    (4, 4, 1, "uniform", 0.0, 0),      # axisymmetric: one phi zone
+    (3, 2, 2, "log", 0.0, 0),          # smallest even phi count
 ]
+
+
+@pytest.mark.parametrize("mode", ["x3", "x6"])
+@pytest.mark.parametrize("nr,nth,nphi,grid,bc", [(4, 8, 4096, "log", 0), (3, 5, 3072, "rand", 1)])
+def test_mixed_long_phi_lines_report_their_floor(S, nr, nth, nphi, grid, bc, mode):
+    """Nphi up to 4096 (six radix-4 stages; a long radix-3 line): the float-float
+    iterate's precision floor grows as Nphi^2 and passes 1e-10 near Nphi = 372, so a
+    1e-10 request stops with SP_ERR_NOT_CONVERGED instead of claiming it; a looser
+    request succeeds with the estimate bounding the true error."""
+    p = W.random_small(nr, nth, nphi, seed=nr + 3 * nth + nphi, grid=grid, outer_bc=bc)
+    prec = S.SP_MIXED_BF16X3 if mode == "x3" else S.SP_MIXED_BF16X6
+    ref = O.solve_exact(O.Geometry(p.r_if, p.th_if, p.nphi), p.rho, outer_bc=bc)
+    rho = torch.from_numpy(np.ascontiguousarray(p.rho)).cuda()
+    strict = S.Plan(p.r_if, p.th_if, p.nphi, outer_bc=bc, precision=prec, tol=TOL)
+    with pytest.raises(S.SpError) as ei:
+        strict.solve(rho)
+    assert ei.value.status == S.SP_ERR_NOT_CONVERGED
+    _, phi, info = mixed_solve(S, p, tol=1e-7, precision=prec)
+    err = rel_err(phi, ref)
+    assert info.status == S.SP_OK
+    assert err <= info.est_rel_error <= 1e-7
 
 
 @pytest.mark.parametrize("mode", ["x3", "x6"])
