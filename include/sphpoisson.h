@@ -94,7 +94,9 @@ typedef struct {
  *  G                 gravitational constant (s = 4 pi G rho)
  *  precision         SP_FP64, SP_MIXED_BF16X3 or SP_MIXED_BF16X6 (mixed: Ntheta <= 128)
  *  tol, max_iter     refinement target max|Phi-Phi_exact|/max|Phi| and iteration cap
- *                    (mixed precision only; e.g. 1e-10 and 8)
+ *                    (mixed precision only; e.g. 1e-10 and 8).  tol below the mixed
+ *                    modes' precision floor 8 x 2^-48 x (Nphi / 2 pi)^2 cannot be met
+ *                    (see sp_solve_info.est_rel_error): 1e-10 holds up to Nphi = 372
  *  stream            set-up work (theta eigensolve on the GPU) runs on this stream and
  *                    is complete when the call returns
  *  out               receives the plan; the plan owns its tables and, until
