@@ -280,7 +280,9 @@ __global__ void __launch_bounds__(256, 3) k_fft_fwd(const Tin* __restrict__ in, 
   CT* bufA = tw + n;
   CT* bufB = bufA + P * PS;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  load_twiddles<T>(tw, twid, n);
+  load_twiddles<T>(tw, twid, n);   // plan-constant: before the dependency wait
+  pdl_trigger();
+  pdl_wait();
   const int line0 = blockIdx.x * lpc;
   const int nl = min(lpc, nlines - line0);
   const int npairs = (nl + 1) / 2;
@@ -391,7 +393,9 @@ __global__ void __launch_bounds__(256, 3) k_fft_inv(const T* __restrict__ spec, 
   CT* bufA = tw + n;
   CT* bufB = bufA + P * PS;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  load_twiddles<T>(tw, twid, n);
+  load_twiddles<T>(tw, twid, n);   // plan-constant: before the dependency wait
+  pdl_trigger();
+  pdl_wait();
   const int line0 = blockIdx.x * lpc;
   const int nl = min(lpc, nlines - line0);
   const int npairs = (nl + 1) / 2;
@@ -641,13 +645,15 @@ cudaError_t fft_forward_panel(const Plan& p, const void* in, bool in_double, flo
   if (in_double) {
     auto kern = k_fft_fwd<float, double>;
     if ((e = prep(kern, smem)) != cudaSuccess) return e;
-    kern<<<grid, 32 * kWarps, smem, s>>>(static_cast<const double*>(in), nlines, p.nth, p.nr, p.sched, p.d_twid32,
-                                         scale, lpc, out, kstride, resident_ctas(kern, smem, p.num_sms));
+    e = launch_pdl(kern, dim3(grid), dim3(32 * kWarps), smem, s, static_cast<const double*>(in), nlines, p.nth, p.nr,
+                   p.sched, (const float*)p.d_twid32, scale, lpc, out, kstride, resident_ctas(kern, smem, p.num_sms));
+    if (e != cudaSuccess) return e;
   } else {
     auto kern = k_fft_fwd<float, float>;
     if ((e = prep(kern, smem)) != cudaSuccess) return e;
-    kern<<<grid, 32 * kWarps, smem, s>>>(static_cast<const float*>(in), nlines, p.nth, p.nr, p.sched, p.d_twid32,
-                                         scale, lpc, out, kstride, resident_ctas(kern, smem, p.num_sms));
+    e = launch_pdl(kern, dim3(grid), dim3(32 * kWarps), smem, s, static_cast<const float*>(in), nlines, p.nth, p.nr,
+                   p.sched, (const float*)p.d_twid32, scale, lpc, out, kstride, resident_ctas(kern, smem, p.num_sms));
+    if (e != cudaSuccess) return e;
   }
   return cudaGetLastError();
 }
@@ -661,9 +667,9 @@ cudaError_t fft_inverse_update(const Plan& p, const float* spec, float* phi_hi, 
   cudaError_t e = prep(kern, smem);
   if (e != cudaSuccess) return e;
   // (prefetching the iterate a wave ahead measured slower here: ahead = 0)
-  kern<<<(nlines + lpc - 1) / lpc, 32 * kWarps, smem, s>>>(spec, nlines, p.nth, p.nr, p.sched, p.d_twid32, lpc, phi_hi,
-                                                           phi_lo, first ? 1 : 0, red, 0, first ? nullptr : phi64);
-  return cudaGetLastError();
+  e = launch_pdl(kern, dim3((nlines + lpc - 1) / lpc), dim3(32 * kWarps), smem, s, spec, nlines, p.nth, p.nr, p.sched,
+                 (const float*)p.d_twid32, lpc, phi_hi, phi_lo, first ? 1 : 0, red, 0, first ? nullptr : phi64);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace sp

@@ -227,6 +227,8 @@ __global__ void __launch_bounds__(kScanThreads) k_thomas_scan(
   __shared__ float sE[kScanSegs][kScanCols], sP[kScanSegs][kScanCols], sC[kScanSegs][kScanCols];
   const int tid = threadIdx.x;
   const size_t st = 2 * (size_t)nth;
+  pdl_trigger();
+  pdl_wait();
   if ((int)blockIdx.x < nlowblk) {
     // ---- float64 near-singular modes: warp pair (re, im) per mode, same segmented scan
     // over the warp's 32 lanes, carries by a shuffle scan of the affine segment maps
@@ -491,6 +493,8 @@ __global__ void __launch_bounds__(kResThreads) k_residual_ff(const double* __res
                                                              int nphi, int row_begin, int row_end, int dirichlet,
                                                              ff dir_coef, ff four_pi_g) {
   __shared__ float line[2][2][kResThreads + 2];   // [row parity][hi, lo][k - k0 + 1]
+  pdl_trigger();
+  pdl_wait();
   const int j = blockIdx.x;
   const int i0 = row_begin + (int)blockIdx.y * kResRows, i1 = min(row_end, i0 + kResRows);
   const int t = threadIdx.x;
@@ -612,6 +616,7 @@ __global__ void __launch_bounds__(256) k_finish(const float* __restrict__ ph, co
 // The same for 16-byte aligned arrays, four values per thread and step.
 __global__ void __launch_bounds__(256) k_finish4(const float4* __restrict__ ph, const float4* __restrict__ pl,
                                                  double2* __restrict__ phi, size_t n4) {
+  pdl_wait();
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n4; q += (size_t)gridDim.x * blockDim.x) {
     const float4 h = __ldg(ph + q), l = __ldg(pl + q);
     phi[2 * q] = make_double2(ff2d(ff{h.x, l.x}), ff2d(ff{h.y, l.y}));
@@ -771,7 +776,8 @@ cudaError_t tc_project_np(const Plan& p, bool inverse, cudaStream_t s) {
   constexpr uint32_t smem = tc::smem_bytes<NP>();
   cudaError_t e = allow_smem(tc::k_tc_gemm_split<NP>, smem);
   if (e != cudaSuccess) return e;
-  tc::k_tc_gemm_split<NP><<<dim3(nsplit, p.mh), tc::kThreads, smem, s>>>(maps, prm);
+  e = launch_pdl(tc::k_tc_gemm_split<NP>, dim3(nsplit, p.mh), dim3(tc::kThreads), smem, s, maps, prm);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
@@ -787,10 +793,11 @@ cudaError_t thomas_mixed(const Plan& p, cudaStream_t s) {
     const int nlowblk = (x.nlow + kScanThreads / 64 - 1) / (kScanThreads / 64);
     cudaError_t e = allow_smem(k_thomas_scan, smem);
     if (e != cudaSuccess) return e;
-    k_thomas_scan<<<nlowblk + nblk, kScanThreads, smem, s>>>(
-        x.sub_r, p.d_lam, x.d32, x.fcp, x.finv, x.panel, p.nr, p.nth, x.kstride,
-        x.low_threshold, nlowblk, x.low_idx, x.nlow, p.d_rad, x.low_fac);
-    return cudaGetLastError();
+    e = launch_pdl(k_thomas_scan, dim3(nlowblk + nblk), dim3(kScanThreads), smem, s, (const float*)x.sub_r,
+                   (const double*)p.d_lam, (const float*)x.d32, (const float*)x.fcp, (const float*)x.finv, x.panel,
+                   p.nr, p.nth, x.kstride, x.low_threshold, nlowblk, (const int*)x.low_idx, x.nlow,
+                   (const RadialRow*)p.d_rad, (const double2*)x.low_fac);
+    return e != cudaSuccess ? e : cudaGetLastError();
   }
   const int nblk = 2 * p.mh * ((p.nth + 31) / 32);
   const int nlowblk = x.nlow;   // one warp per float64 mode
@@ -818,10 +825,11 @@ cudaError_t residual_ff(const Plan& p, const double* rho, cudaStream_t s) {
   const int tpb = p.nphi >= kResThreads ? kResThreads : ((p.nphi + 31) / 32) * 32;
   auto rows = [&](int r0, int r1, cudaStream_t st) {   // rows [r0, r1)
     const dim3 grid(p.nth, (r1 - r0 + kResRows - 1) / kResRows, (p.nphi + tpb - 1) / tpb);
-    k_residual_ff<<<grid, tpb, 0, st>>>(rho, x.phi_hi, x.phi_lo, x.outer_shell, x.r32, x.radff, x.thff, p.nr, p.nth,
-                                        p.nphi, r0, r1, p.outer_bc == SP_OUTER_DIRICHLET ? 1 : 0, x.dir_coef,
-                                        x.four_pi_g);
-    return cudaGetLastError();
+    const cudaError_t e = launch_pdl(k_residual_ff, grid, dim3(tpb), 0, st, rho, (const float*)x.phi_hi,
+                                     (const float*)x.phi_lo, (const double*)x.outer_shell, x.r32,
+                                     (const RadialRowFF*)x.radff, (const ThetaRowFF*)x.thff, p.nr, p.nth, p.nphi, r0,
+                                     r1, p.outer_bc == SP_OUTER_DIRICHLET ? 1 : 0, x.dir_coef, x.four_pi_g);
+    return e != cudaSuccess ? e : cudaGetLastError();
   };
   if (p.outer_bc != SP_OUTER_MULTIPOLE) return rows(0, p.nr, s);
   // The multipole term of the last shell (small: Ntheta x Nphi zones, float64 FFTs and
@@ -850,9 +858,10 @@ cudaError_t finish_mixed(const Plan& p, double* phi, cudaStream_t s) {
   if (aligned) {
     size_t blocks = (n / 4 + 255) / 256;
     if (blocks > (size_t)p.num_sms * 8) blocks = (size_t)p.num_sms * 8;
-    k_finish4<<<(unsigned)blocks, 256, 0, s>>>(reinterpret_cast<const float4*>(x.phi_hi),
-                                               reinterpret_cast<const float4*>(x.phi_lo),
-                                               reinterpret_cast<double2*>(phi), n / 4);
+    const cudaError_t e = launch_pdl(k_finish4, dim3((unsigned)blocks), dim3(256), 0, s,
+                                     reinterpret_cast<const float4*>(x.phi_hi), reinterpret_cast<const float4*>(x.phi_lo),
+                                     reinterpret_cast<double2*>(phi), n / 4);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
   }
   size_t blocks = (n + 255) / 256;

@@ -5,6 +5,7 @@
 #include <atomic>
 #include <cstddef>
 #include <cstdint>
+#include <utility>
 
 #include "ff.cuh"
 #include "sphpoisson.h"
@@ -176,6 +177,30 @@ struct Plan {
 };
 
 // Record a launch of kernel `id` issued by `launch()` on stream s.
+// Programmatic dependent launch (mixed-path kernels): a kernel launched with
+// launch_pdl may be scheduled while the previous kernel of its stream finishes; it
+// signals pdl_trigger() early, runs only its independent prologue (shared memory,
+// barriers, TMEM, plan-constant tables) and calls pdl_wait() -- which returns once the
+// previous kernel has completed and its memory is visible -- before any other global
+// access.  Launched the ordinary way both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
 template <typename F>
 cudaError_t timed_launch(Plan& p, int id, cudaStream_t s, F&& launch) {
   const bool t = p.timing && p.n_timed < kMaxTimedLaunches;

@@ -255,16 +255,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm_split(const __grid_cons
     *abort = 1;
     atomicOr(prm.err, kErrTimeout);
   };
+  // the table planes are plan constants: loaded while the previous kernel may still run
+  pdl_trigger();
+  if (warp == 0 && lane == 0 && nt > 0) {
+    const uint32_t ba = smem_u32(&bar_a);
+    mbar_expect_tx(ba, (uint32_t)kb * NP * kABlockBytes);
+    for (int pl = 0; pl < NP; ++pl)
+      for (int b = 0; b < kb; ++b) tma_load_3d(sA + (pl * kMaxKBlocks + b) * kABlockBytes, &maps.a[pl], b * kKBlk, 0, m, ba);
+  }
+  pdl_wait();
 
   if (warp == 0) {
     if (lane == 0 && nt > 0) {
-      // ---- table planes of m, once
-      const uint32_t ba = smem_u32(&bar_a);
-      mbar_expect_tx(ba, (uint32_t)kb * NP * kABlockBytes);
-      for (int pl = 0; pl < NP; ++pl)
-        for (int b = 0; b < kb; ++b) tma_load_3d(sA + (pl * kMaxKBlocks + b) * kABlockBytes, &maps.a[pl], b * kKBlk, 0, m, ba);
-      // the copy lands before the CTA frees its shared memory
-      mbar_wait(ba, 0);
+      // the table copy lands before the CTA frees its shared memory
+      mbar_wait(smem_u32(&bar_a), 0);
     }
   } else if (warp == 1) {
     if (lane == 0 && nt > 0) {
