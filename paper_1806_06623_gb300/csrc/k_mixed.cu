@@ -766,17 +766,15 @@ cudaError_t tc_project_np(const Plan& p, bool inverse, cudaStream_t s) {
   const MixedTables& x = *p.mixed;
   tc::Maps maps;
   for (int q = 0; q < NP; ++q) std::memcpy(&maps.a[q], inverse ? x.map_Ai[q] : x.map_Af[q], sizeof(CUtensorMap));
-  // one CTA per SM: split an m's column tiles over several CTAs only while the grid
-  // still fits in one wave
+  // one CTA per SM, each with an equal share of the (m, column tile) list
   const int tiles = (2 * p.nr + tc::Cfg<NP>::BN - 1) / tc::Cfg<NP>::BN;
-  int nsplit = p.num_sms / p.mh;
-  if (nsplit > tiles) nsplit = tiles;
-  if (nsplit < 1) nsplit = 1;
-  tc::Params prm{x.d32, x.panel, p.nth, p.nth, x.kstride, 2 * p.nr, (p.nth + tc::kKBlk - 1) / tc::kKBlk, nsplit, p.d_err};
+  const long long total = (long long)tiles * p.mh;
+  const int grid = (int)std::min<long long>(total, p.num_sms);
+  tc::Params prm{x.d32, x.panel, p.nth, p.nth, x.kstride, 2 * p.nr, (p.nth + tc::kKBlk - 1) / tc::kKBlk, p.mh, p.d_err};
   constexpr uint32_t smem = tc::smem_bytes<NP>();
   cudaError_t e = allow_smem(tc::k_tc_gemm_split<NP>, smem);
   if (e != cudaSuccess) return e;
-  e = launch_pdl(tc::k_tc_gemm_split<NP>, dim3(nsplit, p.mh), dim3(tc::kThreads), smem, s, maps, prm);
+  e = launch_pdl(tc::k_tc_gemm_split<NP>, dim3(grid), dim3(tc::kThreads), smem, s, maps, prm);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }

@@ -11,9 +11,13 @@
 //   NP = 3: A2 B0 + A0 B2 + A1 B1 + A1 B0 + A0 B1 + A0 B0      (6 products, ~2^-24)
 // accumulated in float32 in tensor memory.
 //
-// Persistent per m, warp-specialised pipeline (448 threads, one CTA per SM):
-//  - warp 0 (one lane) loads the A planes of m once (TMA, 128B-swizzled K-major boxes of
-//    64 K-elements);
+// Persistent, warp-specialised pipeline (448 threads, one CTA per SM).  The column tiles
+// of all m form one list g = m x tiles + t; CTA c takes the contiguous range
+// [G c / grid, G (c+1) / grid), so every SM gets the same number of tiles give or take one,
+// and the range covers a few consecutive m (a segment per m):
+//  - warp 0 (one lane) loads the A planes of each segment's m (TMA, 128B-swizzled K-major
+//    boxes of 64 K-elements), the next segment's only after the products of the previous
+//    one have completed;
 //  - warps 6..13 stream the panel rows of the CTA's column tiles one K block at a time
 //    (float4 loads, the next block in flight while the current one is converted),
 //    split them into bf16 planes and store those in the 128B-swizzled K-major layout of
@@ -70,7 +74,7 @@ struct Params {
   int kstride;       // panel row stride (multiple of 8)
   int ncol;          // columns per m
   int kblocks;       // ceil(K / 64)
-  int nsplit;        // CTAs per m (gridDim.x); each takes a contiguous range of column tiles
+  int mh;            // number of m (batch of the products)
   int* err;
 };
 
@@ -211,7 +215,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm_split(const __grid_cons
   const uint32_t base_u32 = (smem_u32(smem_raw) + 1023u) & ~1023u;
   const uint32_t sA = base_u32;                                  // [NP][kMaxKBlocks] x 16 KB
   const uint32_t sB = sA + NP * kMaxKBlocks * kABlockBytes;      // [S][NP] x BN*128 B
-  __shared__ __align__(8) uint64_t bar_a;
+  __shared__ __align__(8) uint64_t bar_a, bar_afree;
   __shared__ __align__(8) uint64_t bar_full[S], bar_empty[S];
   __shared__ __align__(8) uint64_t bar_tfull[2], bar_tempty[2];
   __shared__ uint32_t tmem_base;
@@ -220,13 +224,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm_split(const __grid_cons
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
   const int lane = tid & 31;
-  const int m = blockIdx.y;
   const int kb = prm.kblocks;
   const int tiles = (prm.ncol + BN - 1) / BN;
-  const int t0 = (int)(((long long)tiles * blockIdx.x) / prm.nsplit);
-  const int t1 = (int)(((long long)tiles * (blockIdx.x + 1)) / prm.nsplit);
-  const int nt = t1 - t0;
-  const int nq = nt * kb;   // work chunks q = (tile t = q / kb, K block b = q % kb)
+  const long long gtot = (long long)tiles * prm.mh;
+  const int g0 = (int)((gtot * blockIdx.x) / gridDim.x);
+  const int g1 = (int)((gtot * (blockIdx.x + 1)) / gridDim.x);
+  const int nt = g1 - g0;
+  const int nq = nt * kb;   // work chunks q = (tile g0 + q / kb, K block q % kb)
+  const int m0 = g0 / tiles;
+  const int nseg = nt > 0 ? (g1 - 1) / tiles - m0 + 1 : 0;   // consecutive m values covered
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
@@ -236,6 +242,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm_split(const __grid_cons
   if (tid == 32) {
     s_abort = 0;
     mbar_init(smem_u32(&bar_a), 1);
+    mbar_init(smem_u32(&bar_afree), 1);
     for (int q = 0; q < S; ++q) {
       mbar_init(smem_u32(&bar_full[q]), kConvThreads);
       mbar_init(smem_u32(&bar_empty[q]), 1);
@@ -255,20 +262,30 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm_split(const __grid_cons
     *abort = 1;
     atomicOr(prm.err, kErrTimeout);
   };
-  // the table planes are plan constants: loaded while the previous kernel may still run
-  pdl_trigger();
-  if (warp == 0 && lane == 0 && nt > 0) {
+  auto load_a = [&](int m) {
     const uint32_t ba = smem_u32(&bar_a);
     mbar_expect_tx(ba, (uint32_t)kb * NP * kABlockBytes);
     for (int pl = 0; pl < NP; ++pl)
       for (int b = 0; b < kb; ++b) tma_load_3d(sA + (pl * kMaxKBlocks + b) * kABlockBytes, &maps.a[pl], b * kKBlk, 0, m, ba);
-  }
+  };
+  // the table planes are plan constants: loaded while the previous kernel may still run
+  pdl_trigger();
+  if (warp == 0 && lane == 0 && nseg > 0) load_a(m0);
   pdl_wait();
 
   if (warp == 0) {
-    if (lane == 0 && nt > 0) {
-      // the table copy lands before the CTA frees its shared memory
-      mbar_wait(smem_u32(&bar_a), 0);
+    if (lane == 0 && nseg > 0) {
+      // segment sg's table replaces sg-1's once the products reading it have completed
+      int issued = 1;
+      for (; issued < nseg; ++issued) {
+        if (!mbar_wait_or_abort(smem_u32(&bar_afree), (uint32_t)(issued - 1) & 1u, abort)) {
+          fail();
+          break;
+        }
+        load_a(m0 + issued);
+      }
+      // the last table copy issued lands before the CTA frees its shared memory
+      mbar_wait(smem_u32(&bar_a), (uint32_t)(issued - 1) & 1u);
     }
   } else if (warp == 1) {
     if (lane == 0 && nt > 0) {
@@ -280,9 +297,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm_split(const __grid_cons
       // descriptors differ only in the start-address field (address >> 4, below 2^14 for
       // any shared-memory address), so each is a base plus a compile-time offset
       const uint64_t dA0 = smem_desc_sw128(sA);
-      bool ok = mbar_wait_or_abort(smem_u32(&bar_a), 0, abort);
+      bool ok = true;
       for (int q = 0; ok && q < nq; ++q) {
         const int t = q / kb, b = q - t * kb;
+        const int g = g0 + t, sg = g / tiles - m0;
+        // first chunk of a segment: its table has landed
+        if (b == 0 && (t == 0 || g % tiles == 0) && !mbar_wait_or_abort(smem_u32(&bar_a), (uint32_t)sg & 1u, abort)) {
+          ok = false;
+          break;
+        }
         const int st = q % S;
         const uint32_t ph = (uint32_t)(q / S) & 1u;
         const int acc_buf = t & 1;
@@ -307,6 +330,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm_split(const __grid_cons
         }
         umma_commit(smem_u32(&bar_empty[st]));
         if (b == kb - 1) umma_commit(smem_u32(&bar_tfull[acc_buf]));
+        // last chunk of a segment with another one after it: the table may be replaced
+        // once these products complete
+        if (b == kb - 1 && (g + 1) % tiles == 0 && sg + 1 < nseg) umma_commit(smem_u32(&bar_afree));
       }
       if (!ok) fail();
     }
@@ -314,7 +340,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm_split(const __grid_cons
     // ---- epilogue: warps 2..5
     const int quarter = warp & 3;
     const int row = quarter * 32 + lane;
-    float* Dm = prm.D + (size_t)m * prm.ncol * prm.M;
     for (int t = 0; t < nt; ++t) {
       const int acc_buf = t & 1;
       const uint32_t aph = (uint32_t)(t >> 1) & 1u;
@@ -325,8 +350,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm_split(const __grid_cons
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int n0 = (t0 + t) * BN;
-      float* dst = Dm + (size_t)n0 * prm.M + row;
+      const int g = g0 + t, m = g / tiles;
+      const int n0 = (g - m * tiles) * BN;
+      float* dst = prm.D + ((size_t)m * prm.ncol + n0) * prm.M + row;
       const bool full = n0 + BN <= prm.ncol;
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += 32) {
@@ -351,26 +377,33 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm_split(const __grid_cons
     // the float4 (row r = c / 16, k = 64 b + 4 (c mod 16) .. + 3), so a half-warp reads
     // one 256-byte row segment.
     const int ct = tid - 192;
-    const float* Bm = prm.B + (size_t)m * prm.ncol * prm.kstride;
+    // first panel row of tile t of the CTA's range (tiles of one m are consecutive rows)
+    auto tile_rows = [&](int t, int& n0) -> const float* {
+      const int g = g0 + t, m = g / tiles;
+      n0 = (g - m * tiles) * BN;
+      return prm.B + ((size_t)m * prm.ncol + n0) * prm.kstride;
+    };
     auto fetch = [&](int q, float4 (&v)[kConvPer]) {
       const int t = q / kb, b = q - t * kb;
-      const int n0 = (t0 + t) * BN;
+      int n0;
+      const float* Bt = tile_rows(t, n0);
 #pragma unroll
       for (int u = 0; u < kConvPer; ++u) {
         v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
         const int c = ct + kConvThreads * u;
         const int r = c >> 4, k = b * kKBlk + 4 * (c & 15);
         if (n0 + r < prm.ncol && k < prm.kstride)
-          v[u] = __ldg(reinterpret_cast<const float4*>(Bm + (size_t)(n0 + r) * prm.kstride + k));
+          v[u] = __ldg(reinterpret_cast<const float4*>(Bt + (size_t)r * prm.kstride + k));
       }
     };
     // one thread keeps the rows of the tiles two ahead on their way into L2 (a tile's
     // rows are contiguous), so the register loads of the next K block hit L2
     auto prefetch_tile = [&](int t) {
       if (ct != 0 || t >= nt) return;
-      const int n0 = (t0 + t) * BN;
+      int n0;
+      const float* Bt = tile_rows(t, n0);
       const int rows = min(BN, prm.ncol - n0);
-      prefetch_l2_bulk(Bm + (size_t)n0 * prm.kstride, (uint32_t)rows * (uint32_t)prm.kstride * 4u);
+      prefetch_l2_bulk(Bt, (uint32_t)rows * (uint32_t)prm.kstride * 4u);
     };
     prefetch_tile(0);
     prefetch_tile(1);

@@ -49,6 +49,7 @@ CASES = [
     (65, 31, 96, "rand", 0.1, 0),
     (130, 128, 24, "log", 0.0, 0),     # full M tile, ragged N tile
     (300, 96, 192, "log", 0.0, 0),     # radix-3 phi, partial second K block
+    (70, 16, 324, "rand", 0.0, 0),     # 163 m x 2 column tiles over one CTA per SM: table reloads mid-range
     (257, 64, 8, "uniform", 0.0, 1),
     (1600, 6, 4, "log", 0.0, 0),       # radial column beyond the shared-memory scan: ring-staged sweeps
     (4, 4, 1, "uniform", 0.0, 0),      # axisymmetric: one phi zone
