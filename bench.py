@@ -438,10 +438,7 @@ def run_served(S, W, torch, n_requests, rates=(200.0, 2000.0, 20000.0)):
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch from an ncu capture of the
 # named command (full workload), per kernel group; kept only while the kernel is unchanged
 NCU_TRAFFIC = {
-    "mixed": {
-        "residual": {"bytes": (291.32 + 59.17) * 1e6, "kernel": "k_residual_ff (interior rows)",
-                     "profile": "profiles/mixed_x6_550x128x256_kernels.md"},
-    },
+    "mixed": {},
 }
 
 
@@ -452,10 +449,11 @@ def algorithmic_bytes_per_step(p, precision, iters=2):
     solves: forward FFTs read rho (8 B) then r (4 B) and write the float32 panel (4 B);
     projections read and write 4 B per spectral value plus the NP bf16 table planes;
     radial solves read the spectrum and both float32 factor tables and write the panel;
-    inverse FFTs read the spectrum and write (then read and write) the float-float
-    iterate, a correction's also writing float64 Phi; the residual reads rho and the
-    iterate and writes r; without a correction a separate update reads the iterate and
-    writes float64 Phi."""
+    inverse FFTs read the spectrum and write the iterate: the first solve's as its high
+    word only (its low word is zero), a correction's reading it and writing both words
+    and float64 Phi; the residual reads rho and the iterate (the high word only after the
+    first solve) and writes r; without a correction a separate update reads the high
+    word and writes float64 Phi."""
     nr, nth, nphi = p.shape
     mh = nphi // 2 + 1
     Z = float(nr * nth * nphi)
@@ -471,9 +469,9 @@ def algorithmic_bytes_per_step(p, precision, iters=2):
             "project_forward": iters * (8 * S + T),
             "radial_solve": iters * (4 * S + 4 * S + 4 * S),
             "project_inverse": iters * (8 * S + T),
-            "fft_inverse": (4 * S + 8 * Z) + c * (4 * S + 24 * Z),   # corrections also write float64 Phi
-            "residual": c * 20 * Z,
-            "update": 16 * Z if c == 0 else 0.0}
+            "fft_inverse": (4 * S + 4 * Z) + min(c, 1) * (4 * S + 20 * Z) + max(c - 1, 0) * (4 * S + 24 * Z),
+            "residual": min(c, 1) * 16 * Z + max(c - 1, 0) * 20 * Z,
+            "update": 12 * Z if c == 0 else 0.0}
 
 
 def roofline(timing, p, precision, steps, iters=2):

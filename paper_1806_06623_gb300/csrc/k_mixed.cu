@@ -470,7 +470,8 @@ __device__ __forceinline__ void ffd_acc(float& ah, float& al, float ph, float pe
   al += e + pe;
 }
 
-// r = 4 pi G rho - (L Phi) for the float-float iterate Phi = hi + lo, evaluated in
+// r = 4 pi G rho - (L Phi) for the float-float iterate Phi = hi + lo (LO = false: the
+// iterate of a first solve, lo = 0 and not read), evaluated in
 // float-float arithmetic in difference form (every neighbour difference Phi_nb - Phi_c
 // is formed first, so products carry errors relative to the small differences, not to
 // |L||Phi|), stored as float32.  rho is split into a float pair with integer
@@ -483,6 +484,7 @@ __device__ __forceinline__ void ffd_acc(float& ah, float& al, float ph, float pe
 constexpr int kResRows = 16;
 constexpr int kResThreads = 256;
 
+template <bool LO>
 __global__ void __launch_bounds__(kResThreads) k_residual_ff(const double* __restrict__ rho,
                                                              const float* __restrict__ ph,
                                                              const float* __restrict__ pl,
@@ -515,35 +517,37 @@ __global__ void __launch_bounds__(kResThreads) k_residual_ff(const double* __res
   const double* rp = rho + c0 + k;
   float* op = r + c0 + k;
   const ThetaRowFF* angp = ang + (size_t)i0 * nth + j;
-  float ch = hp[0], cl = lp[0];
+  float ch = hp[0], cl = LO ? lp[0] : 0.f;
   float mh = 0.f, ml = 0.f;   // Phi(i-1) - Phi(i)
-  if (i0 > 0) ffd_diff(hp[-(ptrdiff_t)shell], lp[-(ptrdiff_t)shell], ch, cl, mh, ml);
+  if (i0 > 0) ffd_diff(hp[-(ptrdiff_t)shell], LO ? lp[-(ptrdiff_t)shell] : 0.f, ch, cl, mh, ml);
   for (int i = i0; i < i1; ++i) {
     float* bh = line[i & 1][0];
     float* bl = line[i & 1][1];
     if (act) {
       bh[t + 1] = ch;
-      bl[t + 1] = cl;
+      if (LO) bl[t + 1] = cl;
     }
     if (t == 0) {
       bh[0] = hrow[kl];
-      bl[0] = lrow[kl];
       bh[nk + 1] = hrow[kr];
-      bl[nk + 1] = lrow[kr];
+      if (LO) {
+        bl[0] = lrow[kl];
+        bl[nk + 1] = lrow[kr];
+      }
     }
     const bool has_ip = i < nr - 1;
     float nh = 0.f, nl = 0.f, jmh = 0.f, jml = 0.f, jph = 0.f, jpl = 0.f;
     if (has_ip) {
       nh = hp[shell];
-      nl = lp[shell];
+      if (LO) nl = lp[shell];
     }
     if (has_jm) {
       jmh = hp[-nphi];
-      jml = lp[-nphi];
+      if (LO) jml = lp[-nphi];
     }
     if (has_jp) {
       jph = hp[nphi];
-      jpl = lp[nphi];
+      if (LO) jpl = lp[nphi];
     }
     const double rv = *rp;
     const RadialRowFF rr = rad[i];
@@ -575,8 +579,8 @@ __global__ void __launch_bounds__(kResThreads) k_residual_ff(const double* __res
       ffd_acc(sh, sl, p, e);
     }
     float qh, ql;
-    ffd_diff(bh[t + 2], bl[t + 2], ch, cl, qh, ql);
-    ffd_diff(bh[t], bl[t], ch, cl, dh, dl);
+    ffd_diff(bh[t + 2], LO ? bl[t + 2] : 0.f, ch, cl, qh, ql);
+    ffd_diff(bh[t], LO ? bl[t] : 0.f, ch, cl, dh, dl);
     ffd_acc(qh, ql, dh, dl);
     ffd_mul(ar.sphi, qh, ql, p, e);
     ffd_acc(sh, sl, p, e);
@@ -606,19 +610,20 @@ __global__ void __launch_bounds__(kResThreads) k_residual_ff(const double* __res
   }
 }
 
-// float64 Phi = hi + lo
+// float64 Phi = hi + lo (pl null: lo = 0)
 __global__ void __launch_bounds__(256) k_finish(const float* __restrict__ ph, const float* __restrict__ pl,
                                                 double* __restrict__ phi, size_t n) {
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x)
-    phi[idx] = ff2d(ff{ph[idx], pl[idx]});
+    phi[idx] = ff2d(ff{ph[idx], pl ? pl[idx] : 0.f});
 }
 
-// The same for 16-byte aligned arrays, four values per thread and step.
+// The same for 16-byte aligned arrays (pl null or 16-byte aligned), four values per
+// thread and step.
 __global__ void __launch_bounds__(256) k_finish4(const float4* __restrict__ ph, const float4* __restrict__ pl,
                                                  double2* __restrict__ phi, size_t n4) {
   pdl_wait();
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n4; q += (size_t)gridDim.x * blockDim.x) {
-    const float4 h = __ldg(ph + q), l = __ldg(pl + q);
+    const float4 h = __ldg(ph + q), l = pl ? __ldg(pl + q) : make_float4(0.f, 0.f, 0.f, 0.f);
     phi[2 * q] = make_double2(ff2d(ff{h.x, l.x}), ff2d(ff{h.y, l.y}));
     phi[2 * q + 1] = make_double2(ff2d(ff{h.z, l.z}), ff2d(ff{h.w, l.w}));
   }
@@ -823,8 +828,9 @@ cudaError_t residual_ff(const Plan& p, const double* rho, cudaStream_t s) {
   const int tpb = p.nphi >= kResThreads ? kResThreads : ((p.nphi + 31) / 32) * 32;
   auto rows = [&](int r0, int r1, cudaStream_t st) {   // rows [r0, r1)
     const dim3 grid(p.nth, (r1 - r0 + kResRows - 1) / kResRows, (p.nphi + tpb - 1) / tpb);
-    const cudaError_t e = launch_pdl(k_residual_ff, grid, dim3(tpb), 0, st, rho, (const float*)x.phi_hi,
-                                     (const float*)x.phi_lo, (const double*)x.outer_shell, x.r32,
+    const cudaError_t e = launch_pdl(x.lo_zero ? k_residual_ff<false> : k_residual_ff<true>, grid, dim3(tpb), 0, st,
+                                     rho, (const float*)x.phi_hi, (const float*)x.phi_lo,
+                                     (const double*)x.outer_shell, x.r32,
                                      (const RadialRowFF*)x.radff, (const ThetaRowFF*)x.thff, p.nr, p.nth, p.nphi, r0,
                                      r1, p.outer_bc == SP_OUTER_DIRICHLET ? 1 : 0, x.dir_coef, x.four_pi_g);
     return e != cudaSuccess ? e : cudaGetLastError();
@@ -837,7 +843,8 @@ cudaError_t residual_ff(const Plan& p, const double* rho, cudaStream_t s) {
   if ((e = cudaEventRecord(p.ev_fork, s)) != cudaSuccess || (e = cudaStreamWaitEvent(p.side, p.ev_fork, 0)) != cudaSuccess)
     return e;
   const size_t off = (size_t)(p.nr - 1) * sh;
-  k_finish<<<(unsigned)((sh + 255) / 256), 256, 0, p.side>>>(x.phi_hi + off, x.phi_lo + off, x.shell_phi, sh);
+  k_finish<<<(unsigned)((sh + 255) / 256), 256, 0, p.side>>>(x.phi_hi + off, x.lo_zero ? nullptr : x.phi_lo + off,
+                                                              x.shell_phi, sh);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = fft_forward_f64(p, x.shell_phi, 1, 1.0 / p.nphi, p.shell, p.side)) != cudaSuccess) return e;
   if ((e = shell_kappa_f64(p, p.shell, p.shell2, p.side)) != cudaSuccess) return e;
@@ -851,20 +858,21 @@ cudaError_t residual_ff(const Plan& p, const double* rho, cudaStream_t s) {
 cudaError_t finish_mixed(const Plan& p, double* phi, cudaStream_t s) {
   const MixedTables& x = *p.mixed;
   const size_t n = (size_t)p.nr * p.nth * p.nphi;
+  const float* lo = x.lo_zero ? nullptr : x.phi_lo;   // a first solve's iterate: lo = 0, not stored
   const bool aligned = ((reinterpret_cast<uintptr_t>(phi) | reinterpret_cast<uintptr_t>(x.phi_hi) |
-                         reinterpret_cast<uintptr_t>(x.phi_lo)) & 15u) == 0 && (n & 3) == 0;
+                         reinterpret_cast<uintptr_t>(lo)) & 15u) == 0 && (n & 3) == 0;
   if (aligned) {
     size_t blocks = (n / 4 + 255) / 256;
     if (blocks > (size_t)p.num_sms * 8) blocks = (size_t)p.num_sms * 8;
     const cudaError_t e = launch_pdl(k_finish4, dim3((unsigned)blocks), dim3(256), 0, s,
-                                     reinterpret_cast<const float4*>(x.phi_hi), reinterpret_cast<const float4*>(x.phi_lo),
+                                     reinterpret_cast<const float4*>(x.phi_hi), reinterpret_cast<const float4*>(lo),
                                      reinterpret_cast<double2*>(phi), n / 4);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
   }
   size_t blocks = (n + 255) / 256;
   if (blocks > (size_t)p.num_sms * 16) blocks = (size_t)p.num_sms * 16;
-  k_finish<<<(unsigned)blocks, 256, 0, s>>>(x.phi_hi, x.phi_lo, phi, n);
+  k_finish<<<(unsigned)blocks, 256, 0, s>>>(x.phi_hi, lo, phi, n);
   return cudaGetLastError();
 }
 

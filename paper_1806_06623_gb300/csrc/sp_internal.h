@@ -81,6 +81,7 @@ struct MixedTables {
   float* r32 = nullptr;            // [nr][nth][nphi] residual
   float* phi_hi = nullptr;         // [nr][nth][nphi] iterate as float-float
   float* phi_lo = nullptr;
+  bool lo_zero = false;            // the iterate is a first solve's: its low word is zero and not stored
   float* panel = nullptr;          // spectral panel [mh][2nr][kstride] float32 (s_tilde, then f)
   float* d32 = nullptr;            // [mh][2nr][nth] projection output (s_hat, then g)
   float* fcp = nullptr;            // [mh][nr][nth] radial elimination factors c'_i (plan tables)
@@ -262,7 +263,7 @@ struct Planes {
 };
 cudaError_t fft_forward_panel(const Plan& p, const void* in, bool in_double, float scale, int kstride, float* out,
                               cudaStream_t s);
-cudaError_t fft_inverse_update(const Plan& p, const float* spec, float* phi_hi, float* phi_lo, bool first,
+cudaError_t fft_inverse_update(const Plan& p, const float* spec, float* phi_hi, float* phi_lo, bool first, bool lo_read,
                                unsigned int* red, double* phi64, cudaStream_t s);
 cudaError_t finish_mixed(const Plan& p, double* phi, cudaStream_t s);   // float-float iterate -> float64 Phi
 cudaError_t tc_project(const Plan& p, bool inverse, cudaStream_t s);   // pan -> d32

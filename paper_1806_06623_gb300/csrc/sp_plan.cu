@@ -169,8 +169,11 @@ int lp_solve(Plan* p, const void* in, bool in_double, float scale, double* phi, 
   if ((st = launch_status(sp::timed_launch(P, sp::kKThomas, s, [&] { return sp::thomas_mixed(P, s); })))) return st;
   if ((st = launch_status(sp::timed_launch(P, sp::kKGemmInv, s, [&] { return sp::tc_project(P, true, s); }))))
     return st;
-  return launch_status(sp::timed_launch(P, sp::kKFftInv, s, [&] {
-    return sp::fft_inverse_update(P, x.d32, x.phi_hi, x.phi_lo, first, x.red, phi, s); }));
+  const bool lo_read = !first && !x.lo_zero;
+  st = launch_status(sp::timed_launch(P, sp::kKFftInv, s, [&] {
+    return sp::fft_inverse_update(P, x.d32, x.phi_hi, x.phi_lo, first, lo_read, x.red, phi, s); }));
+  x.lo_zero = first;
+  return st;
 }
 
 }  // namespace
