@@ -407,11 +407,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm_split(const __grid_cons
     };
     prefetch_tile(0);
     prefetch_tile(1);
-    float4 cur[kConvPer], nxt[kConvPer];
+    // two K blocks in flight beyond the one being converted
+    float4 cur[kConvPer], nxt[kConvPer], nx2[kConvPer];
     if (nq > 0) fetch(0, cur);
+    if (nq > 1) fetch(1, nxt);
     for (int q = 0; q < nq; ++q) {
       if (q % kb == 0) prefetch_tile(q / kb + 2);
-      if (q + 1 < nq) fetch(q + 1, nxt);
+      if (q + 2 < nq) fetch(q + 2, nx2);
       const int st = q % S;
       const uint32_t ph = (uint32_t)(q / S) & 1u;
       if (q >= S && !mbar_wait_or_abort(smem_u32(&bar_empty[st]), ph ^ 1u, abort)) {
@@ -445,7 +447,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm_split(const __grid_cons
       fence_proxy_async_smem();
       mbar_arrive(smem_u32(&bar_full[st]));
 #pragma unroll
-      for (int u = 0; u < kConvPer; ++u) cur[u] = nxt[u];
+      for (int u = 0; u < kConvPer; ++u) {
+        cur[u] = nxt[u];
+        nxt[u] = nx2[u];
+      }
     }
   }
   // the last products complete before TMEM is freed
