@@ -451,9 +451,10 @@ def algorithmic_bytes_per_step(p, precision, iters=2):
     radial solves read the spectrum and both float32 factor tables and write the panel;
     inverse FFTs read the spectrum and write the iterate: the first solve's as its high
     word only (its low word is zero), a correction's reading it and writing both words
-    and float64 Phi; the residual reads rho and the iterate (the high word only after the
-    first solve) and writes r; without a correction a separate update reads the high
-    word and writes float64 Phi."""
+    and float64 Phi (the first correction with 6 products float64 Phi only); the residual
+    reads rho and the iterate (the high word only after the first solve) and writes r;
+    without a correction a separate update reads the high word and writes float64 Phi,
+    and with 6 products and a second correction one rebuilds both words from float64."""
     nr, nth, nphi = p.shape
     mh = nphi // 2 + 1
     Z = float(nr * nth * nphi)
@@ -469,9 +470,10 @@ def algorithmic_bytes_per_step(p, precision, iters=2):
             "project_forward": iters * (8 * S + T),
             "radial_solve": iters * (4 * S + 4 * S + 4 * S),
             "project_inverse": iters * (8 * S + T),
-            "fft_inverse": (4 * S + 4 * Z) + min(c, 1) * (4 * S + 20 * Z) + max(c - 1, 0) * (4 * S + 24 * Z),
+            "fft_inverse": (4 * S + 4 * Z) + min(c, 1) * (4 * S + (12 if npl == 3 else 20) * Z)
+                           + max(c - 1, 0) * (4 * S + 24 * Z),
             "residual": min(c, 1) * 16 * Z + max(c - 1, 0) * 20 * Z,
-            "update": 12 * Z if c == 0 else 0.0}
+            "update": 12 * Z if c == 0 else (16 * Z if npl == 3 and c >= 2 else 0.0)}
 
 
 def roofline(timing, p, precision, steps, iters=2):

@@ -377,12 +377,13 @@ enum InvOut { kInvWrite = 0, kInvAccumulate = 1, kInvPairUpdate = 2 };
 //    the stored iterate's low word is zero), with max|e| and max|hi| reduced into red[0], red[1]
 //    (non-negative float bit patterns, so integer max orders them); with phi64 given,
 //    the updated iterate is also written as float64 (the solve's output when this
-//    correction turns out to be the last).
+//    correction turns out to be the last), and with hilo = 0 only there (out and phi_lo
+//    are then left as they were).
 template <typename T, typename Tout, int MODE>
 __global__ void __launch_bounds__(256, 3) k_fft_inv(const T* __restrict__ spec, int nlines, int nth, int nrs,
                                                  FftSchedule sch, const T* __restrict__ twid, int lpc,
                                                  Tout* __restrict__ out, float* __restrict__ phi_lo, int first,
-                                                 int lo_read, unsigned int* __restrict__ red, int ahead,
+                                                 int lo_read, int hilo, unsigned int* __restrict__ red, int ahead,
                                                  double* __restrict__ phi64) {
   using CT = typename C2<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -508,8 +509,10 @@ __global__ void __launch_bounds__(256, 3) k_fft_inv(const T* __restrict__ spec, 
                 me = fmaxf(me, fabsf(e));
                 mp = fmaxf(mp, fabsf(nv.hi));
               }
-              *reinterpret_cast<float4*>(out + o) = make_float4(nh[0], nh[1], nh[2], nh[3]);
-              if (!first) *reinterpret_cast<float4*>(phi_lo + o) = make_float4(nl[0], nl[1], nl[2], nl[3]);
+              if (hilo) {
+                *reinterpret_cast<float4*>(out + o) = make_float4(nh[0], nh[1], nh[2], nh[3]);
+                if (!first) *reinterpret_cast<float4*>(phi_lo + o) = make_float4(nl[0], nl[1], nl[2], nl[3]);
+              }
               if (phi64) {
                 reinterpret_cast<double2*>(phi64 + o)[0] = make_double2(ff2d(ff{nh[0], nl[0]}), ff2d(ff{nh[1], nl[1]}));
                 reinterpret_cast<double2*>(phi64 + o)[1] = make_double2(ff2d(ff{nh[2], nl[2]}), ff2d(ff{nh[3], nl[3]}));
@@ -542,8 +545,10 @@ __global__ void __launch_bounds__(256, 3) k_fft_inv(const T* __restrict__ spec, 
             const size_t o = o0 + (size_t)h * n + q;
             const float e = (float)(h ? v.y : v.x);
             const ff nv = first ? ff{e, 0.f} : ff_add_f(ff{oh[h][u], ol[h][u]}, e);
-            out[o] = (Tout)nv.hi;
-            if (!first) phi_lo[o] = nv.lo;
+            if (hilo) {
+              out[o] = (Tout)nv.hi;
+              if (!first) phi_lo[o] = nv.lo;
+            }
             if (phi64) phi64[o] = ff2d(nv);
             me = fmaxf(me, fabsf(e));
             mp = fmaxf(mp, fabsf(nv.hi));
@@ -627,13 +632,13 @@ cudaError_t fft_inverse_f64(const Plan& p, const double* spec, int nrs, double* 
   if (accumulate) {
     auto kern = k_fft_inv<double, double, kInvAccumulate>;
     if ((e = prep(kern, smem)) != cudaSuccess) return e;
-    kern<<<grid, 32 * kWarps, smem, s>>>(spec, nlines, p.nth, nrs, p.sched, p.d_twid, lpc, out, nullptr, 0, 0, nullptr, 0,
-                                         nullptr);
+    kern<<<grid, 32 * kWarps, smem, s>>>(spec, nlines, p.nth, nrs, p.sched, p.d_twid, lpc, out, nullptr, 0, 0, 1, nullptr,
+                                         0, nullptr);
   } else {
     auto kern = k_fft_inv<double, double, kInvWrite>;
     if ((e = prep(kern, smem)) != cudaSuccess) return e;
-    kern<<<grid, 32 * kWarps, smem, s>>>(spec, nlines, p.nth, nrs, p.sched, p.d_twid, lpc, out, nullptr, 0, 0, nullptr, 0,
-                                         nullptr);
+    kern<<<grid, 32 * kWarps, smem, s>>>(spec, nlines, p.nth, nrs, p.sched, p.d_twid, lpc, out, nullptr, 0, 0, 1, nullptr,
+                                         0, nullptr);
   }
   return cudaGetLastError();
 }
@@ -662,7 +667,7 @@ cudaError_t fft_forward_panel(const Plan& p, const void* in, bool in_double, flo
 }
 
 cudaError_t fft_inverse_update(const Plan& p, const float* spec, float* phi_hi, float* phi_lo, bool first, bool lo_read,
-                               unsigned int* red, double* phi64, cudaStream_t s) {
+                               bool f64_only, unsigned int* red, double* phi64, cudaStream_t s) {
   const int nlines = p.nr * p.nth;
   const int lpc = lines_per_cta<float>(p.nphi, nlines);
   const size_t smem = fft_smem<float>(p.nphi, lpc);
@@ -671,8 +676,8 @@ cudaError_t fft_inverse_update(const Plan& p, const float* spec, float* phi_hi, 
   if (e != cudaSuccess) return e;
   // (prefetching the iterate a wave ahead measured slower here: ahead = 0)
   e = launch_pdl(kern, dim3((nlines + lpc - 1) / lpc), dim3(32 * kWarps), smem, s, spec, nlines, p.nth, p.nr, p.sched,
-                 (const float*)p.d_twid32, lpc, phi_hi, phi_lo, first ? 1 : 0, lo_read ? 1 : 0, red, 0,
-                 first ? nullptr : phi64);
+                 (const float*)p.d_twid32, lpc, phi_hi, phi_lo, first ? 1 : 0, lo_read ? 1 : 0,
+                 (f64_only && !first && phi64) ? 0 : 1, red, 0, first ? nullptr : phi64);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 

@@ -617,6 +617,17 @@ __global__ void __launch_bounds__(256) k_finish(const float* __restrict__ ph, co
     phi[idx] = ff2d(ff{ph[idx], pl ? pl[idx] : 0.f});
 }
 
+// float64 iterate -> float-float (hi, lo): the inverse of k_finish up to 2^-48 relative.
+__global__ void __launch_bounds__(256) k_split64(const double* __restrict__ phi, float* __restrict__ ph,
+                                                 float* __restrict__ pl, size_t n) {
+  pdl_wait();
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
+    const ff v = d2ff(phi[idx]);
+    ph[idx] = v.hi;
+    pl[idx] = v.lo;
+  }
+}
+
 // The same for 16-byte aligned arrays (pl null or 16-byte aligned), four values per
 // thread and step.
 __global__ void __launch_bounds__(256) k_finish4(const float4* __restrict__ ph, const float4* __restrict__ pl,
@@ -853,6 +864,15 @@ cudaError_t residual_ff(const Plan& p, const double* rho, cudaStream_t s) {
   if (p.nr > 1 && (e = rows(0, p.nr - 1, s)) != cudaSuccess) return e;
   if ((e = cudaStreamWaitEvent(s, p.ev_join, 0)) != cudaSuccess) return e;
   return rows(p.nr - 1, p.nr, s);
+}
+
+cudaError_t split_iterate(const Plan& p, const double* phi, cudaStream_t s) {
+  const MixedTables& x = *p.mixed;
+  const size_t n = (size_t)p.nr * p.nth * p.nphi;
+  size_t blocks = (n + 255) / 256;
+  if (blocks > (size_t)p.num_sms * 16) blocks = (size_t)p.num_sms * 16;
+  const cudaError_t e = launch_pdl(k_split64, dim3((unsigned)blocks), dim3(256), 0, s, phi, x.phi_hi, x.phi_lo, n);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t finish_mixed(const Plan& p, double* phi, cudaStream_t s) {

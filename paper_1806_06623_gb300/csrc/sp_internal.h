@@ -82,6 +82,7 @@ struct MixedTables {
   float* phi_hi = nullptr;         // [nr][nth][nphi] iterate as float-float
   float* phi_lo = nullptr;
   bool lo_zero = false;            // the iterate is a first solve's: its low word is zero and not stored
+  const double* iter64 = nullptr;  // non-null: the iterate is stored only there, in float64 (hi, lo stale)
   float* panel = nullptr;          // spectral panel [mh][2nr][kstride] float32 (s_tilde, then f)
   float* d32 = nullptr;            // [mh][2nr][nth] projection output (s_hat, then g)
   float* fcp = nullptr;            // [mh][nr][nth] radial elimination factors c'_i (plan tables)
@@ -264,8 +265,10 @@ struct Planes {
 cudaError_t fft_forward_panel(const Plan& p, const void* in, bool in_double, float scale, int kstride, float* out,
                               cudaStream_t s);
 cudaError_t fft_inverse_update(const Plan& p, const float* spec, float* phi_hi, float* phi_lo, bool first, bool lo_read,
-                               unsigned int* red, double* phi64, cudaStream_t s);
+                               bool f64_only, unsigned int* red, double* phi64, cudaStream_t s);
 cudaError_t finish_mixed(const Plan& p, double* phi, cudaStream_t s);   // float-float iterate -> float64 Phi
+cudaError_t split_iterate(const Plan& p, const double* phi, cudaStream_t s);   // float64 iterate -> hi, lo
+bool first_correction_f64_only(const Plan& p);   // the first correction stores the iterate in float64 only
 cudaError_t tc_project(const Plan& p, bool inverse, cudaStream_t s);   // pan -> d32
 cudaError_t thomas_mixed(const Plan& p, cudaStream_t s);   // d32 -> pan (f); float32 + float64 low modes
 cudaError_t residual_ff(const Plan& p, const double* rho, cudaStream_t s);  // iterate -> r32

@@ -170,9 +170,11 @@ int lp_solve(Plan* p, const void* in, bool in_double, float scale, double* phi, 
   if ((st = launch_status(sp::timed_launch(P, sp::kKGemmInv, s, [&] { return sp::tc_project(P, true, s); }))))
     return st;
   const bool lo_read = !first && !x.lo_zero;
+  const bool f64_only = !first && phi && x.lo_zero && sp::first_correction_f64_only(P);
   st = launch_status(sp::timed_launch(P, sp::kKFftInv, s, [&] {
-    return sp::fft_inverse_update(P, x.d32, x.phi_hi, x.phi_lo, first, lo_read, x.red, phi, s); }));
+    return sp::fft_inverse_update(P, x.d32, x.phi_hi, x.phi_lo, first, lo_read, f64_only, x.red, phi, s); }));
   x.lo_zero = first;
+  x.iter64 = f64_only ? phi : nullptr;
   return st;
 }
 
@@ -187,11 +189,21 @@ int mixed_start(Plan* p, const double* rho, cudaStream_t s) {
   return lp_solve(p, rho, true, (float)(4.0 * kPi * p->G / p->nphi), nullptr, true, s);
 }
 
+// Whether the first correction stores the updated iterate only as the float64 output:
+// with 6 products it is normally the last one, so the float-float words it would write
+// are rebuilt from float64 (split_iterate) only when another correction follows.
+bool first_correction_f64_only(const Plan& p) { return p.mixed->np == 3; }
+
 // One correction: float-float residual, then the low-precision solve of L e = r
 // (asynchronous); its inverse FFT also writes the updated iterate to phi in float64.
 int mixed_correct(Plan* p, const double* rho, double* phi, cudaStream_t s) {
   Plan& P = *p;
   int st;
+  if (P.mixed->iter64) {   // the iterate lives in float64 only: rebuild its float-float words
+    if ((st = launch_status(timed_launch(P, kKUpdate, s, [&] { return split_iterate(P, P.mixed->iter64, s); }))))
+      return st;
+    P.mixed->iter64 = nullptr;
+  }
   if ((st = launch_status(timed_launch(P, kKResidual, s, [&] { return residual_ff(P, rho, s); })))) return st;
   if (P.outer_bc == SP_OUTER_MULTIPOLE) P.launches += 5;   // shell: finish, FFT, apply, inverse FFT; split residual
   SP_CUDA(cudaMemsetAsync(P.mixed->red, 0, 2 * sizeof(unsigned int), s));
@@ -278,10 +290,13 @@ int mixed_phase_a(Plan* p, const double* rho, double* phi, cudaStream_t s, Mixed
     if (!capture_phase_a(p, rho, phi)) return phase_a_direct(p, rho, phi, s, R);
   }
   SP_CUDA(cudaGraphLaunch(p->ga_exec, s));
-  // host bookkeeping of what the graph did: its reductions sit in the first host slots
+  // host bookkeeping of what the graph did: its reductions sit in the first host slots,
+  // and the iterate is in the state its one correction leaves
   R.pending = p->ga_pending;
   R.next_slot = p->ga_pending & 1;
   p->phi64_written = p->max_iter >= 1 ? phi : nullptr;
+  p->mixed->lo_zero = false;
+  p->mixed->iter64 = first_correction_f64_only(*p) ? phi : nullptr;
   p->launches += p->ga_launches;
   return SP_OK;
 }

@@ -155,3 +155,26 @@ def test_mixed_equals_fp64_plan_within_tolerance(S):
     plan = S.Plan(p.r_if, p.th_if, p.nphi)
     phi_d, _ = plan.solve(torch.from_numpy(p.rho).cuda())
     assert rel_err(phi_m, phi_d.cpu().numpy()) <= 2 * TOL
+
+
+def test_mixed_x6_second_correction_rebuilds_iterate(S):
+    """With 6 products the first correction stores the iterate in float64 only; a tighter
+    tolerance that needs a second correction rebuilds its float-float words from there.
+    Checked against the exact solution, and bitwise between launch-by-launch solves and
+    graph-replayed ones (the replay restores the iterate's state on the host)."""
+    p = W.random_small(24, 12, 16, seed=21, grid="log")
+    ref = O.solve_exact(O.Geometry(p.r_if, p.th_if, p.nphi), p.rho)
+    rho = torch.from_numpy(np.ascontiguousarray(p.rho)).cuda()
+    direct = S.Plan(p.r_if, p.th_if, p.nphi, precision=S.SP_MIXED_BF16X6, tol=1e-12, max_iter=8)
+    direct.set_graphs(False)
+    phi_d, info_d = direct.solve(rho)
+    torch.cuda.synchronize()
+    assert info_d.status == S.SP_OK and info_d.iterations >= 3, info_d.as_dict()
+    assert rel_err(phi_d.cpu().numpy(), ref) <= 1e-12
+    plan = S.Plan(p.r_if, p.th_if, p.nphi, precision=S.SP_MIXED_BF16X6, tol=1e-12, max_iter=8)
+    out = torch.empty_like(rho)
+    for k in range(4):                 # direct, capture + replay, replay, replay
+        _, info = plan.solve(rho, out)
+        torch.cuda.synchronize()
+        assert torch.equal(out, phi_d), k
+        assert info.iterations == info_d.iterations
