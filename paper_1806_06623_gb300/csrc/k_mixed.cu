@@ -470,16 +470,98 @@ __device__ __forceinline__ void ffd_acc(float& ah, float& al, float ph, float pe
   al += e + pe;
 }
 
-// r = 4 pi G rho - (L Phi) for the float-float iterate Phi = hi + lo (LO = false: the
-// iterate of a first solve, lo = 0 and not read), evaluated in
-// float-float arithmetic in difference form (every neighbour difference Phi_nb - Phi_c
-// is formed first, so products carry errors relative to the small differences, not to
-// |L||Phi|), stored as float32.  rho is split into a float pair with integer
-// operations; the multipole term of the last shell arrives precomputed in outer_shell
-// (float64, already scaled by 3 r_out^2/dV3_N).
-// One CTA per (j, chunk of kResRows radial rows, block of phi columns); each thread
-// marches outward along its (j, k) column with the radial window in registers, so the
-// difference across face i+1/2 serves as the inner difference of row i+1 (negated,
+// Neighbour difference b - c of float-float values; with LO = false both low words are
+// zero and the difference is the error-free two-sum of the high words.
+template <bool LO>
+__device__ __forceinline__ void ffd_diff_lo(float bh, float bl, float ch, float cl, float& dh, float& dl) {
+  if (LO) ffd_diff(bh, bl, ch, cl, dh, dl);
+  else two_sum(bh, -ch, dh, dl);
+}
+
+// Float pair of a float64 source value with integer operations: hi is x truncated to 24
+// significant bits, lo the remaining 29 bits rounded to float (scaled by two exact powers
+// of two), so |hi + lo - x| <= 2^-24 |lo| < 2^-47 |x| for 2^-126 <= |x| < 2^128; smaller
+// magnitudes give (0, 0), larger ones an infinite hi.
+__device__ __forceinline__ ff d2ff_trunc(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned int whi = (unsigned int)(b >> 32), wlo = (unsigned int)b;
+  const unsigned int sgn = whi & 0x80000000u;
+  const int e = (int)((whi >> 20) & 0x7FFu);
+  if (e < 897) return ff{0.f, 0.f};
+  if (e > 1150) return ff{__uint_as_float(sgn | 0x7F800000u), 0.f};
+  // bits 60..29 of x hold the low 9 exponent bits and the top 23 fraction bits; adding
+  // 2^30 (= -384 x 2^23 modulo 2^32) moves the exponent bias from 1023 to 127
+  const float hi = __uint_as_float((__funnelshift_l(wlo, whi, 3) + 0x40000000u) | sgn);
+  const int sc = e - 1075, s1 = sc >> 1, s2 = sc - s1;   // the remainder's unit is 2^(e-1075)
+  const float lo = (float)(wlo & 0x1FFFFFFFu) * __uint_as_float(((unsigned int)(s1 + 127) << 23) | sgn) *
+                   __uint_as_float((unsigned int)(s2 + 127) << 23);
+  return ff{hi, lo};
+}
+
+// r = 4 pi G rho - (L Phi) of one zone for the float-float iterate Phi = hi + lo,
+// evaluated in float-float arithmetic in difference form (every neighbour difference
+// Phi_nb - Phi_c is formed first, so products carry errors relative to the small
+// differences, not to |L||Phi|) and returned as float32.  (mh, ml) = Phi(i-1) - Phi(i)
+// on entry (read when i > 0) and Phi(i) - Phi(i+1) on exit (when i < Nr-1); (qh, ql) is
+// the phi second difference (Phi_k+1 - Phi_k) + (Phi_k-1 - Phi_k); (oh, ol) the outer
+// boundary term of the last shell (multipole or Dirichlet), added when i = Nr-1.
+template <bool LO>
+__device__ __forceinline__ float residual_zone(float ch, float cl, float& mh, float& ml, bool has_im, bool has_ip,
+                                               float nh, float nl, bool has_jm, float jmh, float jml, bool has_jp,
+                                               float jph, float jpl, float qh, float ql, float oh, float ol,
+                                               const RadialRowFF& rr, const ThetaRowFF& ar, double rv,
+                                               const ff& four_pi_g) {
+  float dh, dl, p, e;
+  float sh = 0.f, sl = 0.f;   // L Phi as one unnormalised float-float sum
+  if (has_im) {
+    ffd_mul(rr.sub, mh, ml, p, e);
+    sh = p;
+    sl = e;
+  }
+  if (has_ip) {
+    ffd_diff_lo<LO>(nh, nl, ch, cl, dh, dl);
+    ffd_mul(rr.sup, dh, dl, p, e);
+    ffd_acc(sh, sl, p, e);
+    mh = -dh;
+    ml = -dl;
+  }
+  if (has_jm) {
+    ffd_diff_lo<LO>(jmh, jml, ch, cl, dh, dl);
+    ffd_mul(ar.tm, dh, dl, p, e);
+    ffd_acc(sh, sl, p, e);
+  }
+  if (has_jp) {
+    ffd_diff_lo<LO>(jph, jpl, ch, cl, dh, dl);
+    ffd_mul(ar.tp, dh, dl, p, e);
+    ffd_acc(sh, sl, p, e);
+  }
+  ffd_mul(ar.sphi, qh, ql, p, e);
+  ffd_acc(sh, sl, p, e);
+  if (!has_ip) ffd_acc(sh, sl, oh, ol);
+  const ff sv = ff_mul(four_pi_g, d2ff_trunc(rv));
+  float th_, tl;
+  two_sum(sv.hi, -sh, th_, tl);
+  tl += sv.lo - sl;
+  return th_ + tl;
+}
+
+// Outer boundary term of zone (Nr-1, j, k): Dirichlet coefficient x Phi, or the
+// precomputed multipole term (float64, already scaled by 3 r_out^2/dV3_N).
+__device__ __forceinline__ void outer_term(int dirichlet, const ff& dir_coef, float ch, float cl,
+                                           const double* outer_shell, size_t idx, float& oh, float& ol) {
+  if (dirichlet) {
+    ffd_mul(dir_coef, ch, cl, oh, ol);
+  } else {
+    const ff o = d2ff(outer_shell[idx]);
+    oh = o.hi;
+    ol = o.lo;
+  }
+}
+
+// The residual (LO = false: the iterate of a first solve, lo = 0 and not read), stored as
+// float32.  One CTA per (j, chunk of kResRows radial rows, block of phi columns); each
+// thread marches outward along its (j, k) column with the radial window in registers, so
+// the difference across face i+1/2 serves as the inner difference of row i+1 (negated,
 // exactly), and the phi neighbours come from the row's line staged in shared memory.
 constexpr int kResRows = 16;
 constexpr int kResThreads = 256;
@@ -519,7 +601,7 @@ __global__ void __launch_bounds__(kResThreads) k_residual_ff(const double* __res
   const ThetaRowFF* angp = ang + (size_t)i0 * nth + j;
   float ch = hp[0], cl = LO ? lp[0] : 0.f;
   float mh = 0.f, ml = 0.f;   // Phi(i-1) - Phi(i)
-  if (i0 > 0) ffd_diff(hp[-(ptrdiff_t)shell], LO ? lp[-(ptrdiff_t)shell] : 0.f, ch, cl, mh, ml);
+  if (i0 > 0) ffd_diff_lo<LO>(hp[-(ptrdiff_t)shell], LO ? lp[-(ptrdiff_t)shell] : 0.f, ch, cl, mh, ml);
   for (int i = i0; i < i1; ++i) {
     float* bh = line[i & 1][0];
     float* bl = line[i & 1][1];
@@ -553,51 +635,15 @@ __global__ void __launch_bounds__(kResThreads) k_residual_ff(const double* __res
     const RadialRowFF rr = rad[i];
     const ThetaRowFF ar = *angp;   // R_i x (t_j+1/2, t_j-1/2, S_j lambda-free phi coefficient)
     __syncthreads();
-    float dh, dl, p, e;
-    // L Phi as one unnormalised float-float sum of coefficient x difference terms
-    float sh = 0.f, sl = 0.f;
-    if (i > 0) {
-      ffd_mul(rr.sub, mh, ml, p, e);
-      sh = p;
-      sl = e;
-    }
-    if (has_ip) {
-      ffd_diff(nh, nl, ch, cl, dh, dl);
-      ffd_mul(rr.sup, dh, dl, p, e);
-      ffd_acc(sh, sl, p, e);
-      mh = -dh;
-      ml = -dl;
-    }
-    if (has_jm) {
-      ffd_diff(jmh, jml, ch, cl, dh, dl);
-      ffd_mul(ar.tm, dh, dl, p, e);
-      ffd_acc(sh, sl, p, e);
-    }
-    if (has_jp) {
-      ffd_diff(jph, jpl, ch, cl, dh, dl);
-      ffd_mul(ar.tp, dh, dl, p, e);
-      ffd_acc(sh, sl, p, e);
-    }
-    float qh, ql;
-    ffd_diff(bh[t + 2], LO ? bl[t + 2] : 0.f, ch, cl, qh, ql);
-    ffd_diff(bh[t], LO ? bl[t] : 0.f, ch, cl, dh, dl);
+    float qh, ql, dh, dl;
+    ffd_diff_lo<LO>(bh[t + 2], LO ? bl[t + 2] : 0.f, ch, cl, qh, ql);
+    ffd_diff_lo<LO>(bh[t], LO ? bl[t] : 0.f, ch, cl, dh, dl);
     ffd_acc(qh, ql, dh, dl);
-    ffd_mul(ar.sphi, qh, ql, p, e);
-    ffd_acc(sh, sl, p, e);
-    if (!has_ip) {
-      if (dirichlet) {
-        ffd_mul(dir_coef, ch, cl, p, e);
-        ffd_acc(sh, sl, p, e);
-      } else {
-        const ff o = d2ff(outer_shell[(size_t)j * nphi + k]);
-        ffd_acc(sh, sl, o.hi, o.lo);
-      }
-    }
-    const ff sv = ff_mul(four_pi_g, d2ff(rv));
-    float th_, tl;
-    two_sum(sv.hi, -sh, th_, tl);
-    tl += sv.lo - sl;
-    if (act) *op = th_ + tl;
+    float oh = 0.f, ol = 0.f;
+    if (!has_ip) outer_term(dirichlet, dir_coef, ch, cl, outer_shell, (size_t)j * nphi + k, oh, ol);
+    const float res = residual_zone<LO>(ch, cl, mh, ml, i > 0, has_ip, nh, nl, has_jm, jmh, jml, has_jp, jph, jpl, qh,
+                                        ql, oh, ol, rr, ar, rv, four_pi_g);
+    if (act) *op = res;
     ch = nh;
     cl = nl;
     hrow += shell;
@@ -606,6 +652,122 @@ __global__ void __launch_bounds__(kResThreads) k_residual_ff(const double* __res
     lp += shell;
     rp += shell;
     op += shell;
+    angp += nth;
+  }
+}
+
+// The same for an even number of phi zones, two adjacent columns (k, k+1) per thread:
+// 8- and 16-byte accesses, the per-row work done once per pair, and the phi face between
+// the pair's columns differenced once for both.  rho must be 16-byte aligned.
+template <bool LO>
+__global__ void __launch_bounds__(kResThreads) k_residual_ff2(const double* __restrict__ rho,
+                                                              const float* __restrict__ ph,
+                                                              const float* __restrict__ pl,
+                                                              const double* __restrict__ outer_shell,
+                                                              float* __restrict__ r,
+                                                              const RadialRowFF* __restrict__ rad,
+                                                              const ThetaRowFF* __restrict__ ang, int nr, int nth,
+                                                              int nphi, int row_begin, int row_end, int dirichlet,
+                                                              ff dir_coef, ff four_pi_g) {
+  // [row parity][hi, lo][even, odd column of the pair][pair - p0 + 1]
+  __shared__ float line[2][2][2][kResThreads + 2];
+  pdl_trigger();
+  pdl_wait();
+  const int j = blockIdx.x;
+  const int i0 = row_begin + (int)blockIdx.y * kResRows, i1 = min(row_end, i0 + kResRows);
+  const int t = threadIdx.x;
+  const int np2 = nphi >> 1;                          // column pairs per line
+  const int p0 = blockIdx.z * blockDim.x;             // first pair of this CTA
+  const int nk = min((int)blockDim.x, np2 - p0);      // pairs of this CTA
+  const bool act = t < nk;
+  const int k = 2 * (p0 + (act ? t : nk - 1));        // even column of the pair
+  const int kl = p0 == 0 ? nphi - 1 : 2 * p0 - 1;     // periodic halo columns (odd, even)
+  const int kr = p0 + nk == np2 ? 0 : 2 * (p0 + nk);
+  const size_t shell = (size_t)nth * nphi;
+  const size_t sh2 = shell >> 1;                      // strides in pairs
+  const ptrdiff_t nph2 = np2;
+  const bool has_jm = j > 0, has_jp = j < nth - 1;
+  const size_t c0 = (size_t)i0 * shell + (size_t)j * nphi;
+  const float* hrow = ph + c0;
+  const float* lrow = pl + c0;
+  const float2* hp = reinterpret_cast<const float2*>(hrow + k);
+  const float2* lp = reinterpret_cast<const float2*>(lrow + k);
+  const double2* rp = reinterpret_cast<const double2*>(rho + c0 + k);
+  float2* op = reinterpret_cast<float2*>(r + c0 + k);
+  const ThetaRowFF* angp = ang + (size_t)i0 * nth + j;
+  const float2 z2 = make_float2(0.f, 0.f);
+  float2 ch = hp[0], cl = LO ? lp[0] : z2;
+  float mxh = 0.f, mxl = 0.f, myh = 0.f, myl = 0.f;   // Phi(i-1) - Phi(i) of both columns
+  if (i0 > 0) {
+    const float2 bh = hp[-(ptrdiff_t)sh2], bl = LO ? lp[-(ptrdiff_t)sh2] : z2;
+    ffd_diff_lo<LO>(bh.x, bl.x, ch.x, cl.x, mxh, mxl);
+    ffd_diff_lo<LO>(bh.y, bl.y, ch.y, cl.y, myh, myl);
+  }
+  for (int i = i0; i < i1; ++i) {
+    float* ev = line[i & 1][0][0];   // high words of the even and odd columns
+    float* od = line[i & 1][0][1];
+    float* evl = line[i & 1][1][0];
+    float* odl = line[i & 1][1][1];
+    if (act) {
+      ev[t + 1] = ch.x;
+      od[t + 1] = ch.y;
+      if (LO) {
+        evl[t + 1] = cl.x;
+        odl[t + 1] = cl.y;
+      }
+    }
+    if (t == 0) {
+      od[0] = hrow[kl];
+      ev[nk + 1] = hrow[kr];
+      if (LO) {
+        odl[0] = lrow[kl];
+        evl[nk + 1] = lrow[kr];
+      }
+    }
+    const bool has_ip = i < nr - 1;
+    float2 nh = z2, nl = z2, jmh = z2, jml = z2, jph = z2, jpl = z2;
+    if (has_ip) {
+      nh = hp[sh2];
+      if (LO) nl = lp[sh2];
+    }
+    if (has_jm) {
+      jmh = hp[-nph2];
+      if (LO) jml = lp[-nph2];
+    }
+    if (has_jp) {
+      jph = hp[nph2];
+      if (LO) jpl = lp[nph2];
+    }
+    const double2 rv = *rp;
+    const RadialRowFF rr = rad[i];
+    const ThetaRowFF ar = *angp;
+    __syncthreads();
+    // phi second differences: the face between the pair's columns once for both
+    float dmh, dml, qxh, qxl, qyh, qyl;
+    ffd_diff_lo<LO>(ch.y, cl.y, ch.x, cl.x, dmh, dml);                      // Phi(k+1) - Phi(k)
+    ffd_diff_lo<LO>(od[t], LO ? odl[t] : 0.f, ch.x, cl.x, qxh, qxl);         // Phi(k-1) - Phi(k)
+    ffd_acc(qxh, qxl, dmh, dml);
+    ffd_diff_lo<LO>(ev[t + 2], LO ? evl[t + 2] : 0.f, ch.y, cl.y, qyh, qyl); // Phi(k+2) - Phi(k+1)
+    ffd_acc(qyh, qyl, -dmh, -dml);
+    float oxh = 0.f, oxl = 0.f, oyh = 0.f, oyl = 0.f;
+    if (!has_ip) {
+      outer_term(dirichlet, dir_coef, ch.x, cl.x, outer_shell, (size_t)j * nphi + k, oxh, oxl);
+      outer_term(dirichlet, dir_coef, ch.y, cl.y, outer_shell, (size_t)j * nphi + k + 1, oyh, oyl);
+    }
+    float2 res;
+    res.x = residual_zone<LO>(ch.x, cl.x, mxh, mxl, i > 0, has_ip, nh.x, nl.x, has_jm, jmh.x, jml.x, has_jp, jph.x,
+                              jpl.x, qxh, qxl, oxh, oxl, rr, ar, rv.x, four_pi_g);
+    res.y = residual_zone<LO>(ch.y, cl.y, myh, myl, i > 0, has_ip, nh.y, nl.y, has_jm, jmh.y, jml.y, has_jp, jph.y,
+                              jpl.y, qyh, qyl, oyh, oyl, rr, ar, rv.y, four_pi_g);
+    if (act) *op = res;
+    ch = nh;
+    cl = nl;
+    hrow += shell;
+    lrow += shell;
+    hp += sh2;
+    lp += sh2;
+    rp += sh2;
+    op += sh2;
     angp += nth;
   }
 }
@@ -836,12 +998,16 @@ int create_side_stream(Plan& p) {
 cudaError_t residual_ff(const Plan& p, const double* rho, cudaStream_t s) {
   const MixedTables& x = *p.mixed;
   const size_t sh = (size_t)p.nth * p.nphi;
-  const int tpb = p.nphi >= kResThreads ? kResThreads : ((p.nphi + 31) / 32) * 32;
+  // column pairs per thread when Nphi is even and rho allows 16-byte loads
+  const bool pairs = (p.nphi & 1) == 0 && (reinterpret_cast<uintptr_t>(rho) & 15u) == 0;
+  const int ncols = pairs ? p.nphi / 2 : p.nphi;
+  const int tpb = ncols >= kResThreads ? kResThreads : ((ncols + 31) / 32) * 32;
   auto rows = [&](int r0, int r1, cudaStream_t st) {   // rows [r0, r1)
-    const dim3 grid(p.nth, (r1 - r0 + kResRows - 1) / kResRows, (p.nphi + tpb - 1) / tpb);
-    const cudaError_t e = launch_pdl(x.lo_zero ? k_residual_ff<false> : k_residual_ff<true>, grid, dim3(tpb), 0, st,
-                                     rho, (const float*)x.phi_hi, (const float*)x.phi_lo,
-                                     (const double*)x.outer_shell, x.r32,
+    const dim3 grid(p.nth, (r1 - r0 + kResRows - 1) / kResRows, (ncols + tpb - 1) / tpb);
+    auto kern = pairs ? (x.lo_zero ? k_residual_ff2<false> : k_residual_ff2<true>)
+                      : (x.lo_zero ? k_residual_ff<false> : k_residual_ff<true>);
+    const cudaError_t e = launch_pdl(kern, grid, dim3(tpb), 0, st, rho, (const float*)x.phi_hi,
+                                     (const float*)x.phi_lo, (const double*)x.outer_shell, x.r32,
                                      (const RadialRowFF*)x.radff, (const ThetaRowFF*)x.thff, p.nr, p.nth, p.nphi, r0,
                                      r1, p.outer_bc == SP_OUTER_DIRICHLET ? 1 : 0, x.dir_coef, x.four_pi_g);
     return e != cudaSuccess ? e : cudaGetLastError();
