@@ -194,12 +194,14 @@ __global__ void __launch_bounds__(32) k_thomas_staged(const float* __restrict__ 
 // Radial solves of the low-precision solve as segmented scans.  With the factors
 // precomputed, the forward sweep d_i = b_i + a_i d_{i-1} (b_i = x_i/piv_i,
 // a_i = -sub_i/piv_i) and the back substitution f_i = d_i - c'_i f_{i+1} are first-order
-// linear recurrences.  One CTA per (m, re/im, kScanCols consecutive l): the column
-// block's rows are first staged in shared memory with cp.async (all rows in flight at
-// once), then each of kScanSegs thread groups sweeps one radial segment from a zero
-// start while recording the running product of the coefficients; the first group
-// chains the segment carries and every group adds carry x product to its rows.  The
-// forward values stay in shared memory for the back substitution.  All coefficients
+// linear recurrences.  One CTA per (m, kScanCols consecutive l) and NC of the two
+// components re/im (NC = 2 whenever two such CTAs fit on an SM): the column block's rows
+// are first staged in shared memory with cp.async (all rows in flight at once), then
+// each of kScanSegs thread groups sweeps one radial segment from a zero start while
+// recording the running product of the coefficients, which depends on the matrix only
+// and so serves both components; the first group chains the segment carries and every
+// group adds carry x product to its rows.  The forward values stay in shared memory for
+// the back substitution.  All coefficients
 // are contractive (|a_i|, |c'_i| < 1 for these diagonally dominant systems), so the
 // reassociation does not amplify rounding.  Lanes of near-singular modes idle; the
 // leading CTAs solve those in float64 with the same segmented scan (one warp per mode
@@ -208,23 +210,25 @@ constexpr int kScanCols = 16;
 constexpr int kScanThreads = 256;
 constexpr int kScanSegs = kScanThreads / kScanCols;
 
-// float32 CTAs: D, Q [nr][kScanCols] + sub [nr] floats; float64 CTAs: 8 warps x 2 x nr doubles
-size_t scan_smem_bytes(int nr) {
-  const size_t f32 = (2 * (size_t)nr * kScanCols + (size_t)nr) * sizeof(float);
+// float32 CTAs: NC arrays D and one Q [nr][kScanCols] + sub [nr] floats; float64 CTAs:
+// 8 warps x 2 x nr doubles
+size_t scan_smem_bytes(int nr, int nc) {
+  const size_t f32 = ((nc + 1) * (size_t)nr * kScanCols + (size_t)nr) * sizeof(float);
   const size_t f64 = (size_t)(kScanThreads / 32) * 2 * nr * sizeof(double);
   return f32 > f64 ? f32 : f64;
 }
 
+template <int NC>
 __global__ void __launch_bounds__(kScanThreads) k_thomas_scan(
     const float* __restrict__ sub_r, const double* __restrict__ lam, const float* __restrict__ x,
     const float* __restrict__ fcp, const float* __restrict__ finv, float* __restrict__ pl, int nr, int nth, int kstride,
     double thr, int nlowblk, const int* __restrict__ low_idx, int nlow, const RadialRow* __restrict__ rad64,
     const double2* __restrict__ low_fac) {
   extern __shared__ __align__(16) float sm[];
-  float* D = sm;                            // [nr][kScanCols] right-hand side, then d, then f
-  float* Q = sm + (size_t)nr * kScanCols;   // [nr][kScanCols] 1/pivot or c', then running products
-  float* A = Q + (size_t)nr * kScanCols;    // [nr] sub-diagonal
-  __shared__ float sE[kScanSegs][kScanCols], sP[kScanSegs][kScanCols], sC[kScanSegs][kScanCols];
+  // D[c] [nr][kScanCols]: right-hand side, then d, then f of component c
+  float* Q = sm + (size_t)NC * nr * kScanCols;   // [nr][kScanCols] 1/pivot or c', then running products
+  float* A = Q + (size_t)nr * kScanCols;         // [nr] sub-diagonal
+  __shared__ float sE[NC][kScanSegs][kScanCols], sP[kScanSegs][kScanCols], sC[NC][kScanSegs][kScanCols];
   const int tid = threadIdx.x;
   const size_t st = 2 * (size_t)nth;
   pdl_trigger();
@@ -297,8 +301,8 @@ __global__ void __launch_bounds__(kScanThreads) k_thomas_scan(
   const int col = tid % kScanCols, seg = tid / kScanCols;
   const int ncb = (nth + kScanCols - 1) / kScanCols;
   const int bid = (int)blockIdx.x - nlowblk;
-  const int c = bid & 1;
-  const int mb = bid >> 1;
+  const int c0 = NC == 2 ? 0 : (bid & 1);   // first component of this CTA
+  const int mb = NC == 2 ? bid : (bid >> 1);
   const int m = mb / ncb;
   const int l = (mb - m * ncb) * kScanCols + col;
   const bool valid = l < nth;
@@ -307,7 +311,7 @@ __global__ void __launch_bounds__(kScanThreads) k_thomas_scan(
   int L = (nr + kScanSegs - 1) / kScanSegs;
   L += (L & 1) ^ 1;
   const int i0 = min(nr, seg * L), i1 = min(nr, i0 + L);
-  // ---- stage the right-hand side and 1/pivot of the whole column block: 16-byte copies
+  // ---- stage the right-hand sides and 1/pivot of the whole column block: 16-byte copies
   // (4 threads per 16-column row) when rows start on 16-byte boundaries, else 4-byte
   const int lb0 = (mb - m * ncb) * kScanCols;
   const bool vec4 = (nth & 3) == 0;
@@ -326,46 +330,61 @@ __global__ void __launch_bounds__(kScanThreads) k_thomas_scan(
       for (int i = seg; i < nr; i += kScanSegs, g += kScanSegs * rstride, sd += kScanSegs * kScanCols) cp_async4(sd, g);
     }
   };
-  stage(D, x + (size_t)m * nr * st + (size_t)c * nth + lb0, st);
+#pragma unroll
+  for (int c = 0; c < NC; ++c)
+    stage(sm + (size_t)c * nr * kScanCols, x + (size_t)m * nr * st + (size_t)(c0 + c) * nth + lb0, st);
   stage(Q, finv + (size_t)m * nr * nth + lb0, nth);
   cp_async_commit();
   for (int i = tid; i < nr; i += kScanThreads) A[i] = sub_r[i];
   cp_async_wait<0>();
   __syncthreads();
   const int nseg = i1 - i0;
+  const size_t cst = (size_t)nr * kScanCols;   // distance between the components' arrays
   // ---- forward sweep of this segment from d = 0
-  float d = 0.f, q = 1.f;
+  float d[NC], q = 1.f;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) d[c] = 0.f;
   if (work) {
-    float* Dp = D + i0 * kScanCols + col;
+    float* Dp = sm + i0 * kScanCols + col;
     float* Qp = Q + i0 * kScanCols + col;
     const float* Ap = A + i0;
 #pragma unroll 4
     for (int n = 0; n < nseg; ++n) {
       const float iv = Qp[n * kScanCols];
       const float a = -Ap[n] * iv;
-      d = fmaf(a, d, Dp[n * kScanCols] * iv);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        d[c] = fmaf(a, d[c], Dp[c * cst + n * kScanCols] * iv);
+        Dp[c * cst + n * kScanCols] = d[c];
+      }
       q *= a;
-      Dp[n * kScanCols] = d;
       Qp[n * kScanCols] = q;
     }
   }
-  sE[seg][col] = d;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) sE[c][seg][col] = d[c];
   sP[seg][col] = q;
   __syncthreads();
-  if (seg == 0) {
+  if (seg < NC) {   // group c chains the carries of component c
     float carry = 0.f;   // d_{-1} = 0
     for (int w = 0; w < kScanSegs; ++w) {
-      sC[w][col] = carry;
-      carry = fmaf(sP[w][col], carry, sE[w][col]);
+      sC[seg][w][col] = carry;
+      carry = fmaf(sP[w][col], carry, sE[seg][w][col]);
     }
   }
   __syncthreads();
   if (work) {
-    const float cw = sC[seg][col];
-    float* Dp = D + i0 * kScanCols + col;
+    float cw[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) cw[c] = sC[c][seg][col];
+    float* Dp = sm + i0 * kScanCols + col;
     const float* Qp = Q + i0 * kScanCols + col;
 #pragma unroll 4
-    for (int n = 0; n < nseg; ++n) Dp[n * kScanCols] = fmaf(Qp[n * kScanCols], cw, Dp[n * kScanCols]);
+    for (int n = 0; n < nseg; ++n) {
+      const float qn = Qp[n * kScanCols];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) Dp[c * cst + n * kScanCols] = fmaf(qn, cw[c], Dp[c * cst + n * kScanCols]);
+    }
   }
   __syncthreads();
   // ---- stage c' over the running products, then back-substitute from f = 0
@@ -373,39 +392,51 @@ __global__ void __launch_bounds__(kScanThreads) k_thomas_scan(
   cp_async_commit();
   cp_async_wait<0>();
   __syncthreads();
-  float f = 0.f;
+  float f[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) f[c] = 0.f;
   q = 1.f;
   if (work) {
-    float* Dp = D + (i1 - 1) * kScanCols + col;
+    float* Dp = sm + (i1 - 1) * kScanCols + col;
     float* Qp = Q + (i1 - 1) * kScanCols + col;
 #pragma unroll 4
     for (int n = 0; n < nseg; ++n) {
       const float g = -Qp[-n * kScanCols];
-      f = fmaf(g, f, Dp[-n * kScanCols]);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        f[c] = fmaf(g, f[c], Dp[c * cst - n * kScanCols]);
+        Dp[c * cst - n * kScanCols] = f[c];
+      }
       q *= g;
-      Dp[-n * kScanCols] = f;
       Qp[-n * kScanCols] = q;
     }
   }
-  sE[seg][col] = f;   // value at the segment's first row from a zero start above it
+#pragma unroll
+  for (int c = 0; c < NC; ++c) sE[c][seg][col] = f[c];   // value at the segment's first row from a zero start above it
   sP[seg][col] = q;
   __syncthreads();
-  if (seg == 0) {
+  if (seg < NC) {
     float carry = 0.f;   // f_{nr} is absent
     for (int w = kScanSegs - 1; w >= 0; --w) {
-      sC[w][col] = carry;
-      carry = fmaf(sP[w][col], carry, sE[w][col]);
+      sC[seg][w][col] = carry;
+      carry = fmaf(sP[w][col], carry, sE[seg][w][col]);
     }
   }
   __syncthreads();
   if (work) {
-    const float cw = sC[seg][col];
-    const float* Dp = D + i0 * kScanCols + col;
+    float cw[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) cw[c] = sC[c][seg][col];
+    const float* Dp = sm + i0 * kScanCols + col;
     const float* Qp = Q + i0 * kScanCols + col;
-    float* out = pl + ((size_t)m * nr * 2 + c + 2 * (size_t)i0) * kstride + l;
+    float* out = pl + ((size_t)m * nr * 2 + c0 + 2 * (size_t)i0) * kstride + l;
     const size_t ostep = 2 * (size_t)kstride;
 #pragma unroll 4
-    for (int n = 0; n < nseg; ++n) out[n * ostep] = fmaf(Qp[n * kScanCols], cw, Dp[n * kScanCols]);
+    for (int n = 0; n < nseg; ++n) {
+      const float qn = Qp[n * kScanCols];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) out[n * ostep + c * kstride] = fmaf(qn, cw[c], Dp[c * cst + n * kScanCols]);
+    }
   }
 }
 
@@ -963,13 +994,16 @@ cudaError_t tc_project(const Plan& p, bool inverse, cudaStream_t s) {
 
 cudaError_t thomas_mixed(const Plan& p, cudaStream_t s) {
   const MixedTables& x = *p.mixed;
-  const size_t smem = scan_smem_bytes(p.nr);
+  // both components per CTA while two such CTAs fit on an SM, else one
+  const int nc = scan_smem_bytes(p.nr, 2) <= 108 * 1024 ? 2 : 1;
+  const size_t smem = scan_smem_bytes(p.nr, nc);
   if (smem <= 200 * 1024) {
-    const int nblk = 2 * p.mh * ((p.nth + kScanCols - 1) / kScanCols);
+    const int nblk = (2 / nc) * p.mh * ((p.nth + kScanCols - 1) / kScanCols);
     const int nlowblk = (x.nlow + kScanThreads / 64 - 1) / (kScanThreads / 64);
-    cudaError_t e = allow_smem(k_thomas_scan, smem);
+    auto kern = nc == 2 ? k_thomas_scan<2> : k_thomas_scan<1>;
+    cudaError_t e = allow_smem(kern, smem);
     if (e != cudaSuccess) return e;
-    e = launch_pdl(k_thomas_scan, dim3(nlowblk + nblk), dim3(kScanThreads), smem, s, (const float*)x.sub_r,
+    e = launch_pdl(kern, dim3(nlowblk + nblk), dim3(kScanThreads), smem, s, (const float*)x.sub_r,
                    (const double*)p.d_lam, (const float*)x.d32, (const float*)x.fcp, (const float*)x.finv, x.panel,
                    p.nr, p.nth, x.kstride, x.low_threshold, nlowblk, (const int*)x.low_idx, x.nlow,
                    (const RadialRow*)p.d_rad, (const double2*)x.low_fac);
