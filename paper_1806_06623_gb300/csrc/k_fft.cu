@@ -397,11 +397,17 @@ __global__ void __launch_bounds__(256, 3) k_fft_inv(const T* __restrict__ spec, 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   load_twiddles<T>(tw, twid, n);   // plan-constant: before the dependency wait
   pdl_trigger();
-  pdl_wait();
   const int line0 = blockIdx.x * lpc;
   const int nl = min(lpc, nlines - line0);
   const int npairs = (nl + 1) / 2;
   const int mh = n / 2 + 1;
+  // this CTA's iterate lines (not written by the preceding kernels) head for L2 while the
+  // spectra are read and transformed; a prefetch moves no data into the program
+  if (MODE == kInvPairUpdate && !first && threadIdx.x == 0) {
+    prefetch_lines_l2(out, line0, nl, n);
+    if (lo_read) prefetch_lines_l2(phi_lo, line0, nl, n);
+  }
+  pdl_wait();
   // the iterate lines of the CTA one resident wave ahead go on their way into L2 now
   if (MODE == kInvPairUpdate && !first && threadIdx.x == 0 && ahead > 0 && (int)blockIdx.x + ahead < (int)gridDim.x) {
     const int l2 = (blockIdx.x + ahead) * lpc;
