@@ -435,9 +435,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm_split(const __grid_cons
         for (int e = 0; e < 4; ++e) {
           const float v = (k + e < prm.K) ? x[e] : 0.f;
           h[0][e] = bf16_rn_bits(v);
-          const float r1 = v - __uint_as_float(h[0][e]);
+          const float r1 = __fsub_rn(v, __uint_as_float(h[0][e]));   // exact, <= 16 significant bits
           h[1][e] = bf16_rn_bits(r1);
-          h[2][e] = bf16_rn_bits(r1 - __uint_as_float(h[1][e]));
+          // r1 - x1 is exact with at most 8 significant bits: already a bf16 value
+          if (NP == 3) h[2][e] = __float_as_uint(__fsub_rn(r1, __uint_as_float(h[1][e])));
         }
 #pragma unroll
         for (int pl = 0; pl < NP; ++pl)
