@@ -383,18 +383,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm_split(const __grid_cons
       n0 = (g - m * tiles) * BN;
       return prm.B + ((size_t)m * prm.ncol + n0) * prm.kstride;
     };
+    // the thread's chunks u = 0..kConvPer-1 of a K block: rows r0 + 16 u, K-elements
+    // 4 kc4 .. +3 of the block; rows 16 apart share r mod 8, so their swizzled positions
+    // are 16 x 128 bytes apart
+    const int r0 = ct >> 4, kc4 = ct & 15;
+    const uint32_t off0 = (uint32_t)r0 * 128u + ((uint32_t)((kc4 >> 1) ^ (r0 & 7)) << 4) + (uint32_t)(kc4 & 1) * 8u;
     auto fetch = [&](int q, float4 (&v)[kConvPer]) {
       const int t = q / kb, b = q - t * kb;
       int n0;
       const float* Bt = tile_rows(t, n0);
+      const int k = b * kKBlk + 4 * kc4;
+      const float* src = Bt + (size_t)r0 * prm.kstride + k;
+      const int rows = prm.ncol - n0 - r0;   // rows r0 + 16 u exist while 16 u < rows
+      const bool kin = k < prm.kstride;
 #pragma unroll
-      for (int u = 0; u < kConvPer; ++u) {
-        v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-        const int c = ct + kConvThreads * u;
-        const int r = c >> 4, k = b * kKBlk + 4 * (c & 15);
-        if (n0 + r < prm.ncol && k < prm.kstride)
-          v[u] = __ldg(reinterpret_cast<const float4*>(Bt + (size_t)r * prm.kstride + k));
-      }
+      for (int u = 0; u < kConvPer; ++u)
+        v[u] = (kin && 16 * u < rows) ? __ldg(reinterpret_cast<const float4*>(src + (size_t)(16 * u) * prm.kstride))
+                                      : make_float4(0.f, 0.f, 0.f, 0.f);
     };
     // one thread keeps the rows of the tiles two ahead on their way into L2 (a tile's
     // rows are contiguous), so the register loads of the next K block hit L2
@@ -421,19 +426,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm_split(const __grid_cons
         break;
       }
       const int b = q % kb;
-      const uint32_t bst = sB + st * kStage;
+      const uint32_t bst = sB + st * kStage + off0;
+      const int k = b * kKBlk + 4 * kc4;
+      const bool kfull = k + 4 <= prm.K;   // else the elements at and beyond K enter as zeros
 #pragma unroll
       for (int u = 0; u < kConvPer; ++u) {
-        const int c = ct + kConvThreads * u;
-        const int r = c >> 4, kc4 = c & 15;
-        const int k = b * kKBlk + 4 * kc4;
         // 16-byte chunk kc4/2 of row r sits at chunk (kc4/2) ^ (r mod 8) of the 128-byte row
-        const uint32_t off = (uint32_t)r * 128u + ((uint32_t)((kc4 >> 1) ^ (r & 7)) << 4) + (uint32_t)(kc4 & 1) * 8u;
+        const uint32_t off = 2048u * (uint32_t)u;
         const float x[4] = {cur[u].x, cur[u].y, cur[u].z, cur[u].w};
         uint32_t h[3][4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          const float v = (k + e < prm.K) ? x[e] : 0.f;
+          const float v = (kfull || k + e < prm.K) ? x[e] : 0.f;
           h[0][e] = bf16_rn_bits(v);
           const float r1 = __fsub_rn(v, __uint_as_float(h[0][e]));   // exact, <= 16 significant bits
           h[1][e] = bf16_rn_bits(r1);
