@@ -437,8 +437,22 @@ def run_served(S, W, torch, n_requests, rates=(200.0, 2000.0, 20000.0)):
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch from an ncu capture of the
 # named command (full workload), per kernel group; kept only while the kernel is unchanged
+_PROF = "profiles/mixed_x6_550x128x256_kernels.md"
 NCU_TRAFFIC = {
-    "mixed": {},
+    "mixed": {
+        "residual": {"bytes": (219.18 + 50.40 + 0.80) * 1e6, "kernel": "k_residual_ff2<0> (interior rows + last shell)",
+                     "profile": _PROF},
+        "fft_inverse": {"bytes": (72.17 + 21.87 + 144.36 + 87.36) * 1e6 / 2, "kernel": "k_fft_inv<float, float, 2>",
+                        "profile": _PROF},
+        "fft_forward": {"bytes": (159.62 + 37.65 + 72.15 + 22.12) * 1e6 / 2,
+                        "kernel": "k_fft_fwd<float, double|float>", "profile": _PROF},
+        "radial_solve": {"bytes": (145.73 + 37.40 + 145.74 + 38.09) * 1e6 / 2, "kernel": "k_thomas_scan<2>",
+                         "profile": _PROF},
+        "project_forward": {"bytes": (91.61 + 19.04 + 91.69 + 19.27) * 1e6 / 2, "kernel": "tc::k_tc_gemm_split<3>",
+                            "profile": _PROF},
+        "project_inverse": {"bytes": (91.64 + 19.12 + 91.61 + 19.20) * 1e6 / 2, "kernel": "tc::k_tc_gemm_split<3>",
+                            "profile": _PROF},
+    },
 }
 
 
