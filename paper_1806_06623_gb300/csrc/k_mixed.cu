@@ -687,6 +687,90 @@ __global__ void __launch_bounds__(kResThreads) k_residual_ff(const double* __res
   }
 }
 
+// The float-float helpers on column pairs: paired float32 instructions (one instruction
+// per operation for both columns, each component rounded to nearest as in the scalar
+// forms, the operations in the same order).
+__device__ __forceinline__ float2 f2s(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, neg2(b)); }
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2& s, float2& e) {
+  s = add2(a, b);
+  const float2 bb = sub2(s, a);
+  e = add2(sub2(a, sub2(s, bb)), sub2(b, bb));
+}
+template <bool LO>
+__device__ __forceinline__ void ffd_diff2(float2 bh, float2 bl, float2 ch, float2 cl, float2& dh, float2& dl) {
+  if (LO) {
+    float2 e;
+    two_sum2(bh, neg2(ch), dh, e);
+    dl = add2(e, sub2(bl, cl));
+  } else {
+    two_sum2(bh, neg2(ch), dh, dl);
+  }
+}
+__device__ __forceinline__ void ffd_mul2(const ff& k, float2 dh, float2 dl, float2& p, float2& e) {
+  p = __fmul2_rn(f2s(k.hi), dh);
+  e = __ffma2_rn(f2s(k.hi), dh, neg2(p));
+  e = __ffma2_rn(f2s(k.hi), dl, e);
+  e = __ffma2_rn(f2s(k.lo), dh, e);
+}
+__device__ __forceinline__ void ffd_acc2(float2& ah, float2& al, float2 ph, float2 pe) {
+  float2 s, e;
+  two_sum2(ah, ph, s, e);
+  ah = s;
+  al = add2(al, add2(e, pe));
+}
+
+// residual_zone for the two columns of a pair at once.
+template <bool LO>
+__device__ __forceinline__ float2 residual_zone2(float2 ch, float2 cl, float2& mh, float2& ml, bool has_im,
+                                                 bool has_ip, float2 nh, float2 nl, bool has_jm, float2 jmh,
+                                                 float2 jml, bool has_jp, float2 jph, float2 jpl, float2 qh, float2 ql,
+                                                 float2 oh, float2 ol, const RadialRowFF& rr, const ThetaRowFF& ar,
+                                                 double2 rv, const ff& four_pi_g) {
+  float2 dh, dl, p, e;
+  float2 sh = f2s(0.f), sl = f2s(0.f);
+  if (has_im) {
+    ffd_mul2(rr.sub, mh, ml, p, e);
+    sh = p;
+    sl = e;
+  }
+  if (has_ip) {
+    ffd_diff2<LO>(nh, nl, ch, cl, dh, dl);
+    ffd_mul2(rr.sup, dh, dl, p, e);
+    ffd_acc2(sh, sl, p, e);
+    mh = neg2(dh);
+    ml = neg2(dl);
+  }
+  if (has_jm) {
+    ffd_diff2<LO>(jmh, jml, ch, cl, dh, dl);
+    ffd_mul2(ar.tm, dh, dl, p, e);
+    ffd_acc2(sh, sl, p, e);
+  }
+  if (has_jp) {
+    ffd_diff2<LO>(jph, jpl, ch, cl, dh, dl);
+    ffd_mul2(ar.tp, dh, dl, p, e);
+    ffd_acc2(sh, sl, p, e);
+  }
+  ffd_mul2(ar.sphi, qh, ql, p, e);
+  ffd_acc2(sh, sl, p, e);
+  if (!has_ip) ffd_acc2(sh, sl, oh, ol);
+  // 4 pi G rho as a float-float pair per column (ff_mul, then fast two-sum)
+  const ff rx = d2ff_trunc(rv.x), ry = d2ff_trunc(rv.y);
+  const float2 rh = make_float2(rx.hi, ry.hi), rl = make_float2(rx.lo, ry.lo);
+  const float2 sp = __fmul2_rn(f2s(four_pi_g.hi), rh);
+  float2 se = __ffma2_rn(f2s(four_pi_g.hi), rh, neg2(sp));
+  se = __ffma2_rn(f2s(four_pi_g.hi), rl, se);
+  se = __ffma2_rn(f2s(four_pi_g.lo), rh, se);
+  const float2 svh = add2(sp, se);
+  const float2 svl = sub2(se, sub2(svh, sp));
+  float2 th_, tl;
+  two_sum2(svh, neg2(sh), th_, tl);
+  tl = add2(tl, sub2(svl, sl));
+  return add2(th_, tl);
+}
+
 // The same for an even number of phi zones, two adjacent columns (k, k+1) per thread:
 // 8- and 16-byte accesses, the per-row work done once per pair, and the phi face between
 // the pair's columns differenced once for both.  rho must be 16-byte aligned.
@@ -728,12 +812,8 @@ __global__ void __launch_bounds__(kResThreads) k_residual_ff2(const double* __re
   const ThetaRowFF* angp = ang + (size_t)i0 * nth + j;
   const float2 z2 = make_float2(0.f, 0.f);
   float2 ch = hp[0], cl = LO ? lp[0] : z2;
-  float mxh = 0.f, mxl = 0.f, myh = 0.f, myl = 0.f;   // Phi(i-1) - Phi(i) of both columns
-  if (i0 > 0) {
-    const float2 bh = hp[-(ptrdiff_t)sh2], bl = LO ? lp[-(ptrdiff_t)sh2] : z2;
-    ffd_diff_lo<LO>(bh.x, bl.x, ch.x, cl.x, mxh, mxl);
-    ffd_diff_lo<LO>(bh.y, bl.y, ch.y, cl.y, myh, myl);
-  }
+  float2 m2h = z2, m2l = z2;   // Phi(i-1) - Phi(i) of both columns
+  if (i0 > 0) ffd_diff2<LO>(hp[-(ptrdiff_t)sh2], LO ? lp[-(ptrdiff_t)sh2] : z2, ch, cl, m2h, m2l);
   for (int i = i0; i < i1; ++i) {
     float* ev = line[i & 1][0][0];   // high words of the even and odd columns
     float* od = line[i & 1][0][1];
@@ -774,22 +854,18 @@ __global__ void __launch_bounds__(kResThreads) k_residual_ff2(const double* __re
     const ThetaRowFF ar = *angp;
     __syncthreads();
     // phi second differences: the face between the pair's columns once for both
-    float dmh, dml, qxh, qxl, qyh, qyl;
-    ffd_diff_lo<LO>(ch.y, cl.y, ch.x, cl.x, dmh, dml);                      // Phi(k+1) - Phi(k)
-    ffd_diff_lo<LO>(od[t], LO ? odl[t] : 0.f, ch.x, cl.x, qxh, qxl);         // Phi(k-1) - Phi(k)
-    ffd_acc(qxh, qxl, dmh, dml);
-    ffd_diff_lo<LO>(ev[t + 2], LO ? evl[t + 2] : 0.f, ch.y, cl.y, qyh, qyl); // Phi(k+2) - Phi(k+1)
-    ffd_acc(qyh, qyl, -dmh, -dml);
-    float oxh = 0.f, oxl = 0.f, oyh = 0.f, oyl = 0.f;
+    float dmh, dml;
+    ffd_diff_lo<LO>(ch.y, cl.y, ch.x, cl.x, dmh, dml);   // Phi(k+1) - Phi(k)
+    float2 qh, ql;                                       // Phi(k-1) - Phi(k), Phi(k+2) - Phi(k+1)
+    ffd_diff2<LO>(make_float2(od[t], ev[t + 2]), LO ? make_float2(odl[t], evl[t + 2]) : z2, ch, cl, qh, ql);
+    ffd_acc2(qh, ql, make_float2(dmh, -dmh), make_float2(dml, -dml));
+    float2 oh = z2, ol = z2;
     if (!has_ip) {
-      outer_term(dirichlet, dir_coef, ch.x, cl.x, outer_shell, (size_t)j * nphi + k, oxh, oxl);
-      outer_term(dirichlet, dir_coef, ch.y, cl.y, outer_shell, (size_t)j * nphi + k + 1, oyh, oyl);
+      outer_term(dirichlet, dir_coef, ch.x, cl.x, outer_shell, (size_t)j * nphi + k, oh.x, ol.x);
+      outer_term(dirichlet, dir_coef, ch.y, cl.y, outer_shell, (size_t)j * nphi + k + 1, oh.y, ol.y);
     }
-    float2 res;
-    res.x = residual_zone<LO>(ch.x, cl.x, mxh, mxl, i > 0, has_ip, nh.x, nl.x, has_jm, jmh.x, jml.x, has_jp, jph.x,
-                              jpl.x, qxh, qxl, oxh, oxl, rr, ar, rv.x, four_pi_g);
-    res.y = residual_zone<LO>(ch.y, cl.y, myh, myl, i > 0, has_ip, nh.y, nl.y, has_jm, jmh.y, jml.y, has_jp, jph.y,
-                              jpl.y, qyh, qyl, oyh, oyl, rr, ar, rv.y, four_pi_g);
+    const float2 res = residual_zone2<LO>(ch, cl, m2h, m2l, i > 0, has_ip, nh, nl, has_jm, jmh, jml, has_jp, jph, jpl,
+                                          qh, ql, oh, ol, rr, ar, rv, four_pi_g);
     if (act) *op = res;
     ch = nh;
     cl = nl;
