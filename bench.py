@@ -440,7 +440,7 @@ def run_served(S, W, torch, n_requests, rates=(200.0, 2000.0, 20000.0)):
 _PROF = "profiles/mixed_x6_550x128x256_kernels.md"
 NCU_TRAFFIC = {
     "mixed": {
-        "residual": {"bytes": (219.18 + 50.40 + 0.80) * 1e6, "kernel": "k_residual_ff2<0> (interior rows + last shell)",
+        "residual": {"bytes": (219.40 + 53.22 + 0.80) * 1e6, "kernel": "k_residual_ff2<0> (interior rows + last shell)",
                      "profile": _PROF},
         "fft_inverse": {"bytes": (72.17 + 21.87 + 144.36 + 87.36) * 1e6 / 2, "kernel": "k_fft_inv<float, float, 2>",
                         "profile": _PROF},
