@@ -343,7 +343,10 @@ __global__ void __launch_bounds__(256, 3) k_fft_fwd(const Tin* __restrict__ in, 
   if (nl & 1)
     for (int q = threadIdx.x; q < n; q += blockDim.x) bufA[(nl >> 1) * PS + q].y = T(0);
   __syncthreads();
-  CT* Z = n == 256 ? warp_fft256<false, T>(bufA, bufB, tw, npairs, PS) : warp_fft<false, T>(bufA, bufB, tw, sch, npairs, PS);
+  // the two-pass radix-16 form keeps a half-warp per line pair: it pays only with every
+  // warp busy; few pairs (one shell) take the radix-4 passes with a whole warp per pair
+  CT* Z = (n == 256 && npairs >= 2 * kWarps) ? warp_fft256<false, T>(bufA, bufB, tw, npairs, PS)
+                                             : warp_fft<false, T>(bufA, bufB, tw, sch, npairs, PS);
   __syncthreads();
   const int mh = n / 2 + 1;
   const int l = lane;
@@ -458,7 +461,8 @@ __global__ void __launch_bounds__(256, 3) k_fft_inv(const T* __restrict__ spec, 
     }
   }
   __syncthreads();
-  CT* Z = n == 256 ? warp_fft256<true, T>(bufA, bufB, tw, npairs, PS) : warp_fft<true, T>(bufA, bufB, tw, sch, npairs, PS);
+  CT* Z = (n == 256 && npairs >= 2 * kWarps) ? warp_fft256<true, T>(bufA, bufB, tw, npairs, PS)
+                                             : warp_fft<true, T>(bufA, bufB, tw, sch, npairs, PS);
   float me = 0.f, mp = 0.f;
   for (int p = warp; p < npairs; p += kWarps) {
     const CT* z = Z + p * PS;
