@@ -4,8 +4,9 @@
 //   D[m][n][r] = sum_k A[m][r][k] B[m][n][k]      (r < M = Ntheta rows, k < K = Ntheta)
 // with A the (H^T W)_m or H_m table and B the K-contiguous float32 spectral panel of
 // 2 Nr columns n = (i, re/im).  Both operands enter the products as NP bf16 planes
-// x = x0 + x1 (+ x2) (x0 = RN_bf16(x), x1 = RN_bf16(x - x0), x2 = RN_bf16(x - x0 - x1));
-// the table's planes are precomputed, the panel's are formed in shared memory.  The
+// x = x0 + x1 (+ x2) (x0 = RN_bf16(x), x1 = RN_bf16(x - x0), x2 = RN_bf16(x - x0 - x1),
+// for a float32 x the exact remainder); the table's planes are precomputed, the panel's
+// are formed in shared memory.  The
 // product keeps every plane pair whose index sum is below NP, smallest terms first:
 //   NP = 2: A1 B0 + A0 B1 + A0 B0                              (3 products, ~2^-16)
 //   NP = 3: A2 B0 + A0 B2 + A1 B1 + A1 B0 + A0 B1 + A0 B0      (6 products, ~2^-24)
@@ -19,7 +20,7 @@
 //    boxes of 64 K-elements), the next segment's only after the products of the previous
 //    one have completed;
 //  - warps 6..13 stream the panel rows of the CTA's column tiles one K block at a time
-//    (float4 loads, the next block in flight while the current one is converted),
+//    (float4 loads, the next two blocks in flight while the current one is converted),
 //    split them into bf16 planes and store those in the 128B-swizzled K-major layout of
 //    a ring of stages (full/empty mbarriers per stage, fence.proxy.async before the
 //    arrival);
