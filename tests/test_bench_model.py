@@ -1,0 +1,55 @@
+"""The bench's algorithmic byte model (the numerator of the reported roofline), checked
+against the per-zone counts of each kernel group written out by hand."""
+import types
+
+import bench
+
+NR, NTH, NPHI = 550, 128, 256
+Z = NR * NTH * NPHI
+MH = NPHI // 2 + 1
+S = 2 * MH * NR * NTH
+
+
+def grid():
+    return types.SimpleNamespace(shape=(NR, NTH, NPHI))
+
+
+def test_six_product_solve_with_one_correction():
+    b = bench.algorithmic_bytes_per_step(grid(), "mixed", iters=2)
+    t = 2 * 3 * MH * NTH * NTH                      # three bf16 planes of the table
+    assert b["fft_forward"] == (8 * Z + 4 * S) + (4 * Z + 4 * S)   # rho in, then r in; panel out
+    assert b["project_forward"] == b["project_inverse"] == 2 * (8 * S + t)
+    assert b["radial_solve"] == 2 * 12 * S          # panel in and out, 1/pivot and c' tables
+    # first solve: spectrum in, high word out; correction: spectrum and high word in,
+    # float64 Phi out (the float-float words are not stored)
+    assert b["fft_inverse"] == (4 * S + 4 * Z) + (4 * S + 12 * Z)
+    assert b["residual"] == 16 * Z                  # rho, high word, r
+    assert b["update"] == 0.0
+    total = sum(b.values())
+    assert abs(total / 1e9 - 2.15) < 0.01           # the HBM floor of one solve, 2.15 GB
+
+
+def test_three_product_solve_with_two_corrections():
+    b = bench.algorithmic_bytes_per_step(grid(), "mixed_x3", iters=3)
+    # both corrections store the float-float iterate (and float64 Phi)
+    assert b["fft_inverse"] == (4 * S + 4 * Z) + (4 * S + 20 * Z) + (4 * S + 24 * Z)
+    assert b["residual"] == 16 * Z + 20 * Z         # the second reads both words
+    assert b["update"] == 0.0
+
+
+def test_second_six_product_correction_rebuilds_the_words():
+    b = bench.algorithmic_bytes_per_step(grid(), "mixed", iters=3)
+    assert b["update"] == 16 * Z                    # float64 in, two float words out
+    assert b["residual"] == 16 * Z + 20 * Z
+
+
+def test_no_correction_converts_the_high_word():
+    b = bench.algorithmic_bytes_per_step(grid(), "mixed", iters=1)
+    assert b["update"] == 12 * Z and b["residual"] == 0
+    assert b["fft_inverse"] == 4 * S + 4 * Z
+
+
+def test_float64_path():
+    b = bench.algorithmic_bytes_per_step(grid(), "fp64")
+    assert b["fft_forward"] == 8 * Z + 8 * S and b["fft_inverse"] == 8 * S + 8 * Z
+    assert b["radial_solve"] == 16 * S + 4 * S
