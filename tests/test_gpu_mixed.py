@@ -178,3 +178,25 @@ def test_mixed_x6_second_correction_rebuilds_iterate(S):
         torch.cuda.synchronize()
         assert torch.equal(out, phi_d), k
         assert info.iterations == info_d.iterations
+
+
+def test_mixed_rho_on_an_8_byte_boundary(S):
+    """Even Nphi with rho 16-byte aligned takes the two-column residual; rho on an 8-byte
+    boundary the one-column form. Both meet the tolerance, and agree to rounding."""
+    p = W.random_small(40, 24, 32, seed=17, grid="log")
+    ref = O.solve_exact(O.Geometry(p.r_if, p.th_if, p.nphi), p.rho)
+    plan = S.Plan(p.r_if, p.th_if, p.nphi, precision=S.SP_MIXED_BF16X6)
+    plan.set_graphs(False)
+    n = p.rho.size
+    buf = torch.empty(n + 1, dtype=torch.float64, device="cuda")
+    aligned = torch.from_numpy(np.ascontiguousarray(p.rho)).cuda()
+    shifted = buf[1:].view(p.rho.shape)              # 8 bytes past a 256-byte boundary
+    shifted.copy_(aligned)
+    assert shifted.data_ptr() % 16 == 8
+    phi_a, info_a = plan.solve(aligned)
+    phi_b, info_b = plan.solve(shifted)
+    torch.cuda.synchronize()
+    a, b = phi_a.cpu().numpy(), phi_b.cpu().numpy()
+    assert info_a.status == S.SP_OK and info_b.status == S.SP_OK
+    assert rel_err(a, ref) <= TOL and rel_err(b, ref) <= TOL
+    assert rel_err(b, a) <= 1e-12
