@@ -82,22 +82,28 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, device_index: int):
+    def __init__(self, device_index: int, period_ms: int = 20):
         self.dev = device_index
+        self.period_ms = period_ms
         self.proc = None
         self.path = None
 
     def start(self):
+        """Start sampling (nvidia-smi in the background, one line per period)."""
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu=timestamp,{self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", str(self.period_ms)],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+        time.sleep(0.3)   # the first sample lands before the work starts
 
-    def stop(self):
+    def stop(self, window=None):
+        """Median SM clock and active throttle reasons over the samples; `window` = (t0, t1)
+        wall-clock seconds of the timed region, whose samples are counted separately."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -105,23 +111,37 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sm, smax, reasons = [], [], set()
+        sm, smax, reasons, in_win = [], [], set(), []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in open(self.path):
             f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                sm.append(float(f[1]))
-                smax.append(float(f[2]))
+                mhz, mx = float(f[2]), float(f[3])
             except ValueError:
                 continue
-            for nm, v in zip(names, f[5:9]):
+            sm.append(mhz)
+            smax.append(mx)
+            for nm, v in zip(names, f[6:10]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
+            if window is not None:
+                try:
+                    import datetime
+                    ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                    if window[0] <= ts <= window[1]:
+                        in_win.append(mhz)
+                except ValueError:
+                    pass
         os.unlink(self.path)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        out = {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+               "reasons": sorted(reasons), "samples": len(sm), "period_ms": self.period_ms,
+               "span": "warm-up, timed steps and the per-kernel pass of the headline plan"}
+        if window is not None:
+            out["samples_in_timed_steps"] = len(in_win)
+            out["sm_mhz_in_timed_steps"] = statistics.median(in_win) if in_win else None
+        return out
 
 
 # ------------------------------------------------------------ CPU baseline
@@ -227,16 +247,18 @@ def run_ours(args, rank, world, local):
 
     results = {}
     for name, plan in plans.items():
+        clocks = ClockSampler(local)
+        if name == precision:
+            clocks.start()
         for _ in range(args.warmup):
             plan.solve(rho, phi)
         barrier()
         n0 = plan.launch_count()
-        clocks = ClockSampler(local)
-        clocks.start() if name == precision else None
         barrier()
+        w0 = time.time()
         tot_ms, infos = timed_steps(plan, args.steps, collect=False)
         barrier()
-        ck = clocks.stop() if name == precision else None
+        w1 = time.time()
         launches = plan.launch_count() - n0
         # per-kernel breakdown in a separate pass: the per-launch CUDA events stay out of
         # the timed steps above
@@ -245,6 +267,7 @@ def run_ours(args, rank, world, local):
         timed_steps(plan, nb, collect=True)
         timing = {k: (v[0] * args.steps / nb, v[1] * args.steps // nb) for k, v in plan.timing().items()}
         plan.set_timing(False)
+        ck = clocks.stop(window=(w0, w1)) if name == precision else None
         tot_ms = max_over_ranks(tot_ms, world, dev)
         results[name] = {"ms": tot_ms, "infos": infos, "launches": launches, "timing": timing, "clocks": ck,
                          "phi": phi.detach().cpu().numpy() if (rank == 0 and not args.no_oracle_check) else None}
@@ -289,6 +312,8 @@ def run_ours(args, rank, world, local):
         line[f"{name}_zones_per_s"] = whole_job_rate(zones, args.steps, world, rr["ms"] / 1e3)
         line[f"{name}_ms_per_step"] = rr["ms"] / args.steps
     line["roofline"] = roofline(r["timing"], p, precision, args.steps, r["infos"][-1].get("iterations", 2))
+    line["projection_tensor"] = projection_tensor_rate(r["timing"], p, precision)
+    line["kernel_source_sha"] = kernel_source_hash()
     if not args.no_small:
         line["small_configs"] = run_small(S, W, torch, dev, check=not args.no_oracle_check)
     if not args.no_batched:
@@ -435,25 +460,79 @@ def run_served(S, W, torch, n_requests, rates=(200.0, 2000.0, 20000.0)):
     return out
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum of one launch from an ncu capture of the
-# named command (full workload), per kernel group; kept only while the kernel is unchanged
-_PROF = "profiles/mixed_x6_550x128x256_kernels.md"
+# dram__bytes_read.sum + dram__bytes_write.sum per launch, per kernel group, from one ncu
+# capture of the mixed solve on the full workload.  The counters hold only for the kernel
+# sources they were taken from: `source_sha` is kernel_source_hash() of that build (the
+# device code of the mixed path and its launchers), and the bench reports traffic as
+# null once those sources differ.
+MIXED_KERNEL_SOURCES = ("k_fft.cu", "k_mixed.cu", "tc_gemm.cuh", "ff.cuh", "sp_internal.h")
 NCU_TRAFFIC = {
-    "mixed": {
-        "residual": {"bytes": (219.40 + 53.22 + 0.80) * 1e6, "kernel": "k_residual_ff2<0> (interior rows + last shell)",
-                     "profile": _PROF},
-        "fft_inverse": {"bytes": (72.17 + 21.87 + 144.36 + 87.36) * 1e6 / 2, "kernel": "k_fft_inv<float, float, 2>",
-                        "profile": _PROF},
-        "fft_forward": {"bytes": (159.62 + 37.65 + 72.15 + 22.12) * 1e6 / 2,
-                        "kernel": "k_fft_fwd<float, double|float>", "profile": _PROF},
-        "radial_solve": {"bytes": (145.73 + 37.40 + 145.74 + 38.09) * 1e6 / 2, "kernel": "k_thomas_scan<2>",
-                         "profile": _PROF},
-        "project_forward": {"bytes": (91.61 + 19.04 + 91.69 + 19.27) * 1e6 / 2, "kernel": "tc::k_tc_gemm_split<3>",
-                            "profile": _PROF},
-        "project_inverse": {"bytes": (91.64 + 19.12 + 91.61 + 19.20) * 1e6 / 2, "kernel": "tc::k_tc_gemm_split<3>",
-                            "profile": _PROF},
+    "source_sha": "7e4927d4ac299c18",
+    "mixed": {   # MB read + written, averaged over the group's launches in one solve
+        "fft_forward": {"bytes": ((159.498 + 38.187) + (72.150 + 22.072)) * 1e6 / 2,
+                        "kernel": "k_fft_fwd<float, double> (rho), k_fft_fwd<float, float> (residual)"},
+        "project_forward": {"bytes": ((91.532 + 18.966) + (91.638 + 19.181)) * 1e6 / 2,
+                            "kernel": "tc::k_tc_gemm_split<3>"},
+        "radial_solve": {"bytes": ((145.778 + 39.671) + (145.811 + 39.150)) * 1e6 / 2, "kernel": "k_thomas_scan<2>"},
+        "project_inverse": {"bytes": ((91.504 + 19.132) + (91.562 + 19.159)) * 1e6 / 2,
+                            "kernel": "tc::k_tc_gemm_split<3>"},
+        "fft_inverse": {"bytes": ((72.166 + 21.922) + (144.430 + 87.446)) * 1e6 / 2,
+                        "kernel": "k_fft_inv<float, float, 2> (first solve, correction)"},
+        "residual": {"bytes": (219.411 + 50.577 + 0.801) * 1e6,
+                     "kernel": "k_residual_ff2<0> (interior rows + last shell)"},
     },
 }
+
+
+def kernel_source_hash(names=MIXED_KERNEL_SOURCES):
+    """sha256 (first 16 hex digits) of the named CUDA sources of the library."""
+    import hashlib
+    h = hashlib.sha256()
+    pkg = os.path.join(ROOT, "paper_1806_06623_gb300", "csrc")
+    for name in sorted(names):
+        h.update(name.encode())
+        h.update(open(os.path.join(pkg, name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(precision, name):
+    """Per-launch DRAM bytes of a kernel group from the ncu table, or None when the table
+    was taken from other kernel sources (or has no entry)."""
+    if NCU_TRAFFIC.get("source_sha") != kernel_source_hash():
+        return None
+    return NCU_TRAFFIC.get(precision, {}).get(name)
+
+
+def projection_tensor_rate(timing, p, precision):
+    """Tensor-pipe view of the tcgen05 projections: the paper's algorithmic count
+    2 Nr Ntheta^2 Nphi flops per projection (Sect. 4.1) and the flops the MMAs execute
+    (bf16 products of 128 x 128 x 16 over the padded tiles), per average live launch,
+    against the measured dense bf16 burst peak."""
+    if precision == "fp64":
+        return None
+    nr, nth, nphi = p.shape
+    mh = nphi // 2 + 1
+    ms = sum(timing.get(k, (0.0, 0))[0] for k in ("project_forward", "project_inverse"))
+    cnt = sum(timing.get(k, (0.0, 0))[1] for k in ("project_forward", "project_inverse"))
+    if not cnt:
+        return None
+    per_launch_s = ms / cnt / 1e3
+    nprod = 6 if precision == "mixed" else 3
+    tiles = -(-2 * nr // 128)
+    kblocks = -(-nth // 64)
+    executed = mh * tiles * kblocks * 4 * nprod * 2.0 * 128 * 128 * 16
+    algorithmic = 2.0 * nr * nth * nth * nphi
+    try:
+        peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+        src = "MEASURED_PEAKS.json bf16_tflops (burst, of measured)"
+    except Exception:
+        peak, src = 1900.0, "fallback 1.9 PFLOP/s"
+    a = algorithmic / per_launch_s / 1e12
+    e = executed / per_launch_s / 1e12
+    return {"us_per_launch": per_launch_s * 1e6, "algorithmic_tflops": a, "algorithmic_frac": a / peak,
+            "executed_tflops": e, "executed_frac": e / peak, "peak_tflops": peak, "peak_source": src,
+            "products": nprod, "algorithmic": "2 Nr Ntheta^2 Nphi flops per projection",
+            "executed": f"{mh} m x {tiles} column tiles x {kblocks} K blocks x 4 x {nprod} MMAs of 128x128x16"}
 
 
 def algorithmic_bytes_per_step(p, precision, iters=2):
@@ -516,17 +595,19 @@ def roofline(timing, p, precision, steps, iters=2):
     b = per_step * steps / cnt          # per launch
     ach = b / per_launch_s / 1e9
     pk = float(peaks.get("hbm_gbs", 6800.0))
-    tr = NCU_TRAFFIC.get(precision, {}).get(name)
+    tr = ncu_traffic(precision, name)
     return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s", "frac": ach / pk,
-            "traffic": tr["bytes"] if tr else None, "traffic_source": tr["profile"] if tr else None,
+            "traffic": tr["bytes"] if tr else None, "traffic_kernel": tr["kernel"] if tr else None,
             "algorithmic_bytes_per_launch": b,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s"}
 
 
 def check_vs_oracle(p, phis):
+    """max|dPhi|/max|Phi| against the oracle's exact float64 solution (separated solve
+    plus residual correction with the operator) and the backward error eta."""
     from oracle import sph_poisson as O
     geo = O.Geometry(p.r_if, p.th_if, p.nphi)
-    ref = O.solve_separated(geo, p.rho)
+    ref = O.solve_exact(geo, p.rho)
     out = {}
     for k, v in phis.items():
         if v is None:

@@ -159,8 +159,10 @@ int sp_apply_laplacian(sp_plan* plan, const double* phi_dev, double* out_dev, vo
  * for callers that cannot call cudaMalloc where they need the operator -- code that
  * must not synchronise the device (cudaMalloc/cudaFree may), or that runs under a host
  * framework owning a fixed device-memory pool.  The plan itself is created (and
- * allocates its tables) beforehand.
- *  - Result: identical to sp_apply_laplacian on the same plan and input.
+ * allocates its tables) beforehand; float64 and mixed-precision plans both work.
+ *  - Result: bitwise identical to sp_apply_laplacian on the same plan and input (the
+ *    same kernels in the same order); the launches count in sp_plan_launch_count and
+ *    are timed by the plan's per-kernel timers like sp_apply_laplacian's.
  *  - Scratch: the outer-shell spectra of the multipole boundary term live in one
  *    fixed 4 MiB array inside the library's device image (every GPU that loads the
  *    library holds it until the process exits).  Plans needing more,

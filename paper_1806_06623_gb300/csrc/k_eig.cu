@@ -14,6 +14,14 @@
 // entries at the pole), which the QL iteration resolves to a much smaller error in the
 // equatorial (small-|lambda|) modes than the doubly graded full matrix.
 //
+// Mode order: on a parity-split grid the even modes take l = 0..h-1 and the odd modes
+// l = h..Ntheta-1, each half in descending order of lambda (the radial solves only need
+// each mode's own lambda, so any order serves), and the half blocks are also written as
+// (Ntheta/2)^2 tables (H^T W)_m,p[l][j] and H_m,p[j][l], p = even/odd, j < Ntheta/2:
+// the projections then fold the spectrum into s(j) +- s(Ntheta-1-j) and multiply two
+// half-size matrices per m instead of one full one (Sect. 4.2).  Otherwise l ranks all
+// Ntheta eigenvalues in descending order.
+//
 // Each block is diagonalised by the implicit QL iteration with Wilkinson-type shifts
 // (Bowdler, Martin, Reinsch & Wilkinson 1968; Golub & Van Loan, Sect. 8.3): each sweep
 // chases the bulge from the bottom of the active block to its top with Givens
@@ -106,7 +114,8 @@ __global__ void k_theta_eigen(const double* __restrict__ tdiag, const double* __
                               const double* __restrict__ sqw, int nth, int parity, int outer_bc, double r_out,
                               double r_last, double outer_coef, double* __restrict__ lam_out,
                               double* __restrict__ kappa_out, double* __restrict__ outer_out,
-                              double* __restrict__ H, double* __restrict__ HtW, int* __restrict__ err) {
+                              double* __restrict__ H, double* __restrict__ HtW, double* __restrict__ Hp,
+                              double* __restrict__ HtWp, int* __restrict__ err) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int h = parity ? nth / 2 : nth;       // block size
   const int nblk = parity ? 2 : 1;
@@ -185,11 +194,13 @@ __global__ void k_theta_eigen(const double* __restrict__ tdiag, const double* __
     }
     __syncthreads();
   }
-  // descending rank over all nth eigenvalues, ties broken by index
+  // descending rank, ties broken by index: within the half block of a parity grid
+  // (l = block * h + rank), else over all nth eigenvalues
   for (int a = tid; a < nth; a += blockDim.x) {
-    int rnk = 0;
+    const int b0 = parity ? (a / h) * h : 0, b1 = parity ? b0 + h : nth;
+    int rnk = b0;
     const double va = d[a];
-    for (int b = 0; b < nth; ++b) {
+    for (int b = b0; b < b1; ++b) {
       const double vb = d[b];
       rnk += (vb > va) || (vb == va && b < a);
     }
@@ -228,6 +239,21 @@ __global__ void k_theta_eigen(const double* __restrict__ tdiag, const double* __
     Am[(size_t)lrow * nth + j] = z * sw;
     Hm[(size_t)j * nth + lrow] = z / sw;
   }
+  if (parity) {
+    // half tables [m][p][h][h]: (H^T W)_p[l][j] and H_p[j][l] for j < h, the values of
+    // the full tables' upper half (the lower half mirrors them, with a sign for p = odd)
+    double* Ap = HtWp + (size_t)m * 2 * h * h;
+    double* Hq = Hp + (size_t)m * 2 * h * h;
+    for (int t = tid; t < nth * h; t += blockDim.x) {
+      const int a = t / h, j = t - a * h;
+      const int blk = a / h, col = a - blk * h;
+      const int lrow = rank[a] - blk * h;
+      const double v = Z[blk * h * h + col * h + j] * rsq2;
+      const double sw = sqw[j];
+      Ap[((size_t)blk * h + lrow) * h + j] = v * sw;
+      Hq[((size_t)blk * h + j) * h + lrow] = v / sw;
+    }
+  }
 }
 
 }  // namespace
@@ -247,7 +273,7 @@ cudaError_t theta_eigen(const Plan& p, cudaStream_t s) {
   if (threads < 32) threads = 32;
   k_theta_eigen<<<p.mh, threads, smem, s>>>(p.d_tdiag, p.d_toff, p.d_sqw, nth, p.parity ? 1 : 0, p.outer_bc,
                                             p.r_out, p.r_last, p.outer_coef, p.d_lam, p.d_kappa, p.d_outer,
-                                            p.d_H, p.d_HtW, p.d_err);
+                                            p.d_H, p.d_HtW, p.d_Hp, p.d_HtWp, p.d_err);
   return cudaGetLastError();
 }
 

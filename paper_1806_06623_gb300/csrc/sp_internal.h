@@ -132,6 +132,8 @@ struct Plan {
   double* d_outer = nullptr;      // [mh][nth] outer diagonal term of the radial row N
   double* d_HtW = nullptr;        // [mh][l][j] (H^T W)_m
   double* d_H = nullptr;          // [mh][j][l] H_m
+  double* d_HtWp = nullptr;       // parity grids: [mh][2][h][h] (H^T W)_m,p[l][j], h = nth/2, p = even/odd
+  double* d_Hp = nullptr;         // parity grids: [mh][2][h][h] H_m,p[j][l]
   double* d_oshell = nullptr;     // [mh][j][j'] H_m diag(outer_m) (H^T W)_m (multipole only)
   int* d_err = nullptr;           // device status word
 
@@ -240,6 +242,12 @@ cudaError_t fft_inverse_f64(const Plan& p, const double* spec, int nrs, double* 
 // Batched NT GEMM: C[b][n][r] = sum_k A[b][r][k] B[b][n][k], b < nb.
 cudaError_t gemm_nt_f64(const double* A, const double* B, double* C, int nb, int M, int ncol, int K,
                         cudaStream_t s);
+// Parity-split projections (nth = 2h): forward folds B[n][j] +- B[n][nth-1-j] and writes
+// C[n][p*h + l] = sum_{j<h} A[b][p][l][j] fold_p(j); inverse forms
+// g_p[n][j] = sum_{l<h} A[b][p][j][l] B[n][p*h + l] and writes C[n][j] = g_0 + g_1,
+// C[n][nth-1-j] = g_0 - g_1.
+cudaError_t gemm_parity_f64(const double* A, const double* B, double* C, int nb, int h, int ncol, bool inverse,
+                            cudaStream_t s);
 // Radial Thomas solves for every (m,l), in place on x[m][i][c][l].
 cudaError_t thomas_f64(const Plan& p, double* x, cudaStream_t s);
 // Local part of the finite-volume operator (all interior fluxes, Dirichlet outer term).

@@ -1,13 +1,12 @@
 // sp_apply_laplacian_noalloc: the finite-volume operator without any device allocation.
 //
 // Some callers cannot allocate device memory at the point where they need the
-// operator: code running inside a captured CUDA graph, a hydrodynamics step driven by
-// a host framework that owns a fixed memory pool, or a callback that must not
-// synchronise (cudaMalloc/cudaFree can synchronise the device).  For them this entry
-// point keeps the only scratch the operator needs -- the spectrum of the outermost
-// shell for the multipole boundary term -- in a fixed array that is part of the
-// library's device image, so a call allocates nothing.
-#include <atomic>
+// operator: a hydrodynamics step driven by a host framework that owns a fixed memory
+// pool and forbids other allocations, or a callback that must not synchronise the
+// device (cudaMalloc and cudaFree can).  For them this entry point keeps the only
+// scratch the operator needs -- the spectrum of the outermost shell for the multipole
+// boundary term -- in a fixed array that is part of the library's device image, so a
+// call allocates nothing.
 #include <mutex>
 
 #include "sp_internal.h"
@@ -25,7 +24,8 @@ void* g_scratch_addr[kMaxDevices] = {};
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-// Device address of the scratch array on the current device (set up once per device).
+// Device address of the scratch array on the current device (looked up once per device;
+// in host code the array's name is only a host-side stand-in, not a device address).
 int scratch_address(int dev, void** out) {
   if (dev < 0 || dev >= kMaxDevices) return SP_ERR_UNSUPPORTED;
   std::lock_guard<std::mutex> lock(g_mu);
@@ -41,30 +41,40 @@ int scratch_address(int dev, void** out) {
 }  // namespace
 
 extern "C" int sp_apply_laplacian_noalloc(sp_plan* plan, const double* phi, double* out, void* stream) {
+  cudaGetLastError();   // an earlier failed call of this thread is not this call's error
   if (!plan || !phi || !out) return SP_ERR_INVALID_ARG;
-  const sp::Plan* p = reinterpret_cast<const sp::Plan*>(plan);
-  const size_t bytes = sizeof(double) * (size_t)p->nr * p->nth * p->nphi;
+  sp::Plan& P = *reinterpret_cast<sp::Plan*>(plan);
+  const size_t bytes = sizeof(double) * (size_t)P.nr * P.nth * P.nphi;
   const char* a = reinterpret_cast<const char*>(phi);
   const char* b = reinterpret_cast<const char*>(out);
   if (a < b + bytes && b < a + bytes) return SP_ERR_INVALID_ARG;
-  const size_t shell = align256(sizeof(double) * (size_t)p->mh * 2 * p->nth);
+  const size_t shell = align256(sizeof(double) * (size_t)P.mh * 2 * P.nth);
   if (2 * shell > kNoAllocScratchBytes) return SP_ERR_UNSUPPORTED;
 
   int prev = -1;
   if (cudaGetDevice(&prev) != cudaSuccess) return SP_ERR_CUDA;
-  if (prev != p->device && cudaSetDevice(p->device) != cudaSuccess) return SP_ERR_CUDA;
+  if (prev != P.device && cudaSetDevice(P.device) != cudaSuccess) return SP_ERR_CUDA;
   void* base = nullptr;
-  int st = scratch_address(p->device, &base);
+  int st = scratch_address(P.device, &base);
   if (st == SP_OK) {
-    // the plan's tables with the outer-shell buffers pointed at the static scratch
-    sp::Plan q = *p;
-    q.shell = static_cast<double*>(base);
-    q.shell2 = reinterpret_cast<double*>(static_cast<char*>(base) + shell);
+    double* shell_a = static_cast<double*>(base);
+    double* shell_b = reinterpret_cast<double*>(static_cast<char*>(base) + shell);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cudaError_t e = sp::stencil_f64(q, phi, out, s);
-    if (e == cudaSuccess && q.outer_bc == SP_OUTER_MULTIPOLE) e = sp::outer_term_f64(q, phi, out, s);
+    // the same launches as sp_apply_laplacian, counted and timed on the plan
+    cudaError_t e = sp::timed_launch(P, sp::kKStencil, s, [&] { return sp::stencil_f64(P, phi, out, s); });
+    if (e == cudaSuccess && P.outer_bc == SP_OUTER_MULTIPOLE) {
+      // FFT of the last shell, kappa in the eigenbasis, inverse FFT accumulated into out
+      const size_t off = (size_t)(P.nr - 1) * P.nth * P.nphi;
+      e = sp::timed_launch(P, sp::kKOuter, s, [&] {
+        cudaError_t r = sp::fft_forward_f64(P, phi + off, 1, 1.0 / P.nphi, shell_a, s);
+        if (r == cudaSuccess) r = sp::shell_kappa_f64(P, shell_a, shell_b, s);
+        if (r == cudaSuccess) r = sp::fft_inverse_f64(P, shell_b, 1, out + off, true, s);
+        return r;
+      });
+      P.launches += 2;
+    }
     if (e != cudaSuccess) st = SP_ERR_CUDA;
   }
-  if (prev != p->device) cudaSetDevice(prev);
+  if (prev != P.device) cudaSetDevice(prev);
   return st;
 }

@@ -1,5 +1,6 @@
 // Host side of the C ABI: validation, the geometry of Sect. 3.1, the per-plan tables,
 // workspace management and the float64 solve sequence of Sect. 3.2.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <mutex>
@@ -87,6 +88,8 @@ void free_tables(Plan* p) {
     cudaFree(p->d_outer);
     cudaFree(p->d_HtW);
     cudaFree(p->d_H);
+    cudaFree(p->d_HtWp);
+    cudaFree(p->d_Hp);
     cudaFree(p->d_oshell);
     if (p->mixed) sp::mixed_free_shared(*p->mixed);
     delete p->table_refs;
@@ -138,16 +141,18 @@ int solve_fp64(Plan* p, const double* rho, double* phi, cudaStream_t s) {
   if ((st = launch_status(sp::timed_launch(P, sp::kKFftFwd, s, [&] {
          return sp::fft_forward_f64(P, rho, nr, 4.0 * kPi * P.G / P.nphi, P.specA, s); }))))
     return st;
-  // (2) s_hat = (H^T W)_m s_tilde
+  // (2) s_hat = (H^T W)_m s_tilde (parity grids: two half-size products on the folded spectrum)
   if ((st = launch_status(sp::timed_launch(P, sp::kKGemmFwd, s, [&] {
-         return sp::gemm_nt_f64(P.d_HtW, P.specA, P.specB, mh, nth, 2 * nr, nth, s); }))))
+         return P.parity ? sp::gemm_parity_f64(P.d_HtWp, P.specA, P.specB, mh, nth / 2, 2 * nr, false, s)
+                         : sp::gemm_nt_f64(P.d_HtW, P.specA, P.specB, mh, nth, 2 * nr, nth, s); }))))
     return st;
   // (3) radial solves per (l,m)
   if ((st = launch_status(sp::timed_launch(P, sp::kKThomas, s, [&] { return sp::thomas_f64(P, P.specB, s); }))))
     return st;
-  // (4) g = H_m f
+  // (4) g = H_m f (parity grids: two half-size products, then g(j), g(Ntheta-1-j) = g_even +- g_odd)
   if ((st = launch_status(sp::timed_launch(P, sp::kKGemmInv, s, [&] {
-         return sp::gemm_nt_f64(P.d_H, P.specB, P.specA, mh, nth, 2 * nr, nth, s); }))))
+         return P.parity ? sp::gemm_parity_f64(P.d_Hp, P.specB, P.specA, mh, nth / 2, 2 * nr, true, s)
+                         : sp::gemm_nt_f64(P.d_H, P.specB, P.specA, mh, nth, 2 * nr, nth, s); }))))
     return st;
   // (5) Phi = inverse FFT
   return launch_status(sp::timed_launch(P, sp::kKFftInv, s, [&] {
@@ -640,7 +645,9 @@ int sp_plan_create(const double* r_if, int nr, const double* th_if_in, int nth, 
         cudaMalloc(&p->d_outer, sizeof(double) * tab) != cudaSuccess ||
         cudaMalloc(&p->d_HtW, sizeof(double) * mat) != cudaSuccess ||
         cudaMalloc(&p->d_H, sizeof(double) * mat) != cudaSuccess ||
-        cudaMalloc(&p->d_err, sizeof(int)) != cudaSuccess) {
+        cudaMalloc(&p->d_err, sizeof(int)) != cudaSuccess ||
+        (p->parity && (cudaMalloc(&p->d_HtWp, sizeof(double) * mat / 2) != cudaSuccess ||
+                       cudaMalloc(&p->d_Hp, sizeof(double) * mat / 2) != cudaSuccess))) {
       st = SP_ERR_OOM;
       break;
     }
@@ -775,6 +782,7 @@ int sp_solve_host(sp_plan* plan, const double* rho_host, double* phi_host, void*
 }
 
 int sp_apply_laplacian(sp_plan* plan, const double* phi, double* out, void* stream) {
+  cudaGetLastError();   // an earlier failed call of this thread is not this call's error
   if (!plan || !phi || !out) return SP_ERR_INVALID_ARG;
   Plan* p = reinterpret_cast<Plan*>(plan);
   const size_t bytes = sizeof(double) * (size_t)p->nr * p->nth * p->nphi;
@@ -842,10 +850,27 @@ int sp_plan_get_eigen(const sp_plan* plan, double* lambda, double* H, double* ka
   const Plan* p = reinterpret_cast<const Plan*>(plan);
   DeviceGuard guard(p->device);
   SP_CUDA(cudaDeviceSynchronize());
-  const size_t tab = (size_t)p->mh * p->nth;
-  if (lambda) SP_CUDA(cudaMemcpy(lambda, p->d_lam, sizeof(double) * tab, cudaMemcpyDeviceToHost));
-  if (kappa) SP_CUDA(cudaMemcpy(kappa, p->d_kappa, sizeof(double) * tab, cudaMemcpyDeviceToHost));
-  if (H) SP_CUDA(cudaMemcpy(H, p->d_H, sizeof(double) * tab * p->nth, cudaMemcpyDeviceToHost));
+  const int nth = p->nth;
+  const size_t tab = (size_t)p->mh * nth;
+  std::vector<double> lam(tab), kap(tab), hm(H ? tab * nth : 0);
+  SP_CUDA(cudaMemcpy(lam.data(), p->d_lam, sizeof(double) * tab, cudaMemcpyDeviceToHost));
+  SP_CUDA(cudaMemcpy(kap.data(), p->d_kappa, sizeof(double) * tab, cudaMemcpyDeviceToHost));
+  if (H) SP_CUDA(cudaMemcpy(hm.data(), p->d_H, sizeof(double) * tab * nth, cudaMemcpyDeviceToHost));
+  // the plan's own mode order (even then odd modes on parity grids) -> descending lambda
+  std::vector<int> order(nth);
+  for (int m = 0; m < p->mh; ++m) {
+    const double* lm = lam.data() + (size_t)m * nth;
+    for (int l = 0; l < nth; ++l) order[l] = l;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return lm[a] > lm[b]; });
+    for (int l = 0; l < nth; ++l) {
+      if (lambda) lambda[(size_t)m * nth + l] = lm[order[l]];
+      if (kappa) kappa[(size_t)m * nth + l] = kap[(size_t)m * nth + order[l]];
+    }
+    if (H)
+      for (int j = 0; j < nth; ++j)
+        for (int l = 0; l < nth; ++l)
+          H[((size_t)m * nth + j) * nth + l] = hm[((size_t)m * nth + j) * nth + order[l]];
+  }
   return SP_OK;
 }
 
@@ -878,7 +903,8 @@ namespace sp {
 // Device bytes of the tables a plan shares with its clones.
 size_t plan_table_bytes(const Plan& p) {
   const size_t tab = (size_t)p.mh * p.nth;
-  size_t b = (p.d_oshell ? 3 : 2) * tab * p.nth * sizeof(double) + 3 * tab * sizeof(double) + (size_t)p.nr * sizeof(RadialRow) +
+  size_t b = ((p.d_oshell ? 3 : 2) + (p.d_HtWp ? 1 : 0)) * tab * p.nth * sizeof(double) + 3 * tab * sizeof(double) +
+             (size_t)p.nr * sizeof(RadialRow) +
              (size_t)p.nth * sizeof(ThetaRow) + 2 * (size_t)p.nphi * (sizeof(double) + sizeof(float)) + tab * sizeof(double);
   if (p.mixed) {
     const MixedTables& x = *p.mixed;

@@ -76,6 +76,21 @@ def test_solve_nonuniform_theta(S):
     assert rel_err(phi, ref) <= TOL
 
 
+@pytest.mark.parametrize("nr,nth,nphi", [(12, 10, 16), (20, 64, 32), (9, 160, 8), (6, 2, 6)])
+def test_solve_symmetric_nonuniform_theta(S, nr, nth, nphi):
+    """A non-uniform theta grid that is mirror-symmetric about the equator takes the
+    parity-split projections of Sect. 4.2 (two half-size products per m on the folded
+    spectrum; Ntheta = 160 has two row tiles of its 80-row halves)."""
+    p = W.random_small(nr, nth, nphi, seed=nr + nth, grid="log")
+    p.th_if = W.symmetric_theta_interfaces(nth, seed=nth)
+    _, phi, _ = gpu_solve(S, p)
+    geo = O.Geometry(p.r_if, p.th_if, p.nphi)
+    ref = O.solve_exact(geo, p.rho)
+    assert rel_err(phi, ref) <= TOL
+    eta, _ = O.residuals(geo, phi, p.rho)
+    assert eta <= TOL
+
+
 @pytest.mark.parametrize("make", [W.sphere_blob, W.stellar_noise])
 def test_solve_matches_oracle_workloads(S, make):
     p = make()

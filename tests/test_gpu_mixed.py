@@ -50,6 +50,8 @@ CASES = [
     (130, 128, 24, "log", 0.0, 0),     # full M tile, ragged N tile
     (300, 96, 192, "log", 0.0, 0),     # radix-3 phi, partial second K block
     (70, 16, 324, "rand", 0.0, 0),     # 163 m x 2 column tiles over one CTA per SM: table reloads mid-range
+    (70, 32, 324, "rand", 0.0, 0),     # even/odd mode order of a symmetric grid, table reloads mid-range
+    (90, 96, 12, "log", 0.3, 1),       # inner zero-flux face, Dirichlet, partial second K block
     (257, 64, 8, "uniform", 0.0, 1),
     (1600, 6, 4, "log", 0.0, 0),       # radial column beyond the shared-memory scan: ring-staged sweeps
     (4, 4, 1, "uniform", 0.0, 0),      # axisymmetric: one phi zone
@@ -96,6 +98,25 @@ def test_mixed_matches_exact_small(S, nr, nth, nphi, grid, rin, bc, mode):
     phi64, _ = plan64.solve(torch.from_numpy(np.ascontiguousarray(p.rho)).cuda())
     floor = max(128 * rel_err(phi64.cpu().numpy(), ref), 1e-12)
     assert rel_err(phi, ref) <= max(info.est_rel_error, floor)
+
+
+@pytest.mark.parametrize("mode", ["x3", "x6"])
+@pytest.mark.parametrize("nr,nth,nphi,sym", [(40, 64, 48, True), (24, 10, 16, True), (30, 12, 32, False),
+                                              (50, 128, 16, True)])
+def test_mixed_nonuniform_theta(S, nr, nth, nphi, sym, mode):
+    """Non-uniform theta grids (Sect. 3.1 does not require uniform theta) through the
+    mixed path, mirror-symmetric ones (eigenbasis from the parity-split eigensolve, modes
+    in even/odd order) and asymmetric ones."""
+    p = W.random_small(nr, nth, nphi, seed=nr + nth + nphi, grid="log")
+    p.th_if = W.symmetric_theta_interfaces(nth, seed=nth) if sym else W.random_theta_interfaces(nth, seed=nth)
+    prec = S.SP_MIXED_BF16X3 if mode == "x3" else S.SP_MIXED_BF16X6
+    _, phi, info = mixed_solve(S, p, precision=prec)
+    geo = O.Geometry(p.r_if, p.th_if, p.nphi)
+    ref = O.solve_exact(geo, p.rho)
+    assert info.status == S.SP_OK
+    assert rel_err(phi, ref) <= TOL
+    eta, _ = O.residuals(geo, phi, p.rho)
+    assert eta <= 1e-12
 
 
 @pytest.mark.parametrize("mode", ["x3", "x6"])

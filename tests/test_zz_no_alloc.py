@@ -1,6 +1,6 @@
 """sp_apply_laplacian_noalloc: the operator for callers that cannot allocate device memory
 (code that must not synchronise the device, or that runs inside a host framework owning
-a fixed memory pool).  It must give the same result as sp_apply_laplacian, call after
+a fixed memory pool).  It must give bitwise the result of sp_apply_laplacian, call after
 call, while drawing its scratch from the library's fixed 4 MiB device array.
 
 This file is collected last on purpose, so a run that stops at the first failure has
@@ -32,11 +32,13 @@ def _call_noalloc(S, plan, phi, out):
                                               C.c_void_p(out.data_ptr()), C.c_void_p(stream))
 
 
-@pytest.mark.parametrize("shape,bc", [((33, 17, 48), 0), ((128, 64, 128), 0), ((20, 16, 32), 1)])
-def test_noalloc_matches_apply_laplacian_twice(S, shape, bc):
+@pytest.mark.parametrize("shape,bc,precision", [((33, 17, 48), 0, 0), ((128, 64, 128), 0, 0), ((20, 16, 32), 1, 0),
+                                              ((24, 16, 32), 0, 2)])
+def test_noalloc_matches_apply_laplacian_twice(S, shape, bc, precision):
     nr, nth, nphi = shape
     p = W.random_small(nr, nth, nphi, seed=7, grid="log", outer_bc=bc)
-    plan = S.Plan(p.r_if, p.th_if, p.nphi, outer_bc=bc)
+    kw = dict(precision=precision, tol=1e-10) if precision else {}
+    plan = S.Plan(p.r_if, p.th_if, p.nphi, outer_bc=bc, **kw)
     rng = np.random.default_rng(11)
     for call in range(2):
         phi = torch.from_numpy(rng.standard_normal(shape)).cuda()
@@ -44,12 +46,14 @@ def test_noalloc_matches_apply_laplacian_twice(S, shape, bc):
         out = torch.full_like(phi, float("nan"))
         torch.cuda.synchronize()
         free_before = torch.cuda.mem_get_info()[0]
+        launches = plan.launch_count()
         assert _call_noalloc(S, plan, phi, out) == S.SP_OK
         torch.cuda.synchronize()
         if call == 1:   # after the first call's one-time set-up nothing is allocated
             assert torch.cuda.mem_get_info()[0] == free_before
-        scale = float(torch.max(torch.abs(ref)))
-        assert float(torch.max(torch.abs(out - ref))) <= 1e-14 * scale
+        # the same launches as sp_apply_laplacian, counted on the plan
+        assert plan.launch_count() - launches == (1 if bc == 1 else 4)
+        assert torch.equal(out, ref)
 
 
 def test_noalloc_full_size_workload(S):
@@ -61,8 +65,27 @@ def test_noalloc_full_size_workload(S):
         out = torch.empty_like(phi)
         assert _call_noalloc(S, plan, phi, out) == S.SP_OK
         torch.cuda.synchronize()
-        scale = float(torch.max(torch.abs(ref)))
-        assert float(torch.max(torch.abs(out - ref))) <= 1e-14 * scale
+        assert torch.equal(out, ref)
+
+
+def test_noalloc_near_its_scratch_limit(S):
+    # (2048/2+1) x 2 x 127 doubles, 256-byte aligned, twice: 4,165,632 of the 4,194,304 bytes
+    p = W.random_small(3, 127, 2048, seed=2, grid="log")
+    plan = S.Plan(p.r_if, p.th_if, p.nphi)
+    rng = np.random.default_rng(5)
+    for _ in range(2):
+        phi = torch.from_numpy(rng.standard_normal(p.rho.shape)).cuda()
+        ref = plan.apply_laplacian(phi)
+        out = torch.full_like(phi, float("nan"))
+        assert _call_noalloc(S, plan, phi, out) == S.SP_OK
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref)
+    # one more theta zone: (1025 x 2 x 128 doubles) x 2 = 4,198,400 bytes, over the limit
+    q = W.random_small(3, 128, 2048, seed=2, grid="log")
+    plan2 = S.Plan(q.r_if, q.th_if, q.nphi)
+    x = torch.zeros(q.rho.shape, dtype=torch.float64, device="cuda")
+    y = torch.zeros_like(x)
+    assert _call_noalloc(S, plan2, x, y) == S.SP_ERR_UNSUPPORTED
 
 
 def test_noalloc_rejects_plans_beyond_its_scratch(S):

@@ -288,6 +288,20 @@ def random_theta_interfaces(nth, seed=0) -> np.ndarray:
     return np.concatenate([[0.0], np.cumsum(d) / d.sum() * math.pi])
 
 
+def symmetric_theta_interfaces(nth, seed=0) -> np.ndarray:
+    """Non-uniform polar interfaces from 0 to pi, mirror-symmetric about the equator
+    (theta_j + theta_{nth-j} = pi exactly); nth must be even."""
+    if nth % 2:
+        raise ValueError("a mirror-symmetric grid needs an even number of zones")
+    rng = np.random.default_rng(seed)
+    d = rng.uniform(0.6, 1.4, nth // 2)
+    half = np.cumsum(d) / d.sum() * (0.5 * math.pi)
+    lower = np.concatenate([[0.0], half[:-1]])
+    th = np.concatenate([lower, [0.5 * math.pi], (math.pi - lower[::-1])])
+    th[-1] = math.pi
+    return th
+
+
 CONFIGS = {
     "sphere_blob": sphere_blob,
     "stellar_noise": stellar_noise,
