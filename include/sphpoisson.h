@@ -177,6 +177,26 @@ int sp_apply_laplacian(sp_plan* plan, const double* phi_dev, double* out_dev, vo
  *  phi_dev, out_dev  device, Nr*Ntheta*Nphi float64; must not overlap */
 int sp_apply_laplacian_noalloc(sp_plan* plan, const double* phi_dev, double* out_dev, void* stream);
 
+/* Gradient of Phi on every cell face, in float64: the gradients whose fluxes make up the
+ * finite-volume operator of Eq. (fin_vol0)-(fin_vol3), so that their discrete divergence
+ * (outward face area x gradient, over the cell volume, Sect. 3.1) is exactly (Delta Phi).
+ * The gravitational acceleration is minus these; taken from the exact potential of
+ * sp_solve they give the momentum-conserving gravity source terms the paper's
+ * introduction (Sect. 1) names as a use of an exact solver.
+ *  g_r_dev      device, (Nr+1)*Ntheta*Nphi: face i (i = 0..Nr) between cells i-1 and i,
+ *               (Phi_i - Phi_{i-1})/(r_i - r_{i-1}); face 0 is zero (zero flux through
+ *               r_{1/2}); face Nr is the outer boundary condition's gradient (multipole:
+ *               kappa applied to the last shell in the theta/phi eigenbasis; Dirichlet:
+ *               -Phi_N/(r_{N+1/2} - r_N))
+ *  g_theta_dev  device, Nr*(Ntheta+1)*Nphi: face j between polar cells j-1 and j,
+ *               (Phi_j - Phi_{j-1})/(r_i (theta_j - theta_{j-1})); zero at the poles
+ *  g_phi_dev    device, Nr*Ntheta*Nphi: face k+1/2 between k and k+1 (periodic),
+ *               (Phi_{k+1} - Phi_k)/(r_i sin(theta_j) 2 pi/Nphi); zero when Nphi = 1
+ * Cell centres r_i, theta_j as everywhere (midpoints of the interfaces).  phi_dev and the
+ * three outputs must not overlap; uses the plan's workspace. */
+int sp_face_gradients(sp_plan* plan, const double* phi_dev, double* g_r_dev, double* g_theta_dev,
+                      double* g_phi_dev, void* stream);
+
 /* Copy the plan's theta eigenbasis (Sect. 3.2) to host memory, any pointer may be NULL:
  *  lambda   (Nphi/2+1) x Ntheta: lambda_Omega,l,m, row m, descending in l
  *  H        (Nphi/2+1) x Ntheta x Ntheta: H[m][j][l] = H_{l,m}(j), W-orthonormal

@@ -381,6 +381,52 @@ def outer_kappa_separated(geo: Geometry, u):
     return np.fft.irfft(out * geo.nphi, n=geo.nphi, axis=-1)
 
 
+# ------------------------------------------- gravitational acceleration (Sect. 1)
+def face_gradients(geo: Geometry, phi, outer_bc=OUTER_MULTIPOLE, kmat=None):
+    """Gradient of Phi on every cell face, as the finite-volume operator of Eq.
+    fin_vol3 uses it in its fluxes (the gravitational acceleration is minus this):
+
+    * radial faces i = 0..Nr (face i between cells i-1 and i): (Phi_i - Phi_{i-1}) /
+      (r_i - r_{i-1}); zero at r_{1/2} (R9); the outer face carries the boundary
+      condition's gradient (R6).  Shape (Nr+1, Ntheta, Nphi).
+    * theta faces j = 0..Ntheta: (Phi_j - Phi_{j-1}) / (r_i (theta_j - theta_{j-1})),
+      zero at the poles.  Shape (Nr, Ntheta+1, Nphi).
+    * phi faces k+1/2 (between k and k+1, periodic): (Phi_{k+1} - Phi_k) /
+      (r_i sin(theta_j) dphi).  Shape (Nr, Ntheta, Nphi).
+    Cell centres r_i, theta_j as in R8."""
+    phi = np.asarray(phi, dtype=np.float64)
+    nr, nth, nphi = phi.shape
+    gr = np.zeros((nr + 1, nth, nphi))
+    if nr > 1:
+        gr[1:-1] = (phi[1:] - phi[:-1]) / (geo.rc[1:] - geo.rc[:-1])[:, None, None]
+    gr[-1] = outer_gradient(geo, phi[-1], outer_bc, kmat)
+    gt = np.zeros((nr, nth + 1, nphi))
+    if nth > 1:
+        gt[:, 1:-1, :] = ((phi[:, 1:, :] - phi[:, :-1, :])
+                          / (geo.rc[:, None, None] * (geo.thc[1:] - geo.thc[:-1])[None, :, None]))
+    gp = np.zeros((nr, nth, nphi))
+    if nphi > 1:
+        gp = (np.roll(phi, -1, axis=2) - phi) / (geo.rc[:, None, None] * geo.sin_c[None, :, None] * geo.dphi)
+    return gr, gt, gp
+
+
+def face_divergence(geo: Geometry, gr, gt, gp):
+    """Discrete divergence of face-centred vector components: the sum over a cell's
+    faces of (outward area x component), divided by the cell volume (the areas and
+    volumes of Sect. 3.1)."""
+    nr, nth, nphi = gp.shape
+    r2 = geo.r_if ** 2
+    area_r = r2[:, None] * geo.w[None, :] * geo.dphi                          # (Nr+1, Nth)
+    half_r2 = 0.5 * (geo.r_if[1:] ** 2 - geo.r_if[:-1] ** 2)                  # (Nr,)
+    area_t = half_r2[:, None] * geo.sin_if[None, :] * geo.dphi                 # (Nr, Nth+1)
+    area_p = half_r2[:, None] * geo.dth[None, :]                               # (Nr, Nth)
+    vol = geo.cell_volume()[:, :, None]
+    div = (area_r[1:, :, None] * gr[1:] - area_r[:-1, :, None] * gr[:-1])
+    div = div + (area_t[:, 1:, None] * gt[:, 1:, :] - area_t[:, :-1, None] * gt[:, :-1, :])
+    div = div + area_p[:, :, None] * (gp - np.roll(gp, 1, axis=2))
+    return div / vol
+
+
 # ------------------------------------------------------- closed forms (pins)
 def gauss_law_potential(geo: Geometry, rho_r, G=1.0, outer_bc=OUTER_MULTIPOLE):
     """Exact discrete solution for a spherically symmetric source rho(r_i), from the

@@ -79,6 +79,7 @@ _SIGS = {
     "sp_apply_laplacian": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "sp_apply_laplacian_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "sp_plan_get_eigen": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sp_face_gradients": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "sp_plan_last_status": (C.c_int, [C.c_void_p]),
     "sp_plan_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "sp_plan_collect_timing": (C.c_int, [C.c_void_p]),
@@ -261,6 +262,14 @@ def sp_apply_laplacian(plan, phi, out, shape, stream=None):
                                     _stream_ptr(stream, phi.device)), "sp_apply_laplacian")
 
 
+def sp_face_gradients(plan, phi, g_r, g_theta, g_phi, shape, stream=None):
+    nr, nth, nphi = shape
+    n = nr * nth * nphi
+    _check(lib().sp_face_gradients(plan, _dev_ptr(phi, n, "phi"), _dev_ptr(g_r, n + nth * nphi, "g_r"),
+                                   _dev_ptr(g_theta, n + nr * nphi, "g_theta"), _dev_ptr(g_phi, n, "g_phi"),
+                                   _stream_ptr(stream, phi.device)), "sp_face_gradients")
+
+
 def sp_apply_laplacian_noalloc(plan, phi, out, shape, stream=None):
     """sp_apply_laplacian for callers that cannot allocate device memory: its scratch is
     a fixed 4 MiB array in the library (see include/sphpoisson.h)."""
@@ -363,6 +372,17 @@ class Plan:
             out = torch.empty_like(phi)
         sp_apply_laplacian(self._h, phi, out, self.shape, stream)
         return out
+
+    def face_gradients(self, phi, stream=None):
+        """(g_r, g_theta, g_phi) face gradients of phi; the acceleration is minus these."""
+        import torch
+        nr, nth, nphi = self.shape
+        kw = dict(dtype=torch.float64, device=phi.device)
+        g_r = torch.empty((nr + 1, nth, nphi), **kw)
+        g_t = torch.empty((nr, nth + 1, nphi), **kw)
+        g_p = torch.empty((nr, nth, nphi), **kw)
+        sp_face_gradients(self._h, phi, g_r, g_t, g_p, self.shape, stream)
+        return g_r, g_t, g_p
 
     def eigen(self):
         return sp_plan_get_eigen(self._h, self.mh, self.shape[1])

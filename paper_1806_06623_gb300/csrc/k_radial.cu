@@ -124,7 +124,60 @@ __global__ void __launch_bounds__(32 * kShellRows) k_shell_apply(const double* _
   }
 }
 
+// Face gradients (minus the gravitational acceleration) of Eq. fin_vol3's fluxes: one
+// thread per cell writes the gradient on its inner radial face i, its lower polar face j
+// (and the pole face j = Ntheta after the last row) and its azimuthal face k+1/2.  The
+// outer radial face (index nr) holds on entry the multipole term O_m Phi_last computed by
+// the shell transforms (scaled here by 1/outer_coef), or is set from the Dirichlet
+// condition.
+__global__ void __launch_bounds__(256) k_face_grad(const double* __restrict__ phi, double* __restrict__ gr,
+                                                   double* __restrict__ gt, double* __restrict__ gp,
+                                                   const FaceCoef* __restrict__ fr, const FaceCoef* __restrict__ ft,
+                                                   int nr, int nth, int nphi, int dirichlet, double outer_scale) {
+  const size_t n = (size_t)nr * nth * nphi;
+  const size_t shell = (size_t)nth * nphi;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(idx % nphi);
+    const size_t ij = idx / nphi;
+    const int j = (int)(ij % nth);
+    const int i = (int)(ij / nth);
+    const double c = phi[idx];
+    const FaceCoef r = fr[i];
+    const FaceCoef t = ft[j];
+    gr[idx] = i > 0 ? (c - phi[idx - shell]) * r.inv_d : 0.0;
+    if (i == nr - 1) {
+      double* o = gr + idx + shell;   // outer face
+      *o = dirichlet ? -c * outer_scale : *o * outer_scale;
+    }
+    const size_t tix = ((size_t)i * (nth + 1) + j) * nphi + k;
+    gt[tix] = j > 0 ? (c - phi[idx - nphi]) * r.inv_c * t.inv_d : 0.0;
+    if (j == nth - 1) gt[tix + nphi] = 0.0;
+    const size_t kp = (k + 1 == nphi) ? idx - k : idx + 1;
+    gp[idx] = (phi[kp] - c) * r.inv_c * t.inv_c;
+  }
+}
+
 }  // namespace
+
+cudaError_t face_gradients_f64(const Plan& p, const double* phi, double* gr, double* gt, double* gp, cudaStream_t s) {
+  const bool dir = p.outer_bc == SP_OUTER_DIRICHLET;
+  const size_t off = (size_t)(p.nr - 1) * p.nth * p.nphi;
+  const size_t sh = (size_t)p.nth * p.nphi;
+  cudaError_t e;
+  if (!dir) {
+    // O_m phi_last = outer_coef x kappa(A_Omega) phi_last into the outer face
+    if ((e = fft_forward_f64(p, phi + off, 1, 1.0 / p.nphi, p.shell, s)) != cudaSuccess) return e;
+    if ((e = shell_kappa_f64(p, p.shell, p.shell2, s)) != cudaSuccess) return e;
+    if ((e = fft_inverse_f64(p, p.shell2, 1, gr + off + sh, false, s)) != cudaSuccess) return e;
+  }
+  const size_t n = (size_t)p.nr * p.nth * p.nphi;
+  size_t blocks = (n + 255) / 256;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  const double scale = dir ? 1.0 / (p.r_out - p.r_last) : 1.0 / p.outer_coef;
+  k_face_grad<<<(unsigned)blocks, 256, 0, s>>>(phi, gr, gt, gp, p.d_face_r, p.d_face_t, p.nr, p.nth, p.nphi,
+                                               dir ? 1 : 0, scale);
+  return cudaGetLastError();
+}
 
 cudaError_t thomas_f64(const Plan& p, double* x, cudaStream_t s) {
   const int n = p.mh * p.nth;

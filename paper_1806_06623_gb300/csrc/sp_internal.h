@@ -50,6 +50,13 @@ struct ThetaRow {
   double tp, tm, sphi, pad;
 };
 
+// Face-gradient coefficients (gravitational acceleration): radial row i holds
+// 1/(r_i - r_{i-1}) (0 for i = 0) and 1/r_i; polar row j holds 1/(theta_j - theta_{j-1})
+// (0 for j = 0) and 1/(sin(theta_j) dphi) (0 when Nphi = 1), centres as in the operator.
+struct FaceCoef {
+  double inv_d, inv_c;
+};
+
 // float copy of RadialRow for the float32 radial solves
 struct RadialRowF {
   float sub, sup, R, base;
@@ -135,6 +142,8 @@ struct Plan {
   double* d_HtWp = nullptr;       // parity grids: [mh][2][h][h] (H^T W)_m,p[l][j], h = nth/2, p = even/odd
   double* d_Hp = nullptr;         // parity grids: [mh][2][h][h] H_m,p[j][l]
   double* d_oshell = nullptr;     // [mh][j][j'] H_m diag(outer_m) (H^T W)_m (multipole only)
+  FaceCoef* d_face_r = nullptr;   // [nr] radial face-gradient coefficients
+  FaceCoef* d_face_t = nullptr;   // [nth] polar face-gradient coefficients
   int* d_err = nullptr;           // device status word
 
   // workspace (plan-owned or caller-provided)
@@ -257,6 +266,9 @@ cudaError_t outer_term_f64(const Plan& p, const double* phi, double* out, cudaSt
 // out[m] = H_m diag(outer[m]) (H^T W)_m in[m] for the two real columns of one shell spectrum.
 cudaError_t shell_kappa_f64(const Plan& p, const double* in, double* out, cudaStream_t s);
 cudaError_t outer_operator_f64(const Plan& p, cudaStream_t s);
+// Face gradients of phi (radial [nr+1][nth][nphi], polar [nr][nth+1][nphi], azimuthal
+// [nr][nth][nphi]); the outer radial face carries the boundary condition's gradient.
+cudaError_t face_gradients_f64(const Plan& p, const double* phi, double* gr, double* gt, double* gp, cudaStream_t s);
 // theta eigensolve for every m; writes lam, kappa, outer, H, HtW.
 cudaError_t theta_eigen(const Plan& p, cudaStream_t s);
 

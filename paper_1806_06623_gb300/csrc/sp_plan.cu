@@ -91,6 +91,8 @@ void free_tables(Plan* p) {
     cudaFree(p->d_HtWp);
     cudaFree(p->d_Hp);
     cudaFree(p->d_oshell);
+    cudaFree(p->d_face_r);
+    cudaFree(p->d_face_t);
     if (p->mixed) sp::mixed_free_shared(*p->mixed);
     delete p->table_refs;
   }
@@ -599,6 +601,11 @@ int sp_plan_create(const double* r_if, int nr, const double* th_if_in, int nth, 
     const double S = dth[j] / (sinc[j] * w[j]);
     thr[j] = {tp, tm, (nphi > 1) ? S / (dphi * dphi) : 0.0, 0.0};
   }
+  // face-gradient coefficients (the operator's own centres and spacings)
+  std::vector<sp::FaceCoef> face_r(nr), face_t(nth);
+  for (int i = 0; i < nr; ++i) face_r[i] = {i > 0 ? 1.0 / (rc[i] - rc[i - 1]) : 0.0, 1.0 / rc[i]};
+  for (int j = 0; j < nth; ++j)
+    face_t[j] = {j > 0 ? 1.0 / (thc[j] - thc[j - 1]) : 0.0, nphi > 1 ? 1.0 / (sinc[j] * dphi) : 0.0};
   // T_m = W^-1/2 B_m W^-1/2: diag (B_jj)/w_j, offdiag t_{j+1/2}/sqrt(w_j w_{j+1})
   const int mh = p->mh;
   std::vector<double> tdiag((size_t)mh * nth), toff(nth, 0.0), sqw(nth);
@@ -638,6 +645,8 @@ int sp_plan_create(const double* r_if, int nr, const double* th_if_in, int nth, 
     if ((st = upload(&p->d_tdiag, tdiag.data(), tdiag.size()))) break;
     if ((st = upload(&p->d_toff, toff.data(), toff.size()))) break;
     if ((st = upload(&p->d_sqw, sqw.data(), sqw.size()))) break;
+    if ((st = upload(&p->d_face_r, face_r.data(), face_r.size()))) break;
+    if ((st = upload(&p->d_face_t, face_t.data(), face_t.size()))) break;
     const size_t tab = (size_t)mh * nth;
     const size_t mat = tab * nth;
     if (cudaMalloc(&p->d_lam, sizeof(double) * tab) != cudaSuccess ||
@@ -791,6 +800,31 @@ int sp_apply_laplacian(sp_plan* plan, const double* phi, double* out, void* stre
   int st = ensure_workspace(p);
   if (st) return st;
   return apply_laplacian_impl(p, phi, out, static_cast<cudaStream_t>(stream));
+}
+
+int sp_face_gradients(sp_plan* plan, const double* phi, double* g_r, double* g_theta, double* g_phi, void* stream) {
+  cudaGetLastError();   // an earlier failed call of this thread is not this call's error
+  if (!plan || !phi || !g_r || !g_theta || !g_phi) return SP_ERR_INVALID_ARG;
+  Plan* p = reinterpret_cast<Plan*>(plan);
+  const size_t cells = (size_t)p->nr * p->nth * p->nphi;
+  const size_t b = sizeof(double) * cells;
+  const size_t br = sizeof(double) * (cells + (size_t)p->nth * p->nphi);
+  const size_t bt = sizeof(double) * (cells + (size_t)p->nr * p->nphi);
+  auto ov = [](const void* a, size_t na, const void* c, size_t nc) {
+    const char* x = static_cast<const char*>(a);
+    const char* y = static_cast<const char*>(c);
+    return x < y + nc && y < x + na;
+  };
+  if (ov(phi, b, g_r, br) || ov(phi, b, g_theta, bt) || ov(phi, b, g_phi, b) || ov(g_r, br, g_theta, bt) ||
+      ov(g_r, br, g_phi, b) || ov(g_theta, bt, g_phi, b))
+    return SP_ERR_INVALID_ARG;
+  DeviceGuard guard(p->device);
+  int st = ensure_workspace(p);
+  if (st) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st = launch_status(sp::timed_launch(*p, sp::kKStencil, s, [&] { return sp::face_gradients_f64(*p, phi, g_r, g_theta, g_phi, s); }));
+  if (p->outer_bc == SP_OUTER_MULTIPOLE) p->launches += 3;   // the outer face's shell transforms
+  return st;
 }
 
 int sp_plan_set_graphs(sp_plan* plan, int enable) {

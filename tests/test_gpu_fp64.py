@@ -204,3 +204,63 @@ def test_solve_host_mixed_equals_device(pinned):
         phi_np[:] = 0.0
         plan.solve_host(rho_np, phi_np)
         assert np.array_equal(phi_np, ref)
+
+
+@pytest.mark.parametrize("nr,nth,nphi,grid,rin,bc", [CASES[0], CASES[2], CASES[3], CASES[4], CASES[5], CASES[7],
+                                                      CASES[8]])
+def test_face_gradients_match_oracle(S, nr, nth, nphi, grid, rin, bc):
+    """Face gradients (minus the gravitational acceleration) against the oracle's, both
+    outer conditions; their discrete divergence is the operator itself."""
+    p = W.random_small(nr, nth, nphi, seed=9, grid=grid, r_inner=rin, outer_bc=bc)
+    plan = S.Plan(p.r_if, p.th_if, p.nphi, outer_bc=bc)
+    phi = np.random.default_rng(4).standard_normal(p.rho.shape)
+    got = [g.cpu().numpy() for g in plan.face_gradients(torch.from_numpy(phi).cuda())]
+    geo = O.Geometry(p.r_if, p.th_if, p.nphi)
+    kmat = O.outer_operator_dense(geo) if (bc == 0 and nth * nphi <= 1200) else None
+    ref = O.face_gradients(geo, phi, bc, kmat)
+    for a, b in zip(got, ref):
+        assert a.shape == b.shape
+        assert np.max(np.abs(a - b)) <= 1e-13 * max(np.max(np.abs(b)), 1e-300)
+    div = O.face_divergence(geo, *got)
+    lap = O.apply_laplacian(geo, phi, bc, kmat)
+    assert np.max(np.abs(div - lap)) <= 1e-13 * np.max(O.abs_apply(geo, phi, bc, kmat))
+
+
+def test_acceleration_of_solved_sphere_is_enclosed_mass(S):
+    """Acceleration from the exact GPU potential of a spherical source: -G M_enc/r^2 on
+    every radial face (discrete Gauss law), no angular component."""
+    g = O.Geometry(W.log_r_interfaces(64), W.uniform_theta_interfaces(16), 32)
+    rho_r = 1.0 / (1.0 + (g.rc / 0.1) ** 2)
+    p = W.Problem("sphere", g.r_if, g.th_if, 32, np.ascontiguousarray(
+        np.broadcast_to(rho_r[:, None, None], (64, 16, 32))))
+    plan, phi, _ = gpu_solve(S, p)
+    gr, gt, gp = [x.cpu().numpy() for x in plan.face_gradients(torch.from_numpy(phi).cuda())]
+    m_enc = np.concatenate([[0.0], np.cumsum(4.0 * math.pi * rho_r * g.dv3 / 3.0)])
+    ex = np.zeros(65)
+    ex[1:] = m_enc[1:] / g.r_if[1:] ** 2
+    scale = np.max(ex)
+    assert np.max(np.abs(gr - ex[:, None, None])) <= 1e-11 * scale
+    assert np.max(np.abs(gt)) <= 1e-11 * scale and np.max(np.abs(gp)) <= 1e-11 * scale
+
+
+def test_face_gradients_full_size(S):
+    """550x128x256: sampled radial, polar and azimuthal face gradients against the
+    definition, and the outer face against the oracle's multipole gradient."""
+    p = W.stellar_sh()
+    plan = S.Plan(p.r_if, p.th_if, p.nphi)
+    phi_d = torch.from_numpy(p.rho).cuda()     # any field serves
+    gr, gt, gp = [x.cpu().numpy() for x in plan.face_gradients(phi_d)]
+    geo = O.Geometry(p.r_if, p.th_if, p.nphi)
+    phi = p.rho
+    rng = np.random.default_rng(0)
+    for _ in range(200):
+        i, j, k = int(rng.integers(1, 550)), int(rng.integers(1, 128)), int(rng.integers(0, 256))
+        a = (phi[i, j, k] - phi[i - 1, j, k]) / (geo.rc[i] - geo.rc[i - 1])
+        b = (phi[i, j, k] - phi[i, j - 1, k]) / (geo.rc[i] * (geo.thc[j] - geo.thc[j - 1]))
+        c = (phi[i, j, (k + 1) % 256] - phi[i, j, k]) / (geo.rc[i] * geo.sin_c[j] * geo.dphi)
+        assert abs(gr[i, j, k] - a) <= 1e-12 * abs(a) + 1e-300
+        assert abs(gt[i, j, k] - b) <= 1e-12 * abs(b) + 1e-300
+        assert abs(gp[i, j, k] - c) <= 1e-12 * abs(c) + 1e-300
+    outer = O.outer_gradient(geo, phi[-1], O.OUTER_MULTIPOLE)
+    assert np.max(np.abs(gr[-1] - outer)) <= 1e-12 * np.max(np.abs(outer))
+    assert np.all(gr[0] == 0.0) and np.all(gt[:, 0] == 0.0) and np.all(gt[:, -1] == 0.0)

@@ -425,3 +425,56 @@ def test_displaced_point_source_matches_paper():
     assert max(adj) <= bound
     assert 0.5 * bound <= rel.max() <= 1.5 * bound
     assert rel[d > 20 * d[i + 1, j, k]].max() < 1e-2
+
+
+# ------------------------------------------------ face gradients (acceleration)
+@pytest.mark.parametrize("bc", [O.OUTER_MULTIPOLE, O.OUTER_DIRICHLET])
+@pytest.mark.parametrize("nr,nth,nphi,grid,rin", [(5, 6, 8, "rand", 0.1), (4, 4, 1, "uniform", 0.0),
+                                                   (3, 1, 4, "log", 0.0), (6, 5, 2, "rand", 0.0)])
+def test_face_gradient_divergence_is_the_operator(nr, nth, nphi, grid, rin, bc):
+    """The face gradients are the ones the finite-volume fluxes of Eq. fin_vol3 use: their
+    discrete divergence (outward area x gradient over the cell volume, Sect. 3.1) is the
+    operator O3 itself, so accelerations taken from them are exactly consistent with the
+    potential (the conservative form the paper's introduction asks of an exact solver)."""
+    p = W.random_small(nr, nth, nphi, seed=nr + nth, grid=grid, r_inner=rin)
+    g = geo_of(p)
+    phi = np.random.default_rng(2).standard_normal((nr, nth, nphi))
+    k = O.outer_operator_dense(g) if bc == O.OUTER_MULTIPOLE else None
+    div = O.face_divergence(g, *O.face_gradients(g, phi, bc, k))
+    lap = O.apply_laplacian(g, phi, bc, k)
+    assert np.max(np.abs(div - lap)) <= 1e-13 * np.max(O.abs_apply(g, phi, bc, k))
+
+
+def test_face_gradient_of_spherical_source_is_enclosed_mass():
+    """For a spherically symmetric source the radial face gradient of the discrete
+    solution is G M_enc(r_{i+1/2}) / r_{i+1/2}^2 at every interface (inner face 0, outer
+    face G M / r_out^2), and the angular gradients vanish."""
+    r_if = np.logspace(-2, 0, 41)
+    g = O.Geometry(r_if, W.uniform_theta_interfaces(6), 8)
+    rho_r = 1.0 / (1.0 + (g.rc / 0.1) ** 2)
+    rho = np.broadcast_to(rho_r[:, None, None], (40, 6, 8))
+    phi = O.solve_separated(g, rho)
+    gr, gt, gp = O.face_gradients(g, phi)
+    m_enc = np.concatenate([[0.0], np.cumsum(4.0 * math.pi * rho_r * g.dv3 / 3.0)])
+    ex = np.zeros(41)
+    ex[1:] = m_enc[1:] / r_if[1:] ** 2
+    assert np.max(np.abs(gr[:, 0, 0] - ex)) <= 1e-12 * np.max(ex)
+    assert np.max(np.abs(gr - gr[:, :1, :1])) <= 1e-12 * np.max(ex)
+    assert np.max(np.abs(gt)) <= 1e-12 * np.max(ex) and np.max(np.abs(gp)) <= 1e-12 * np.max(ex)
+
+
+def test_face_gradient_closed_forms():
+    """r^2 on a uniform radial grid: the radial face gradient is exactly 2 r_{i+1/2};
+    cos(theta): the theta face gradient tends to -sin(theta_face)/r at second order."""
+    g = O.Geometry(W.uniform_r_interfaces(10), W.uniform_theta_interfaces(4), 4)
+    phi = np.broadcast_to((g.rc ** 2)[:, None, None], (10, 4, 4)).copy()
+    gr, _, _ = O.face_gradients(g, phi, O.OUTER_DIRICHLET)
+    assert np.max(np.abs(gr[1:-1, 0, 0] - 2.0 * g.r_if[1:-1])) <= 1e-14
+    errs = []
+    for nth in (16, 32, 64):
+        g = O.Geometry(W.uniform_r_interfaces(2, 1.0, 2.0), W.uniform_theta_interfaces(nth), 2)
+        phi = np.broadcast_to(np.cos(g.thc)[None, :, None], (2, nth, 2)).copy()
+        _, gt, _ = O.face_gradients(g, phi, O.OUTER_DIRICHLET)
+        ex = -np.sin(g.th_if[1:-1])[None, :] / g.rc[:, None]
+        errs.append(np.max(np.abs(gt[:, 1:-1, 0] - ex)))
+    assert 3.0 < errs[0] / errs[1] < 5.0 and 3.0 < errs[1] / errs[2] < 5.0
