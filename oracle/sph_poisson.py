@@ -446,6 +446,50 @@ def gauss_law_potential(geo: Geometry, rho_r, G=1.0, outer_bc=OUTER_MULTIPOLE):
     return phi
 
 
+def ellipsoid_potential(x, y, z, a, b, c, rho0=1.0, G=1.0):
+    """Continuum potential of the homogeneous ellipsoid x^2/a^2 + y^2/b^2 + z^2/c^2 <= 1
+    (Sect. 5.2): Phi = pi G rho0 a b c (A x^2 + B y^2 + C z^2 - D) with
+    A = int_u^inf dl / sqrt((a^2+l)^3 (b^2+l) (c^2+l)) (B, C likewise) and
+    D = int_u^inf dl / sqrt((a^2+l)(b^2+l)(c^2+l)); u = 0 inside, else the positive
+    root of x^2/(a^2+u) + y^2/(b^2+u) + z^2/(c^2+u) = 1.  In Carlson's symmetric forms
+    (a library primitive here): D = 2 R_F(a^2+u, b^2+u, c^2+u) and
+    A = (2/3) R_D(b^2+u, c^2+u, a^2+u), with B, C by permutation."""
+    import scipy.special as sps
+    x, y, z = (np.asarray(v, dtype=np.float64) for v in (x, y, z))
+    a2, b2, c2 = a * a, b * b, c * c
+    q = x * x / a2 + y * y / b2 + z * z / c2
+    u = np.zeros_like(q)
+    out = q > 1.0
+    if np.any(out):
+        xo, yo, zo = x[out] ** 2, y[out] ** 2, z[out] ** 2
+        # f(u) = sum x_i^2/(a_i^2+u) - 1 is convex and decreasing; its root is the largest
+        # root of the cubic prod (a_i^2+u) - sum x_i^2 prod_{k!=i} (a_k^2+u), taken in
+        # closed form (trigonometric / Cardano), then polished by Newton steps on f
+        c2_ = a2 + b2 + c2 - (xo + yo + zo)
+        c1_ = a2 * b2 + b2 * c2 + c2 * a2 - xo * (b2 + c2) - yo * (a2 + c2) - zo * (a2 + b2)
+        c0_ = a2 * b2 * c2 - xo * b2 * c2 - yo * a2 * c2 - zo * a2 * b2
+        # u = t - c2/3: t^3 + p t + q = 0
+        pp = c1_ - c2_ * c2_ / 3.0
+        qq = 2.0 * c2_ ** 3 / 27.0 - c2_ * c1_ / 3.0 + c0_
+        disc = (qq / 2.0) ** 2 + (pp / 3.0) ** 3
+        t_one = np.cbrt(-qq / 2.0 + np.sqrt(np.maximum(disc, 0.0))) + np.cbrt(-qq / 2.0 - np.sqrt(np.maximum(disc, 0.0)))
+        mm = 2.0 * np.sqrt(np.maximum(-pp / 3.0, 0.0))
+        arg = np.where(mm > 0, 3.0 * qq / (pp * np.where(mm > 0, mm, 1.0)), 0.0)
+        t_three = mm * np.cos(np.arccos(np.clip(arg, -1.0, 1.0)) / 3.0)
+        uu = np.where(disc > 0, t_one, t_three) - c2_ / 3.0
+        uu = np.maximum(uu, np.maximum(0.0, xo + yo + zo - max(a2, b2, c2)))
+        for _ in range(2):
+            f = xo / (a2 + uu) + yo / (b2 + uu) + zo / (c2 + uu) - 1.0
+            df = -(xo / (a2 + uu) ** 2 + yo / (b2 + uu) ** 2 + zo / (c2 + uu) ** 2)
+            uu = uu - f / df
+        u[out] = uu
+    A = (2.0 / 3.0) * sps.elliprd(b2 + u, c2 + u, a2 + u)
+    B = (2.0 / 3.0) * sps.elliprd(a2 + u, c2 + u, b2 + u)
+    C = (2.0 / 3.0) * sps.elliprd(a2 + u, b2 + u, c2 + u)
+    D = 2.0 * sps.elliprf(a2 + u, b2 + u, c2 + u)
+    return math.pi * G * rho0 * a * b * c * (A * x * x + B * y * y + C * z * z - D)
+
+
 def homogeneous_sphere_potential(r, radius, rho0=1.0, G=1.0):
     """Continuum potential of a homogeneous sphere."""
     r = np.asarray(r, dtype=np.float64)

@@ -478,3 +478,47 @@ def test_face_gradient_closed_forms():
         ex = -np.sin(g.th_if[1:-1])[None, :] / g.rc[:, None]
         errs.append(np.max(np.abs(gt[:, 1:-1, 0] - ex)))
     assert 3.0 < errs[0] / errs[1] < 5.0 and 3.0 < errs[1] / errs[2] < 5.0
+
+
+# ------------------------------------------------- ellipsoid of Sect. 5.2
+def test_ellipsoid_potential_closed_form():
+    """The analytic ellipsoid potential (Sect. 5.2, Carlson forms): the homogeneous
+    sphere for a = b = c; Laplacian 4 pi G rho inside and 0 outside (finite differences);
+    continuous across the surface; -G M / r far away."""
+    r = np.linspace(0.01, 3.0, 40)
+    n = np.array([0.3, 0.4, math.sqrt(0.75)])
+    sph = O.ellipsoid_potential(r * n[0], r * n[1], r * n[2], 0.7, 0.7, 0.7)
+    assert np.max(np.abs(sph - O.homogeneous_sphere_potential(r, 0.7))) <= 1e-14 * np.max(np.abs(sph))
+
+    def f(q):
+        return O.ellipsoid_potential(np.array([q[0]]), np.array([q[1]]), np.array([q[2]]), 1.0, 1.5, 2.0)[0]
+
+    def lap(p, h=1e-3):
+        p = np.asarray(p, dtype=float)
+        tot = 0.0
+        for d in range(3):
+            e = np.zeros(3)
+            e[d] = h
+            tot += (f(p + e) + f(p - e) - 2.0 * f(p)) / h ** 2
+        return tot
+
+    assert abs(lap((0.2, 0.3, -0.4)) / (4.0 * math.pi) - 1.0) <= 1e-6
+    assert abs(lap((1.2, 1.0, 1.5))) <= 1e-5 and abs(lap((0.0, 0.0, 3.0))) <= 1e-5
+    # continuity at a surface point (1/sqrt 3)(a, b, c)
+    s = np.array([1.0, 1.5, 2.0]) / math.sqrt(3.0)
+    assert abs(f(s * (1 - 1e-9)) - f(s * (1 + 1e-9))) <= 1e-8 * abs(f(s))
+    mass = 4.0 * math.pi / 3.0 * 1.0 * 1.5 * 2.0
+    assert abs(f((0.0, 0.0, 1e4)) * 1e4 / -mass - 1.0) <= 1e-7
+
+
+def test_ellipsoid_density_integrates_exactly():
+    """The sub-volume integrated source holds the ellipsoid's mass 4/3 pi a b c, every
+    cell fraction lies in [0, 1], and cells far inside / outside are 1 / 0."""
+    p = W.ellipsoid("uniform", 64, 16, 32)
+    vol = W.cell_volumes(p.r_if, p.th_if, p.nphi)[:, :, None]
+    assert abs(np.sum(p.rho * vol) / (4.0 * math.pi) - 1.0) <= 1e-12
+    assert p.rho.min() >= 0.0 and p.rho.max() <= 1.0
+    rc = 0.5 * (p.r_if[1:] + p.r_if[:-1])
+    assert np.all(p.rho[rc < 0.9] == 1.0) and np.all(p.rho[rc > 2.1] == 0.0)
+    r = W.ellipsoid_r_interfaces("stretched", 512)
+    assert abs(r[-1] - 48.7) < 0.1 and np.all(np.diff(r) > 0)

@@ -302,6 +302,70 @@ def symmetric_theta_interfaces(nth, seed=0) -> np.ndarray:
     return th
 
 
+# ------------------------------------------- ellipsoid of Sect. 5.2 (a, b, c) = (1, 1.5, 2)
+def ellipsoid_r_interfaces(kind: str, nr: int = 512) -> np.ndarray:
+    """The three radial grids of Sect. 5.2 at Nr zones: "uniform" in (0, 5]; "stretched",
+    the same uniform zones up to r = 1.5 and beyond a constant ratio r_{i+1}/r_i = 1 + dr
+    (dr = 5/Nr: r_out = 48.7 at Nr = 512); "jump", the uniform spacing up to r = 1.5 and
+    1.5 dr beyond."""
+    dr = 5.0 / nr
+    if kind == "uniform":
+        return np.arange(nr + 1) * dr
+    n_in = int(math.ceil(1.5 / dr - 1e-9))          # first interface at or beyond 1.5
+    inner = np.arange(n_in + 1) * dr
+    m = nr - n_in
+    if kind == "stretched":
+        outer = inner[-1] * (1.0 + dr) ** np.arange(1, m + 1)
+    elif kind == "jump":
+        outer = inner[-1] + 1.5 * dr * np.arange(1, m + 1)
+    else:
+        raise ValueError(kind)
+    return np.concatenate([inner, outer])
+
+
+def ellipsoid_density(r_if, th_if, nphi, a=1.0, b=1.5, c=2.0, q=8) -> np.ndarray:
+    """Cell-averaged density of the homogeneous (rho = 1) ellipsoid centred on the origin
+    with semi-axes a, b, c along x, y, z: the fraction of each cell's volume inside.
+    The ellipsoid is star-shaped about the origin, so along a direction n the inside
+    part of a cell is r < r_s(n) = 1/sqrt(n_x^2/a^2 + n_y^2/b^2 + n_z^2/c^2): the radial
+    integral of r^2 dr is exact, and the solid angle is integrated with a q x q
+    Gauss-Legendre rule in (cos theta, phi) per angular cell (a finer sub-volume
+    integration than the recursive octant splitting of Sect. 5.2)."""
+    r_if = np.asarray(r_if, dtype=np.float64)
+    th_if = np.asarray(th_if, dtype=np.float64)
+    nr, nth = len(r_if) - 1, len(th_if) - 1
+    gx, gw = np.polynomial.legendre.leggauss(q)
+    mu_if = np.cos(th_if)
+    dphi = 2.0 * math.pi / nphi
+    r3 = r_if ** 3
+    dv3 = r3[1:] - r3[:-1]
+    rho = np.zeros((nr, nth, nphi))
+    rmax = max(a, b, c)
+    imax = min(nr, int(np.searchsorted(r_if, rmax, side="right")))
+    for j in range(nth):
+        # q x q directions of every phi cell of row j: mu in [cos th_{j+1}, cos th_j]
+        mu = 0.5 * (mu_if[j] + mu_if[j + 1]) + 0.5 * (mu_if[j] - mu_if[j + 1]) * gx           # (q,)
+        ph = (np.arange(nphi)[:, None] + 0.5 + 0.5 * gx[None, :]) * dphi                        # (nphi, q)
+        st = np.sqrt(np.maximum(0.0, 1.0 - mu * mu))
+        nx = st[None, :, None] * np.cos(ph)[:, None, :]
+        ny = st[None, :, None] * np.sin(ph)[:, None, :]
+        nz = np.broadcast_to(mu[None, :, None], nx.shape)
+        rs = 1.0 / np.sqrt(nx * nx / a ** 2 + ny * ny / b ** 2 + nz * nz / c ** 2)           # (nphi, q, q)
+        w = (gw[:, None] * gw[None, :]) / 4.0                                                   # sums to 1
+        rs3 = rs ** 3
+        for i in range(imax):
+            frac = np.clip((rs3 - r3[i]) / dv3[i], 0.0, 1.0)
+            rho[i, j, :] = np.einsum("kab,ab->k", frac, w)
+    return rho
+
+
+def ellipsoid(kind: str = "uniform", nr: int = 512, nth: int = 128, nphi: int = 256) -> Problem:
+    """Sect. 5.2's convergence test: the (1, 1.5, 2) ellipsoid on one of its radial grids."""
+    r_if = ellipsoid_r_interfaces(kind, nr)
+    th_if = uniform_theta_interfaces(nth)
+    return Problem(f"ellipsoid_{kind}", r_if, th_if, nphi, ellipsoid_density(r_if, th_if, nphi))
+
+
 CONFIGS = {
     "sphere_blob": sphere_blob,
     "stellar_noise": stellar_noise,
