@@ -59,6 +59,15 @@ typedef enum {
  * exists for tests and for bounded domains. */
 enum { SP_OUTER_MULTIPOLE = 0, SP_OUTER_DIRICHLET = 1 };
 
+/* Inner radial boundary (only meaningful when r_{1/2} > 0).  SP_INNER_ZERO_FLUX: no flux
+ * through r_{1/2} (exact for the l = 0 part when no mass lies inside).  SP_INNER_REGULAR:
+ * the region r < r_{1/2} is empty and holds the regular Laplace solution, so each mode
+ * (l,m) is extrapolated as f ~ r^q from the innermost zone, q = (-1 + sqrt(1 - 4
+ * lambda_Omega,l,m))/2: the inner-face gradient is q f_1 (r_{1/2}/r_1)^q / r_{1/2} (the
+ * mirror image of the paper's outer condition, Sect. 3.2; the paper itself treats
+ * r_{1/2} = 0 only). */
+enum { SP_INNER_ZERO_FLUX = 0, SP_INNER_REGULAR = 1 };
+
 /* Arithmetic of sp_solve.  SP_FP64: every step in float64.  The mixed modes run a
  * low-precision solve -- phi FFTs and radial solves in float32 (float64 for the
  * near-singular |lambda| < 30 radial modes), theta projections on the tensor cores
@@ -89,7 +98,7 @@ typedef struct {
  *  r_interfaces      host, Nr+1 values, strictly increasing, r_interfaces[0] >= 0
  *  theta_interfaces  host, Ntheta+1 values, strictly increasing from 0 to pi
  *                    (|last - pi| <= 1e-12); NULL = uniform theta
- *  Nr, Ntheta >= 1; Ntheta <= 160.  Nphi >= 1 with Nphi = 2^a 3^b, Nphi <= 4096.
+ *  Nr, Ntheta >= 1; Ntheta <= 160.  Nphi >= 1 with Nphi = 2^a 3^b 5^c, Nphi <= 4096.
  *  outer_bc          SP_OUTER_MULTIPOLE or SP_OUTER_DIRICHLET
  *  G                 gravitational constant (s = 4 pi G rho)
  *  precision         SP_FP64, SP_MIXED_BF16X3 or SP_MIXED_BF16X6 (mixed: Ntheta <= 128)
@@ -107,6 +116,31 @@ int sp_plan_create(const double* r_interfaces, int Nr,
                    const double* theta_interfaces, int Ntheta,
                    int Nphi, int outer_bc, double G, int precision,
                    double tol, int max_iter, void* stream, sp_plan** out);
+
+/* Everything sp_plan_create takes, plus explicit cell centres and the inner boundary.
+ *  r_centres      host, Nr values with r_interfaces[i] < r_centres[i] < r_interfaces[i+1],
+ *                 or NULL for the midpoints; the operator's r_i (radial differences,
+ *                 R_i and the boundary extrapolations) are these points
+ *  theta_centres  host, Ntheta values strictly inside their cells, or NULL for the
+ *                 midpoints (theta_j of the differences and of S_j = dtheta_j/(sin
+ *                 theta_j w_j))
+ *  inner_bc       SP_INNER_ZERO_FLUX or SP_INNER_REGULAR (float64 plans only)
+ * Returns what sp_plan_create returns; SP_ERR_GRID for centres outside their cells,
+ * SP_ERR_UNSUPPORTED for SP_INNER_REGULAR on a mixed-precision plan. */
+typedef struct {
+    const double* r_interfaces; int Nr;
+    const double* theta_interfaces; int Ntheta;
+    int Nphi;
+    const double* r_centres;
+    const double* theta_centres;
+    int inner_bc;
+    int outer_bc;
+    double G;
+    int precision;
+    double tol;
+    int max_iter;
+} sp_plan_desc;
+int sp_plan_create_ex(const sp_plan_desc* desc, void* stream, sp_plan** out);
 
 /* A second plan for the same problem that shares the source plan's read-only tables
  * (geometry, theta eigenbasis, radial elimination factors) and has its own workspace,

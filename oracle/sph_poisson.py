@@ -30,7 +30,12 @@ Readings of the paper taken here (the printed formulas are partly garbled):
 * R6  outer boundary: the outer-face gradient is replaced by
       -p f_N (r_{N+1/2}/r_N)^(-p) / r_{N+1/2},  p = (1+sqrt(1-4 lambda_Omega))/2.
 * R8  cell centres are midpoints of their interfaces.
-* R9  inner boundary: zero flux through r_{1/2} (the area vanishes when r_{1/2}=0).
+* R9  inner boundary: zero flux through r_{1/2} (the area vanishes when r_{1/2}=0);
+      optionally, for r_{1/2} > 0, a "regular interior": the empty region r < r_{1/2}
+      holds the regular Laplace solution, so each mode (l,m) is extrapolated as
+      f ~ r^q from the innermost zone, q = (-1 + sqrt(1 - 4 lambda_Omega))/2.
+* R8' explicit cell centres may replace the midpoints (any point strictly inside
+      the cell); the operator's r_i, theta_j are then those centres.
 * R10 forward FFT normalised by 1/Nphi; half spectrum m = 0..Nphi//2.
 * R11 eigenvalues sorted descending (l=0 is lambda=0 for m=0); eigenvector
       signs are arbitrary, so only Phi is compared.
@@ -50,12 +55,14 @@ import scipy.linalg
 
 OUTER_MULTIPOLE = 0
 OUTER_DIRICHLET = 1
+INNER_ZERO_FLUX = 0
+INNER_REGULAR = 1
 
 
 class Geometry:
     """Geometric factors of Sect. 3.1 (areas, volumes, R_i, S_j, w_j)."""
 
-    def __init__(self, r_if, th_if, nphi: int):
+    def __init__(self, r_if, th_if, nphi: int, r_centres=None, th_centres=None, inner_bc=INNER_ZERO_FLUX):
         r_if = np.asarray(r_if, dtype=np.float64)
         th_if = np.asarray(th_if, dtype=np.float64)
         if r_if.ndim != 1 or len(r_if) < 2 or np.any(np.diff(r_if) <= 0) or r_if[0] < 0:
@@ -69,9 +76,18 @@ class Geometry:
         self.nr, self.nth = len(r_if) - 1, len(th_if) - 1
         rm, rp = r_if[:-1], r_if[1:]
         self.rc = 0.5 * (rm + rp)                              # R8
+        if r_centres is not None:                              # R8'
+            self.rc = np.asarray(r_centres, dtype=np.float64).copy()
+            if self.rc.shape != rm.shape or np.any(self.rc <= rm) or np.any(self.rc >= rp):
+                raise ValueError("radial centres must lie strictly inside their cells")
         self.dv3 = rp ** 3 - rm ** 3                           # 3 dV / (w dphi)
         self.R = 3.0 * (rp ** 2 - rm ** 2) / (2.0 * self.rc * self.dv3)
         self.thc = 0.5 * (th_if[:-1] + th_if[1:])              # R8
+        if th_centres is not None:                             # R8'
+            self.thc = np.asarray(th_centres, dtype=np.float64).copy()
+            if (self.thc.shape != (self.nth,) or np.any(self.thc <= th_if[:-1])
+                    or np.any(self.thc >= th_if[1:])):
+                raise ValueError("polar centres must lie strictly inside their cells")
         self.w = np.cos(th_if[:-1]) - np.cos(th_if[1:])
         self.dth = th_if[1:] - th_if[:-1]
         self.sin_c = np.sin(self.thc)
@@ -82,6 +98,9 @@ class Geometry:
         self.sin_if = sin_if
         self.dphi = 2.0 * math.pi / self.nphi
         self.r_out = r_if[-1]
+        self.r_in = r_if[0]
+        self.inner_regular = inner_bc == INNER_REGULAR and r_if[0] > 0.0
+        self._kin_dense = None
 
     # ------------------------------------------------------------ volumes
     def cell_volume(self):
@@ -99,6 +118,15 @@ def kappa(lam, r_out, r_last):
     lam = np.asarray(lam, dtype=np.float64)
     p = 0.5 * (1.0 + np.sqrt(1.0 - 4.0 * lam))
     return -p / r_out * np.exp(-p * math.log(r_out / r_last))
+
+
+def kappa_inner(lam, r_in, r_first):
+    """Inner-face gradient per unit f_1 for angular eigenvalue lam with a regular
+    interior (R9): f ~ r^q extrapolated from the innermost zone to r_{1/2},
+    q = (-1 + sqrt(1 - 4 lam))/2 >= 0 (q = l for the continuum eigenvalue -l(l+1))."""
+    lam = np.asarray(lam, dtype=np.float64)
+    q = 0.5 * (-1.0 + np.sqrt(1.0 - 4.0 * lam))
+    return q / r_in * np.exp(q * math.log(r_in / r_first))
 
 
 # =================================================================== O3
@@ -120,9 +148,10 @@ def angular_apply(geo: Geometry, u):
     return out
 
 
-def outer_operator_dense(geo: Geometry):
-    """Matrix K of kappa(A_Omega) on the outermost shell, by a dense eigendecomposition
-    of the full 2-D angular operator (no FFT, no per-m split).  Tiny grids only."""
+def outer_operator_dense(geo: Geometry, fn=None):
+    """Matrix K of kappa(A_Omega) on the outermost shell (or of another function `fn` of
+    the angular eigenvalue), by a dense eigendecomposition of the full 2-D angular
+    operator (no FFT, no per-m split).  Tiny grids only."""
     n = geo.nth * geo.nphi
     a = np.zeros((n, n))
     eye = np.eye(n).reshape(n, geo.nth, geo.nphi)
@@ -133,8 +162,22 @@ def outer_operator_dense(geo: Geometry):
     m = (sq[:, None] * a) / sq[None, :]
     m = 0.5 * (m + m.T)
     lam, v = np.linalg.eigh(m)
-    kap = kappa(lam, geo.r_out, geo.rc[-1])
+    kap = kappa(lam, geo.r_out, geo.rc[-1]) if fn is None else fn(lam)
     return ((v * kap[None, :]) @ v.T) / sq[:, None] * sq[None, :]
+
+
+def inner_gradient(geo: Geometry, phi_first):
+    """Inner-face gradient for every (j,k) of the first shell: zero flux, or with a
+    regular interior kappa_inner(A_Omega) applied to the first shell (R9)."""
+    phi_first = np.asarray(phi_first, dtype=np.float64)
+    if not geo.inner_regular:
+        return np.zeros_like(phi_first)
+    fn = lambda lam: kappa_inner(lam, geo.r_in, geo.rc[0])   # noqa: E731
+    if geo.nth * geo.nphi <= 1200:
+        if geo._kin_dense is None:
+            geo._kin_dense = outer_operator_dense(geo, fn)
+        return (geo._kin_dense @ phi_first.reshape(-1)).reshape(phi_first.shape)
+    return outer_kappa_separated(geo, phi_first, fn)
 
 
 def outer_gradient(geo: Geometry, phi_last, outer_bc, kmat=None):
@@ -156,7 +199,9 @@ def apply_laplacian(geo: Geometry, phi, outer_bc=OUTER_MULTIPOLE, kmat=None):
         flux = k_face[:, None, None] * (phi[1:] - phi[:-1])
         out[:-1] += flux
         out[1:] -= flux
-    # inner face r_{1/2}: zero flux (R9).  Outer face: boundary condition (R6).
+    # inner face r_{1/2}: zero flux or regular interior (R9).  Outer face: boundary
+    # condition (R6).
+    out[0] -= geo.r_in ** 2 * inner_gradient(geo, phi[0])
     out[-1] += geo.r_out ** 2 * outer_gradient(geo, phi[-1], outer_bc, kmat)
     out *= (3.0 / geo.dv3)[:, None, None]
     # angular part, scaled by R_i
@@ -192,6 +237,8 @@ def abs_apply(geo: Geometry, phi, outer_bc=OUTER_MULTIPOLE, kmat=None):
         off += cphi[:, :, None] * (np.roll(a, -1, -1) + np.roll(a, 1, -1))
         diag -= 2.0 * cphi[:, :, None]
     out = off
+    if geo.inner_regular:
+        out[0] += np.abs(3.0 * geo.r_in ** 2 / geo.dv3[0] * inner_gradient(geo, np.asarray(phi, dtype=np.float64)[0]))
     if outer_bc == OUTER_DIRICHLET:
         diag[-1] -= 3.0 * geo.r_out ** 2 / ((geo.r_out - geo.rc[-1]) * geo.dv3[-1])
         out += np.abs(diag) * a
@@ -283,6 +330,8 @@ def radial_system(geo: Geometry, lam, outer_bc=OUTER_MULTIPOLE):
         sub[1:] = 3.0 * k_face / geo.dv3[1:]
     base = -(sub + sup)
     diag = base + geo.R * lam[..., None]
+    if geo.inner_regular:
+        diag[..., 0] += -3.0 * geo.r_in ** 2 * kappa_inner(lam, geo.r_in, geo.rc[0]) / geo.dv3[0]
     if outer_bc == OUTER_DIRICHLET:
         diag[..., -1] += -3.0 * geo.r_out ** 2 / ((geo.r_out - geo.rc[-1]) * geo.dv3[-1])
     else:
@@ -367,13 +416,14 @@ def solve_exact(geo: Geometry, rho, G=1.0, outer_bc=OUTER_MULTIPOLE, max_steps=6
     return (phi, hist) if return_history else phi
 
 
-def outer_kappa_separated(geo: Geometry, u):
-    """kappa(A_Omega) u on the last shell through the per-m eigenbasis (FFT, projection,
-    scale, back projection, inverse FFT).  Used for O3 on grids too large for the dense K."""
+def outer_kappa_separated(geo: Geometry, u, fn=None):
+    """kappa(A_Omega) u on the last shell (or `fn` of the angular eigenvalue) through the
+    per-m eigenbasis (FFT, projection, scale, back projection, inverse FFT).  Used for
+    O3 on grids too large for the dense K."""
     u = np.asarray(u, dtype=np.float64)
     lams, hs = all_theta_eigen(geo)
     ut = np.fft.rfft(u, axis=-1) / geo.nphi                      # (Nth, Mh)
-    kap = kappa(lams, geo.r_out, geo.rc[-1])                     # (Mh, Nth)
+    kap = kappa(lams, geo.r_out, geo.rc[-1]) if fn is None else fn(lams)   # (Mh, Nth)
     out = np.zeros_like(ut)
     for m in range(ut.shape[-1]):
         c = (hs[m] * geo.w[:, None]).T @ ut[:, m]
@@ -399,6 +449,7 @@ def face_gradients(geo: Geometry, phi, outer_bc=OUTER_MULTIPOLE, kmat=None):
     gr = np.zeros((nr + 1, nth, nphi))
     if nr > 1:
         gr[1:-1] = (phi[1:] - phi[:-1]) / (geo.rc[1:] - geo.rc[:-1])[:, None, None]
+    gr[0] = inner_gradient(geo, phi[0])
     gr[-1] = outer_gradient(geo, phi[-1], outer_bc, kmat)
     gt = np.zeros((nr, nth + 1, nphi))
     if nth > 1:

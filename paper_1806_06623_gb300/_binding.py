@@ -25,6 +25,8 @@ SP_ERR_UNSUPPORTED = 8
 
 SP_OUTER_MULTIPOLE = 0
 SP_OUTER_DIRICHLET = 1
+SP_INNER_ZERO_FLUX = 0
+SP_INNER_REGULAR = 1
 SP_FP64 = 0
 SP_MIXED_BF16X3 = 1
 SP_MIXED_BF16X6 = 2
@@ -46,6 +48,13 @@ class SolveInfo(C.Structure):
         return d
 
 
+class PlanDesc(C.Structure):
+    _fields_ = [("r_interfaces", C.c_void_p), ("Nr", C.c_int), ("theta_interfaces", C.c_void_p), ("Ntheta", C.c_int),
+                ("Nphi", C.c_int), ("r_centres", C.c_void_p), ("theta_centres", C.c_void_p), ("inner_bc", C.c_int),
+                ("outer_bc", C.c_int), ("G", C.c_double), ("precision", C.c_int), ("tol", C.c_double),
+                ("max_iter", C.c_int)]
+
+
 class ServerStats(C.Structure):
     _fields_ = [("completed", C.c_longlong), ("failed", C.c_longlong), ("queued", C.c_longlong),
                 ("running_peak", C.c_int), ("resident_plans", C.c_int), ("evictions", C.c_longlong),
@@ -62,6 +71,7 @@ _LIB = None
 _SIGS = {
     "sp_plan_create": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_double,
                                  C.c_int, C.c_double, C.c_int, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "sp_plan_create_ex": (C.c_int, [C.POINTER(PlanDesc), C.c_void_p, C.POINTER(C.c_void_p)]),
     "sp_plan_clone": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p)]),
     "sp_solve_batched": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "sp_server_create": (C.c_int, [C.c_size_t, C.c_int, C.POINTER(C.c_void_p)]),
@@ -161,6 +171,26 @@ def sp_plan_create(r_interfaces, theta_interfaces, nphi, outer_bc=SP_OUTER_MULTI
                               int(nphi), int(outer_bc), float(G), int(precision), float(tol), int(max_iter),
                               _stream_ptr(stream), C.byref(out))
     _check(st, "sp_plan_create")
+    return out
+
+
+def sp_plan_create_ex(r_interfaces, theta_interfaces, nphi, r_centres=None, theta_centres=None,
+                      inner_bc=SP_INNER_ZERO_FLUX, outer_bc=SP_OUTER_MULTIPOLE, G=1.0, precision=SP_FP64, tol=1e-10,
+                      max_iter=8, stream=None):
+    r = np.ascontiguousarray(r_interfaces, dtype=np.float64)
+    th = np.ascontiguousarray(theta_interfaces, dtype=np.float64)
+    rc = None if r_centres is None else np.ascontiguousarray(r_centres, dtype=np.float64)
+    tc = None if theta_centres is None else np.ascontiguousarray(theta_centres, dtype=np.float64)
+    if rc is not None and len(rc) != len(r) - 1:
+        raise ValueError("r_centres needs one value per radial zone")
+    if tc is not None and len(tc) != len(th) - 1:
+        raise ValueError("theta_centres needs one value per polar zone")
+    d = PlanDesc(r.ctypes.data_as(C.c_void_p), len(r) - 1, th.ctypes.data_as(C.c_void_p), len(th) - 1, int(nphi),
+                 None if rc is None else rc.ctypes.data_as(C.c_void_p),
+                 None if tc is None else tc.ctypes.data_as(C.c_void_p), int(inner_bc), int(outer_bc), float(G),
+                 int(precision), float(tol), int(max_iter))
+    out = C.c_void_p()
+    _check(lib().sp_plan_create_ex(C.byref(d), _stream_ptr(stream), C.byref(out)), "sp_plan_create_ex")
     return out
 
 
@@ -329,14 +359,19 @@ class Plan:
     """One solver plan: grid, boundary condition, precision and its device tables."""
 
     def __init__(self, r_interfaces, theta_interfaces, nphi, outer_bc=SP_OUTER_MULTIPOLE, G=1.0,
-                 precision=SP_FP64, tol=1e-10, max_iter=8, stream=None):
+                 precision=SP_FP64, tol=1e-10, max_iter=8, stream=None, r_centres=None, theta_centres=None,
+                 inner_bc=SP_INNER_ZERO_FLUX):
         self.r_if = np.asarray(r_interfaces, dtype=np.float64)
         self.th_if = np.asarray(theta_interfaces, dtype=np.float64)
         self.shape = (len(self.r_if) - 1, len(self.th_if) - 1, int(nphi))
         self.mh = int(nphi) // 2 + 1
         self.precision = precision
         self._h = None
-        self._h = sp_plan_create(self.r_if, self.th_if, nphi, outer_bc, G, precision, tol, max_iter, stream)
+        if r_centres is None and theta_centres is None and inner_bc == SP_INNER_ZERO_FLUX:
+            self._h = sp_plan_create(self.r_if, self.th_if, nphi, outer_bc, G, precision, tol, max_iter, stream)
+        else:
+            self._h = sp_plan_create_ex(self.r_if, self.th_if, nphi, r_centres, theta_centres, inner_bc, outer_bc, G,
+                                        precision, tol, max_iter, stream)
 
     @property
     def handle(self):

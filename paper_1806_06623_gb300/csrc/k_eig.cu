@@ -112,8 +112,10 @@ __device__ void ql_block(double* d, double* e, double* Z, int n, double* rc, dou
 
 __global__ void k_theta_eigen(const double* __restrict__ tdiag, const double* __restrict__ toff,
                               const double* __restrict__ sqw, int nth, int parity, int outer_bc, double r_out,
-                              double r_last, double outer_coef, double* __restrict__ lam_out,
+                              double r_last, double outer_coef, int inner_regular, double r_in, double r_first,
+                              double inner_coef, double* __restrict__ lam_out,
                               double* __restrict__ kappa_out, double* __restrict__ outer_out,
+                              double* __restrict__ inner_out,
                               double* __restrict__ H, double* __restrict__ HtW, double* __restrict__ Hp,
                               double* __restrict__ HtWp, int* __restrict__ err) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -216,6 +218,14 @@ __global__ void k_theta_eigen(const double* __restrict__ tdiag, const double* __
     kappa_out[(size_t)m * nth + lrow] = kap;
     outer_out[(size_t)m * nth + lrow] =
         (outer_bc == SP_OUTER_DIRICHLET) ? -outer_coef / (r_out - r_last) : outer_coef * kap;
+    // regular interior: inner-face gradient q f_1 (r_in/r_1)^q / r_in, q = (-1 + sqrt(1 - 4 lambda))/2,
+    // entering row 1 with minus the face area over the volume
+    double in_d = 0.0;
+    if (inner_regular) {
+      const double q = 0.5 * (-1.0 + sqrt(1.0 - 4.0 * lam));
+      in_d = -inner_coef * (q / r_in) * exp(q * log(r_in / r_first));
+    }
+    inner_out[(size_t)m * nth + lrow] = in_d;
   }
   // H[m][j][l] = q_j/sqrt(w_j), HtW[m][l][j] = q_j sqrt(w_j), l = rank[a]
   double* Hm = H + (size_t)m * nth * nth;
@@ -272,7 +282,9 @@ cudaError_t theta_eigen(const Plan& p, cudaStream_t s) {
   int threads = ((nth + 31) / 32) * 32;
   if (threads < 32) threads = 32;
   k_theta_eigen<<<p.mh, threads, smem, s>>>(p.d_tdiag, p.d_toff, p.d_sqw, nth, p.parity ? 1 : 0, p.outer_bc,
-                                            p.r_out, p.r_last, p.outer_coef, p.d_lam, p.d_kappa, p.d_outer,
+                                            p.r_out, p.r_last, p.outer_coef,
+                                            p.inner_bc == SP_INNER_REGULAR ? 1 : 0, p.r_in, p.r_first, p.inner_coef,
+                                            p.d_lam, p.d_kappa, p.d_outer, p.d_inner,
                                             p.d_H, p.d_HtW, p.d_Hp, p.d_HtWp, p.d_err);
   return cudaGetLastError();
 }

@@ -3,7 +3,7 @@
 // One CTA (8 warps) transforms a chunk of up to 32 consecutive phi lines (line
 // g = i*Ntheta + j, Nphi contiguous values each).  Two real lines are packed into one
 // complex line z = x_A + i x_B; every packed line is owned by one warp, which runs a
-// mixed-radix (4, 2, 3) Stockham FFT on it in shared memory with only warp-level
+// mixed-radix (4, 2, 3, 5) Stockham FFT on it in shared memory with only warp-level
 // synchronisation.  Lines are stored at a padded stride of Nphi+1 complex values so
 // that lanes addressing consecutive lines hit different banks.  The forward kernel
 // separates X_A[m] = (Z[m] + conj Z[N-m])/2, X_B[m] = (Z[m] - conj Z[N-m])/(2i) and
@@ -78,6 +78,31 @@ __device__ __forceinline__ void butterfly(const typename C2<T>::t* __restrict__ 
     }
     d[base] = cadd(v0, v1);
     d[base + Ns] = csub(v0, v1);
+  } else if (R == 5) {
+    CT v0 = s[b], v1 = s[b + stride], v2 = s[b + 2 * stride], v3 = s[b + 3 * stride], v4 = s[b + 4 * stride];
+    if (k != 0) {
+      CT w1 = tw[k * tstep], w2 = tw[2 * k * tstep], w3 = tw[3 * k * tstep], w4 = tw[4 * k * tstep];
+      if (INV) { w1.y = -w1.y; w2.y = -w2.y; w3.y = -w3.y; w4.y = -w4.y; }
+      v1 = cmul(v1, w1); v2 = cmul(v2, w2); v3 = cmul(v3, w3); v4 = cmul(v4, w4);
+    }
+    // X_q = sum_r v_r w^(r q), w = exp(-+2 pi i / 5), from the pairs r and 5-r:
+    // X_1, X_4 = a1 -+ i b1 and X_2, X_3 = a2 -+ i b2 (forward signs)
+    const T c1 = T(0.30901699437494742410229341718281906);    // cos(2 pi/5)
+    const T c2 = T(-0.80901699437494742410229341718281906);   // cos(4 pi/5)
+    const T s1 = T(0.95105651629515357211643933337938214);    // sin(2 pi/5)
+    const T s2 = T(0.58778525229247312916870595463907277);    // sin(4 pi/5)
+    CT t1 = cadd(v1, v4), t2 = cadd(v2, v3), t3 = csub(v1, v4), t4 = csub(v2, v3);
+    CT a1, a2, b1, b2;
+    a1.x = v0.x + c1 * t1.x + c2 * t2.x; a1.y = v0.y + c1 * t1.y + c2 * t2.y;
+    a2.x = v0.x + c2 * t1.x + c1 * t2.x; a2.y = v0.y + c2 * t1.y + c1 * t2.y;
+    b1.x = s1 * t3.x + s2 * t4.x; b1.y = s1 * t3.y + s2 * t4.y;
+    b2.x = s2 * t3.x - s1 * t4.x; b2.y = s2 * t3.y - s1 * t4.y;
+    const CT jb1 = mul_mi<INV>(b1), jb2 = mul_mi<INV>(b2);
+    d[base] = cadd(v0, cadd(t1, t2));
+    d[base + Ns] = cadd(a1, jb1);
+    d[base + 2 * Ns] = cadd(a2, jb2);
+    d[base + 3 * Ns] = csub(a2, jb2);
+    d[base + 4 * Ns] = csub(a1, jb1);
   } else {  // R == 3
     CT v0 = s[b], v1 = s[b + stride], v2 = s[b + 2 * stride];
     if (k != 0) {

@@ -16,14 +16,16 @@ namespace sp {
 namespace {
 
 __global__ void __launch_bounds__(128) k_thomas_f64(const RadialRow* __restrict__ rad, const double* __restrict__ lam,
-                                                    const double* __restrict__ outer, double* __restrict__ x,
-                                                    double* __restrict__ cp, int nr, int nth, int mh) {
+                                                    const double* __restrict__ outer, const double* __restrict__ inner,
+                                                    double* __restrict__ x, double* __restrict__ cp, int nr, int nth,
+                                                    int mh) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= mh * nth) return;
   const int m = t / nth;
   const int l = t - m * nth;
   const double L = lam[t];
   const double od = outer[t];
+  const double id = inner[t];
   double* X = x + (size_t)m * nr * 2 * nth + l;
   double* CP = cp + (size_t)m * nr * nth + l;
   const size_t st = 2 * (size_t)nth;
@@ -31,6 +33,7 @@ __global__ void __launch_bounds__(128) k_thomas_f64(const RadialRow* __restrict_
   for (int i = 0; i < nr; ++i) {
     const RadialRow rr = rad[i];
     double b = fma(rr.R, L, rr.base);
+    if (i == 0) b += id;
     if (i == nr - 1) b += od;
     const double piv = b - rr.sub * cprev;
     const double inv = 1.0 / piv;
@@ -129,11 +132,13 @@ __global__ void __launch_bounds__(32 * kShellRows) k_shell_apply(const double* _
 // (and the pole face j = Ntheta after the last row) and its azimuthal face k+1/2.  The
 // outer radial face (index nr) holds on entry the multipole term O_m Phi_last computed by
 // the shell transforms (scaled here by 1/outer_coef), or is set from the Dirichlet
-// condition.
+// condition; the inner face (index 0) holds O_in Phi_first for a regular interior
+// (scaled by -1/inner_coef), else zero (inner_scale = 0).
 __global__ void __launch_bounds__(256) k_face_grad(const double* __restrict__ phi, double* __restrict__ gr,
                                                    double* __restrict__ gt, double* __restrict__ gp,
                                                    const FaceCoef* __restrict__ fr, const FaceCoef* __restrict__ ft,
-                                                   int nr, int nth, int nphi, int dirichlet, double outer_scale) {
+                                                   int nr, int nth, int nphi, int dirichlet, double outer_scale,
+                                                   double inner_scale) {
   const size_t n = (size_t)nr * nth * nphi;
   const size_t shell = (size_t)nth * nphi;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
@@ -144,7 +149,8 @@ __global__ void __launch_bounds__(256) k_face_grad(const double* __restrict__ ph
     const double c = phi[idx];
     const FaceCoef r = fr[i];
     const FaceCoef t = ft[j];
-    gr[idx] = i > 0 ? (c - phi[idx - shell]) * r.inv_d : 0.0;
+    // inner face: zero flux, or (regular interior) O_in phi_first on entry, scaled
+    gr[idx] = i > 0 ? (c - phi[idx - shell]) * r.inv_d : gr[idx] * inner_scale;
     if (i == nr - 1) {
       double* o = gr + idx + shell;   // outer face
       *o = dirichlet ? -c * outer_scale : *o * outer_scale;
@@ -170,18 +176,25 @@ cudaError_t face_gradients_f64(const Plan& p, const double* phi, double* gr, dou
     if ((e = shell_kappa_f64(p, p.shell, p.shell2, s)) != cudaSuccess) return e;
     if ((e = fft_inverse_f64(p, p.shell2, 1, gr + off + sh, false, s)) != cudaSuccess) return e;
   }
+  const bool reg = p.inner_bc == SP_INNER_REGULAR;
+  if (reg) {
+    // O_in phi_first = -inner_coef x kappa_in(A_Omega) phi_first into the inner face
+    if ((e = fft_forward_f64(p, phi, 1, 1.0 / p.nphi, p.shell, s)) != cudaSuccess) return e;
+    if ((e = shell_apply_f64(p, p.d_ishell, p.shell, p.shell2, s)) != cudaSuccess) return e;
+    if ((e = fft_inverse_f64(p, p.shell2, 1, gr, false, s)) != cudaSuccess) return e;
+  }
   const size_t n = (size_t)p.nr * p.nth * p.nphi;
   size_t blocks = (n + 255) / 256;
   if (blocks > 152 * 64) blocks = 152 * 64;
   const double scale = dir ? 1.0 / (p.r_out - p.r_last) : 1.0 / p.outer_coef;
   k_face_grad<<<(unsigned)blocks, 256, 0, s>>>(phi, gr, gt, gp, p.d_face_r, p.d_face_t, p.nr, p.nth, p.nphi,
-                                               dir ? 1 : 0, scale);
+                                               dir ? 1 : 0, scale, reg ? -1.0 / p.inner_coef : 0.0);
   return cudaGetLastError();
 }
 
 cudaError_t thomas_f64(const Plan& p, double* x, cudaStream_t s) {
   const int n = p.mh * p.nth;
-  k_thomas_f64<<<(n + 127) / 128, 128, 0, s>>>(p.d_rad, p.d_lam, p.d_outer, x, p.cp, p.nr, p.nth, p.mh);
+  k_thomas_f64<<<(n + 127) / 128, 128, 0, s>>>(p.d_rad, p.d_lam, p.d_outer, p.d_inner, x, p.cp, p.nr, p.nth, p.mh);
   return cudaGetLastError();
 }
 
@@ -194,15 +207,28 @@ cudaError_t stencil_f64(const Plan& p, const double* phi, double* out, cudaStrea
   return cudaGetLastError();
 }
 
-cudaError_t shell_kappa_f64(const Plan& p, const double* in, double* out, cudaStream_t s) {
-  k_shell_apply<<<dim3((p.nth + kShellRows - 1) / kShellRows, p.mh), 32 * kShellRows, 0, s>>>(p.d_oshell, in, out,
-                                                                                           p.nth);
+cudaError_t shell_apply_f64(const Plan& p, const double* O, const double* in, double* out, cudaStream_t s) {
+  k_shell_apply<<<dim3((p.nth + kShellRows - 1) / kShellRows, p.mh), 32 * kShellRows, 0, s>>>(O, in, out, p.nth);
   return cudaGetLastError();
 }
 
-cudaError_t outer_operator_f64(const Plan& p, cudaStream_t s) {
-  k_outer_operator<<<dim3(p.nth, p.mh), 128, 0, s>>>(p.d_HtW, p.d_H, p.d_outer, p.d_oshell, p.nth);
+cudaError_t shell_kappa_f64(const Plan& p, const double* in, double* out, cudaStream_t s) {
+  return shell_apply_f64(p, p.d_oshell, in, out, s);
+}
+
+cudaError_t shell_operator_f64(const Plan& p, const double* diag, double* dst, cudaStream_t s) {
+  k_outer_operator<<<dim3(p.nth, p.mh), 128, 0, s>>>(p.d_HtW, p.d_H, diag, dst, p.nth);
   return cudaGetLastError();
+}
+
+cudaError_t outer_operator_f64(const Plan& p, cudaStream_t s) { return shell_operator_f64(p, p.d_outer, p.d_oshell, s); }
+
+cudaError_t inner_term_f64(const Plan& p, const double* phi, double* out, cudaStream_t s) {
+  cudaError_t e = fft_forward_f64(p, phi, 1, 1.0 / p.nphi, p.shell, s);
+  if (e != cudaSuccess) return e;
+  e = shell_apply_f64(p, p.d_ishell, p.shell, p.shell2, s);
+  if (e != cudaSuccess) return e;
+  return fft_inverse_f64(p, p.shell2, 1, out, true, s);
 }
 
 cudaError_t outer_term_f64(const Plan& p, const double* phi, double* out, cudaStream_t s) {

@@ -16,7 +16,7 @@ constexpr int kMaxStages = 16;
 constexpr int kMaxNtheta = 160;   // theta eigenvectors of one m are kept in shared memory
 constexpr int kMaxNphi = 4096;
 
-// Radix schedule of a length-n complex FFT, n = 2^a 3^b (radix 4 first, then 2, then 3).
+// Radix schedule of a length-n complex FFT, n = 2^a 3^b 5^c (radix 4 first, then 2, 3, 5).
 // Per stage: Ns (product of the earlier radices), the twiddle-table step n/(Ns R), and
 // the division b/Ns as a shift (power-of-two Ns) or a multiply-high by magic =
 // floor(2^32/Ns)+1 (exact for b < 8192).
@@ -119,11 +119,13 @@ struct Plan {
   int num_sms = 1;                // streaming multiprocessors of the device
   int nr = 0, nth = 0, nphi = 0, mh = 0;
   int outer_bc = SP_OUTER_MULTIPOLE;
+  int inner_bc = SP_INNER_ZERO_FLUX;   // SP_INNER_REGULAR only with r_{1/2} > 0 (set otherwise to zero flux)
   int precision = SP_FP64;
   double G = 1.0, tol = 1e-10;
   int max_iter = 8;
   bool parity = false;   // theta grid symmetric about the equator with even Ntheta
   double r_out = 0, r_last = 0, outer_coef = 0;  // outer_coef = 3 r_out^2 / dV3_N
+  double r_in = 0, r_first = 0, inner_coef = 0;  // inner_coef = 3 r_in^2 / dV3_1 (regular interior)
   FftSchedule sched{};
 
   // device tables owned by the plan
@@ -137,6 +139,8 @@ struct Plan {
   double* d_lam = nullptr;        // [mh][nth] lambda_Omega,l,m (descending in l)
   double* d_kappa = nullptr;      // [mh][nth] outer-face gradient per unit f_N
   double* d_outer = nullptr;      // [mh][nth] outer diagonal term of the radial row N
+  double* d_inner = nullptr;      // [mh][nth] inner diagonal term of the radial row 1 (0 with zero flux)
+  double* d_ishell = nullptr;     // [mh][j][j'] H_m diag(inner_m) (H^T W)_m (regular interior only)
   double* d_HtW = nullptr;        // [mh][l][j] (H^T W)_m
   double* d_H = nullptr;          // [mh][j][l] H_m
   double* d_HtWp = nullptr;       // parity grids: [mh][2][h][h] (H^T W)_m,p[l][j], h = nth/2, p = even/odd
@@ -265,7 +269,13 @@ cudaError_t stencil_f64(const Plan& p, const double* phi, double* out, cudaStrea
 cudaError_t outer_term_f64(const Plan& p, const double* phi, double* out, cudaStream_t s);
 // out[m] = H_m diag(outer[m]) (H^T W)_m in[m] for the two real columns of one shell spectrum.
 cudaError_t shell_kappa_f64(const Plan& p, const double* in, double* out, cudaStream_t s);
+// the same with the per-m shell operator O ([mh][j][j'])
+cudaError_t shell_apply_f64(const Plan& p, const double* O, const double* in, double* out, cudaStream_t s);
+// O = H diag(diag) H^T W per m, into dst
+cudaError_t shell_operator_f64(const Plan& p, const double* diag, double* dst, cudaStream_t s);
 cudaError_t outer_operator_f64(const Plan& p, cudaStream_t s);
+// Regular-interior inner term on the first shell: out[0] += O_in phi[0].
+cudaError_t inner_term_f64(const Plan& p, const double* phi, double* out, cudaStream_t s);
 // Face gradients of phi (radial [nr+1][nth][nphi], polar [nr][nth+1][nphi], azimuthal
 // [nr][nth][nphi]); the outer radial face carries the boundary condition's gradient.
 cudaError_t face_gradients_f64(const Plan& p, const double* phi, double* gr, double* gt, double* gp, cudaStream_t s);

@@ -73,6 +73,16 @@ extern "C" int sp_apply_laplacian_noalloc(sp_plan* plan, const double* phi, doub
       });
       P.launches += 2;
     }
+    if (e == cudaSuccess && P.inner_bc == SP_INNER_REGULAR) {
+      // the regular-interior term of the first shell, through the same scratch (stream order)
+      e = sp::timed_launch(P, sp::kKOuter, s, [&] {
+        cudaError_t r = sp::fft_forward_f64(P, phi, 1, 1.0 / P.nphi, shell_a, s);
+        if (r == cudaSuccess) r = sp::shell_apply_f64(P, P.d_ishell, shell_a, shell_b, s);
+        if (r == cudaSuccess) r = sp::fft_inverse_f64(P, shell_b, 1, out, true, s);
+        return r;
+      });
+      P.launches += 2;
+    }
     if (e != cudaSuccess) st = SP_ERR_CUDA;
   }
   if (prev != P.device) cudaSetDevice(prev);

@@ -44,6 +44,7 @@ bool make_schedule(int n, sp::FftSchedule* s) {
   while (r % 4 == 0) { if (s->nstages >= sp::kMaxStages) return false; s->radix[s->nstages++] = 4; r /= 4; }
   while (r % 2 == 0) { if (s->nstages >= sp::kMaxStages) return false; s->radix[s->nstages++] = 2; r /= 2; }
   while (r % 3 == 0) { if (s->nstages >= sp::kMaxStages) return false; s->radix[s->nstages++] = 3; r /= 3; }
+  while (r % 5 == 0) { if (s->nstages >= sp::kMaxStages) return false; s->radix[s->nstages++] = 5; r /= 5; }
   if (r != 1) return false;
   int ns = 1;
   for (int st = 0; st < s->nstages; ++st) {
@@ -86,6 +87,8 @@ void free_tables(Plan* p) {
     cudaFree(p->d_lam);
     cudaFree(p->d_kappa);
     cudaFree(p->d_outer);
+    cudaFree(p->d_inner);
+    cudaFree(p->d_ishell);
     cudaFree(p->d_HtW);
     cudaFree(p->d_H);
     cudaFree(p->d_HtWp);
@@ -444,6 +447,12 @@ int apply_laplacian_impl(Plan* p, const double* phi, double* out, cudaStream_t s
     // FFT of the last shell, kappa in the eigenbasis, inverse FFT accumulated: 3 launches
     st = launch_status(sp::timed_launch(P, sp::kKOuter, s, [&] { return sp::outer_term_f64(P, phi, out, s); }));
     P.launches += 2;
+    if (st) return st;
+  }
+  if (P.inner_bc == SP_INNER_REGULAR) {
+    // the same for the first shell with the regular-interior operator
+    st = launch_status(sp::timed_launch(P, sp::kKOuter, s, [&] { return sp::inner_term_f64(P, phi, out, s); }));
+    P.launches += 2;
   }
   return st;
 }
@@ -501,11 +510,33 @@ const char* sp_status_string(int status) {
 
 int sp_plan_create(const double* r_if, int nr, const double* th_if_in, int nth, int nphi, int outer_bc,
                    double G, int precision, double tol, int max_iter, void* stream, sp_plan** out) {
-  if (!out || !r_if) return SP_ERR_INVALID_ARG;
+  sp_plan_desc d = {};
+  d.r_interfaces = r_if;
+  d.Nr = nr;
+  d.theta_interfaces = th_if_in;
+  d.Ntheta = nth;
+  d.Nphi = nphi;
+  d.inner_bc = SP_INNER_ZERO_FLUX;
+  d.outer_bc = outer_bc;
+  d.G = G;
+  d.precision = precision;
+  d.tol = tol;
+  d.max_iter = max_iter;
+  return sp_plan_create_ex(&d, stream, out);
+}
+
+int sp_plan_create_ex(const sp_plan_desc* desc, void* stream, sp_plan** out) {
+  if (!out || !desc || !desc->r_interfaces) return SP_ERR_INVALID_ARG;
+  const double* r_if = desc->r_interfaces;
+  const double* th_if_in = desc->theta_interfaces;
+  const int nr = desc->Nr, nth = desc->Ntheta, nphi = desc->Nphi, outer_bc = desc->outer_bc;
+  const int precision = desc->precision, max_iter = desc->max_iter;
+  const double G = desc->G, tol = desc->tol;
   *out = nullptr;
   cudaGetLastError();   // an earlier failed call of this thread is not this call's error
   if (nr < 1 || nth < 1 || nphi < 1) return SP_ERR_GRID;
   if (outer_bc != SP_OUTER_MULTIPOLE && outer_bc != SP_OUTER_DIRICHLET) return SP_ERR_INVALID_ARG;
+  if (desc->inner_bc != SP_INNER_ZERO_FLUX && desc->inner_bc != SP_INNER_REGULAR) return SP_ERR_INVALID_ARG;
   if (precision != SP_FP64 && precision != SP_MIXED_BF16X3 && precision != SP_MIXED_BF16X6) return SP_ERR_INVALID_ARG;
   if (!std::isfinite(G)) return SP_ERR_INVALID_ARG;
   if (nth > sp::kMaxNtheta || nphi > sp::kMaxNphi) return SP_ERR_UNSUPPORTED;
@@ -527,6 +558,15 @@ int sp_plan_create(const double* r_if, int nr, const double* th_if_in, int nth, 
     for (int j = 0; j <= nth; ++j) th[j] = kPi * j / nth;
     th[nth] = kPi;
   }
+  // explicit centres strictly inside their cells
+  if (desc->r_centres)
+    for (int i = 0; i < nr; ++i)
+      if (!(desc->r_centres[i] > r_if[i] && desc->r_centres[i] < r_if[i + 1])) return SP_ERR_GRID;
+  if (desc->theta_centres)
+    for (int j = 0; j < nth; ++j)
+      if (!(desc->theta_centres[j] > th[j] && desc->theta_centres[j] < th[j + 1])) return SP_ERR_GRID;
+  const bool inner_regular = desc->inner_bc == SP_INNER_REGULAR && r_if[0] > 0.0;
+  if (inner_regular && precision != SP_FP64) return SP_ERR_UNSUPPORTED;
 
   Plan* p = new (std::nothrow) Plan();
   if (!p) return SP_ERR_OOM;
@@ -554,7 +594,7 @@ int sp_plan_create(const double* r_if, int nr, const double* th_if_in, int nth, 
   std::vector<double> rc(nr), dv3(nr), R(nr);
   for (int i = 0; i < nr; ++i) {
     const double rm = r_if[i], rp = r_if[i + 1];
-    rc[i] = 0.5 * (rm + rp);
+    rc[i] = desc->r_centres ? desc->r_centres[i] : 0.5 * (rm + rp);
     dv3[i] = rp * rp * rp - rm * rm * rm;
     R[i] = 3.0 * (rp * rp - rm * rm) / (2.0 * rc[i] * dv3[i]);
   }
@@ -567,11 +607,15 @@ int sp_plan_create(const double* r_if, int nr, const double* th_if_in, int nth, 
   p->r_out = r_if[nr];
   p->r_last = rc[nr - 1];
   p->outer_coef = 3.0 * p->r_out * p->r_out / dv3[nr - 1];
+  p->inner_bc = inner_regular ? SP_INNER_REGULAR : SP_INNER_ZERO_FLUX;
+  p->r_in = r_if[0];
+  p->r_first = rc[0];
+  p->inner_coef = 3.0 * r_if[0] * r_if[0] / dv3[0];
 
   std::vector<double> thc(nth), w(nth), dth(nth), sinc(nth), sinf(nth + 1), tface(nth > 1 ? nth - 1 : 1, 0.0);
   for (int j = 0; j <= nth; ++j) sinf[j] = (j == 0 || j == nth) ? 0.0 : std::sin(th[j]);
   for (int j = 0; j < nth; ++j) {
-    thc[j] = 0.5 * (th[j] + th[j + 1]);
+    thc[j] = desc->theta_centres ? desc->theta_centres[j] : 0.5 * (th[j] + th[j + 1]);
     w[j] = std::cos(th[j]) - std::cos(th[j + 1]);
     dth[j] = th[j + 1] - th[j];
     sinc[j] = std::sin(thc[j]);
@@ -582,6 +626,8 @@ int sp_plan_create(const double* r_if, int nr, const double* th_if_in, int nth, 
   bool symmetric = (nth % 2 == 0);
   for (int j = 0; symmetric && j <= nth; ++j)
     if (std::fabs(th[j] + th[nth - j] - kPi) > 1e-13) symmetric = false;
+  for (int j = 0; symmetric && j < nth; ++j)   // explicit centres must be mirrored as well
+    if (std::fabs(thc[j] + thc[nth - 1 - j] - kPi) > 1e-13) symmetric = false;
   if (symmetric) {
     for (int j = nth / 2; j < nth; ++j) {
       const int q = nth - 1 - j;
@@ -652,6 +698,7 @@ int sp_plan_create(const double* r_if, int nr, const double* th_if_in, int nth, 
     if (cudaMalloc(&p->d_lam, sizeof(double) * tab) != cudaSuccess ||
         cudaMalloc(&p->d_kappa, sizeof(double) * tab) != cudaSuccess ||
         cudaMalloc(&p->d_outer, sizeof(double) * tab) != cudaSuccess ||
+        cudaMalloc(&p->d_inner, sizeof(double) * tab) != cudaSuccess ||
         cudaMalloc(&p->d_HtW, sizeof(double) * mat) != cudaSuccess ||
         cudaMalloc(&p->d_H, sizeof(double) * mat) != cudaSuccess ||
         cudaMalloc(&p->d_err, sizeof(int)) != cudaSuccess ||
@@ -672,6 +719,10 @@ int sp_plan_create(const double* r_if, int nr, const double* th_if_in, int nth, 
     if (outer_bc == SP_OUTER_MULTIPOLE) {
       if (cudaMalloc(&p->d_oshell, sizeof(double) * mat) != cudaSuccess) { st = SP_ERR_OOM; break; }
       if ((st = launch_status(sp::outer_operator_f64(*p, s)))) break;
+    }
+    if (inner_regular) {
+      if (cudaMalloc(&p->d_ishell, sizeof(double) * mat) != cudaSuccess) { st = SP_ERR_OOM; break; }
+      if ((st = launch_status(sp::shell_operator_f64(*p, p->d_inner, p->d_ishell, s)))) break;
     }
     if (precision != SP_FP64 && (st = sp::mixed_create_tables(*p, s))) break;
     if (precision != SP_FP64 && cudaMallocHost(&p->h_red, 8 * sizeof(unsigned int)) != cudaSuccess) {
@@ -824,6 +875,7 @@ int sp_face_gradients(sp_plan* plan, const double* phi, double* g_r, double* g_t
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   st = launch_status(sp::timed_launch(*p, sp::kKStencil, s, [&] { return sp::face_gradients_f64(*p, phi, g_r, g_theta, g_phi, s); }));
   if (p->outer_bc == SP_OUTER_MULTIPOLE) p->launches += 3;   // the outer face's shell transforms
+  if (p->inner_bc == SP_INNER_REGULAR) p->launches += 3;     // the inner face's
   return st;
 }
 
@@ -937,7 +989,8 @@ namespace sp {
 // Device bytes of the tables a plan shares with its clones.
 size_t plan_table_bytes(const Plan& p) {
   const size_t tab = (size_t)p.mh * p.nth;
-  size_t b = ((p.d_oshell ? 3 : 2) + (p.d_HtWp ? 1 : 0)) * tab * p.nth * sizeof(double) + 3 * tab * sizeof(double) +
+  size_t b = ((p.d_oshell ? 3 : 2) + (p.d_ishell ? 1 : 0) + (p.d_HtWp ? 1 : 0)) * tab * p.nth * sizeof(double) +
+             4 * tab * sizeof(double) +
              (size_t)p.nr * sizeof(RadialRow) +
              (size_t)p.nth * sizeof(ThetaRow) + 2 * (size_t)p.nphi * (sizeof(double) + sizeof(float)) + tab * sizeof(double);
   if (p.mixed) {

@@ -59,7 +59,7 @@ def _create(r, th, nphi, **kw):
     ([-0.1, 0.5, 1.0], np.linspace(0, np.pi, 5), 8, S.SP_ERR_GRID),              # negative radius
     ([0.0, 0.5, 1.0], np.linspace(0, 3.0, 5), 8, S.SP_ERR_GRID),                  # theta not to pi
     ([0.0, 0.5, 1.0], np.array([0.0, 1.0, 0.9, np.pi]), 8, S.SP_ERR_GRID),       # theta not increasing
-    ([0.0, 0.5, 1.0], np.linspace(0, np.pi, 5), 10, S.SP_ERR_UNSUPPORTED),       # radix 5
+    ([0.0, 0.5, 1.0], np.linspace(0, np.pi, 5), 14, S.SP_ERR_UNSUPPORTED),       # radix 7
     ([0.0, 0.5, 1.0], np.linspace(0, np.pi, 200), 8, S.SP_ERR_UNSUPPORTED),      # Ntheta > 160
     ([0.0, 0.5, 1.0], np.linspace(0, np.pi, 5), 0, S.SP_ERR_GRID),               # no phi zones
 ])

@@ -54,6 +54,10 @@ CASES = [
     (9, 6, 384, "uniform", 0.0, 1),   # long phi lines
     (3, 4, 4096, "log", 0.0, 0),      # largest supported Nphi
     (2, 3, 3072, "uniform", 0.0, 1),  # long radix-3 line, Dirichlet
+    (6, 4, 5, "log", 0.0, 0),         # radix 5 alone
+    (9, 8, 40, "rand", 0.0, 0),       # radix 4 x 2 x 5
+    (5, 6, 150, "uniform", 0.2, 1),   # radix 2 x 3 x 5 x 5
+    (3, 4, 3000, "log", 0.0, 0),      # 4 x 2 x 3 x 5^3: long line with three radix-5 stages
 ]
 
 
@@ -264,3 +268,56 @@ def test_face_gradients_full_size(S):
     outer = O.outer_gradient(geo, phi[-1], O.OUTER_MULTIPOLE)
     assert np.max(np.abs(gr[-1] - outer)) <= 1e-12 * np.max(np.abs(outer))
     assert np.all(gr[0] == 0.0) and np.all(gt[:, 0] == 0.0) and np.all(gt[:, -1] == 0.0)
+
+
+@pytest.mark.parametrize("centres,inner,bc", [(True, 0, 0), (False, 1, 0), (True, 1, 1), (True, 1, 0)])
+def test_solve_centres_and_regular_interior(S, centres, inner, bc):
+    """Explicit cell centres (sp_plan_create_ex) and the regular-interior inner face
+    against the oracle's exact solution, with the operator and face gradients."""
+    nr, nth, nphi = 24, 10, 16
+    p = W.random_small(nr, nth, nphi, seed=21, grid="rand", r_inner=0.3, outer_bc=bc)
+    rng = np.random.default_rng(21)
+    rc = p.r_if[:-1] + rng.uniform(0.25, 0.75, nr) * np.diff(p.r_if) if centres else None
+    tc = p.th_if[:-1] + rng.uniform(0.25, 0.75, nth) * np.diff(p.th_if) if centres else None
+    geo = O.Geometry(p.r_if, p.th_if, p.nphi, r_centres=rc, th_centres=tc, inner_bc=inner)
+    plan = S.Plan(p.r_if, p.th_if, p.nphi, outer_bc=bc, r_centres=rc, theta_centres=tc, inner_bc=inner)
+    phi_d, _ = plan.solve(torch.from_numpy(p.rho).cuda())
+    phi = phi_d.cpu().numpy()
+    ref = O.solve_exact(geo, p.rho, outer_bc=bc)
+    assert rel_err(phi, ref) <= TOL
+    kmat = O.outer_operator_dense(geo) if bc == 0 else None
+    lap = plan.apply_laplacian(phi_d).cpu().numpy()
+    assert np.max(np.abs(lap - O.apply_laplacian(geo, phi, bc, kmat))) <= 1e-14 * np.max(O.abs_apply(geo, phi, bc, kmat))
+    # the boundary faces go through the per-m eigenbasis here and a dense eigensolve in
+    # the oracle: the float64 tolerance of the solve; the regular-interior face operator
+    # kappa_in(A_Omega) grows with the mode (q ~ sqrt(-lambda)), and the oracle's own dense
+    # and per-m routes to it differ by 2e-11 of its largest value on this grid
+    ftol = 3e-11 if inner else TOL
+    for a, b in zip([g.cpu().numpy() for g in plan.face_gradients(phi_d)], O.face_gradients(geo, phi, bc, kmat)):
+        assert np.max(np.abs(a - b)) <= ftol * np.max(np.abs(b))
+
+
+def test_symmetric_centres_keep_parity_and_asymmetric_do_not(S):
+    """Mirrored explicit theta centres keep the parity-split projections; the result
+    matches the oracle either way."""
+    nr, nth, nphi = 16, 12, 16
+    p = W.random_small(nr, nth, nphi, seed=5, grid="log")
+    half = p.th_if[:-1][: nth // 2] + 0.3 * np.diff(p.th_if)[: nth // 2]
+    sym = np.concatenate([half, np.pi - half[::-1]])
+    asym = p.th_if[:-1] + 0.3 * np.diff(p.th_if)
+    for tc in (sym, asym):
+        plan = S.Plan(p.r_if, p.th_if, p.nphi, theta_centres=tc)
+        phi = plan.solve(torch.from_numpy(p.rho).cuda())[0].cpu().numpy()
+        ref = O.solve_exact(O.Geometry(p.r_if, p.th_if, p.nphi, th_centres=tc), p.rho)
+        assert rel_err(phi, ref) <= TOL
+
+
+def test_create_ex_validation(S):
+    r = np.array([0.1, 0.5, 1.0])
+    th = np.linspace(0, np.pi, 5)
+    with pytest.raises(S.SpError) as e:
+        S.Plan(r, th, 8, r_centres=np.array([0.05, 0.7]))          # centre outside its cell
+    assert e.value.status == S.SP_ERR_GRID
+    with pytest.raises(S.SpError) as e:
+        S.Plan(r, th, 8, inner_bc=S.SP_INNER_REGULAR, precision=S.SP_MIXED_BF16X6)
+    assert e.value.status == S.SP_ERR_UNSUPPORTED

@@ -56,6 +56,9 @@ CASES = [
     (1600, 6, 4, "log", 0.0, 0),       # radial column beyond the shared-memory scan: ring-staged sweeps
     (4, 4, 1, "uniform", 0.0, 0),      # axisymmetric: one phi zone
     (3, 2, 2, "log", 0.0, 0),          # smallest even phi count
+    (20, 16, 80, "log", 0.0, 0),       # radix 4 x 4 x 5
+    (33, 12, 360, "rand", 0.1, 1),     # radix 4 x 2 x 3 x 3 x 5 (floor still below 1e-10)
+    (7, 5, 25, "uniform", 0.0, 0),     # odd Nphi, radix 5 x 5
 ]
 
 

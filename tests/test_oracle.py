@@ -522,3 +522,65 @@ def test_ellipsoid_density_integrates_exactly():
     assert np.all(p.rho[rc < 0.9] == 1.0) and np.all(p.rho[rc > 2.1] == 0.0)
     r = W.ellipsoid_r_interfaces("stretched", 512)
     assert abs(r[-1] - 48.7) < 0.1 and np.all(np.diff(r) > 0)
+
+
+# ------------------------------------ explicit centres, regular-interior inner face
+def _centred_geo(nr, nth, nphi, seed, inner_bc=O.INNER_ZERO_FLUX, r_inner=0.2, centres=True):
+    p = W.random_small(nr, nth, nphi, seed=seed, grid="rand", r_inner=r_inner)
+    rng = np.random.default_rng(seed)
+    rc = th = None
+    if centres:
+        rc = p.r_if[:-1] + rng.uniform(0.2, 0.8, nr) * np.diff(p.r_if)
+        th = p.th_if[:-1] + rng.uniform(0.2, 0.8, nth) * np.diff(p.th_if)
+    return p, O.Geometry(p.r_if, p.th_if, p.nphi, r_centres=rc, th_centres=th, inner_bc=inner_bc)
+
+
+@pytest.mark.parametrize("bc", [O.OUTER_MULTIPOLE, O.OUTER_DIRICHLET])
+@pytest.mark.parametrize("centres,inner", [(True, O.INNER_ZERO_FLUX), (False, O.INNER_REGULAR),
+                                           (True, O.INNER_REGULAR)])
+def test_separated_equals_dense_lu_centres_and_inner_face(centres, inner, bc):
+    """Explicit cell centres (R8') and the regular-interior inner face (R9) enter the
+    separated solve (per-mode inner row) and the assembled operator (dense inner term)
+    by independent routes; they agree to rounding."""
+    p, g = _centred_geo(5, 6, 8, seed=3, inner_bc=inner, centres=centres)
+    a = O.solve_separated(g, p.rho, outer_bc=bc)
+    b = O.solve_dense(g, p.rho, outer_bc=bc)
+    assert np.max(np.abs(a - b)) / np.max(np.abs(b)) <= 1e-13
+
+
+def test_midpoints_given_explicitly_change_nothing():
+    p = W.random_small(6, 5, 8, seed=4, grid="rand")
+    g0 = O.Geometry(p.r_if, p.th_if, p.nphi)
+    g1 = O.Geometry(p.r_if, p.th_if, p.nphi, r_centres=0.5 * (p.r_if[1:] + p.r_if[:-1]),
+                    th_centres=0.5 * (p.th_if[1:] + p.th_if[:-1]))
+    assert np.array_equal(O.solve_separated(g0, p.rho), O.solve_separated(g1, p.rho))
+
+
+def test_regular_interior_mimics_empty_core():
+    """With no mass inside r = 0.5, the regular-interior inner face at r_{1/2} = 0.5
+    reproduces the solution of the grid that also covers the empty core (same zones
+    beyond 0.5), to discretisation accuracy; zero flux there does not (it holds only for
+    the l = 0 part)."""
+    nth, nphi = 8, 8
+    r_full = W.uniform_r_interfaces(64)
+    th = W.uniform_theta_interfaces(nth)
+    g_full = O.Geometry(r_full, th, nphi)
+    rng = np.random.default_rng(6)
+    rho = np.zeros((64, nth, nphi))
+    rho[40:56] = rng.uniform(0.0, 1.0, (16, nth, nphi))
+    ref = O.solve_separated(g_full, rho)[32:]
+    g_reg = O.Geometry(r_full[32:], th, nphi, inner_bc=O.INNER_REGULAR)
+    g_zf = O.Geometry(r_full[32:], th, nphi)
+    reg = O.solve_separated(g_reg, rho[32:])
+    zf = O.solve_separated(g_zf, rho[32:])
+    scale = np.max(np.abs(ref))
+    err_reg = np.max(np.abs(reg - ref)) / scale
+    err_zf = np.max(np.abs(zf - ref)) / scale
+    assert err_reg < 2e-3 and err_zf > 10 * err_reg
+
+
+def test_kappa_inner_continuum_exponent():
+    """At the continuum eigenvalue -l(l+1) the regular exponent is q = l."""
+    for l in range(6):
+        k = O.kappa_inner(-l * (l + 1.0), 2.0, 2.0)
+        assert abs(k * 2.0 - l) <= 1e-13

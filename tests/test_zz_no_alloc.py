@@ -97,3 +97,20 @@ def test_noalloc_rejects_plans_beyond_its_scratch(S):
     assert _call_noalloc(S, plan, x, y) == S.SP_ERR_UNSUPPORTED
     with pytest.raises(S.SpError):
         S.sp_apply_laplacian_noalloc(plan.handle, x, y, p.rho.shape)
+
+
+def test_noalloc_regular_interior_plan(S):
+    """A plan with a regular-interior inner face adds the first shell's term, through the
+    same scratch: still bitwise sp_apply_laplacian."""
+    p = W.random_small(20, 12, 24, seed=3, grid="log", r_inner=0.2)
+    plan = S.Plan(p.r_if, p.th_if, p.nphi, inner_bc=S.SP_INNER_REGULAR)
+    rng = np.random.default_rng(2)
+    for _ in range(2):
+        phi = torch.from_numpy(rng.standard_normal(p.rho.shape)).cuda()
+        ref = plan.apply_laplacian(phi)
+        out = torch.full_like(phi, float("nan"))
+        launches = plan.launch_count()
+        assert _call_noalloc(S, plan, phi, out) == S.SP_OK
+        torch.cuda.synchronize()
+        assert plan.launch_count() - launches == 7
+        assert torch.equal(out, ref)
