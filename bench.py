@@ -219,6 +219,10 @@ def run_ours(args, rank, world, local):
         plans["mixed_x3"] = S.Plan(p.r_if, p.th_if, p.nphi, precision=S.SP_MIXED_BF16X3, tol=1e-10)
     if precision == "mixed":
         plans["mixed"] = S.Plan(p.r_if, p.th_if, p.nphi, precision=S.SP_MIXED_BF16X6, tol=1e-10)
+    if precision == "mixed" and not args.headline_only:
+        # the same 6-product solve refined with a float64 iterate and the float64 stencil
+        plans["mixed_f64_residual"] = S.Plan(p.r_if, p.th_if, p.nphi, precision=S.SP_MIXED_BF16X6, tol=1e-10)
+        plans["mixed_f64_residual"].set_residual(S.SP_RESIDUAL_FLOAT64)
     head = plans[precision]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
 
@@ -311,6 +315,7 @@ def run_ours(args, rank, world, local):
     for name, rr in results.items():
         line[f"{name}_zones_per_s"] = whole_job_rate(zones, args.steps, world, rr["ms"] / 1e3)
         line[f"{name}_ms_per_step"] = rr["ms"] / args.steps
+        line[f"{name}_iterations"] = rr["infos"][-1].get("iterations")
     line["roofline"] = roofline(r["timing"], p, precision, args.steps, r["infos"][-1].get("iterations", 2))
     line["projection_tensor"] = projection_tensor_rate(r["timing"], p, precision)
     line["kernel_source_sha"] = kernel_source_hash()

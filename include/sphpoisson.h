@@ -79,17 +79,29 @@ enum { SP_INNER_ZERO_FLUX = 0, SP_INNER_REGULAR = 1 };
  *                    needs fewer refinement steps. */
 enum { SP_FP64 = 0, SP_MIXED_BF16X3 = 1, SP_MIXED_BF16X6 = 2 };
 
+/* Arithmetic of the mixed modes' refinement residual (sp_plan_set_residual; no
+ * counterpart in the paper).  SP_RESIDUAL_FLOAT_FLOAT: the iterate is kept as a pair of
+ * floats (48 bits) and the residual evaluated in float-float arithmetic, with no
+ * float64 instructions (GB300's float64 rate is 1/64 of float32); its precision floor
+ * is 8 x 2^-48 x (Nphi / 2 pi)^2.  SP_RESIDUAL_FLOAT64: the iterate is float64 (held in
+ * the caller's output) and the residual is the float64 finite-volume stencil; floor
+ * 2^-40 (measured fixed points ~3e-14 up to Nphi = 4096), at several times the
+ * residual's cost.  SP_RESIDUAL_AUTO (the default) takes float-float where its floor is
+ * below tol and float64 otherwise: at tol 1e-10 float-float up to Nphi = 372. */
+enum { SP_RESIDUAL_AUTO = 0, SP_RESIDUAL_FLOAT_FLOAT = 1, SP_RESIDUAL_FLOAT64 = 2 };
+
 typedef struct {
     int iterations;        /* low-precision solves performed (1 for SP_FP64) */
     int precision_used;    /* SP_FP64, SP_MIXED_BF16X3 or SP_MIXED_BF16X6 */
     double last_update;    /* max|e|/max|Phi| of the last correction (0 for SP_FP64) */
     double est_rel_error;  /* estimated max|Phi - Phi_exact|/max|Phi| (0 for SP_FP64): the larger of
                               the refinement's contraction estimate and its precision floor
-                              8 x 2^-48 x (Nphi / 2 pi)^2 (the 48-bit float-float iterate seen
-                              through the phi part of the operator; 4.7e-11 at Nphi = 256).
-                              When the floor exceeds tol the solve stops and returns
-                              SP_ERR_NOT_CONVERGED: use SP_FP64 or a looser tol there
-                              (at tol 1e-10 the mixed modes reach Nphi = 372) */
+                              8 x 2^-48 x (Nphi / 2 pi)^2 with the float-float residual (the
+                              48-bit iterate seen through the phi part of the operator;
+                              4.7e-11 at Nphi = 256), 2^-40 with the float64 one.  When the
+                              floor exceeds tol the solve stops and returns
+                              SP_ERR_NOT_CONVERGED (with SP_RESIDUAL_AUTO only for tol below
+                              2^-40 or a float-float residual chosen explicitly) */
     int status;            /* sp_status of the solve */
     double update_history[8]; /* max|e_k|/max|Phi| of the first 8 solves (k = 0 is the first solve) */
 } sp_solve_info;
@@ -104,8 +116,8 @@ typedef struct {
  *  precision         SP_FP64, SP_MIXED_BF16X3 or SP_MIXED_BF16X6 (mixed: Ntheta <= 128)
  *  tol, max_iter     refinement target max|Phi-Phi_exact|/max|Phi| and iteration cap
  *                    (mixed precision only; e.g. 1e-10 and 8).  tol below the mixed
- *                    modes' precision floor 8 x 2^-48 x (Nphi / 2 pi)^2 cannot be met
- *                    (see sp_solve_info.est_rel_error): 1e-10 holds up to Nphi = 372
+ *                    modes' precision floor cannot be met (see sp_solve_info.est_rel_error
+ *                    and SP_RESIDUAL_AUTO)
  *  stream            set-up work (theta eigensolve on the GPU) runs on this stream and
  *                    is complete when the call returns
  *  out               receives the plan; the plan owns its tables and, until
@@ -249,6 +261,10 @@ int sp_plan_get_eigen(const sp_plan* plan, double* lambda, double* H, double* ka
 int sp_plan_set_timing(sp_plan* plan, int enable);
 int sp_plan_collect_timing(sp_plan* plan);
 int sp_plan_get_timing(const sp_plan* plan, double* ms, long long* count, int n);
+
+/* Choose the refinement residual of a mixed-precision plan (SP_RESIDUAL_*; the default
+ * is SP_RESIDUAL_AUTO).  A float64 plan ignores it.  Drops the plan's captured graph. */
+int sp_plan_set_residual(sp_plan* plan, int mode);
 
 /* CUDA-graph replay of a mixed solve's first phase (no counterpart in the paper; on by
  * default).  Phase A of sp_solve and sp_solve_batched -- the first low-precision solve,

@@ -8,7 +8,7 @@ streams."""
 from ._binding import (  # noqa: F401
     SP_ERR_CUDA, SP_ERR_DEVICE_CHECK, SP_ERR_GRID, SP_ERR_INVALID_ARG, SP_ERR_NOT_CONVERGED, SP_ERR_OOM,
     SP_ERR_TIMEOUT, SP_ERR_UNSUPPORTED, SP_FP64, SP_MIXED_BF16X3, SP_MIXED_BF16X6, SP_OK, SP_OUTER_DIRICHLET,
-    SP_OUTER_MULTIPOLE, SP_INNER_ZERO_FLUX, SP_INNER_REGULAR, Plan, PlanDesc, sp_plan_create_ex, SolveInfo, SpError, declared_symbols, lib, library_path,
+    SP_OUTER_MULTIPOLE, SP_INNER_ZERO_FLUX, SP_INNER_REGULAR, SP_RESIDUAL_AUTO, SP_RESIDUAL_FLOAT_FLOAT, SP_RESIDUAL_FLOAT64, Plan, PlanDesc, sp_plan_create_ex, SolveInfo, SpError, declared_symbols, lib, library_path,
     sp_apply_laplacian, sp_apply_laplacian_noalloc, sp_face_gradients, sp_plan_create, sp_plan_destroy, sp_plan_get_eigen, sp_plan_last_status,
     sp_plan_set_workspace, sp_plan_workspace_bytes, sp_plan_set_timing, sp_plan_collect_timing,
     sp_plan_get_timing, sp_plan_launch_count, KERNEL_NAMES, sp_plan_clone, sp_solve_batched, sp_server_create,

@@ -27,6 +27,9 @@ SP_OUTER_MULTIPOLE = 0
 SP_OUTER_DIRICHLET = 1
 SP_INNER_ZERO_FLUX = 0
 SP_INNER_REGULAR = 1
+SP_RESIDUAL_AUTO = 0
+SP_RESIDUAL_FLOAT_FLOAT = 1
+SP_RESIDUAL_FLOAT64 = 2
 SP_FP64 = 0
 SP_MIXED_BF16X3 = 1
 SP_MIXED_BF16X6 = 2
@@ -95,6 +98,7 @@ _SIGS = {
     "sp_plan_collect_timing": (C.c_int, [C.c_void_p]),
     "sp_plan_get_timing": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "sp_plan_set_graphs": (C.c_int, [C.c_void_p, C.c_int]),
+    "sp_plan_set_residual": (C.c_int, [C.c_void_p, C.c_int]),
     "sp_plan_launch_count": (C.c_longlong, [C.c_void_p]),
     "sp_plan_destroy": (C.c_int, [C.c_void_p]),
     "sp_status_string": (C.c_char_p, [C.c_int]),
@@ -433,6 +437,10 @@ class Plan:
 
     def set_graphs(self, enable=True):
         _check(lib().sp_plan_set_graphs(self._h, int(bool(enable))), "sp_plan_set_graphs")
+
+    def set_residual(self, mode=SP_RESIDUAL_AUTO):
+        """Arithmetic of the mixed modes' refinement residual (SP_RESIDUAL_*)."""
+        _check(lib().sp_plan_set_residual(self._h, int(mode)), "sp_plan_set_residual")
 
     def launch_count(self) -> int:
         return sp_plan_launch_count(self._h)

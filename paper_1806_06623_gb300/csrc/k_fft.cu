@@ -395,7 +395,7 @@ __global__ void __launch_bounds__(256, 3) k_fft_fwd(const Tin* __restrict__ in, 
   }
 }
 
-enum InvOut { kInvWrite = 0, kInvAccumulate = 1, kInvPairUpdate = 2 };
+enum InvOut { kInvWrite = 0, kInvAccumulate = 1, kInvPairUpdate = 2, kInvF64Update = 3 };
 
 // Inverse: half spectra spec[m][i][c][j] (row stride Ntheta) of lines [line0, line0+nl)
 // -> real lines:
@@ -407,6 +407,8 @@ enum InvOut { kInvWrite = 0, kInvAccumulate = 1, kInvPairUpdate = 2 };
 //    the updated iterate is also written as float64 (the solve's output when this
 //    correction turns out to be the last), and with hilo = 0 only there (out and phi_lo
 //    are then left as they were).
+//  MODE kInvF64Update: float64 iterate out = e (first) or out + e, with the same two
+//    reductions (max|e|, max|out| as float).
 template <typename T, typename Tout, int MODE>
 __global__ void __launch_bounds__(256, 3) k_fft_inv(const T* __restrict__ spec, int nlines, int nth, int nrs,
                                                  FftSchedule sch, const T* __restrict__ twid, int lpc,
@@ -493,7 +495,21 @@ __global__ void __launch_bounds__(256, 3) k_fft_inv(const T* __restrict__ spec, 
     const CT* z = Z + p * PS;
     const bool hasb = 2 * p + 1 < nl;
     const size_t o0 = (size_t)(line0 + 2 * p) * n;
-    if (MODE != kInvPairUpdate) {
+    if (MODE == kInvF64Update) {
+      for (int q = lane; q < n; q += 32) {
+        const CT v = z[q];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (h == 1 && !hasb) continue;
+          const size_t o = o0 + (size_t)h * n + q;
+          const float e = (float)(h ? v.y : v.x);
+          const double nv = first ? (double)e : (double)out[o] + (double)e;
+          out[o] = (Tout)nv;
+          me = fmaxf(me, fabsf(e));
+          mp = fmaxf(mp, fabsf((float)nv));
+        }
+      }
+    } else if (MODE != kInvPairUpdate) {
       for (int q = lane; q < n; q += 32) {
         const CT v = z[q];
         if (MODE == kInvWrite) {
@@ -592,7 +608,7 @@ __global__ void __launch_bounds__(256, 3) k_fft_inv(const T* __restrict__ spec, 
       }
     }
   }
-  if (MODE == kInvPairUpdate) {
+  if (MODE == kInvPairUpdate || MODE == kInvF64Update) {
     for (int o = 16; o > 0; o >>= 1) {
       me = fmaxf(me, __shfl_xor_sync(0xffffffffu, me, o));
       mp = fmaxf(mp, __shfl_xor_sync(0xffffffffu, mp, o));
@@ -699,6 +715,19 @@ cudaError_t fft_forward_panel(const Plan& p, const void* in, bool in_double, flo
     if (e != cudaSuccess) return e;
   }
   return cudaGetLastError();
+}
+
+cudaError_t fft_inverse_update64(const Plan& p, const float* spec, double* phi, bool first, unsigned int* red,
+                                 cudaStream_t s) {
+  const int nlines = p.nr * p.nth;
+  const int lpc = lines_per_cta<float>(p.nphi, nlines);
+  const size_t smem = fft_smem<float>(p.nphi, lpc);
+  auto kern = k_fft_inv<float, double, kInvF64Update>;
+  cudaError_t e = prep(kern, smem);
+  if (e != cudaSuccess) return e;
+  e = launch_pdl(kern, dim3((nlines + lpc - 1) / lpc), dim3(32 * kWarps), smem, s, spec, nlines, p.nth, p.nr, p.sched,
+                 (const float*)p.d_twid32, lpc, phi, (float*)nullptr, first ? 1 : 0, 0, 1, red, 0, (double*)nullptr);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t fft_inverse_update(const Plan& p, const float* spec, float* phi_hi, float* phi_lo, bool first, bool lo_read,

@@ -1142,6 +1142,62 @@ cudaError_t residual_ff(const Plan& p, const double* rho, cudaStream_t s) {
   return rows(p.nr - 1, p.nr, s);
 }
 
+// Refinement residual in float64 for a float64 iterate: r = 4 pi G rho - (Delta Phi) with
+// the operator of Eq. fin_vol3 (the float64 stencil's arithmetic), stored in float32 as
+// the next low-precision right-hand side; the multipole term of the last shell comes
+// from outer_shell.
+__global__ void __launch_bounds__(256) k_residual_f64(const double* __restrict__ rho, const double* __restrict__ phi,
+                                                      const double* __restrict__ outer_shell, float* __restrict__ r,
+                                                      const RadialRow* __restrict__ rad,
+                                                      const ThetaRow* __restrict__ th, int nr, int nth, int nphi,
+                                                      int dirichlet, double dir_coef, double four_pi_g) {
+  pdl_wait();
+  const size_t n = (size_t)nr * nth * nphi;
+  const size_t shell = (size_t)nth * nphi;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(idx % nphi);
+    const size_t ij = idx / nphi;
+    const int j = (int)(ij % nth);
+    const int i = (int)(ij / nth);
+    const double c = phi[idx];
+    const RadialRow rr = rad[i];
+    const ThetaRow tr = th[j];
+    double v = 0.0;
+    if (i > 0) v += rr.sub * (phi[idx - shell] - c);
+    if (i < nr - 1) v += rr.sup * (phi[idx + shell] - c);
+    double a = 0.0;
+    if (j > 0) a += tr.tm * (phi[idx - nphi] - c);
+    if (j < nth - 1) a += tr.tp * (phi[idx + nphi] - c);
+    const size_t kp = (k + 1 == nphi) ? idx - k : idx + 1;
+    const size_t km = (k == 0) ? idx + (nphi - 1) : idx - 1;
+    a += tr.sphi * ((phi[kp] - c) + (phi[km] - c));
+    v += rr.R * a;
+    if (i == nr - 1) v += dirichlet ? dir_coef * c : outer_shell[idx - (size_t)(nr - 1) * shell];
+    r[idx] = (float)(four_pi_g * rho[idx] - v);
+  }
+}
+
+cudaError_t residual_f64(const Plan& p, const double* rho, const double* phi, cudaStream_t s) {
+  const MixedTables& x = *p.mixed;
+  const size_t sh = (size_t)p.nth * p.nphi;
+  const size_t n = (size_t)p.nr * sh;
+  const bool dir = p.outer_bc == SP_OUTER_DIRICHLET;
+  cudaError_t e;
+  if (!dir) {
+    // the multipole term of the last shell from the float64 iterate itself
+    const size_t off = (size_t)(p.nr - 1) * sh;
+    if ((e = fft_forward_f64(p, phi + off, 1, 1.0 / p.nphi, p.shell, s)) != cudaSuccess) return e;
+    if ((e = shell_kappa_f64(p, p.shell, p.shell2, s)) != cudaSuccess) return e;
+    if ((e = fft_inverse_f64(p, p.shell2, 1, x.outer_shell, false, s)) != cudaSuccess) return e;
+  }
+  size_t blocks = (n + 255) / 256;
+  if (blocks > (size_t)p.num_sms * 32) blocks = (size_t)p.num_sms * 32;
+  e = launch_pdl(k_residual_f64, dim3((unsigned)blocks), dim3(256), 0, s, rho, phi, (const double*)x.outer_shell, x.r32,
+                 (const RadialRow*)p.d_rad, (const ThetaRow*)p.d_theta, p.nr, p.nth, p.nphi, dir ? 1 : 0,
+                 dir ? -p.outer_coef / (p.r_out - p.r_last) : 0.0, 4.0 * 3.14159265358979323846264338327950288 * p.G);
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
 cudaError_t split_iterate(const Plan& p, const double* phi, cudaStream_t s) {
   const MixedTables& x = *p.mixed;
   const size_t n = (size_t)p.nr * p.nth * p.nphi;

@@ -89,6 +89,7 @@ struct MixedTables {
   float* phi_hi = nullptr;         // [nr][nth][nphi] iterate as float-float
   float* phi_lo = nullptr;
   bool lo_zero = false;            // the iterate is a first solve's: its low word is zero and not stored
+  bool resid64 = false;            // float64 iterate (in the caller's output) and float64 residual
   const double* iter64 = nullptr;  // non-null: the iterate is stored only there, in float64 (hi, lo stale)
   float* panel = nullptr;          // spectral panel [mh][2nr][kstride] float32 (s_tilde, then f)
   float* d32 = nullptr;            // [mh][2nr][nth] projection output (s_hat, then g)
@@ -302,6 +303,10 @@ bool first_correction_f64_only(const Plan& p);   // the first correction stores 
 cudaError_t tc_project(const Plan& p, bool inverse, cudaStream_t s);   // pan -> d32
 cudaError_t thomas_mixed(const Plan& p, cudaStream_t s);   // d32 -> pan (f); float32 + float64 low modes
 cudaError_t residual_ff(const Plan& p, const double* rho, cudaStream_t s);  // iterate -> r32
+cudaError_t residual_f64(const Plan& p, const double* rho, const double* phi, cudaStream_t s);  // float64 iterate -> r32
+// inverse FFT adding the correction into a float64 iterate (first: phi = e), reductions into red
+cudaError_t fft_inverse_update64(const Plan& p, const float* spec, double* phi, bool first, unsigned int* red,
+                                 cudaStream_t s);
 int create_side_stream(Plan& p);   // side stream and events of a mixed multipole plan; sp_status
 
 // ---- solve phases shared by sp_solve, sp_solve_batched and the server ----
@@ -316,7 +321,8 @@ struct MixedRun {
   bool floor_limited = false;   // the iterate's precision floor is above the tolerance
 };
 constexpr int kRedErrWord = 4;   // h_red: two slots of (max|e|, max|Phi|), then the status word
-int mixed_start(Plan* p, const double* rho, cudaStream_t s);
+int mixed_start(Plan* p, const double* rho, double* phi, cudaStream_t s);
+double mixed_floor(const Plan& p, bool resid64);   // precision floor of the refinement
 int mixed_correct(Plan* p, const double* rho, double* phi, cudaStream_t s);
 int mixed_issue_read(Plan* p, cudaStream_t s, MixedRun& R);
 // First low-precision solve and (max_iter >= 1) the first correction, each with the copy

@@ -179,6 +179,14 @@ int lp_solve(Plan* p, const void* in, bool in_double, float scale, double* phi, 
   if ((st = launch_status(sp::timed_launch(P, sp::kKThomas, s, [&] { return sp::thomas_mixed(P, s); })))) return st;
   if ((st = launch_status(sp::timed_launch(P, sp::kKGemmInv, s, [&] { return sp::tc_project(P, true, s); }))))
     return st;
+  if (x.resid64) {
+    // float64 iterate in the caller's output: phi = e (first) or phi + e
+    st = launch_status(sp::timed_launch(P, sp::kKFftInv, s, [&] {
+      return sp::fft_inverse_update64(P, x.d32, phi, first, x.red, s); }));
+    x.lo_zero = false;
+    x.iter64 = nullptr;
+    return st;
+  }
   const bool lo_read = !first && !x.lo_zero;
   const bool f64_only = !first && phi && x.lo_zero && sp::first_correction_f64_only(P);
   st = launch_status(sp::timed_launch(P, sp::kKFftInv, s, [&] {
@@ -192,11 +200,25 @@ int lp_solve(Plan* p, const void* in, bool in_double, float scale, double* phi, 
 
 namespace sp {
 
-// First low-precision solve of L Phi = 4 pi G rho (asynchronous).
-int mixed_start(Plan* p, const double* rho, cudaStream_t s) {
+// First low-precision solve of L Phi = 4 pi G rho (asynchronous); with a float64 iterate
+// its result goes straight to phi.
+int mixed_start(Plan* p, const double* rho, double* phi, cudaStream_t s) {
   p->phi64_written = nullptr;
   SP_CUDA(cudaMemsetAsync(p->mixed->red, 0, 2 * sizeof(unsigned int), s));
-  return lp_solve(p, rho, true, (float)(4.0 * kPi * p->G / p->nphi), nullptr, true, s);
+  const bool r64 = p->mixed->resid64;
+  const int st = lp_solve(p, rho, true, (float)(4.0 * kPi * p->G / p->nphi), r64 ? phi : nullptr, true, s);
+  if (st == SP_OK && r64) p->phi64_written = phi;
+  return st;
+}
+
+// Precision floor of the refinement (see decide_one).  Float-float iterate and residual:
+// 8 x 2^-48 x (Nphi / 2 pi)^2.  Float64 iterate and residual: 2^-40, flat (measured fixed
+// points 1.2e-14 .. 3.2e-14 for Nphi = 256 .. 4096 at Nr x Ntheta = 4x8, 16x64, 40x32,
+// the level of the float64 separated solve itself).
+double mixed_floor(const Plan& p, bool resid64) {
+  if (resid64) return 9.094947017729282e-13;
+  const double kq = p.nphi / (2.0 * kPi);
+  return 8.0 * 3.552713678800501e-15 * kq * kq;
 }
 
 // Whether the first correction stores the updated iterate only as the float64 output:
@@ -209,6 +231,15 @@ bool first_correction_f64_only(const Plan& p) { return p.mixed->np == 3; }
 int mixed_correct(Plan* p, const double* rho, double* phi, cudaStream_t s) {
   Plan& P = *p;
   int st;
+  if (P.mixed->resid64) {
+    // float64 residual of the float64 iterate held in phi (shell term first on this stream)
+    if ((st = launch_status(timed_launch(P, kKResidual, s, [&] { return residual_f64(P, rho, phi, s); })))) return st;
+    if (P.outer_bc == SP_OUTER_MULTIPOLE) P.launches += 3;   // shell FFT, apply, inverse FFT
+    SP_CUDA(cudaMemsetAsync(P.mixed->red, 0, 2 * sizeof(unsigned int), s));
+    st = lp_solve(p, P.mixed->r32, false, (float)(1.0 / P.nphi), phi, false, s);
+    if (st == SP_OK) P.phi64_written = phi;
+    return st;
+  }
   if (P.mixed->iter64) {   // the iterate lives in float64 only: rebuild its float-float words
     if ((st = launch_status(timed_launch(P, kKUpdate, s, [&] { return split_iterate(P, P.mixed->iter64, s); }))))
       return st;
@@ -236,7 +267,7 @@ namespace {
 
 int phase_a_direct(Plan* p, const double* rho, double* phi, cudaStream_t s, MixedRun& R) {
   int st;
-  if ((st = mixed_start(p, rho, s))) return st;
+  if ((st = mixed_start(p, rho, phi, s))) return st;
   if ((st = mixed_issue_read(p, s, R))) return st;
   if (p->max_iter >= 1) {
     if ((st = mixed_correct(p, rho, phi, s))) return st;
@@ -304,9 +335,9 @@ int mixed_phase_a(Plan* p, const double* rho, double* phi, cudaStream_t s, Mixed
   // and the iterate is in the state its one correction leaves
   R.pending = p->ga_pending;
   R.next_slot = p->ga_pending & 1;
-  p->phi64_written = p->max_iter >= 1 ? phi : nullptr;
+  p->phi64_written = (p->max_iter >= 1 || p->mixed->resid64) ? phi : nullptr;
   p->mixed->lo_zero = false;
-  p->mixed->iter64 = first_correction_f64_only(*p) ? phi : nullptr;
+  p->mixed->iter64 = (first_correction_f64_only(*p) && !p->mixed->resid64) ? phi : nullptr;
   p->launches += p->ga_launches;
   return SP_OK;
 }
@@ -317,7 +348,8 @@ namespace {
 // the current one is smaller by the contraction factor of the refinement, taken as the
 // larger of the observed ratio of successive corrections and a bound for the mode
 // (largest ratio measured over the stellar, ragged, point-mass and random-source
-// workloads, times two: 1.9e-5 for 6 products, 1.2e-3 for 3 products).
+// workloads at Nphi <= 256, times two: 1.9e-5 for 6 products, 1.2e-3 for 3 products;
+// grown as (Nphi/256)^2 beyond).
 void decide_one(Plan* p, MixedRun& R, const unsigned int* slot) {
   float v[2];
   std::memcpy(v, slot, sizeof(v));
@@ -335,7 +367,12 @@ void decide_one(Plan* p, MixedRun& R, const unsigned int* slot) {
   }
   R.last = e_cur / R.pmax;
   if (R.iters < 8) R.hist[R.iters] = R.last;
-  const double bound = (p->mixed->np == 3) ? 4e-5 : 2.5e-3;
+  // the bounds were measured for Nphi <= 256; the low-precision solve's relative error
+  // on the high phi modes grows with their eigenvalue range, so beyond that they grow as
+  // (Nphi / 256)^2 (measured single-correction contractions of the 6-product mode:
+  // ~2e-4 at Nphi = 1024, ~8e-4 at 2048)
+  const double grow = p->nphi > 256 ? (p->nphi / 256.0) * (p->nphi / 256.0) : 1.0;
+  const double bound = ((p->mixed->np == 3) ? 4e-5 : 2.5e-3) * grow;
   const double ratio = (R.iters >= 2 && R.e_prev > 0.0) ? e_cur / R.e_prev : 0.0;
   const double c = ratio > bound ? ratio : bound;
   R.est = c < 1.0 ? R.last * c / (1.0 - c) : R.last;
@@ -345,8 +382,7 @@ void decide_one(Plan* p, MixedRun& R, const unsigned int* slot) {
   // from the exact solution by up to floor = 8 x 2^-48 x (Nphi / 2 pi)^2 (8: the largest
   // measured ratio of error to 2^-48 (Nphi / 2 pi)^2 was 5.9, over Ntheta 8 and 64,
   // Nphi 128..4096).  Below the floor no further correction helps.
-  const double kq = p->nphi / (2.0 * kPi);
-  const double floor = 8.0 * 3.552713678800501e-15 * kq * kq;
+  const double floor = mixed_floor(*p, p->mixed->resid64);
   if (floor > R.est) R.est = floor;
   R.floor_limited = floor > p->tol;
   R.done = R.est <= p->tol || R.last <= 1e-15 || R.floor_limited;
@@ -725,6 +761,8 @@ int sp_plan_create_ex(const sp_plan_desc* desc, void* stream, sp_plan** out) {
       if ((st = launch_status(sp::shell_operator_f64(*p, p->d_inner, p->d_ishell, s)))) break;
     }
     if (precision != SP_FP64 && (st = sp::mixed_create_tables(*p, s))) break;
+    // the float-float residual's floor above the tolerance: float64 iterate and residual
+    if (precision != SP_FP64) p->mixed->resid64 = sp::mixed_floor(*p, false) > tol;
     if (precision != SP_FP64 && cudaMallocHost(&p->h_red, 8 * sizeof(unsigned int)) != cudaSuccess) {
       st = SP_ERR_OOM;
       break;
@@ -877,6 +915,21 @@ int sp_face_gradients(sp_plan* plan, const double* phi, double* g_r, double* g_t
   if (p->outer_bc == SP_OUTER_MULTIPOLE) p->launches += 3;   // the outer face's shell transforms
   if (p->inner_bc == SP_INNER_REGULAR) p->launches += 3;     // the inner face's
   return st;
+}
+
+int sp_plan_set_residual(sp_plan* plan, int mode) {
+  if (!plan) return SP_ERR_INVALID_ARG;
+  Plan* p = reinterpret_cast<Plan*>(plan);
+  if (mode != SP_RESIDUAL_AUTO && mode != SP_RESIDUAL_FLOAT_FLOAT && mode != SP_RESIDUAL_FLOAT64) return SP_ERR_INVALID_ARG;
+  if (!p->mixed) return SP_OK;   // float64 plans have no refinement
+  DeviceGuard guard(p->device);
+  const bool r64 = mode == SP_RESIDUAL_FLOAT64 || (mode == SP_RESIDUAL_AUTO && sp::mixed_floor(*p, false) > p->tol);
+  if (r64 != p->mixed->resid64) {
+    p->mixed->resid64 = r64;
+    sp::drop_phase_graph(*p);
+    p->phase_a_warm = false;
+  }
+  return SP_OK;
 }
 
 int sp_plan_set_graphs(sp_plan* plan, int enable) {

@@ -63,17 +63,26 @@ CASES = [
 
 
 @pytest.mark.parametrize("mode", ["x3", "x6"])
-@pytest.mark.parametrize("nr,nth,nphi,grid,bc", [(4, 8, 4096, "log", 0), (3, 5, 3072, "rand", 1)])
-def test_mixed_long_phi_lines_report_their_floor(S, nr, nth, nphi, grid, bc, mode):
-    """Nphi up to 4096 (six radix-4 stages; a long radix-3 line): the float-float
-    iterate's precision floor grows as Nphi^2 and passes 1e-10 near Nphi = 372, so a
-    1e-10 request stops with SP_ERR_NOT_CONVERGED instead of claiming it; a looser
-    request succeeds with the estimate bounding the true error."""
+@pytest.mark.parametrize("nr,nth,nphi,grid,bc", [(4, 8, 4096, "log", 0), (3, 5, 3072, "rand", 1), (6, 12, 1024, "log", 0),
+                                                 (5, 8, 480, "rand", 0)])
+def test_mixed_long_phi_lines(S, nr, nth, nphi, grid, bc, mode):
+    """Nphi up to 4096 (six radix-4 stages; a long radix-3 line).  The float-float
+    iterate's precision floor 8 x 2^-48 x (Nphi/2pi)^2 passes 1e-10 near Nphi = 372, so
+    beyond it the plan refines with a float64 iterate and the float64 residual stencil
+    (SP_RESIDUAL_AUTO), which meets 1e-10; forced to float-float the same request stops
+    with SP_ERR_NOT_CONVERGED instead of claiming it, and a looser request succeeds with
+    the estimate bounding the true error."""
     p = W.random_small(nr, nth, nphi, seed=nr + 3 * nth + nphi, grid=grid, outer_bc=bc)
     prec = S.SP_MIXED_BF16X3 if mode == "x3" else S.SP_MIXED_BF16X6
     ref = O.solve_exact(O.Geometry(p.r_if, p.th_if, p.nphi), p.rho, outer_bc=bc)
     rho = torch.from_numpy(np.ascontiguousarray(p.rho)).cuda()
+    auto = S.Plan(p.r_if, p.th_if, p.nphi, outer_bc=bc, precision=prec, tol=TOL)
+    for _ in range(3):                       # direct, then graph capture and replay
+        phi, info = auto.solve(rho)
+        err = rel_err(phi.cpu().numpy(), ref)
+        assert info.status == S.SP_OK and err <= info.est_rel_error <= TOL
     strict = S.Plan(p.r_if, p.th_if, p.nphi, outer_bc=bc, precision=prec, tol=TOL)
+    strict.set_residual(S.SP_RESIDUAL_FLOAT_FLOAT)
     with pytest.raises(S.SpError) as ei:
         strict.solve(rho)
     assert ei.value.status == S.SP_ERR_NOT_CONVERGED
@@ -81,6 +90,31 @@ def test_mixed_long_phi_lines_report_their_floor(S, nr, nth, nphi, grid, bc, mod
     err = rel_err(phi, ref)
     assert info.status == S.SP_OK
     assert err <= info.est_rel_error <= 1e-7
+    # below the float64 residual's floor (2^-40) the request is refused as well
+    tight = S.Plan(p.r_if, p.th_if, p.nphi, outer_bc=bc, precision=prec, tol=1e-13)
+    with pytest.raises(S.SpError) as ei:
+        tight.solve(rho)
+    assert ei.value.status == S.SP_ERR_NOT_CONVERGED
+
+
+@pytest.mark.parametrize("mode", ["x3", "x6"])
+@pytest.mark.parametrize("nr,nth,nphi,grid,rin,bc", [CASES[1], CASES[6], CASES[8], CASES[11]])
+def test_mixed_float64_residual(S, nr, nth, nphi, grid, rin, bc, mode):
+    """The float64 refinement residual chosen explicitly on grids where float-float would
+    do: the same solution within the tolerance, the estimate bounding the error."""
+    p = W.random_small(nr, nth, nphi, seed=nr + 3 * nth + nphi, grid=grid, r_inner=rin, outer_bc=bc)
+    prec = S.SP_MIXED_BF16X3 if mode == "x3" else S.SP_MIXED_BF16X6
+    plan = S.Plan(p.r_if, p.th_if, p.nphi, outer_bc=bc, precision=prec, tol=TOL)
+    plan.set_residual(S.SP_RESIDUAL_FLOAT64)
+    ref = O.solve_exact(O.Geometry(p.r_if, p.th_if, p.nphi), p.rho, outer_bc=bc)
+    rho = torch.from_numpy(np.ascontiguousarray(p.rho)).cuda()
+    outs = []
+    for _ in range(3):
+        phi, info = plan.solve(rho)
+        outs.append(phi.cpu().numpy())
+        assert info.status == S.SP_OK
+        assert rel_err(outs[-1], ref) <= max(info.est_rel_error, 1e-13) and info.est_rel_error <= TOL
+    assert np.array_equal(outs[1], outs[2])    # graph replay = direct launches
 
 
 @pytest.mark.parametrize("mode", ["x3", "x6"])
