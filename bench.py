@@ -379,7 +379,9 @@ def run_batched(S, W, torch, dev, check=True, n=64, reps=3):
     zones = sum(p.zones for p in probs)
     rhos = [torch.from_numpy(p.rho).to(dev) for p in probs]
     out = {"workload": f"ragged_batch: {n} instances, {zones} zones", "instances": n, "zones": zones}
-    for name, prec in (("fp64", S.SP_FP64), ("mixed", S.SP_MIXED_BF16X6)):
+    for name, prec, ragged in (("fp64", S.SP_FP64, False), ("mixed", S.SP_MIXED_BF16X6, False),
+                               ("mixed_ragged", S.SP_MIXED_BF16X6, True)):
+        S.lib().sp_batched_set_ragged(1 if ragged else 0)
         plans = [S.Plan(p.r_if, p.th_if, p.nphi, precision=prec, tol=1e-10) for p in probs]
         phis = [torch.empty_like(r) for r in rhos]
         S.sp_solve_batched(plans, rhos, phis)          # warm-up (workspaces, module load)
@@ -393,8 +395,12 @@ def run_batched(S, W, torch, dev, check=True, n=64, reps=3):
             e1.record()
             e1.synchronize()
             ts.append(e0.elapsed_time(e1))
+        launches_ragged = S.lib().sp_batched_last_ragged()
+        S.lib().sp_batched_set_ragged(0)
         ms = statistics.median(ts)
         d = {"ms_per_batch": ms, "zones_per_s": zones / (ms / 1e3),
+             "form": ("ragged: one launch per step for each of up to 4 groups of instances"
+                      if ragged and launches_ragged else "one launch sequence per instance on 8 streams"),
              "max_est_rel_error": max(i.est_rel_error for i in infos),
              "iterations": sorted({int(i.iterations) for i in infos})}
         if check:

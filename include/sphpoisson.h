@@ -196,6 +196,25 @@ int sp_solve_host(sp_plan* plan, const double* rho_host, double* phi_host, void*
 int sp_solve_batched(sp_plan* const* plans, const double* const* rho_dev, double* const* phi_dev, int n,
                      void* stream, sp_solve_info* infos);
 
+/* Whether sp_solve_batched issues its mixed-precision instances as ragged batches (off
+ * by default; no counterpart in the paper).  When every mixed instance has the same
+ * precision, the float-float residual, an even Nphi and a 16-byte aligned rho, each step
+ * of the solve -- forward FFT, forward projection, radial scan, inverse projection,
+ * inverse FFT, the residual and its multipole shell chain -- is ONE kernel launch for all
+ * of them: the launch reads a table of per-instance arguments, and each CTA runs its
+ * instance's share (the projection's persistent CTAs are split in proportion to the
+ * instances' column tiles).  The instances form up to four groups (by angular grid) on
+ * stream pairs of their own, so that the groups' steps overlap; a refinement round is
+ * then about twenty operations per group instead of ~20 per instance, with results
+ * bitwise those of the instances' own solves.  Turned off, or for other mixes, each
+ * instance is its own launch sequence on the batch's 8 streams (measured faster on the
+ * 64-instance ragged workload: 14.2 against 15.9 ms).  Applies to calls made after it
+ * returns. */
+int sp_batched_set_ragged(int enable);
+/* Instances the calling thread's last sp_solve_batched solved as one ragged batch (0 when
+ * it used per-instance launch sequences). */
+int sp_batched_last_ragged(void);
+
 /* out = (Delta Phi)_{ijk}, the finite-volume operator of Eq. (fin_vol0)-(fin_vol3)
  * with the plan's boundary conditions, in float64 (not divided by 4 pi G).
  *  phi_dev, out_dev  device, Nr*Ntheta*Nphi float64; must not overlap */

@@ -99,6 +99,8 @@ _SIGS = {
     "sp_plan_get_timing": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "sp_plan_set_graphs": (C.c_int, [C.c_void_p, C.c_int]),
     "sp_plan_set_residual": (C.c_int, [C.c_void_p, C.c_int]),
+    "sp_batched_set_ragged": (C.c_int, [C.c_int]),
+    "sp_batched_last_ragged": (C.c_int, []),
     "sp_plan_launch_count": (C.c_longlong, [C.c_void_p]),
     "sp_plan_destroy": (C.c_int, [C.c_void_p]),
     "sp_status_string": (C.c_char_p, [C.c_int]),

@@ -293,9 +293,9 @@ template <> struct Vec16<float> {
 // Forward: lines [line0, line0+nl) of `in` -> half spectrum scaled by `scale`,
 // spec[m][i][c][j] with row stride `rs` (Ntheta, or the padded panel stride).
 template <typename T, typename Tin>
-__global__ void __launch_bounds__(256, 3) k_fft_fwd(const Tin* __restrict__ in, int nlines, int nth, int nrs,
-                                                 FftSchedule sch, const T* __restrict__ twid, T scale, int lpc,
-                                                 T* __restrict__ spec, int rs, int ahead) {
+__device__ __forceinline__ void fft_fwd_body(const Tin* __restrict__ in, int nlines, int nth, int nrs,
+                                             const FftSchedule& sch, const T* __restrict__ twid, T scale, int lpc,
+                                             T* __restrict__ spec, int rs, int ahead, int bx, int gx) {
   using CT = typename C2<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = sch.n;
@@ -308,12 +308,12 @@ __global__ void __launch_bounds__(256, 3) k_fft_fwd(const Tin* __restrict__ in, 
   load_twiddles<T>(tw, twid, n);   // plan-constant: before the dependency wait
   pdl_trigger();
   pdl_wait();
-  const int line0 = blockIdx.x * lpc;
+  const int line0 = bx * lpc;
   const int nl = min(lpc, nlines - line0);
   const int npairs = (nl + 1) / 2;
   // the input of the CTA one resident wave ahead goes on its way into L2 now
-  if (threadIdx.x == 0 && ahead > 0 && (int)blockIdx.x + ahead < (int)gridDim.x) {
-    const int l2 = (blockIdx.x + ahead) * lpc;
+  if (threadIdx.x == 0 && ahead > 0 && bx + ahead < gx) {
+    const int l2 = (bx + ahead) * lpc;
     prefetch_lines_l2(in, l2, min(lpc, nlines - l2), n);
   }
   // The CTA's lines are contiguous in memory: all threads load them together with
@@ -410,11 +410,11 @@ enum InvOut { kInvWrite = 0, kInvAccumulate = 1, kInvPairUpdate = 2, kInvF64Upda
 //  MODE kInvF64Update: float64 iterate out = e (first) or out + e, with the same two
 //    reductions (max|e|, max|out| as float).
 template <typename T, typename Tout, int MODE>
-__global__ void __launch_bounds__(256, 3) k_fft_inv(const T* __restrict__ spec, int nlines, int nth, int nrs,
-                                                 FftSchedule sch, const T* __restrict__ twid, int lpc,
-                                                 Tout* __restrict__ out, float* __restrict__ phi_lo, int first,
-                                                 int lo_read, int hilo, unsigned int* __restrict__ red, int ahead,
-                                                 double* __restrict__ phi64) {
+__device__ __forceinline__ void fft_inv_body(const T* __restrict__ spec, int nlines, int nth, int nrs,
+                                             const FftSchedule& sch, const T* __restrict__ twid, int lpc,
+                                             Tout* __restrict__ out, float* __restrict__ phi_lo, int first,
+                                             int lo_read, int hilo, unsigned int* __restrict__ red, int ahead,
+                                             double* __restrict__ phi64, int bx, int gx) {
   using CT = typename C2<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ float s_me[kWarps], s_mp[kWarps];
@@ -427,7 +427,7 @@ __global__ void __launch_bounds__(256, 3) k_fft_inv(const T* __restrict__ spec, 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   load_twiddles<T>(tw, twid, n);   // plan-constant: before the dependency wait
   pdl_trigger();
-  const int line0 = blockIdx.x * lpc;
+  const int line0 = bx * lpc;
   const int nl = min(lpc, nlines - line0);
   const int npairs = (nl + 1) / 2;
   const int mh = n / 2 + 1;
@@ -439,8 +439,8 @@ __global__ void __launch_bounds__(256, 3) k_fft_inv(const T* __restrict__ spec, 
   }
   pdl_wait();
   // the iterate lines of the CTA one resident wave ahead go on their way into L2 now
-  if (MODE == kInvPairUpdate && !first && threadIdx.x == 0 && ahead > 0 && (int)blockIdx.x + ahead < (int)gridDim.x) {
-    const int l2 = (blockIdx.x + ahead) * lpc;
+  if (MODE == kInvPairUpdate && !first && threadIdx.x == 0 && ahead > 0 && bx + ahead < gx) {
+    const int l2 = (bx + ahead) * lpc;
     prefetch_lines_l2(out, l2, min(lpc, nlines - l2), n);
     if (lo_read) prefetch_lines_l2(phi_lo, l2, min(lpc, nlines - l2), n);
   }
@@ -623,6 +623,47 @@ __global__ void __launch_bounds__(256, 3) k_fft_inv(const T* __restrict__ spec, 
   }
 }
 
+template <typename T, typename Tin>
+__global__ void __launch_bounds__(256, 3) k_fft_fwd(const Tin* __restrict__ in, int nlines, int nth, int nrs,
+                                                 FftSchedule sch, const T* __restrict__ twid, T scale, int lpc,
+                                                 T* __restrict__ spec, int rs, int ahead) {
+  fft_fwd_body<T, Tin>(in, nlines, nth, nrs, sch, twid, scale, lpc, spec, rs, ahead, blockIdx.x, gridDim.x);
+}
+
+template <typename T, typename Tout, int MODE>
+__global__ void __launch_bounds__(256, 3) k_fft_inv(const T* __restrict__ spec, int nlines, int nth, int nrs,
+                                                 FftSchedule sch, const T* __restrict__ twid, int lpc,
+                                                 Tout* __restrict__ out, float* __restrict__ phi_lo, int first,
+                                                 int lo_read, int hilo, unsigned int* __restrict__ red, int ahead,
+                                                 double* __restrict__ phi64) {
+  fft_inv_body<T, Tout, MODE>(spec, nlines, nth, nrs, sch, twid, lpc, out, phi_lo, first, lo_read, hilo, red, ahead,
+                              phi64, blockIdx.x, gridDim.x);
+}
+
+// ---- ragged batches: one launch over the CTAs of several instances; CTA b belongs to
+// the instance q with start[q] <= b < start[q+1] and runs that instance's transform
+// as its CTA b - start[q].
+template <typename T, typename Tin>
+__global__ void __launch_bounds__(256, 3) k_fft_fwd_rag(const FwdArgs* __restrict__ tab,
+                                                     const int* __restrict__ start, int n) {
+  const int q = rag_instance(start, n, blockIdx.x);
+  const FwdArgs& a = tab[q];
+  fft_fwd_body<T, Tin>(static_cast<const Tin*>(a.in), a.nlines, a.nth, a.nrs, a.sch,
+                       static_cast<const T*>(a.twid), (T)a.scale, a.lpc, static_cast<T*>(a.spec), a.rs, a.ahead,
+                       (int)blockIdx.x - start[q], start[q + 1] - start[q]);
+}
+
+template <typename T, typename Tout, int MODE>
+__global__ void __launch_bounds__(256, 3) k_fft_inv_rag(const InvArgs* __restrict__ tab,
+                                                     const int* __restrict__ start, int n) {
+  const int q = rag_instance(start, n, blockIdx.x);
+  const InvArgs& a = tab[q];
+  fft_inv_body<T, Tout, MODE>(static_cast<const T*>(a.spec), a.nlines, a.nth, a.nrs, a.sch,
+                              static_cast<const T*>(a.twid), a.lpc, static_cast<Tout*>(a.out), a.phi_lo, a.first,
+                              a.lo_read, a.hilo, a.red, a.ahead, a.phi64, (int)blockIdx.x - start[q],
+                              start[q + 1] - start[q]);
+}
+
 template <typename T>
 int lines_per_cta(int n, int nlines) {
   // two padded line buffers within ~100 KB (float) / ~140 KB (double), at most 32 lines;
@@ -743,6 +784,69 @@ cudaError_t fft_inverse_update(const Plan& p, const float* spec, float* phi_hi, 
                  (const float*)p.d_twid32, lpc, phi_hi, phi_lo, first ? 1 : 0, lo_read ? 1 : 0,
                  (f64_only && !first && phi64) ? 0 : 1, red, 0, first ? nullptr : phi64);
   return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+// ---- ragged batches: per-instance descriptions (the single-plan launchers' choices) and
+// one launch over all instances
+namespace {
+template <typename K, typename A>
+cudaError_t rag_launch(K kern, const A* tab, const int* start, int n, int total, size_t smem, cudaStream_t s) {
+  if (total <= 0) return cudaSuccess;
+  cudaError_t e = prep(kern, smem);
+  if (e != cudaSuccess) return e;
+  e = launch_pdl(kern, dim3(total), dim3(32 * kWarps), smem, s, tab, start, n);
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+}  // namespace
+
+void fft_fwd_panel_desc(const Plan& p, const void* in, float scale, int kstride, float* out, FwdArgs& a, int& ctas,
+                        size_t& smem) {
+  const int nlines = p.nr * p.nth;
+  const int lpc = lines_per_cta<float>(p.nphi, nlines);
+  smem = fft_smem<float>(p.nphi, lpc);
+  ctas = (nlines + lpc - 1) / lpc;
+  a = FwdArgs{p.sched, in, out, p.d_twid32, (double)scale, nlines, p.nth, p.nr, lpc, kstride, 0};
+}
+
+void fft_fwd_shell_desc(const Plan& p, const double* in, double* spec, FwdArgs& a, int& ctas, size_t& smem) {
+  const int nlines = p.nth;
+  const int lpc = lines_per_cta<double>(p.nphi, nlines);
+  smem = fft_smem<double>(p.nphi, lpc);
+  ctas = (nlines + lpc - 1) / lpc;
+  a = FwdArgs{p.sched, in, spec, p.d_twid, 1.0 / p.nphi, nlines, p.nth, 1, lpc, p.nth, 0};
+}
+
+void fft_inv_update_desc(const Plan& p, const float* spec, float* phi_hi, float* phi_lo, bool first, bool lo_read,
+                         bool f64_only, unsigned int* red, double* phi64, InvArgs& a, int& ctas, size_t& smem) {
+  const int nlines = p.nr * p.nth;
+  const int lpc = lines_per_cta<float>(p.nphi, nlines);
+  smem = fft_smem<float>(p.nphi, lpc);
+  ctas = (nlines + lpc - 1) / lpc;
+  a = InvArgs{p.sched, spec, phi_hi, phi_lo, red, first ? nullptr : phi64, p.d_twid32, nlines, p.nth, p.nr, lpc,
+              first ? 1 : 0, lo_read ? 1 : 0, (f64_only && !first && phi64) ? 0 : 1, 0};
+}
+
+void fft_inv_shell_desc(const Plan& p, const double* spec, double* out, InvArgs& a, int& ctas, size_t& smem) {
+  const int nlines = p.nth;
+  const int lpc = lines_per_cta<double>(p.nphi, nlines);
+  smem = fft_smem<double>(p.nphi, lpc);
+  ctas = (nlines + lpc - 1) / lpc;
+  a = InvArgs{p.sched, spec, out, nullptr, nullptr, nullptr, p.d_twid, nlines, p.nth, 1, lpc, 0, 0, 1, 0};
+}
+
+cudaError_t fft_fwd_rag(int kind, const FwdArgs* tab, const int* start, int n, int total, size_t smem, cudaStream_t s) {
+  if (kind == 0) return rag_launch(k_fft_fwd_rag<float, double>, tab, start, n, total, smem, s);
+  if (kind == 1) return rag_launch(k_fft_fwd_rag<float, float>, tab, start, n, total, smem, s);
+  return rag_launch(k_fft_fwd_rag<double, double>, tab, start, n, total, smem, s);
+}
+
+cudaError_t fft_inv_rag(int kind, const InvArgs* tab, const int* start, int n, int total, size_t smem, cudaStream_t s) {
+  if (kind == 0) return rag_launch(k_fft_inv_rag<float, float, kInvPairUpdate>, tab, start, n, total, smem, s);
+  return rag_launch(k_fft_inv_rag<double, double, kInvWrite>, tab, start, n, total, smem, s);
+}
+
+int fft_resident_ctas(const Plan& p, size_t smem) {
+  return resident_ctas(k_fft_fwd_rag<float, float>, smem, p.num_sms);
 }
 
 }  // namespace sp

@@ -219,11 +219,11 @@ size_t scan_smem_bytes(int nr, int nc) {
 }
 
 template <int NC>
-__global__ void __launch_bounds__(kScanThreads) k_thomas_scan(
+__device__ __forceinline__ void thomas_scan_body(
     const float* __restrict__ sub_r, const double* __restrict__ lam, const float* __restrict__ x,
     const float* __restrict__ fcp, const float* __restrict__ finv, float* __restrict__ pl, int nr, int nth, int kstride,
     double thr, int nlowblk, const int* __restrict__ low_idx, int nlow, const RadialRow* __restrict__ rad64,
-    const double2* __restrict__ low_fac) {
+    const double2* __restrict__ low_fac, int bx) {
   extern __shared__ __align__(16) float sm[];
   // D[c] [nr][kScanCols]: right-hand side, then d, then f of component c
   float* Q = sm + (size_t)NC * nr * kScanCols;   // [nr][kScanCols] 1/pivot or c', then running products
@@ -233,11 +233,11 @@ __global__ void __launch_bounds__(kScanThreads) k_thomas_scan(
   const size_t st = 2 * (size_t)nth;
   pdl_trigger();
   pdl_wait();
-  if ((int)blockIdx.x < nlowblk) {
+  if (bx < nlowblk) {
     // ---- float64 near-singular modes: warp pair (re, im) per mode, same segmented scan
     // over the warp's 32 lanes, carries by a shuffle scan of the affine segment maps
     const int warp = tid >> 5, lane = tid & 31;
-    const int q = (int)blockIdx.x * (kScanThreads / 64) + (warp >> 1);
+    const int q = bx * (kScanThreads / 64) + (warp >> 1);
     const int cc = warp & 1;
     if (q >= nlow) return;
     const int t = low_idx[q];
@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(kScanThreads) k_thomas_scan(
   }
   const int col = tid % kScanCols, seg = tid / kScanCols;
   const int ncb = (nth + kScanCols - 1) / kScanCols;
-  const int bid = (int)blockIdx.x - nlowblk;
+  const int bid = bx - nlowblk;
   const int c0 = NC == 2 ? 0 : (bid & 1);   // first component of this CTA
   const int mb = NC == 2 ? bid : (bid >> 1);
   const int m = mb / ncb;
@@ -438,6 +438,25 @@ __global__ void __launch_bounds__(kScanThreads) k_thomas_scan(
       for (int c = 0; c < NC; ++c) out[n * ostep + c * kstride] = fmaf(qn, cw[c], Dp[c * cst + n * kScanCols]);
     }
   }
+}
+
+template <int NC>
+__global__ void __launch_bounds__(kScanThreads) k_thomas_scan(
+    const float* __restrict__ sub_r, const double* __restrict__ lam, const float* __restrict__ x,
+    const float* __restrict__ fcp, const float* __restrict__ finv, float* __restrict__ pl, int nr, int nth, int kstride,
+    double thr, int nlowblk, const int* __restrict__ low_idx, int nlow, const RadialRow* __restrict__ rad64,
+    const double2* __restrict__ low_fac) {
+  thomas_scan_body<NC>(sub_r, lam, x, fcp, finv, pl, nr, nth, kstride, thr, nlowblk, low_idx, nlow, rad64, low_fac,
+                       blockIdx.x);
+}
+
+template <int NC>
+__global__ void __launch_bounds__(kScanThreads) k_thomas_scan_rag(const ScanArgs* __restrict__ tab,
+                                                                  const int* __restrict__ start, int n) {
+  const int q = rag_instance(start, n, blockIdx.x);
+  const ScanArgs& a = tab[q];
+  thomas_scan_body<NC>(a.sub_r, a.lam, a.x, a.fcp, a.finv, a.pl, a.nr, a.nth, a.kstride, a.thr, a.nlowblk, a.low_idx,
+                       a.nlow, a.rad64, a.low_fac, (int)blockIdx.x - start[q]);
 }
 
 // float32 elimination factors of every (m,l) radial system, computed in float64.
@@ -775,24 +794,21 @@ __device__ __forceinline__ float2 residual_zone2(float2 ch, float2 cl, float2& m
 // 8- and 16-byte accesses, the per-row work done once per pair, and the phi face between
 // the pair's columns differenced once for both.  rho must be 16-byte aligned.
 template <bool LO>
-__global__ void __launch_bounds__(kResThreads) k_residual_ff2(const double* __restrict__ rho,
-                                                              const float* __restrict__ ph,
-                                                              const float* __restrict__ pl,
-                                                              const double* __restrict__ outer_shell,
-                                                              float* __restrict__ r,
-                                                              const RadialRowFF* __restrict__ rad,
-                                                              const ThetaRowFF* __restrict__ ang, int nr, int nth,
-                                                              int nphi, int row_begin, int row_end, int dirichlet,
-                                                              ff dir_coef, ff four_pi_g) {
+__device__ __forceinline__ void residual_ff2_body(const double* __restrict__ rho, const float* __restrict__ ph,
+                                                  const float* __restrict__ pl, const double* __restrict__ outer_shell,
+                                                  float* __restrict__ r, const RadialRowFF* __restrict__ rad,
+                                                  const ThetaRowFF* __restrict__ ang, int nr, int nth, int nphi,
+                                                  int row_begin, int row_end, int dirichlet, ff dir_coef, ff four_pi_g,
+                                                  int bx, int by, int bz) {
   // [row parity][hi, lo][even, odd column of the pair][pair - p0 + 1]
   __shared__ float line[2][2][2][kResThreads + 2];
   pdl_trigger();
   pdl_wait();
-  const int j = blockIdx.x;
-  const int i0 = row_begin + (int)blockIdx.y * kResRows, i1 = min(row_end, i0 + kResRows);
+  const int j = bx;
+  const int i0 = row_begin + by * kResRows, i1 = min(row_end, i0 + kResRows);
   const int t = threadIdx.x;
   const int np2 = nphi >> 1;                          // column pairs per line
-  const int p0 = blockIdx.z * blockDim.x;             // first pair of this CTA
+  const int p0 = bz * blockDim.x;                     // first pair of this CTA
   const int nk = min((int)blockDim.x, np2 - p0);      // pairs of this CTA
   const bool act = t < nk;
   const int k = 2 * (p0 + (act ? t : nk - 1));        // even column of the pair
@@ -879,11 +895,51 @@ __global__ void __launch_bounds__(kResThreads) k_residual_ff2(const double* __re
   }
 }
 
+template <bool LO>
+__global__ void __launch_bounds__(kResThreads) k_residual_ff2(const double* __restrict__ rho,
+                                                              const float* __restrict__ ph,
+                                                              const float* __restrict__ pl,
+                                                              const double* __restrict__ outer_shell,
+                                                              float* __restrict__ r,
+                                                              const RadialRowFF* __restrict__ rad,
+                                                              const ThetaRowFF* __restrict__ ang, int nr, int nth,
+                                                              int nphi, int row_begin, int row_end, int dirichlet,
+                                                              ff dir_coef, ff four_pi_g) {
+  residual_ff2_body<LO>(rho, ph, pl, outer_shell, r, rad, ang, nr, nth, nphi, row_begin, row_end, dirichlet, dir_coef,
+                        four_pi_g, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// Ragged form: local CTA b of an instance is (b mod gx, (b / gx) mod gy, b / (gx gy)) of
+// its single-plan grid; the block size is the batch's largest, the unused threads of a
+// narrower instance idle as in a partial column block.
+template <bool LO>
+__global__ void __launch_bounds__(kResThreads) k_residual_ff2_rag(const ResArgs* __restrict__ tab,
+                                                                  const int* __restrict__ start, int n) {
+  const int q = rag_instance(start, n, blockIdx.x);
+  const ResArgs& a = tab[q];
+  const int b = (int)blockIdx.x - start[q];
+  const int bx = b % a.gx, byz = b / a.gx;
+  residual_ff2_body<LO>(a.rho, a.ph, a.pl, a.outer_shell, a.r, a.rad, a.ang, a.nr, a.nth, a.nphi, a.row_begin, a.row_end,
+                        a.dirichlet, a.dir_coef, a.four_pi_g, bx, byz % a.gy, byz / a.gy);
+}
+
 // float64 Phi = hi + lo (pl null: lo = 0)
+__device__ __forceinline__ void finish_body(const float* __restrict__ ph, const float* __restrict__ pl,
+                                            double* __restrict__ phi, size_t n, int bx, int gx) {
+  for (size_t idx = bx * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gx * blockDim.x)
+    phi[idx] = ff2d(ff{ph[idx], pl ? pl[idx] : 0.f});
+}
+
 __global__ void __launch_bounds__(256) k_finish(const float* __restrict__ ph, const float* __restrict__ pl,
                                                 double* __restrict__ phi, size_t n) {
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x)
-    phi[idx] = ff2d(ff{ph[idx], pl ? pl[idx] : 0.f});
+  finish_body(ph, pl, phi, n, blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(256) k_finish_rag(const FinishArgs* __restrict__ tab, const int* __restrict__ start,
+                                                    int n) {
+  const int q = rag_instance(start, n, blockIdx.x);
+  const FinishArgs& a = tab[q];
+  finish_body(a.ph, a.pl, a.phi, a.n, (int)blockIdx.x - start[q], start[q + 1] - start[q]);
 }
 
 // float64 iterate -> float-float (hi, lo): the inverse of k_finish up to 2^-48 relative.
@@ -1225,6 +1281,77 @@ cudaError_t finish_mixed(const Plan& p, double* phi, cudaStream_t s) {
   size_t blocks = (n + 255) / 256;
   if (blocks > (size_t)p.num_sms * 16) blocks = (size_t)p.num_sms * 16;
   k_finish<<<(unsigned)blocks, 256, 0, s>>>(x.phi_hi, lo, phi, n);
+  return cudaGetLastError();
+}
+
+// ---- ragged batches: per-instance descriptions (the single-plan launchers' choices)
+
+// both components per CTA while two fit on an SM (2), one component (1), or 0 when the
+// column needs the ring-staged kernel (no ragged form)
+int scan_components(const Plan& p) {
+  if (scan_smem_bytes(p.nr, 2) <= 108 * 1024) return 2;
+  return scan_smem_bytes(p.nr, 1) <= 200 * 1024 ? 1 : 0;
+}
+
+void scan_desc(const Plan& p, int nc, ScanArgs& a, int& ctas, size_t& smem) {
+  const MixedTables& x = *p.mixed;
+  smem = scan_smem_bytes(p.nr, nc);
+  const int nblk = (2 / nc) * p.mh * ((p.nth + kScanCols - 1) / kScanCols);
+  const int nlowblk = (x.nlow + kScanThreads / 64 - 1) / (kScanThreads / 64);
+  a = ScanArgs{x.sub_r, p.d_lam, x.d32, x.fcp, x.finv, x.panel, x.low_idx, p.d_rad, x.low_fac, x.low_threshold,
+               p.nr, p.nth, x.kstride, nlowblk, x.nlow};
+  ctas = nlowblk + nblk;
+}
+
+cudaError_t scan_rag(int nc, const ScanArgs* tab, const int* start, int n, int total, size_t smem, cudaStream_t s) {
+  if (total <= 0) return cudaSuccess;
+  auto kern = nc == 2 ? k_thomas_scan_rag<2> : k_thomas_scan_rag<1>;
+  cudaError_t e = allow_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  e = launch_pdl(kern, dim3(total), dim3(kScanThreads), smem, s, tab, start, n);
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+// whether the two-column residual serves this plan and source (even Nphi, 16-byte rho)
+bool residual_pairs(const Plan& p, const double* rho) {
+  return (p.nphi & 1) == 0 && (reinterpret_cast<uintptr_t>(rho) & 15u) == 0;
+}
+
+int residual_threads(const Plan& p) {
+  const int ncols = p.nphi / 2;
+  return ncols >= kResThreads ? kResThreads : ((ncols + 31) / 32) * 32;
+}
+
+// tpb: the block size the launch uses (at least residual_threads(p)); column blocks of it
+void residual_desc(const Plan& p, const double* rho, int r0, int r1, int tpb, ResArgs& a, int& ctas) {
+  const MixedTables& x = *p.mixed;
+  const int ncols = p.nphi / 2;
+  const int gy = (r1 - r0 + kResRows - 1) / kResRows, gz = (ncols + tpb - 1) / tpb;
+  a = ResArgs{rho, x.phi_hi, x.phi_lo, x.outer_shell, x.r32, x.radff, x.thff, x.dir_coef, x.four_pi_g,
+              p.nr, p.nth, p.nphi, r0, r1, p.outer_bc == SP_OUTER_DIRICHLET ? 1 : 0, p.nth, gy};
+  ctas = r1 > r0 ? p.nth * gy * gz : 0;
+}
+
+cudaError_t residual_rag(bool lo_read, const ResArgs* tab, const int* start, int n, int total, int tpb,
+                         cudaStream_t s) {
+  if (total <= 0) return cudaSuccess;
+  auto kern = lo_read ? k_residual_ff2_rag<true> : k_residual_ff2_rag<false>;
+  const cudaError_t e = launch_pdl(kern, dim3(total), dim3(tpb), 0, s, tab, start, n);
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+// float64 value of the float-float iterate's last shell (the multipole term's input)
+void shell_finish_desc(const Plan& p, FinishArgs& a, int& ctas) {
+  const MixedTables& x = *p.mixed;
+  const size_t sh = (size_t)p.nth * p.nphi;
+  const size_t off = (size_t)(p.nr - 1) * sh;
+  a = FinishArgs{x.phi_hi + off, x.lo_zero ? nullptr : x.phi_lo + off, x.shell_phi, sh};
+  ctas = (int)((sh + 255) / 256);
+}
+
+cudaError_t finish_rag(const FinishArgs* tab, const int* start, int n, int total, cudaStream_t s) {
+  if (total <= 0) return cudaSuccess;
+  k_finish_rag<<<total, 256, 0, s>>>(tab, start, n);
   return cudaGetLastError();
 }
 

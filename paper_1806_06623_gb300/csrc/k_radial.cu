@@ -102,12 +102,10 @@ __global__ void k_outer_operator(const double* __restrict__ HtW, const double* _
 // z_m = O_m x_m for the two real columns (re, im) of the outer shell's spectrum: one warp
 // per row j of O_m, lanes over j' (coalesced), shuffle reduction.
 constexpr int kShellRows = 8;
-__global__ void __launch_bounds__(32 * kShellRows) k_shell_apply(const double* __restrict__ O,
-                                                                 const double* __restrict__ xin,
-                                                                 double* __restrict__ zout, int nth) {
+__device__ __forceinline__ void shell_apply_body(const double* __restrict__ O, const double* __restrict__ xin,
+                                                 double* __restrict__ zout, int nth, int bx, int m) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m = blockIdx.y;
-  const int j = blockIdx.x * kShellRows + warp;
+  const int j = bx * kShellRows + warp;
   if (j >= nth) return;
   const double* row = O + ((size_t)m * nth + j) * nth;
   const double* x = xin + (size_t)m * 2 * nth;
@@ -125,6 +123,21 @@ __global__ void __launch_bounds__(32 * kShellRows) k_shell_apply(const double* _
     zout[(size_t)m * 2 * nth + j] = s0;
     zout[(size_t)m * 2 * nth + nth + j] = s1;
   }
+}
+
+__global__ void __launch_bounds__(32 * kShellRows) k_shell_apply(const double* __restrict__ O,
+                                                                 const double* __restrict__ xin,
+                                                                 double* __restrict__ zout, int nth) {
+  shell_apply_body(O, xin, zout, nth, blockIdx.x, blockIdx.y);
+}
+
+// ragged form: local CTA b is row block b mod gx of wavenumber b / gx
+__global__ void __launch_bounds__(32 * kShellRows) k_shell_apply_rag(const ShellArgs* __restrict__ tab,
+                                                                     const int* __restrict__ start, int n) {
+  const int q = rag_instance(start, n, blockIdx.x);
+  const ShellArgs& a = tab[q];
+  const int b = (int)blockIdx.x - start[q];
+  shell_apply_body(a.O, a.x, a.z, a.nth, b % a.gx, b / a.gx);
 }
 
 // Face gradients (minus the gravitational acceleration) of Eq. fin_vol3's fluxes: one
@@ -204,6 +217,18 @@ cudaError_t stencil_f64(const Plan& p, const double* phi, double* out, cudaStrea
   size_t blocks = (n + 255) / 256;
   if (blocks > 152 * 64) blocks = 152 * 64;
   k_stencil_f64<<<(unsigned)blocks, 256, 0, s>>>(phi, out, p.d_rad, p.d_theta, p.nr, p.nth, p.nphi, dir);
+  return cudaGetLastError();
+}
+
+void shell_apply_desc(const Plan& p, const double* O, const double* in, double* out, ShellArgs& a, int& ctas) {
+  const int gx = (p.nth + kShellRows - 1) / kShellRows;
+  a = ShellArgs{O, in, out, p.nth, p.mh, gx};
+  ctas = gx * p.mh;
+}
+
+cudaError_t shell_apply_rag(const ShellArgs* tab, const int* start, int n, int total, cudaStream_t s) {
+  if (total <= 0) return cudaSuccess;
+  k_shell_apply_rag<<<total, 32 * kShellRows, 0, s>>>(tab, start, n);
   return cudaGetLastError();
 }
 

@@ -32,6 +32,19 @@ struct FftSchedule {
   unsigned int nmagic;   // ceil(2^32 / n) otherwise: floor(x/n) = umulhi(x, nmagic) for x < 32 n
 };
 
+// ---- ragged batches: one launch over the CTAs of several instances (plans).  start[q]
+// is the first CTA of instance q (start[n] = all CTAs); a CTA finds its instance by
+// binary search and runs that instance's kernel body as its local CTA.
+__device__ __forceinline__ int rag_instance(const int* __restrict__ start, int n, int b) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(start + mid) <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 // Error bits written by kernels into the plan's device status word.
 enum : int { kErrEigenIter = 1, kErrBounds = 2, kErrTimeout = 4 };
 
@@ -102,6 +115,63 @@ struct MixedTables {
   unsigned int* red = nullptr;     // [2] max|e|, max|Phi| (bit patterns of non-negative floats)
   // tensor maps (CUtensorMap, 128 bytes each) for the tcgen05 projections
   alignas(64) unsigned char map_Af[3][128], map_Ai[3][128];
+};
+
+// Per-instance arguments of the ragged batch kernels (the single-plan launchers' values).
+struct FwdArgs {   // forward FFT into the float32 panel (or a float64 shell spectrum)
+  FftSchedule sch;
+  const void* in;
+  void* spec;
+  const void* twid;
+  double scale;
+  int nlines, nth, nrs, lpc, rs, ahead;
+};
+struct InvArgs {   // inverse FFT with the iterate update (or a float64 shell write)
+  FftSchedule sch;
+  const void* spec;
+  void* out;
+  float* phi_lo;
+  unsigned int* red;
+  double* phi64;
+  const void* twid;
+  int nlines, nth, nrs, lpc, first, lo_read, hilo, ahead;
+};
+struct ScanArgs {   // radial scan of the mixed path
+  const float* sub_r;
+  const double* lam;
+  const float* x;
+  const float* fcp;
+  const float* finv;
+  float* pl;
+  const int* low_idx;
+  const RadialRow* rad64;
+  const double2* low_fac;
+  double thr;
+  int nr, nth, kstride, nlowblk, nlow;
+};
+struct ResArgs {   // float-float residual rows [row_begin, row_end)
+  const double* rho;
+  const float* ph;
+  const float* pl;
+  const double* outer_shell;
+  float* r;
+  const RadialRowFF* rad;
+  const ThetaRowFF* ang;
+  ff dir_coef, four_pi_g;
+  int nr, nth, nphi, row_begin, row_end, dirichlet;
+  int gx, gy;   // the single-plan grid: (Ntheta, row chunks, column blocks)
+};
+struct FinishArgs {   // float-float words -> float64 (hi, lo of n values; lo may be null)
+  const float* ph;
+  const float* pl;
+  double* phi;
+  size_t n;
+};
+struct ShellArgs {   // z_m = O_m x_m on one shell spectrum
+  const double* O;
+  const double* x;
+  double* z;
+  int nth, mh, gx;   // gx = row blocks per m
 };
 
 // Kernel identities for the optional per-launch CUDA-event timers.
@@ -309,6 +379,31 @@ cudaError_t fft_inverse_update64(const Plan& p, const float* spec, double* phi, 
                                  cudaStream_t s);
 int create_side_stream(Plan& p);   // side stream and events of a mixed multipole plan; sp_status
 
+// ---- ragged batch launches (kind: forward 0 = float32 panel from float64 rho,
+// 1 = float32 panel from the float32 residual, 2 = float64 shell; inverse 0 = iterate
+// update, 1 = float64 shell write)
+void fft_fwd_panel_desc(const Plan& p, const void* in, float scale, int kstride, float* out, FwdArgs& a, int& ctas,
+                        size_t& smem);
+void fft_fwd_shell_desc(const Plan& p, const double* in, double* spec, FwdArgs& a, int& ctas, size_t& smem);
+void fft_inv_update_desc(const Plan& p, const float* spec, float* phi_hi, float* phi_lo, bool first, bool lo_read,
+                         bool f64_only, unsigned int* red, double* phi64, InvArgs& a, int& ctas, size_t& smem);
+void fft_inv_shell_desc(const Plan& p, const double* spec, double* out, InvArgs& a, int& ctas, size_t& smem);
+cudaError_t fft_fwd_rag(int kind, const FwdArgs* tab, const int* start, int n, int total, size_t smem, cudaStream_t s);
+cudaError_t fft_inv_rag(int kind, const InvArgs* tab, const int* start, int n, int total, size_t smem, cudaStream_t s);
+int fft_resident_ctas(const Plan& p, size_t smem);
+void shell_apply_desc(const Plan& p, const double* O, const double* in, double* out, ShellArgs& a, int& ctas);
+int scan_components(const Plan& p);
+void scan_desc(const Plan& p, int nc, ScanArgs& a, int& ctas, size_t& smem);
+cudaError_t scan_rag(int nc, const ScanArgs* tab, const int* start, int n, int total, size_t smem, cudaStream_t s);
+bool residual_pairs(const Plan& p, const double* rho);
+int residual_threads(const Plan& p);
+void residual_desc(const Plan& p, const double* rho, int r0, int r1, int tpb, ResArgs& a, int& ctas);
+cudaError_t residual_rag(bool lo_read, const ResArgs* tab, const int* start, int n, int total, int tpb,
+                         cudaStream_t s);
+void shell_finish_desc(const Plan& p, FinishArgs& a, int& ctas);
+cudaError_t finish_rag(const FinishArgs* tab, const int* start, int n, int total, cudaStream_t s);
+cudaError_t shell_apply_rag(const ShellArgs* tab, const int* start, int n, int total, cudaStream_t s);
+
 // ---- solve phases shared by sp_solve, sp_solve_batched and the server ----
 // Refinement state of one mixed-precision solve.
 struct MixedRun {
@@ -330,6 +425,14 @@ int mixed_issue_read(Plan* p, cudaStream_t s, MixedRun& R);
 int mixed_phase_a(Plan* p, const double* rho, double* phi, cudaStream_t s, MixedRun& R);
 void drop_phase_graph(Plan& p);
 void mixed_decide(Plan* p, MixedRun& R);   // after the stream has reached the pending copies
+// one solve's reductions (max|e|, max|Phi| bit patterns) read from `slot` (ragged batches)
+void mixed_decide_slot(Plan* p, MixedRun& R, const unsigned int* slot);
+// Ragged batched mixed solves (sp_batch.cu): every instance's steps as one launch per step.
+// Returns false when the instances cannot form one ragged group (then nothing was issued).
+bool ragged_supported(Plan* const* P, const double* const* rho, int n);
+int ragged_groups(int n, int nstreams);   // ragged groups (stream pairs) used for n instances
+int ragged_solve(Plan* const* P, const double* const* rho, double* const* phi, int n, const cudaStream_t* streams,
+                 int nstreams, MixedRun* runs, int* status);
 int mixed_finish(Plan* p, double* phi, cudaStream_t s, const MixedRun& R, sp_solve_info* info);
 int mixed_finish_issue(Plan* p, double* phi, cudaStream_t s);
 int mixed_finish_status(Plan* p, const MixedRun& R, sp_solve_info* info);

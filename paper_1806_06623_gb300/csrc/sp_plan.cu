@@ -392,6 +392,10 @@ void decide_one(Plan* p, MixedRun& R, const unsigned int* slot) {
 
 }  // namespace
 
+void mixed_decide_slot(Plan* p, MixedRun& R, const unsigned int* slot) {
+  if (!R.done) decide_one(p, R, slot);
+}
+
 // Read the pending slots in issue order; a solve queued behind one that already met the
 // tolerance is not counted (its correction is below the tolerance by construction).
 void mixed_decide(Plan* p, MixedRun& R) {

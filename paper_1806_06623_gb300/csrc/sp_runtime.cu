@@ -14,6 +14,7 @@
 // that arrive while others run start as soon as a slot and memory are free and their
 // kernels overlap on the device.  Latency is measured from submission to completion.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -69,7 +70,20 @@ struct DeviceScope {
   }
 };
 
+// sp_solve_batched issues same-precision mixed instances as ragged batches when turned on
+// (off by default: on the 64-instance ragged workload the per-instance streams measured
+// 14.2 against 15.9 ms, the ragged form issuing ~30x fewer launches)
+std::atomic<int> g_ragged{0};
+thread_local int t_last_ragged = 0;   // instances of this thread's last call solved as a ragged batch
+
 }  // namespace
+
+extern "C" int sp_batched_set_ragged(int enable) {
+  g_ragged.store(enable ? 1 : 0);
+  return SP_OK;
+}
+
+extern "C" int sp_batched_last_ragged(void) { return t_last_ragged; }
 
 extern "C" int sp_solve_batched(sp_plan* const* plans, const double* const* rho, double* const* phi, int n,
                                 void* stream, sp_solve_info* infos) {
@@ -107,9 +121,40 @@ extern "C" int sp_solve_batched(sp_plan* const* plans, const double* const* rho,
 
   std::vector<int> status(n, SP_OK);
   std::vector<sp::MixedRun> runs(n);
-  auto stream_of = [&](int i) { return pool->s[i % ns]; };
+  // the mixed instances as one ragged batch on stream 0 (side stream 1) when they form one;
+  // the rest keep one launch sequence each on the pool's streams
+  std::vector<int> mixed_idx;
+  for (int i = 0; i < n; ++i)
+    if (P[i]->mixed) mixed_idx.push_back(i);
+  std::vector<Plan*> MP;
+  std::vector<const double*> MR;
+  std::vector<double*> MF;
+  for (int i : mixed_idx) {
+    MP.push_back(P[i]);
+    MR.push_back(rho[i]);
+    MF.push_back(phi[i]);
+  }
+  const bool ragged = g_ragged.load() && ns >= 2 && sp::ragged_supported(MP.data(), MR.data(), (int)MP.size());
+  t_last_ragged = ragged ? (int)MP.size() : 0;
+  const int groups = ragged ? sp::ragged_groups((int)MP.size(), ns) : 0;
+  auto stream_of = [&](int i) { return ragged ? pool->s[2 * (i % groups)] : pool->s[i % ns]; };
+  if (ragged) {
+    // float64 instances on the groups' main streams ahead of their ragged rounds
+    for (int i = 0; i < n; ++i)
+      if (!P[i]->mixed) status[i] = sp::solve_fp64_async(P[i], rho[i], phi[i], stream_of(i));
+    std::vector<sp::MixedRun> mr(MP.size());
+    std::vector<int> ms(MP.size(), SP_OK);
+    const int st = sp::ragged_solve(MP.data(), MR.data(), MF.data(), (int)MP.size(), pool->s, ns, mr.data(), ms.data());
+    for (size_t k = 0; k < mixed_idx.size(); ++k) {
+      runs[mixed_idx[k]] = mr[k];
+      status[mixed_idx[k]] = st ? st : ms[k];
+    }
+    for (size_t k = 0; k < mixed_idx.size(); ++k)
+      if (!status[mixed_idx[k]])
+        status[mixed_idx[k]] = sp::mixed_finish_issue(P[mixed_idx[k]], phi[mixed_idx[k]], pool->s[0]);
+  }
   // round 0: float64 solves and the first low-precision solves
-  for (int i = 0; i < n; ++i) {
+  for (int i = 0; i < n && !ragged; ++i) {
     if (P[i]->mixed) {
       // the first correction goes right behind the first solve (see solve_mixed)
       status[i] = sp::mixed_phase_a(P[i], rho[i], phi[i], stream_of(i), runs[i]);
@@ -119,7 +164,7 @@ extern "C" int sp_solve_batched(sp_plan* const* plans, const double* const* rho,
   }
   // refinement rounds
   std::vector<int> active;
-  for (int i = 0; i < n; ++i)
+  for (int i = 0; i < n && !ragged; ++i)
     if (P[i]->mixed && !status[i]) active.push_back(i);
   while (!active.empty()) {
     for (int k = 0; k < ns; ++k)
@@ -138,7 +183,7 @@ extern "C" int sp_solve_batched(sp_plan* const* plans, const double* const* rho,
       if (!status[i]) active.push_back(i);
   }
   // float-float iterates -> float64 results
-  for (int i = 0; i < n; ++i)
+  for (int i = 0; i < n && !ragged; ++i)
     if (P[i]->mixed && !status[i]) status[i] = sp::mixed_finish_issue(P[i], phi[i], stream_of(i));
   bool any_mixed = false;
   for (int i = 0; i < n; ++i) any_mixed = any_mixed || P[i]->mixed;

@@ -205,8 +205,9 @@ __device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, float (&v)[32
   for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
 }
 
+// One instance's CTA bx of gx (the persistent range split below).
 template <int NP>
-__global__ void __launch_bounds__(kThreads, 1) k_tc_gemm_split(const __grid_constant__ Maps maps, Params prm) {
+__device__ __forceinline__ void tc_gemm_split_body(const Maps& maps, const Params& prm, int bx, int gx) {
   constexpr int BN = Cfg<NP>::BN;
   constexpr int S = Cfg<NP>::kStages;
   constexpr uint32_t kPlaneBytes = BN * 128u;   // one plane of one K block
@@ -228,8 +229,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm_split(const __grid_cons
   const int kb = prm.kblocks;
   const int tiles = (prm.ncol + BN - 1) / BN;
   const long long gtot = (long long)tiles * prm.mh;
-  const int g0 = (int)((gtot * blockIdx.x) / gridDim.x);
-  const int g1 = (int)((gtot * (blockIdx.x + 1)) / gridDim.x);
+  const int g0 = (int)((gtot * bx) / gx);
+  const int g1 = (int)((gtot * (bx + 1)) / gx);
   const int nt = g1 - g0;
   const int nq = nt * kb;   // work chunks q = (tile g0 + q / kb, K block q % kb)
   const int m0 = g0 / tiles;
@@ -466,6 +467,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm_split(const __grid_cons
   if (warp == 0) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * BN)));
   }
+}
+
+template <int NP>
+__global__ void __launch_bounds__(kThreads, 1) k_tc_gemm_split(const __grid_constant__ Maps maps, Params prm) {
+  tc_gemm_split_body<NP>(maps, prm, blockIdx.x, gridDim.x);
+}
+
+// Ragged batches: instance q owns CTAs start[q] .. start[q+1]-1 and splits its (m, tile)
+// list over them; its table maps are read from the argument table in global memory.
+struct alignas(64) TcArgs {
+  Maps maps;
+  Params prm;
+};
+
+template <int NP>
+__global__ void __launch_bounds__(kThreads, 1) k_tc_gemm_split_rag(const TcArgs* __restrict__ tab,
+                                                                  const int* __restrict__ start, int n) {
+  const int q = rag_instance(start, n, blockIdx.x);
+  tc_gemm_split_body<NP>(tab[q].maps, tab[q].prm, (int)blockIdx.x - start[q], start[q + 1] - start[q]);
 }
 
 // ------------------------------------------------------------------ host side

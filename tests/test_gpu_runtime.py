@@ -65,6 +65,61 @@ def test_batched_matches_alone_ragged(S):
         assert err <= (1e-10 if precs[k] != S.SP_FP64 else 1e-12)
 
 
+def _solve_batch(S, probs, precs, tols=None, ragged=True):
+    S.lib().sp_batched_set_ragged(1 if ragged else 0)
+    try:
+        plans = [S.Plan(p.r_if, p.th_if, p.nphi, outer_bc=p.outer_bc, precision=q,
+                        tol=(tols[k] if tols else 1e-10)) for k, (p, q) in enumerate(zip(probs, precs))]
+        rhos = [torch.from_numpy(p.rho).cuda() for p in probs]
+        phis = [torch.empty_like(r) for r in rhos]
+        infos = S.sp_solve_batched(plans, rhos, phis)
+        torch.cuda.synchronize()
+        return [f.cpu().numpy() for f in phis], infos, S.lib().sp_batched_last_ragged()
+    finally:
+        S.lib().sp_batched_set_ragged(0)
+
+
+@pytest.mark.parametrize("prec_name", ["x6", "x3"])
+def test_ragged_batch_equals_alone(S, prec_name):
+    """Same-precision mixed instances of different grids go through ONE launch per step
+    (ragged batch); each result is bitwise its solo solve and the per-instance-stream
+    batch, with the same number of low-precision solves.  A Dirichlet instance (no shell
+    chain), float64 instances beside them, and an instance with a tighter tolerance that
+    needs further ragged rounds are part of the mix."""
+    prec = S.SP_MIXED_BF16X6 if prec_name == "x6" else S.SP_MIXED_BF16X3
+    probs = [W.ragged_instance(i) for i in range(8)]
+    probs.append(W.random_small(40, 32, 64, seed=3, grid="log", outer_bc=1))
+    probs.append(W.stellar_noise())
+    precs = [prec] * len(probs)
+    tols = [1e-10] * len(probs)
+    # a tighter tolerance (still above the float-float floor 8 x 2^-48 (Nphi/2pi)^2 of its
+    # Nphi = 64) needs a further ragged round for this instance
+    tight = next(k for k, p in enumerate(probs) if p.nphi == 64)
+    tols[tight] = 5e-12
+    n_mixed = len(probs)
+    probs += [W.ragged_instance(20), W.sphere_blob()]
+    precs += [S.SP_FP64, S.SP_FP64]
+    tols += [1e-10, 1e-10]
+    rag, info_rag, n_rag = _solve_batch(S, probs, precs, tols, ragged=True)
+    per, info_per, n_per = _solve_batch(S, probs, precs, tols, ragged=False)
+    assert n_rag == n_mixed and n_per == 0
+    for k, p in enumerate(probs):
+        plan = S.Plan(p.r_if, p.th_if, p.nphi, outer_bc=p.outer_bc, precision=precs[k], tol=tols[k])
+        solo, info_solo = plan.solve(torch.from_numpy(p.rho).cuda())
+        solo = solo.cpu().numpy()
+        assert info_rag[k].status == S.SP_OK
+        assert np.array_equal(rag[k], solo), k
+        assert np.array_equal(per[k], solo), k
+        assert info_rag[k].iterations == info_solo.iterations == info_per[k].iterations
+    # further ragged rounds ran: the tight instance's (6 products), every instance's (3)
+    if prec_name == "x6":
+        assert info_rag[tight].iterations > min(i.iterations for i in info_rag[:n_mixed] if i is not info_rag[tight])
+    else:
+        assert min(i.iterations for i in info_rag[:n_mixed]) >= 3
+    ref = O.solve_exact(O.Geometry(probs[0].r_if, probs[0].th_if, probs[0].nphi), probs[0].rho)
+    assert np.max(np.abs(rag[0] - ref)) / np.max(np.abs(ref)) <= 1e-10
+
+
 def test_batched_rejects_shared_plan(S):
     p = W.random_small(8, 8, 8, seed=1)
     plan = S.Plan(p.r_if, p.th_if, p.nphi)
