@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--no-served", action="store_true", help="skip the served Poisson-arrival stream")
     ap.add_argument("--served-requests", type=int, default=400)
     ap.add_argument("--no-small", action="store_true", help="skip the 32x16x32 and 128x64x128 configurations")
+    ap.add_argument("--autotune", action="store_true",
+                    help="tune each plan's launch configuration (sp_plan_autotune) before timing")
     ap.add_argument("--headline-only", action="store_true",
                     help="time the headline precision only (no float64 / 3-product comparison plans)")
     return ap.parse_args()
@@ -249,6 +251,12 @@ def run_ours(args, rank, world, local):
                 plan.collect_timing()
         return tot, infos
 
+    tuning = {}
+    if args.autotune:
+        # launch configuration per plan from timed solves of this workload (sp_plan_autotune)
+        for name, plan in plans.items():
+            _, conf = plan.autotune(rho, phi)
+            tuning[name] = dict(zip(("fft_lines_per_cta", "radix_order", "projection_ctas", "scan_components"), conf))
     results = {}
     for name, plan in plans.items():
         clocks = ClockSampler(local)
@@ -319,6 +327,7 @@ def run_ours(args, rank, world, local):
     line["roofline"] = roofline(r["timing"], p, precision, args.steps, r["infos"][-1].get("iterations", 2))
     line["projection_tensor"] = projection_tensor_rate(r["timing"], p, precision)
     line["kernel_source_sha"] = kernel_source_hash()
+    line["autotuned"] = tuning or None
     if not args.no_small:
         line["small_configs"] = run_small(S, W, torch, dev, check=not args.no_oracle_check)
     if not args.no_batched:

@@ -299,6 +299,23 @@ int sp_plan_set_residual(sp_plan* plan, int mode);
  * a NULL plan. */
 int sp_plan_set_graphs(sp_plan* plan, int enable);
 
+/* Autotune the plan's launch configuration (no counterpart in the paper): the phi lines
+ * per CTA of the mixed path's float32 FFTs (which also decides whether Nphi = 256 takes
+ * two radix-16 passes), the order of the FFT radix stages, the tensor-core projection's
+ * persistent CTA count and the radial scan's components per CTA, one after the other,
+ * each candidate timed as the median of three solves of rho_dev into phi_dev on `stream`.
+ * The best configuration stays in the plan (and its later clones).  With cache_path
+ * (a JSON file, created or updated; NULL for none) an entry for the same device, shape,
+ * precision and outer condition is applied without timing (*from_cache = 1 then;
+ * from_cache may be NULL) and a new result is added.  Different radix orders round
+ * differently, so a tuned plan's results may differ from an untuned one's in the last
+ * bits (both within the precision's tolerance).  Synchronises the stream. */
+int sp_plan_autotune(sp_plan* plan, const double* rho_dev, double* phi_dev, const char* cache_path, void* stream,
+                     int* from_cache);
+/* The plan's tuned values (0 = built-in heuristic): values[0..3] = FFT lines per CTA,
+ * radix order (0 default, 1 reversed), projection CTAs, scan components per CTA. */
+int sp_plan_get_tuning(const sp_plan* plan, int* values);
+
 /* Number of kernel launches this plan has issued since creation (host counter). */
 long long sp_plan_launch_count(const sp_plan* plan);
 

@@ -101,6 +101,8 @@ _SIGS = {
     "sp_plan_set_residual": (C.c_int, [C.c_void_p, C.c_int]),
     "sp_batched_set_ragged": (C.c_int, [C.c_int]),
     "sp_batched_last_ragged": (C.c_int, []),
+    "sp_plan_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_char_p, C.c_void_p, C.POINTER(C.c_int)]),
+    "sp_plan_get_tuning": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "sp_plan_launch_count": (C.c_longlong, [C.c_void_p]),
     "sp_plan_destroy": (C.c_int, [C.c_void_p]),
     "sp_status_string": (C.c_char_p, [C.c_int]),
@@ -439,6 +441,24 @@ class Plan:
 
     def set_graphs(self, enable=True):
         _check(lib().sp_plan_set_graphs(self._h, int(bool(enable))), "sp_plan_set_graphs")
+
+    def autotune(self, rho, phi=None, cache_path=None, stream=None):
+        """Tune the launch configuration on rho (see sp_plan_autotune); returns
+        (from_cache, [lines per CTA, radix order, projection CTAs, scan components])."""
+        import torch
+        n = int(np.prod(self.shape))
+        if phi is None:
+            phi = torch.empty_like(rho)
+        fc = C.c_int(0)
+        _check(lib().sp_plan_autotune(self._h, _dev_ptr(rho, n, "rho"), _dev_ptr(phi, n, "phi"),
+                                      None if cache_path is None else str(cache_path).encode(),
+                                      _stream_ptr(stream, rho.device), C.byref(fc)), "sp_plan_autotune")
+        return bool(fc.value), self.tuning()
+
+    def tuning(self):
+        v = (C.c_int * 4)()
+        _check(lib().sp_plan_get_tuning(self._h, v), "sp_plan_get_tuning")
+        return list(v)
 
     def set_residual(self, mode=SP_RESIDUAL_AUTO):
         """Arithmetic of the mixed modes' refinement residual (SP_RESIDUAL_*)."""

@@ -679,6 +679,18 @@ int lines_per_cta(int n, int nlines) {
 }
 
 template <typename T>
+size_t fft_smem(int n, int lpc);
+}  // namespace
+
+int panel_lpc(const Plan& p, int nlines) {
+  const int dflt = lines_per_cta<float>(p.nphi, nlines);
+  // a tuned value is used when it is even and no larger than the default (which the
+  // shared-memory budget allows)
+  return (p.tune.lpc >= 2 && p.tune.lpc <= dflt && (p.tune.lpc & 1) == 0) ? p.tune.lpc : dflt;
+}
+
+namespace {
+template <typename T>
 size_t fft_smem(int n, int lpc) {
   const size_t P = (size_t)(lpc / 2);
   const size_t psb = n == 256 ? (size_t)kPad256 : (size_t)n + 1;
@@ -738,7 +750,7 @@ cudaError_t fft_inverse_f64(const Plan& p, const double* spec, int nrs, double* 
 cudaError_t fft_forward_panel(const Plan& p, const void* in, bool in_double, float scale, int kstride, float* out,
                               cudaStream_t s) {
   const int nlines = p.nr * p.nth;
-  const int lpc = lines_per_cta<float>(p.nphi, nlines);
+  const int lpc = panel_lpc(p, nlines);
   const size_t smem = fft_smem<float>(p.nphi, lpc);
   const int grid = (nlines + lpc - 1) / lpc;
   cudaError_t e;
@@ -761,7 +773,7 @@ cudaError_t fft_forward_panel(const Plan& p, const void* in, bool in_double, flo
 cudaError_t fft_inverse_update64(const Plan& p, const float* spec, double* phi, bool first, unsigned int* red,
                                  cudaStream_t s) {
   const int nlines = p.nr * p.nth;
-  const int lpc = lines_per_cta<float>(p.nphi, nlines);
+  const int lpc = panel_lpc(p, nlines);
   const size_t smem = fft_smem<float>(p.nphi, lpc);
   auto kern = k_fft_inv<float, double, kInvF64Update>;
   cudaError_t e = prep(kern, smem);
@@ -774,7 +786,7 @@ cudaError_t fft_inverse_update64(const Plan& p, const float* spec, double* phi, 
 cudaError_t fft_inverse_update(const Plan& p, const float* spec, float* phi_hi, float* phi_lo, bool first, bool lo_read,
                                bool f64_only, unsigned int* red, double* phi64, cudaStream_t s) {
   const int nlines = p.nr * p.nth;
-  const int lpc = lines_per_cta<float>(p.nphi, nlines);
+  const int lpc = panel_lpc(p, nlines);
   const size_t smem = fft_smem<float>(p.nphi, lpc);
   auto kern = k_fft_inv<float, float, kInvPairUpdate>;
   cudaError_t e = prep(kern, smem);
@@ -802,7 +814,7 @@ cudaError_t rag_launch(K kern, const A* tab, const int* start, int n, int total,
 void fft_fwd_panel_desc(const Plan& p, const void* in, float scale, int kstride, float* out, FwdArgs& a, int& ctas,
                         size_t& smem) {
   const int nlines = p.nr * p.nth;
-  const int lpc = lines_per_cta<float>(p.nphi, nlines);
+  const int lpc = panel_lpc(p, nlines);
   smem = fft_smem<float>(p.nphi, lpc);
   ctas = (nlines + lpc - 1) / lpc;
   a = FwdArgs{p.sched, in, out, p.d_twid32, (double)scale, nlines, p.nth, p.nr, lpc, kstride, 0};
@@ -819,7 +831,7 @@ void fft_fwd_shell_desc(const Plan& p, const double* in, double* spec, FwdArgs& 
 void fft_inv_update_desc(const Plan& p, const float* spec, float* phi_hi, float* phi_lo, bool first, bool lo_read,
                          bool f64_only, unsigned int* red, double* phi64, InvArgs& a, int& ctas, size_t& smem) {
   const int nlines = p.nr * p.nth;
-  const int lpc = lines_per_cta<float>(p.nphi, nlines);
+  const int lpc = panel_lpc(p, nlines);
   smem = fft_smem<float>(p.nphi, lpc);
   ctas = (nlines + lpc - 1) / lpc;
   a = InvArgs{p.sched, spec, phi_hi, phi_lo, red, first ? nullptr : phi64, p.d_twid32, nlines, p.nth, p.nr, lpc,

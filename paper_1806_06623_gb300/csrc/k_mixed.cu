@@ -1110,7 +1110,7 @@ cudaError_t tc_project_np(const Plan& p, bool inverse, cudaStream_t s) {
   // one CTA per SM, each with an equal share of the (m, column tile) list
   const int tiles = (2 * p.nr + tc::Cfg<NP>::BN - 1) / tc::Cfg<NP>::BN;
   const long long total = (long long)tiles * p.mh;
-  const int grid = (int)std::min<long long>(total, p.num_sms);
+  const int grid = (int)std::min<long long>(total, p.tune.tc_ctas > 0 ? p.tune.tc_ctas : p.num_sms);
   tc::Params prm{x.d32, x.panel, p.nth, p.nth, x.kstride, 2 * p.nr, (p.nth + tc::kKBlk - 1) / tc::kKBlk, p.mh, p.d_err};
   constexpr uint32_t smem = tc::smem_bytes<NP>();
   cudaError_t e = allow_smem(tc::k_tc_gemm_split<NP>, smem);
@@ -1127,7 +1127,8 @@ cudaError_t tc_project(const Plan& p, bool inverse, cudaStream_t s) {
 cudaError_t thomas_mixed(const Plan& p, cudaStream_t s) {
   const MixedTables& x = *p.mixed;
   // both components per CTA while two such CTAs fit on an SM, else one
-  const int nc = scan_smem_bytes(p.nr, 2) <= 108 * 1024 ? 2 : 1;
+  int nc = scan_smem_bytes(p.nr, 2) <= 108 * 1024 ? 2 : 1;
+  if (p.tune.scan_nc == 1 || (p.tune.scan_nc == 2 && scan_smem_bytes(p.nr, 2) <= 200 * 1024)) nc = p.tune.scan_nc;
   const size_t smem = scan_smem_bytes(p.nr, nc);
   if (smem <= 200 * 1024) {
     const int nblk = (2 / nc) * p.mh * ((p.nth + kScanCols - 1) / kScanCols);
@@ -1289,8 +1290,9 @@ cudaError_t finish_mixed(const Plan& p, double* phi, cudaStream_t s) {
 // both components per CTA while two fit on an SM (2), one component (1), or 0 when the
 // column needs the ring-staged kernel (no ragged form)
 int scan_components(const Plan& p) {
-  if (scan_smem_bytes(p.nr, 2) <= 108 * 1024) return 2;
-  return scan_smem_bytes(p.nr, 1) <= 200 * 1024 ? 1 : 0;
+  if (scan_smem_bytes(p.nr, 1) > 200 * 1024) return 0;
+  if (p.tune.scan_nc == 1 || (p.tune.scan_nc == 2 && scan_smem_bytes(p.nr, 2) <= 200 * 1024)) return p.tune.scan_nc;
+  return scan_smem_bytes(p.nr, 2) <= 108 * 1024 ? 2 : 1;
 }
 
 void scan_desc(const Plan& p, int nc, ScanArgs& a, int& ctas, size_t& smem) {

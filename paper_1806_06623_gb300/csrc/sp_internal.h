@@ -254,6 +254,14 @@ struct Plan {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
+  // launch configuration chosen by sp_plan_autotune (0 = the built-in heuristic)
+  struct Tune {
+    int lpc = 0;           // phi lines per CTA of the float32 panel FFTs
+    int radix_order = 0;   // 0: radix 4, 2, 3, 5 stages in that order; 1: reversed
+    int tc_ctas = 0;       // persistent CTAs of the tensor-core projection
+    int scan_nc = 0;       // components per CTA of the radial scan (1 or 2)
+  } tune;
+
   // launch accounting and optional CUDA-event timers (one event pair per launch)
   long long launches = 0;
   bool timing = false;
@@ -378,6 +386,11 @@ cudaError_t residual_f64(const Plan& p, const double* rho, const double* phi, cu
 cudaError_t fft_inverse_update64(const Plan& p, const float* spec, double* phi, bool first, unsigned int* red,
                                  cudaStream_t s);
 int create_side_stream(Plan& p);   // side stream and events of a mixed multipole plan; sp_status
+
+// phi lines per CTA of the float32 panel FFTs (the tuned value when one is set)
+int panel_lpc(const Plan& p, int nlines);
+// radix schedule of a length-n FFT; order 1 reverses the default stage order
+bool make_fft_schedule(int n, int order, FftSchedule* s);
 
 // ---- ragged batch launches (kind: forward 0 = float32 panel from float64 rho,
 // 1 = float32 panel from the float32 residual, 2 = float64 shell; inverse 0 = iterate

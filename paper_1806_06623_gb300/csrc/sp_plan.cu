@@ -37,7 +37,7 @@ struct DeviceGuard {
     }                                                  \
   } while (0)
 
-bool make_schedule(int n, sp::FftSchedule* s) {
+bool make_schedule(int n, sp::FftSchedule* s, int order = 0) {
   s->n = n;
   s->nstages = 0;
   int r = n;
@@ -46,6 +46,7 @@ bool make_schedule(int n, sp::FftSchedule* s) {
   while (r % 3 == 0) { if (s->nstages >= sp::kMaxStages) return false; s->radix[s->nstages++] = 3; r /= 3; }
   while (r % 5 == 0) { if (s->nstages >= sp::kMaxStages) return false; s->radix[s->nstages++] = 5; r /= 5; }
   if (r != 1) return false;
+  if (order == 1) std::reverse(s->radix, s->radix + s->nstages);
   int ns = 1;
   for (int st = 0; st < s->nstages; ++st) {
     s->ns[st] = ns;
@@ -65,6 +66,14 @@ bool make_schedule(int n, sp::FftSchedule* s) {
 }
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace
+
+namespace sp {
+bool make_fft_schedule(int n, int order, FftSchedule* s) { return make_schedule(n, s, order); }
+}  // namespace sp
+
+namespace {
 
 template <typename T>
 int upload(T** dst, const T* src, size_t n) {

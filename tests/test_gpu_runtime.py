@@ -253,3 +253,32 @@ def test_graph_replay_equals_direct(S, prec_name):
     plan.solve(rho_p, out_a)
     torch.cuda.synchronize()
     assert torch.equal(out_a, ref_p)
+
+
+@pytest.mark.parametrize("prec_name", ["fp64", "x6"])
+def test_autotune_cache_and_parity(S, tmp_path, prec_name):
+    """sp_plan_autotune picks a launch configuration by timing solves, stores it in the
+    JSON cache, and a second plan of the same shape takes it from there; solves with the
+    tuned configuration still meet the precision's tolerance against the oracle."""
+    import json
+    prec = S.SP_FP64 if prec_name == "fp64" else S.SP_MIXED_BF16X6
+    p = W.ragged_instance(2)            # Nphi = 192: both radix orders are candidates
+    rho = torch.from_numpy(p.rho).cuda()
+    cache = tmp_path / "tune.json"
+    a = S.Plan(p.r_if, p.th_if, p.nphi, precision=prec)
+    hit, conf = a.autotune(rho, cache_path=cache)
+    assert not hit
+    entries = json.load(open(cache))
+    assert len(entries) == 1
+    b = S.Plan(p.r_if, p.th_if, p.nphi, precision=prec)
+    hit2, conf2 = b.autotune(rho, cache_path=cache)
+    assert hit2 and conf2 == conf
+    ref = O.solve_exact(O.Geometry(p.r_if, p.th_if, p.nphi), p.rho)
+    for plan in (a, b, b.clone()):
+        phi, info = plan.solve(rho)
+        assert info.status == S.SP_OK
+        err = float(np.max(np.abs(phi.cpu().numpy() - ref)) / np.max(np.abs(ref)))
+        assert err <= (1e-12 if prec == S.SP_FP64 else 1e-10)
+    pa, _ = a.solve(rho)
+    pb, _ = b.solve(rho)
+    assert torch.equal(pa, pb)        # the same configuration: the same bits
