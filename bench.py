@@ -296,6 +296,16 @@ def run_ours(args, rank, world, local):
         head.solve_host(rho_np, phi_np)
     e2e_s = time.perf_counter() - t0
     e2e_s = max_over_ranks(e2e_s, world, dev)
+    # the link's own rate for the same buffers: one step's H2D and D2H copies alone
+    d_tmp = torch.empty_like(rho)
+    torch.cuda.synchronize(dev)
+    c0 = time.perf_counter()
+    for _ in range(args.steps):
+        d_tmp.copy_(rho_h, non_blocking=True)
+        phi_h.copy_(d_tmp, non_blocking=True)
+    torch.cuda.synchronize(dev)
+    copy_s = (time.perf_counter() - c0) / args.steps
+    del d_tmp
 
     if rank != 0:
         return
@@ -317,7 +327,11 @@ def run_ours(args, rank, world, local):
         "clocks": r["clocks"],
         "gpu_launches": r["launches"],
         "e2e": {"value": whole_job_rate(zones, args.steps, world, e2e_s), "unit": "zones/s",
-                "h2d_bytes_per_step": int(p.rho.nbytes), "d2h_bytes_per_step": int(p.rho.nbytes)},
+                "h2d_bytes_per_step": int(p.rho.nbytes), "d2h_bytes_per_step": int(p.rho.nbytes),
+                "copy_ms_per_step": 1e3 * copy_s,
+                "copy_bound_zones_per_s": zones / copy_s,
+                "note": "the step's two copies alone (pinned, one stream) take copy_ms_per_step; a solve "
+                        "can overlap them only at its first and last transform"},
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in r["timing"].items()},
     }
     for name, rr in results.items():
