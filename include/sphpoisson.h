@@ -185,6 +185,26 @@ int sp_solve(sp_plan* plan, const double* rho_dev, double* phi_dev, void* stream
 int sp_solve_host(sp_plan* plan, const double* rho_host, double* phi_host, void* stream,
                   sp_solve_info* info);
 
+/* n solves of one plan from host buffers, q = 0..n-1 in order: rho_host[q] -> phi_host[q]
+ * (Sect. 3.2 for each; no counterpart in the paper's design).  The same results as n calls
+ * of sp_solve_host, but pipelined: the upload of q+1 and the download of q-1 run on two
+ * copy streams of the plan while q is solved on `stream`, through two device (rho, Phi)
+ * buffer pairs owned by the plan (4 x Nr x Ntheta x Nphi doubles, allocated on first use,
+ * freed with the plan).  With page-locked host buffers the copies overlap the solves and
+ * each other; with pageable ones the call is correct but the copies do not overlap.
+ * The host arrays must stay valid, and phi_host[q] unread, until the call returns (it
+ * synchronises `stream`); a phi_host pointer may repeat (later solves overwrite it in
+ * order), none may overlap a rho_host buffer.
+ *  n          number of solves (0: nothing to do)
+ *  rho_host   n host pointers, each Nr x Ntheta x Nphi doubles
+ *  phi_host   n host pointers, each Nr x Ntheta x Nphi doubles
+ *  infos      host array of n entries or NULL
+ * Returns SP_OK, SP_ERR_INVALID_ARG (a NULL plan, array or entry, or n < 0: nothing runs),
+ * SP_ERR_OOM, SP_ERR_CUDA, or the first failing solve's status; solves after a failing
+ * one are not run (their infos[q].status is the same error, iterations 0). */
+int sp_solve_host_pipelined(sp_plan* plan, int n, const double* const* rho_host, double* const* phi_host,
+                            void* stream, sp_solve_info* infos);
+
 /* n independent solves (Sect. 3.2 for each), any mix of grids and precisions, as one
  * call: instance q solves plans[q] with rho[q] -> phi[q] (device buffers as for
  * sp_solve).  The plans must be distinct (use sp_plan_clone for several problems on one

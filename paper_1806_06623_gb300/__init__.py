@@ -12,5 +12,5 @@ from ._binding import (  # noqa: F401
     sp_apply_laplacian, sp_apply_laplacian_noalloc, sp_face_gradients, sp_plan_create, sp_plan_destroy, sp_plan_get_eigen, sp_plan_last_status,
     sp_plan_set_workspace, sp_plan_workspace_bytes, sp_plan_set_timing, sp_plan_collect_timing,
     sp_plan_get_timing, sp_plan_launch_count, KERNEL_NAMES, sp_plan_clone, sp_solve_batched, sp_server_create,
-    sp_server_submit, sp_server_wait, sp_server_stats, sp_server_destroy, sp_server_reset_stats, ServerStats, sp_solve, sp_solve_host, sp_status_string,
+    sp_server_submit, sp_server_wait, sp_server_stats, sp_server_destroy, sp_server_reset_stats, ServerStats, sp_solve, sp_solve_host, sp_solve_host_pipelined, sp_status_string,
 )

@@ -89,6 +89,7 @@ _SIGS = {
     "sp_plan_set_workspace": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "sp_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(SolveInfo)]),
     "sp_solve_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(SolveInfo)]),
+    "sp_solve_host_pipelined": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "sp_apply_laplacian": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "sp_apply_laplacian_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "sp_plan_get_eigen": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -294,6 +295,25 @@ def sp_solve_host(plan, rho, phi, stream=None):
     return info
 
 
+def sp_solve_host_pipelined(plan, rhos, phis, stream=None):
+    """rhos, phis: lists of contiguous float64 host arrays of the plan's size (page-locked
+    for overlapped copies); solves q = 0..n-1 in order, returns the n SolveInfo."""
+    n = len(rhos)
+    if len(phis) != n:
+        raise ValueError("rhos and phis must have the same length")
+    size = rhos[0].size if n else 0
+    for r, f in zip(rhos, phis):
+        for a, name in ((r, "rho"), (f, "phi")):
+            if a.dtype != np.float64 or not a.flags.c_contiguous or a.size != size:
+                raise ValueError(f"{name} arrays must be contiguous float64 arrays of one size")
+    rp = (C.c_void_p * max(n, 1))(*[r.ctypes.data for r in rhos])
+    pp = (C.c_void_p * max(n, 1))(*[f.ctypes.data for f in phis])
+    infos = (SolveInfo * max(n, 1))()
+    st = lib().sp_solve_host_pipelined(plan, n, rp, pp, _stream_ptr(stream), infos)
+    _check(st, "sp_solve_host_pipelined")
+    return list(infos)[:n]
+
+
 def sp_apply_laplacian(plan, phi, out, shape, stream=None):
     n = int(np.prod(shape))
     _check(lib().sp_apply_laplacian(plan, _dev_ptr(phi, n, "phi"), _dev_ptr(out, n, "out"),
@@ -408,6 +428,14 @@ class Plan:
             out = np.empty(self.shape, dtype=np.float64)
         info = sp_solve_host(self._h, rho, out, stream)
         return out, info
+
+    def solve_host_pipelined(self, rhos, outs=None, stream=None):
+        """n solves from host arrays with the copies of neighbouring solves overlapped;
+        returns (outs, infos)."""
+        if outs is None:
+            outs = [np.empty(self.shape, dtype=np.float64) for _ in rhos]
+        infos = sp_solve_host_pipelined(self._h, rhos, outs, stream)
+        return outs, infos
 
     def apply_laplacian(self, phi, out=None, stream=None):
         import torch

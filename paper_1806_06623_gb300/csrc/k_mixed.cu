@@ -1357,4 +1357,19 @@ cudaError_t finish_rag(const FinishArgs* tab, const int* start, int n, int total
   return cudaGetLastError();
 }
 
+namespace {
+__global__ void __launch_bounds__(256) k_post_words(const unsigned int* __restrict__ src, unsigned int* dst, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+}  // namespace
+
+// A few result words of the device into page-locked host memory by the GPU's own stores:
+// no copy-engine transfer, so the host's read of a refinement decision does not queue
+// behind bulk host copies that other streams have in flight.
+cudaError_t post_words(const unsigned int* src, unsigned int* host_dst, int n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_post_words<<<1, 256, 0, s>>>(src, host_dst, n);
+  return cudaGetLastError();
+}
+
 }  // namespace sp

@@ -36,6 +36,7 @@ struct RagBuffers {
   size_t hcap = 0;
   unsigned int* d_red = nullptr;
   unsigned int* h_red = nullptr;
+  unsigned int* h_red_dev = nullptr;   // device address of h_red
   int red_n = 0;
   cudaEvent_t fork = nullptr, join = nullptr;
 };
@@ -56,10 +57,10 @@ int ensure(RagBuffers& b, size_t bytes, int n) {
     cudaFree(b.d_red);
     cudaFreeHost(b.h_red);
     b.d_red = nullptr;
-    b.h_red = nullptr;
+    b.h_red = b.h_red_dev = nullptr;
     b.red_n = 0;
     if (cudaMalloc(&b.d_red, sizeof(unsigned int) * 4 * n) != cudaSuccess) return SP_ERR_OOM;
-    if (cudaMallocHost(&b.h_red, sizeof(unsigned int) * 4 * n) != cudaSuccess) return SP_ERR_OOM;
+    if (const int st = alloc_host_words(4 * n, &b.h_red, &b.h_red_dev)) return st;
     b.red_n = n;
   }
   return SP_OK;
@@ -375,7 +376,7 @@ int run(Plan* const* P, const double* const* rho, double* const* phi, std::vecto
     if (!st) st = cuda_st(issue_solve<NP>(b, s0, i0, g.s));
     if (!st) st = cuda_st(issue_residual(b, r1, g.s, g.side));
     if (!st) st = cuda_st(issue_solve<NP>(b, s1, i1, g.s));
-    if (!st) st = cuda_st(cudaMemcpyAsync(b.h_red, b.d_red, sizeof(unsigned int) * 4 * n, cudaMemcpyDeviceToHost, g.s));
+    if (!st) st = cuda_st(post_words(b.d_red, b.h_red_dev, 4 * n, g.s));
     if (st) return st;
   }
   for (auto& g : groups)
@@ -416,7 +417,7 @@ int run(Plan* const* P, const double* const* rho, double* const* phi, std::vecto
       if (!st) st = cuda_st(cudaMemsetAsync(b.d_red, 0, sizeof(unsigned int) * words, g.s));
       if (!st) st = cuda_st(issue_residual(b, rr, g.s, g.side));
       if (!st) st = cuda_st(issue_solve<NP>(b, ss, ii, g.s));
-      if (!st) st = cuda_st(cudaMemcpyAsync(b.h_red, b.d_red, sizeof(unsigned int) * words, cudaMemcpyDeviceToHost, g.s));
+      if (!st) st = cuda_st(post_words(b.d_red, b.h_red_dev, words, g.s));
       if (st) return st;
     }
     if (!any) break;

@@ -234,21 +234,39 @@ struct Plan {
   // host-buffer path
   double* d_rho_io = nullptr;
   double* d_phi_io = nullptr;
+  // pipelined host-buffer path: two device (rho, Phi) pairs, copy streams and their events
+  struct HostPipe {
+    double* rho[2] = {nullptr, nullptr};
+    double* phi[2] = {nullptr, nullptr};
+    cudaStream_t h2d = nullptr, d2h = nullptr;
+    cudaEvent_t in[2] = {nullptr, nullptr};       // rho[b] uploaded
+    cudaEvent_t solved[2] = {nullptr, nullptr};   // the solve reading rho[b] / writing phi[b] done
+    cudaEvent_t out[2] = {nullptr, nullptr};      // phi[b] downloaded
+    cudaEvent_t join = nullptr;
+  };
+  HostPipe* pipe = nullptr;
 
   MixedTables* mixed = nullptr;
   unsigned int* h_red = nullptr;  // pinned host copy of the mixed-path reductions
+  unsigned int* h_red_dev = nullptr;   // the same memory as the device addresses it
   const double* phi64_written = nullptr;   // output already holding the current iterate in float64
-  // CUDA graph of phase A of a mixed solve (first low-precision solve + first correction
-  // with their host reads), captured on a private stream for one (rho, phi, workspace)
+  // CUDA graphs of phase A of a mixed solve (first low-precision solve + first correction
+  // with their host reads), captured on a private stream, each for one (rho, phi,
+  // workspace); two are kept, so that callers alternating two buffer pairs replay both
   bool graphs = true;
   bool phase_a_warm = false;      // one direct phase A ran (attributes set, workspace bound)
   cudaStream_t cap_stream = nullptr;
-  cudaGraphExec_t ga_exec = nullptr;
-  const void* ga_rho = nullptr;
-  const void* ga_phi = nullptr;
-  const void* ga_ws = nullptr;
-  long long ga_launches = 0;
-  int ga_pending = 0;
+  struct PhaseGraph {
+    cudaGraphExec_t exec = nullptr;
+    const void* rho = nullptr;
+    const void* phi = nullptr;
+    const void* ws = nullptr;
+    long long launches = 0;
+    int pending = 0;
+  };
+  static constexpr int kPhaseGraphs = 2;
+  PhaseGraph ga[kPhaseGraphs];
+  int ga_victim = 0;              // the entry the next capture replaces when both are taken
   // side stream (high priority) and fork/join events: the multipole shell term of the
   // mixed residual runs beside the residual's interior rows
   cudaStream_t side = nullptr;
@@ -415,6 +433,11 @@ cudaError_t residual_rag(bool lo_read, const ResArgs* tab, const int* start, int
                          cudaStream_t s);
 void shell_finish_desc(const Plan& p, FinishArgs& a, int& ctas);
 cudaError_t finish_rag(const FinishArgs* tab, const int* start, int n, int total, cudaStream_t s);
+// n result words of the device -> page-locked host memory (`host_dst` a device-accessible
+// pointer of a cudaMallocHost allocation), by one kernel's stores instead of a copy
+cudaError_t post_words(const unsigned int* src, unsigned int* host_dst, int n, cudaStream_t s);
+// n page-locked host words and the device address of the same memory (SP_OK / SP_ERR_*)
+int alloc_host_words(int n, unsigned int** host, unsigned int** dev);
 cudaError_t shell_apply_rag(const ShellArgs* tab, const int* start, int n, int total, cudaStream_t s);
 
 // ---- solve phases shared by sp_solve, sp_solve_batched and the server ----

@@ -83,6 +83,23 @@ int upload(T** dst, const T* src, size_t n) {
 }
 
 // Release what the plan owns; the shared tables go with the last plan using them.
+void free_pipe(Plan* p) {
+  if (!p->pipe) return;
+  Plan::HostPipe& q = *p->pipe;
+  for (int b = 0; b < 2; ++b) {
+    cudaFree(q.rho[b]);
+    cudaFree(q.phi[b]);
+    if (q.in[b]) cudaEventDestroy(q.in[b]);
+    if (q.solved[b]) cudaEventDestroy(q.solved[b]);
+    if (q.out[b]) cudaEventDestroy(q.out[b]);
+  }
+  if (q.join) cudaEventDestroy(q.join);
+  if (q.h2d) cudaStreamDestroy(q.h2d);
+  if (q.d2h) cudaStreamDestroy(q.d2h);
+  delete p->pipe;
+  p->pipe = nullptr;
+}
+
 void free_tables(Plan* p) {
   const bool last = !p->table_refs || p->table_refs->fetch_sub(1) == 1;
   if (last) {
@@ -113,6 +130,7 @@ void free_tables(Plan* p) {
   cudaFree(p->d_err);
   cudaFree(p->d_rho_io);
   cudaFree(p->d_phi_io);
+  free_pipe(p);
   if (p->h_red) cudaFreeHost(p->h_red);
   if (p->ws_owned) cudaFree(p->ws);
   for (int i = 0; i < 2 * sp::kMaxTimedLaunches; ++i)
@@ -265,8 +283,8 @@ int mixed_correct(Plan* p, const double* rho, double* phi, cudaStream_t s) {
 // Queue the copy of the reductions of the last low-precision solve to the next of two
 // pinned host slots.
 int mixed_issue_read(Plan* p, cudaStream_t s, MixedRun& R) {
-  SP_CUDA(cudaMemcpyAsync(p->h_red + 2 * R.next_slot, p->mixed->red, 2 * sizeof(unsigned int), cudaMemcpyDeviceToHost,
-                          s));
+  SP_CUDA(post_words(p->mixed->red, p->h_red_dev + 2 * R.next_slot, 2, s));
+  ++p->launches;
   R.next_slot ^= 1;
   ++R.pending;
   return SP_OK;
@@ -286,8 +304,9 @@ int phase_a_direct(Plan* p, const double* rho, double* phi, cudaStream_t s, Mixe
 }
 
 // Capture phase A on the plan's private stream (thread-local capture mode, so other host
-// threads' calls are unaffected) and instantiate it; false leaves the plan without a graph.
-bool capture_phase_a(Plan* p, const double* rho, double* phi) {
+// threads' calls are unaffected) and instantiate it into `g`; false leaves the plan
+// without graphs.
+bool capture_phase_a(Plan* p, const double* rho, double* phi, Plan::PhaseGraph& g) {
   if (!p->cap_stream && cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
     p->cap_stream = nullptr;
     return false;
@@ -296,58 +315,74 @@ bool capture_phase_a(Plan* p, const double* rho, double* phi) {
   MixedRun Rc;
   if (cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return false;
   const int st = phase_a_direct(p, rho, phi, p->cap_stream, Rc);
-  cudaGraph_t g = nullptr;
-  const cudaError_t e = cudaStreamEndCapture(p->cap_stream, &g);
-  p->ga_launches = p->launches - l0;
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(p->cap_stream, &graph);
+  g.launches = p->launches - l0;
   p->launches = l0;   // nothing ran yet
-  bool ok = st == SP_OK && e == cudaSuccess && g != nullptr;
-  if (ok && cudaGraphInstantiate(&p->ga_exec, g, 0) != cudaSuccess) {
-    p->ga_exec = nullptr;
+  bool ok = st == SP_OK && e == cudaSuccess && graph != nullptr;
+  if (ok && cudaGraphInstantiate(&g.exec, graph, 0) != cudaSuccess) {
+    g.exec = nullptr;
     ok = false;
   }
-  if (g) cudaGraphDestroy(g);
+  if (graph) cudaGraphDestroy(graph);
   if (!ok) {
     cudaGetLastError();   // clear a capture error; the plan runs phase A directly from now on
     p->graphs = false;
+    drop_phase_graph(*p);
     return false;
   }
-  p->ga_rho = rho;
-  p->ga_phi = phi;
-  p->ga_ws = p->ws;
-  p->ga_pending = Rc.pending;
+  g.rho = rho;
+  g.phi = phi;
+  g.ws = p->ws;
+  g.pending = Rc.pending;
   return true;
 }
 
 }  // namespace
 
 void drop_phase_graph(Plan& p) {
-  if (p.ga_exec) cudaGraphExecDestroy(p.ga_exec);
-  p.ga_exec = nullptr;
-  p.ga_rho = p.ga_phi = p.ga_ws = nullptr;
+  for (auto& g : p.ga) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g = Plan::PhaseGraph{};
+  }
+  p.ga_victim = 0;
 }
 
 // The first call runs directly (it sets the kernels' shared-memory attributes and binds the
 // workspace); later calls replay a graph captured for the same rho, phi and workspace
-// (re-captured when one of them changes).  Per-launch timers need the direct path.
+// (captured when none of the plan's two graphs matches, replacing the older one).
+// Per-launch timers need the direct path.
 int mixed_phase_a(Plan* p, const double* rho, double* phi, cudaStream_t s, MixedRun& R) {
   if (!p->graphs || p->timing || !p->phase_a_warm) {
     const int st = phase_a_direct(p, rho, phi, s, R);
     if (st == SP_OK) p->phase_a_warm = true;
     return st;
   }
-  if (!(p->ga_exec && p->ga_rho == rho && p->ga_phi == phi && p->ga_ws == p->ws)) {
-    drop_phase_graph(*p);
-    if (!capture_phase_a(p, rho, phi)) return phase_a_direct(p, rho, phi, s, R);
+  Plan::PhaseGraph* g = nullptr;
+  for (auto& c : p->ga)
+    if (c.exec && c.rho == rho && c.phi == phi && c.ws == p->ws) g = &c;
+  if (!g) {
+    int k = -1;
+    for (int i = 0; i < Plan::kPhaseGraphs && k < 0; ++i)
+      if (!p->ga[i].exec) k = i;
+    if (k < 0) {
+      k = p->ga_victim;
+      p->ga_victim = (k + 1) % Plan::kPhaseGraphs;
+      cudaGraphExecDestroy(p->ga[k].exec);
+      p->ga[k] = Plan::PhaseGraph{};
+    }
+    if (!capture_phase_a(p, rho, phi, p->ga[k])) return phase_a_direct(p, rho, phi, s, R);
+    g = &p->ga[k];
   }
-  SP_CUDA(cudaGraphLaunch(p->ga_exec, s));
+  SP_CUDA(cudaGraphLaunch(g->exec, s));
   // host bookkeeping of what the graph did: its reductions sit in the first host slots,
   // and the iterate is in the state its one correction leaves
-  R.pending = p->ga_pending;
-  R.next_slot = p->ga_pending & 1;
+  R.pending = g->pending;
+  R.next_slot = g->pending & 1;
   p->phi64_written = (p->max_iter >= 1 || p->mixed->resid64) ? phi : nullptr;
   p->mixed->lo_zero = false;
   p->mixed->iter64 = (first_correction_f64_only(*p) && !p->mixed->resid64) ? phi : nullptr;
-  p->launches += p->ga_launches;
+  p->launches += g->launches;
   return SP_OK;
 }
 
@@ -421,7 +456,8 @@ int mixed_finish_issue(Plan* p, double* phi, cudaStream_t s) {
   if (P.phi64_written != phi &&
       (st = launch_status(timed_launch(P, kKUpdate, s, [&] { return finish_mixed(P, phi, s); }))))
     return st;
-  SP_CUDA(cudaMemcpyAsync(P.h_red + kRedErrWord, P.d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  SP_CUDA(post_words(reinterpret_cast<const unsigned int*>(P.d_err), P.h_red_dev + kRedErrWord, 1, s));
+  ++P.launches;
   return SP_OK;
 }
 
@@ -776,10 +812,7 @@ int sp_plan_create_ex(const sp_plan_desc* desc, void* stream, sp_plan** out) {
     if (precision != SP_FP64 && (st = sp::mixed_create_tables(*p, s))) break;
     // the float-float residual's floor above the tolerance: float64 iterate and residual
     if (precision != SP_FP64) p->mixed->resid64 = sp::mixed_floor(*p, false) > tol;
-    if (precision != SP_FP64 && cudaMallocHost(&p->h_red, 8 * sizeof(unsigned int)) != cudaSuccess) {
-      st = SP_ERR_OOM;
-      break;
-    }
+    if (precision != SP_FP64 && (st = sp::alloc_host_words(8, &p->h_red, &p->h_red_dev))) break;
     if ((st = sp::create_side_stream(*p))) break;
   } while (0);
   if (st != SP_OK) {
@@ -808,6 +841,7 @@ int sp_plan_clone(const sp_plan* src_plan, sp_plan** out) {
   c->specA = c->specB = c->cp = c->shell = c->shell2 = nullptr;
   c->d_rho_io = c->d_phi_io = nullptr;
   c->h_red = nullptr;
+  c->h_red_dev = nullptr;
   c->launches = 0;
   c->timing = false;
   c->n_timed = 0;
@@ -819,13 +853,14 @@ int sp_plan_clone(const sp_plan* src_plan, sp_plan** out) {
     c->mixed = new (std::nothrow) sp::MixedTables(*src->mixed);
     if (!c->mixed) st = SP_ERR_OOM;
     else sp::mixed_clear_workspace(*c->mixed);
-    if (st == SP_OK && cudaMallocHost(&c->h_red, 8 * sizeof(unsigned int)) != cudaSuccess) st = SP_ERR_OOM;
+    if (st == SP_OK) st = sp::alloc_host_words(8, &c->h_red, &c->h_red_dev);
   }
   c->side = nullptr;
   c->ev_fork = c->ev_join = nullptr;
   c->cap_stream = nullptr;
-  c->ga_exec = nullptr;
-  c->ga_rho = c->ga_phi = c->ga_ws = nullptr;
+  for (auto& g : c->ga) g = sp::Plan::PhaseGraph{};
+  c->ga_victim = 0;
+  c->pipe = nullptr;
   c->phase_a_warm = false;
   if (st == SP_OK) st = sp::create_side_stream(*c);
   if (st == SP_OK && cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess) st = SP_ERR_OOM;
@@ -890,6 +925,98 @@ int sp_solve_host(sp_plan* plan, const double* rho_host, double* phi_host, void*
   SP_CUDA(cudaMemcpyAsync(phi_host, p->d_phi_io, bytes, cudaMemcpyDeviceToHost, s));
   SP_CUDA(cudaStreamSynchronize(s));
   return SP_OK;
+}
+
+// Device buffers, copy streams and events of the pipelined host path (made on first use).
+static int ensure_pipe(Plan* p, size_t bytes) {
+  if (p->pipe) return SP_OK;
+  p->pipe = new (std::nothrow) Plan::HostPipe;
+  if (!p->pipe) return SP_ERR_OOM;
+  Plan::HostPipe& q = *p->pipe;
+  bool ok = cudaStreamCreateWithFlags(&q.h2d, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&q.d2h, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&q.join, cudaEventDisableTiming) == cudaSuccess;
+  for (int b = 0; b < 2 && ok; ++b)
+    ok = cudaEventCreateWithFlags(&q.in[b], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&q.solved[b], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&q.out[b], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    free_pipe(p);
+    return SP_ERR_CUDA;
+  }
+  for (int b = 0; b < 2; ++b)
+    if (cudaMalloc(&q.rho[b], bytes) != cudaSuccess || cudaMalloc(&q.phi[b], bytes) != cudaSuccess) {
+      cudaGetLastError();
+      free_pipe(p);
+      return SP_ERR_OOM;
+    }
+  return SP_OK;
+}
+
+int sp_solve_host_pipelined(sp_plan* plan, int n, const double* const* rho_host, double* const* phi_host,
+                            void* stream, sp_solve_info* infos) {
+  cudaGetLastError();   // an earlier failed call of this thread is not this call's error
+  if (!plan || n < 0 || (n > 0 && (!rho_host || !phi_host))) return SP_ERR_INVALID_ARG;
+  for (int q = 0; q < n; ++q)
+    if (!rho_host[q] || !phi_host[q]) return SP_ERR_INVALID_ARG;
+  if (n == 0) return SP_OK;
+  Plan* p = reinterpret_cast<Plan*>(plan);
+  const size_t bytes = sizeof(double) * (size_t)p->nr * p->nth * p->nphi;
+  DeviceGuard guard(p->device);
+  int st = ensure_pipe(p, bytes);
+  if (st) return st;
+  Plan::HostPipe& P = *p->pipe;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // Solve q uses buffer pair b = q mod 2.  The upload of q waits for solve q-2 (the last
+  // reader of rho[b]); solve q waits for its upload and for the download of q-2 (the last
+  // reader of phi[b]); the download of q waits for solve q.  Upload q+1 and download q-1
+  // are queued before solve q, so both copy directions run while q computes, also across
+  // the host waits of a mixed solve.
+  auto upload = [&](int q) -> cudaError_t {
+    const int b = q & 1;
+    cudaError_t e = q >= 2 ? cudaStreamWaitEvent(P.h2d, P.solved[b], 0) : cudaSuccess;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(P.rho[b], rho_host[q], bytes, cudaMemcpyHostToDevice, P.h2d);
+    if (e == cudaSuccess) e = cudaEventRecord(P.in[b], P.h2d);
+    return e;
+  };
+  int first_err = SP_OK, done = 0;
+  if (upload(0) != cudaSuccess) first_err = SP_ERR_CUDA;
+  for (int q = 0; q < n && first_err == SP_OK; ++q) {
+    const int b = q & 1;
+    if (q + 1 < n && upload(q + 1) != cudaSuccess) { first_err = SP_ERR_CUDA; break; }
+    if (cudaStreamWaitEvent(s, P.in[b], 0) != cudaSuccess ||
+        (q >= 2 && cudaStreamWaitEvent(s, P.out[b], 0) != cudaSuccess)) {
+      first_err = SP_ERR_CUDA;
+      break;
+    }
+    const int r = sp_solve(plan, P.rho[b], P.phi[b], stream, infos ? &infos[q] : nullptr);
+    done = q + 1;
+    if (r != SP_OK) {
+      first_err = r;
+      break;
+    }
+    if (cudaEventRecord(P.solved[b], s) != cudaSuccess || cudaStreamWaitEvent(P.d2h, P.solved[b], 0) != cudaSuccess ||
+        cudaMemcpyAsync(phi_host[q], P.phi[b], bytes, cudaMemcpyDeviceToHost, P.d2h) != cudaSuccess ||
+        cudaEventRecord(P.out[b], P.d2h) != cudaSuccess) {
+      first_err = SP_ERR_CUDA;
+      break;
+    }
+  }
+  // join both copy streams into the caller's stream and wait for everything queued
+  const bool joined = cudaEventRecord(P.join, P.h2d) == cudaSuccess && cudaStreamWaitEvent(s, P.join, 0) == cudaSuccess &&
+                      cudaEventRecord(P.join, P.d2h) == cudaSuccess && cudaStreamWaitEvent(s, P.join, 0) == cudaSuccess;
+  const cudaError_t se = cudaStreamSynchronize(s);
+  if (!joined) {
+    cudaStreamSynchronize(P.h2d);
+    cudaStreamSynchronize(P.d2h);
+  }
+  if (first_err == SP_OK && (!joined || se != cudaSuccess)) first_err = SP_ERR_CUDA;
+  if (infos)
+    for (int q = done; q < n; ++q) {   // not solved: a call before them failed
+      infos[q] = sp_solve_info{};
+      infos[q].status = first_err;
+    }
+  return first_err;
 }
 
 int sp_apply_laplacian(sp_plan* plan, const double* phi, double* out, void* stream) {
@@ -1071,6 +1198,23 @@ size_t plan_table_bytes(const Plan& p) {
 }  // namespace sp
 
 namespace sp {
+
+int alloc_host_words(int n, unsigned int** host, unsigned int** dev) {
+  *host = *dev = nullptr;
+  if (cudaMallocHost(host, sizeof(unsigned int) * n) != cudaSuccess) {
+    cudaGetLastError();
+    *host = nullptr;
+    return SP_ERR_OOM;
+  }
+  if (cudaHostGetDevicePointer(reinterpret_cast<void**>(dev), *host, 0) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFreeHost(*host);
+    *host = *dev = nullptr;
+    return SP_ERR_CUDA;
+  }
+  std::memset(*host, 0, sizeof(unsigned int) * n);
+  return SP_OK;
+}
 
 cudaError_t allow_dynamic_smem(const void* kernel, size_t bytes) {
   static std::mutex mu;

@@ -76,3 +76,11 @@ def test_invalid_enums_and_null_output():
     assert S.lib().sp_plan_create(r.ctypes.data_as(C.c_void_p), 2, None, 4, 8, 0, 1.0, 0, 1e-10, 8, None,
                                   None) == S.SP_ERR_INVALID_ARG
     assert S.lib().sp_plan_destroy(None) == S.SP_OK
+
+
+def test_pipelined_host_solve_rejects_null_arguments():
+    """Argument checks of sp_solve_host_pipelined run on the host before any copy or solve."""
+    L = S.lib()
+    one = (C.c_void_p * 1)(None)
+    assert L.sp_solve_host_pipelined(None, 1, one, one, None, None) == S.SP_ERR_INVALID_ARG
+    assert L.sp_solve_host_pipelined(None, -1, None, None, None, None) == S.SP_ERR_INVALID_ARG

@@ -282,3 +282,54 @@ def test_autotune_cache_and_parity(S, tmp_path, prec_name):
     pa, _ = a.solve(rho)
     pb, _ = b.solve(rho)
     assert torch.equal(pa, pb)        # the same configuration: the same bits
+
+
+@pytest.mark.parametrize("prec_name", ["SP_FP64", "SP_MIXED_BF16X6"])
+def test_host_pipelined_equals_single_calls(S, prec_name):
+    """sp_solve_host_pipelined gives bitwise the results of one sp_solve_host call per
+    problem (copies of neighbouring solves overlapped, two device buffer pairs in turn),
+    with page-locked and with pageable host buffers, and a repeated output pointer holds
+    the last solve's result."""
+    prec = getattr(S, prec_name)
+    p = W.stellar_noise()
+    srcs = [W.stellar_noise(seed=20 + k).rho for k in range(5)]
+    plan = S.Plan(p.r_if, p.th_if, p.nphi, precision=prec)
+    ref = [plan.solve_host(r)[0] for r in srcs]
+    infos_ref = [plan.solve_host(r)[1] for r in srcs]
+    pinned = [torch.from_numpy(r).pin_memory().numpy() for r in srcs]
+    outs = [torch.empty(p.rho.shape, dtype=torch.float64).pin_memory().numpy() for _ in srcs]
+    for rhos in (pinned, srcs):
+        for o in outs:
+            o.fill(np.nan)
+        got, infos = plan.solve_host_pipelined(rhos, outs)
+        for k in range(len(srcs)):
+            assert infos[k].status == S.SP_OK
+            assert np.array_equal(got[k], ref[k]), k
+            assert infos[k].iterations == infos_ref[k].iterations
+    shared = np.empty(p.rho.shape)
+    _, infos = plan.solve_host_pipelined(pinned[:3], [shared] * 3)
+    assert np.array_equal(shared, ref[2])
+    assert plan.solve_host_pipelined([], [])[1] == []
+    plan.close()
+
+
+def test_graphs_kept_for_two_buffer_pairs(S):
+    """A mixed plan alternating two (rho, Phi) pairs (the plan keeps a phase-A graph for
+    each) stays bitwise equal to the direct path."""
+    p = W.stellar_noise()
+    q = W.stellar_noise(seed=7)
+    direct = S.Plan(p.r_if, p.th_if, p.nphi, precision=S.SP_MIXED_BF16X6)
+    direct.set_graphs(False)
+    rp = torch.from_numpy(p.rho).cuda()
+    rq = torch.from_numpy(q.rho).cuda()
+    ref_p, _ = direct.solve(rp)
+    ref_q, _ = direct.solve(rq)
+    plan = S.Plan(p.r_if, p.th_if, p.nphi, precision=S.SP_MIXED_BF16X6)
+    oa, ob = torch.empty_like(rp), torch.empty_like(rp)
+    for k in range(6):
+        plan.solve(rp, oa)
+        plan.solve(rq, ob)
+        torch.cuda.synchronize()
+        assert torch.equal(oa, ref_p) and torch.equal(ob, ref_q), k
+    direct.close()
+    plan.close()
