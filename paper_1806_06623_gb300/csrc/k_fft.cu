@@ -12,6 +12,8 @@
 // inverse kernel rebuilds the Hermitian spectrum of each line pair with one lane-pair
 // shuffle, runs the inverse FFT and writes (or accumulates, or adds into a
 // float-float iterate) both real lines.
+#include <algorithm>
+
 #include "sp_internal.h"
 
 namespace sp {
@@ -244,6 +246,81 @@ __device__ typename C2<T>::t* warp_fft256(typename C2<T>::t* bufA, typename C2<T
   return bufA;
 }
 
+// The same two passes in place (float panels): each half-warp reads its line pair into
+// registers before it overwrites the pair's region, so one buffer of kPsInplace entries
+// per pair holds the line, the padded intermediate and the spectrum in turn.  The stride
+// is odd, so a lane pair per line pair in the load and store phases (stride PS between
+// lanes) spreads over the banks too.
+constexpr int kPsInplace = 273;
+
+// PLANAR: the pair's region holds the two real lines one after the other (line A in the
+// first 256 values, line B in the next 256) rather than as complex values; the first
+// pass then reads A and B separately (the half-warps' pairs sit kWarps pairs = 16 banks
+// apart, so the 32-bit reads do not conflict).
+template <bool INV, bool PLANAR, typename T>
+__device__ typename C2<T>::t* warp_fft256_inplace(typename C2<T>::t* buf, const typename C2<T>::t* tw, int npairs) {
+  using CT = typename C2<T>::t;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int b = lane & 15;
+  CT v[16];
+  for (int p0 = warp; p0 < npairs; p0 += 2 * kWarps) {
+    const int p = p0 + (lane >> 4) * kWarps;   // pair p stays with warp p mod kWarps
+    CT* z = buf + p * kPsInplace;
+    if (p < npairs) {
+      if (PLANAR) {
+        const T* za = reinterpret_cast<const T*>(z);
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+          v[r].x = za[b + 16 * r];
+          v[r].y = za[256 + b + 16 * r];
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[r] = z[b + 16 * r];
+      }
+      dft16<INV, T>(v);
+    }
+    __syncwarp();   // the half-warp has read its whole pair
+    if (p < npairs) {
+#pragma unroll
+      for (int q1 = 0; q1 < 4; ++q1)
+#pragma unroll
+        for (int q2 = 0; q2 < 4; ++q2) z[17 * b + q1 + 4 * q2] = v[4 * q1 + q2];
+    }
+  }
+  __syncwarp();
+  for (int p0 = warp; p0 < npairs; p0 += 2 * kWarps) {
+    const int p = p0 + (lane >> 4) * kWarps;
+    CT* z = buf + p * kPsInplace;
+    if (p < npairs) {
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {
+        CT x = z[17 * r + b];
+        if (r != 0 && b != 0) {
+          CT t = tw[r * b];
+          if (INV) t.y = -t.y;
+          x = cmul(x, t);
+        }
+        v[r] = x;
+      }
+      dft16<INV, T>(v);
+    }
+    __syncwarp();
+    if (p < npairs) {
+#pragma unroll
+      for (int q1 = 0; q1 < 4; ++q1)
+#pragma unroll
+        for (int q2 = 0; q2 < 4; ++q2) z[b + 16 * (q1 + 4 * q2)] = v[4 * q1 + q2];
+    }
+  }
+  __syncwarp();
+  return buf;
+}
+
+// Float panels of Nphi = 256 run the in-place radix-16 passes.
+template <typename T>
+__host__ __device__ constexpr bool fft_inplace(int n) { return sizeof(T) == 4 && n == 256; }
+
 // Bulk prefetch of the `lines` contiguous lines starting at `line` into L2 (16-byte
 // multiples only; a hint, so nothing happens otherwise).
 template <typename Tv>
@@ -299,11 +376,12 @@ __device__ __forceinline__ void fft_fwd_body(const Tin* __restrict__ in, int nli
   using CT = typename C2<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = sch.n;
-  const int PS = n + 1;
+  const bool inplace = fft_inplace<T>(n);
+  const int PS = inplace ? kPsInplace : n + 1;
   const int P = lpc / 2;
   CT* tw = reinterpret_cast<CT*>(smem_raw);
   CT* bufA = tw + n;
-  CT* bufB = bufA + P * PS;
+  CT* bufB = inplace ? nullptr : bufA + P * PS;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   load_twiddles<T>(tw, twid, n);   // plan-constant: before the dependency wait
   pdl_trigger();
@@ -341,9 +419,25 @@ __device__ __forceinline__ void fft_fwd_body(const Tin* __restrict__ in, int nli
           const int ev = e * V;
           const int line = sch.nshift >= 0 ? (ev >> sch.nshift) : (int)__umulhi((unsigned int)ev, sch.nmagic);
           const int q = ev - line * n;
-          T* dst = reinterpret_cast<T*>(bufA + (line >> 1) * PS + q) + (line & 1);
+          if (inplace) {
+            // planar: V consecutive values of one line in 8-byte stores (the pair stride
+            // is even in values); with V = 4 the upper half of each 16 threads stores its
+            // second half first, so that a half-warp's 8-byte stores cover all 32 banks
+            T* dst = reinterpret_cast<T*>(bufA + (line >> 1) * PS) + (line & 1) * n + q;
+            const int i0 = (V == 4 && (threadIdx.x & 8)) ? 2 : 0;
 #pragma unroll
-          for (int i = 0; i < V; ++i) dst[2 * i] = cvt_in<T>(Vec16<Tin>::at(w[u], i));
+            for (int h = 0; h < V; h += 2) {
+              const int i = h ^ i0;
+              typename C2<T>::t t2;
+              t2.x = cvt_in<T>(Vec16<Tin>::at(w[u], i));
+              t2.y = cvt_in<T>(Vec16<Tin>::at(w[u], i + 1));
+              *reinterpret_cast<typename C2<T>::t*>(dst + i) = t2;
+            }
+          } else {
+            T* dst = reinterpret_cast<T*>(bufA + (line >> 1) * PS + q) + (line & 1);
+#pragma unroll
+            for (int i = 0; i < V; ++i) dst[2 * i] = cvt_in<T>(Vec16<Tin>::at(w[u], i));
+          }
         }
       }
     }
@@ -361,17 +455,22 @@ __device__ __forceinline__ void fft_fwd_body(const Tin* __restrict__ in, int nli
       if (e < tot) {
         const int line = sch.nshift >= 0 ? (e >> sch.nshift) : (int)__umulhi((unsigned int)e, sch.nmagic);
         const int q = e - line * n;
-        reinterpret_cast<T*>(bufA + (line >> 1) * PS + q)[line & 1] = v[u];
+        if (inplace) reinterpret_cast<T*>(bufA + (line >> 1) * PS)[(line & 1) * n + q] = v[u];
+        else reinterpret_cast<T*>(bufA + (line >> 1) * PS + q)[line & 1] = v[u];
       }
     }
   }
   if (nl & 1)
-    for (int q = threadIdx.x; q < n; q += blockDim.x) bufA[(nl >> 1) * PS + q].y = T(0);
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+      if (inplace) reinterpret_cast<T*>(bufA + (nl >> 1) * PS)[n + q] = T(0);
+      else bufA[(nl >> 1) * PS + q].y = T(0);
+    }
   __syncthreads();
   // the two-pass radix-16 form keeps a half-warp per line pair: it pays only with every
   // warp busy; few pairs (one shell) take the radix-4 passes with a whole warp per pair
-  CT* Z = (n == 256 && npairs >= 2 * kWarps) ? warp_fft256<false, T>(bufA, bufB, tw, npairs, PS)
-                                             : warp_fft<false, T>(bufA, bufB, tw, sch, npairs, PS);
+  CT* Z = inplace ? warp_fft256_inplace<false, true, T>(bufA, tw, npairs)
+          : (n == 256 && npairs >= 2 * kWarps) ? warp_fft256<false, T>(bufA, bufB, tw, npairs, PS)
+                                               : warp_fft<false, T>(bufA, bufB, tw, sch, npairs, PS);
   __syncthreads();
   const int mh = n / 2 + 1;
   const int l = lane;
@@ -419,11 +518,12 @@ __device__ __forceinline__ void fft_inv_body(const T* __restrict__ spec, int nli
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ float s_me[kWarps], s_mp[kWarps];
   const int n = sch.n;
-  const int PS = n + 1;
+  const bool inplace = fft_inplace<T>(n);
+  const int PS = inplace ? kPsInplace : n + 1;
   const int P = lpc / 2;
   CT* tw = reinterpret_cast<CT*>(smem_raw);
   CT* bufA = tw + n;
-  CT* bufB = bufA + P * PS;
+  CT* bufB = inplace ? nullptr : bufA + P * PS;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   load_twiddles<T>(tw, twid, n);   // plan-constant: before the dependency wait
   pdl_trigger();
@@ -488,8 +588,9 @@ __device__ __forceinline__ void fft_inv_body(const T* __restrict__ spec, int nli
     }
   }
   __syncthreads();
-  CT* Z = (n == 256 && npairs >= 2 * kWarps) ? warp_fft256<true, T>(bufA, bufB, tw, npairs, PS)
-                                             : warp_fft<true, T>(bufA, bufB, tw, sch, npairs, PS);
+  CT* Z = inplace ? warp_fft256_inplace<true, false, T>(bufA, tw, npairs)
+          : (n == 256 && npairs >= 2 * kWarps) ? warp_fft256<true, T>(bufA, bufB, tw, npairs, PS)
+                                               : warp_fft<true, T>(bufA, bufB, tw, sch, npairs, PS);
   float me = 0.f, mp = 0.f;
   for (int p = warp; p < npairs; p += kWarps) {
     const CT* z = Z + p * PS;
@@ -624,14 +725,14 @@ __device__ __forceinline__ void fft_inv_body(const T* __restrict__ spec, int nli
 }
 
 template <typename T, typename Tin>
-__global__ void __launch_bounds__(256, 3) k_fft_fwd(const Tin* __restrict__ in, int nlines, int nth, int nrs,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 3) k_fft_fwd(const Tin* __restrict__ in, int nlines, int nth, int nrs,
                                                  FftSchedule sch, const T* __restrict__ twid, T scale, int lpc,
                                                  T* __restrict__ spec, int rs, int ahead) {
   fft_fwd_body<T, Tin>(in, nlines, nth, nrs, sch, twid, scale, lpc, spec, rs, ahead, blockIdx.x, gridDim.x);
 }
 
 template <typename T, typename Tout, int MODE>
-__global__ void __launch_bounds__(256, 3) k_fft_inv(const T* __restrict__ spec, int nlines, int nth, int nrs,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 3) k_fft_inv(const T* __restrict__ spec, int nlines, int nth, int nrs,
                                                  FftSchedule sch, const T* __restrict__ twid, int lpc,
                                                  Tout* __restrict__ out, float* __restrict__ phi_lo, int first,
                                                  int lo_read, int hilo, unsigned int* __restrict__ red, int ahead,
@@ -644,7 +745,7 @@ __global__ void __launch_bounds__(256, 3) k_fft_inv(const T* __restrict__ spec, 
 // the instance q with start[q] <= b < start[q+1] and runs that instance's transform
 // as its CTA b - start[q].
 template <typename T, typename Tin>
-__global__ void __launch_bounds__(256, 3) k_fft_fwd_rag(const FwdArgs* __restrict__ tab,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 3) k_fft_fwd_rag(const FwdArgs* __restrict__ tab,
                                                      const int* __restrict__ start, int n) {
   const int q = rag_instance(start, n, blockIdx.x);
   const FwdArgs& a = tab[q];
@@ -654,7 +755,7 @@ __global__ void __launch_bounds__(256, 3) k_fft_fwd_rag(const FwdArgs* __restric
 }
 
 template <typename T, typename Tout, int MODE>
-__global__ void __launch_bounds__(256, 3) k_fft_inv_rag(const InvArgs* __restrict__ tab,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 3) k_fft_inv_rag(const InvArgs* __restrict__ tab,
                                                      const int* __restrict__ start, int n) {
   const int q = rag_instance(start, n, blockIdx.x);
   const InvArgs& a = tab[q];
@@ -693,6 +794,7 @@ namespace {
 template <typename T>
 size_t fft_smem(int n, int lpc) {
   const size_t P = (size_t)(lpc / 2);
+  if (fft_inplace<T>(n)) return sizeof(typename C2<T>::t) * ((size_t)n + P * kPsInplace);
   const size_t psb = n == 256 ? (size_t)kPad256 : (size_t)n + 1;
   return sizeof(typename C2<T>::t) * ((size_t)n + P * (n + 1) + P * psb);
 }
@@ -747,24 +849,35 @@ cudaError_t fft_inverse_f64(const Plan& p, const double* spec, int nrs, double* 
   return cudaGetLastError();
 }
 
+// How many CTAs ahead the forward transform prefetches its input: one resident wave, but
+// no more than ~32 MB of input in flight towards L2 (a farther prefetch is evicted again
+// before its CTA reads it: 190 against 144 MB read for the float64 source at 608 CTAs).
+static int prefetch_ahead(int resident, size_t bytes_per_cta) {
+  const size_t cap = (size_t(32) << 20) / (bytes_per_cta ? bytes_per_cta : 1);
+  return (int)std::min<size_t>((size_t)resident, cap);
+}
+
 cudaError_t fft_forward_panel(const Plan& p, const void* in, bool in_double, float scale, int kstride, float* out,
                               cudaStream_t s) {
   const int nlines = p.nr * p.nth;
   const int lpc = panel_lpc(p, nlines);
   const size_t smem = fft_smem<float>(p.nphi, lpc);
   const int grid = (nlines + lpc - 1) / lpc;
+  const size_t cta_bytes = (size_t)lpc * p.nphi * (in_double ? sizeof(double) : sizeof(float));
   cudaError_t e;
   if (in_double) {
     auto kern = k_fft_fwd<float, double>;
     if ((e = prep(kern, smem)) != cudaSuccess) return e;
     e = launch_pdl(kern, dim3(grid), dim3(32 * kWarps), smem, s, static_cast<const double*>(in), nlines, p.nth, p.nr,
-                   p.sched, (const float*)p.d_twid32, scale, lpc, out, kstride, resident_ctas(kern, smem, p.num_sms));
+                   p.sched, (const float*)p.d_twid32, scale, lpc, out, kstride,
+                   prefetch_ahead(resident_ctas(kern, smem, p.num_sms), cta_bytes));
     if (e != cudaSuccess) return e;
   } else {
     auto kern = k_fft_fwd<float, float>;
     if ((e = prep(kern, smem)) != cudaSuccess) return e;
     e = launch_pdl(kern, dim3(grid), dim3(32 * kWarps), smem, s, static_cast<const float*>(in), nlines, p.nth, p.nr,
-                   p.sched, (const float*)p.d_twid32, scale, lpc, out, kstride, resident_ctas(kern, smem, p.num_sms));
+                   p.sched, (const float*)p.d_twid32, scale, lpc, out, kstride,
+                   prefetch_ahead(resident_ctas(kern, smem, p.num_sms), cta_bytes));
     if (e != cudaSuccess) return e;
   }
   return cudaGetLastError();
