@@ -541,7 +541,7 @@ def run_served(S, W, torch, n_requests, rates=(200.0, 2000.0, 20000.0)):
 # sources they were taken from: `source_sha` is kernel_source_hash() of that build (the
 # device code of the mixed path and its launchers), and the bench reports traffic as
 # null once those sources differ.
-MIXED_KERNEL_SOURCES = ("k_fft.cu", "k_mixed.cu", "tc_gemm.cuh", "ff.cuh", "sp_internal.h")
+MIXED_KERNEL_SOURCES = ("k_fft.cu", "k_mixed.cu", "fft_dev.cuh", "tc_gemm.cuh", "ff.cuh", "sp_internal.h")
 NCU_TRAFFIC = {
     "source_sha": "307ef65aa68a3859",
     "mixed": {   # MB read + written, averaged over the group's launches in one solve
@@ -611,7 +611,7 @@ def projection_tensor_rate(timing, p, precision):
             "executed": f"{mh} m x {tiles} column tiles x {kblocks} K blocks x 4 x {nprod} MMAs of 128x128x16"}
 
 
-def algorithmic_bytes_per_step(p, precision, iters=2):
+def algorithmic_bytes_per_step(p, precision, iters=2, fused=None):
     """Bytes each kernel group must move per solve (inputs read once, outputs written once).
 
     Z = zones, S = spectral values 2 mh Nr Ntheta.  Mixed path with `iters` low-precision
@@ -623,7 +623,10 @@ def algorithmic_bytes_per_step(p, precision, iters=2):
     and float64 Phi (the first correction with 6 products float64 Phi only); the residual
     reads rho and the iterate (the high word only after the first solve) and writes r;
     without a correction a separate update reads the high word and writes float64 Phi,
-    and with 6 products and a second correction one rebuilds both words from float64."""
+    and with 6 products and a second correction one rebuilds both words from float64.
+    Where the library fuses the residual with its forward FFT (`fused`; by default for
+    Nphi = 256 and even Ntheta, as the library does) the residual writes the panel (4 B per
+    spectral value) instead of r, and the forward FFT group is the transform of rho alone."""
     nr, nth, nphi = p.shape
     mh = nphi // 2 + 1
     Z = float(nr * nth * nphi)
@@ -635,13 +638,16 @@ def algorithmic_bytes_per_step(p, precision, iters=2):
     npl = 3 if precision == "mixed" else 2
     T = 2.0 * npl * mh * nth * nth
     c = iters - 1   # corrections
-    return {"fft_forward": (8 * Z + 4 * S) + c * (4 * Z + 4 * S),
+    if fused is None:
+        fused = nphi == 256 and nth % 2 == 0
+    res_out = 4 * S if fused else 4 * Z      # the residual's output: the panel, or r
+    return {"fft_forward": (8 * Z + 4 * S) + (0 if fused else c * (4 * Z + 4 * S)),
             "project_forward": iters * (8 * S + T),
             "radial_solve": iters * (4 * S + 4 * S + 4 * S),
             "project_inverse": iters * (8 * S + T),
             "fft_inverse": (4 * S + 4 * Z) + min(c, 1) * (4 * S + (12 if npl == 3 else 20) * Z)
                            + max(c - 1, 0) * (4 * S + 24 * Z),
-            "residual": min(c, 1) * 16 * Z + max(c - 1, 0) * 20 * Z,
+            "residual": min(c, 1) * (12 * Z + res_out) + max(c - 1, 0) * (16 * Z + res_out),
             "update": 12 * Z if c == 0 else (16 * Z if npl == 3 and c >= 2 else 0.0)}
 
 

@@ -12,6 +12,7 @@
 #include <new>
 #include <vector>
 
+#include "fft_dev.cuh"
 #include "sp_internal.h"
 #include "tc_gemm.cuh"
 
@@ -923,6 +924,189 @@ __global__ void __launch_bounds__(kResThreads) k_residual_ff2_rag(const ResArgs*
                         a.dirichlet, a.dir_coef, a.four_pi_g, bx, byz % a.gy, byz / a.gy);
 }
 
+// ---- The residual fused with its forward phi FFT (Nphi = 256, float-float iterate).
+//
+// residual_zone2 with the theta window carried instead of the radial one: the difference
+// Phi(j-1) - Phi(j) comes in (dmh, dml; the negated Phi(j+1) - Phi(j) of the previous
+// line, exactly), Phi(i-1) comes as values.  The terms are summed in the same order with
+// the same operations, so the residual is bitwise that of k_residual_ff2.
+template <bool LO>
+__device__ __forceinline__ float2 residual_zone2j(float2 ch, float2 cl, bool has_im, float2 imh, float2 iml,
+                                                  bool has_ip, float2 nh, float2 nl, bool has_jm, float2& dmh,
+                                                  float2& dml, bool has_jp, float2 jph, float2 jpl, float2 qh,
+                                                  float2 ql, float2 oh, float2 ol, const RadialRowFF& rr,
+                                                  const ThetaRowFF& ar, double2 rv, const ff& four_pi_g) {
+  float2 dh, dl, p, e;
+  float2 sh = f2s(0.f), sl = f2s(0.f);
+  if (has_im) {
+    ffd_diff2<LO>(imh, iml, ch, cl, dh, dl);
+    ffd_mul2(rr.sub, dh, dl, p, e);
+    sh = p;
+    sl = e;
+  }
+  if (has_ip) {
+    ffd_diff2<LO>(nh, nl, ch, cl, dh, dl);
+    ffd_mul2(rr.sup, dh, dl, p, e);
+    ffd_acc2(sh, sl, p, e);
+  }
+  if (has_jm) {
+    ffd_mul2(ar.tm, dmh, dml, p, e);
+    ffd_acc2(sh, sl, p, e);
+  }
+  if (has_jp) {
+    ffd_diff2<LO>(jph, jpl, ch, cl, dh, dl);
+    ffd_mul2(ar.tp, dh, dl, p, e);
+    ffd_acc2(sh, sl, p, e);
+    dmh = neg2(dh);
+    dml = neg2(dl);
+  }
+  ffd_mul2(ar.sphi, qh, ql, p, e);
+  ffd_acc2(sh, sl, p, e);
+  if (!has_ip) ffd_acc2(sh, sl, oh, ol);
+  const ff rx = d2ff_trunc(rv.x), ry = d2ff_trunc(rv.y);
+  const float2 rh = make_float2(rx.hi, ry.hi), rl = make_float2(rx.lo, ry.lo);
+  const float2 sp = __fmul2_rn(f2s(four_pi_g.hi), rh);
+  float2 se = __ffma2_rn(f2s(four_pi_g.hi), rh, neg2(sp));
+  se = __ffma2_rn(f2s(four_pi_g.hi), rl, se);
+  se = __ffma2_rn(f2s(four_pi_g.lo), rh, se);
+  const float2 svh = add2(sp, se);
+  const float2 svl = sub2(se, sub2(svh, sp));
+  float2 th_, tl;
+  two_sum2(svh, neg2(sh), th_, tl);
+  tl = add2(tl, sub2(svl, sl));
+  return add2(th_, tl);
+}
+
+// One CTA per (radial row i, block of lpc consecutive j; even lpc <= 32): each half of the
+// 256 threads takes lpc/2 consecutive lines of the block, a thread per phi column pair,
+// and marches in j with the theta window in registers (Phi(j+1) loaded, Phi(j) and the
+// face difference kept; Phi(i-1), Phi(i+1), rho and the (i, j) coefficients loaded per
+// line; the line's phi neighbours from a shared-memory copy of it).  The residual lines
+// go planar into the in-place radix-16 buffer, then the block's half spectrum (scaled by
+// `scale`) to the panel spec[m][i][c][j] with row stride rs.  This drops the float32
+// residual's round trip through HBM (write, then the FFT's read: 8 bytes per zone).
+// Ntheta even, so every block starts on an even line and pairs the lines as the
+// stand-alone transform does: the spectrum is bitwise that of k_residual_ff2 followed by
+// k_fft_fwd<float, float>.
+constexpr int kRfN = 256;               // Nphi
+constexpr int kRfPairs = kRfN / 2;      // column pairs per line = threads per half
+template <bool LO>
+__global__ void __launch_bounds__(256, 4) k_residual_fft(
+    const double* __restrict__ rho, const float* __restrict__ ph, const float* __restrict__ pl,
+    const double* __restrict__ outer_shell, const RadialRowFF* __restrict__ rad, const ThetaRowFF* __restrict__ ang,
+    int nr, int nth, int row_begin, int lpc, int dirichlet, ff dir_coef, ff four_pi_g,
+    const float* __restrict__ twid, float scale, float* __restrict__ spec, int rs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // [step parity][half][hi, lo][even, odd column of the pair][pair + 1, with the wrap]
+  __shared__ float line[2][2][2][2][kRfPairs + 2];
+  float2* tw = reinterpret_cast<float2*>(smem_raw);
+  float2* buf = tw + kRfN;
+  load_twiddles<float>(tw, twid, kRfN);   // plan-constant: before the dependency wait
+  pdl_trigger();
+  pdl_wait();
+  const int ncb = (nth + lpc - 1) / lpc;
+  const int i = row_begin + (int)blockIdx.x / ncb;
+  const int j0 = ((int)blockIdx.x % ncb) * lpc;
+  const int nl = min(lpc, nth - j0);
+  const int half = lpc >> 1;
+  const int t = threadIdx.x & (kRfPairs - 1);
+  const int h = threadIdx.x >> 7;
+  const int l0 = h * half;                        // first line of this half in the block
+  const int nlh = max(0, min(half, nl - l0));     // lines of this half
+  const size_t shell = (size_t)nth * kRfN;
+  const size_t sh2 = shell >> 1;                  // strides in pairs
+  const bool has_im = i > 0, has_ip = i < nr - 1;
+  const float2 z2 = make_float2(0.f, 0.f);
+  const RadialRowFF rr = rad[i];
+  const int k = 2 * t;                            // even column of the pair
+  // pair pointers of line (i, j) at step 0
+  int j = j0 + l0;
+  size_t c0 = (size_t)i * shell + (size_t)j * kRfN + k;
+  const float2* hp = reinterpret_cast<const float2*>(ph + c0);
+  const float2* lp = reinterpret_cast<const float2*>(pl + c0);
+  float2 ch = z2, cl = z2, dmh = z2, dml = z2;
+  if (nlh > 0) {
+    ch = hp[0];
+    if (LO) cl = lp[0];
+    if (j > 0) {
+      const float2 bh = hp[-(ptrdiff_t)(kRfN / 2)], bl = LO ? lp[-(ptrdiff_t)(kRfN / 2)] : z2;
+      ffd_diff2<LO>(bh, bl, ch, cl, dmh, dml);   // Phi(j-1) - Phi(j)
+    }
+  }
+  for (int st = 0; st < half; ++st) {
+    const bool act = st < nlh;
+    float* ev = line[st & 1][h][0][0];
+    float* od = line[st & 1][h][0][1];
+    float* evl = line[st & 1][h][1][0];
+    float* odl = line[st & 1][h][1][1];
+    if (act) {
+      ev[t + 1] = ch.x;
+      od[t + 1] = ch.y;
+      if (t == kRfPairs - 1) od[0] = ch.y;   // column Nphi-1, left of column 0
+      if (t == 0) ev[kRfPairs + 1] = ch.x;   // column 0, right of column Nphi-1
+      if (LO) {
+        evl[t + 1] = cl.x;
+        odl[t + 1] = cl.y;
+        if (t == kRfPairs - 1) odl[0] = cl.y;
+        if (t == 0) evl[kRfPairs + 1] = cl.x;
+      }
+    }
+    const bool has_jm = j > 0, has_jp = j < nth - 1;
+    float2 nh = z2, nl2 = z2, imh = z2, iml = z2, jph = z2, jpl = z2;
+    double2 rv = make_double2(0.0, 0.0);
+    ThetaRowFF ar{};
+    if (act) {
+      if (has_ip) {
+        nh = hp[sh2];
+        if (LO) nl2 = lp[sh2];
+      }
+      if (has_im) {
+        imh = hp[-(ptrdiff_t)sh2];
+        if (LO) iml = lp[-(ptrdiff_t)sh2];
+      }
+      if (has_jp) {
+        jph = hp[kRfN / 2];
+        if (LO) jpl = lp[kRfN / 2];
+      }
+      rv = *reinterpret_cast<const double2*>(rho + c0);
+      ar = ang[(size_t)i * nth + j];
+    }
+    // the halves exchange nothing: each waits for its own 4 warps only (barriers 1, 2)
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + h), "r"(kRfPairs) : "memory");
+    if (act) {
+      float dmh_, dml_;
+      ffd_diff_lo<LO>(ch.y, cl.y, ch.x, cl.x, dmh_, dml_);   // Phi(k+1) - Phi(k)
+      float2 qh, ql;                                          // Phi(k-1) - Phi(k), Phi(k+2) - Phi(k+1)
+      ffd_diff2<LO>(make_float2(od[t], ev[t + 2]), LO ? make_float2(odl[t], evl[t + 2]) : z2, ch, cl, qh, ql);
+      ffd_acc2(qh, ql, make_float2(dmh_, -dmh_), make_float2(dml_, -dml_));
+      float2 oh = z2, ol = z2;
+      if (!has_ip) {
+        outer_term(dirichlet, dir_coef, ch.x, cl.x, outer_shell, (size_t)j * kRfN + k, oh.x, ol.x);
+        outer_term(dirichlet, dir_coef, ch.y, cl.y, outer_shell, (size_t)j * kRfN + k + 1, oh.y, ol.y);
+      }
+      const float2 res = residual_zone2j<LO>(ch, cl, has_im, imh, iml, has_ip, nh, nl2, has_jm, dmh, dml, has_jp,
+                                             jph, jpl, qh, ql, oh, ol, rr, ar, rv, four_pi_g);
+      // planar into the transform buffer: line l = l0 + st of pair l / 2
+      const int l = l0 + st;
+      *reinterpret_cast<float2*>(reinterpret_cast<float*>(buf + (l >> 1) * kPsInplace) + (l & 1) * kRfN + k) = res;
+      ch = jph;
+      cl = jpl;
+      hp += kRfN / 2;
+      lp += kRfN / 2;
+      c0 += kRfN;
+      ++j;
+    }
+  }
+  __syncthreads();
+  const int npairs = (nl + 1) / 2;
+  if (nl & 1)   // (not with even Ntheta and lpc; kept for the general form)
+    for (int q = threadIdx.x; q < kRfN; q += blockDim.x) reinterpret_cast<float*>(buf + (nl >> 1) * kPsInplace)[kRfN + q] = 0.f;
+  __syncthreads();
+  float2* Z = warp_fft256_inplace<false, true, float>(buf, tw, npairs);
+  __syncthreads();
+  store_half_spectrum<float>(Z, kPsInplace, nl, i * nth + j0, nth, nr, kRfN, scale, spec, rs);
+}
+
 // float64 Phi = hi + lo (pl null: lo = 0)
 __device__ __forceinline__ void finish_body(const float* __restrict__ ph, const float* __restrict__ pl,
                                             double* __restrict__ phi, size_t n, int bx, int gx) {
@@ -1197,6 +1381,46 @@ cudaError_t residual_ff(const Plan& p, const double* rho, cudaStream_t s) {
   if (p.nr > 1 && (e = rows(0, p.nr - 1, s)) != cudaSuccess) return e;
   if ((e = cudaStreamWaitEvent(s, p.ev_join, 0)) != cudaSuccess) return e;
   return rows(p.nr - 1, p.nr, s);
+}
+
+bool residual_fft_supported(const Plan& p, const double* rho) {
+  return p.nphi == kRfN && (p.nth & 1) == 0 && (reinterpret_cast<uintptr_t>(rho) & 15u) == 0 && !p.mixed->resid64;
+}
+
+// The float-float residual fused with its forward FFT into the panel (see k_residual_fft),
+// with the same side-stream shell term as residual_ff: interior rows in blocks of 32
+// lines while the shell chain runs, the last shell after the join in blocks of 4 lines
+// (more CTAs for the one row on the critical path).
+cudaError_t residual_fft(const Plan& p, const double* rho, cudaStream_t s) {
+  const MixedTables& x = *p.mixed;
+  auto kern = x.lo_zero ? k_residual_fft<false> : k_residual_fft<true>;
+  auto rows = [&](int r0, int r1, int lpc, cudaStream_t st) {
+    const size_t smem = sizeof(float2) * ((size_t)kRfN + (size_t)(lpc / 2) * kPsInplace);
+    cudaError_t e = allow_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    const int ncb = (p.nth + lpc - 1) / lpc;
+    e = launch_pdl(kern, dim3((unsigned)((r1 - r0) * ncb)), dim3(256), smem, st, rho, (const float*)x.phi_hi,
+                   (const float*)x.phi_lo, (const double*)x.outer_shell, (const RadialRowFF*)x.radff,
+                   (const ThetaRowFF*)x.thff, p.nr, p.nth, r0, lpc, p.outer_bc == SP_OUTER_DIRICHLET ? 1 : 0,
+                   x.dir_coef, x.four_pi_g, (const float*)p.d_twid32, (float)(1.0 / p.nphi), x.panel, x.kstride);
+    return e != cudaSuccess ? e : cudaGetLastError();
+  };
+  if (p.outer_bc != SP_OUTER_MULTIPOLE) return rows(0, p.nr, 32, s);
+  cudaError_t e;
+  if ((e = cudaEventRecord(p.ev_fork, s)) != cudaSuccess || (e = cudaStreamWaitEvent(p.side, p.ev_fork, 0)) != cudaSuccess)
+    return e;
+  const size_t sh = (size_t)p.nth * p.nphi;
+  const size_t off = (size_t)(p.nr - 1) * sh;
+  k_finish<<<(unsigned)((sh + 255) / 256), 256, 0, p.side>>>(x.phi_hi + off, x.lo_zero ? nullptr : x.phi_lo + off,
+                                                              x.shell_phi, sh);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = fft_forward_f64(p, x.shell_phi, 1, 1.0 / p.nphi, p.shell, p.side)) != cudaSuccess) return e;
+  if ((e = shell_kappa_f64(p, p.shell, p.shell2, p.side)) != cudaSuccess) return e;
+  if ((e = fft_inverse_f64(p, p.shell2, 1, x.outer_shell, false, p.side)) != cudaSuccess) return e;
+  if ((e = cudaEventRecord(p.ev_join, p.side)) != cudaSuccess) return e;
+  if (p.nr > 1 && (e = rows(0, p.nr - 1, 32, s)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(s, p.ev_join, 0)) != cudaSuccess) return e;
+  return rows(p.nr - 1, p.nr, 4, s);
 }
 
 // Refinement residual in float64 for a float64 iterate: r = 4 pi G rho - (Delta Phi) with

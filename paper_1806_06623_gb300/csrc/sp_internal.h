@@ -399,6 +399,10 @@ bool first_correction_f64_only(const Plan& p);   // the first correction stores 
 cudaError_t tc_project(const Plan& p, bool inverse, cudaStream_t s);   // pan -> d32
 cudaError_t thomas_mixed(const Plan& p, cudaStream_t s);   // d32 -> pan (f); float32 + float64 low modes
 cudaError_t residual_ff(const Plan& p, const double* rho, cudaStream_t s);  // iterate -> r32
+// the float-float residual fused with its forward FFT (iterate -> panel), where
+// residual_fft_supported: Nphi = 256, even Ntheta, 16-byte aligned rho, float-float residual
+bool residual_fft_supported(const Plan& p, const double* rho);
+cudaError_t residual_fft(const Plan& p, const double* rho, cudaStream_t s);
 cudaError_t residual_f64(const Plan& p, const double* rho, const double* phi, cudaStream_t s);  // float64 iterate -> r32
 // inverse FFT adding the correction into a float64 iterate (first: phi = e), reductions into red
 cudaError_t fft_inverse_update64(const Plan& p, const float* spec, double* phi, bool first, unsigned int* red,

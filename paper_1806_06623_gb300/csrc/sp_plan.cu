@@ -194,12 +194,13 @@ int solve_fp64(Plan* p, const double* rho, double* phi, cudaStream_t s) {
 // One low-precision separated solve of L e = (scale*Nphi) * input: FFT (float32, bf16
 // split), tcgen05 projection, float32/float64 radial solves, tcgen05 back projection,
 // inverse FFT with Phi (+)= e and the max|e|, max|Phi| reductions.
+// in == nullptr: the panel already holds the right-hand side's spectrum.
 int lp_solve(Plan* p, const void* in, bool in_double, float scale, double* phi, bool first, cudaStream_t s) {
   Plan& P = *p;
   sp::MixedTables& x = *P.mixed;
   int st;
-  if ((st = launch_status(sp::timed_launch(P, sp::kKFftFwd, s, [&] {
-         return sp::fft_forward_panel(P, in, in_double, scale, x.kstride, x.panel, s); }))))
+  if (in && (st = launch_status(sp::timed_launch(P, sp::kKFftFwd, s, [&] {
+                return sp::fft_forward_panel(P, in, in_double, scale, x.kstride, x.panel, s); }))))
     return st;
   if ((st = launch_status(sp::timed_launch(P, sp::kKGemmFwd, s, [&] { return sp::tc_project(P, false, s); }))))
     return st;
@@ -272,10 +273,15 @@ int mixed_correct(Plan* p, const double* rho, double* phi, cudaStream_t s) {
       return st;
     P.mixed->iter64 = nullptr;
   }
-  if ((st = launch_status(timed_launch(P, kKResidual, s, [&] { return residual_ff(P, rho, s); })))) return st;
+  // the residual and its forward FFT in one kernel where supported (the spectrum goes
+  // straight to the panel), else the residual to r32 and the transform in lp_solve
+  const bool fused = residual_fft_supported(P, rho);
+  if ((st = launch_status(timed_launch(P, kKResidual, s, [&] {
+         return fused ? residual_fft(P, rho, s) : residual_ff(P, rho, s); }))))
+    return st;
   if (P.outer_bc == SP_OUTER_MULTIPOLE) P.launches += 5;   // shell: finish, FFT, apply, inverse FFT; split residual
   SP_CUDA(cudaMemsetAsync(P.mixed->red, 0, 2 * sizeof(unsigned int), s));
-  st = lp_solve(p, P.mixed->r32, false, (float)(1.0 / P.nphi), phi, false, s);
+  st = lp_solve(p, fused ? nullptr : P.mixed->r32, false, (float)(1.0 / P.nphi), phi, false, s);
   if (st == SP_OK) P.phi64_written = phi;
   return st;
 }

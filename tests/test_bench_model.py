@@ -15,7 +15,7 @@ def grid():
 
 
 def test_six_product_solve_with_one_correction():
-    b = bench.algorithmic_bytes_per_step(grid(), "mixed", iters=2)
+    b = bench.algorithmic_bytes_per_step(grid(), "mixed", iters=2, fused=False)
     t = 2 * 3 * MH * NTH * NTH                      # three bf16 planes of the table
     assert b["fft_forward"] == (8 * Z + 4 * S) + (4 * Z + 4 * S)   # rho in, then r in; panel out
     assert b["project_forward"] == b["project_inverse"] == 2 * (8 * S + t)
@@ -30,7 +30,7 @@ def test_six_product_solve_with_one_correction():
 
 
 def test_three_product_solve_with_two_corrections():
-    b = bench.algorithmic_bytes_per_step(grid(), "mixed_x3", iters=3)
+    b = bench.algorithmic_bytes_per_step(grid(), "mixed_x3", iters=3, fused=False)
     # both corrections store the float-float iterate (and float64 Phi)
     assert b["fft_inverse"] == (4 * S + 4 * Z) + (4 * S + 20 * Z) + (4 * S + 24 * Z)
     assert b["residual"] == 16 * Z + 20 * Z         # the second reads both words
@@ -38,13 +38,13 @@ def test_three_product_solve_with_two_corrections():
 
 
 def test_second_six_product_correction_rebuilds_the_words():
-    b = bench.algorithmic_bytes_per_step(grid(), "mixed", iters=3)
+    b = bench.algorithmic_bytes_per_step(grid(), "mixed", iters=3, fused=False)
     assert b["update"] == 16 * Z                    # float64 in, two float words out
     assert b["residual"] == 16 * Z + 20 * Z
 
 
 def test_no_correction_converts_the_high_word():
-    b = bench.algorithmic_bytes_per_step(grid(), "mixed", iters=1)
+    b = bench.algorithmic_bytes_per_step(grid(), "mixed", iters=1, fused=False)
     assert b["update"] == 12 * Z and b["residual"] == 0
     assert b["fft_inverse"] == 4 * S + 4 * Z
 
@@ -53,3 +53,14 @@ def test_float64_path():
     b = bench.algorithmic_bytes_per_step(grid(), "fp64")
     assert b["fft_forward"] == 8 * Z + 8 * S and b["fft_inverse"] == 8 * S + 8 * Z
     assert b["radial_solve"] == 16 * S + 4 * S
+
+
+def test_residual_fused_with_its_transform():
+    """Nphi = 256: the residual kernel writes the panel, so r's write and read are gone."""
+    b = bench.algorithmic_bytes_per_step(grid(), "mixed", iters=2)
+    u = bench.algorithmic_bytes_per_step(grid(), "mixed", iters=2, fused=False)
+    assert b["fft_forward"] == 8 * Z + 4 * S                      # rho alone
+    assert b["residual"] == 8 * Z + 4 * Z + 4 * S                 # rho, high word in; panel out
+    assert sum(u.values()) - sum(b.values()) == 8 * Z             # r written and read once each
+    b3 = bench.algorithmic_bytes_per_step(grid(), "mixed_x3", iters=3)
+    assert b3["residual"] == (12 * Z + 4 * S) + (16 * Z + 4 * S)  # the second reads both words
