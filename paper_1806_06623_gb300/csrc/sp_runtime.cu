@@ -232,7 +232,9 @@ struct Request {
 struct Resident {
   sp_plan* master = nullptr;
   size_t table_bytes = 0;
-  size_t clone_bytes = 0;   // workspace of one clone
+  size_t clone_bytes = 0;   // device memory of one clone beside its workspace (error word)
+  size_t ws_bytes = 0;      // the grid's workspace, held by the slot that runs it
+  size_t io_bytes = 0;      // the grid's device rho and Phi, held by the slot that runs it
   int active = 0;
   bool creating = false;
   int create_status = SP_OK;
@@ -320,6 +322,8 @@ void sp_server::worker(int slot) {
   cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
   double* d_io = nullptr;
   size_t d_io_bytes = 0;
+  void* ws = nullptr;        // this slot's workspace
+  size_t ws_bytes = 0;
   std::unique_lock<std::mutex> lock(mu);
   while (true) {
     // admit the oldest request whose plan memory fits (or any request when nothing runs)
@@ -335,10 +339,14 @@ void sp_server::worker(int slot) {
       auto r = resident.find(c->key);
       const bool have = r != resident.end() && r->second.master;
       if (r != resident.end() && r->second.creating) continue;   // another slot builds its plan
-      // rough need before the plan exists: tables + workspace of the float64 layout
+      // rough need before the plan exists: tables + workspace of the float64 layout;
+      // for a resident grid, a clone if none is idle and this slot's workspace growth
       size_t need = c->io_bytes;
       if (!have) need += 64u << 20;
-      else if (r->second.idle.empty()) need += r->second.clone_bytes;
+      else {
+        if (r->second.idle.empty()) need += r->second.clone_bytes;
+        if (r->second.ws_bytes > ws_bytes) need += r->second.ws_bytes - ws_bytes;
+      }
       if (mem_used + need <= budget || evict_for(need) || running == 0) {
         q = c;
         reserve = c->io_bytes;
@@ -371,7 +379,9 @@ void sp_server::worker(int slot) {
         res.master = m;
         const Plan* pm = reinterpret_cast<const Plan*>(m);
         res.table_bytes = sp::plan_table_bytes(*pm);
-        res.clone_bytes = sp_plan_workspace_bytes(m);
+        res.clone_bytes = 256;
+        res.ws_bytes = sp_plan_workspace_bytes(m);
+        res.io_bytes = 2 * q->zones * sizeof(double);
         mem_used += res.table_bytes;
         mem_peak = std::max(mem_peak, mem_used);
       }
@@ -396,13 +406,55 @@ void sp_server::worker(int slot) {
     // slots launch kernel by kernel: a graph capture on one slot's thread while another
     // slot's thread allocates or synchronises would make that thread's call fail
     if (st == SP_OK && !plan && (st = sp_plan_clone(master, &plan)) == SP_OK) sp_plan_set_graphs(plan, 0);
-    const size_t need_io = 2 * q->zones * sizeof(double);
+    // the plan runs in this slot's workspace (grown to the largest grid the slot has run),
+    // so a clone allocates no workspace of its own and reusing one costs a pointer rebind
+    if (st == SP_OK) {
+      size_t need_ws = sp_plan_workspace_bytes(plan);
+      if (need_ws > ws_bytes) {
+        // grow once to the largest resident grid's workspace that the budget leaves room
+        // for (a free synchronises the device, so repeated growth would stall every slot)
+        lock.lock();
+        size_t want = need_ws;
+        for (const auto& kv : resident) want = std::max(want, kv.second.ws_bytes);
+        if (want > need_ws && mem_used - ws_bytes + want > budget) want = need_ws;
+        lock.unlock();
+        need_ws = want;
+        cudaFree(ws);
+        ws = nullptr;
+        const size_t old = ws_bytes;
+        ws_bytes = 0;
+        if (cudaMalloc(&ws, need_ws) != cudaSuccess) {
+          cudaGetLastError();
+          ws = nullptr;
+          st = SP_ERR_OOM;
+        } else {
+          ws_bytes = need_ws;
+        }
+        lock.lock();
+        mem_used = mem_used - old + ws_bytes;
+        mem_peak = std::max(mem_peak, mem_used);
+        lock.unlock();
+      }
+      if (st == SP_OK && reinterpret_cast<Plan*>(plan)->ws != ws) st = sp_plan_set_workspace(plan, ws, ws_bytes);
+    }
+    size_t need_io = 2 * q->zones * sizeof(double);
     if (st == SP_OK && d_io_bytes < need_io) {
+      // as the workspace: once to the largest resident grid's (budget permitting)
+      lock.lock();
+      size_t want = need_io;
+      for (const auto& kv : resident) want = std::max(want, kv.second.io_bytes);
+      if (want > need_io && mem_used + want > budget) want = need_io;
+      lock.unlock();
+      need_io = want;
       cudaFree(d_io);
       d_io = nullptr;
       d_io_bytes = 0;
-      if (cudaMalloc(&d_io, need_io) != cudaSuccess) st = SP_ERR_OOM;
-      else d_io_bytes = need_io;
+      if (cudaMalloc(&d_io, need_io) != cudaSuccess) {
+        cudaGetLastError();
+        st = SP_ERR_OOM;
+      } else {
+        d_io_bytes = need_io;
+      }
     }
     sp_solve_info info{};
     if (st == SP_OK) {
@@ -447,8 +499,10 @@ void sp_server::worker(int slot) {
     cv_done.notify_all();
     cv_work.notify_all();
   }
+  mem_used -= ws_bytes;
   lock.unlock();
   cudaFree(d_io);
+  cudaFree(ws);
   cudaStreamDestroy(s);
 }
 
