@@ -543,19 +543,18 @@ def run_served(S, W, torch, n_requests, rates=(200.0, 2000.0, 20000.0)):
 # null once those sources differ.
 MIXED_KERNEL_SOURCES = ("k_fft.cu", "k_mixed.cu", "fft_dev.cuh", "tc_gemm.cuh", "ff.cuh", "sp_internal.h")
 NCU_TRAFFIC = {
-    "source_sha": "307ef65aa68a3859",
+    "source_sha": "5d80588854243225",
     "mixed": {   # MB read + written, averaged over the group's launches in one solve
-        "fft_forward": {"bytes": ((159.815 + 38.332) + (72.186 + 22.034)) * 1e6 / 2,
-                        "kernel": "k_fft_fwd<float, double> (rho), k_fft_fwd<float, float> (residual)"},
-        "project_forward": {"bytes": ((91.442 + 19.287) + (91.619 + 19.686)) * 1e6 / 2,
+        "fft_forward": {"bytes": (173.52 + 36.51) * 1e6, "kernel": "k_fft_fwd<float, double> (rho)"},
+        "project_forward": {"bytes": ((91.48 + 18.96) + (91.64 + 19.30)) * 1e6 / 2,
                             "kernel": "tc::k_tc_gemm_split<3>"},
-        "radial_solve": {"bytes": ((145.790 + 38.804) + (145.785 + 38.967)) * 1e6 / 2, "kernel": "k_thomas_scan<2>"},
-        "project_inverse": {"bytes": ((91.566 + 19.055) + (91.577 + 19.302)) * 1e6 / 2,
+        "radial_solve": {"bytes": ((145.76 + 38.53) + (145.85 + 38.43)) * 1e6 / 2, "kernel": "k_thomas_scan<2>"},
+        "project_inverse": {"bytes": ((91.57 + 19.33) + (91.56 + 19.17)) * 1e6 / 2,
                             "kernel": "tc::k_tc_gemm_split<3>"},
-        "fft_inverse": {"bytes": ((72.166 + 21.997) + (144.367 + 87.471)) * 1e6 / 2,
+        "fft_inverse": {"bytes": ((72.17 + 20.70) + (145.23 + 85.12)) * 1e6 / 2,
                         "kernel": "k_fft_inv<float, float, 2> (first solve, correction)"},
-        "residual": {"bytes": (219.370 + 50.544 + 0.801) * 1e6,
-                     "kernel": "k_residual_ff2<0> (interior rows + last shell)"},
+        "residual": {"bytes": (218.80 + 44.48 + 0.82) * 1e6,
+                     "kernel": "k_residual_fft<0> (interior rows + last shell: residual and its forward FFT)"},
     },
 }
 
