@@ -1185,7 +1185,7 @@ void mixed_bind_workspace(Plan& p, char* c) {
   p.shell2 = reinterpret_cast<double*>(c);
   c += al256((size_t)p.mh * 2 * p.nth * 8);
   x.red = reinterpret_cast<unsigned int*>(c);
-  p.specA = p.specB = p.cp = nullptr;
+  p.specA = p.specB = nullptr;
 }
 
 int mixed_create_tables(Plan& p, cudaStream_t s) {

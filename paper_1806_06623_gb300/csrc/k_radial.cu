@@ -15,10 +15,15 @@
 namespace sp {
 namespace {
 
-__global__ void __launch_bounds__(128) k_thomas_f64(const RadialRow* __restrict__ rad, const double* __restrict__ lam,
-                                                    const double* __restrict__ outer, const double* __restrict__ inner,
-                                                    double* __restrict__ x, double* __restrict__ cp, int nr, int nth,
-                                                    int mh) {
+// Elimination factors of every (m,l) radial system (plan set-up, float64): the forward
+// sweep of the Thomas algorithm without a right-hand side, storing 1/pivot_i and
+// c'_i = sup_i / pivot_i; the diagonal carries R_i lambda_lm, the multipole outer row and
+// the regular-interior inner row.
+__global__ void __launch_bounds__(128) k_radial_factors_f64(const RadialRow* __restrict__ rad,
+                                                            const double* __restrict__ lam,
+                                                            const double* __restrict__ outer,
+                                                            const double* __restrict__ inner, double* __restrict__ tinv,
+                                                            double* __restrict__ tcp, int nr, int nth, int mh) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= mh * nth) return;
   const int m = t / nth;
@@ -26,10 +31,9 @@ __global__ void __launch_bounds__(128) k_thomas_f64(const RadialRow* __restrict_
   const double L = lam[t];
   const double od = outer[t];
   const double id = inner[t];
-  double* X = x + (size_t)m * nr * 2 * nth + l;
-  double* CP = cp + (size_t)m * nr * nth + l;
-  const size_t st = 2 * (size_t)nth;
-  double cprev = 0.0, dre = 0.0, dim = 0.0;
+  double* INV = tinv + (size_t)m * nr * nth + l;
+  double* CP = tcp + (size_t)m * nr * nth + l;
+  double cprev = 0.0;
   for (int i = 0; i < nr; ++i) {
     const RadialRow rr = rad[i];
     double b = fma(rr.R, L, rr.base);
@@ -37,21 +41,74 @@ __global__ void __launch_bounds__(128) k_thomas_f64(const RadialRow* __restrict_
     if (i == nr - 1) b += od;
     const double piv = b - rr.sub * cprev;
     const double inv = 1.0 / piv;
-    const double xr = X[i * st];
-    const double xi = X[i * st + nth];
     cprev = rr.sup * inv;
-    dre = (xr - rr.sub * dre) * inv;
-    dim = (xi - rr.sub * dim) * inv;
-    X[i * st] = dre;
-    X[i * st + nth] = dim;
+    INV[(size_t)i * nth] = inv;
     CP[(size_t)i * nth] = cprev;
   }
-  for (int i = nr - 2; i >= 0; --i) {
-    const double c = CP[(size_t)i * nth];
-    dre = X[i * st] - c * dre;
-    dim = X[i * st + nth] - c * dim;
-    X[i * st] = dre;
-    X[i * st + nth] = dim;
+}
+
+// The radial solves of the separated system (Sect. 3.2, Eq. tridiag), float64, one thread
+// per (m,l) and both components: forward elimination d_i = (x_i - sub_i d_{i-1}) / pivot_i
+// and back substitution f_i = d_i - c'_i f_{i+1} with the plan's factor tables, so no
+// division on the (narrow) float64 pipe; the rows are taken kThomasU at a time with all
+// their loads issued before the recurrence uses them.
+constexpr int kThomasU = 8;
+__global__ void __launch_bounds__(64) k_thomas_f64(const RadialRow* __restrict__ rad, const double* __restrict__ tinv,
+                                                   const double* __restrict__ tcp, double* __restrict__ x, int nr,
+                                                   int nth, int mh) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= mh * nth) return;
+  const int m = t / nth;
+  const int l = t - m * nth;
+  double* X = x + (size_t)m * nr * 2 * nth + l;
+  const double* INV = tinv + (size_t)m * nr * nth + l;
+  const double* CP = tcp + (size_t)m * nr * nth + l;
+  const size_t st = 2 * (size_t)nth;
+  double dre = 0.0, dim = 0.0;
+  for (int i0 = 0; i0 < nr; i0 += kThomasU) {
+    double xr[kThomasU], xi[kThomasU], iv[kThomasU], sb[kThomasU];
+#pragma unroll
+    for (int u = 0; u < kThomasU; ++u) {
+      const int i = i0 + u;
+      if (i < nr) {
+        xr[u] = X[i * st];
+        xi[u] = X[i * st + nth];
+        iv[u] = INV[(size_t)i * nth];
+        sb[u] = rad[i].sub;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kThomasU; ++u) {
+      const int i = i0 + u;
+      if (i < nr) {
+        dre = (xr[u] - sb[u] * dre) * iv[u];
+        dim = (xi[u] - sb[u] * dim) * iv[u];
+        X[i * st] = dre;
+        X[i * st + nth] = dim;
+      }
+    }
+  }
+  for (int i1 = nr - 2; i1 >= 0; i1 -= kThomasU) {
+    double xr[kThomasU], xi[kThomasU], c[kThomasU];
+#pragma unroll
+    for (int u = 0; u < kThomasU; ++u) {
+      const int i = i1 - u;
+      if (i >= 0) {
+        c[u] = CP[(size_t)i * nth];
+        xr[u] = X[i * st];
+        xi[u] = X[i * st + nth];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kThomasU; ++u) {
+      const int i = i1 - u;
+      if (i >= 0) {
+        dre = xr[u] - c[u] * dre;
+        dim = xi[u] - c[u] * dim;
+        X[i * st] = dre;
+        X[i * st + nth] = dim;
+      }
+    }
   }
 }
 
@@ -207,7 +264,14 @@ cudaError_t face_gradients_f64(const Plan& p, const double* phi, double* gr, dou
 
 cudaError_t thomas_f64(const Plan& p, double* x, cudaStream_t s) {
   const int n = p.mh * p.nth;
-  k_thomas_f64<<<(n + 127) / 128, 128, 0, s>>>(p.d_rad, p.d_lam, p.d_outer, p.d_inner, x, p.cp, p.nr, p.nth, p.mh);
+  k_thomas_f64<<<(n + 63) / 64, 64, 0, s>>>(p.d_rad, p.d_tinv, p.d_tcp, x, p.nr, p.nth, p.mh);
+  return cudaGetLastError();
+}
+
+cudaError_t radial_factors_f64(const Plan& p, cudaStream_t s) {
+  const int n = p.mh * p.nth;
+  k_radial_factors_f64<<<(n + 127) / 128, 128, 0, s>>>(p.d_rad, p.d_lam, p.d_outer, p.d_inner, p.d_tinv, p.d_tcp,
+                                                      p.nr, p.nth, p.mh);
   return cudaGetLastError();
 }
 

@@ -217,6 +217,8 @@ struct Plan {
   double* d_HtWp = nullptr;       // parity grids: [mh][2][h][h] (H^T W)_m,p[l][j], h = nth/2, p = even/odd
   double* d_Hp = nullptr;         // parity grids: [mh][2][h][h] H_m,p[j][l]
   double* d_oshell = nullptr;     // [mh][j][j'] H_m diag(outer_m) (H^T W)_m (multipole only)
+  double* d_tinv = nullptr;       // [mh][nr][nth] 1/pivot of each (m,l) radial system (float64 plans)
+  double* d_tcp = nullptr;        // [mh][nr][nth] c' = sup/pivot of the same elimination
   FaceCoef* d_face_r = nullptr;   // [nr] radial face-gradient coefficients
   FaceCoef* d_face_t = nullptr;   // [nth] polar face-gradient coefficients
   int* d_err = nullptr;           // device status word
@@ -227,7 +229,6 @@ struct Plan {
   bool ws_owned = false;
   double* specA = nullptr;        // [mh][nr][2][nth]
   double* specB = nullptr;        // [mh][nr][2][nth]
-  double* cp = nullptr;           // [mh][nr][nth] Thomas forward coefficients
   double* shell = nullptr;        // [mh][1][2][nth] outer-shell spectrum
   double* shell2 = nullptr;       // [mh][1][2][nth]
 
@@ -360,6 +361,7 @@ cudaError_t gemm_parity_f64(const double* A, const double* B, double* C, int nb,
                             cudaStream_t s);
 // Radial Thomas solves for every (m,l), in place on x[m][i][c][l].
 cudaError_t thomas_f64(const Plan& p, double* x, cudaStream_t s);
+cudaError_t radial_factors_f64(const Plan& p, cudaStream_t s);   // d_tinv, d_tcp (plan set-up)
 // Local part of the finite-volume operator (all interior fluxes, Dirichlet outer term).
 cudaError_t stencil_f64(const Plan& p, const double* phi, double* out, cudaStream_t s);
 // Multipole outer term on the last shell: out[nr-1] += outer_coef * kappa(A_Omega) phi[nr-1].

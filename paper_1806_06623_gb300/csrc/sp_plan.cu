@@ -114,6 +114,8 @@ void free_tables(Plan* p) {
     cudaFree(p->d_kappa);
     cudaFree(p->d_outer);
     cudaFree(p->d_inner);
+    cudaFree(p->d_tinv);
+    cudaFree(p->d_tcp);
     cudaFree(p->d_ishell);
     cudaFree(p->d_HtW);
     cudaFree(p->d_H);
@@ -555,9 +557,8 @@ namespace sp {
 size_t workspace_bytes(const Plan& p) {
   if (p.mixed) return mixed_workspace_bytes(p);
   const size_t spec = sizeof(double) * (size_t)p.mh * p.nr * 2 * p.nth;
-  const size_t cpb = sizeof(double) * (size_t)p.mh * p.nr * p.nth;
   const size_t shell = sizeof(double) * (size_t)p.mh * 2 * p.nth;
-  return align256(spec) * 2 + align256(cpb) + align256(shell) * 2;
+  return align256(spec) * 2 + align256(shell) * 2;
 }
 
 void bind_workspace(Plan& p, void* base) {
@@ -567,14 +568,11 @@ void bind_workspace(Plan& p, void* base) {
     return;
   }
   const size_t spec = align256(sizeof(double) * (size_t)p.mh * p.nr * 2 * p.nth);
-  const size_t cpb = align256(sizeof(double) * (size_t)p.mh * p.nr * p.nth);
   const size_t shell = align256(sizeof(double) * (size_t)p.mh * 2 * p.nth);
   p.specA = reinterpret_cast<double*>(c);
   c += spec;
   p.specB = reinterpret_cast<double*>(c);
   c += spec;
-  p.cp = reinterpret_cast<double*>(c);
-  c += cpb;
   p.shell = reinterpret_cast<double*>(c);
   c += shell;
   p.shell2 = reinterpret_cast<double*>(c);
@@ -815,6 +813,15 @@ int sp_plan_create_ex(const sp_plan_desc* desc, void* stream, sp_plan** out) {
       if (cudaMalloc(&p->d_ishell, sizeof(double) * mat) != cudaSuccess) { st = SP_ERR_OOM; break; }
       if ((st = launch_status(sp::shell_operator_f64(*p, p->d_inner, p->d_ishell, s)))) break;
     }
+    if (precision == SP_FP64) {
+      const size_t rad_tab = (size_t)mh * nr * nth;
+      if (cudaMalloc(&p->d_tinv, sizeof(double) * rad_tab) != cudaSuccess ||
+          cudaMalloc(&p->d_tcp, sizeof(double) * rad_tab) != cudaSuccess) {
+        st = SP_ERR_OOM;
+        break;
+      }
+      if ((st = launch_status(sp::radial_factors_f64(*p, s)))) break;
+    }
     if (precision != SP_FP64 && (st = sp::mixed_create_tables(*p, s))) break;
     // the float-float residual's floor above the tolerance: float64 iterate and residual
     if (precision != SP_FP64) p->mixed->resid64 = sp::mixed_floor(*p, false) > tol;
@@ -844,7 +851,7 @@ int sp_plan_clone(const sp_plan* src_plan, sp_plan** out) {
   c->ws = nullptr;
   c->ws_bytes = 0;
   c->ws_owned = false;
-  c->specA = c->specB = c->cp = c->shell = c->shell2 = nullptr;
+  c->specA = c->specB = c->shell = c->shell2 = nullptr;
   c->d_rho_io = c->d_phi_io = nullptr;
   c->h_red = nullptr;
   c->h_red_dev = nullptr;
@@ -1189,6 +1196,7 @@ namespace sp {
 size_t plan_table_bytes(const Plan& p) {
   const size_t tab = (size_t)p.mh * p.nth;
   size_t b = ((p.d_oshell ? 3 : 2) + (p.d_ishell ? 1 : 0) + (p.d_HtWp ? 1 : 0)) * tab * p.nth * sizeof(double) +
+             (p.d_tinv ? 2 * (size_t)p.mh * p.nr * p.nth * sizeof(double) : 0) +
              4 * tab * sizeof(double) +
              (size_t)p.nr * sizeof(RadialRow) +
              (size_t)p.nth * sizeof(ThetaRow) + 2 * (size_t)p.nphi * (sizeof(double) + sizeof(float)) + tab * sizeof(double);
