@@ -105,9 +105,13 @@ __device__ __forceinline__ void st_shared_v2(uint32_t addr, uint32_t a, uint32_t
 
 // Round-to-nearest-even of a finite float to bf16 with integer operations (faster than
 // the conversion unit here), returned as float bits with the low half zero.
-__device__ __forceinline__ uint32_t bf16_rn_bits(float v) {
-  const uint32_t u = __float_as_uint(v);
-  return (u + 0x7FFFu + ((u >> 16) & 1u)) & 0xFFFF0000u;
+// Two float32 values rounded to nearest-even bf16 and packed, `lo` in bits 0-15: one
+// conversion instruction, for finite values the same words as the integer form
+// (u + 0x7FFF + ((u >> 16) & 1)) >> 16.
+__device__ __forceinline__ uint32_t bf16x2_rn(float lo, float hi) {
+  uint32_t d;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
 }
 
 // Bulk prefetch of [p, p + bytes) into L2 (16-byte aligned address and size).
@@ -436,20 +440,28 @@ __device__ __forceinline__ void tc_gemm_split_body(const Maps& maps, const Param
         // 16-byte chunk kc4/2 of row r sits at chunk (kc4/2) ^ (r mod 8) of the 128-byte row
         const uint32_t off = 2048u * (uint32_t)u;
         const float x[4] = {cur[u].x, cur[u].y, cur[u].z, cur[u].w};
-        uint32_t h[3][4];
+        float v[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const float v = (kfull || k + e < prm.K) ? x[e] : 0.f;
-          h[0][e] = bf16_rn_bits(v);
-          const float r1 = __fsub_rn(v, __uint_as_float(h[0][e]));   // exact, <= 16 significant bits
-          h[1][e] = bf16_rn_bits(r1);
-          // r1 - x1 is exact with at most 8 significant bits: already a bf16 value
-          if (NP == 3) h[2][e] = __float_as_uint(__fsub_rn(r1, __uint_as_float(h[1][e])));
+        for (int e = 0; e < 4; ++e) v[e] = (kfull || k + e < prm.K) ? x[e] : 0.f;
+        // planes in pairs of elements: bf16 words of (e, e+1) packed by one conversion,
+        // unpacked to float to form the exact remainder (<= 16 significant bits), whose
+        // rounding is the second plane; the second remainder (<= 8 bits) is already bf16
+        uint32_t w[3][2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const float a = v[2 * q], b = v[2 * q + 1];
+          w[0][q] = bf16x2_rn(a, b);
+          const float ra = __fsub_rn(a, __uint_as_float(w[0][q] << 16));
+          const float rb = __fsub_rn(b, __uint_as_float(w[0][q] & 0xFFFF0000u));
+          w[1][q] = bf16x2_rn(ra, rb);
+          if (NP == 3) {
+            const float sa = __fsub_rn(ra, __uint_as_float(w[1][q] << 16));
+            const float sb = __fsub_rn(rb, __uint_as_float(w[1][q] & 0xFFFF0000u));
+            w[2][q] = __byte_perm(__float_as_uint(sa), __float_as_uint(sb), 0x7632);
+          }
         }
 #pragma unroll
-        for (int pl = 0; pl < NP; ++pl)
-          st_shared_v2(bst + (uint32_t)pl * kPlaneBytes + off, __byte_perm(h[pl][0], h[pl][1], 0x7632),
-                       __byte_perm(h[pl][2], h[pl][3], 0x7632));
+        for (int pl = 0; pl < NP; ++pl) st_shared_v2(bst + (uint32_t)pl * kPlaneBytes + off, w[pl][0], w[pl][1]);
       }
       fence_proxy_async_smem();
       mbar_arrive(smem_u32(&bar_full[st]));
