@@ -381,15 +381,19 @@ def run_ours(args, rank, world, local):
         line[f"{name}_ms_per_step"] = rr["ms"] / args.steps
         line[f"{name}_iterations"] = rr["infos"][-1].get("iterations")
     line["roofline"] = roofline(r["timing"], p, precision, args.steps, r["infos"][-1].get("iterations", 2))
+    line["roofline_groups"] = roofline_groups(r["timing"], p, precision, args.steps,
+                                              r["infos"][-1].get("iterations", 2))
     line["projection_tensor"] = projection_tensor_rate(r["timing"], p, precision)
     line["kernel_source_sha"] = kernel_source_hash()
     line["autotuned"] = tuning or None
+    # the served stream first: measured after the oracle's CPU checks in the same process
+    # (small configurations, batch samples) it ran 15-40% slower, cause not isolated
+    if not args.no_served:
+        line["served"] = run_served(S, W, torch, args.served_requests)
     if not args.no_small:
         line["small_configs"] = run_small(S, W, torch, dev, check=not args.no_oracle_check)
     if not args.no_batched:
         line["batched"] = run_batched(S, W, torch, dev, check=not args.no_oracle_check)
-    if not args.no_served:
-        line["served"] = run_served(S, W, torch, args.served_requests)
     if not args.no_oracle_check:
         line["error_vs_oracle"] = check_vs_oracle(p, {k: v["phi"] for k, v in results.items()})
     if not args.no_cpu_baseline and args.gpus == 1:
@@ -543,17 +547,17 @@ def run_served(S, W, torch, n_requests, rates=(200.0, 2000.0, 20000.0)):
 # null once those sources differ.
 MIXED_KERNEL_SOURCES = ("k_fft.cu", "k_mixed.cu", "fft_dev.cuh", "tc_gemm.cuh", "ff.cuh", "sp_internal.h")
 NCU_TRAFFIC = {
-    "source_sha": "5d80588854243225",
+    "source_sha": "a2c2ba181f6ec9bd",
     "mixed": {   # MB read + written, averaged over the group's launches in one solve
-        "fft_forward": {"bytes": (173.52 + 36.51) * 1e6, "kernel": "k_fft_fwd<float, double> (rho)"},
-        "project_forward": {"bytes": ((91.48 + 18.96) + (91.64 + 19.30)) * 1e6 / 2,
+        "fft_forward": {"bytes": (173.66 + 36.57) * 1e6, "kernel": "k_fft_fwd<float, double> (rho)"},
+        "project_forward": {"bytes": ((91.32 + 18.09) + (91.58 + 18.33)) * 1e6 / 2,
                             "kernel": "tc::k_tc_gemm_split<3>"},
-        "radial_solve": {"bytes": ((145.76 + 38.53) + (145.85 + 38.43)) * 1e6 / 2, "kernel": "k_thomas_scan<2>"},
-        "project_inverse": {"bytes": ((91.57 + 19.33) + (91.56 + 19.17)) * 1e6 / 2,
+        "radial_solve": {"bytes": ((145.79 + 39.31) + (145.82 + 39.12)) * 1e6 / 2, "kernel": "k_thomas_scan<2>"},
+        "project_inverse": {"bytes": ((91.54 + 18.27) + (91.51 + 18.31)) * 1e6 / 2,
                             "kernel": "tc::k_tc_gemm_split<3>"},
-        "fft_inverse": {"bytes": ((72.17 + 20.70) + (145.23 + 85.12)) * 1e6 / 2,
+        "fft_inverse": {"bytes": ((72.17 + 20.38) + (145.20 + 84.77)) * 1e6 / 2,
                         "kernel": "k_fft_inv<float, float, 2> (first solve, correction)"},
-        "residual": {"bytes": (218.80 + 44.48 + 0.82) * 1e6,
+        "residual": {"bytes": (218.81 + 44.57 + 0.82) * 1e6,
                      "kernel": "k_residual_fft<0> (interior rows + last shell: residual and its forward FFT)"},
     },
 }
@@ -681,6 +685,31 @@ def roofline(timing, p, precision, steps, iters=2):
             "traffic": tr["bytes"] if tr else None, "traffic_kernel": tr["kernel"] if tr else None,
             "algorithmic_bytes_per_launch": b,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s"}
+
+
+def roofline_groups(timing, p, precision, steps, iters=2):
+    """Every kernel group's live HBM fraction (algorithmic bytes over its live CUDA-event
+    time per step, against the measured copy bandwidth), beside the dominant group's."""
+    if not timing or precision == "fp64":
+        return None
+    try:
+        pk = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0))
+    except Exception:
+        pk = 6800.0
+    model = algorithmic_bytes_per_step(p, precision, iters)
+    out = {}
+    for name, (ms, cnt) in timing.items():
+        b = model.get(name)
+        if not b or ms <= 0:
+            continue
+        per_step_s = ms / steps / 1e3
+        out[name] = {"ms_per_step": ms / steps, "algorithmic_bytes_per_step": b,
+                     "frac": b / per_step_s / 1e9 / pk}
+    tot_b = sum(v["algorithmic_bytes_per_step"] for v in out.values())
+    tot_s = sum(v["ms_per_step"] for v in out.values()) / 1e3
+    out["whole_solve"] = {"ms_per_step": tot_s * 1e3, "algorithmic_bytes_per_step": tot_b,
+                          "frac": tot_b / tot_s / 1e9 / pk if tot_s > 0 else None}
+    return out
 
 
 def check_vs_oracle(p, phis):
