@@ -59,6 +59,11 @@ CASES = [
     (20, 16, 80, "log", 0.0, 0),       # radix 4 x 4 x 5
     (33, 12, 360, "rand", 0.1, 1),     # radix 4 x 2 x 3 x 3 x 5 (floor still below 1e-10)
     (7, 5, 25, "uniform", 0.0, 0),     # odd Nphi, radix 5 x 5
+    # Nphi = 256 with even Ntheta: the residual fused with its forward FFT
+    (40, 34, 256, "rand", 0.1, 0),     # partial 32-line theta block, inner zero-flux face
+    (24, 6, 256, "log", 0.0, 1),       # Dirichlet (no shell chain), one short block per row
+    (2, 64, 256, "uniform", 0.0, 0),   # two shells: the interior rows and the last shell
+    (21, 5, 256, "uniform", 0.0, 0),   # odd Ntheta: the separate residual and FFT
 ]
 
 
