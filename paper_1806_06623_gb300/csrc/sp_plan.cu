@@ -300,6 +300,8 @@ int mixed_issue_read(Plan* p, cudaStream_t s, MixedRun& R) {
 
 namespace {
 
+// Phase A ends with the copy of the device status word too, so that a solve which stops
+// after it (the usual case) returns without another kernel or synchronisation.
 int phase_a_direct(Plan* p, const double* rho, double* phi, cudaStream_t s, MixedRun& R) {
   int st;
   if ((st = mixed_start(p, rho, phi, s))) return st;
@@ -308,6 +310,8 @@ int phase_a_direct(Plan* p, const double* rho, double* phi, cudaStream_t s, Mixe
     if ((st = mixed_correct(p, rho, phi, s))) return st;
     if ((st = mixed_issue_read(p, s, R))) return st;
   }
+  SP_CUDA(post_words(reinterpret_cast<const unsigned int*>(p->d_err), p->h_red_dev + kRedErrWord, 1, s));
+  ++p->launches;
   return SP_OK;
 }
 
@@ -523,12 +527,16 @@ int solve_mixed(Plan* p, const double* rho, double* phi, cudaStream_t s, sp_solv
   int k = p->max_iter >= 1 ? 2 : 1;
   SP_CUDA(cudaStreamSynchronize(s));
   sp::mixed_decide(p, R);
+  bool more = false;   // kernels queued after phase A (its status word copy is then stale)
   for (; k <= p->max_iter && !R.done; ++k) {
     if ((st = sp::mixed_correct(p, rho, phi, s))) return st;
     if ((st = sp::mixed_issue_read(p, s, R))) return st;
+    more = true;
     SP_CUDA(cudaStreamSynchronize(s));
     sp::mixed_decide(p, R);
   }
+  // stopped after phase A with the output already in float64: its status word is current
+  if (!more && p->phi64_written == phi) return sp::mixed_finish_status(p, R, info);
   return sp::mixed_finish(p, phi, s, R, info);
 }
 
