@@ -163,6 +163,7 @@ extern "C" int sp_solve_batched(sp_plan* const* plans, const double* const* rho,
     }
   }
   // refinement rounds
+  std::vector<char> more(n, 0);   // corrections queued after phase A (its status copy then stale)
   std::vector<int> active;
   for (int i = 0; i < n && !ragged; ++i)
     if (P[i]->mixed && !status[i]) active.push_back(i);
@@ -177,14 +178,17 @@ extern "C" int sp_solve_batched(sp_plan* const* plans, const double* const* rho,
     for (int i : next) {
       status[i] = sp::mixed_correct(P[i], rho[i], phi[i], stream_of(i));
       if (!status[i]) status[i] = sp::mixed_issue_read(P[i], stream_of(i), runs[i]);
+      more[i] = 1;
     }
     active.clear();
     for (int i : next)
       if (!status[i]) active.push_back(i);
   }
-  // float-float iterates -> float64 results
+  // float-float iterates -> float64 results (not for instances that stopped after phase A
+  // with the float64 output written: its status word copy is current)
   for (int i = 0; i < n && !ragged; ++i)
-    if (P[i]->mixed && !status[i]) status[i] = sp::mixed_finish_issue(P[i], phi[i], stream_of(i));
+    if (P[i]->mixed && !status[i] && (more[i] || P[i]->phi64_written != phi[i]))
+      status[i] = sp::mixed_finish_issue(P[i], phi[i], stream_of(i));
   bool any_mixed = false;
   for (int i = 0; i < n; ++i) any_mixed = any_mixed || P[i]->mixed;
   if (any_mixed)
