@@ -253,7 +253,8 @@ struct Plan {
   const double* phi64_written = nullptr;   // output already holding the current iterate in float64
   // CUDA graphs of phase A of a mixed solve (first low-precision solve + first correction
   // with their host reads), captured on a private stream, each for one (rho, phi,
-  // workspace); two are kept, so that callers alternating two buffer pairs replay both
+  // workspace); eight are kept, so that callers alternating buffer pairs (the pipelined
+  // host path) or the solve server's slots (each with its own buffers) replay theirs
   bool graphs = true;
   bool phase_a_warm = false;      // one direct phase A ran (attributes set, workspace bound)
   cudaStream_t cap_stream = nullptr;
@@ -265,7 +266,7 @@ struct Plan {
     long long launches = 0;
     int pending = 0;
   };
-  static constexpr int kPhaseGraphs = 2;
+  static constexpr int kPhaseGraphs = 8;
   PhaseGraph ga[kPhaseGraphs];
   int ga_victim = 0;              // the entry the next capture replaces when both are taken
   // side stream (high priority) and fork/join events: the multipole shell term of the

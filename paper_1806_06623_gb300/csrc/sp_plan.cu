@@ -908,12 +908,14 @@ int sp_plan_set_workspace(sp_plan* plan, void* dev, size_t bytes) {
   if (p->ws_owned) {
     cudaDeviceSynchronize();
     cudaFree(p->ws);
+    sp::drop_phase_graph(*p);   // graphs captured on the freed workspace
   }
+  // graphs are keyed by (rho, phi, workspace): those of a caller-owned workspace stay for
+  // when it is bound again (the layout depends on the plan's shape only)
   p->ws = dev;
   p->ws_bytes = bytes;
   p->ws_owned = false;
   sp::bind_workspace(*p, dev);
-  sp::drop_phase_graph(*p);
   return SP_OK;
 }
 

@@ -406,10 +406,9 @@ void sp_server::worker(int slot) {
     sp_plan* master = res.master;
     const size_t clone_bytes = res.clone_bytes;
     lock.unlock();
-    // ---- run on this slot's stream
-    // slots launch kernel by kernel: a graph capture on one slot's thread while another
-    // slot's thread allocates or synchronises would make that thread's call fail
-    if (st == SP_OK && !plan && (st = sp_plan_clone(master, &plan)) == SP_OK) sp_plan_set_graphs(plan, 0);
+    // ---- run on this slot's stream (a clone replays the phase-A graph it captured for
+    // this slot's buffers; a capture that fails leaves that clone launching directly)
+    if (st == SP_OK && !plan) st = sp_plan_clone(master, &plan);
     // the plan runs in this slot's workspace (grown to the largest grid the slot has run),
     // so a clone allocates no workspace of its own and reusing one costs a pointer rebind
     if (st == SP_OK) {

@@ -253,6 +253,16 @@ def test_graph_replay_equals_direct(S, prec_name):
     plan.solve(rho_p, out_a)
     torch.cuda.synchronize()
     assert torch.equal(out_a, ref_p)
+    # caller-owned workspaces bound in turn (as the solve server's slots do): each keeps
+    # its graph, and results stay bitwise
+    ws2 = torch.empty_like(ws)
+    for w in (ws2, ws, ws2, ws):
+        S.sp_plan_set_workspace(plan._h, w)
+        out_a.zero_()
+        plan.solve(rho_p, out_a)
+        plan.solve(rho_q, out_b)
+        torch.cuda.synchronize()
+        assert torch.equal(out_a, ref_p) and torch.equal(out_b, ref_q)
 
 
 @pytest.mark.parametrize("prec_name", ["fp64", "x6"])
