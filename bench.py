@@ -562,17 +562,17 @@ def run_served(S, W, torch, n_requests, rates=(200.0, 2000.0, 20000.0)):
 # null once those sources differ.
 MIXED_KERNEL_SOURCES = ("k_fft.cu", "k_mixed.cu", "fft_dev.cuh", "tc_gemm.cuh", "ff.cuh", "sp_internal.h")
 NCU_TRAFFIC = {
-    "source_sha": "a2c2ba181f6ec9bd",
+    "source_sha": "e1a8922ead3cec1b",
     "mixed": {   # MB read + written, averaged over the group's launches in one solve
-        "fft_forward": {"bytes": (173.66 + 36.57) * 1e6, "kernel": "k_fft_fwd<float, double> (rho)"},
-        "project_forward": {"bytes": ((91.32 + 18.09) + (91.58 + 18.33)) * 1e6 / 2,
+        "fft_forward": {"bytes": (173.51 + 36.55) * 1e6, "kernel": "k_fft_fwd<float, double> (rho)"},
+        "project_forward": {"bytes": ((91.33 + 18.09) + (91.53 + 18.43)) * 1e6 / 2,
                             "kernel": "tc::k_tc_gemm_split<3>"},
-        "radial_solve": {"bytes": ((145.79 + 39.31) + (145.82 + 39.12)) * 1e6 / 2, "kernel": "k_thomas_scan<2>"},
-        "project_inverse": {"bytes": ((91.54 + 18.27) + (91.51 + 18.31)) * 1e6 / 2,
+        "radial_solve": {"bytes": ((145.80 + 38.13) + (145.79 + 38.98)) * 1e6 / 2, "kernel": "k_thomas_scan<2>"},
+        "project_inverse": {"bytes": ((91.49 + 18.27) + (91.50 + 18.29)) * 1e6 / 2,
                             "kernel": "tc::k_tc_gemm_split<3>"},
-        "fft_inverse": {"bytes": ((72.17 + 20.38) + (145.20 + 84.77)) * 1e6 / 2,
+        "fft_inverse": {"bytes": ((72.17 + 20.33) + (145.21 + 84.91)) * 1e6 / 2,
                         "kernel": "k_fft_inv<float, float, 2> (first solve, correction)"},
-        "residual": {"bytes": (218.81 + 44.57 + 0.82) * 1e6,
+        "residual": {"bytes": (218.81 + 44.66 + 0.82) * 1e6,
                      "kernel": "k_residual_fft<0> (interior rows + last shell: residual and its forward FFT)"},
     },
 }
