@@ -508,10 +508,11 @@ cudaError_t fft_inverse_f64(const Plan& p, const double* spec, int nrs, double* 
 }
 
 // How many CTAs ahead the forward transform prefetches its input: one resident wave, but
-// no more than ~32 MB of input in flight towards L2 (a farther prefetch is evicted again
-// before its CTA reads it: 190 against 144 MB read for the float64 source at 608 CTAs).
+// no more than ~16 MB of input in flight towards L2 (a farther prefetch is evicted again
+// before its CTA reads it: the float64 source of 144 MB was read as 190 MB with the
+// full wave of 608 CTAs ahead, 174 MB at 32 MB ahead, 149 MB at 16 MB).
 static int prefetch_ahead(int resident, size_t bytes_per_cta) {
-  const size_t cap = (size_t(32) << 20) / (bytes_per_cta ? bytes_per_cta : 1);
+  const size_t cap = (size_t(16) << 20) / (bytes_per_cta ? bytes_per_cta : 1);
   return (int)std::min<size_t>((size_t)resident, cap);
 }
 
