@@ -562,17 +562,17 @@ def run_served(S, W, torch, n_requests, rates=(200.0, 2000.0, 20000.0)):
 # null once those sources differ.
 MIXED_KERNEL_SOURCES = ("k_fft.cu", "k_mixed.cu", "fft_dev.cuh", "tc_gemm.cuh", "ff.cuh", "sp_internal.h")
 NCU_TRAFFIC = {
-    "source_sha": "e1a8922ead3cec1b",
+    "source_sha": "4138198f28cdf977",
     "mixed": {   # MB read + written, averaged over the group's launches in one solve
-        "fft_forward": {"bytes": (173.51 + 36.55) * 1e6, "kernel": "k_fft_fwd<float, double> (rho)"},
-        "project_forward": {"bytes": ((91.33 + 18.09) + (91.53 + 18.43)) * 1e6 / 2,
+        "fft_forward": {"bytes": (149.13 + 36.45) * 1e6, "kernel": "k_fft_fwd<float, double> (rho)"},
+        "project_forward": {"bytes": ((91.34 + 18.06) + (91.52 + 18.38)) * 1e6 / 2,
                             "kernel": "tc::k_tc_gemm_split<3>"},
-        "radial_solve": {"bytes": ((145.80 + 38.13) + (145.79 + 38.98)) * 1e6 / 2, "kernel": "k_thomas_scan<2>"},
-        "project_inverse": {"bytes": ((91.49 + 18.27) + (91.50 + 18.29)) * 1e6 / 2,
+        "radial_solve": {"bytes": ((145.78 + 39.22) + (145.83 + 39.14)) * 1e6 / 2, "kernel": "k_thomas_scan<2>"},
+        "project_inverse": {"bytes": ((91.50 + 18.26) + (91.51 + 18.25)) * 1e6 / 2,
                             "kernel": "tc::k_tc_gemm_split<3>"},
-        "fft_inverse": {"bytes": ((72.17 + 20.33) + (145.21 + 84.91)) * 1e6 / 2,
+        "fft_inverse": {"bytes": ((72.17 + 20.32) + (145.20 + 84.86)) * 1e6 / 2,
                         "kernel": "k_fft_inv<float, float, 2> (first solve, correction)"},
-        "residual": {"bytes": (218.81 + 44.66 + 0.82) * 1e6,
+        "residual": {"bytes": (218.80 + 44.63 + 0.82) * 1e6,
                      "kernel": "k_residual_fft<0> (interior rows + last shell: residual and its forward FFT)"},
     },
 }
