@@ -153,6 +153,10 @@ __device__ __forceinline__ void fft_fwd_body(const Tin* __restrict__ in, int nli
 }
 
 enum InvOut { kInvWrite = 0, kInvAccumulate = 1, kInvPairUpdate = 2, kInvF64Update = 3 };
+// spectrum rows a warp has in flight in the inverse transform's load (float: 16; double:
+// 8, where 16 would spill)
+template <typename T>
+constexpr int inv_rows() { return sizeof(T) == 4 ? 16 : 8; }
 
 // Inverse: half spectra spec[m][i][c][j] (row stride Ntheta) of lines [line0, line0+nl)
 // -> real lines:
@@ -211,11 +215,12 @@ __device__ __forceinline__ void fft_inv_body(const T* __restrict__ spec, int nli
       j = g - i * nth;
     }
     // Z[m] = G_A[m] + i G_B[m] (even lane writes), Z[n-m] = conj G_A[m] + i conj G_B[m] (odd lane);
-    // eight m-rows are loaded before any is consumed
-    for (int m0 = warp; m0 < mh; m0 += 8 * kWarps) {
-      CT vv[8];
+    // inv_rows m-rows are loaded before any is consumed
+    constexpr int kRows = inv_rows<T>();
+    for (int m0 = warp; m0 < mh; m0 += kRows * kWarps) {
+      CT vv[kRows];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
+      for (int u = 0; u < kRows; ++u) {
         const int m = m0 + u * kWarps;
         vv[u].x = T(0);
         vv[u].y = T(0);
@@ -226,7 +231,7 @@ __device__ __forceinline__ void fft_inv_body(const T* __restrict__ spec, int nli
         }
       }
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
+      for (int u = 0; u < kRows; ++u) {
         const int m = m0 + u * kWarps;
         const CT v = vv[u];
         CT o;
