@@ -562,17 +562,17 @@ def run_served(S, W, torch, n_requests, rates=(200.0, 2000.0, 20000.0)):
 # null once those sources differ.
 MIXED_KERNEL_SOURCES = ("k_fft.cu", "k_mixed.cu", "fft_dev.cuh", "tc_gemm.cuh", "ff.cuh", "sp_internal.h")
 NCU_TRAFFIC = {
-    "source_sha": "4138198f28cdf977",
+    "source_sha": "25bf8f80631ca02d",
     "mixed": {   # MB read + written, averaged over the group's launches in one solve
-        "fft_forward": {"bytes": (149.13 + 36.45) * 1e6, "kernel": "k_fft_fwd<float, double> (rho)"},
-        "project_forward": {"bytes": ((91.34 + 18.06) + (91.52 + 18.38)) * 1e6 / 2,
+        "fft_forward": {"bytes": (148.94 + 36.97) * 1e6, "kernel": "k_fft_fwd<float, double> (rho)"},
+        "project_forward": {"bytes": ((91.24 + 18.06) + (91.48 + 18.26)) * 1e6 / 2,
                             "kernel": "tc::k_tc_gemm_split<3>"},
-        "radial_solve": {"bytes": ((145.78 + 39.22) + (145.83 + 39.14)) * 1e6 / 2, "kernel": "k_thomas_scan<2>"},
-        "project_inverse": {"bytes": ((91.50 + 18.26) + (91.51 + 18.25)) * 1e6 / 2,
+        "radial_solve": {"bytes": ((145.78 + 39.36) + (145.83 + 39.19)) * 1e6 / 2, "kernel": "k_thomas_scan<2>"},
+        "project_inverse": {"bytes": ((91.39 + 18.23) + (91.35 + 18.23)) * 1e6 / 2,
                             "kernel": "tc::k_tc_gemm_split<3>"},
-        "fft_inverse": {"bytes": ((72.17 + 20.32) + (145.20 + 84.86)) * 1e6 / 2,
+        "fft_inverse": {"bytes": ((72.17 + 20.08) + (145.28 + 84.62)) * 1e6 / 2,
                         "kernel": "k_fft_inv<float, float, 2> (first solve, correction)"},
-        "residual": {"bytes": (218.80 + 44.63 + 0.82) * 1e6,
+        "residual": {"bytes": (218.86 + 44.34 + 0.82) * 1e6,
                      "kernel": "k_residual_fft<0> (interior rows + last shell: residual and its forward FFT)"},
     },
 }
