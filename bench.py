@@ -284,6 +284,32 @@ def run_ours(args, rank, world, local):
         results[name] = {"ms": tot_ms, "infos": infos, "launches": launches, "timing": timing, "clocks": ck,
                          "phi": phi.detach().cpu().numpy() if (rank == 0 and not args.no_oracle_check) else None}
 
+    # the acceleration on the faces (sp_face_gradients) of the solved potential: float64,
+    # reads Phi (8 B per zone) and writes the r, theta and phi face gradients (8 B per face)
+    face = None
+    if rank == 0:
+        fplan = plans.get("fp64", head)
+        g = fplan.face_gradients(phi)
+        torch.cuda.synchronize(dev)
+        reps = 10
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            g = fplan.face_gradients(phi)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        nbytes = 8 * (phi.numel() + sum(x.numel() for x in g))
+        try:
+            pk = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0))
+        except Exception:
+            pk = 6800.0
+        face = {"ms": ms, "algorithmic_bytes": nbytes, "frac": nbytes / (ms / 1e3) / 1e9 / pk,
+                "note": "float64 face gradients of Phi on the r, theta and phi faces (boundary faces through "
+                        "the outer and inner conditions), L2 not flushed between the 10 calls"}
+        del g
+
     # end-to-end through the host-buffer entry points (page-locked buffers, copies timed):
     # K solves in one pipelined call (the upload of step k+1 and the download of step k-1
     # overlap the solve of step k), and K single sp_solve_host calls (copy, solve, copy)
@@ -385,6 +411,8 @@ def run_ours(args, rank, world, local):
                                               r["infos"][-1].get("iterations", 2))
     line["projection_tensor"] = projection_tensor_rate(r["timing"], p, precision)
     line["kernel_source_sha"] = kernel_source_hash()
+    if face is not None:
+        line["face_gradients"] = face
     line["autotuned"] = tuning or None
     # the served stream first: measured after the oracle's CPU checks in the same process
     # (small configurations, batch samples) it ran 15-40% slower, cause not isolated
