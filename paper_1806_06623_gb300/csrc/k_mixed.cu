@@ -709,32 +709,59 @@ __global__ void __launch_bounds__(kResThreads) k_residual_ff(const double* __res
 
 // The float-float helpers on column pairs: paired float32 instructions (one instruction
 // per operation for both columns, each component rounded to nearest as in the scalar
-// forms, the operations in the same order).
+// forms, the operations in the same order).  No operand of a paired instruction is
+// negated: a - b is the fused (-1) b + a (one rounding, the same value), and where an
+// algorithm needs -x the helpers carry the negated quantity instead (round to nearest is
+// symmetric, so every value is exactly that of the form with the negation).
 __device__ __forceinline__ float2 f2s(float a) { return make_float2(a, a); }
-__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, neg2(b)); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2s(-1.f), a); }
 __device__ __forceinline__ void two_sum2(float2 a, float2 b, float2& s, float2& e) {
   s = add2(a, b);
   const float2 bb = sub2(s, a);
   e = add2(sub2(a, sub2(s, bb)), sub2(b, bb));
 }
+// two_sum2(a, -b): s = a - b and its exact error
+__device__ __forceinline__ void two_diff2(float2 a, float2 b, float2& s, float2& e) {
+  s = sub2(a, b);
+  const float2 bb = sub2(s, a);
+  e = sub2(sub2(a, sub2(s, bb)), add2(b, bb));
+}
+// Neighbour difference b - c of float-float values (LO = false: the error-free
+// difference of the high words).  The result is antisymmetric: the difference c - b is
+// exactly its negation.
 template <bool LO>
 __device__ __forceinline__ void ffd_diff2(float2 bh, float2 bl, float2 ch, float2 cl, float2& dh, float2& dl) {
   if (LO) {
     float2 e;
-    two_sum2(bh, neg2(ch), dh, e);
+    two_diff2(bh, ch, dh, e);
     dl = add2(e, sub2(bl, cl));
   } else {
-    two_sum2(bh, neg2(ch), dh, dl);
+    two_diff2(bh, ch, dh, dl);
   }
 }
-__device__ __forceinline__ void ffd_mul2(const ff& k, float2 dh, float2 dl, float2& p, float2& e) {
-  p = __fmul2_rn(f2s(k.hi), dh);
-  e = __ffma2_rn(f2s(k.hi), dh, neg2(p));
-  e = __ffma2_rn(f2s(k.hi), dl, e);
-  e = __ffma2_rn(f2s(k.lo), dh, e);
+// A float-float coefficient with its negation, each word broadcast to both columns.
+struct ffc2 {
+  float2 hi, nhi, nlo;
+};
+__device__ __forceinline__ ffc2 coef2(const ff& k) { return ffc2{f2s(k.hi), f2s(-k.hi), f2s(-k.lo)}; }
+// the coefficient -k
+__device__ __forceinline__ ffc2 ncoef2(const ff& k) { return ffc2{f2s(-k.hi), f2s(k.hi), f2s(k.lo)}; }
+// k (dh + dl) = p + e, returned as p and ne = -e
+__device__ __forceinline__ void ffd_mul2(const ffc2& k, float2 dh, float2 dl, float2& p, float2& ne) {
+  p = __fmul2_rn(k.hi, dh);
+  ne = __ffma2_rn(k.nhi, dh, p);
+  ne = __ffma2_rn(k.nhi, dl, ne);
+  ne = __ffma2_rn(k.nlo, dh, ne);
 }
+// Sum (ah, -nal) += (ph, -npe): the low word is carried negated.
+__device__ __forceinline__ void ffd_nacc2(float2& ah, float2& nal, float2 ph, float2 npe) {
+  float2 s, e;
+  two_sum2(ah, ph, s, e);
+  ah = s;
+  nal = sub2(nal, sub2(e, npe));
+}
+// (ah, al) += (ph, pe), both low words as they are
 __device__ __forceinline__ void ffd_acc2(float2& ah, float2& al, float2 ph, float2 pe) {
   float2 s, e;
   two_sum2(ah, ph, s, e);
@@ -742,53 +769,64 @@ __device__ __forceinline__ void ffd_acc2(float2& ah, float2& al, float2 ph, floa
   al = add2(al, add2(e, pe));
 }
 
-// residual_zone for the two columns of a pair at once.
+// 4 pi G rho - (sh - nsl) of both columns, rounded to float32: the float-float source
+// term (ff_mul, then fast two-sum), then the difference.
+__device__ __forceinline__ float2 residual_finish2(float2 sh, float2 nsl, double2 rv, const ffc2& fpg) {
+  const ff rx = d2ff_trunc(rv.x), ry = d2ff_trunc(rv.y);
+  const float2 rh = make_float2(rx.hi, ry.hi), rl = make_float2(rx.lo, ry.lo);
+  float2 sp, nse;
+  ffd_mul2(fpg, rh, rl, sp, nse);
+  const float2 svh = sub2(sp, nse);
+  const float2 nsvl = add2(nse, sub2(svh, sp));
+  float2 th_, tl;
+  two_diff2(svh, sh, th_, tl);
+  tl = add2(tl, sub2(nsl, nsvl));
+  return add2(th_, tl);
+}
+
+// residual_zone for the two columns of a pair at once.  (mh, ml) = Phi(i) - Phi(i-1) on
+// entry (read when i > 0) and Phi(i+1) - Phi(i) on exit (when i < Nr-1): the radial
+// difference is carried with its sign and the inner face's term takes the coefficient
+// -sub.
 template <bool LO>
 __device__ __forceinline__ float2 residual_zone2(float2 ch, float2 cl, float2& mh, float2& ml, bool has_im,
                                                  bool has_ip, float2 nh, float2 nl, bool has_jm, float2 jmh,
                                                  float2 jml, bool has_jp, float2 jph, float2 jpl, float2 qh, float2 ql,
                                                  float2 oh, float2 ol, const RadialRowFF& rr, const ThetaRowFF& ar,
                                                  double2 rv, const ff& four_pi_g) {
-  float2 dh, dl, p, e;
-  float2 sh = f2s(0.f), sl = f2s(0.f);
+  float2 dh, dl, p, ne;
+  float2 sh = f2s(0.f), nsl = f2s(0.f);
   if (has_im) {
-    ffd_mul2(rr.sub, mh, ml, p, e);
+    ffd_mul2(ncoef2(rr.sub), mh, ml, p, ne);
     sh = p;
-    sl = e;
+    nsl = ne;
   }
   if (has_ip) {
     ffd_diff2<LO>(nh, nl, ch, cl, dh, dl);
-    ffd_mul2(rr.sup, dh, dl, p, e);
-    ffd_acc2(sh, sl, p, e);
-    mh = neg2(dh);
-    ml = neg2(dl);
+    ffd_mul2(coef2(rr.sup), dh, dl, p, ne);
+    ffd_nacc2(sh, nsl, p, ne);
+    mh = dh;
+    ml = dl;
   }
   if (has_jm) {
     ffd_diff2<LO>(jmh, jml, ch, cl, dh, dl);
-    ffd_mul2(ar.tm, dh, dl, p, e);
-    ffd_acc2(sh, sl, p, e);
+    ffd_mul2(coef2(ar.tm), dh, dl, p, ne);
+    ffd_nacc2(sh, nsl, p, ne);
   }
   if (has_jp) {
     ffd_diff2<LO>(jph, jpl, ch, cl, dh, dl);
-    ffd_mul2(ar.tp, dh, dl, p, e);
-    ffd_acc2(sh, sl, p, e);
+    ffd_mul2(coef2(ar.tp), dh, dl, p, ne);
+    ffd_nacc2(sh, nsl, p, ne);
   }
-  ffd_mul2(ar.sphi, qh, ql, p, e);
-  ffd_acc2(sh, sl, p, e);
-  if (!has_ip) ffd_acc2(sh, sl, oh, ol);
-  // 4 pi G rho as a float-float pair per column (ff_mul, then fast two-sum)
-  const ff rx = d2ff_trunc(rv.x), ry = d2ff_trunc(rv.y);
-  const float2 rh = make_float2(rx.hi, ry.hi), rl = make_float2(rx.lo, ry.lo);
-  const float2 sp = __fmul2_rn(f2s(four_pi_g.hi), rh);
-  float2 se = __ffma2_rn(f2s(four_pi_g.hi), rh, neg2(sp));
-  se = __ffma2_rn(f2s(four_pi_g.hi), rl, se);
-  se = __ffma2_rn(f2s(four_pi_g.lo), rh, se);
-  const float2 svh = add2(sp, se);
-  const float2 svl = sub2(se, sub2(svh, sp));
-  float2 th_, tl;
-  two_sum2(svh, neg2(sh), th_, tl);
-  tl = add2(tl, sub2(svl, sl));
-  return add2(th_, tl);
+  ffd_mul2(coef2(ar.sphi), qh, ql, p, ne);
+  ffd_nacc2(sh, nsl, p, ne);
+  if (!has_ip) {
+    float2 s, e;
+    two_sum2(sh, oh, s, e);
+    sh = s;
+    nsl = sub2(nsl, add2(e, ol));
+  }
+  return residual_finish2(sh, nsl, rv, coef2(four_pi_g));
 }
 
 // The same for an even number of phi zones, two adjacent columns (k, k+1) per thread:
@@ -829,8 +867,8 @@ __device__ __forceinline__ void residual_ff2_body(const double* __restrict__ rho
   const ThetaRowFF* angp = ang + (size_t)i0 * nth + j;
   const float2 z2 = make_float2(0.f, 0.f);
   float2 ch = hp[0], cl = LO ? lp[0] : z2;
-  float2 m2h = z2, m2l = z2;   // Phi(i-1) - Phi(i) of both columns
-  if (i0 > 0) ffd_diff2<LO>(hp[-(ptrdiff_t)sh2], LO ? lp[-(ptrdiff_t)sh2] : z2, ch, cl, m2h, m2l);
+  float2 m2h = z2, m2l = z2;   // Phi(i) - Phi(i-1) of both columns
+  if (i0 > 0) ffd_diff2<LO>(ch, cl, hp[-(ptrdiff_t)sh2], LO ? lp[-(ptrdiff_t)sh2] : z2, m2h, m2l);
   for (int i = i0; i < i1; ++i) {
     float* ev = line[i & 1][0][0];   // high words of the even and odd columns
     float* od = line[i & 1][0][1];
@@ -927,54 +965,50 @@ __global__ void __launch_bounds__(kResThreads) k_residual_ff2_rag(const ResArgs*
 // ---- The residual fused with its forward phi FFT (Nphi = 256, float-float iterate).
 //
 // residual_zone2 with the theta window carried instead of the radial one: the difference
-// Phi(j-1) - Phi(j) comes in (dmh, dml; the negated Phi(j+1) - Phi(j) of the previous
-// line, exactly), Phi(i-1) comes as values.  The terms are summed in the same order with
-// the same operations, so the residual is bitwise that of k_residual_ff2.
+// Phi(j) - Phi(j-1) comes in (dmh, dml; the Phi(j+1) - Phi(j) of the previous line) and
+// the lower polar face's term takes the coefficient -tm; Phi(i-1) comes as values.  The
+// terms are summed in the same order with the same operations, so the residual is
+// bitwise that of k_residual_ff2.
 template <bool LO>
 __device__ __forceinline__ float2 residual_zone2j(float2 ch, float2 cl, bool has_im, float2 imh, float2 iml,
                                                   bool has_ip, float2 nh, float2 nl, bool has_jm, float2& dmh,
                                                   float2& dml, bool has_jp, float2 jph, float2 jpl, float2 qh,
-                                                  float2 ql, float2 oh, float2 ol, const RadialRowFF& rr,
-                                                  const ThetaRowFF& ar, double2 rv, const ff& four_pi_g) {
-  float2 dh, dl, p, e;
-  float2 sh = f2s(0.f), sl = f2s(0.f);
+                                                  float2 ql, float2 oh, float2 ol, const ffc2& csub,
+                                                  const ffc2& csup, const ThetaRowFF& ar, double2 rv,
+                                                  const ffc2& fpg) {
+  float2 dh, dl, p, ne;
+  float2 sh = f2s(0.f), nsl = f2s(0.f);
   if (has_im) {
-    ffd_diff2<LO>(imh, iml, ch, cl, dh, dl);
-    ffd_mul2(rr.sub, dh, dl, p, e);
+    ffd_diff2<LO>(ch, cl, imh, iml, dh, dl);   // Phi(i) - Phi(i-1), the term's coefficient -sub
+    ffd_mul2(csub, dh, dl, p, ne);
     sh = p;
-    sl = e;
+    nsl = ne;
   }
   if (has_ip) {
     ffd_diff2<LO>(nh, nl, ch, cl, dh, dl);
-    ffd_mul2(rr.sup, dh, dl, p, e);
-    ffd_acc2(sh, sl, p, e);
+    ffd_mul2(csup, dh, dl, p, ne);
+    ffd_nacc2(sh, nsl, p, ne);
   }
   if (has_jm) {
-    ffd_mul2(ar.tm, dmh, dml, p, e);
-    ffd_acc2(sh, sl, p, e);
+    ffd_mul2(ncoef2(ar.tm), dmh, dml, p, ne);
+    ffd_nacc2(sh, nsl, p, ne);
   }
   if (has_jp) {
     ffd_diff2<LO>(jph, jpl, ch, cl, dh, dl);
-    ffd_mul2(ar.tp, dh, dl, p, e);
-    ffd_acc2(sh, sl, p, e);
-    dmh = neg2(dh);
-    dml = neg2(dl);
+    ffd_mul2(coef2(ar.tp), dh, dl, p, ne);
+    ffd_nacc2(sh, nsl, p, ne);
+    dmh = dh;
+    dml = dl;
   }
-  ffd_mul2(ar.sphi, qh, ql, p, e);
-  ffd_acc2(sh, sl, p, e);
-  if (!has_ip) ffd_acc2(sh, sl, oh, ol);
-  const ff rx = d2ff_trunc(rv.x), ry = d2ff_trunc(rv.y);
-  const float2 rh = make_float2(rx.hi, ry.hi), rl = make_float2(rx.lo, ry.lo);
-  const float2 sp = __fmul2_rn(f2s(four_pi_g.hi), rh);
-  float2 se = __ffma2_rn(f2s(four_pi_g.hi), rh, neg2(sp));
-  se = __ffma2_rn(f2s(four_pi_g.hi), rl, se);
-  se = __ffma2_rn(f2s(four_pi_g.lo), rh, se);
-  const float2 svh = add2(sp, se);
-  const float2 svl = sub2(se, sub2(svh, sp));
-  float2 th_, tl;
-  two_sum2(svh, neg2(sh), th_, tl);
-  tl = add2(tl, sub2(svl, sl));
-  return add2(th_, tl);
+  ffd_mul2(coef2(ar.sphi), qh, ql, p, ne);
+  ffd_nacc2(sh, nsl, p, ne);
+  if (!has_ip) {
+    float2 s, e;
+    two_sum2(sh, oh, s, e);
+    sh = s;
+    nsl = sub2(nsl, add2(e, ol));
+  }
+  return residual_finish2(sh, nsl, rv, fpg);
 }
 
 // One CTA per (radial row i, block of lpc consecutive j; even lpc <= 32): each half of the
@@ -1018,6 +1052,7 @@ __global__ void __launch_bounds__(256, 4) k_residual_fft(
   const bool has_im = i > 0, has_ip = i < nr - 1;
   const float2 z2 = make_float2(0.f, 0.f);
   const RadialRowFF rr = rad[i];
+  const ffc2 csub = ncoef2(rr.sub), csup = coef2(rr.sup), fpg = coef2(four_pi_g);
   const int k = 2 * t;                            // even column of the pair
   // pair pointers of line (i, j) at step 0
   int j = j0 + l0;
@@ -1030,7 +1065,7 @@ __global__ void __launch_bounds__(256, 4) k_residual_fft(
     if (LO) cl = lp[0];
     if (j > 0) {
       const float2 bh = hp[-(ptrdiff_t)(kRfN / 2)], bl = LO ? lp[-(ptrdiff_t)(kRfN / 2)] : z2;
-      ffd_diff2<LO>(bh, bl, ch, cl, dmh, dml);   // Phi(j-1) - Phi(j)
+      ffd_diff2<LO>(ch, cl, bh, bl, dmh, dml);   // Phi(j) - Phi(j-1)
     }
   }
   for (int st = 0; st < half; ++st) {
@@ -1085,7 +1120,7 @@ __global__ void __launch_bounds__(256, 4) k_residual_fft(
         outer_term(dirichlet, dir_coef, ch.y, cl.y, outer_shell, (size_t)j * kRfN + k + 1, oh.y, ol.y);
       }
       const float2 res = residual_zone2j<LO>(ch, cl, has_im, imh, iml, has_ip, nh, nl2, has_jm, dmh, dml, has_jp,
-                                             jph, jpl, qh, ql, oh, ol, rr, ar, rv, four_pi_g);
+                                             jph, jpl, qh, ql, oh, ol, csub, csup, ar, rv, fpg);
       // planar into the transform buffer: line l = l0 + st of pair l / 2
       const int l = l0 + st;
       *reinterpret_cast<float2*>(reinterpret_cast<float*>(buf + (l >> 1) * kPsInplace) + (l & 1) * kRfN + k) = res;

@@ -197,39 +197,63 @@ __global__ void __launch_bounds__(32 * kShellRows) k_shell_apply_rag(const Shell
   shell_apply_body(a.O, a.x, a.z, a.nth, b % a.gx, b / a.gx);
 }
 
-// Face gradients (minus the gravitational acceleration) of Eq. fin_vol3's fluxes: one
-// thread per cell writes the gradient on its inner radial face i, its lower polar face j
-// (and the pole face j = Ntheta after the last row) and its azimuthal face k+1/2.  The
-// outer radial face (index nr) holds on entry the multipole term O_m Phi_last computed by
-// the shell transforms (scaled here by 1/outer_coef), or is set from the Dirichlet
-// condition; the inner face (index 0) holds O_in Phi_first for a regular interior
-// (scaled by -1/inner_coef), else zero (inner_scale = 0).
-__global__ void __launch_bounds__(256) k_face_grad(const double* __restrict__ phi, double* __restrict__ gr,
-                                                   double* __restrict__ gt, double* __restrict__ gp,
-                                                   const FaceCoef* __restrict__ fr, const FaceCoef* __restrict__ ft,
-                                                   int nr, int nth, int nphi, int dirichlet, double outer_scale,
-                                                   double inner_scale) {
-  const size_t n = (size_t)nr * nth * nphi;
+// Face gradients (minus the gravitational acceleration) of Eq. fin_vol3's fluxes: a warp
+// per (i, j) line, its lanes over the azimuthal cells, writing the gradient on each cell's
+// inner radial face i, its lower polar face j (and the pole face j = Ntheta after the last
+// row) and its azimuthal face k+1/2.  The line's coefficient products are formed once,
+// so a cell costs three float64 differences and three products.  The outer radial face
+// (index nr) holds on entry the multipole term O_m Phi_last computed by the shell
+// transforms (scaled here by 1/outer_coef), or is set from the Dirichlet condition; the
+// inner face (index 0) holds O_in Phi_first for a regular interior (scaled by
+// -1/inner_coef), else it is zero (inner_scale = 0).
+constexpr int kFaceWarps = 8;
+constexpr int kFaceU = 4;   // cells per lane in flight
+__global__ void __launch_bounds__(32 * kFaceWarps) k_face_grad(const double* __restrict__ phi, double* __restrict__ gr,
+                                                               double* __restrict__ gt, double* __restrict__ gp,
+                                                               const FaceCoef* __restrict__ fr,
+                                                               const FaceCoef* __restrict__ ft, int nr, int nth,
+                                                               int nphi, int dirichlet, double outer_scale,
+                                                               double inner_scale) {
+  const int lane = threadIdx.x & 31;
+  const int lines = nr * nth;
   const size_t shell = (size_t)nth * nphi;
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
-    const int k = (int)(idx % nphi);
-    const size_t ij = idx / nphi;
-    const int j = (int)(ij % nth);
-    const int i = (int)(ij / nth);
-    const double c = phi[idx];
+  for (int ln = blockIdx.x * kFaceWarps + (threadIdx.x >> 5); ln < lines; ln += gridDim.x * kFaceWarps) {
+    const int i = ln / nth, j = ln - i * nth;
     const FaceCoef r = fr[i];
     const FaceCoef t = ft[j];
-    // inner face: zero flux, or (regular interior) O_in phi_first on entry, scaled
-    gr[idx] = i > 0 ? (c - phi[idx - shell]) * r.inv_d : gr[idx] * inner_scale;
-    if (i == nr - 1) {
-      double* o = gr + idx + shell;   // outer face
-      *o = dirichlet ? -c * outer_scale : *o * outer_scale;
+    const double ct = r.inv_c * t.inv_d, cp = r.inv_c * t.inv_c;
+    const size_t o = (size_t)ln * nphi;
+    const double* row = phi + o;
+    double* grl = gr + o;
+    double* gtl = gt + ((size_t)i * (nth + 1) + j) * nphi;
+    double* gpl = gp + o;
+    for (int k0 = lane; k0 < nphi; k0 += 32 * kFaceU) {
+      double c[kFaceU], cn[kFaceU], ci[kFaceU], cj[kFaceU];
+#pragma unroll
+      for (int u = 0; u < kFaceU; ++u) {
+        const int k = k0 + 32 * u;
+        if (k < nphi) {
+          c[u] = row[k];
+          cn[u] = row[k + 1 == nphi ? 0 : k + 1];
+          ci[u] = i > 0 ? row[(ptrdiff_t)k - (ptrdiff_t)shell] : (inner_scale != 0.0 ? grl[k] : 0.0);
+          cj[u] = j > 0 ? row[k - nphi] : 0.0;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kFaceU; ++u) {
+        const int k = k0 + 32 * u;
+        if (k >= nphi) continue;
+        // inner face: zero flux, or (regular interior) O_in phi_first on entry, scaled
+        grl[k] = i > 0 ? (c[u] - ci[u]) * r.inv_d : ci[u] * inner_scale;
+        if (i == nr - 1) {
+          double* of = grl + shell + k;   // outer face
+          *of = dirichlet ? -c[u] * outer_scale : *of * outer_scale;
+        }
+        gtl[k] = j > 0 ? (c[u] - cj[u]) * ct : 0.0;
+        if (j == nth - 1) gtl[nphi + k] = 0.0;
+        gpl[k] = (cn[u] - c[u]) * cp;
+      }
     }
-    const size_t tix = ((size_t)i * (nth + 1) + j) * nphi + k;
-    gt[tix] = j > 0 ? (c - phi[idx - nphi]) * r.inv_c * t.inv_d : 0.0;
-    if (j == nth - 1) gt[tix + nphi] = 0.0;
-    const size_t kp = (k + 1 == nphi) ? idx - k : idx + 1;
-    gp[idx] = (phi[kp] - c) * r.inv_c * t.inv_c;
   }
 }
 
@@ -253,11 +277,11 @@ cudaError_t face_gradients_f64(const Plan& p, const double* phi, double* gr, dou
     if ((e = shell_apply_f64(p, p.d_ishell, p.shell, p.shell2, s)) != cudaSuccess) return e;
     if ((e = fft_inverse_f64(p, p.shell2, 1, gr, false, s)) != cudaSuccess) return e;
   }
-  const size_t n = (size_t)p.nr * p.nth * p.nphi;
-  size_t blocks = (n + 255) / 256;
-  if (blocks > 152 * 64) blocks = 152 * 64;
+  const int lines = p.nr * p.nth;
+  int blocks = (lines + kFaceWarps - 1) / kFaceWarps;
+  if (blocks > p.num_sms * 8) blocks = p.num_sms * 8;   // one resident wave, 8 CTAs per SM
   const double scale = dir ? 1.0 / (p.r_out - p.r_last) : 1.0 / p.outer_coef;
-  k_face_grad<<<(unsigned)blocks, 256, 0, s>>>(phi, gr, gt, gp, p.d_face_r, p.d_face_t, p.nr, p.nth, p.nphi,
+  k_face_grad<<<(unsigned)blocks, 32 * kFaceWarps, 0, s>>>(phi, gr, gt, gp, p.d_face_r, p.d_face_t, p.nr, p.nth, p.nphi,
                                                dir ? 1 : 0, scale, reg ? -1.0 / p.inner_coef : 0.0);
   return cudaGetLastError();
 }
