@@ -529,24 +529,19 @@ __device__ __forceinline__ void ffd_diff_lo(float bh, float bl, float ch, float 
   else two_sum(bh, -ch, dh, dl);
 }
 
-// Float pair of a float64 source value with integer operations: hi is x truncated to 24
-// significant bits, lo the remaining 29 bits rounded to float (scaled by two exact powers
-// of two), so |hi + lo - x| <= 2^-24 |lo| < 2^-47 |x| for 2^-126 <= |x| < 2^128; smaller
-// magnitudes give (0, 0), larger ones an infinite hi.
+// Float pair of a float64 source value: hi is x rounded toward zero to float (x truncated
+// to 24 significant bits; one conversion instruction), lo the remaining 29 fraction bits
+// rounded to float and scaled by 2^(E-52), E the exponent of x and hi, as two exact powers
+// of two taken from hi's exponent field; so |hi + lo - x| <= 2^-24 |lo| < 2^-47 |x| for
+// 2^-100 <= |x| < 2^128.  Smaller magnitudes keep hi alone (lo = 0, an error below one
+// unit of hi's last place); larger ones lie outside the float range of the low-precision
+// solve.
 __device__ __forceinline__ ff d2ff_trunc(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned int whi = (unsigned int)(b >> 32), wlo = (unsigned int)b;
-  const unsigned int sgn = whi & 0x80000000u;
-  const int e = (int)((whi >> 20) & 0x7FFu);
-  if (e < 897) return ff{0.f, 0.f};
-  if (e > 1150) return ff{__uint_as_float(sgn | 0x7F800000u), 0.f};
-  // bits 60..29 of x hold the low 9 exponent bits and the top 23 fraction bits; adding
-  // 2^30 (= -384 x 2^23 modulo 2^32) moves the exponent bias from 1023 to 127
-  const float hi = __uint_as_float((__funnelshift_l(wlo, whi, 3) + 0x40000000u) | sgn);
-  const int sc = e - 1075, s1 = sc >> 1, s2 = sc - s1;   // the remainder's unit is 2^(e-1075)
-  const float lo = (float)(wlo & 0x1FFFFFFFu) * __uint_as_float(((unsigned int)(s1 + 127) << 23) | sgn) *
-                   __uint_as_float((unsigned int)(s2 + 127) << 23);
-  return ff{hi, lo};
+  const float hi = __double2float_rz(x);
+  const unsigned int hb = __float_as_uint(hi);
+  const unsigned int wlo = (unsigned int)__double_as_longlong(x);
+  const float lo = (float)(wlo & 0x1FFFFFFFu) * __uint_as_float((hb & 0xFF800000u) - (26u << 23)) * 0x1p-26f;
+  return ff{hi, (hb & 0x7F800000u) >= (27u << 23) ? lo : 0.f};
 }
 
 // r = 4 pi G rho - (L Phi) of one zone for the float-float iterate Phi = hi + lo,
