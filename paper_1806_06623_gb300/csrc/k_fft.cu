@@ -19,16 +19,14 @@
 namespace sp {
 namespace {
 
+// float64 input to the transform's type; to float by the rounding conversion, one
+// instruction on the float64 pipe, which the transform leaves otherwise idle
 template <typename T>
 __device__ __forceinline__ T load_in(const double* p) { return (T)*p; }
-template <>
-__device__ __forceinline__ float load_in<float>(const double* p) { return d2ff(*p).hi; }   // no float64 pipe
 template <typename T>
 __device__ __forceinline__ T load_in(const float* p) { return (T)*p; }
 template <typename T>
 __device__ __forceinline__ T cvt_in(double x) { return (T)x; }
-template <>
-__device__ __forceinline__ float cvt_in<float>(double x) { return d2ff(x).hi; }   // no float64 pipe
 template <typename T>
 __device__ __forceinline__ T cvt_in(float x) { return (T)x; }
 
