@@ -406,7 +406,9 @@ def run_ours(args, rank, world, local):
         line[f"{name}_zones_per_s"] = whole_job_rate(zones, args.steps, world, rr["ms"] / 1e3)
         line[f"{name}_ms_per_step"] = rr["ms"] / args.steps
         line[f"{name}_iterations"] = rr["infos"][-1].get("iterations")
-    line["roofline"] = roofline(r["timing"], p, precision, args.steps, r["infos"][-1].get("iterations", 2))
+    line["roofline"] = roofline(r["timing"], p, precision, args.steps, r["infos"][-1].get("iterations", 2),
+                                sm_mhz=(r["clocks"] or {}).get("sm_mhz"),
+                                num_sms=torch.cuda.get_device_properties(dev).multi_processor_count)
     line["roofline_groups"] = roofline_groups(r["timing"], p, precision, args.steps,
                                               r["infos"][-1].get("iterations", 2))
     line["projection_tensor"] = projection_tensor_rate(r["timing"], p, precision)
@@ -590,17 +592,18 @@ def run_served(S, W, torch, n_requests, rates=(200.0, 2000.0, 20000.0)):
 # null once those sources differ.
 MIXED_KERNEL_SOURCES = ("k_fft.cu", "k_mixed.cu", "fft_dev.cuh", "tc_gemm.cuh", "ff.cuh", "sp_internal.h")
 NCU_TRAFFIC = {
-    "source_sha": "25bf8f80631ca02d",
-    "mixed": {   # MB read + written, averaged over the group's launches in one solve
-        "fft_forward": {"bytes": (148.94 + 36.97) * 1e6, "kernel": "k_fft_fwd<float, double> (rho)"},
-        "project_forward": {"bytes": ((91.24 + 18.06) + (91.48 + 18.26)) * 1e6 / 2,
+    "source_sha": "9492bf7366df847b",
+    "mixed": {   # MB read + written and warp instructions, averaged over the group's launches in one solve
+        "fft_forward": {"bytes": (146.87 + 36.10) * 1e6, "inst": 29.28e6, "kernel": "k_fft_fwd<float, double> (rho)"},
+        "project_forward": {"bytes": ((91.35 + 18.10) + (91.56 + 18.28)) * 1e6 / 2, "inst": 13.91e6,
                             "kernel": "tc::k_tc_gemm_split<3>"},
-        "radial_solve": {"bytes": ((145.78 + 39.36) + (145.83 + 39.19)) * 1e6 / 2, "kernel": "k_thomas_scan<2>"},
-        "project_inverse": {"bytes": ((91.39 + 18.23) + (91.35 + 18.23)) * 1e6 / 2,
+        "radial_solve": {"bytes": ((145.85 + 39.42) + (145.82 + 38.94)) * 1e6 / 2, "inst": 19.96e6,
+                         "kernel": "k_thomas_scan<2>"},
+        "project_inverse": {"bytes": ((91.51 + 18.63) + (91.51 + 18.16)) * 1e6 / 2, "inst": 13.91e6,
                             "kernel": "tc::k_tc_gemm_split<3>"},
-        "fft_inverse": {"bytes": ((72.17 + 20.08) + (145.28 + 84.62)) * 1e6 / 2,
+        "fft_inverse": {"bytes": ((72.17 + 20.46) + (145.26 + 84.63)) * 1e6 / 2, "inst": (35.91e6 + 65.81e6) / 2,
                         "kernel": "k_fft_inv<float, float, 2> (first solve, correction)"},
-        "residual": {"bytes": (218.86 + 44.34 + 0.82) * 1e6,
+        "residual": {"bytes": (218.83 + 44.57 + 0.82) * 1e6, "inst": 96.09e6 + 0.41e6,
                      "kernel": "k_residual_fft<0> (interior rows + last shell: residual and its forward FFT)"},
     },
 }
@@ -697,7 +700,7 @@ def algorithmic_bytes_per_step(p, precision, iters=2, fused=None):
             "update": 12 * Z if c == 0 else (16 * Z if npl == 3 and c >= 2 else 0.0)}
 
 
-def roofline(timing, p, precision, steps, iters=2):
+def roofline(timing, p, precision, steps, iters=2, sm_mhz=None, num_sms=152):
     """Dominant kernel group's achieved rate: algorithmic bytes per launch over its
     average live CUDA-event duration."""
     nr, nth, nphi = p.shape
@@ -724,10 +727,18 @@ def roofline(timing, p, precision, steps, iters=2):
     ach = b / per_launch_s / 1e9
     pk = float(peaks.get("hbm_gbs", 6800.0))
     tr = ncu_traffic(precision, name)
-    return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s", "frac": ach / pk,
-            "traffic": tr["bytes"] if tr else None, "traffic_kernel": tr["kernel"] if tr else None,
-            "algorithmic_bytes_per_launch": b,
-            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s"}
+    out = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s", "frac": ach / pk,
+           "traffic": tr["bytes"] if tr else None, "traffic_kernel": tr["kernel"] if tr else None,
+           "algorithmic_bytes_per_launch": b,
+           "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s"}
+    if tr and tr.get("inst") and sm_mhz:
+        # the instruction-issue view of the same launch: warp instructions (ncu) over the
+        # issue rate of 4 per clock per SM at the median SM clock, for the live duration
+        issue = 4.0 * num_sms * sm_mhz * 1e6
+        out["issue"] = {"warp_instructions_per_launch": tr["inst"], "issue_peak_per_s": issue,
+                        "frac": tr["inst"] / (issue * per_launch_s),
+                        "peak": f"4 warp instructions per clock per SM x {num_sms} SMs x {sm_mhz:.0f} MHz"}
+    return out
 
 
 def roofline_groups(timing, p, precision, steps, iters=2):
