@@ -150,7 +150,7 @@ __device__ __forceinline__ void fft_fwd_body(const Tin* __restrict__ in, int nli
   store_half_spectrum<T>(Z, PS, nl, line0, nth, nrs, n, scale, spec, rs);
 }
 
-enum InvOut { kInvWrite = 0, kInvAccumulate = 1, kInvPairUpdate = 2, kInvF64Update = 3 };
+enum InvOut { kInvWrite = 0, kInvAccumulate = 1, kInvPairUpdate = 2, kInvF64Update = 3, kInvPairToF64 = 4 };
 // spectrum rows a warp has in flight in the inverse transform's load (float: 16; double:
 // 8, where 16 would spill)
 template <typename T>
@@ -168,6 +168,10 @@ constexpr int inv_rows() { return sizeof(T) == 4 ? 16 : 8; }
 //    are then left as they were).
 //  MODE kInvF64Update: float64 iterate out = e (first) or out + e, with the same two
 //    reductions (max|e|, max|out| as float).
+//  MODE kInvPairToF64: kInvPairUpdate of an iterate with a zero low word (not first,
+//    lo_read = 0) that writes only phi64 (hilo = 0): phi64 = out + e in one float64
+//    addition, the value the float-float sum gives, and max|out + e| from the float sum,
+//    its high word.
 template <typename T, typename Tout, int MODE>
 __device__ __forceinline__ void fft_inv_body(const T* __restrict__ spec, int nlines, int nth, int nrs,
                                              const FftSchedule& sch, const T* __restrict__ twid, int lpc,
@@ -193,13 +197,13 @@ __device__ __forceinline__ void fft_inv_body(const T* __restrict__ spec, int nli
   const int mh = n / 2 + 1;
   // this CTA's iterate lines (not written by the preceding kernels) head for L2 while the
   // spectra are read and transformed; a prefetch moves no data into the program
-  if (MODE == kInvPairUpdate && !first && threadIdx.x == 0) {
+  if ((MODE == kInvPairUpdate || MODE == kInvPairToF64) && !first && threadIdx.x == 0) {
     prefetch_lines_l2(out, line0, nl, n);
     if (lo_read) prefetch_lines_l2(phi_lo, line0, nl, n);
   }
   pdl_wait();
   // the iterate lines of the CTA one resident wave ahead go on their way into L2 now
-  if (MODE == kInvPairUpdate && !first && threadIdx.x == 0 && ahead > 0 && bx + ahead < gx) {
+  if ((MODE == kInvPairUpdate || MODE == kInvPairToF64) && !first && threadIdx.x == 0 && ahead > 0 && bx + ahead < gx) {
     const int l2 = (bx + ahead) * lpc;
     prefetch_lines_l2(out, l2, min(lpc, nlines - l2), n);
     if (lo_read) prefetch_lines_l2(phi_lo, l2, min(lpc, nlines - l2), n);
@@ -269,6 +273,41 @@ __device__ __forceinline__ void fft_inv_body(const T* __restrict__ spec, int nli
           out[o] = (Tout)nv;
           me = fmaxf(me, fabsf(e));
           mp = fmaxf(mp, fabsf((float)nv));
+        }
+      }
+    } else if (MODE == kInvPairToF64) {
+      // each lane owns 4 consecutive points of two segments of both lines: the iterate's
+      // high words in 16-byte loads (all four in flight), Phi in 16-byte stores (the
+      // launcher checks n and the alignment)
+      for (int qb = 4 * lane; qb < n; qb += 256) {
+        float4 w[2][2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int sg = 0; sg < 2; ++sg) {
+            const int q = qb + 128 * sg;
+            w[h][sg] = q < n && (h == 0 || hasb) ? *reinterpret_cast<const float4*>(out + o0 + (size_t)h * n + q)
+                                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+#pragma unroll
+        for (int sg = 0; sg < 2; ++sg) {
+          const int q = qb + 128 * sg;
+          if (q >= n) continue;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            if (h == 1 && !hasb) continue;
+            const float oh4[4] = {w[h][sg].x, w[h][sg].y, w[h][sg].z, w[h][sg].w};
+            double* d = phi64 + o0 + (size_t)h * n + q;
+#pragma unroll
+            for (int i = 0; i < 4; i += 2) {
+              const CT v0 = z[q + i], v1 = z[q + i + 1];
+              const float e0 = (float)(h ? v0.y : v0.x), e1 = (float)(h ? v1.y : v1.x);
+              reinterpret_cast<double2*>(d)[i >> 1] =
+                  make_double2(f2d_bits(oh4[i]) + f2d_bits(e0), f2d_bits(oh4[i + 1]) + f2d_bits(e1));
+              me = fmaxf(me, fmaxf(fabsf(e0), fabsf(e1)));
+              mp = fmaxf(mp, fmaxf(fabsf(__fadd_rn(oh4[i], e0)), fabsf(__fadd_rn(oh4[i + 1], e1))));
+            }
+          }
         }
       }
     } else if (MODE != kInvPairUpdate) {
@@ -370,7 +409,7 @@ __device__ __forceinline__ void fft_inv_body(const T* __restrict__ spec, int nli
       }
     }
   }
-  if (MODE == kInvPairUpdate || MODE == kInvF64Update) {
+  if (MODE == kInvPairUpdate || MODE == kInvF64Update || MODE == kInvPairToF64) {
     for (int o = 16; o > 0; o >>= 1) {
       me = fmaxf(me, __shfl_xor_sync(0xffffffffu, me, o));
       mp = fmaxf(mp, __shfl_xor_sync(0xffffffffu, mp, o));
@@ -563,13 +602,18 @@ cudaError_t fft_inverse_update(const Plan& p, const float* spec, float* phi_hi, 
   const int nlines = p.nr * p.nth;
   const int lpc = panel_lpc(p, nlines);
   const size_t smem = fft_smem<float>(p.nphi, lpc);
-  auto kern = k_fft_inv<float, float, kInvPairUpdate>;
+  const bool hilo = !(f64_only && !first && phi64);
+  // an iterate with a zero low word that is written only as float64 Phi: the direct
+  // float64 update (16-byte accesses)
+  const bool direct = !hilo && !lo_read && (p.nphi & 3) == 0 && (reinterpret_cast<uintptr_t>(phi64) & 15u) == 0 &&
+                      (reinterpret_cast<uintptr_t>(phi_hi) & 15u) == 0;
+  auto kern = direct ? k_fft_inv<float, float, kInvPairToF64> : k_fft_inv<float, float, kInvPairUpdate>;
   cudaError_t e = prep(kern, smem);
   if (e != cudaSuccess) return e;
   // (prefetching the iterate a wave ahead measured slower here: ahead = 0)
   e = launch_pdl(kern, dim3((nlines + lpc - 1) / lpc), dim3(32 * kWarps), smem, s, spec, nlines, p.nth, p.nr, p.sched,
-                 (const float*)p.d_twid32, lpc, phi_hi, phi_lo, first ? 1 : 0, lo_read ? 1 : 0,
-                 (f64_only && !first && phi64) ? 0 : 1, red, 0, first ? nullptr : phi64);
+                 (const float*)p.d_twid32, lpc, phi_hi, phi_lo, first ? 1 : 0, lo_read ? 1 : 0, hilo ? 1 : 0, red, 0,
+                 first ? nullptr : phi64);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
