@@ -101,7 +101,10 @@ typedef struct {
                               4.7e-11 at Nphi = 256), 2^-40 with the float64 one.  When the
                               floor exceeds tol the solve stops and returns
                               SP_ERR_NOT_CONVERGED (with SP_RESIDUAL_AUTO only for tol below
-                              2^-40 or a float-float residual chosen explicitly) */
+                              2^-40 or a float-float residual chosen explicitly); a NaN or an
+                              infinity in a correction or the iterate (a non-finite rho) stops
+                              the refinement with SP_ERR_NOT_CONVERGED and an infinite
+                              estimate */
     int status;            /* sp_status of the solve */
     double update_history[8]; /* max|e_k|/max|Phi| of the first 8 solves (k = 0 is the first solve) */
 } sp_solve_info;

@@ -209,8 +209,10 @@ def sp_plan_clone(plan):
     return out
 
 
-def sp_solve_batched(plans, rhos, phis, stream=None):
-    """plans: list of Plan; rhos, phis: lists of CUDA float64 tensors (one per plan)."""
+def sp_solve_batched(plans, rhos, phis, stream=None, check=True):
+    """plans: list of Plan; rhos, phis: lists of CUDA float64 tensors (one per plan).
+    Returns the per-instance infos; with check=False a failing instance does not raise
+    (its info.status says how it failed)."""
     n = len(plans)
     if not (len(rhos) == len(phis) == n):
         raise ValueError("plans, rhos and phis must have the same length")
@@ -220,7 +222,8 @@ def sp_solve_batched(plans, rhos, phis, stream=None):
     infos = (SolveInfo * n)()
     dev = rhos[0].device if n else None
     st = lib().sp_solve_batched(hp, rp, pp, n, _stream_ptr(stream, dev), infos)
-    _check(st, "sp_solve_batched")
+    if check:
+        _check(st, "sp_solve_batched")
     return list(infos)
 
 

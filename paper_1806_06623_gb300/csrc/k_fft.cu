@@ -150,6 +150,13 @@ __device__ __forceinline__ void fft_fwd_body(const Tin* __restrict__ in, int nli
   store_half_spectrum<T>(Z, PS, nl, line0, nth, nrs, n, scale, spec, rs);
 }
 
+// max(m, |x|) for m >= 0 that keeps a NaN: non-negative float bit patterns order as
+// unsigned integers, every NaN above +inf (a NaN in a correction then reaches the host's
+// stopping decision instead of being dropped as fmaxf drops it)
+__device__ __forceinline__ float amax(float m, float x) {
+  return __uint_as_float(max(__float_as_uint(m), __float_as_uint(fabsf(x))));
+}
+
 enum InvOut { kInvWrite = 0, kInvAccumulate = 1, kInvPairUpdate = 2, kInvF64Update = 3, kInvPairToF64 = 4 };
 // spectrum rows a warp has in flight in the inverse transform's load (float: 16; double:
 // 8, where 16 would spill)
@@ -271,8 +278,8 @@ __device__ __forceinline__ void fft_inv_body(const T* __restrict__ spec, int nli
           const float e = (float)(h ? v.y : v.x);
           const double nv = first ? (double)e : (double)out[o] + (double)e;
           out[o] = (Tout)nv;
-          me = fmaxf(me, fabsf(e));
-          mp = fmaxf(mp, fabsf((float)nv));
+          me = amax(me, e);
+          mp = amax(mp, (float)nv);
         }
       }
     } else if (MODE == kInvPairToF64) {
@@ -304,8 +311,8 @@ __device__ __forceinline__ void fft_inv_body(const T* __restrict__ spec, int nli
               const float e0 = (float)(h ? v0.y : v0.x), e1 = (float)(h ? v1.y : v1.x);
               reinterpret_cast<double2*>(d)[i >> 1] =
                   make_double2(f2d_bits(oh4[i]) + f2d_bits(e0), f2d_bits(oh4[i + 1]) + f2d_bits(e1));
-              me = fmaxf(me, fmaxf(fabsf(e0), fabsf(e1)));
-              mp = fmaxf(mp, fmaxf(fabsf(__fadd_rn(oh4[i], e0)), fabsf(__fadd_rn(oh4[i + 1], e1))));
+              me = amax(amax(me, e0), e1);
+              mp = amax(amax(mp, __fadd_rn(oh4[i], e0)), __fadd_rn(oh4[i + 1], e1));
             }
           }
         }
@@ -358,8 +365,8 @@ __device__ __forceinline__ void fft_inv_body(const T* __restrict__ spec, int nli
                 const ff nv = first ? ff{e, 0.f} : ff_add_f(ff{oh4[i], ol4[i]}, e);
                 nh[i] = nv.hi;
                 nl[i] = nv.lo;
-                me = fmaxf(me, fabsf(e));
-                mp = fmaxf(mp, fabsf(nv.hi));
+                me = amax(me, e);
+                mp = amax(mp, nv.hi);
               }
               if (hilo) {
                 *reinterpret_cast<float4*>(out + o) = make_float4(nh[0], nh[1], nh[2], nh[3]);
@@ -402,8 +409,8 @@ __device__ __forceinline__ void fft_inv_body(const T* __restrict__ spec, int nli
               if (!first) phi_lo[o] = nv.lo;
             }
             if (phi64) phi64[o] = ff2d(nv);
-            me = fmaxf(me, fabsf(e));
-            mp = fmaxf(mp, fabsf(nv.hi));
+            me = amax(me, e);
+            mp = amax(mp, nv.hi);
           }
         }
       }
@@ -411,13 +418,13 @@ __device__ __forceinline__ void fft_inv_body(const T* __restrict__ spec, int nli
   }
   if (MODE == kInvPairUpdate || MODE == kInvF64Update || MODE == kInvPairToF64) {
     for (int o = 16; o > 0; o >>= 1) {
-      me = fmaxf(me, __shfl_xor_sync(0xffffffffu, me, o));
-      mp = fmaxf(mp, __shfl_xor_sync(0xffffffffu, mp, o));
+      me = amax(me, __shfl_xor_sync(0xffffffffu, me, o));
+      mp = amax(mp, __shfl_xor_sync(0xffffffffu, mp, o));
     }
     if (lane == 0) { s_me[warp] = me; s_mp[warp] = mp; }
     __syncthreads();
     if (threadIdx.x == 0) {
-      for (int w = 1; w < kWarps; ++w) { me = fmaxf(me, s_me[w]); mp = fmaxf(mp, s_mp[w]); }
+      for (int w = 1; w < kWarps; ++w) { me = amax(me, s_me[w]); mp = amax(mp, s_mp[w]); }
       atomicMax(red, __float_as_uint(me));
       atomicMax(red + 1, __float_as_uint(mp));
     }

@@ -457,6 +457,7 @@ struct MixedRun {
   int next_slot = 0;   // host slot of the next copy
   bool done = false;
   bool floor_limited = false;   // the iterate's precision floor is above the tolerance
+  bool nonfinite = false;       // a correction or the iterate held a NaN or an infinity
 };
 constexpr int kRedErrWord = 4;   // h_red: two slots of (max|e|, max|Phi|), then the status word
 int mixed_start(Plan* p, const double* rho, double* phi, cudaStream_t s);

@@ -2,6 +2,7 @@
 // workspace management and the float64 solve sequence of Sect. 3.2.
 #include <algorithm>
 #include <cmath>
+#include <limits>
 #include <cstdio>
 #include <mutex>
 #include <unordered_map>
@@ -411,6 +412,13 @@ void decide_one(Plan* p, MixedRun& R, const unsigned int* slot) {
   std::memcpy(v, slot, sizeof(v));
   const double e_cur = v[0];
   R.pmax = v[1];
+  if (!std::isfinite(e_cur) || !std::isfinite(R.pmax)) {   // a non-finite source or iterate
+    R.done = R.nonfinite = true;
+    R.est = R.last = std::numeric_limits<double>::infinity();
+    if (R.iters < 8) R.hist[R.iters] = R.last;
+    ++R.iters;
+    return;
+  }
   if (R.iters == 0) {
     R.e_prev = e_cur;
     R.hist[0] = R.pmax > 0.0 ? e_cur / R.pmax : 0.0;
@@ -478,7 +486,7 @@ int mixed_finish_status(Plan* p, const MixedRun& R, sp_solve_info* info) {
   Plan& P = *p;
   const int herr = (int)P.h_red[kRedErrWord];
   const int st = herr ? ((herr & kErrTimeout) ? SP_ERR_TIMEOUT : SP_ERR_DEVICE_CHECK)
-                      : ((R.done && !R.floor_limited) ? SP_OK : SP_ERR_NOT_CONVERGED);
+                      : ((R.done && !R.floor_limited && !R.nonfinite) ? SP_OK : SP_ERR_NOT_CONVERGED);
   if (info) {
     info->iterations = R.iters;
     info->precision_used = P.precision;

@@ -205,6 +205,32 @@ def test_mixed_reports_non_convergence(S):
     assert info.status == S.SP_OK
 
 
+@pytest.mark.parametrize("mode", ["x3", "x6"])
+@pytest.mark.parametrize("bad", [float("nan"), float("inf")])
+def test_mixed_nonfinite_source_is_not_converged(S, mode, bad):
+    """A NaN or an infinity in rho reaches the stopping decision (the device reductions
+    keep a NaN, which a float max would drop, leaving max|Phi| = 0 and a claimed
+    convergence) and the solve returns SP_ERR_NOT_CONVERGED; the plan stays usable, and in
+    a batch only the instance with the bad source fails."""
+    prec = S.SP_MIXED_BF16X3 if mode == "x3" else S.SP_MIXED_BF16X6
+    for nphi in (32, 256):   # the separate and the fused residual
+        p = W.random_small(12, 8, nphi, seed=5, grid="log")
+        bad_rho = np.ascontiguousarray(p.rho).copy()
+        bad_rho[3, 2, 5] = bad
+        plan = S.Plan(p.r_if, p.th_if, p.nphi, precision=prec, tol=TOL)
+        with pytest.raises(S.SpError) as ei:
+            plan.solve(torch.from_numpy(bad_rho).cuda())
+        assert ei.value.status == S.SP_ERR_NOT_CONVERGED
+        _, info = plan.solve(torch.from_numpy(np.ascontiguousarray(p.rho)).cuda())
+        assert info.status == S.SP_OK
+        plans = [S.Plan(p.r_if, p.th_if, p.nphi, precision=prec, tol=TOL) for _ in range(2)]
+        rhos = [torch.from_numpy(bad_rho).cuda(), torch.from_numpy(np.ascontiguousarray(p.rho)).cuda()]
+        infos = S.sp_solve_batched(plans, rhos, [torch.empty_like(r) for r in rhos], check=False)
+        torch.cuda.synchronize()
+        assert infos[0].status == S.SP_ERR_NOT_CONVERGED and not np.isfinite(infos[0].est_rel_error)
+        assert infos[1].status == S.SP_OK
+
+
 def test_mixed_zero_source(S):
     p = W.random_small(6, 8, 8, seed=1)
     p.rho[:] = 0.0
