@@ -1395,8 +1395,9 @@ cudaError_t residual_ff(const Plan& p, const double* rho, cudaStream_t s) {
   };
   if (p.outer_bc != SP_OUTER_MULTIPOLE) return rows(0, p.nr, s);
   // The multipole term of the last shell (small: Ntheta x Nphi zones, float64 FFTs and
-  // per-m operator) runs on the high-priority side stream while the interior rows,
-  // which do not need it, run here; the last shell alone follows the join.
+  // per-m operator) and then the last shell's residual run on the high-priority side
+  // stream while the interior rows, which do not need the term, run here; the join
+  // follows both.
   cudaError_t e;
   if ((e = cudaEventRecord(p.ev_fork, s)) != cudaSuccess || (e = cudaStreamWaitEvent(p.side, p.ev_fork, 0)) != cudaSuccess)
     return e;
@@ -1407,10 +1408,10 @@ cudaError_t residual_ff(const Plan& p, const double* rho, cudaStream_t s) {
   if ((e = fft_forward_f64(p, x.shell_phi, 1, 1.0 / p.nphi, p.shell, p.side)) != cudaSuccess) return e;
   if ((e = shell_kappa_f64(p, p.shell, p.shell2, p.side)) != cudaSuccess) return e;
   if ((e = fft_inverse_f64(p, p.shell2, 1, x.outer_shell, false, p.side)) != cudaSuccess) return e;
+  if ((e = rows(p.nr - 1, p.nr, p.side)) != cudaSuccess) return e;
   if ((e = cudaEventRecord(p.ev_join, p.side)) != cudaSuccess) return e;
   if (p.nr > 1 && (e = rows(0, p.nr - 1, s)) != cudaSuccess) return e;
-  if ((e = cudaStreamWaitEvent(s, p.ev_join, 0)) != cudaSuccess) return e;
-  return rows(p.nr - 1, p.nr, s);
+  return cudaStreamWaitEvent(s, p.ev_join, 0);
 }
 
 bool residual_fft_supported(const Plan& p, const double* rho) {
@@ -1419,8 +1420,8 @@ bool residual_fft_supported(const Plan& p, const double* rho) {
 
 // The float-float residual fused with its forward FFT into the panel (see k_residual_fft),
 // with the same side-stream shell term as residual_ff: interior rows in blocks of 32
-// lines while the shell chain runs, the last shell after the join in blocks of 4 lines
-// (more CTAs for the one row on the critical path).
+// lines here while the shell chain and then the last shell (in blocks of 4 lines: more
+// CTAs for the one row) run on the side stream; the join follows both.
 cudaError_t residual_fft(const Plan& p, const double* rho, cudaStream_t s) {
   const MixedTables& x = *p.mixed;
   auto kern = x.lo_zero ? k_residual_fft<false> : k_residual_fft<true>;
@@ -1447,10 +1448,10 @@ cudaError_t residual_fft(const Plan& p, const double* rho, cudaStream_t s) {
   if ((e = fft_forward_f64(p, x.shell_phi, 1, 1.0 / p.nphi, p.shell, p.side)) != cudaSuccess) return e;
   if ((e = shell_kappa_f64(p, p.shell, p.shell2, p.side)) != cudaSuccess) return e;
   if ((e = fft_inverse_f64(p, p.shell2, 1, x.outer_shell, false, p.side)) != cudaSuccess) return e;
+  if ((e = rows(p.nr - 1, p.nr, 4, p.side)) != cudaSuccess) return e;
   if ((e = cudaEventRecord(p.ev_join, p.side)) != cudaSuccess) return e;
   if (p.nr > 1 && (e = rows(0, p.nr - 1, 32, s)) != cudaSuccess) return e;
-  if ((e = cudaStreamWaitEvent(s, p.ev_join, 0)) != cudaSuccess) return e;
-  return rows(p.nr - 1, p.nr, 4, s);
+  return cudaStreamWaitEvent(s, p.ev_join, 0);
 }
 
 // Refinement residual in float64 for a float64 iterate: r = 4 pi G rho - (Delta Phi) with
