@@ -1616,6 +1616,11 @@ namespace {
 __global__ void __launch_bounds__(256) k_post_words(const unsigned int* __restrict__ src, unsigned int* dst, int n) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
 }
+__global__ void __launch_bounds__(256) k_post_words2(const unsigned int* __restrict__ a, unsigned int* da, int na,
+                                                     const unsigned int* __restrict__ b, unsigned int* db, int nb) {
+  for (int i = threadIdx.x; i < na; i += blockDim.x) da[i] = a[i];
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) db[i] = b[i];
+}
 }  // namespace
 
 // A few result words of the device into page-locked host memory by the GPU's own stores:
@@ -1624,6 +1629,13 @@ __global__ void __launch_bounds__(256) k_post_words(const unsigned int* __restri
 cudaError_t post_words(const unsigned int* src, unsigned int* host_dst, int n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   k_post_words<<<1, 256, 0, s>>>(src, host_dst, n);
+  return cudaGetLastError();
+}
+
+// Two such groups of words in one launch.
+cudaError_t post_words2(const unsigned int* a, unsigned int* host_a, int na, const unsigned int* b,
+                        unsigned int* host_b, int nb, cudaStream_t s) {
+  k_post_words2<<<1, 256, 0, s>>>(a, host_a, na, b, host_b, nb);
   return cudaGetLastError();
 }
 

@@ -443,6 +443,8 @@ cudaError_t finish_rag(const FinishArgs* tab, const int* start, int n, int total
 // n result words of the device -> page-locked host memory (`host_dst` a device-accessible
 // pointer of a cudaMallocHost allocation), by one kernel's stores instead of a copy
 cudaError_t post_words(const unsigned int* src, unsigned int* host_dst, int n, cudaStream_t s);
+cudaError_t post_words2(const unsigned int* a, unsigned int* host_a, int na, const unsigned int* b,
+                        unsigned int* host_b, int nb, cudaStream_t s);
 // n page-locked host words and the device address of the same memory (SP_OK / SP_ERR_*)
 int alloc_host_words(int n, unsigned int** host, unsigned int** dev);
 cudaError_t shell_apply_rag(const ShellArgs* tab, const int* start, int n, int total, cudaStream_t s);

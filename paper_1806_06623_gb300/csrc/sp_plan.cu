@@ -301,17 +301,31 @@ int mixed_issue_read(Plan* p, cudaStream_t s, MixedRun& R) {
 
 namespace {
 
-// Phase A ends with the copy of the device status word too, so that a solve which stops
-// after it (the usual case) returns without another kernel or synchronisation.
+// Phase A ends with the copy of the device status word too (with the correction's
+// reductions, one launch), so that a solve which stops after it (the usual case) returns
+// without another kernel or synchronisation.  The first solve's reductions are copied on
+// the side stream beside the correction's residual when the residual's multipole chain
+// joins that stream back before the reductions are cleared (float-float residual); else
+// here.
 int phase_a_direct(Plan* p, const double* rho, double* phi, cudaStream_t s, MixedRun& R) {
   int st;
   if ((st = mixed_start(p, rho, phi, s))) return st;
-  if ((st = mixed_issue_read(p, s, R))) return st;
+  if (p->max_iter >= 1 && p->side && !p->mixed->resid64 && p->outer_bc == SP_OUTER_MULTIPOLE) {
+    SP_CUDA(cudaEventRecord(p->ev_fork, s));
+    SP_CUDA(cudaStreamWaitEvent(p->side, p->ev_fork, 0));
+    if ((st = mixed_issue_read(p, p->side, R))) return st;
+  } else if ((st = mixed_issue_read(p, s, R))) {
+    return st;
+  }
+  const unsigned int* err = reinterpret_cast<const unsigned int*>(p->d_err);
   if (p->max_iter >= 1) {
     if ((st = mixed_correct(p, rho, phi, s))) return st;
-    if ((st = mixed_issue_read(p, s, R))) return st;
+    SP_CUDA(post_words2(p->mixed->red, p->h_red_dev + 2 * R.next_slot, 2, err, p->h_red_dev + kRedErrWord, 1, s));
+    R.next_slot ^= 1;
+    ++R.pending;
+  } else {
+    SP_CUDA(post_words(err, p->h_red_dev + kRedErrWord, 1, s));
   }
-  SP_CUDA(post_words(reinterpret_cast<const unsigned int*>(p->d_err), p->h_red_dev + kRedErrWord, 1, s));
   ++p->launches;
   return SP_OK;
 }
