@@ -592,18 +592,18 @@ def run_served(S, W, torch, n_requests, rates=(200.0, 2000.0, 20000.0)):
 # null once those sources differ.
 MIXED_KERNEL_SOURCES = ("k_fft.cu", "k_mixed.cu", "fft_dev.cuh", "tc_gemm.cuh", "ff.cuh", "sp_internal.h")
 NCU_TRAFFIC = {
-    "source_sha": "2a63db9acff471eb",
+    "source_sha": "50a3c14557fab3ab",
     "mixed": {   # MB read + written and warp instructions, averaged over the group's launches in one solve
-        "fft_forward": {"bytes": (147.20 + 36.37) * 1e6, "inst": 29.28e6, "kernel": "k_fft_fwd<float, double> (rho)"},
-        "project_forward": {"bytes": ((91.41 + 18.45) + (91.56 + 18.38)) * 1e6 / 2, "inst": 13.91e6,
+        "fft_forward": {"bytes": (146.97 + 36.68) * 1e6, "inst": 29.28e6, "kernel": "k_fft_fwd<float, double> (rho)"},
+        "project_forward": {"bytes": ((91.35 + 18.13) + (91.58 + 18.69)) * 1e6 / 2, "inst": 13.91e6,
                             "kernel": "tc::k_tc_gemm_split<3>"},
-        "radial_solve": {"bytes": ((145.82 + 39.00) + (145.78 + 38.46)) * 1e6 / 2, "inst": 19.96e6,
+        "radial_solve": {"bytes": ((145.79 + 39.33) + (145.79 + 38.58)) * 1e6 / 2, "inst": 19.96e6,
                          "kernel": "k_thomas_scan<2>"},
-        "project_inverse": {"bytes": ((91.47 + 18.29) + (91.48 + 18.25)) * 1e6 / 2, "inst": 13.92e6,
+        "project_inverse": {"bytes": ((91.43 + 18.18) + (91.46 + 18.25)) * 1e6 / 2, "inst": 13.90e6,
                             "kernel": "tc::k_tc_gemm_split<3>"},
-        "fft_inverse": {"bytes": ((72.17 + 20.14) + (145.08 + 84.05)) * 1e6 / 2, "inst": (37.17e6 + 56.29e6) / 2,
+        "fft_inverse": {"bytes": ((72.16 + 20.20) + (145.02 + 83.71)) * 1e6 / 2, "inst": (37.17e6 + 56.29e6) / 2,
                         "kernel": "k_fft_inv<float, float, 2> (first solve), k_fft_inv<float, float, 4> (correction)"},
-        "residual": {"bytes": (218.76 + 44.15 + 0.82) * 1e6, "inst": 96.09e6 + 0.41e6,
+        "residual": {"bytes": (218.78 + 44.01 + 0.82) * 1e6, "inst": 96.09e6 + 0.41e6,
                      "kernel": "k_residual_fft<0> (interior rows + last shell: residual and its forward FFT)"},
     },
 }
