@@ -298,8 +298,9 @@ int sp_plan_get_eigen(const sp_plan* plan, double* lambda, double* H, double* ka
  * recorded events and adds their durations to per-kernel totals;
  * sp_plan_get_timing copies the totals (milliseconds) and launch counts of the first
  * n kernel identities, in this order: forward FFT, forward projection, radial solve,
- * inverse projection, inverse FFT, stencil, outer-shell term, residual, split,
- * update, eigensolve.  Enabling resets the totals. */
+ * inverse projection, inverse FFT, stencil, outer-shell term, residual (with its shell
+ * term on the side stream), split, update, eigensolve, and the residual's interior-row
+ * kernel alone (inside the residual's span).  Enabling resets the totals. */
 int sp_plan_set_timing(sp_plan* plan, int enable);
 int sp_plan_collect_timing(sp_plan* plan);
 int sp_plan_get_timing(const sp_plan* plan, double* ms, long long* count, int n);

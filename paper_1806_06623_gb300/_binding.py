@@ -353,7 +353,7 @@ def sp_plan_last_status(plan) -> int:
 
 
 KERNEL_NAMES = ["fft_forward", "project_forward", "radial_solve", "project_inverse", "fft_inverse",
-                "stencil", "outer_term", "residual", "split", "update", "eigensolve"]
+                "stencil", "outer_term", "residual", "split", "update", "eigensolve", "residual_rows"]
 
 
 def sp_plan_set_timing(plan, enable: bool):

@@ -1376,7 +1376,7 @@ int create_side_stream(Plan& p) {
   return SP_OK;
 }
 
-cudaError_t residual_ff(const Plan& p, const double* rho, cudaStream_t s) {
+cudaError_t residual_ff(Plan& p, const double* rho, cudaStream_t s) {
   const MixedTables& x = *p.mixed;
   const size_t sh = (size_t)p.nth * p.nphi;
   // column pairs per thread when Nphi is even and rho allows 16-byte loads
@@ -1393,7 +1393,7 @@ cudaError_t residual_ff(const Plan& p, const double* rho, cudaStream_t s) {
                                      r1, p.outer_bc == SP_OUTER_DIRICHLET ? 1 : 0, x.dir_coef, x.four_pi_g);
     return e != cudaSuccess ? e : cudaGetLastError();
   };
-  if (p.outer_bc != SP_OUTER_MULTIPOLE) return rows(0, p.nr, s);
+  if (p.outer_bc != SP_OUTER_MULTIPOLE) return timed_span(p, kKResidualRows, s, [&] { return rows(0, p.nr, s); });
   // The multipole term of the last shell (small: Ntheta x Nphi zones, float64 FFTs and
   // per-m operator) and then the last shell's residual run on the high-priority side
   // stream while the interior rows, which do not need the term, run here; the join
@@ -1410,7 +1410,8 @@ cudaError_t residual_ff(const Plan& p, const double* rho, cudaStream_t s) {
   if ((e = fft_inverse_f64(p, p.shell2, 1, x.outer_shell, false, p.side)) != cudaSuccess) return e;
   if ((e = rows(p.nr - 1, p.nr, p.side)) != cudaSuccess) return e;
   if ((e = cudaEventRecord(p.ev_join, p.side)) != cudaSuccess) return e;
-  if (p.nr > 1 && (e = rows(0, p.nr - 1, s)) != cudaSuccess) return e;
+  if (p.nr > 1 && (e = timed_span(p, kKResidualRows, s, [&] { return rows(0, p.nr - 1, s); })) != cudaSuccess)
+    return e;
   return cudaStreamWaitEvent(s, p.ev_join, 0);
 }
 
@@ -1422,7 +1423,7 @@ bool residual_fft_supported(const Plan& p, const double* rho) {
 // with the same side-stream shell term as residual_ff: interior rows in blocks of 32
 // lines here while the shell chain and then the last shell (in blocks of 4 lines: more
 // CTAs for the one row) run on the side stream; the join follows both.
-cudaError_t residual_fft(const Plan& p, const double* rho, cudaStream_t s) {
+cudaError_t residual_fft(Plan& p, const double* rho, cudaStream_t s) {
   const MixedTables& x = *p.mixed;
   auto kern = x.lo_zero ? k_residual_fft<false> : k_residual_fft<true>;
   auto rows = [&](int r0, int r1, int lpc, cudaStream_t st) {
@@ -1436,7 +1437,7 @@ cudaError_t residual_fft(const Plan& p, const double* rho, cudaStream_t s) {
                    x.dir_coef, x.four_pi_g, (const float*)p.d_twid32, (float)(1.0 / p.nphi), x.panel, x.kstride);
     return e != cudaSuccess ? e : cudaGetLastError();
   };
-  if (p.outer_bc != SP_OUTER_MULTIPOLE) return rows(0, p.nr, 32, s);
+  if (p.outer_bc != SP_OUTER_MULTIPOLE) return timed_span(p, kKResidualRows, s, [&] { return rows(0, p.nr, 32, s); });
   cudaError_t e;
   if ((e = cudaEventRecord(p.ev_fork, s)) != cudaSuccess || (e = cudaStreamWaitEvent(p.side, p.ev_fork, 0)) != cudaSuccess)
     return e;
@@ -1450,7 +1451,8 @@ cudaError_t residual_fft(const Plan& p, const double* rho, cudaStream_t s) {
   if ((e = fft_inverse_f64(p, p.shell2, 1, x.outer_shell, false, p.side)) != cudaSuccess) return e;
   if ((e = rows(p.nr - 1, p.nr, 4, p.side)) != cudaSuccess) return e;
   if ((e = cudaEventRecord(p.ev_join, p.side)) != cudaSuccess) return e;
-  if (p.nr > 1 && (e = rows(0, p.nr - 1, 32, s)) != cudaSuccess) return e;
+  if (p.nr > 1 && (e = timed_span(p, kKResidualRows, s, [&] { return rows(0, p.nr - 1, 32, s); })) != cudaSuccess)
+    return e;
   return cudaStreamWaitEvent(s, p.ev_join, 0);
 }
 

@@ -177,7 +177,9 @@ struct ShellArgs {   // z_m = O_m x_m on one shell spectrum
 // Kernel identities for the optional per-launch CUDA-event timers.
 enum KernelId : int {
   kKFftFwd = 0, kKGemmFwd, kKThomas, kKGemmInv, kKFftInv, kKStencil, kKOuter, kKResidual,
-  kKSplit, kKUpdate, kKEigen, kNumKernelIds
+  kKSplit, kKUpdate, kKEigen,
+  kKResidualRows,   // the residual's interior-row kernel alone, inside the kKResidual span
+  kNumKernelIds
 };
 constexpr int kMaxTimedLaunches = 256;
 
@@ -318,14 +320,20 @@ cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t sme
 }
 
 template <typename F>
-cudaError_t timed_launch(Plan& p, int id, cudaStream_t s, F&& launch) {
-  const bool t = p.timing && p.n_timed < kMaxTimedLaunches;
-  if (t) cudaEventRecord(p.ev[2 * p.n_timed], s);
+cudaError_t timed_span(Plan& p, int id, cudaStream_t s, F&& launch) {
+  // the event pair's slot is taken before the launch, so spans may nest
+  const int k = (p.timing && p.n_timed < kMaxTimedLaunches) ? p.n_timed++ : -1;
+  if (k >= 0) cudaEventRecord(p.ev[2 * k], s);
   cudaError_t e = launch();
-  if (t) {
-    cudaEventRecord(p.ev[2 * p.n_timed + 1], s);
-    p.ev_kernel[p.n_timed++] = id;
+  if (k >= 0) {
+    cudaEventRecord(p.ev[2 * k + 1], s);
+    p.ev_kernel[k] = id;
   }
+  return e;
+}
+template <typename F>
+cudaError_t timed_launch(Plan& p, int id, cudaStream_t s, F&& launch) {
+  const cudaError_t e = timed_span(p, id, s, static_cast<F&&>(launch));
   ++p.launches;
   return e;
 }
@@ -401,11 +409,11 @@ cudaError_t split_iterate(const Plan& p, const double* phi, cudaStream_t s);   /
 bool first_correction_f64_only(const Plan& p);   // the first correction stores the iterate in float64 only
 cudaError_t tc_project(const Plan& p, bool inverse, cudaStream_t s);   // pan -> d32
 cudaError_t thomas_mixed(const Plan& p, cudaStream_t s);   // d32 -> pan (f); float32 + float64 low modes
-cudaError_t residual_ff(const Plan& p, const double* rho, cudaStream_t s);  // iterate -> r32
+cudaError_t residual_ff(Plan& p, const double* rho, cudaStream_t s);  // iterate -> r32
 // the float-float residual fused with its forward FFT (iterate -> panel), where
 // residual_fft_supported: Nphi = 256, even Ntheta, 16-byte aligned rho, float-float residual
 bool residual_fft_supported(const Plan& p, const double* rho);
-cudaError_t residual_fft(const Plan& p, const double* rho, cudaStream_t s);
+cudaError_t residual_fft(Plan& p, const double* rho, cudaStream_t s);
 cudaError_t residual_f64(const Plan& p, const double* rho, const double* phi, cudaStream_t s);  // float64 iterate -> r32
 // inverse FFT adding the correction into a float64 iterate (first: phi = e), reductions into red
 cudaError_t fft_inverse_update64(const Plan& p, const float* spec, double* phi, bool first, unsigned int* red,
