@@ -289,3 +289,28 @@ def test_mixed_rho_on_an_8_byte_boundary(S):
     assert info_a.status == S.SP_OK and info_b.status == S.SP_OK
     assert rel_err(a, ref) <= TOL and rel_err(b, ref) <= TOL
     assert rel_err(b, a) <= 1e-12
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+def test_timing_spans_of_a_mixed_solve(S, bc):
+    """Per-kernel CUDA-event timers: every group of the 6-product solve is timed, the
+    residual's interior-row kernel has a span of its own inside the residual's (nested
+    spans, one per residual), and the launch counter does not count the nested span."""
+    p = W.random_small(12, 8, 256, seed=3, grid="log", outer_bc=bc)
+    plan = S.Plan(p.r_if, p.th_if, p.nphi, outer_bc=bc, precision=S.SP_MIXED_BF16X6, tol=TOL)
+    rho = torch.from_numpy(np.ascontiguousarray(p.rho)).cuda()
+    c0 = S.sp_plan_launch_count(plan.handle)
+    plan.solve(rho)   # (launched directly: graphs are captured from the second solve on)
+    n0 = S.sp_plan_launch_count(plan.handle)
+    plan.set_timing(True)
+    _, info = plan.solve(rho)
+    torch.cuda.synchronize()
+    plan.collect_timing()
+    t = plan.timing()
+    n1 = S.sp_plan_launch_count(plan.handle)
+    plan.set_timing(False)
+    for name in ("fft_forward", "project_forward", "radial_solve", "project_inverse", "fft_inverse", "residual"):
+        assert name in t and t[name][0] > 0.0
+    assert t["residual_rows"][1] == t["residual"][1] == info.iterations - 1
+    assert 0.0 < t["residual_rows"][0] <= t["residual"][0]
+    assert n1 - n0 == n0 - c0   # the same launches with and without timers (both direct)
