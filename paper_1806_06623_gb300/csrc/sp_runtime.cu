@@ -137,7 +137,24 @@ extern "C" int sp_solve_batched(sp_plan* const* plans, const double* const* rho,
   const bool ragged = g_ragged.load() && ns >= 2 && sp::ragged_supported(MP.data(), MR.data(), (int)MP.size());
   t_last_ragged = ragged ? (int)MP.size() : 0;
   const int groups = ragged ? sp::ragged_groups((int)MP.size(), ns) : 0;
-  auto stream_of = [&](int i) { return ragged ? pool->s[2 * (i % groups)] : pool->s[i % ns]; };
+  // per-instance launch sequences: largest instances first, each to the stream with the
+  // fewest zones so far, so that the streams end together and the small instances fill
+  // the GPU beside the last large ones
+  std::vector<int> order(n), lane(n, 0);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  auto zones = [&](int i) { return (double)P[i]->nr * P[i]->nth * P[i]->nphi; };
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return zones(a) > zones(b); });
+  {
+    std::vector<double> load(ns > 0 ? ns : 1, 0.0);
+    for (int i : order) {
+      int k = 0;
+      for (int q = 1; q < ns; ++q)
+        if (load[q] < load[k]) k = q;
+      lane[i] = k;
+      load[k] += zones(i);
+    }
+  }
+  auto stream_of = [&](int i) { return ragged ? pool->s[2 * (i % groups)] : pool->s[lane[i]]; };
   if (ragged) {
     // float64 instances on the groups' main streams ahead of their ragged rounds
     for (int i = 0; i < n; ++i)
@@ -153,8 +170,9 @@ extern "C" int sp_solve_batched(sp_plan* const* plans, const double* const* rho,
       if (!status[mixed_idx[k]])
         status[mixed_idx[k]] = sp::mixed_finish_issue(P[mixed_idx[k]], phi[mixed_idx[k]], pool->s[0]);
   }
-  // round 0: float64 solves and the first low-precision solves
-  for (int i = 0; i < n && !ragged; ++i) {
+  // round 0: float64 solves and the first low-precision solves, largest first
+  for (int k = 0; k < n && !ragged; ++k) {
+    const int i = order[k];
     if (P[i]->mixed) {
       // the first correction goes right behind the first solve (see solve_mixed)
       status[i] = sp::mixed_phase_a(P[i], rho[i], phi[i], stream_of(i), runs[i]);
