@@ -349,7 +349,11 @@ long long sp_plan_launch_count(const sp_plan* plan);
  * are kept resident across requests of the same grid (least recently used plans are
  * evicted when memory runs short) and every slot solves on its own clone, so requests
  * that arrive while others run overlap with them on the device.  The device is the
- * current CUDA device at sp_server_create. */
+ * current CUDA device at sp_server_create.  Slots capture the first phase of a mixed
+ * solve into CUDA graphs (sp_plan_set_graphs) on their own threads, so while a server
+ * runs, other threads should synchronise streams or events rather than the whole device:
+ * a device-wide synchronisation (cudaDeviceSynchronize) that meets a capture fails with
+ * cudaErrorStreamCaptureUnsupported. */
 typedef struct sp_server sp_server;
 typedef struct {
     long long completed, failed, queued;

@@ -23,9 +23,11 @@ def S():
 
 
 def alone(S, p, precision):
+    # (the caller's stream only: the server tests call this while slots run, and a
+    # device-wide synchronisation fails when it meets a slot's graph capture)
     plan = S.Plan(p.r_if, p.th_if, p.nphi, outer_bc=p.outer_bc, precision=precision)
     phi, info = plan.solve(torch.from_numpy(p.rho).cuda())
-    torch.cuda.synchronize()
+    torch.cuda.current_stream().synchronize()
     return phi.cpu().numpy(), info
 
 
@@ -135,6 +137,7 @@ def test_server_mix_equals_alone(S):
         p = W.ragged_instance(i % 5)
         prec = S.SP_MIXED_BF16X6 if i % 3 else S.SP_FP64
         specs.append((p, prec))
+    refs = [alone(S, p, prec)[0] for p, prec in specs]   # before the server's threads run
     srv = S.sp_server_create(8 << 30, 4)
     try:
         outs, tickets, keep = [], [], []
@@ -144,10 +147,9 @@ def test_server_mix_equals_alone(S):
             outs.append(out)
             tickets.append(t)
             keep.append(k)
-        for (p, prec), out, t in zip(specs, outs, tickets):
+        for out, t, ref_alone in zip(outs, tickets, refs):
             st, info = S.sp_server_wait(srv, t, 120.0)
             assert st == S.SP_OK
-            ref_alone, _ = alone(S, p, prec)
             assert np.array_equal(out, ref_alone)
         stats = S.sp_server_stats(srv)
         assert stats["completed"] == len(specs) and stats["failed"] == 0
@@ -159,14 +161,14 @@ def test_server_mix_equals_alone(S):
 
 def test_server_evicts_under_a_small_budget(S):
     probs = [W.ragged_instance(i) for i in range(4)]
+    refs = [alone(S, p, S.SP_MIXED_BF16X6)[0] for p in probs]   # before the server's threads run
     srv = S.sp_server_create(256 << 20, 1)   # one slot: plans of earlier grids must make room
     try:
-        for p in probs + probs[:2]:
+        for p, ref_alone in zip(probs + probs[:2], refs + refs[:2]):
             out = np.empty_like(p.rho)
             t, _ = S.sp_server_submit(srv, p.r_if, p.th_if, p.nphi, p.rho, out, precision=S.SP_MIXED_BF16X6)
             st, _ = S.sp_server_wait(srv, t, 120.0)
             assert st == S.SP_OK
-            ref_alone, _ = alone(S, p, S.SP_MIXED_BF16X6)
             assert np.array_equal(out, ref_alone)
         stats = S.sp_server_stats(srv)
         assert stats["evictions"] >= 1
@@ -207,12 +209,12 @@ def test_server_burst_of_mixed_sizes_all_succeed(S):
         for (p, prec, out), t in zip(outs, tickets):
             st, _ = S.sp_server_wait(srv, t, 300.0)
             assert st == S.SP_OK, S.sp_status_string(st)
-        for p, prec, out in outs[:10]:
-            ref_alone, _ = alone(S, p, prec)
-            assert np.array_equal(out, ref_alone)
         assert S.sp_server_stats(srv)["failed"] == 0
     finally:
         S.sp_server_destroy(srv)
+    for p, prec, out in outs[:10]:   # after the server's threads have ended
+        ref_alone, _ = alone(S, p, prec)
+        assert np.array_equal(out, ref_alone)
 
 
 @pytest.mark.parametrize("prec_name", ["SP_MIXED_BF16X6", "SP_MIXED_BF16X3"])
