@@ -64,3 +64,27 @@ def test_residual_fused_with_its_transform():
     assert sum(u.values()) - sum(b.values()) == 8 * Z             # r written and read once each
     b3 = bench.algorithmic_bytes_per_step(grid(), "mixed_x3", iters=3)
     assert b3["residual"] == (12 * Z + 4 * S) + (16 * Z + 4 * S)  # the second reads both words
+
+
+def test_roofline_reports_the_residual_interior_kernel():
+    """The residual's span holds the side stream's shell term and last shell: the line's
+    roofline reports its interior-row kernel, with (Nr-1)/Nr of the residual's bytes, its
+    own live time, and the issue fraction from the instruction count."""
+    p = types.SimpleNamespace(shape=(550, 128, 256))
+    steps = 20
+    timing = {"residual": (0.150 * steps, steps), "residual_rows": (0.120 * steps, steps),
+              "fft_inverse": (0.125 * steps, 2 * steps), "radial_solve": (0.128 * steps, 2 * steps)}
+    r = bench.roofline(timing, p, "mixed", steps, 2, sm_mhz=2000.0, num_sms=152)
+    full = bench.algorithmic_bytes_per_step(p, "mixed", 2)["residual"]
+    assert r["kernel"].startswith("residual_rows")
+    assert abs(r["algorithmic_bytes_per_launch"] - full * 549 / 550) < 1.0
+    assert abs(r["achieved"] - full * 549 / 550 / 0.120e-3 / 1e9) < 1e-6 * r["achieved"]
+    if r.get("issue"):   # only when the ncu table matches the sources
+        assert abs(r["issue"]["frac"] - r["issue"]["warp_instructions_per_launch"] / (4 * 152 * 2000e6 * 0.120e-3)) < 1e-9
+    # without the interior span, the residual's whole span
+    r2 = bench.roofline({"residual": timing["residual"]}, p, "mixed", steps, 2)
+    assert r2["kernel"] == "residual"
+    assert abs(r2["algorithmic_bytes_per_launch"] - full) < 1.0
+    # the interior span is never the dominant group itself
+    r3 = bench.roofline({"residual_rows": (9.0, steps), "fft_inverse": timing["fft_inverse"]}, p, "mixed", steps, 2)
+    assert r3["kernel"] == "fft_inverse"
