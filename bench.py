@@ -401,6 +401,8 @@ def run_ours(args, rank, world, local):
                         "directions and an independent device solve at once (the device-to-host copy "
                         "slows under the solve's memory traffic), the bound a pipelined step meets"},
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in r["timing"].items()},
+        "kernel_ms_note": "per-kernel-group CUDA-event spans of a separate timing pass (kernels launched one "
+                          "by one); residual_rows is the residual's interior-row kernel, a span inside residual",
     }
     for name, rr in results.items():
         line[f"{name}_zones_per_s"] = whole_job_rate(zones, args.steps, world, rr["ms"] / 1e3)
